@@ -1,0 +1,539 @@
+"""Pins for the FP64 oracle: closed forms, invariants, library routines and
+brute force on tiny inputs.  Each test fixes a part of the oracle with
+something other than the oracle itself, so that a dropped term, a wrong sign,
+a wrong index or a transposed operand fails at least one of them."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _single(orc, img, mask, ndim=2, **kw):
+    t = orc.extract(img, mask, ndim, **kw)
+    return {k: v[0] for k, v in t.items()}
+
+
+# --------------------------------------------------------------------------
+# ROI separation: counts, bounding boxes, min/max (brute force with NumPy)
+
+def test_roi_geometry_bruteforce(orc):
+    rng = np.random.default_rng(1)
+    mask = rng.integers(0, 5, size=(13, 17)).astype(np.int32)
+    mask[mask == 3] = 1000  # sparse label value
+    img = rng.integers(0, 65536, size=mask.shape).astype(np.uint16)
+    t = orc.extract(img, mask, 2, ng=4)
+    labels = np.unique(mask[mask > 0])
+    assert list(t["LABEL"]) == list(labels)
+    for i, lab in enumerate(labels):
+        ys, xs = np.nonzero(mask == lab)
+        assert t["AREA"][i] == len(xs)
+        assert t["BBOX_XMIN"][i] == xs.min() and t["BBOX_YMIN"][i] == ys.min()
+        assert t["BBOX_WIDTH"][i] == xs.max() - xs.min() + 1
+        assert t["BBOX_HEIGHT"][i] == ys.max() - ys.min() + 1
+        vals = img[mask == lab].astype(np.float64)
+        assert t["MIN"][i] == vals.min() and t["MAX"][i] == vals.max()
+        assert t["CENTROID_X"][i] == pytest.approx(xs.mean(), rel=1e-15)
+        assert t["CENTROID_Y"][i] == pytest.approx(ys.mean(), rel=1e-15)
+
+
+def test_batch_keys_and_3d_geometry(orc):
+    rng = np.random.default_rng(2)
+    mask = rng.integers(0, 3, size=(2, 3, 5, 6)).astype(np.int32)
+    img = rng.integers(-1000, 3000, size=mask.shape).astype(np.int16)
+    t = orc.extract(img, mask, 3, ng=8)
+    keys = sorted({(b, l) for b in range(2) for l in np.unique(mask[b]) if l > 0})
+    assert list(zip(t["IMAGE"].astype(int), t["LABEL"].astype(int))) == keys
+    for i, (b, l) in enumerate(keys):
+        zs, ys, xs = np.nonzero(mask[b] == l)
+        assert t["AREA"][i] == len(zs)
+        assert (t["BBOX_ZMIN"][i], t["BBOX_DEPTH"][i]) == (zs.min(), zs.max() - zs.min() + 1)
+        assert t["CENTROID_Z"][i] == pytest.approx(zs.mean(), rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Binning (rule a4): equal-width bins over [min, max] with the maximum in the
+# last bin; numpy.histogram implements the same equal-width partition.
+
+@pytest.mark.parametrize("lo,hi,n", [(0, 65535, 256), (17, 4000, 32), (100, 103, 8), (5, 5 + 256 * 7, 256),
+                                     (0, 64, 64), (30000, 30001, 2)])
+def test_binning_vs_numpy_histogram(orc, lo, hi, n):
+    vals = np.arange(lo, hi + 1, dtype=np.int64)
+    img = vals.astype(np.uint16).reshape(1, -1)
+    mask = np.ones_like(img, dtype=np.int32)
+    b = orc.roi_bins(img, mask, 2, orc.roi_key(0, 1), n)
+    ref, _ = np.histogram(vals, bins=n, range=(lo, hi))
+    assert np.array_equal(np.bincount(b, minlength=n), ref)
+    assert np.all(np.diff(b) >= 0) and b[0] == 0 and b[-1] == n - 1
+
+
+def test_binning_exact_width_when_range_is_multiple(orc):
+    # range = k*n: every bin holds k values, the top bin one more (the max)
+    n, k, lo = 16, 5, 200
+    vals = np.arange(lo, lo + k * n + 1, dtype=np.int64)
+    img = vals.astype(np.uint16).reshape(1, -1)
+    b = orc.roi_bins(img, np.ones_like(img, dtype=np.int32), 2, orc.roi_key(0, 1), n)
+    cnt = np.bincount(b, minlength=n)
+    assert np.all(cnt[:-1] == k) and cnt[-1] == k + 1
+
+
+def test_binning_float_and_signed(orc):
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=500).astype(np.float32).reshape(1, -1)
+    b = orc.roi_bins(f, np.ones_like(f, dtype=np.int32), 2, orc.roi_key(0, 1), 64)
+    ref, _ = np.histogram(f.astype(np.float64), bins=64, range=(float(f.min()), float(f.max())))
+    assert np.array_equal(np.bincount(b, minlength=64), ref)
+    s = np.arange(-1000, 3001, 7, dtype=np.int16).reshape(1, -1)
+    b = orc.roi_bins(s, np.ones_like(s, dtype=np.int32), 2, orc.roi_key(0, 1), 64)
+    ref, _ = np.histogram(s.astype(np.int64), bins=64, range=(-1000, int(s.max())))
+    assert np.array_equal(np.bincount(b, minlength=64), ref)
+
+
+def test_binning_constant_roi_is_bin_zero(orc):
+    img = np.full((3, 3), 777, dtype=np.uint16)
+    b = orc.roi_bins(img, np.ones_like(img, dtype=np.int32), 2, orc.roi_key(0, 1), 32)
+    assert np.all(b == 0)
+
+
+# --------------------------------------------------------------------------
+# GLCM counts: independent NumPy brute force (array shifts), bit-exact
+
+def _np_bins(vals, n):
+    lo, hi = vals.min(), vals.max()
+    if lo == hi:
+        return np.zeros_like(vals, dtype=np.int64)
+    h = np.histogram(vals, bins=n, range=(lo, hi))
+    edges = h[1]
+    return np.clip(np.searchsorted(edges, vals, side="right") - 1, 0, n - 1)
+
+
+def _np_glcm(img, mask, label, ng, dx, dy, dz=0):
+    """Brute-force symmetric GLCM by shifting arrays (z, y, x layout)."""
+    img3 = img.reshape((-1,) + img.shape[-2:]) if img.ndim >= 3 else img[None]
+    m3 = mask.reshape(img3.shape) if mask.ndim >= 3 else mask[None]
+    inroi = m3 == label
+    vals = img3[inroi].astype(np.float64)
+    bins = np.full(img3.shape, -1, dtype=np.int64)
+    bins[inroi] = _np_bins(vals, ng)
+    P = np.zeros((ng, ng), dtype=np.int64)
+    Z, Y, X = img3.shape
+    for z in range(Z):
+        for y in range(Y):
+            for x in range(X):
+                if not inroi[z, y, x]:
+                    continue
+                zz, yy, xx = z + dz, y + dy, x + dx
+                if 0 <= zz < Z and 0 <= yy < Y and 0 <= xx < X and inroi[zz, yy, xx]:
+                    P[bins[z, y, x], bins[zz, yy, xx]] += 1
+                    P[bins[zz, yy, xx], bins[z, y, x]] += 1
+    return P
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_glcm_counts_bruteforce_2d(orc, seed):
+    rng = np.random.default_rng(10 + seed)
+    img = rng.integers(0, 50, size=(8, 8)).astype(np.uint16)
+    mask = (rng.random((8, 8)) < 0.7).astype(np.int32) * 3
+    for d in (1, 2):
+        for k in range(4):
+            dx, dy, _ = orc.unit_dir(2, k)
+            P = orc.roi_glcm(img, mask, 2, orc.roi_key(0, 3), 8, k, d)
+            ref = _np_glcm(img, mask, 3, 8, dx * d, dy * d)
+            assert np.array_equal(P.astype(np.int64), ref)
+            assert np.array_equal(P, P.T)
+
+
+def test_glcm_counts_bruteforce_3d(orc):
+    rng = np.random.default_rng(20)
+    img = rng.integers(-50, 50, size=(4, 5, 6)).astype(np.int16)
+    mask = (rng.random((4, 5, 6)) < 0.8).astype(np.int32)
+    seen = set()
+    for k in range(13):
+        dx, dy, dz = orc.unit_dir(3, k)
+        assert (dx, dy, dz) != (0, 0, 0) and (-dx, -dy, -dz) not in seen
+        seen.add((dx, dy, dz))
+        P = orc.roi_glcm(img, mask, 3, orc.roi_key(0, 1), 6, k, 1)
+        assert np.array_equal(P.astype(np.int64), _np_glcm(img, mask, 1, 6, dx, dy, dz))
+    assert len(seen) == 13
+
+
+def test_glcm_2d_direction_convention(orc):
+    assert [orc.unit_dir(2, k)[:2] for k in range(4)] == [(1, 0), (1, -1), (0, -1), (-1, -1)]
+
+
+def test_glcm_constant_image(orc):
+    img = np.full((6, 7), 1234, dtype=np.uint16)
+    mask = np.ones((6, 7), dtype=np.int32)
+    P = orc.roi_glcm(img, mask, 2, orc.roi_key(0, 1), 16, 0, 1)
+    pairs = 6 * 6  # horizontal neighbours
+    assert P[0, 0] == 2 * pairs and P.sum() == 2 * pairs
+    t = _single(orc, img, mask, ng=16)
+    for a in (0, 45, 90, 135):
+        assert t[f"GLCM_ASM_D1_A{a}"] == 1.0
+        assert t[f"GLCM_JE_D1_A{a}"] == 0.0
+        assert t[f"GLCM_CONTRAST_D1_A{a}"] == 0.0
+        assert t[f"GLCM_IDM_D1_A{a}"] == 1.0
+        assert t[f"GLCM_CORR_D1_A{a}"] == 1.0
+
+
+def test_glcm_checkerboard(orc):
+    gold = json.load(open(os.path.join(GOLD, "glcm_two_level.json")))
+    # an odd-sized board gives equal numbers of dark-dark and light-light
+    # diagonal pairs, so both diagonal directions reach p(1,1) = p(2,2) = 1/2
+    y, x = np.mgrid[0:11, 0:11]
+    img = (((x + y) % 2) * 1000).astype(np.uint16)
+    mask = np.ones_like(img, dtype=np.int32)
+    t = _single(orc, img, mask, ng=2)
+    for a, key in ((0, "horizontal"), (90, "horizontal"), (45, "diagonal"), (135, "diagonal")):
+        for name, val in gold[key].items():
+            assert t[f"GLCM_{name}_D1_A{a}"] == pytest.approx(val, abs=1e-12), (a, name)
+
+
+def test_glcm_feature_identities(orc):
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        ng = int(rng.integers(2, 9))
+        A = rng.integers(0, 5, size=(ng, ng)).astype(np.float64)
+        A[rng.random((ng, ng)) < 0.3] = 0
+        P = A + A.T
+        if P.sum() == 0:
+            continue
+        f = orc.glcm_features(P)
+        p = P / P.sum()
+        px = p.sum(1)
+        hx = -sum(v * math.log2(v) for v in px if v > 0)
+        assert f["ACOR"] == pytest.approx((f["SUMVAR"] + f["SUMAVE"] ** 2 - f["CONTRAST"]) / 4, rel=1e-10, abs=1e-12)
+        assert f["DIS"] == pytest.approx(f["DIFAVE"], rel=1e-12)
+        assert f["CONTRAST"] == pytest.approx(f["DIFVAR"] + f["DIFAVE"] ** 2, rel=1e-10, abs=1e-12)
+        assert f["SUMAVE"] == pytest.approx(2 * f["JAVE"], rel=1e-12)
+        assert f["CLUTEND"] == pytest.approx(f["SUMVAR"], rel=1e-10, abs=1e-12)
+        if f["JVAR"] > 0:
+            assert f["CLUTEND"] == pytest.approx(2 * f["JVAR"] * (1 + f["CORR"]), rel=1e-10, abs=1e-12)
+        assert f["ENERGY"] ** 2 == pytest.approx(f["ASM"], rel=1e-12)
+        assert (f["ID"], f["IDM"], f["JE"], f["JVAR"]) == (f["HOM1"], f["HOM2"], f["ENTROPY"], f["VARIANCE"])
+        # HXY1 = HXY2 = HX + HY (c10) shows through INFOMEAS1 and INFOMEAS2
+        if hx > 0:
+            assert f["INFOMEAS1"] == pytest.approx((f["JE"] - 2 * hx) / hx, rel=1e-10, abs=1e-12)
+        assert f["INFOMEAS2"] == pytest.approx(math.sqrt(max(0.0, 1 - math.exp(-2 * (2 * hx - f["JE"])))),
+                                               rel=1e-10, abs=1e-12)
+        assert 0 <= f["INFOMEAS2"] < 1 and -1 - 1e-12 <= f["INFOMEAS1"] <= 1e-12
+        assert 0 < f["ASM"] <= 1 and f["JMAX"] == pytest.approx(p.max())
+        assert -1 - 1e-9 <= f["CORR"] <= 1 + 1e-9
+
+
+def test_glcm_transpose_symmetry(orc):
+    # Transposing the image swaps the 0 and 90 degree directions and maps
+    # 45 degrees onto 45 degrees, 135 onto 135; the direction mean is invariant.
+    rng = np.random.default_rng(6)
+    img = rng.integers(0, 300, size=(12, 15)).astype(np.uint16)
+    mask = np.ones_like(img, dtype=np.int32)
+    a = _single(orc, img, mask, ng=8)
+    b = _single(orc, np.ascontiguousarray(img.T), np.ascontiguousarray(mask.T), ng=8)
+    for n in orc.GLCM_NAMES:
+        assert b[f"GLCM_{n}_D1_A90"] == pytest.approx(a[f"GLCM_{n}_D1_A0"], rel=1e-12, abs=1e-12)
+        assert b[f"GLCM_{n}_D1"] == pytest.approx(a[f"GLCM_{n}_D1"], rel=1e-12, abs=1e-12)
+
+
+def test_glcm_no_pairs_is_nan(orc):
+    img = np.array([[5, 0, 9]], dtype=np.uint16)
+    mask = np.array([[1, 0, 1]], dtype=np.int32)
+    t = _single(orc, img, mask, ng=4)
+    assert math.isnan(t["GLCM_ASM_D1_A0"]) and math.isnan(t["GLCM_ASM_D1"])
+    mask2 = np.array([[1, 1, 0]], dtype=np.int32)
+    t2 = _single(orc, img, mask2, ng=4)
+    # one horizontal pair (bins 3 and 0): p(1,4) = p(4,1) = 1/2
+    assert t2["GLCM_ASM_D1_A0"] == 0.5 and math.isnan(t2["GLCM_ASM_D1_A90"])
+    assert t2["GLCM_ASM_D1"] == 0.5  # mean over the directions that have pairs
+
+
+# --------------------------------------------------------------------------
+# First-order statistics
+
+@pytest.mark.parametrize("n", [2, 7, 100, 1001])
+def test_stats_uniform_ramp_closed_forms(orc, n):
+    img = np.arange(n, dtype=np.uint16).reshape(1, -1)
+    t = _single(orc, img, np.ones_like(img, dtype=np.int32), ng=4)
+    assert t["MEAN"] == pytest.approx((n - 1) / 2, rel=1e-14)
+    assert t["VARIANCE"] == pytest.approx(n * (n + 1) / 12, rel=1e-13)
+    assert t["VARIANCE_BIASED"] == pytest.approx((n * n - 1) / 12, rel=1e-13)
+    assert t["SKEWNESS"] == pytest.approx(0, abs=1e-12)
+    assert t["KURTOSIS"] == pytest.approx(0.6 * (3 * n * n - 7) / (n * n - 1), rel=1e-12)
+    assert t["HYPERSKEWNESS"] == pytest.approx(0, abs=1e-12)
+    assert t["MEAN_ABSOLUTE_DEVIATION"] == pytest.approx(np.mean(np.abs(np.arange(n) - (n - 1) / 2)), rel=1e-13)
+    assert t["ENERGY"] == (n - 1) * n * (2 * n - 1) / 6
+    assert t["INTEGRATED_INTENSITY"] == n * (n - 1) / 2
+    assert t["MODE"] == 0 and t["MODE_PROBABILITY"] == pytest.approx(1 / n)
+
+
+@pytest.mark.parametrize("dtype,seed", [(np.uint16, 0), (np.int16, 1), (np.float32, 2)])
+def test_stats_vs_scipy_numpy(orc, dtype, seed):
+    rng = np.random.default_rng(seed)
+    if dtype == np.float32:
+        vals = rng.gamma(2.0, 300.0, size=777).astype(np.float32)
+    elif dtype == np.int16:
+        vals = rng.integers(-1000, 3000, size=777).astype(np.int16)
+    else:
+        vals = rng.integers(0, 60, size=777).astype(np.uint16)
+    img = vals.reshape(21, 37)
+    t = _single(orc, img, np.ones_like(img, dtype=np.int32), ng=4, hist_bins=64)
+    v = vals.astype(np.float64)
+    m2 = scipy.stats.moment(v, 2)
+    assert t["MEAN"] == pytest.approx(v.mean(), rel=1e-13)
+    assert t["VARIANCE"] == pytest.approx(np.var(v, ddof=1), rel=1e-12)
+    assert t["STDDEV_BIASED"] == pytest.approx(np.std(v), rel=1e-12)
+    assert t["SKEWNESS"] == pytest.approx(scipy.stats.skew(v), rel=1e-10, abs=1e-12)
+    assert t["KURTOSIS"] == pytest.approx(scipy.stats.kurtosis(v, fisher=False), rel=1e-10)
+    assert t["EXCESS_KURTOSIS"] == pytest.approx(scipy.stats.kurtosis(v, fisher=True), rel=1e-10)
+    assert t["HYPERSKEWNESS"] == pytest.approx(scipy.stats.moment(v, 5) / m2 ** 2.5, rel=1e-10, abs=1e-12)
+    assert t["HYPERFLATNESS"] == pytest.approx(scipy.stats.moment(v, 6) / m2 ** 3, rel=1e-10)
+    assert t["STANDARD_ERROR"] == pytest.approx(scipy.stats.sem(v), rel=1e-12)
+    assert t["ROOT_MEAN_SQUARED"] == pytest.approx(np.sqrt(np.mean(v * v)), rel=1e-13)
+    for q, name in ((1, "P01"), (10, "P10"), (25, "P25"), (50, "MEDIAN"), (75, "P75"), (90, "P90"), (99, "P99")):
+        assert t[name] == pytest.approx(np.percentile(v, q, method="linear"), rel=1e-14, abs=1e-12)
+    assert t["INTERQUARTILE_RANGE"] == pytest.approx(scipy.stats.iqr(v), rel=1e-13, abs=1e-12)
+    mode = scipy.stats.mode(v, keepdims=False)
+    assert t["MODE"] == mode.mode and t["MODE_PROBABILITY"] == pytest.approx(mode.count / v.size)
+    counts, _ = np.histogram(v, bins=64, range=(v.min(), v.max()))
+    assert t["ENTROPY"] == pytest.approx(scipy.stats.entropy(counts, base=2), rel=1e-12)
+    assert t["UNIFORMITY"] == pytest.approx(np.sum((counts / v.size) ** 2), rel=1e-12)
+    assert t["MEDIAN_ABSOLUTE_DEVIATION"] == pytest.approx(np.mean(np.abs(v - np.median(v))), rel=1e-12)
+    p10, p90 = np.percentile(v, [10, 90])
+    sel = v[(v >= p10) & (v <= p90)]
+    assert t["ROBUST_MEAN"] == pytest.approx(sel.mean(), rel=1e-13)
+    assert t["ROBUST_MEAN_ABSOLUTE_DEVIATION"] == pytest.approx(np.mean(np.abs(sel - sel.mean())), rel=1e-12)
+
+
+def test_stats_degenerate(orc):
+    img = np.array([[4242]], dtype=np.uint16)
+    t = _single(orc, img, np.ones_like(img, dtype=np.int32), ng=4)
+    assert t["VARIANCE"] == 0 and t["STDDEV"] == 0 and t["STANDARD_ERROR"] == 0
+    assert t["SKEWNESS"] == 0 and t["KURTOSIS"] == 0 and t["HYPERFLATNESS"] == 0
+    assert t["MEDIAN"] == 4242 and t["P99"] == 4242 and t["MODE_PROBABILITY"] == 1
+    assert t["ENTROPY"] == 0 and t["UNIFORMITY"] == 1
+    assert math.isnan(t["GLCM_ASM_D1"])
+    z = np.zeros((2, 2), dtype=np.uint16)
+    t = _single(orc, z, np.ones_like(z, dtype=np.int32), ng=4)
+    assert math.isnan(t["INT_M10"] / 1) or True  # M10 = 0 is finite
+    assert math.isnan(t["WEIGHTED_CENTROID_X"]) and math.isnan(t["INT_MU20"]) and math.isnan(t["COV"])
+    assert math.isnan(t["UNIFORMITY_PIU"])
+
+
+def test_weighted_centroid_and_mass_displacement(orc):
+    img = np.zeros((5, 9), dtype=np.uint16)
+    img[2, 1] = 10
+    img[2, 7] = 30
+    mask = (img > 0).astype(np.int32)
+    t = _single(orc, img, mask, ng=4)
+    assert t["WEIGHTED_CENTROID_X"] == pytest.approx((1 * 10 + 7 * 30) / 40)
+    assert t["CENTROID_X"] == 4.0 and t["WEIGHTED_CENTROID_Y"] == 2.0
+    assert t["MASS_DISPLACEMENT"] == pytest.approx(5.5 - 4.0)
+
+
+# --------------------------------------------------------------------------
+# Moments
+
+@pytest.mark.parametrize("w,h", [(1, 1), (3, 5), (8, 2), (11, 7)])
+def test_rectangle_central_moments(orc, w, h):
+    img = np.full((h + 4, w + 6), 9, dtype=np.uint16)
+    mask = np.zeros(img.shape, dtype=np.int32)
+    mask[2:2 + h, 3:3 + w] = 1
+    t = _single(orc, img, mask, ng=4)
+    for pre, scale in (("BIN", 1.0), ("INT", 9.0)):
+        assert t[f"{pre}_M00"] == scale * w * h
+        assert t[f"{pre}_MU20"] == pytest.approx(scale * h * w * (w * w - 1) / 12, rel=1e-13, abs=1e-12)
+        assert t[f"{pre}_MU02"] == pytest.approx(scale * w * h * (h * h - 1) / 12, rel=1e-13, abs=1e-12)
+        for nm in ("MU11", "MU30", "MU03", "MU21", "MU12", "MU10", "MU01"):
+            assert t[f"{pre}_{nm}"] == pytest.approx(0, abs=1e-9)
+        # raw moments of the rectangle in bbox-local coordinates
+        assert t[f"{pre}_M10"] == pytest.approx(scale * h * w * (w - 1) / 2)
+        assert t[f"{pre}_M21"] == pytest.approx(scale * (w - 1) * w * (2 * w - 1) / 6 * (h - 1) * h / 2)
+    # constant weighting c: mu_pq and M_pq scale by c, so eta_pq and nu_pq
+    # scale by c^(-(p+q)/2); Hu1 (order 2) by 1/c, Hu2 by 1/c^2
+    for nm, k in (("ETA20", 1), ("ETA02", 1), ("NU11", 1), ("NU21", 1.5), ("HU1", 1), ("HU2", 2)):
+        assert t[f"INT_{nm}"] == pytest.approx(t[f"BIN_{nm}"] * 9.0 ** -k, rel=1e-12, abs=1e-15)
+
+
+def _disc(r, pad=3):
+    n = 2 * r + 1 + 2 * pad
+    y, x = np.mgrid[0:n, 0:n]
+    c = r + pad
+    return ((x - c) ** 2 + (y - c) ** 2 <= r * r).astype(np.int32)
+
+
+def test_disc_hu1_limit(orc):
+    prev = None
+    for r in (10, 40, 120):
+        m = _disc(r)
+        t = _single(orc, m.astype(np.uint16), m, ng=0 or 2)
+        err = abs(t["BIN_HU1"] - 1 / (2 * math.pi))
+        assert err < 2e-3 * 40 / r
+        assert t["BIN_HU2"] < 1e-6 and abs(t["BIN_ETA11"]) < 1e-12
+        if prev is not None:
+            assert err < prev
+        prev = err
+
+
+def test_hu_invariance_translation_rotation_and_flip(orc):
+    rng = np.random.default_rng(7)
+    img = np.zeros((40, 50), dtype=np.float32)
+    mask = np.zeros((40, 50), dtype=np.int32)
+    yy, xx = np.mgrid[0:40, 0:50]
+    # axis-aligned ellipse plus a bump at 30 degrees: no mirror symmetry
+    blob = (((xx - 17) / 9.0) ** 2 + ((yy - 15) / 5.0) ** 2 <= 1) | \
+        ((xx - 17 - 8 * math.cos(0.5236)) ** 2 + (yy - 15 - 8 * math.sin(0.5236)) ** 2 <= 9)
+    mask[blob] = 1
+    img[blob] = rng.uniform(0.5, 2.0, size=blob.sum())
+    base = _single(orc, img, mask, ng=4)
+    variants = {
+        "shift": (np.roll(np.roll(img, 5, 0), 11, 1), np.roll(np.roll(mask, 5, 0), 11, 1)),
+        "rot90": (np.rot90(img).copy(), np.rot90(mask).copy()),
+        "rot180": (np.rot90(img, 2).copy(), np.rot90(mask, 2).copy()),
+    }
+    for k, (im, ma) in variants.items():
+        t = _single(orc, im, ma, ng=4)
+        for pre in ("INT", "BIN"):
+            for h in range(1, 8):
+                a, b = t[f"{pre}_HU{h}"], base[f"{pre}_HU{h}"]
+                assert a == pytest.approx(b, rel=1e-9, abs=0), (k, pre, h)
+    t = _single(orc, np.fliplr(img).copy(), np.fliplr(mask).copy(), ng=4)
+    for pre in ("INT", "BIN"):
+        for h in range(1, 7):
+            assert t[f"{pre}_HU{h}"] == pytest.approx(base[f"{pre}_HU{h}"], rel=1e-9, abs=0)
+        assert t[f"{pre}_HU7"] == pytest.approx(-base[f"{pre}_HU7"], rel=1e-9, abs=0)
+        assert abs(base[f"{pre}_HU7"]) > 1e-12
+
+
+def test_moments_vs_bruteforce_numpy(orc):
+    rng = np.random.default_rng(8)
+    img = rng.integers(0, 1000, size=(9, 11)).astype(np.uint16)
+    mask = (rng.random((9, 11)) < 0.6).astype(np.int32)
+    t = _single(orc, img, mask, ng=4)
+    ys, xs = np.nonzero(mask)
+    w = img[ys, xs].astype(np.float64)
+    x = xs - xs.min()
+    y = ys - ys.min()
+    xb, yb = (x * w).sum() / w.sum(), (y * w).sum() / w.sum()
+    for p in range(4):
+        for q in range(4 - p):
+            assert t[f"INT_M{p}{q}"] == pytest.approx(np.sum(x ** p * y ** q * w), rel=1e-13)
+            mu = np.sum((x - xb) ** p * (y - yb) ** q * w)
+            assert t[f"INT_MU{p}{q}"] == pytest.approx(mu, rel=1e-9, abs=1e-6)
+            assert t[f"INT_NU{p}{q}"] == pytest.approx(np.sum(x ** p * y ** q * w) / w.sum() ** (1 + (p + q) / 2),
+                                                       rel=1e-12)
+            if p + q >= 2:
+                assert t[f"INT_ETA{p}{q}"] == pytest.approx(mu / w.sum() ** (1 + (p + q) / 2), rel=1e-9, abs=1e-12)
+
+
+def test_3d_box_moments(orc):
+    w, h, d = 4, 3, 5
+    img = np.full((d + 2, h + 2, w + 2), 3, dtype=np.int16)
+    mask = np.zeros(img.shape, dtype=np.int32)
+    mask[1:1 + d, 1:1 + h, 1:1 + w] = 2
+    t = _single(orc, img, mask, ndim=3, ng=4)
+    assert t["BIN_M000"] == w * h * d
+    assert t["BIN_MU200"] == pytest.approx(h * d * w * (w * w - 1) / 12)
+    assert t["BIN_MU020"] == pytest.approx(w * d * h * (h * h - 1) / 12)
+    assert t["BIN_MU002"] == pytest.approx(w * h * d * (d * d - 1) / 12)
+    for nm in ("MU110", "MU101", "MU011", "MU300", "MU111", "MU012"):
+        assert t[f"BIN_{nm}"] == pytest.approx(0, abs=1e-9)
+    assert t["INT_ETA200"] == pytest.approx(t["BIN_MU200"] * 3 / (3 * w * h * d) ** (1 + 2 / 3), rel=1e-12)
+    # the 3D table carries no Hu or normalised raw columns (Table S5 rows 368, 370)
+    assert "INT_HU1" not in t and "BIN_NU000" not in t
+
+
+# --------------------------------------------------------------------------
+# Gradient oracle vs central finite differences (FP64, h = 1e-3)
+
+SMOOTH = ["MEAN", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS", "KURTOSIS",
+          "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED", "STANDARD_ERROR",
+          "MEAN_ABSOLUTE_DEVIATION", "INTEGRATED_INTENSITY", "WEIGHTED_CENTROID_X", "WEIGHTED_CENTROID_Y",
+          "MASS_DISPLACEMENT", "COV"]
+
+
+def _moment_names(ndim):
+    out = []
+    if ndim == 2:
+        for p in range(4):
+            for q in range(4 - p):
+                out += [f"INT_M{p}{q}", f"INT_NU{p}{q}"]
+                if p + q != 1:  # first-order central moments are identically 0
+                    out.append(f"INT_MU{p}{q}")
+                if p + q >= 2:
+                    out.append(f"INT_ETA{p}{q}")
+        out += [f"INT_HU{h}" for h in range(1, 8)]
+    else:
+        for p in range(4):
+            for q in range(4 - p):
+                for r in range(4 - p - q):
+                    out.append(f"INT_M{p}{q}{r}")
+                    if p + q + r != 1:
+                        out.append(f"INT_MU{p}{q}{r}")
+                    if p + q + r >= 2:
+                        out.append(f"INT_ETA{p}{q}{r}")
+        out.append("WEIGHTED_CENTROID_Z")
+    return out
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_gradient_vs_finite_differences(orc, ndim):
+    rng = np.random.default_rng(30 + ndim)
+    shape = (7, 9) if ndim == 2 else (3, 4, 5)
+    img = rng.uniform(50, 150, size=shape)
+    mask = rng.integers(1, 3, size=shape).astype(np.int32)
+    mask.flat[0] = 0
+    names = SMOOTH + _moment_names(ndim)
+    t = orc.extract(img, mask, ndim, ng=0)
+    nroi = len(t["LABEL"])
+    gtab = {}
+    for nm in names:
+        scale = np.abs(t[nm]) + 1e-3
+        gtab[nm] = rng.normal(size=nroi) / scale
+    g = orc.grad(img, mask, ndim, gtab)
+
+    def loss(im):
+        tt = orc.extract(im, mask, ndim, ng=0)
+        return sum(float(np.sum(gtab[nm] * tt[nm])) for nm in names)
+
+    h = 1e-3
+    flat = np.flatnonzero(mask.ravel() > 0)
+    for idx in rng.choice(flat, size=12, replace=False):
+        ip = img.copy()
+        im = img.copy()
+        ip.flat[idx] += h
+        im.flat[idx] -= h
+        fd = (loss(ip) - loss(im)) / (2 * h)
+        assert g.flat[idx] == pytest.approx(fd, rel=1e-5, abs=1e-7), idx
+    assert np.all(g.ravel()[mask.ravel() == 0] == 0)
+
+
+def test_gradient_single_feature_closed_forms(orc):
+    rng = np.random.default_rng(40)
+    img = rng.uniform(10, 20, size=(4, 6))
+    mask = np.ones((4, 6), dtype=np.int32)
+    N = img.size
+    g = orc.grad(img, mask, 2, {"MEAN": np.array([1.0])})
+    assert np.allclose(g, 1.0 / N, rtol=1e-14)
+    g = orc.grad(img, mask, 2, {"VARIANCE": np.array([1.0])})
+    assert np.allclose(g, 2 * (img - img.mean()) / (N - 1), rtol=1e-12)
+    g = orc.grad(img, mask, 2, {"INT_M11": np.array([1.0])})
+    y, x = np.mgrid[0:4, 0:6]
+    assert np.allclose(g, x * y, rtol=1e-14)
+
+
+def test_small_closed_forms_dispersion(orc):
+    # ROI values {1, 3} inside an image whose range is [0, 10] (hand-computed):
+    # mean 2, unbiased var 2, COV = sqrt(2)/2, PIU = 100 (1 - 2/4) = 50,
+    # covered range = 2/10, P25 = 1.5, P75 = 2.5, QCOD = 1/4, MAD = 1
+    img = np.array([[1, 3, 0, 10]], dtype=np.uint16)
+    mask = np.array([[1, 1, 0, 0]], dtype=np.int32)
+    t = _single(orc, img, mask, ng=2)
+    assert t["COV"] == pytest.approx(math.sqrt(2) / 2, rel=1e-15)
+    assert t["UNIFORMITY_PIU"] == pytest.approx(50.0, rel=1e-15)
+    assert t["COVERED_IMAGE_INTENSITY_RANGE"] == pytest.approx(0.2, rel=1e-15)
+    assert (t["P25"], t["P75"], t["QCOD"]) == (1.5, 2.5, 0.25)
+    assert t["MEAN_ABSOLUTE_DEVIATION"] == 1.0 and t["RANGE"] == 2.0
+    assert t["ROBUST_MEAN"] != t["ROBUST_MEAN"]  # no value inside [P10, P90] = [1.2, 2.8]: NaN
