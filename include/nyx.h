@@ -1,0 +1,193 @@
+/*
+ * nyx.h -- C ABI of the GB300 per-ROI feature-extraction library (libnyxgpu).
+ *
+ * The operation (arxiv 2603.12016, "Nyxus", section "Nyxus architecture" and
+ * "Feature Control and Tunability"): given an intensity image and an integer
+ * label mask of the same shape, separate the pixels of every labelled region
+ * of interest (ROI) and compute, per ROI, a selected set of features --
+ * first-order intensity statistics (Table S1 / S5), raw, central and
+ * normalised geometric moments with Hu invariants (Table S2 rows 123-135,
+ * Table S5 rows 368/370) and grey-level co-occurrence (GLCM) features (Table
+ * S3 rows 140-174, Table S5 row 361) -- under hyperparameters chosen by the
+ * caller (grey depth g, offsets s, histogram bins h of the O(m,h) and
+ * O(m,g,s) cost model).  The result is one FP64 row per ROI.
+ *
+ * Conventions shared by every call:
+ *   - Device pointers ("d_" prefix) are owned by the caller and must stay
+ *     valid until the stream has passed the end of the call.  The library
+ *     never frees or retains them.
+ *   - Calls are stream-ordered on the `stream` argument (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream) and asynchronous unless
+ *     stated otherwise.
+ *   - Every call returns a nyx_status.  No C++ exception crosses the ABI.
+ *     Errors found on the device (negative label, non-finite float pixel
+ *     inside an ROI, capacity overflow) are recorded in a device error word
+ *     and reported by nyx_sync_status() or by a call made with NYX_SYNC.
+ *   - A context (nyx_ctx) and its plans may be used from one host thread at
+ *     a time.
+ */
+#ifndef NYX_H_
+#define NYX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NYX_ABI_VERSION 1
+
+typedef enum {
+  NYX_OK = 0,
+  NYX_ERR_ARG = 1,        /* null pointer, out-of-range parameter, misaligned pointer */
+  NYX_ERR_DTYPE = 2,      /* unsupported pixel dtype */
+  NYX_ERR_SHAPE = 3,      /* dims / batch inconsistent or too large */
+  NYX_ERR_BAD_LABEL = 4,  /* a negative label in the mask */
+  NYX_ERR_NONFINITE = 5,  /* NaN or Inf float pixel inside an ROI */
+  NYX_ERR_CAPACITY = 6,   /* more ROIs than cap_roi / plan max_rois, or an ROI beyond the size limits */
+  NYX_ERR_CUDA = 7,       /* a CUDA runtime call failed (message in nyx_last_error) */
+  NYX_ERR_OOM = 8,        /* device allocation of the plan workspace failed */
+  NYX_ERR_TIMEOUT = 9,    /* a bounded device wait ran out */
+  NYX_ERR_STATE = 10      /* call out of order (e.g. backward without a saved forward) */
+} nyx_status;
+
+typedef enum { NYX_U16 = 0, NYX_I16 = 1, NYX_F32 = 2 } nyx_dtype;
+
+/* Arithmetic of the per-pixel accumulations.  FP32_COMP: FP32 partial sums
+ * merged with two-sum compensation, centred at a pass-1 reference, FP64 only
+ * for per-ROI normalisation.  FP64_PLAIN: the same per-ROI algorithm with
+ * FP64 accumulation throughout (the in-repo comparison path). */
+typedef enum { NYX_PREC_FP32_COMP = 0, NYX_PREC_FP64_PLAIN = 1 } nyx_prec;
+
+/* Flags of nyx_extract. */
+#define NYX_SAVE_FOR_BACKWARD 1u /* keep per-ROI state for nyx_backward */
+#define NYX_SYNC 2u              /* synchronise the stream and return the device error word */
+
+/* Hyperparameters of one plan.  POD; set struct_size = sizeof(nyx_params)
+ * (ABI versioning).  Zero-initialise and fill; nyx_params_default() gives the
+ * untargeted default profile. */
+typedef struct {
+  uint32_t struct_size;
+  int32_t ndim;              /* 2 or 3 spatial dimensions */
+  int64_t dims[3];           /* (x, y, z) extent of ONE image; z = 1 for 2D.  Row-major
+                                [batch][z][y][x], dense (pitch = x) */
+  int32_t batch;             /* images of identical shape stored back to back (>= 1) */
+  int32_t dtype;             /* nyx_dtype */
+  uint64_t feature_mask[4];  /* bit i selects feature id i (nyx_feature_id); all ones =
+                                untargeted extraction, a subset = targeted */
+  int32_t glcm_levels;       /* grey levels Ng of the GLCM quantisation, 2..256 (0 = no GLCM) */
+  int32_t n_dist;            /* number of GLCM distances (1..8) */
+  int32_t dists[8];          /* GLCM distances (Chebyshev), each 1..8 */
+  int32_t glcm_per_offset_cols; /* 0: mean over directions per distance; 1: also one column
+                                   per (distance, direction) */
+  int32_t hist_bins;         /* bins of the entropy / uniformity histogram, 2..4096 */
+  int32_t precision;         /* nyx_prec */
+  int64_t max_rois;          /* upper bound on ROIs per call (sizes the workspace) */
+} nyx_params;
+
+typedef struct nyx_ctx nyx_ctx;
+typedef struct nyx_plan nyx_plan;
+
+/* Fill *p with the default untargeted profile for a 2D uint16 image of the
+ * given extent: all features, Ng = 64, distance 1, 256 histogram bins,
+ * FP32_COMP, max_rois = 65536.  Always succeeds for non-null p. */
+nyx_status nyx_params_default(nyx_params* p, int64_t nx, int64_t ny);
+
+/* Create a context bound to CUDA device `device`.  *out owns only library
+ * state.  Errors: NYX_ERR_ARG (null out), NYX_ERR_CUDA (bad device). */
+nyx_status nyx_create(nyx_ctx** out, int device);
+void nyx_destroy(nyx_ctx* ctx);
+
+/* Message of the last failing call on this context (static storage owned by
+ * the context, valid until the next call on it). */
+const char* nyx_last_error(const nyx_ctx* ctx);
+
+/* Validate params and allocate the plan's device workspace (hash tables,
+ * per-ROI state, accumulators), sized by dims, batch and max_rois.  The plan
+ * owns its workspace and frees it in nyx_plan_destroy.
+ * Errors: NYX_ERR_ARG / NYX_ERR_DTYPE / NYX_ERR_SHAPE (params), NYX_ERR_OOM. */
+nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** out);
+void nyx_plan_destroy(nyx_plan* plan);
+
+/* Number of FP64 columns of one output row, and the name of column `col`
+ * (NUL-terminated, truncated to cap).  Column order: LABEL, IMAGE, AREA,
+ * bounding box, centroid, then the selected features in feature-id order;
+ * GLCM features expand to one column per distance (suffix _D<d>) and, when
+ * glcm_per_offset_cols = 1, one per direction (_A<deg> in 2D, _O<k> in 3D). */
+nyx_status nyx_num_columns(const nyx_plan* plan, int* n_col);
+nyx_status nyx_column_name(const nyx_plan* plan, int col, char* buf, size_t cap);
+
+/* Feature id of a feature name (e.g. "MEAN", "INT_HU", "GLCM_CONTRAST"), -1
+ * if unknown.  Moment families are one id each (INT_M, INT_MU, INT_ETA,
+ * INT_NU, INT_HU and the BIN_ variants). */
+int nyx_feature_id(const char* name);
+
+/* Run the label scan only and return the number of ROIs (distinct
+ * (image, label > 0) pairs) in *n_roi.  Synchronises `stream` (reads 8 bytes
+ * back).  d_img: dims x batch pixels of params.dtype; d_mask: int32, same
+ * shape; both 16-byte aligned.  Errors: NYX_ERR_ARG, NYX_ERR_BAD_LABEL,
+ * NYX_ERR_CAPACITY (more than max_rois), NYX_ERR_CUDA. */
+nyx_status nyx_count_rois(nyx_plan* plan, const void* d_img, const int32_t* d_mask, int64_t* n_roi,
+                          void* stream);
+
+/* Extract the feature table.  Rows are the ROIs in ascending
+ * (image, label) order.  d_table: caller-allocated FP64 [cap_roi x n_col],
+ * row-major; rows >= n_roi are left untouched.  d_n_roi: device int64
+ * receiving the ROI count (may be NULL).  flags: NYX_SAVE_FOR_BACKWARD,
+ * NYX_SYNC.  Without NYX_SYNC the call is asynchronous and device-detected
+ * errors surface at the next nyx_sync_status().
+ * Errors: NYX_ERR_ARG (null/misaligned pointers, cap_roi < 0), NYX_ERR_STATE
+ * (plan busy), NYX_ERR_CUDA; with NYX_SYNC also the device-detected codes. */
+nyx_status nyx_extract(nyx_plan* plan, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
+                       int64_t* d_n_roi, uint32_t flags, void* stream);
+
+/* Synchronise `stream` and return the device error word of the plan's last
+ * calls as a status (NYX_OK if clean); clears the word. */
+nyx_status nyx_sync_status(nyx_plan* plan, void* stream);
+
+/* Backward pass of the smooth intensity features (first-order statistics
+ * except order statistics, weighted centroids, mass displacement and every
+ * intensity-weighted moment) with respect to the pixel intensities: given
+ * dL/dF for every output cell (d_grad_table, FP64 [n_roi x n_col], same
+ * layout as the last nyx_extract made with NYX_SAVE_FOR_BACKWARD), write
+ * dL/dI for every pixel to d_grad_img (FP32, image shape; 0 outside ROIs).
+ * Non-smooth columns (min/max, order statistics, histogram, GLCM, binary
+ * moments, geometry) contribute nothing.  Not in the paper: it makes the
+ * features usable as a differentiable layer for the AI/ML use the paper's
+ * introduction motivates.  Errors: NYX_ERR_STATE (no saved forward),
+ * NYX_ERR_ARG, NYX_ERR_CUDA. */
+nyx_status nyx_backward(nyx_plan* plan, const void* d_img, const int32_t* d_mask, const double* d_grad_table,
+                        float* d_grad_img, void* stream);
+
+/* Test hook: GLCM counts of ROI row `roi` (0-based, ascending key order) for
+ * offset index `off` (distance index * n_directions + direction) as found by
+ * the last nyx_extract, written densely to h_counts (host, uint32 [Ng x Ng],
+ * symmetric).  Requires that nyx_debug_select(plan, roi) preceded that
+ * extract.  Synchronises. */
+nyx_status nyx_debug_select(nyx_plan* plan, int64_t roi);
+nyx_status nyx_debug_glcm(nyx_plan* plan, int off, uint32_t* h_counts);
+
+/* Test hook: per-pixel GLCM bin index (rule: b = floor(Ng (x - min)/(max - min)),
+ * clamped to Ng-1, per-ROI min/max; 0xFFFF outside ROIs) of the last
+ * extract's image, written to d_bins (device uint16, image shape). */
+nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_mask, uint16_t* d_bins,
+                          void* stream);
+
+/* Profiling hook (not in the paper): with `slots` > 0, every nyx_extract
+ * records CUDA events on its stream between its phases into a ring of
+ * `slots` event sets (slots = 0 turns recording off).  nyx_phase_times waits
+ * for the events of the extract `back` calls ago (0 = the last one, up to
+ * slots - 1) and writes up to NYX_N_PHASES durations in milliseconds:
+ * [0] counters + label scan, [1] key sort + per-ROI setup, [2] ROI kernel of
+ * the small class, [3] ROI kernel of the medium class, [4] table reset.
+ * Errors: NYX_ERR_ARG (null plan/ms, slots out of 0..1024, back out of
+ * range), NYX_ERR_STATE (that extract was not recorded), NYX_ERR_CUDA. */
+#define NYX_N_PHASES 5
+nyx_status nyx_profile_enable(nyx_plan* plan, int slots);
+nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NYX_H_ */

@@ -1,0 +1,651 @@
+// nyx_api.cu -- host side of the C ABI declared in include/nyx.h: parameter
+// validation, column registry, plan workspace, and the stream-ordered launch
+// sequence of one extraction:
+//   k_begin -> k_scan -> k_sort_keys -> k_setup -> k_roi (per size class)
+//   -> k_reset
+// All data stays on the device; the host reads back only the 4-byte error
+// word (and the ROI count in nyx_count_rois).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nyx_internal.cuh"
+
+namespace nyx {
+cudaError_t launch_roi_u16(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_roi_i16(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_roi_f32(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_reset(const KParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_init_table(const KParams& p, unsigned cap, cudaStream_t st);
+cudaError_t launch_debug_bins(const KParams& p, uint16_t* out, int nsm, cudaStream_t st);
+cudaError_t launch_backward(const KParams& p, const double* gtab, float* gimg, int nsm, cudaStream_t st);
+}  // namespace nyx
+
+using namespace nyx;
+
+// ---------------------------------------------------------------------------
+// feature registry: ids 0..40 statistics, 41..50 moment families, 51..80 GLCM
+
+namespace {
+
+const char* STAT_NAMES[N_STATS] = {
+    "MEAN", "MIN", "MAX", "RANGE", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS", "KURTOSIS",
+    "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED", "STANDARD_ERROR",
+    "MEAN_ABSOLUTE_DEVIATION", "MEDIAN_ABSOLUTE_DEVIATION", "INTEGRATED_INTENSITY", "WEIGHTED_CENTROID_X",
+    "WEIGHTED_CENTROID_Y", "WEIGHTED_CENTROID_Z", "MASS_DISPLACEMENT", "COV", "COVERED_IMAGE_INTENSITY_RANGE",
+    "UNIFORMITY_PIU", "MEDIAN", "P01", "P10", "P25", "P75", "P90", "P99", "INTERQUARTILE_RANGE", "QCOD", "ROBUST_MEAN",
+    "ROBUST_MEAN_ABSOLUTE_DEVIATION", "MODE", "MODE_PROBABILITY", "ENTROPY", "UNIFORMITY"};
+const char* MOM_FAMILY[5] = {"M", "MU", "ETA", "NU", "HU"};
+const char* GLCM_NAMES[NGLCM] = {
+    "ASM", "ACOR", "CLUPROM", "CLUSHADE", "CLUTEND", "CONTRAST", "CORR", "DIFAVE", "DIFENTRO", "DIFVAR",
+    "DIS", "ENERGY", "ENTROPY", "HOM1", "HOM2", "IDM", "INFOMEAS1", "INFOMEAS2", "IDMN", "ID",
+    "IDN", "IV", "JAVE", "JE", "JMAX", "SUMAVE", "SUMENT", "JVAR", "SUMVAR", "VARIANCE"};
+constexpr int FID_MOM = N_STATS;         // 41
+constexpr int FID_GLCM = N_STATS + 10;   // 51
+constexpr int N_FID = FID_GLCM + NGLCM;  // 81
+
+bool is_order_stat(int s) {
+  return s == S_MEDIAN || s == S_P01 || s == S_P10 || s == S_P25 || s == S_P75 || s == S_P90 || s == S_P99 ||
+         s == S_IQR || s == S_QCOD || s == S_RMEAN || s == S_RMAD || s == S_MODE || s == S_MODE_PROB || s == S_MEDAD;
+}
+
+bool fbit(const nyx_params& p, int id) { return (p.feature_mask[id >> 6] >> (id & 63)) & 1ull; }
+
+}  // namespace
+
+struct nyx_ctx {
+  int device = 0;
+  int nsm = 0;
+  std::string err;
+};
+
+struct nyx_plan {
+  nyx_ctx* ctx = nullptr;
+  nyx_params prm{};
+  std::vector<std::string> col_names;
+  std::vector<int> col_map;  // Q_TOTAL entries
+  KParams kp{};
+  unsigned hcap = 0;
+  void* ws = nullptr;         // one device allocation for the workspace
+  int* d_col_map = nullptr;
+  double* d_saved = nullptr;
+  unsigned* d_dbg = nullptr;
+  bool have_saved = false;
+  int64_t saved_rows = 0;
+  int n_off = 0;
+  int64_t dbg_roi = -1;
+  int prof_slots = 0;                // ring of event sets, 0 = off
+  int64_t prof_count = 0;            // profiled extracts so far
+  std::vector<cudaEvent_t> ev;       // prof_slots * (NYX_N_PHASES + 1)
+};
+
+static nyx_status fail(nyx_ctx* c, nyx_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define NYX_CUDA(ctx, call)                                                                 \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, NYX_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+static nyx_status err_to_status(unsigned e) {
+  if (e & E_BAD_LABEL) return NYX_ERR_BAD_LABEL;
+  if (e & E_NONFINITE) return NYX_ERR_NONFINITE;
+  if (e & (E_HASH_FULL | E_ROI_CAP | E_TOO_LARGE | E_SORT_CAP)) return NYX_ERR_CAPACITY;
+  if (e & E_TIMEOUT) return NYX_ERR_TIMEOUT;
+  if (e) return NYX_ERR_STATE;
+  return NYX_OK;
+}
+
+extern "C" {
+
+nyx_status nyx_params_default(nyx_params* p, int64_t nx, int64_t ny) {
+  if (!p) return NYX_ERR_ARG;
+  memset(p, 0, sizeof *p);
+  p->struct_size = sizeof(nyx_params);
+  p->ndim = 2;
+  p->dims[0] = nx;
+  p->dims[1] = ny;
+  p->dims[2] = 1;
+  p->batch = 1;
+  p->dtype = NYX_U16;
+  for (int i = 0; i < 4; ++i) p->feature_mask[i] = ~0ull;
+  p->glcm_levels = 64;
+  p->n_dist = 1;
+  p->dists[0] = 1;
+  p->glcm_per_offset_cols = 0;
+  p->hist_bins = 256;
+  p->precision = NYX_PREC_FP32_COMP;
+  p->max_rois = 65536;
+  return NYX_OK;
+}
+
+nyx_status nyx_create(nyx_ctx** out, int device) {
+  if (!out) return NYX_ERR_ARG;
+  *out = nullptr;
+  nyx_ctx* c = new (std::nothrow) nyx_ctx();
+  if (!c) return NYX_ERR_OOM;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    delete c;
+    return NYX_ERR_CUDA;
+  }
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return NYX_ERR_CUDA;
+  }
+  *out = c;
+  return NYX_OK;
+}
+
+void nyx_destroy(nyx_ctx* ctx) { delete ctx; }
+
+const char* nyx_last_error(const nyx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int nyx_feature_id(const char* name) {
+  if (!name) return -1;
+  for (int i = 0; i < N_STATS; ++i)
+    if (!strcmp(name, STAT_NAMES[i])) return i;
+  for (int w = 0; w < 2; ++w)
+    for (int f = 0; f < 5; ++f) {
+      char b[32];
+      snprintf(b, sizeof b, "%s_%s", w ? "BIN" : "INT", MOM_FAMILY[f]);
+      if (!strcmp(name, b)) return FID_MOM + w * 5 + f;
+    }
+  for (int g = 0; g < NGLCM; ++g) {
+    char b[48];
+    snprintf(b, sizeof b, "GLCM_%s", GLCM_NAMES[g]);
+    if (!strcmp(name, b)) return FID_GLCM + g;
+  }
+  return -1;
+}
+
+static nyx_status validate(nyx_ctx* c, const nyx_params* p) {
+  if (p->struct_size != sizeof(nyx_params))
+    return fail(c, NYX_ERR_ARG, "params.struct_size %u != %zu", p->struct_size, sizeof(nyx_params));
+  if (p->ndim != 2 && p->ndim != 3) return fail(c, NYX_ERR_SHAPE, "ndim must be 2 or 3");
+  for (int i = 0; i < 3; ++i)
+    if (p->dims[i] < 1 || p->dims[i] > (1ll << 31)) return fail(c, NYX_ERR_SHAPE, "dims[%d] out of range", i);
+  if (p->ndim == 2 && p->dims[2] != 1) return fail(c, NYX_ERR_SHAPE, "2D images need dims[2] = 1");
+  if (p->batch < 1 || p->batch > (1 << 20)) return fail(c, NYX_ERR_SHAPE, "batch out of range");
+  if (p->dtype < 0 || p->dtype > 2) return fail(c, NYX_ERR_DTYPE, "unsupported dtype %d", p->dtype);
+  if (p->glcm_levels != 0 && (p->glcm_levels < 2 || p->glcm_levels > 256))
+    return fail(c, NYX_ERR_ARG, "glcm_levels must be 0 or 2..256");
+  if (p->n_dist < 1 || p->n_dist > MAX_DIST) return fail(c, NYX_ERR_ARG, "n_dist must be 1..8");
+  for (int i = 0; i < p->n_dist; ++i)
+    if (p->dists[i] < 1 || p->dists[i] > 8) return fail(c, NYX_ERR_ARG, "dists[%d] must be 1..8", i);
+  if (p->hist_bins < 2 || p->hist_bins > 4096) return fail(c, NYX_ERR_ARG, "hist_bins must be 2..4096");
+  if (p->precision != NYX_PREC_FP32_COMP && p->precision != NYX_PREC_FP64_PLAIN)
+    return fail(c, NYX_ERR_ARG, "unknown precision");
+  if (p->max_rois < 1 || p->max_rois > (1ll << 24)) return fail(c, NYX_ERR_ARG, "max_rois must be 1..2^24");
+  if (p->glcm_per_offset_cols != 0 && p->glcm_per_offset_cols != 1)
+    return fail(c, NYX_ERR_ARG, "glcm_per_offset_cols must be 0 or 1");
+  return NYX_OK;
+}
+
+// Build the column list and the quantity -> column map.
+static void build_columns(nyx_plan* pl) {
+  const nyx_params& p = pl->prm;
+  const bool d3 = p.ndim == 3;
+  pl->col_map.assign(Q_TOTAL, -1);
+  pl->col_names.clear();
+  auto add = [&](int q, const std::string& nm) {
+    pl->col_map[q] = (int)pl->col_names.size();
+    pl->col_names.push_back(nm);
+  };
+  add(Q_LABEL, "LABEL");
+  add(Q_IMAGE, "IMAGE");
+  add(Q_AREA, "AREA");
+  add(Q_BB_X, "BBOX_XMIN");
+  add(Q_BB_Y, "BBOX_YMIN");
+  if (d3) add(Q_BB_Z, "BBOX_ZMIN");
+  add(Q_BB_W, "BBOX_WIDTH");
+  add(Q_BB_H, "BBOX_HEIGHT");
+  if (d3) add(Q_BB_D, "BBOX_DEPTH");
+  add(Q_CEN_X, "CENTROID_X");
+  add(Q_CEN_Y, "CENTROID_Y");
+  if (d3) add(Q_CEN_Z, "CENTROID_Z");
+  for (int s = 0; s < N_STATS; ++s) {
+    if (s == S_WCZ && !d3) continue;
+    if (fbit(p, s)) add(Q_STATS + s, STAT_NAMES[s]);
+  }
+  const int nm = d3 ? 20 : 10;
+  for (int w = 0; w < 2; ++w)
+    for (int f = 0; f < 5; ++f) {
+      if (!fbit(p, FID_MOM + w * 5 + f)) continue;
+      if (d3 && (f == F_NU || f == F_HU)) continue;
+      if (f == F_HU) {
+        for (int h = 0; h < 7; ++h)
+          add(Q_MOM + (w * 5 + f) * 20 + h, std::string(w ? "BIN_HU" : "INT_HU") + std::to_string(h + 1));
+        continue;
+      }
+      for (int k = 0; k < nm; ++k) {
+        // lexicographic (p, q, r) with p + q + r <= 3, same order as the kernel
+        int idx = 0, pp = 0, qq = 0, rr = 0;
+        for (int a = 0; a <= 3; ++a)
+          for (int b = 0; a + b <= 3; ++b)
+            for (int c = 0; c <= (d3 ? 3 - a - b : 0); ++c) {
+              if (idx == k) {
+                pp = a;
+                qq = b;
+                rr = c;
+              }
+              ++idx;
+            }
+        if (f == F_ETA && pp + qq + rr < 2) continue;
+        std::string nmc = std::string(w ? "BIN_" : "INT_") + MOM_FAMILY[f] + std::to_string(pp) + std::to_string(qq);
+        if (d3) nmc += std::to_string(rr);
+        add(Q_MOM + (w * 5 + f) * 20 + k, nmc);
+      }
+    }
+  if (p.glcm_levels > 0) {
+    const int ndirs = d3 ? 13 : 4;
+    for (int di = 0; di < p.n_dist; ++di)
+      for (int g = 0; g < NGLCM; ++g)
+        if (fbit(p, FID_GLCM + g))
+          add(Q_GLCM_D + di * NGLCM + g, std::string("GLCM_") + GLCM_NAMES[g] + "_D" + std::to_string(p.dists[di]));
+    if (p.glcm_per_offset_cols)
+      for (int di = 0; di < p.n_dist; ++di)
+        for (int o = 0; o < ndirs; ++o)
+          for (int g = 0; g < NGLCM; ++g)
+            if (fbit(p, FID_GLCM + g))
+              add(Q_GLCM_O + (di * MAX_DIRS + o) * NGLCM + g,
+                  std::string("GLCM_") + GLCM_NAMES[g] + "_D" + std::to_string(p.dists[di]) +
+                      (d3 ? "_O" + std::to_string(o) : "_A" + std::to_string(45 * o)));
+  }
+}
+
+// GLCM unit directions: 2D angles 0/45/90/135 degrees as (dx,dy) = (1,0),
+// (1,-1), (0,-1), (-1,-1) with the row index growing downward; 3D the 13
+// vectors of {-1,0,1}^3 whose first nonzero component in (dz, dy, dx) order
+// is positive, dz outermost and dx fastest.
+static void unit_dirs(int ndim, int dirs[13][3]) {
+  if (ndim == 2) {
+    const int d2[4][2] = {{1, 0}, {1, -1}, {0, -1}, {-1, -1}};
+    for (int k = 0; k < 4; ++k) {
+      dirs[k][0] = d2[k][0];
+      dirs[k][1] = d2[k][1];
+      dirs[k][2] = 0;
+    }
+    return;
+  }
+  int k = 0;
+  for (int z = -1; z <= 1; ++z)
+    for (int y = -1; y <= 1; ++y)
+      for (int x = -1; x <= 1; ++x) {
+        const int first = z != 0 ? z : (y != 0 ? y : x);
+        if (first <= 0) continue;
+        dirs[k][0] = x;
+        dirs[k][1] = y;
+        dirs[k][2] = z;
+        ++k;
+      }
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** out) {
+  if (!ctx || !params || !out) return fail(ctx, NYX_ERR_ARG, "null argument");
+  *out = nullptr;
+  nyx_status st = validate(ctx, params);
+  if (st != NYX_OK) return st;
+  NYX_CUDA(ctx, cudaSetDevice(ctx->device));
+  nyx_plan* pl = new (std::nothrow) nyx_plan();
+  if (!pl) return fail(ctx, NYX_ERR_OOM, "host allocation failed");
+  pl->ctx = ctx;
+  pl->prm = *params;
+  build_columns(pl);
+  const nyx_params& p = pl->prm;
+  unsigned hcap = 1024;
+  while (hcap < 2 * (uint64_t)p.max_rois) hcap <<= 1;
+  pl->hcap = hcap;
+  const int64_t mr = p.max_rois;
+  // workspace carve-up
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = up256(off + bytes);
+    return o;
+  };
+  const size_t o_keys = take(8ull * hcap), o_slots = take(sizeof(SlotAcc) * hcap), o_slist = take(4ull * hcap),
+               o_sdense = take(4ull * hcap), o_sorted = take(8ull * mr), o_rois = take(sizeof(RoiInfo) * mr),
+               o_queue = take(4ull * 3 * mr), o_small = take(64), o_imin = take(4ull * p.batch),
+               o_imax = take(4ull * p.batch), o_cmap = take(4ull * Q_TOTAL);
+  cudaError_t e = cudaMalloc(&pl->ws, off);
+  if (e != cudaSuccess) {
+    delete pl;
+    return fail(ctx, NYX_ERR_OOM, "workspace allocation of %zu bytes failed: %s", off, cudaGetErrorString(e));
+  }
+  char* w = (char*)pl->ws;
+  KParams& k = pl->kp;
+  memset(&k, 0, sizeof k);
+  k.nx = p.dims[0];
+  k.ny = p.dims[1];
+  k.nz = p.dims[2];
+  k.batch = p.batch;
+  k.rows_total = (int64_t)p.batch * p.dims[2] * p.dims[1];
+  k.ndim = p.ndim;
+  k.dtype = p.dtype;
+  k.ng = p.glcm_levels;
+  k.n_dist = p.n_dist;
+  k.n_dirs = p.ndim == 3 ? 13 : 4;
+  k.per_offset = p.glcm_per_offset_cols;
+  k.hist_bins = p.hist_bins;
+  int dmax = 0;
+  int dirs[13][3];
+  unit_dirs(p.ndim, dirs);
+  for (int di = 0; di < p.n_dist; ++di) {
+    k.dists[di] = p.dists[di];
+    if (p.dists[di] > dmax) dmax = p.dists[di];
+    for (int o = 0; o < k.n_dirs; ++o)
+      for (int a = 0; a < 3; ++a) k.off[di * k.n_dirs + o][a] = dirs[o][a] * p.dists[di];
+  }
+  k.pad = dmax;
+  pl->n_off = p.n_dist * k.n_dirs;
+  // computation groups
+  unsigned need = 0;
+  for (int s = 0; s < N_STATS; ++s) {
+    if (!fbit(p, s)) continue;
+    if (is_order_stat(s)) need |= NEED_ORDER;
+    else if (s == S_ENTROPY || s == S_UNIFORMITY) need |= NEED_HIST;
+    else need |= NEED_STATS;
+  }
+  for (int f = 0; f < 5; ++f) {
+    if (fbit(p, FID_MOM + f)) need |= NEED_MOM_INT;
+    if (fbit(p, FID_MOM + 5 + f)) need |= NEED_MOM_BIN;
+  }
+  if (p.glcm_levels > 0)
+    for (int g = 0; g < NGLCM; ++g)
+      if (fbit(p, FID_GLCM + g)) need |= NEED_GLCM;
+  k.need = need;
+  k.keys = (unsigned long long*)(w + o_keys);
+  k.slots = (SlotAcc*)(w + o_slots);
+  k.hmask = hcap - 1;
+  k.slot_list = (int*)(w + o_slist);
+  k.slot_dense = (int*)(w + o_sdense);
+  k.sorted_keys = (unsigned long long*)(w + o_sorted);
+  k.rois = (RoiInfo*)(w + o_rois);
+  k.queue = (int*)(w + o_queue);
+  unsigned* small = (unsigned*)(w + o_small);
+  k.n_used = small + 0;
+  k.n_roi = small + 1;
+  k.err = small + 2;
+  k.qlen = small + 4;
+  k.qhead = small + 8;
+  k.img_vmin = (unsigned*)(w + o_imin);
+  k.img_vmax = (unsigned*)(w + o_imax);
+  pl->d_col_map = (int*)(w + o_cmap);
+  k.col_map = pl->d_col_map;
+  k.n_col = (int)pl->col_names.size();
+  k.max_rois = mr;
+  k.dbg_roi = -1;
+  k.lim_pix[0] = 1024;
+  k.lim_cells[0] = 4096;
+  k.lim_pix[1] = 8192;
+  k.lim_cells[1] = 16384;
+  e = cudaMemcpy(pl->d_col_map, pl->col_map.data(), 4ull * Q_TOTAL, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(small, 0, 64);
+  if (e == cudaSuccess) {
+    e = launch_init_table(k, hcap, 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(pl->ws);
+    delete pl;
+    return fail(ctx, NYX_ERR_CUDA, "plan initialisation failed: %s", cudaGetErrorString(e));
+  }
+  *out = pl;
+  return NYX_OK;
+}
+
+void nyx_plan_destroy(nyx_plan* pl) {
+  if (!pl) return;
+  cudaSetDevice(pl->ctx->device);
+  for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+  cudaFree(pl->ws);
+  if (pl->d_saved) cudaFree(pl->d_saved);
+  if (pl->d_dbg) cudaFree(pl->d_dbg);
+  delete pl;
+}
+
+nyx_status nyx_num_columns(const nyx_plan* pl, int* n_col) {
+  if (!pl || !n_col) return NYX_ERR_ARG;
+  *n_col = (int)pl->col_names.size();
+  return NYX_OK;
+}
+
+nyx_status nyx_column_name(const nyx_plan* pl, int col, char* buf, size_t cap) {
+  if (!pl || !buf || cap == 0 || col < 0 || col >= (int)pl->col_names.size()) return NYX_ERR_ARG;
+  snprintf(buf, cap, "%s", pl->col_names[col].c_str());
+  return NYX_OK;
+}
+
+static nyx_status check_ptrs(nyx_plan* pl, const void* img, const int32_t* mask) {
+  if (!img || !mask) return fail(pl->ctx, NYX_ERR_ARG, "null image or mask pointer");
+  if (((uintptr_t)img & 15) || ((uintptr_t)mask & 15))
+    return fail(pl->ctx, NYX_ERR_ARG, "image and mask must be 16-byte aligned");
+  return NYX_OK;
+}
+
+// Front half of every call: counters and label scan; then key sort + setup.
+static nyx_status run_front(nyx_plan* pl, KParams& k, cudaStream_t st) {
+  NYX_CUDA(pl->ctx, launch_front(k, pl->ctx->nsm, st));
+  return NYX_OK;
+}
+
+static nyx_status run_sort_setup(nyx_plan* pl, KParams& k, cudaStream_t st) {
+  NYX_CUDA(pl->ctx, launch_sort_setup(k, pl->ctx->nsm, st));
+  return NYX_OK;
+}
+
+static nyx_status run_reset(nyx_plan* pl, KParams& k, cudaStream_t st) {
+  NYX_CUDA(pl->ctx, launch_reset(k, pl->ctx->nsm, st));
+  return NYX_OK;
+}
+
+static nyx_status read_err(nyx_plan* pl, cudaStream_t st) {
+  unsigned h = 0;
+  NYX_CUDA(pl->ctx, cudaMemcpyAsync(&h, pl->kp.err, 4, cudaMemcpyDeviceToHost, st));
+  NYX_CUDA(pl->ctx, cudaStreamSynchronize(st));
+  if (h) {
+    NYX_CUDA(pl->ctx, cudaMemsetAsync(pl->kp.err, 0, 4, st));
+    NYX_CUDA(pl->ctx, cudaStreamSynchronize(st));
+    return fail(pl->ctx, err_to_status(h), "device reported error bits 0x%x", h);
+  }
+  return NYX_OK;
+}
+
+nyx_status nyx_count_rois(nyx_plan* pl, const void* d_img, const int32_t* d_mask, int64_t* n_roi, void* stream) {
+  if (!pl || !n_roi) return NYX_ERR_ARG;
+  nyx_status s = check_ptrs(pl, d_img, d_mask);
+  if (s != NYX_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+  KParams k = pl->kp;
+  k.img = d_img;
+  k.mask = d_mask;
+  k.vec = (k.nx % 4) == 0;
+  if ((s = run_front(pl, k, st)) != NYX_OK) return s;
+  unsigned h = 0;
+  NYX_CUDA(pl->ctx, cudaMemcpyAsync(&h, k.n_used, 4, cudaMemcpyDeviceToHost, st));
+  if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
+  s = read_err(pl, st);
+  *n_roi = h;
+  return s;
+}
+
+nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
+                       int64_t* d_n_roi, uint32_t flags, void* stream) {
+  if (!pl) return NYX_ERR_ARG;
+  nyx_status s = check_ptrs(pl, d_img, d_mask);
+  if (s != NYX_OK) return s;
+  if (!d_table && cap_roi > 0) return fail(pl->ctx, NYX_ERR_ARG, "null table");
+  if (cap_roi < 0) return fail(pl->ctx, NYX_ERR_ARG, "cap_roi < 0");
+  if ((uintptr_t)d_table & 7) return fail(pl->ctx, NYX_ERR_ARG, "table must be 8-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  nyx_ctx* c = pl->ctx;
+  NYX_CUDA(c, cudaSetDevice(c->device));
+  KParams k = pl->kp;
+  k.img = d_img;
+  k.mask = d_mask;
+  k.vec = (k.nx % 4) == 0;
+  k.table = d_table;
+  k.cap_roi = cap_roi < pl->prm.max_rois ? cap_roi : pl->prm.max_rois;
+  k.n_roi_out = d_n_roi;
+  if (flags & NYX_SAVE_FOR_BACKWARD) {
+    if (!pl->d_saved) {
+      // saved per-ROI state, then the backward pass's per-ROI coefficients (40 floats)
+      cudaError_t e = cudaMalloc(&pl->d_saved, (8ull * SV_WORDS + 4ull * 40) * pl->prm.max_rois);
+      if (e != cudaSuccess) {
+        pl->d_saved = nullptr;
+        return fail(c, NYX_ERR_OOM, "saved-state allocation failed");
+      }
+    }
+    k.saved = pl->d_saved;
+    k.need |= NEED_SAVE;
+    pl->have_saved = true;
+  } else {
+    pl->have_saved = false;
+  }
+  if (pl->dbg_roi >= 0 && pl->d_dbg && (k.need & NEED_GLCM)) {
+    k.dbg_roi = pl->dbg_roi;
+    k.dbg_glcm = pl->d_dbg;
+    NYX_CUDA(c, cudaMemsetAsync(pl->d_dbg, 0, 4ull * pl->n_off * k.ng * k.ng, st));
+  }
+  const bool prof = pl->prof_slots > 0;
+  cudaEvent_t* ev = prof ? &pl->ev[(size_t)(pl->prof_count % pl->prof_slots) * (NYX_N_PHASES + 1)] : nullptr;
+  if (prof) NYX_CUDA(c, cudaEventRecord(ev[0], st));
+  if ((s = run_front(pl, k, st)) != NYX_OK) return s;
+  if (prof) NYX_CUDA(c, cudaEventRecord(ev[1], st));
+  if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
+  if (prof) NYX_CUDA(c, cudaEventRecord(ev[2], st));
+  const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
+  for (int cls = 0; cls < 2; ++cls) {
+    cudaError_t e;
+    switch (k.dtype) {
+      case NYX_U16: e = launch_roi_u16(k, cls, fp64, c->nsm, st); break;
+      case NYX_I16: e = launch_roi_i16(k, cls, fp64, c->nsm, st); break;
+      default: e = launch_roi_f32(k, cls, fp64, c->nsm, st); break;
+    }
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
+    if (prof) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
+  }
+  if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
+  if (prof) {
+    NYX_CUDA(c, cudaEventRecord(ev[5], st));
+    ++pl->prof_count;
+  }
+  if (flags & NYX_SYNC) return read_err(pl, st);
+  return NYX_OK;
+}
+
+nyx_status nyx_profile_enable(nyx_plan* pl, int slots) {
+  if (!pl || slots < 0 || slots > 1024) return NYX_ERR_ARG;
+  NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+  NYX_CUDA(pl->ctx, cudaDeviceSynchronize());
+  for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+  pl->ev.assign((size_t)slots * (NYX_N_PHASES + 1), nullptr);
+  for (auto& e : pl->ev) NYX_CUDA(pl->ctx, cudaEventCreate(&e));
+  pl->prof_slots = slots;
+  pl->prof_count = 0;
+  return NYX_OK;
+}
+
+nyx_status nyx_phase_times(nyx_plan* pl, int back, float* ms, int n) {
+  if (!pl || !ms || back < 0 || back >= pl->prof_slots) return NYX_ERR_ARG;
+  if (back >= pl->prof_count) return fail(pl->ctx, NYX_ERR_STATE, "extract not recorded");
+  const int64_t which = pl->prof_count - 1 - back;
+  cudaEvent_t* ev = &pl->ev[(size_t)(which % pl->prof_slots) * (NYX_N_PHASES + 1)];
+  NYX_CUDA(pl->ctx, cudaEventSynchronize(ev[NYX_N_PHASES]));
+  for (int i = 0; i < n && i < NYX_N_PHASES; ++i) NYX_CUDA(pl->ctx, cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+  return NYX_OK;
+}
+
+nyx_status nyx_sync_status(nyx_plan* pl, void* stream) {
+  if (!pl) return NYX_ERR_ARG;
+  NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+  return read_err(pl, (cudaStream_t)stream);
+}
+
+nyx_status nyx_debug_select(nyx_plan* pl, int64_t roi) {
+  if (!pl) return NYX_ERR_ARG;
+  pl->dbg_roi = roi;
+  if (roi >= 0 && !pl->d_dbg && pl->prm.glcm_levels > 0) {
+    NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+    NYX_CUDA(pl->ctx, cudaMalloc(&pl->d_dbg, 4ull * pl->n_off * pl->prm.glcm_levels * pl->prm.glcm_levels));
+  }
+  return NYX_OK;
+}
+
+nyx_status nyx_debug_glcm(nyx_plan* pl, int off, uint32_t* h_counts) {
+  if (!pl || !h_counts || off < 0 || off >= pl->n_off || !pl->d_dbg) return NYX_ERR_ARG;
+  const int ng = pl->prm.glcm_levels;
+  NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+  NYX_CUDA(pl->ctx, cudaDeviceSynchronize());
+  NYX_CUDA(pl->ctx, cudaMemcpy(h_counts, pl->d_dbg + (size_t)off * ng * ng, 4ull * ng * ng, cudaMemcpyDeviceToHost));
+  return NYX_OK;
+}
+
+nyx_status nyx_debug_bins(nyx_plan* pl, const void* d_img, const int32_t* d_mask, uint16_t* d_bins, void* stream) {
+  if (!pl || !d_bins) return NYX_ERR_ARG;
+  nyx_status s = check_ptrs(pl, d_img, d_mask);
+  if (s != NYX_OK) return s;
+  if (pl->prm.glcm_levels < 2) return fail(pl->ctx, NYX_ERR_ARG, "plan has no GLCM levels");
+  cudaStream_t st = (cudaStream_t)stream;
+  nyx_ctx* c = pl->ctx;
+  NYX_CUDA(c, cudaSetDevice(c->device));
+  KParams k = pl->kp;
+  k.img = d_img;
+  k.mask = d_mask;
+  k.vec = (k.nx % 4) == 0;
+  k.cap_roi = pl->prm.max_rois;
+  if ((s = run_front(pl, k, st)) != NYX_OK) return s;
+  if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
+  NYX_CUDA(c, launch_debug_bins(k, d_bins, c->nsm, st));
+  if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
+  return read_err(pl, st);
+}
+
+nyx_status nyx_backward(nyx_plan* pl, const void* d_img, const int32_t* d_mask, const double* d_grad_table,
+                        float* d_grad_img, void* stream) {
+  if (!pl || !d_grad_table || !d_grad_img) return NYX_ERR_ARG;
+  nyx_status s = check_ptrs(pl, d_img, d_mask);
+  if (s != NYX_OK) return s;
+  if (!pl->have_saved) return fail(pl->ctx, NYX_ERR_STATE, "no forward pass saved for backward");
+  cudaStream_t st = (cudaStream_t)stream;
+  nyx_ctx* c = pl->ctx;
+  NYX_CUDA(c, cudaSetDevice(c->device));
+  KParams k = pl->kp;
+  k.img = d_img;
+  k.mask = d_mask;
+  k.vec = (k.nx % 4) == 0;
+  k.saved = pl->d_saved;
+  k.cap_roi = pl->prm.max_rois;
+  // rebuild the label -> ROI map of this image (the forward pass released it)
+  if ((s = run_front(pl, k, st)) != NYX_OK) return s;
+  if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
+  cudaError_t e = launch_backward(k, d_grad_table, d_grad_img, c->nsm, st);
+  if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
+  return run_reset(pl, k, st);
+}
+
+}  // extern "C"

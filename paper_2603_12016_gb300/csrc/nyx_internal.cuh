@@ -1,0 +1,227 @@
+// nyx_internal.cuh -- device-side data structures and helpers shared by the
+// kernels of libnyxgpu (GB300 / sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nyx.h"
+
+namespace nyx {
+
+// ---------------------------------------------------------------------------
+// device error word bits (reported through nyx_sync_status)
+enum : unsigned {
+  E_BAD_LABEL = 1u,   // negative label in the mask
+  E_NONFINITE = 2u,   // NaN/Inf float pixel inside an ROI
+  E_HASH_FULL = 4u,   // more distinct labels than the plan's label table holds
+  E_ROI_CAP = 8u,     // more ROIs than cap_roi
+  E_TOO_LARGE = 16u,  // an ROI exceeds the per-ROI size limits of every path
+  E_TIMEOUT = 32u,    // a bounded wait ran out
+  E_SORT_CAP = 64u,   // more ROIs than the label sort handles
+  E_INTERNAL = 128u,  // staged pixel count disagrees with the scan (never expected)
+};
+
+constexpr unsigned long long EMPTY_KEY = 0xFFFFFFFFFFFFFFFFull;
+constexpr int MAX_DIST = 8;
+constexpr int MAX_DIRS = 13;
+constexpr int NGLCM = 30;
+constexpr int SORT_CAP = 16384;  // ROIs sortable by the single-block label sort
+
+// Per (image, label) accumulator filled by the label scan.  Intensities use
+// an order-preserving uint32 encoding so that min/max are integer atomics.
+struct SlotAcc {
+  unsigned count;
+  unsigned vmin, vmax;
+  int xmin, xmax, ymin, ymax, zmin, zmax;
+  unsigned pad[3];
+};
+
+// Per ROI, in output (ascending key) order.
+struct RoiInfo {
+  unsigned long long key;  // image << 32 | label
+  unsigned n;              // pixel count
+  int x0, y0, z0, w, h, d; // bounding box (image coordinates, extents)
+  unsigned vmin, vmax;     // encoded intensity range
+  int cls;                 // processing class
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// output quantity index space.  The host maps each quantity to an output
+// column (or -1) in col_map[].
+enum : int {
+  Q_LABEL = 0, Q_IMAGE, Q_AREA, Q_BB_X, Q_BB_Y, Q_BB_Z, Q_BB_W, Q_BB_H, Q_BB_D, Q_CEN_X, Q_CEN_Y, Q_CEN_Z,
+  Q_STATS = 12,
+  N_STATS = 41,
+  Q_MOM = Q_STATS + N_STATS,          // + (weighting*5 + family)*20 + k
+  Q_GLCM_D = Q_MOM + 200,             // + di*30 + g
+  Q_GLCM_O = Q_GLCM_D + MAX_DIST * NGLCM,  // + (di*13 + dir)*30 + g
+  Q_TOTAL = Q_GLCM_O + MAX_DIST * MAX_DIRS * NGLCM
+};
+
+// first-order statistics (Table S1 / S5), index within Q_STATS
+enum : int {
+  S_MEAN = 0, S_MIN, S_MAX, S_RANGE, S_VAR, S_VAR_B, S_STD, S_STD_B, S_SKEW, S_KURT, S_EXKURT, S_HSKEW, S_HFLAT,
+  S_ENERGY, S_RMS, S_SE, S_MAD, S_MEDAD, S_II, S_WCX, S_WCY, S_WCZ, S_MD, S_COV, S_COVERED, S_PIU, S_MEDIAN,
+  S_P01, S_P10, S_P25, S_P75, S_P90, S_P99, S_IQR, S_QCOD, S_RMEAN, S_RMAD, S_MODE, S_MODE_PROB, S_ENTROPY,
+  S_UNIFORMITY
+};
+
+// moment families
+enum : int { F_M = 0, F_MU = 1, F_ETA = 2, F_NU = 3, F_HU = 4 };
+
+// GLCM features (Table S3 rows 140-174 without AVEAMP), index g
+enum : int {
+  G_ASM = 0, G_ACOR, G_CLUPROM, G_CLUSHADE, G_CLUTEND, G_CONTRAST, G_CORR, G_DIFAVE, G_DIFENTRO, G_DIFVAR, G_DIS,
+  G_ENERGY, G_ENTROPY, G_HOM1, G_HOM2, G_IDM, G_INFOMEAS1, G_INFOMEAS2, G_IDMN, G_ID, G_IDN, G_IV, G_JAVE, G_JE,
+  G_JMAX, G_SUMAVE, G_SUMENT, G_JVAR, G_SUMVAR, G_VARIANCE
+};
+
+// computation groups derived from the feature selection
+enum : unsigned {
+  NEED_STATS = 1u,    // central power sums of the intensities
+  NEED_ORDER = 2u,    // sorted values (percentiles, mode, robust stats)
+  NEED_HIST = 4u,     // entropy / uniformity histogram
+  NEED_MOM_INT = 8u,  // intensity-weighted moments
+  NEED_MOM_BIN = 16u, // binary moments
+  NEED_GLCM = 32u,
+  NEED_SAVE = 64u,    // keep per-ROI state for the backward pass
+};
+
+// saved per-ROI state for the backward pass (FP64 words per ROI)
+enum : int {
+  SV_N = 0, SV_MEAN, SV_M2, SV_M3, SV_M4, SV_M5, SV_M6, SV_SGN, SV_ENERGY, SV_SUMI,
+  SV_CX, SV_CY, SV_CZ,          // intensity centroid, ROI-local
+  SV_BX, SV_BY, SV_BZ,          // binary centroid, image coordinates
+  SV_X0, SV_Y0, SV_Z0,          // bounding-box origin
+  SV_MU = 19,                   // 20 central intensity moments
+  SV_WORDS = SV_MU + 20
+};
+
+// Kernel parameters (by value).
+struct KParams {
+  const void* img;
+  const int32_t* mask;
+  int64_t nx, ny, nz, rows_total;  // rows_total = batch * nz * ny
+  int batch, ndim, dtype, vec;     // vec: 16-byte vector loads are legal
+  int ng, n_dist, n_dirs, per_offset, hist_bins, pad;
+  int dists[MAX_DIST];
+  int off[MAX_DIST * MAX_DIRS][3]; // (dx, dy, dz) of every offset
+  unsigned need;
+  const int* col_map;
+  int n_col;
+  // label table
+  unsigned long long* keys;
+  SlotAcc* slots;
+  unsigned hmask;                  // capacity - 1 (power of two)
+  int* slot_list;
+  unsigned* n_used;
+  unsigned* img_vmin;
+  unsigned* img_vmax;
+  // ROI table
+  unsigned long long* sorted_keys;
+  RoiInfo* rois;
+  int* slot_dense;
+  int* queue;                      // [3][max_rois]
+  unsigned* qlen;                  // [3]
+  unsigned* qhead;                 // [3]
+  unsigned* n_roi;                 // device ROI count
+  unsigned* err;
+  int64_t max_rois, cap_roi;
+  double* table;
+  int64_t* n_roi_out;
+  double* saved;
+  // debug hook
+  int64_t dbg_roi;
+  unsigned* dbg_glcm;              // [n_off][ng*ng]
+  // class limits (pixels, padded raster cells) of the single-block paths
+  int lim_pix[2], lim_cells[2];
+};
+
+// ---------------------------------------------------------------------------
+// order-preserving encodings of pixel values
+template <class T> struct Enc;
+template <> struct Enc<uint16_t> {
+  __host__ __device__ static unsigned enc(uint16_t v) { return v; }
+  __host__ __device__ static double dec(unsigned e) { return (double)e; }
+  __host__ __device__ static float decf(unsigned e) { return (float)e; }
+  static constexpr int BITS = 16;
+  static constexpr bool INTEGER = true;
+};
+template <> struct Enc<int16_t> {
+  __host__ __device__ static unsigned enc(int16_t v) { return (unsigned)((int)v + 32768); }
+  __host__ __device__ static double dec(unsigned e) { return (double)((int)e - 32768); }
+  __host__ __device__ static float decf(unsigned e) { return (float)((int)e - 32768); }
+  static constexpr int BITS = 16;
+  static constexpr bool INTEGER = true;
+};
+template <> struct Enc<float> {
+  __device__ static unsigned enc(float v) {
+    unsigned b = __float_as_uint(v);
+    return b ^ ((b & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u);
+  }
+  __device__ static float decf(unsigned e) {
+    unsigned b = (e & 0x80000000u) ? (e ^ 0x80000000u) : ~e;
+    return __uint_as_float(b);
+  }
+  __device__ static double dec(unsigned e) { return (double)decf(e); }
+  static constexpr int BITS = 32;
+  static constexpr bool INTEGER = false;
+};
+
+__host__ __device__ inline unsigned long long mix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Find the slot of `key` in the global label table (read-only), -1 if absent.
+__device__ inline int g_find(const unsigned long long* keys, unsigned hmask, unsigned long long key) {
+  unsigned h = (unsigned)mix64(key) & hmask;
+  for (unsigned i = 0; i <= hmask; ++i) {
+    unsigned long long k = keys[h];
+    if (k == key) return (int)h;
+    if (k == EMPTY_KEY) return -1;
+    h = (h + 1) & hmask;
+  }
+  return -1;
+}
+
+// Division by an invariant 32-bit divisor (Granlund & Montgomery 1994,
+// "Division by invariant integers using multiplication", unsigned case):
+// exact for every 32-bit dividend.
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+  __device__ void init(unsigned d) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)d) ++l;  // l = ceil(log2 d)
+    unsigned long long num = ((1ull << l) - d) << 32;
+    m = (unsigned)(num / d + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l - 1 > 0 ? l - 1 : 0;
+  }
+  __device__ unsigned div(unsigned n) const {
+    unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+// Two-sum (Knuth): s + e = a + b exactly.
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ inline unsigned lanemask_lt() {
+  unsigned m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace nyx

@@ -1,0 +1,472 @@
+// nyx_scan.cu -- label scan: ROI separation of the image + label mask.
+//
+// Paper: "Nyxus architecture" -- features are computed on an internal ROI
+// layout (per-ROI pixel sets) separated from the image and mask; Table S2
+// rows 41, 44-49 (area, bounding box, centroid) fall out of the separation.
+//
+// One streaming pass over image and mask (each byte read once) finds every
+// distinct (image, label > 0) pair and accumulates its pixel count, bounding
+// box and intensity range, plus the intensity range of every image.
+// Aggregation is hierarchical so that few atomics reach global memory:
+//   lane    : its 4 contiguous pixels collapse into runs
+//   warp    : lanes holding the same label merge with match/reduce intrinsics
+//   block   : a shared-memory hash table per 32 x 128 tile
+//   global  : one insert + field atomics per (tile, label)
+#include <cstdio>
+
+#include "nyx_internal.cuh"
+
+namespace nyx {
+
+namespace {
+
+constexpr int TX = 128;   // tile columns (32 lanes x 4 pixels)
+constexpr int TY = 32;    // tile rows
+constexpr int SCAP = 256; // shared table capacity (labels per tile)
+constexpr int SCAN_NT = 256;
+
+__device__ inline void acc_identity(SlotAcc& a) {
+  a.count = 0;
+  a.vmin = 0xFFFFFFFFu;
+  a.vmax = 0;
+  a.xmin = a.ymin = a.zmin = 0x7FFFFFFF;
+  a.xmax = a.ymax = a.zmax = (int)0x80000000;
+}
+
+// Insert-or-find in the global label table; records new slots in slot_list.
+__device__ int g_find_insert(const KParams& p, unsigned long long key) {
+  unsigned h = (unsigned)mix64(key) & p.hmask;
+  for (unsigned i = 0; i <= p.hmask; ++i) {
+    unsigned long long k = p.keys[h];
+    if (k == key) return (int)h;
+    if (k == EMPTY_KEY) {
+      unsigned long long old = atomicCAS(&p.keys[h], EMPTY_KEY, key);
+      if (old == EMPTY_KEY) {
+        unsigned pos = atomicAdd(p.n_used, 1u);
+        p.slot_list[pos] = (int)h;
+        return (int)h;
+      }
+      if (old == key) return (int)h;
+    }
+    h = (h + 1) & p.hmask;
+  }
+  return -1;
+}
+
+__device__ int s_find_insert(unsigned long long* s_key, unsigned long long key) {
+  unsigned h = (unsigned)mix64(key) & (SCAP - 1);
+  for (int i = 0; i < SCAP; ++i) {
+    unsigned long long k = *(volatile unsigned long long*)&s_key[h];
+    if (k == key) return (int)h;
+    if (k == EMPTY_KEY) {
+      unsigned long long old = atomicCAS(&s_key[h], EMPTY_KEY, key);
+      if (old == EMPTY_KEY || old == key) return (int)h;
+    }
+    h = (h + 1) & (SCAP - 1);
+  }
+  return -1;
+}
+
+// Merge one run / group into an accumulator (shared or global memory).
+__device__ inline void acc_merge(SlotAcc* a, unsigned cnt, unsigned vmn, unsigned vmx, int xmn, int xmx, int y, int z) {
+  atomicAdd(&a->count, cnt);
+  atomicMin(&a->vmin, vmn);
+  atomicMax(&a->vmax, vmx);
+  atomicMin(&a->xmin, xmn);
+  atomicMax(&a->xmax, xmx);
+  atomicMin(&a->ymin, y);
+  atomicMax(&a->ymax, y);
+  atomicMin(&a->zmin, z);
+  atomicMax(&a->zmax, z);
+}
+
+__device__ inline void acc_merge_acc(SlotAcc* a, const SlotAcc& s) {
+  atomicAdd(&a->count, s.count);
+  atomicMin(&a->vmin, s.vmin);
+  atomicMax(&a->vmax, s.vmax);
+  atomicMin(&a->xmin, s.xmin);
+  atomicMax(&a->xmax, s.xmax);
+  atomicMin(&a->ymin, s.ymin);
+  atomicMax(&a->ymax, s.ymax);
+  atomicMin(&a->zmin, s.zmin);
+  atomicMax(&a->zmax, s.zmax);
+}
+
+template <class T> struct Vec4;
+template <> struct Vec4<uint16_t> { using V = uint2; };
+template <> struct Vec4<int16_t> { using V = uint2; };
+template <> struct Vec4<float> { using V = uint4; };
+
+template <class T> __device__ inline void unpack4(uint2 v, unsigned ev[4]) {
+  ev[0] = Enc<T>::enc((T)(v.x & 0xFFFFu));
+  ev[1] = Enc<T>::enc((T)(v.x >> 16));
+  ev[2] = Enc<T>::enc((T)(v.y & 0xFFFFu));
+  ev[3] = Enc<T>::enc((T)(v.y >> 16));
+}
+template <class T> __device__ inline void unpack4(uint4 v, unsigned ev[4]) {
+  ev[0] = Enc<T>::enc(__uint_as_float(v.x));
+  ev[1] = Enc<T>::enc(__uint_as_float(v.y));
+  ev[2] = Enc<T>::enc(__uint_as_float(v.z));
+  ev[3] = Enc<T>::enc(__uint_as_float(v.w));
+}
+
+template <class T>
+__device__ inline void load4(const KParams& p, int64_t base, int64_t xs, int lab[4], unsigned ev[4], bool valid[4]) {
+  const T* img = (const T*)p.img;
+  if (p.vec && xs + 3 < p.nx) {
+    int4 m = __ldg((const int4*)(p.mask + base + xs));
+    lab[0] = m.x; lab[1] = m.y; lab[2] = m.z; lab[3] = m.w;
+    const typename Vec4<T>::V v = __ldg((const typename Vec4<T>::V*)(img + base + xs));
+    unpack4<T>(v, ev);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) valid[j] = true;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      valid[j] = xs + j < p.nx;
+      lab[j] = valid[j] ? p.mask[base + xs + j] : 0;
+      ev[j] = valid[j] ? Enc<T>::enc(img[base + xs + j]) : 0;
+    }
+  }
+}
+
+template <class T> __device__ inline bool finite_enc(unsigned) { return true; }
+template <> __device__ inline bool finite_enc<float>(unsigned e) { return isfinite(Enc<float>::decf(e)); }
+
+}  // namespace
+
+template <class T>
+__global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
+  __shared__ unsigned long long s_key[SCAP];
+  __shared__ SlotAcc s_acc[SCAP];
+  for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
+    s_key[i] = EMPTY_KEY;
+    acc_identity(s_acc[i]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (p.rows_total + TY - 1) / TY;
+  const int64_t ntiles = ntx * nty;
+  unsigned im_mn = 0xFFFFFFFFu, im_mx = 0;
+  int64_t im_b = -1;
+  unsigned errbits = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t ty = t / ntx, tx = t - ty * ntx;
+    const int64_t x0 = tx * TX;
+    for (int rr = warp; rr < TY; rr += SCAN_NT / 32) {
+      const int64_t row = ty * TY + rr;
+      if (row >= p.rows_total) break;
+      const int64_t y = row % p.ny, zb = row / p.ny;
+      const int64_t z = zb % p.nz, b = zb / p.nz;
+      if (b != im_b) {  // warp-uniform: flush the running image range
+        unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
+        if (lane == 0 && im_b >= 0) {
+          atomicMin(&p.img_vmin[im_b], mn);
+          atomicMax(&p.img_vmax[im_b], mx);
+        }
+        im_b = b;
+        im_mn = 0xFFFFFFFFu;
+        im_mx = 0;
+      }
+      const int64_t xs = x0 + 4 * lane;
+      int lab[4];
+      unsigned ev[4];
+      bool valid[4];
+      load4<T>(p, row * p.nx, xs, lab, ev, valid);
+      // lane-local runs of equal label; a run is identified by its first
+      // pixel j, and round j merges the runs that start at pixel j
+      int L[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        L[j] = valid[j] ? lab[j] : 0;
+        if (valid[j]) {
+          im_mn = min(im_mn, ev[j]);
+          im_mx = max(im_mx, ev[j]);
+          if (L[j] < 0) errbits |= E_BAD_LABEL;
+          if (L[j] > 0 && !finite_enc<T>(ev[j])) errbits |= E_NONFINITE;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool act = L[j] > 0 && (j == 0 || L[j - 1] != L[j]);
+        if (!__any_sync(0xFFFFFFFFu, act)) continue;
+        unsigned c = 0, mn = 0xFFFFFFFFu, mx = 0;
+        int xe = j;
+        bool cont = true;
+#pragma unroll
+        for (int q = j; q < 4; ++q) {
+          cont = cont && L[q] == L[j];
+          if (cont) {
+            ++c;
+            mn = min(mn, ev[q]);
+            mx = max(mx, ev[q]);
+            xe = q;
+          }
+        }
+        const unsigned long long k =
+            act ? (((unsigned long long)b << 32) | (unsigned)L[j]) : (0xFFFFFFFF00000000ull | (unsigned)lane);
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+        const unsigned cnt = __reduce_add_sync(peers, act ? c : 0u);
+        const unsigned vmn = __reduce_min_sync(peers, act ? mn : 0xFFFFFFFFu);
+        const unsigned vmx = __reduce_max_sync(peers, act ? mx : 0u);
+        const int xmn = (int)__reduce_min_sync(peers, act ? (unsigned)(xs + j) : 0x7FFFFFFFu);
+        const int xmx = (int)__reduce_max_sync(peers, act ? (unsigned)(xs + xe) : 0u);
+        if (act && (peers & lanemask_lt()) == 0) {
+          const int s = s_find_insert(s_key, k);
+          if (s >= 0) {
+            acc_merge(&s_acc[s], cnt, vmn, vmx, xmn, xmx, (int)y, (int)z);
+          } else {
+            const int g = g_find_insert(p, k);
+            if (g >= 0) acc_merge(&p.slots[g], cnt, vmn, vmx, xmn, xmx, (int)y, (int)z);
+            else errbits |= E_HASH_FULL;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // flush the tile table to the global label table
+    for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
+      unsigned long long k = s_key[i];
+      if (k == EMPTY_KEY) continue;
+      int g = g_find_insert(p, k);
+      if (g >= 0) acc_merge_acc(&p.slots[g], s_acc[i]);
+      else errbits |= E_HASH_FULL;
+      s_key[i] = EMPTY_KEY;
+      acc_identity(s_acc[i]);
+    }
+    __syncthreads();
+  }
+  {
+    unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
+    bool any = __any_sync(0xFFFFFFFFu, im_b >= 0);
+    long long bb = __reduce_max_sync(0xFFFFFFFFu, (unsigned)(im_b + 1)) - 1;  // warp-uniform image index
+    if (lane == 0 && any && bb >= 0) {
+      atomicMin(&p.img_vmin[bb], mn);
+      atomicMax(&p.img_vmax[bb], mx);
+    }
+  }
+  errbits = __reduce_or_sync(0xFFFFFFFFu, errbits);
+  if (lane == 0 && errbits) atomicOr(p.err, errbits);
+}
+
+// Sort the distinct keys ascending (bitonic, one block, shared memory):
+// dense ROI id = rank of its (image, label) key.
+__global__ void __launch_bounds__(1024) k_sort_keys(KParams p) {
+  extern __shared__ unsigned long long s_sort[];
+  const unsigned n = *p.n_used;
+  // the host sized s_sort for min(max_rois, SORT_CAP) keys
+  if (n > (unsigned)SORT_CAP || (int64_t)n > p.max_rois) {
+    if (threadIdx.x == 0) {
+      atomicOr(p.err, n > (unsigned)SORT_CAP ? E_SORT_CAP : E_ROI_CAP);
+      *p.n_roi = 0;
+      if (p.n_roi_out) *p.n_roi_out = (int64_t)n;
+    }
+    return;
+  }
+  unsigned np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (unsigned i = threadIdx.x; i < np2; i += blockDim.x)
+    s_sort[i] = i < n ? p.keys[p.slot_list[i]] : EMPTY_KEY;
+  __syncthreads();
+  for (unsigned k = 2; k <= np2; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      for (unsigned i = threadIdx.x; i < np2; i += blockDim.x) {
+        unsigned ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = s_sort[i], c = s_sort[ixj];
+          bool up = (i & k) == 0;
+          if ((a > c) == up) {
+            s_sort[i] = c;
+            s_sort[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) p.sorted_keys[i] = s_sort[i];
+  if (threadIdx.x == 0) {
+    *p.n_roi = n;
+    if (p.n_roi_out) *p.n_roi_out = (int64_t)n;
+    if ((int64_t)n > p.cap_roi) atomicOr(p.err, E_ROI_CAP);
+  }
+}
+
+// Per ROI: gather its scan accumulator, decide the processing class and
+// append it to that class's work queue.
+__global__ void k_setup(KParams p) {
+  const unsigned n = *p.n_roi;
+  const int pad = (p.need & NEED_GLCM) ? p.pad : 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long key = p.sorted_keys[i];
+    const int s = g_find(p.keys, p.hmask, key);
+    RoiInfo r;
+    r.key = key;
+    if (s < 0) {  // cannot happen: every sorted key came from the table
+      atomicOr(p.err, E_INTERNAL);
+      r.n = 0;
+      r.cls = 3;
+      p.rois[i] = r;
+      continue;
+    }
+    p.slot_dense[s] = (int)i;
+    const SlotAcc a = p.slots[s];
+    r.n = a.count;
+    r.x0 = a.xmin;
+    r.y0 = a.ymin;
+    r.z0 = a.zmin;
+    r.w = a.xmax - a.xmin + 1;
+    r.h = a.ymax - a.ymin + 1;
+    r.d = a.zmax - a.zmin + 1;
+    r.vmin = a.vmin;
+    r.vmax = a.vmax;
+    const long long cells = (long long)(r.w + 2 * pad) * (r.h + 2 * pad) * (p.ndim == 3 ? r.d + 2 * pad : 1);
+    bool pack_ok = p.ndim == 3 ? (r.w + 2 * pad <= 2048 && r.h + 2 * pad <= 2048 && r.d + 2 * pad <= 1024)
+                               : (r.w + 2 * pad <= 65535 && r.h + 2 * pad <= 65535);
+    int cls = 2;
+    if (pack_ok && r.n <= (unsigned)p.lim_pix[0] && cells <= p.lim_cells[0]) cls = 0;
+    else if (pack_ok && r.n <= (unsigned)p.lim_pix[1] && cells <= p.lim_cells[1]) cls = 1;
+    r.cls = cls;
+    r.pad = 0;
+    p.rois[i] = r;
+    if ((int64_t)i >= p.cap_roi) continue;  // no room for its output row
+    if (cls == 2) {
+      atomicOr(p.err, E_TOO_LARGE);
+      continue;
+    }
+    unsigned q = atomicAdd(&p.qlen[cls], 1u);
+    p.queue[(int64_t)cls * p.max_rois + q] = (int)i;
+  }
+}
+
+// Return the label table to its empty state (only the slots this call used).
+__global__ void k_reset(KParams p) {
+  const unsigned n = *p.n_used;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = p.slot_list[i];
+    p.keys[s] = EMPTY_KEY;
+    acc_identity(p.slots[s]);
+  }
+}
+
+__global__ void k_init_table(KParams p, unsigned cap) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+    p.keys[i] = EMPTY_KEY;
+    acc_identity(p.slots[i]);
+  }
+}
+
+// Per-pixel GLCM bin (test hook): rule a4 with the ROI's min/max.
+template <class T>
+__global__ void k_debug_bins(KParams p, uint16_t* out) {
+  const int64_t total = p.rows_total * p.nx;
+  const int64_t per = p.nx * p.ny * p.nz;
+  const T* img = (const T*)p.img;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int L = p.mask[i];
+    uint16_t res = 0xFFFF;
+    if (L > 0) {
+      const unsigned long long key = ((unsigned long long)(i / per) << 32) | (unsigned)L;
+      const int s = g_find(p.keys, p.hmask, key);
+      if (s >= 0) {
+        const RoiInfo r = p.rois[p.slot_dense[s]];
+        const unsigned e = Enc<T>::enc(img[i]);
+        if (r.vmax == r.vmin) {
+          res = 0;
+        } else if (Enc<T>::INTEGER) {
+          unsigned long long q = (unsigned long long)p.ng * (e - r.vmin) / (r.vmax - r.vmin);
+          res = (uint16_t)(q > (unsigned)(p.ng - 1) ? p.ng - 1 : q);
+        } else {
+          double x = Enc<T>::dec(e), mn = Enc<T>::dec(r.vmin), mx = Enc<T>::dec(r.vmax);
+          double q = __ddiv_rn(__dmul_rn((double)p.ng, __dsub_rn(x, mn)), __dsub_rn(mx, mn));
+          long long b = (long long)floor(q);
+          res = (uint16_t)(b > p.ng - 1 ? p.ng - 1 : (b < 0 ? 0 : b));
+        }
+      }
+    }
+    out[i] = res;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers (kernel templates are launched only from this file)
+
+__global__ void k_begin(KParams p) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    *p.n_used = 0;
+    *p.n_roi = 0;
+  }
+  if (t < 3) {
+    p.qlen[t] = 0;
+    p.qhead[t] = 0;
+  }
+  for (int b = t; b < p.batch; b += blockDim.x) {
+    p.img_vmin[b] = 0xFFFFFFFFu;
+    p.img_vmax[b] = 0;
+  }
+}
+
+template <class T>
+static cudaError_t launch_scan_t(const KParams& p, int nsm, cudaStream_t st) {
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<T>, SCAN_NT, 0);
+  if (e != cudaSuccess) return e;
+  k_scan<T><<<(nb > 0 ? nb : 1) * nsm, SCAN_NT, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+// counters reset + label scan
+cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st) {
+  k_begin<<<1, 256, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  switch (p.dtype) {
+    case NYX_U16: return launch_scan_t<uint16_t>(p, nsm, st);
+    case NYX_I16: return launch_scan_t<int16_t>(p, nsm, st);
+    default: return launch_scan_t<float>(p, nsm, st);
+  }
+}
+
+// key sort (one block) + per-ROI setup
+cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st) {
+  unsigned np2 = 1;
+  while (np2 < (unsigned)p.max_rois && np2 < (unsigned)SORT_CAP) np2 <<= 1;
+  const int smem = (int)(8 * np2);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static int configured[64] = {0};
+  if (dev < 64 && configured[dev] < smem) {
+    e = cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured[dev] = smem;
+  }
+  k_sort_keys<<<1, 1024, smem, st>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int g = (int)((p.max_rois + 255) / 256);
+  if (g > 4 * nsm) g = 4 * nsm;
+  k_setup<<<g, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const KParams& p, int nsm, cudaStream_t st) {
+  k_reset<<<2 * nsm, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_table(const KParams& p, unsigned cap, cudaStream_t st) {
+  k_init_table<<<256, 256, 0, st>>>(p, cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_bins(const KParams& p, uint16_t* out, int nsm, cudaStream_t st) {
+  switch (p.dtype) {
+    case NYX_U16: k_debug_bins<uint16_t><<<4 * nsm, 256, 0, st>>>(p, out); break;
+    case NYX_I16: k_debug_bins<int16_t><<<4 * nsm, 256, 0, st>>>(p, out); break;
+    default: k_debug_bins<float><<<4 * nsm, 256, 0, st>>>(p, out); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nyx

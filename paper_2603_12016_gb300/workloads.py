@@ -1,0 +1,253 @@
+"""Seeded synthetic image + label-mask workloads.
+
+The paper measures on TissueNet (2D fluorescence), the Medical Segmentation
+Decathlon (3D CT/MR) and a synthetic slide set of varying ROI size and count
+(Fig. 3 and its "scalability" paragraph).  None of those datasets is
+available here, so these generators produce inputs with the same shape of
+problem: an intensity image plus an int32 label mask whose ROIs have the
+size ranges and counts of the benchmark configurations.
+
+This module holds no feature arithmetic: it only draws random numbers and
+paints shapes.  Both the CUDA path and the CPU oracle receive its arrays.
+Every generator is deterministic in its seed (NumPy PCG64).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Dict, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    image: np.ndarray          # [batch,] [z,] y, x
+    mask: np.ndarray           # int32, same shape
+    ndim: int                  # spatial dimensions (2 or 3)
+    params: Dict = field(default_factory=dict)   # extraction hyperparameters
+    meta: Dict = field(default_factory=dict)     # realised counts / sizes
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _relabel_drop_small(mask: np.ndarray, min_px: int) -> np.ndarray:
+    """Remove labels with fewer than min_px pixels (set to background)."""
+    labels, counts = np.unique(mask, return_counts=True)
+    small = labels[(counts < min_px) & (labels > 0)]
+    if len(small):
+        mask[np.isin(mask, small)] = 0
+    return mask
+
+
+def _meta(mask: np.ndarray) -> Dict:
+    labels, counts = np.unique(mask[mask > 0], return_counts=True)
+    return {
+        "n_roi": int(len(labels)),
+        "roi_px_total": int(counts.sum()) if len(counts) else 0,
+        "roi_px_min": int(counts.min()) if len(counts) else 0,
+        "roi_px_max": int(counts.max()) if len(counts) else 0,
+        "roi_px_median": float(np.median(counts)) if len(counts) else 0.0,
+        "coverage": float(counts.sum() / mask.size) if len(counts) else 0.0,
+    }
+
+
+# ---------------------------------------------------------------------------
+# 2D small: Gaussian blobs, Voronoi ROIs cut by a per-blob radius
+
+def blobs_2d(size: int = 256, n_blobs: int = 64, seed: int = 1001, ng: int = 32) -> Workload:
+    """256x256 uint16: Gamma(k=2, theta=300) background plus Gaussian blobs
+    (sigma 3-10 px, peak 2000-40000).  The mask is the Voronoi partition of
+    the blob centres, restricted to a disc per blob whose area is drawn from
+    [50, 1500] px."""
+    rng = _rng(seed)
+    img = rng.gamma(2.0, 300.0, size=(size, size))
+    cy = rng.uniform(8, size - 8, n_blobs)
+    cx = rng.uniform(8, size - 8, n_blobs)
+    sig = rng.uniform(3, 10, n_blobs)
+    peak = rng.uniform(2000, 40000, n_blobs)
+    area = rng.uniform(50, 1500, n_blobs)
+    yy, xx = np.mgrid[0:size, 0:size].astype(np.float64)
+    d2 = (yy[None] - cy[:, None, None]) ** 2 + (xx[None] - cx[:, None, None]) ** 2
+    for k in range(n_blobs):
+        img += peak[k] * np.exp(-d2[k] / (2 * sig[k] ** 2))
+    owner = np.argmin(d2, axis=0)
+    radius2 = area / math.pi
+    mine = np.take_along_axis(d2, owner[None], 0)[0]
+    mask = np.where(mine <= radius2[owner], owner + 1, 0).astype(np.int32)
+    mask = _relabel_drop_small(mask, 20)
+    img = np.clip(np.rint(img), 0, 65535).astype(np.uint16)
+    return Workload("blobs2d_256_u16_64roi", img, mask, 2,
+                    params=dict(glcm_levels=ng, dists=(1,), hist_bins=256), meta=_meta(mask))
+
+
+# ---------------------------------------------------------------------------
+# 2D fluorescence-like: ellipses on Gamma background with salt noise
+
+def _paint_ellipses(mask, img, cy, cx, a, b, th, labels, value_fn):
+    H, W = mask.shape
+    for k in range(len(cy)):
+        r = max(a[k], b[k]) + 1
+        y0, y1 = max(0, int(cy[k] - r)), min(H, int(cy[k] + r) + 2)
+        x0, x1 = max(0, int(cx[k] - r)), min(W, int(cx[k] + r) + 2)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+        dy, dx = yy - cy[k], xx - cx[k]
+        c, s = math.cos(th[k]), math.sin(th[k])
+        u = (dx * c + dy * s) / a[k]
+        v = (-dx * s + dy * c) / b[k]
+        inside = u * u + v * v <= 1.0
+        mask[y0:y1, x0:x1][inside] = labels[k]
+        if img is not None:
+            sub = img[y0:y1, x0:x1]
+            sub[inside] = value_fn(k, int(inside.sum()), sub[inside])
+
+
+def nuclei_2d(size: int = 2048, n_roi: int = 4000, seed: int = 1002, ng: int = 256,
+              dists=(1, 2), salt: float = 0.02, axis_range=(4.0, 40.0), min_px: int = 50) -> Workload:
+    """2048x2048 uint16 fluorescence-like image: Gamma(2, 300) background,
+    n_roi ellipses (log-uniform semi-axes in axis_range, random angle) whose
+    brightness ~ lognormal(mu=8, sigma=0.6) is added with +-20% per-pixel
+    texture, then `salt` of all pixels set to 65535.  Ellipses are painted in
+    random order (later ones overwrite); ROIs under min_px are dropped."""
+    rng = _rng(seed)
+    img = rng.gamma(2.0, 300.0, size=(size, size))
+    mask = np.zeros((size, size), dtype=np.int32)
+    lo, hi = math.log(axis_range[0]), math.log(axis_range[1])
+    a = np.exp(rng.uniform(lo, hi, n_roi))
+    b = np.exp(rng.uniform(lo, hi, n_roi))
+    th = rng.uniform(0, math.pi, n_roi)
+    cy = rng.uniform(0, size, n_roi)
+    cx = rng.uniform(0, size, n_roi)
+    bright = rng.lognormal(8.0, 0.6, n_roi)
+    labels = rng.permutation(n_roi).astype(np.int32) + 1
+    tex = rng.uniform(0.8, 1.2, size=(size, size))
+
+    def val(k, n, cur):
+        return cur + bright[k]
+
+    _paint_ellipses(mask, img, cy, cx, a, b, th, labels, val)
+    inroi = mask > 0
+    img[inroi] = img[inroi] * tex[inroi]
+    salt_px = rng.random((size, size)) < salt
+    img[salt_px] = 65535
+    mask = _relabel_drop_small(mask, min_px)
+    img = np.clip(np.rint(img), 0, 65535).astype(np.uint16)
+    return Workload(f"nuclei2d_{size}_u16_{n_roi}roi", img, mask, 2,
+                    params=dict(glcm_levels=ng, dists=tuple(dists), hist_bins=256), meta=_meta(mask))
+
+
+# ---------------------------------------------------------------------------
+# 3D CT-like volume: smoothed random field + ellipsoids
+
+def _smooth_field(rng, shape, sigma):
+    from scipy.ndimage import gaussian_filter
+
+    f = gaussian_filter(rng.standard_normal(shape).astype(np.float32), sigma=sigma, mode="wrap")
+    f /= max(float(f.std()), 1e-6)
+    return f
+
+
+def ct_3d(shape=(128, 512, 512), n_roi: int = 200, seed: int = 1003, ng: int = 64,
+          vol_range=(1e3, 1e6), force_extremes: bool = True) -> Workload:
+    """512x512x128 int16 in [-1000, 3000]: a Gaussian-smoothed (sigma = 4 vox)
+    random field (background around -300) plus n_roi ellipsoids with volumes
+    log-uniform in vol_range (one forced to each end), each with a positive
+    mean interior (200-1500 HU plus the field)."""
+    rng = _rng(seed)
+    Z, Y, X = shape
+    field = _smooth_field(rng, shape, 4.0)
+    img = -300.0 + 250.0 * field
+    mask = np.zeros(shape, dtype=np.int32)
+    vol = np.exp(rng.uniform(math.log(vol_range[0]), math.log(vol_range[1]), n_roi))
+    if force_extremes and n_roi >= 2:
+        vol[0], vol[1] = vol_range[1], vol_range[0]
+    order = rng.permutation(n_roi)
+    level = rng.uniform(200, 1500, n_roi)
+    labels = rng.permutation(n_roi).astype(np.int32) + 1
+    zmax_semi = (Z - 2) / 2.0
+    for k in order:
+        r = (3 * vol[k] / (4 * math.pi)) ** (1 / 3)
+        ez = rng.uniform(0.7, 1.0)
+        ey = rng.uniform(0.8, 1.3)
+        c = min(r * ez, zmax_semi)
+        ab = vol[k] * 3 / (4 * math.pi) / c
+        a = math.sqrt(ab * ey)
+        b = ab / a
+        cz = rng.uniform(c, Z - c) if Z > 2 * c else Z / 2
+        cy = rng.uniform(0, Y)
+        cx = rng.uniform(0, X)
+        z0, z1 = max(0, int(cz - c) - 1), min(Z, int(cz + c) + 2)
+        y0, y1 = max(0, int(cy - b) - 1), min(Y, int(cy + b) + 2)
+        x0, x1 = max(0, int(cx - a) - 1), min(X, int(cx + a) + 2)
+        zz, yy, xx = np.ogrid[z0:z1, y0:y1, x0:x1]
+        inside = ((zz - cz) / c) ** 2 + ((yy - cy) / b) ** 2 + ((xx - cx) / a) ** 2 <= 1.0
+        mask[z0:z1, y0:y1, x0:x1][inside] = labels[k]
+        sub = img[z0:z1, y0:y1, x0:x1]
+        sub[inside] = level[k] + 200.0 * field[z0:z1, y0:y1, x0:x1][inside]
+    mask = _relabel_drop_small(mask, 100)
+    img = np.clip(np.rint(img), -1000, 3000).astype(np.int16)
+    return Workload(f"ct3d_{X}x{Y}x{Z}_i16_{n_roi}roi", img, mask, 3,
+                    params=dict(glcm_levels=ng, dists=(1,), hist_bins=256), meta=_meta(mask))
+
+
+# ---------------------------------------------------------------------------
+# batch of float32 blob images (differentiation workload)
+
+def blob_batch_f32(batch: int = 64, size: int = 512, seed: int = 1004, roi_range=(4, 256),
+                   px_range=(30, 20000), coverage: float = 0.7) -> Workload:
+    """batch x size x size float32 images of Gaussian blobs on N(100, 10)
+    background; image b holds n_b ROIs (log-uniform in roi_range) whose disc
+    areas are log-uniform in px_range, scaled down so that the summed area
+    stays under `coverage` of the image."""
+    rng = _rng(seed)
+    img = rng.normal(100.0, 10.0, size=(batch, size, size)).astype(np.float32)
+    mask = np.zeros((batch, size, size), dtype=np.int32)
+    yy, xx = np.mgrid[0:size, 0:size].astype(np.float32)
+    lo, hi = math.log(roi_range[0]), math.log(roi_range[1])
+    for bi in range(batch):
+        n = int(round(math.exp(rng.uniform(lo, hi))))
+        areas = np.exp(rng.uniform(math.log(px_range[0]), math.log(px_range[1]), n))
+        tot = areas.sum()
+        if tot > coverage * size * size:
+            areas *= coverage * size * size / tot
+        labels = rng.permutation(n).astype(np.int32) + 1
+        for k in range(n):
+            r = math.sqrt(max(areas[k], px_range[0]) / math.pi)
+            cy, cx = rng.uniform(r, size - r), rng.uniform(r, size - r)
+            amp = rng.uniform(200, 2000)
+            sig = max(r / 2.0, 1.0)
+            y0, y1 = max(0, int(cy - r) - 1), min(size, int(cy + r) + 2)
+            x0, x1 = max(0, int(cx - r) - 1), min(size, int(cx + r) + 2)
+            d2 = (yy[y0:y1, x0:x1] - cy) ** 2 + (xx[y0:y1, x0:x1] - cx) ** 2
+            img[bi, y0:y1, x0:x1] += (amp * np.exp(-d2 / (2 * sig * sig))).astype(np.float32)
+            mask[bi, y0:y1, x0:x1][d2 <= r * r] = labels[k]
+    for bi in range(batch):
+        mask[bi] = _relabel_drop_small(mask[bi], 10)
+    return Workload(f"blobbatch_{batch}x{size}_f32", img, mask, 2,
+                    params=dict(glcm_levels=0, dists=(1,), hist_bins=256), meta=_meta(mask))
+
+
+# ---------------------------------------------------------------------------
+# named configurations (sizes of the benchmark table) and small variants
+
+def config(name: str, seed_offset: int = 0) -> Workload:
+    if name == "blobs2d":
+        return blobs_2d(seed=1001 + seed_offset)
+    if name == "nuclei2d":
+        return nuclei_2d(seed=1002 + seed_offset)
+    if name == "nuclei2d_small":
+        return nuclei_2d(size=512, n_roi=250, seed=1102 + seed_offset)
+    if name == "ct3d":
+        return ct_3d(seed=1003 + seed_offset)
+    if name == "ct3d_small":
+        return ct_3d(shape=(32, 96, 96), n_roi=12, seed=1103 + seed_offset, vol_range=(200, 2e4))
+    if name == "blobbatch":
+        return blob_batch_f32(seed=1004 + seed_offset)
+    if name == "blobbatch_small":
+        return blob_batch_f32(batch=4, size=128, seed=1104 + seed_offset, roi_range=(4, 32), px_range=(30, 2000))
+    raise KeyError(name)

@@ -1,0 +1,61 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports
+every function include/nyx.h declares, and its host-only calls behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nyxlib():
+    from paper_2603_12016_gb300 import build
+
+    build.build()
+    from paper_2603_12016_gb300 import nyx
+
+    return nyx
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nyx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nyx_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("nyx_create", "nyx_plan_create", "nyx_extract", "nyx_count_rois", "nyx_backward",
+                 "nyx_num_columns", "nyx_column_name", "nyx_sync_status", "nyx_debug_glcm", "nyx_debug_bins"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(nyxlib):
+    L = nyxlib.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_feature_ids(nyxlib):
+    fid = nyxlib.feature_id
+    assert fid("MEAN") == 0 and fid("UNIFORMITY") == 40
+    assert fid("INT_M") == 41 and fid("BIN_HU") == 50
+    assert fid("GLCM_ASM") == 51 and fid("GLCM_VARIANCE") == 80
+    assert fid("NOPE") == -1
+    ids = [fid(n) for n in ("MEAN", "INT_HU", "GLCM_CORR")]
+    assert len(set(ids)) == 3
+
+
+def test_params_default_and_validation(nyxlib):
+    L = nyxlib.lib()
+    p = nyxlib.NyxParams()
+    assert L.nyx_params_default(ctypes.byref(p), 640, 480) == 0
+    assert p.struct_size == ctypes.sizeof(nyxlib.NyxParams)
+    assert (p.dims[0], p.dims[1], p.dims[2], p.ndim, p.batch) == (640, 480, 1, 2, 1)
+    assert p.glcm_levels == 64 and p.hist_bins == 256 and all(m == 2 ** 64 - 1 for m in p.feature_mask)
+    # a null context is rejected before any device call
+    assert L.nyx_plan_create(None, ctypes.byref(p), ctypes.byref(ctypes.c_void_p())) == 1
+    assert L.nyx_create(None, 0) == 1
+    assert L.nyx_extract(None, None, None, None, 0, None, 0, None) == 1
