@@ -72,15 +72,101 @@ struct SmemLayout {
 };
 
 // ----------------------------------------------------------------------------
-// block reductions
+// Arithmetic discipline.  GB300's FP64 pipe retires a few thread-operations
+// per clock per SM and occupies it for a whole warp instruction even when one
+// lane is active, so the fast path keeps every per-pixel AND per-ROI step in
+// the accumulation type A (float), converts results to the FP64 table with
+// integer bit manipulation, and uses FP64 arithmetic only where an output must
+// match a double-precision definition bit for bit (percentile interpolation).
+// With A = double (the plain FP64 path) the same code runs in FP64.
+
+// exact float -> double without the FP64 pipe
+__device__ inline double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned ex = (u >> 23) & 0xFFu, man = u & 0x7FFFFFu;
+  unsigned long long bits;
+  if (ex == 0xFFu) {
+    bits = sign | 0x7FF0000000000000ull | ((unsigned long long)man << 29);
+  } else if (ex != 0) {
+    bits = sign | ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)man << 29);
+  } else if (man == 0) {
+    bits = sign;
+  } else {  // subnormal float: normalise
+    const int lz = __clz(man) - 8;  // leading zeros within the 23-bit field
+    const unsigned m = (man << (lz + 1)) & 0x7FFFFFu;
+    bits = sign | ((unsigned long long)(896 - lz) << 52) | ((unsigned long long)m << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// f * 2^e2 as a double (exact; the result is assumed to be a normal double)
+__device__ inline double f2d_scaled(float f, int e2) {
+  double d = f2d(f);
+  long long b = __double_as_longlong(d);
+  const long long ex = (b >> 52) & 0x7FF;
+  if (ex == 0 || ex == 0x7FF) return d;  // zero / inf / nan unchanged
+  b += (long long)e2 << 52;
+  return __longlong_as_double(b);
+}
+
+// exact integer -> double for |v| < 2^53 without the FP64 pipe
+__device__ inline double i2d(long long v) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int msb = 63 - __clzll((long long)a);
+  const unsigned long long man = (a << (52 - msb)) & ((1ull << 52) - 1);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(msb + 1023) << 52) | man));
+}
+
+__device__ inline double to_d(float v) { return f2d(v); }
+__device__ inline double to_d(double v) { return v; }
+
+__device__ inline void put(const KParams& p, double* row, int q, double v) {
+  const int c = __ldg(p.col_map + q);
+  if (c >= 0) row[c] = v;
+}
+template <class A>
+__device__ inline void putA(const KParams& p, double* row, int q, A v) {
+  const int c = __ldg(p.col_map + q);
+  if (c >= 0) row[c] = to_d(v);
+}
+
+__device__ inline float alog2(float x) { return log2f(x); }
+__device__ inline double alog2(double x) { return log2(x); }
+__device__ inline float asqrt(float x) { return sqrtf(x); }
+__device__ inline double asqrt(double x) { return sqrt(x); }
+__device__ inline float aexp(float x) { return expf(x); }
+__device__ inline double aexp(double x) { return exp(x); }
+__device__ inline float acbrt(float x) { return cbrtf(x); }
+__device__ inline double acbrt(double x) { return cbrt(x); }
+
+template <class A>
+__device__ inline A anan() {
+  if constexpr (std::is_same<A, float>::value) return __int_as_float(0x7FC00000);
+  else return __longlong_as_double(0x7FF8000000000000ll);
+}
+
+// decode an encoded value straight into the accumulation type
+template <class T, class A>
+__device__ inline A decA(unsigned e) {
+  if constexpr (std::is_same<A, float>::value) return Enc<T>::decf(e);
+  else return Enc<T>::dec(e);
+}
+
+// ----------------------------------------------------------------------------
+// block reductions (results are left in shared memory for every thread)
 
 template <class C, class A, int NV>
-__device__ inline void block_sum(A (&v)[NV], double* scratch, double* out) {
+__device__ inline void block_sum(A (&v)[NV], double* scratch, A* out) {
   static_assert(NV <= RED_MAX, "reduction too wide");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (std::is_same<A, float>::value) {
+    // compensated (hi, lo) float pairs through the warp tree and across warps
+    float2* sc = (float2*)scratch;
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if constexpr (std::is_same<A, float>::value) {
+    for (int i = 0; i < NV; ++i) {
       float hi = v[i], lo = 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -91,19 +177,34 @@ __device__ inline void block_sum(A (&v)[NV], double* scratch, double* out) {
         hi = s;
         lo = __fadd_rn(__fadd_rn(lo, l2), e);
       }
-      if (lane == 0) scratch[warp * NV + i] = (double)hi + (double)lo;
-    } else {
+      if (lane == 0) sc[warp * NV + i] = make_float2(hi, lo);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NV; i += C::NT) {
+      float hi = 0.f, lo = 0.f;
+      for (int w = 0; w < C::NW; ++w) {
+        const float2 x = sc[w * NV + i];
+        float s, e;
+        two_sum(hi, x.x, s, e);
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, x.y), e);
+      }
+      out[i] = __fadd_rn(hi, lo);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
       double x = v[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
       if (lane == 0) scratch[warp * NV + i] = x;
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NV; i += C::NT) {
-    double s = 0;
-    for (int w = 0; w < C::NW; ++w) s += scratch[w * NV + i];
-    out[i] = s;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NV; i += C::NT) {
+      double s = 0;
+      for (int w = 0; w < C::NW; ++w) s += scratch[w * NV + i];
+      out[i] = s;
+    }
   }
   __syncthreads();
 }
@@ -129,26 +230,12 @@ __device__ inline void block_sum_i64(long long (&v)[NV], double* scratch_d, long
 }
 
 template <class C>
-__device__ inline float block_max(float v, double* scratch_d) {
-  float* scratch = (float*)scratch_d;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-  if (lane == 0) scratch[warp] = v;
-  __syncthreads();
-  float m = scratch[0];
-  for (int w = 1; w < C::NW; ++w) m = fmaxf(m, scratch[w]);
-  __syncthreads();
-  return m;
-}
-
-template <class C>
 __device__ inline unsigned long long block_max_u64(unsigned long long v, double* scratch_d) {
   unsigned long long* scratch = (unsigned long long*)scratch_d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, v, o);
     v = u > v ? u : v;
   }
   if (lane == 0) scratch[warp] = v;
@@ -178,27 +265,7 @@ __device__ inline void warp_exclusive_scan(unsigned* a, int n) {
 }
 
 // ----------------------------------------------------------------------------
-// helpers
-
-__device__ inline void put(const KParams& p, double* row, int q, double v) {
-  const int c = __ldg(p.col_map + q);
-  if (c >= 0) row[c] = v;
-}
-
-__device__ inline double ipow_d(double x, int k) {
-  double r = 1.0;
-  for (int i = 0; i < k; ++i) r *= x;
-  return r;
-}
-
-__device__ inline float alog2(float x) { return log2f(x); }
-__device__ inline double alog2(double x) { return log2(x); }
-
-__device__ inline int binom(int n, int k) {
-  int r = 1;
-  for (int i = 0; i < k; ++i) r = r * (n - i) / (i + 1);
-  return r;
-}
+// moments helpers
 
 // moment index <-> exponents (p, q, r), lexicographic with p+q+r <= 3
 // (2D: r = 0, 10 entries; 3D: 20 entries)
@@ -223,10 +290,15 @@ __device__ inline void mexp(int k, int& p, int& q, int& r) {
   p = q = r = 0;
 }
 
+// binomial coefficients C(n, k) for n <= 6
+__device__ __constant__ const signed char c_binom[7][7] = {{1},          {1, 1},          {1, 2, 1},
+                                                           {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
+                                                           {1, 6, 15, 20, 15, 6, 1}};
+
 // Hu's seven invariants (Hu 1962) from normalised central moments.
-__device__ inline void hu7(double n20, double n02, double n11, double n30, double n21, double n12, double n03,
-                           double* h) {
-  const double a = n30 - 3 * n12, b = 3 * n21 - n03, s = n30 + n12, t = n21 + n03;
+template <class A>
+__device__ inline void hu7(A n20, A n02, A n11, A n30, A n21, A n12, A n03, A* h) {
+  const A a = n30 - 3 * n12, b = 3 * n21 - n03, s = n30 + n12, t = n21 + n03;
   h[0] = n20 + n02;
   h[1] = (n20 - n02) * (n20 - n02) + 4 * n11 * n11;
   h[2] = a * a + b * b;
@@ -236,18 +308,18 @@ __device__ inline void hu7(double n20, double n02, double n11, double n30, doubl
   h[6] = b * s * (s * s - 3 * t * t) - a * t * (3 * s * s - t * t);
 }
 
-// normalisation exponent mu00^(1 + o/2) (2D) or mu000^(1 + o/3) (3D)
-template <int NDIM>
-__device__ inline double norm_pow(double m00, int o) {
+// normalisation mu00^(1 + o/2) (2D) or mu000^(1 + o/3) (3D)
+template <int NDIM, class A>
+__device__ inline A norm_pow(A m00, int o) {
   if (NDIM == 2) {
     switch (o) {
       case 0: return m00;
-      case 1: return m00 * sqrt(m00);
+      case 1: return m00 * asqrt(m00);
       case 2: return m00 * m00;
-      default: return m00 * m00 * sqrt(m00);
+      default: return m00 * m00 * asqrt(m00);
     }
   }
-  const double c = cbrt(m00);
+  const A c = acbrt(m00);
   switch (o) {
     case 0: return m00;
     case 1: return m00 * c;
@@ -256,177 +328,182 @@ __device__ inline double norm_pow(double m00, int o) {
   }
 }
 
-// Finalise one weighting's moments from centred sums C[] about (c0,c1,c2)
-// (ROI-local), where the exact centroid is (k0,k1,k2): shift, then raw,
-// normalised and Hu.  valid = false -> every derived value NaN.
-template <int NDIM>
-__device__ __noinline__ void finalize_moments(const KParams& p, double* row, int wbase, const double* Cs, double c0, double c1,
-                                 double c2, double k0, double k1, double k2, bool valid, double* save_mu) {
+// One weighting's moments, one lane per moment.  Cs[] are the centred sums
+// sum w (x - c0)^p (y - c1)^q (z - c2)^r about the FP32 rounding of the
+// centroid (c0, c1, c2); that rounding (< 1e-5 px) moves every moment by far
+// less than the accumulation error, so Cs are the central moments mu_pqr.
+// Raw moments follow by the binomial expansion about the centroid.  valid =
+// false (zero total weight) leaves raw moments finite and every derived value
+// NaN.  Hu invariants are evaluated on eta rescaled to O(1) and scaled back by
+// an exact power of two, so tiny intensity-weighted invariants neither
+// underflow nor lose precision in FP32.
+template <int NDIM, class A>
+__device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row, int wbase, const A* Cs, A c0, A c1,
+                                                   A c2, bool valid, double* save_mu) {
   constexpr int NM = NDIM == 3 ? 20 : 10;
-  double mu[NM], M[NM];
-  const double d0 = c0 - k0, d1 = c1 - k1, d2 = c2 - k2;  // shift from sum centre to exact centroid
-  for (int k = 0; k < NM; ++k) {
-    int a, b, c;
-    mexp<NDIM>(k, a, b, c);
-    double s = 0;
-    for (int i = 0; i <= a; ++i)
-      for (int j = 0; j <= b; ++j)
-        for (int l = 0; l <= c; ++l)
-          s += binom(a, i) * binom(b, j) * binom(c, l) * ipow_d(d0, a - i) * ipow_d(d1, b - j) * ipow_d(d2, c - l) *
-               Cs[midx<NDIM>(i, j, l)];
-    mu[k] = s;
+  const int lane = threadIdx.x & 31;
+  if (lane >= NM) return;
+  const A nan = anan<A>();
+  int a, b, c;
+  mexp<NDIM>(lane, a, b, c);
+  const int o = a + b + c;
+  A mu = Cs[lane];
+  if (valid && o == 1) mu = 0;  // first-order central moments vanish at the centroid
+  const A pw0[4] = {1, c0, c0 * c0, c0 * c0 * c0}, pw1[4] = {1, c1, c1 * c1, c1 * c1 * c1},
+          pw2[4] = {1, c2, c2 * c2, c2 * c2 * c2};
+  A M = 0;
+  for (int i = 0; i <= a; ++i)
+    for (int j = 0; j <= b; ++j)
+      for (int l = 0; l <= c; ++l) {
+        const A muk = (valid && i + j + l == 1) ? (A)0 : Cs[midx<NDIM>(i, j, l)];
+        M += (A)(c_binom[a][i] * c_binom[b][j] * c_binom[c][l]) * pw0[a - i] * pw1[b - j] * pw2[c - l] * muk;
+      }
+  const A mu00 = Cs[0];
+  putA(p, row, Q_MOM + (wbase + F_M) * 20 + lane, M);
+  putA(p, row, Q_MOM + (wbase + F_MU) * 20 + lane, valid ? mu : nan);
+  if (o >= 2) putA(p, row, Q_MOM + (wbase + F_ETA) * 20 + lane, valid ? mu / norm_pow<NDIM>(mu00, o) : nan);
+  if (NDIM == 2) putA(p, row, Q_MOM + (wbase + F_NU) * 20 + lane, valid ? M / norm_pow<NDIM>(mu00, o) : nan);
+  if (save_mu) save_mu[lane] = to_d(mu);
+  if (NDIM == 2 && lane == 0) {
+    const A g20 = norm_pow<2>(mu00, 2), g30 = norm_pow<2>(mu00, 3);
+    const A e20 = Cs[midx<2>(2, 0, 0)] / g20, e02 = Cs[midx<2>(0, 2, 0)] / g20, e11 = Cs[midx<2>(1, 1, 0)] / g20;
+    // scale lambda = 2^k close to eta20 + eta02: eta_o / lambda^(o/2) = O(1)
+    int k = 0;
+    if (valid) {
+      const A s2 = (e20 > 0 ? e20 : -e20) + (e02 > 0 ? e02 : -e02);
+      int ex;
+      if constexpr (std::is_same<A, float>::value) (void)frexpf(s2, &ex);
+      else (void)frexp(s2, &ex);
+      k = s2 > 0 ? ex : 0;
+      k &= ~1;  // even, so that lambda^(1/2) and lambda^(3/2) are exact powers of two
+    }
+    A il, il15;
+    if constexpr (std::is_same<A, float>::value) {
+      il = ldexpf(1.f, -k);
+      il15 = ldexpf(1.f, -(3 * k) / 2);
+    } else {
+      il = ldexp(1.0, -k);
+      il15 = ldexp(1.0, -(3 * k) / 2);
+    }
+    A h[7];
+    hu7<A>(e20 * il, e02 * il, e11 * il, Cs[midx<2>(3, 0, 0)] / g30 * il15, Cs[midx<2>(2, 1, 0)] / g30 * il15,
+           Cs[midx<2>(1, 2, 0)] / g30 * il15, Cs[midx<2>(0, 3, 0)] / g30 * il15, h);
+    const int deg[7] = {1, 2, 3, 3, 6, 4, 6};  // degree of each invariant in eta20-like units
+    for (int i = 0; i < 7; ++i) {
+      double v;
+      if constexpr (std::is_same<A, float>::value) v = f2d_scaled(h[i], k * deg[i]);
+      else v = ldexp(h[i], k * deg[i]);
+      put(p, row, Q_MOM + (wbase + F_HU) * 20 + i, valid ? v : to_d(nan));
+    }
   }
-  // first-order central moments vanish at the exact centroid
-  if (valid) {
-    mu[midx<NDIM>(1, 0, 0)] = 0;
-    mu[midx<NDIM>(0, 1, 0)] = 0;
-    if (NDIM == 3) mu[midx<NDIM>(0, 0, 1)] = 0;
-  }
-  for (int k = 0; k < NM; ++k) {
-    int a, b, c;
-    mexp<NDIM>(k, a, b, c);
-    double s = 0;
-    for (int i = 0; i <= a; ++i)
-      for (int j = 0; j <= b; ++j)
-        for (int l = 0; l <= c; ++l)
-          s += binom(a, i) * binom(b, j) * binom(c, l) * ipow_d(k0, a - i) * ipow_d(k1, b - j) * ipow_d(k2, c - l) *
-               mu[midx<NDIM>(i, j, l)];
-    M[k] = s;
-  }
-  const double nan = __longlong_as_double(0x7FF8000000000000ll);
-  const double m00 = M[0];
-  for (int k = 0; k < NM; ++k) {
-    int a, b, c;
-    mexp<NDIM>(k, a, b, c);
-    const int o = a + b + c;
-    put(p, row, Q_MOM + (wbase + F_M) * 20 + k, M[k]);
-    put(p, row, Q_MOM + (wbase + F_MU) * 20 + k, valid ? mu[k] : nan);
-    if (o >= 2) put(p, row, Q_MOM + (wbase + F_ETA) * 20 + k, valid ? mu[k] / norm_pow<NDIM>(mu[0], o) : nan);
-    if (NDIM == 2) put(p, row, Q_MOM + (wbase + F_NU) * 20 + k, valid ? M[k] / norm_pow<NDIM>(m00, o) : nan);
-  }
-  if (NDIM == 2) {
-    double h[7];
-    const double g20 = norm_pow<2>(mu[0], 2), g30 = norm_pow<2>(mu[0], 3);
-    hu7(mu[midx<2>(2, 0, 0)] / g20, mu[midx<2>(0, 2, 0)] / g20, mu[midx<2>(1, 1, 0)] / g20, mu[midx<2>(3, 0, 0)] / g30,
-        mu[midx<2>(2, 1, 0)] / g30, mu[midx<2>(1, 2, 0)] / g30, mu[midx<2>(0, 3, 0)] / g30, h);
-    for (int i = 0; i < 7; ++i) put(p, row, Q_MOM + (wbase + F_HU) * 20 + i, valid ? h[i] : nan);
-  }
-  if (save_mu)
-    for (int k = 0; k < NM; ++k) save_mu[k] = mu[k];
 }
 
-
 // Statistics of Table S1 / S5 from the centred power sums S_k = sum (I - c)^k
-// about a centring point c close to the mean (exact for integer images); the
-// residual offset S_1 / n is removed by a binomial shift.
-template <class T, int NDIM>
-__device__ __noinline__ void finalize_stats(const KParams& p, double* row, const double* res_st, int n, double mean,
-                                            double sumI, double energy, unsigned vmin, unsigned vmax, int64_t bimg,
-                                            int x0, int y0, int z0, double cx, double cy, double cz, double bx,
-                                            double by, double bz, bool wvalid, double* save) {
-  const double nan = __longlong_as_double(0x7FF8000000000000ll);
-  const double S1 = res_st[0];
-  const double dl = S1 / n;
-  double Sk[7];
-  Sk[0] = n;
-  for (int k = 1; k <= 6; ++k) Sk[k] = res_st[k - 1];
-  double m[7];
+// about a centring point c close to the mean; the residual offset S_1 / n is
+// removed by a binomial shift.
+template <class T, int NDIM, class A>
+__device__ __noinline__ void finalize_stats(const KParams& p, double* row, const A* res_st, int n, A mean, A sumI,
+                                            A energy, unsigned vmin, unsigned vmax, int64_t bimg, int x0, int y0,
+                                            int z0, A cx, A cy, A cz, A bx, A by, A bz, bool wvalid, double* save) {
+  const A nan = anan<A>();
+  const A nA = (A)n;
+  const A dl = res_st[0] / nA;
+  A pd[7];
+  pd[0] = 1;
+  for (int k = 1; k <= 6; ++k) pd[k] = pd[k - 1] * -dl;
+  A m[7];
   m[0] = 1;
   for (int k = 1; k <= 6; ++k) {
-    double s = 0;
-    for (int j = 0; j <= k; ++j) s += binom(k, j) * ipow_d(-dl, k - j) * Sk[j];
-    m[k] = s / n;
+    A s = pd[k] * nA;  // j = 0 term: S_0 = n
+    for (int j = 1; j <= k; ++j) s += (A)c_binom[k][j] * pd[k - j] * res_st[j - 1];
+    m[k] = s / nA;
   }
-  const double m2 = m[2] > 0 ? m[2] : 0.0;
-  const double var = n > 1 ? m2 * n / (n - 1) : 0.0;
-  const double sd = sqrt(var);
-  const double mn = Enc<T>::dec(vmin), mx = Enc<T>::dec(vmax);
-  const double imn = Enc<T>::dec(p.img_vmin[bimg]), imx = Enc<T>::dec(p.img_vmax[bimg]);
-  put(p, row, Q_STATS + S_MEAN, mean);
-  put(p, row, Q_STATS + S_MIN, mn);
-  put(p, row, Q_STATS + S_MAX, mx);
-  put(p, row, Q_STATS + S_RANGE, mx - mn);
-  put(p, row, Q_STATS + S_VAR, var);
-  put(p, row, Q_STATS + S_VAR_B, m2);
-  put(p, row, Q_STATS + S_STD, sd);
-  put(p, row, Q_STATS + S_STD_B, sqrt(m2));
+  const A m2 = m[2] > 0 ? m[2] : (A)0;
+  const A var = n > 1 ? m2 * nA / (nA - 1) : (A)0;
+  const A sd = asqrt(var);
+  const A mn = decA<T, A>(vmin), mx = decA<T, A>(vmax);
+  const A imn = decA<T, A>(p.img_vmin[bimg]), imx = decA<T, A>(p.img_vmax[bimg]);
+  putA(p, row, Q_STATS + S_MEAN, mean);
+  putA(p, row, Q_STATS + S_VAR, var);
+  putA(p, row, Q_STATS + S_VAR_B, m2);
+  putA(p, row, Q_STATS + S_STD, sd);
+  putA(p, row, Q_STATS + S_STD_B, asqrt(m2));
   const bool pos = m2 > 0;
-  const double kurt = pos ? m[4] / (m2 * m2) : 0.0;
-  put(p, row, Q_STATS + S_SKEW, pos ? m[3] / (m2 * sqrt(m2)) : 0.0);
-  put(p, row, Q_STATS + S_KURT, kurt);
-  put(p, row, Q_STATS + S_EXKURT, pos ? kurt - 3.0 : 0.0);
-  put(p, row, Q_STATS + S_HSKEW, pos ? m[5] / (m2 * m2 * sqrt(m2)) : 0.0);
-  put(p, row, Q_STATS + S_HFLAT, pos ? m[6] / (m2 * m2 * m2) : 0.0);
-  put(p, row, Q_STATS + S_ENERGY, energy);
-  put(p, row, Q_STATS + S_RMS, sqrt(energy / n));
-  put(p, row, Q_STATS + S_SE, sd / sqrt((double)n));
-  put(p, row, Q_STATS + S_MAD, res_st[6] / n);
-  put(p, row, Q_STATS + S_II, sumI);
-  const double wcx = wvalid ? x0 + cx : nan, wcy = wvalid ? y0 + cy : nan, wcz = wvalid ? z0 + cz : nan;
-  const double gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
-  put(p, row, Q_CEN_X, gx);
-  put(p, row, Q_CEN_Y, gy);
-  put(p, row, Q_CEN_Z, gz);
-  put(p, row, Q_STATS + S_WCX, wcx);
-  put(p, row, Q_STATS + S_WCY, wcy);
-  put(p, row, Q_STATS + S_WCZ, wcz);
-  double md = (wcx - gx) * (wcx - gx) + (wcy - gy) * (wcy - gy);
-  if (NDIM == 3) md += (wcz - gz) * (wcz - gz);
-  put(p, row, Q_STATS + S_MD, sqrt(md));
-  put(p, row, Q_STATS + S_COV, mean != 0 ? sd / mean : nan);
-  put(p, row, Q_STATS + S_COVERED, imx != imn ? (mx - mn) / (imx - imn) : nan);
-  put(p, row, Q_STATS + S_PIU, (mx + mn) != 0 ? 100.0 * (1.0 - (mx - mn) / (mx + mn)) : nan);
+  const A kurt = pos ? m[4] / (m2 * m2) : (A)0;
+  putA(p, row, Q_STATS + S_SKEW, pos ? m[3] / (m2 * asqrt(m2)) : (A)0);
+  putA(p, row, Q_STATS + S_KURT, kurt);
+  putA(p, row, Q_STATS + S_EXKURT, pos ? kurt - 3 : (A)0);
+  putA(p, row, Q_STATS + S_HSKEW, pos ? m[5] / (m2 * m2 * asqrt(m2)) : (A)0);
+  putA(p, row, Q_STATS + S_HFLAT, pos ? m[6] / (m2 * m2 * m2) : (A)0);
+  putA(p, row, Q_STATS + S_RMS, asqrt(energy / nA));
+  putA(p, row, Q_STATS + S_SE, sd / asqrt(nA));
+  putA(p, row, Q_STATS + S_MAD, res_st[6] / nA);
+  putA(p, row, Q_STATS + S_COV, mean != 0 ? sd / mean : nan);
+  putA(p, row, Q_STATS + S_COVERED, imx != imn ? (mx - mn) / (imx - imn) : nan);
+  putA(p, row, Q_STATS + S_PIU, (mx + mn) != 0 ? (A)100 * ((A)1 - (mx - mn) / (mx + mn)) : nan);
+  // centroids in image coordinates: integer origin + local offset (exact sum
+  // in FP64 of two exactly converted terms keeps the local precision)
+  put(p, row, Q_CEN_X, i2d(x0) + to_d(bx));
+  put(p, row, Q_CEN_Y, i2d(y0) + to_d(by));
+  put(p, row, Q_CEN_Z, i2d(z0) + to_d(bz));
+  put(p, row, Q_STATS + S_WCX, wvalid ? i2d(x0) + to_d(cx) : to_d(nan));
+  put(p, row, Q_STATS + S_WCY, wvalid ? i2d(y0) + to_d(cy) : to_d(nan));
+  put(p, row, Q_STATS + S_WCZ, wvalid ? i2d(z0) + to_d(cz) : to_d(nan));
+  A md = (cx - bx) * (cx - bx) + (cy - by) * (cy - by);
+  if (NDIM == 3) md += (cz - bz) * (cz - bz);
+  putA(p, row, Q_STATS + S_MD, wvalid ? asqrt(md) : nan);
   if (save) {
-    save[SV_N] = n;
-    save[SV_MEAN] = mean;
-    for (int k = 2; k <= 6; ++k) save[SV_M2 + k - 2] = m[k];
-    save[SV_SGN] = res_st[7];
-    save[SV_ENERGY] = energy;
-    save[SV_SUMI] = sumI;
-    save[SV_CX] = cx;
-    save[SV_CY] = cy;
-    save[SV_CZ] = cz;
-    save[SV_BX] = gx;
-    save[SV_BY] = gy;
-    save[SV_BZ] = gz;
-    save[SV_X0] = x0;
-    save[SV_Y0] = y0;
-    save[SV_Z0] = z0;
+    save[SV_N] = i2d(n);
+    save[SV_MEAN] = to_d(mean);
+    for (int k = 2; k <= 6; ++k) save[SV_M2 + k - 2] = to_d(m[k]);
+    save[SV_SGN] = to_d(res_st[7]);
+    save[SV_ENERGY] = to_d(energy);
+    save[SV_SUMI] = to_d(sumI);
+    save[SV_CX] = to_d(cx);
+    save[SV_CY] = to_d(cy);
+    save[SV_CZ] = to_d(cz);
+    save[SV_BX] = i2d(x0) + to_d(bx);
+    save[SV_BY] = i2d(y0) + to_d(by);
+    save[SV_BZ] = i2d(z0) + to_d(bz);
+    save[SV_X0] = i2d(x0);
+    save[SV_Y0] = i2d(y0);
+    save[SV_Z0] = i2d(z0);
   }
 }
 
 // GLCM features of one offset (Table S3 rows 140-174) from the reduced sums
 // of the marginals and cells; accumulates the direction mean in gsum.
-static __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const double* r, double mu, double sumave,
-                                           double difave, float jmax, int di, int dir, double* gsum) {
-  double f[NGLCM];
-  const double hx = r[0], var = r[1], sument = r[2], sumvar = r[3], clushade = r[4], cluprom = r[5],
-               contrast = r[6], id = r[7], idm = r[8], idn = r[9], idmn = r[10], iv = r[11], difvar = r[12],
-               difent = r[13], asmv = r[14], je = r[15], mi = r[16];
+template <class A>
+__device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const A* r, A mu, A sumave, A difave,
+                                           A jmax, int di, int dir, A* gsum) {
+  A f[NGLCM];
+  const A hx = r[0], var = r[1], sument = r[2], sumvar = r[3], clushade = r[4], cluprom = r[5], contrast = r[6],
+          id = r[7], idm = r[8], idn = r[9], idmn = r[10], iv = r[11], difvar = r[12], difent = r[13], asmv = r[14],
+          je = r[15], mi = r[16];
   // covariance from the sum and difference marginals:
   // (i+j-2mu)^2 - (i-j)^2 = 4 (i-mu)(j-mu)
-  const double cov = (sumvar - contrast) / 4.0;
+  const A cov = (sumvar - contrast) / 4;
   f[G_ASM] = asmv;
   f[G_ACOR] = cov + mu * mu;
   f[G_CLUPROM] = cluprom;
   f[G_CLUSHADE] = clushade;
   f[G_CLUTEND] = sumvar;
   f[G_CONTRAST] = contrast;
-  f[G_CORR] = var > 0 ? cov / var : 1.0;
+  f[G_CORR] = var > 0 ? cov / var : (A)1;
   f[G_DIFAVE] = difave;
   f[G_DIFENTRO] = difent;
   f[G_DIFVAR] = difvar;
   f[G_DIS] = difave;
-  f[G_ENERGY] = sqrt(asmv);
+  f[G_ENERGY] = asqrt(asmv);
   f[G_ENTROPY] = je;
   f[G_HOM1] = id;
   f[G_HOM2] = idm;
   f[G_IDM] = idm;
   // HXY1 = HXY2 = HX + HY and HX = HY for a symmetric matrix, so
   // HXY - HXY1 = -MI and HXY2 - HXY = MI (mutual information)
-  f[G_INFOMEAS1] = hx > 0 ? -mi / hx : 0.0;
-  const double arg = 1.0 - exp(-2.0 * mi);
-  f[G_INFOMEAS2] = sqrt(arg > 0 ? arg : 0.0);
+  f[G_INFOMEAS1] = hx > 0 ? -mi / hx : (A)0;
+  const A arg = (A)1 - aexp((A)-2 * mi);
+  f[G_INFOMEAS2] = asqrt(arg > 0 ? arg : (A)0);
   f[G_IDMN] = idmn;
   f[G_ID] = id;
   f[G_IDN] = idn;
@@ -440,57 +517,99 @@ static __device__ __noinline__ void finalize_glcm(const KParams& p, double* row,
   f[G_SUMVAR] = sumvar;
   f[G_VARIANCE] = var;
   for (int g = 0; g < NGLCM; ++g) {
-    if (p.per_offset) put(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
+    if (p.per_offset) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
     gsum[g] += f[g];
   }
-  gsum[NGLCM] += 1.0;
+  gsum[NGLCM] += 1;
 }
 
-// Percentiles by linear interpolation at h = (n-1) q on sorted values, and
-// the index range of values inside [P10, P90].
+// Percentiles by linear interpolation at h = (n-1) q on the sorted values,
+// computed in FP64 with separately rounded operations like the definition,
+// one lane per percentile.  Lane 0 also finds the index range of the values
+// inside [P10, P90].  Writes median, P10, P90 to sc[] (FP64).
 template <class T>
 __device__ __noinline__ void finalize_percentiles(const KParams& p, double* row, const unsigned* v, int n, double* sc,
                                                   int* idx) {
-  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  const int lane = threadIdx.x & 31;
   const double qs[7] = {0.01, 0.10, 0.25, 0.50, 0.75, 0.90, 0.99};
-  double pv_[7];
-  for (int k = 0; k < 7; ++k) {
-    const double h = __dmul_rn((double)(n - 1), qs[k]);
+  const int qcol[7] = {S_P01, S_P10, S_P25, S_MEDIAN, S_P75, S_P90, S_P99};
+  double pv_ = 0;
+  if (lane < 7) {
+    const double h = __dmul_rn((double)(n - 1), qs[lane]);
     const int lo = (int)floor(h);
     if (lo >= n - 1) {
-      pv_[k] = Enc<T>::dec(v[n - 1]);
+      pv_ = Enc<T>::dec(v[n - 1]);
     } else {
       const double a = Enc<T>::dec(v[lo]), b = Enc<T>::dec(v[lo + 1]);
-      pv_[k] = __dadd_rn(a, __dmul_rn(__dsub_rn(h, (double)lo), __dsub_rn(b, a)));
+      pv_ = __dadd_rn(a, __dmul_rn(__dsub_rn(h, (double)lo), __dsub_rn(b, a)));
     }
+    put(p, row, Q_STATS + qcol[lane], pv_);
   }
-  sc[0] = pv_[3];
-  sc[1] = pv_[1];
-  sc[2] = pv_[5];
-  put(p, row, Q_STATS + S_P01, pv_[0]);
-  put(p, row, Q_STATS + S_P10, pv_[1]);
-  put(p, row, Q_STATS + S_P25, pv_[2]);
-  put(p, row, Q_STATS + S_MEDIAN, pv_[3]);
-  put(p, row, Q_STATS + S_P75, pv_[4]);
-  put(p, row, Q_STATS + S_P90, pv_[5]);
-  put(p, row, Q_STATS + S_P99, pv_[6]);
-  put(p, row, Q_STATS + S_IQR, pv_[4] - pv_[2]);
-  put(p, row, Q_STATS + S_QCOD, (pv_[4] + pv_[2]) != 0 ? (pv_[4] - pv_[2]) / (pv_[4] + pv_[2]) : nan);
+  const double p25 = __shfl_sync(0xFFFFFFFFu, pv_, 2), p75 = __shfl_sync(0xFFFFFFFFu, pv_, 4);
+  const double p10 = __shfl_sync(0xFFFFFFFFu, pv_, 1), p90 = __shfl_sync(0xFFFFFFFFu, pv_, 5);
+  const double med = __shfl_sync(0xFFFFFFFFu, pv_, 3);
+  if (lane != 0) return;
+  put(p, row, Q_STATS + S_IQR, __dsub_rn(p75, p25));
+  {
+    const float a = (float)p75, b = (float)p25;
+    put(p, row, Q_STATS + S_QCOD, (a + b) != 0.f ? f2d((a - b) / (a + b)) : f2d(__int_as_float(0x7FC00000)));
+  }
+  sc[0] = med;
+  sc[1] = p10;
+  sc[2] = p90;
   int lo = 0, hi = n;
-  while (lo < hi) {
-    const int m = (lo + hi) >> 1;
-    if (Enc<T>::dec(v[m]) < pv_[1]) lo = m + 1;
-    else hi = m;
+  if (Enc<T>::INTEGER) {
+    // integer values: v >= P10 <=> v >= ceil(P10); v <= P90 <=> v <= floor(P90)
+    const long long t10 = (long long)ceil(p10), t90 = (long long)floor(p90);
+    const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if ((long long)v[m] - bias < t10) lo = m + 1;
+      else hi = m;
+    }
+    idx[0] = lo;
+    lo = 0;
+    hi = n;
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if ((long long)v[m] - bias <= t90) lo = m + 1;
+      else hi = m;
+    }
+    idx[1] = lo;
+  } else {
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if (Enc<T>::dec(v[m]) < p10) lo = m + 1;
+      else hi = m;
+    }
+    idx[0] = lo;  // first value >= P10
+    lo = 0;
+    hi = n;
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if (Enc<T>::dec(v[m]) <= p90) lo = m + 1;
+      else hi = m;
+    }
+    idx[1] = lo;  // one past the last value <= P90
   }
-  idx[0] = lo;  // first value >= P10
-  lo = 0;
-  hi = n;
-  while (lo < hi) {
-    const int m = (lo + hi) >> 1;
-    if (Enc<T>::dec(v[m]) <= pv_[5]) lo = m + 1;
-    else hi = m;
+}
+
+// Rule a4 for float images: b = floor(n (x - min) / (max - min)) in FP64 with
+// separately rounded operations.  An FP32 evaluation decides whenever it is
+// farther than 1e-4 (relative) from a bin edge, which covers the FP32
+// rounding with a wide margin; otherwise the FP64 expression is evaluated.
+__device__ inline unsigned bin_float(float x, float mn, float mx, int nb) {
+  const float q = (float)nb * (x - mn) / (mx - mn);
+  const float fl = floorf(q);
+  const float tol = 1e-4f * (1.f + q);
+  unsigned b;
+  if (q - fl > tol && fl + 1.f - q > tol) {
+    b = (unsigned)fl;
+  } else {
+    const double dq = __ddiv_rn(__dmul_rn((double)nb, __dsub_rn((double)x, (double)mn)), __dsub_rn((double)mx, (double)mn));
+    b = (unsigned)floor(dq);
   }
-  idx[1] = lo;  // one past the last value <= P90
+  return min(b, (unsigned)(nb - 1));
 }
 
 // ----------------------------------------------------------------------------
@@ -508,15 +627,17 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
   unsigned* hist = (unsigned*)(smem + L.hist);
   unsigned* marg = (unsigned*)(smem + L.marg);
   double* red = (double*)(smem + L.red);
-  double* res = (double*)(smem + L.res);
+  A* res = (A*)(smem + L.res);
   __shared__ RoiInfo s_r;
   __shared__ int s_item;
   __shared__ unsigned s_rowcnt[C::NW], s_rowbase[C::NW + 1];
   __shared__ FastDiv s_fd;
-  __shared__ double s_sc[16];
-  __shared__ long long s_i64[16];
+  __shared__ A s_sc[16];
+  __shared__ double s_sd[4];
+  __shared__ long long s_i64[16];  // [0..7] pass 1, [8..11] GLCM moments, [12..14] GLCM cells
   __shared__ int s_idx[4];
-  __shared__ double s_gsum[NGLCM + 1];
+  __shared__ A s_gsum[NGLCM + 1];
+  __shared__ A s_pa[10];  // per-ROI scalars: mean (hi, lo), centroids, sums
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned* qlen = p.qlen + cls;
@@ -524,7 +645,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
   const int64_t per = p.nx * p.ny * p.nz;
   const bool need_glcm = (p.need & NEED_GLCM) != 0;
   const int pad = need_glcm ? p.pad : 0;
-  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  const A nan = anan<A>();
 
   for (;;) {
     if (tid == 0) {
@@ -548,6 +669,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
     const int64_t origin = bimg * per + ((int64_t)r.z0 * p.ny + r.y0) * p.nx + r.x0;
     const unsigned vmin = r.vmin, vmax = r.vmax;
     double* row = p.table + (int64_t)item * p.n_col;
+    const unsigned need = p.need;
 
     // ---- stage the ROI: raster of bins, pixel list, value histogram -------
     for (int i = tid; i < cells; i += C::NT) raster[i] = 0xFFFF;
@@ -556,6 +678,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
     __syncthreads();
     const int nrows = H * D;
     const T* img = (const T*)p.img;
+    const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
     for (int rb = 0; rb < nrows; rb += C::NW) {
       const int rr = rb + warp;
       const bool have = rr < nrows;
@@ -598,19 +721,20 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             if (vmax > vmin) {
               if (Enc<T>::INTEGER) {
                 const unsigned dv = e - vmin;
-                gb = s_fd.div((unsigned)p.ng * dv);
-                hb = s_fd.div((unsigned)p.hist_bins * dv);
+                gb = min(s_fd.div((unsigned)p.ng * dv), (unsigned)(p.ng - 1));
+                hb = min(s_fd.div((unsigned)p.hist_bins * dv), (unsigned)(p.hist_bins - 1));
               } else {
-                const double xv = Enc<T>::dec(e), mn = Enc<T>::dec(vmin), mx = Enc<T>::dec(vmax);
-                const double den = __dsub_rn(mx, mn), dx = __dsub_rn(xv, mn);
-                if (need_glcm) gb = (unsigned)floor(__ddiv_rn(__dmul_rn((double)p.ng, dx), den));
-                if (p.need & NEED_HIST) hb = (unsigned)floor(__ddiv_rn(__dmul_rn((double)p.hist_bins, dx), den));
+                const float xv = Enc<T>::decf(e);
+                if (need_glcm) gb = bin_float(xv, fmn, fmx, p.ng);
+                if (need & NEED_HIST) hb = bin_float(xv, fmn, fmx, p.hist_bins);
               }
-              gb = min(gb, (unsigned)(p.ng - 1));
-              hb = min(hb, (unsigned)(p.hist_bins - 1));
             }
-            if (need_glcm) raster[((rz + pad) * Hp + (ry + pad)) * Wp + (x + pad)] = (uint16_t)gb;
-            if (p.need & NEED_HIST) atomicAdd(&hist[hb], 1u);
+            if (need_glcm) {
+              const int ri = ((NDIM == 3 ? rz + pad : 0) * Hp + (ry + pad)) * Wp + (x + pad);
+              if (ri < cells) raster[ri] = (uint16_t)gb;
+              else atomicOr(p.err, E_INTERNAL);
+            }
+            if (need & NEED_HIST) atomicAdd(&hist[hb], 1u);
           }
           base += __popc(bal);
         }
@@ -618,22 +742,31 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
     __syncthreads();
     if (tid == 0 && s_rowbase[C::NW] != (unsigned)n) atomicOr(p.err, E_INTERNAL);
 
-    // ---- geometry columns ----------------------------------------------------
+    // ---- geometry and range columns (exact integers) -------------------------
     if (tid == 0) {
-      put(p, row, Q_LABEL, (double)label);
-      put(p, row, Q_IMAGE, (double)bimg);
-      put(p, row, Q_AREA, (double)n);
-      put(p, row, Q_BB_X, (double)r.x0);
-      put(p, row, Q_BB_Y, (double)r.y0);
-      put(p, row, Q_BB_Z, (double)r.z0);
-      put(p, row, Q_BB_W, (double)W);
-      put(p, row, Q_BB_H, (double)H);
-      put(p, row, Q_BB_D, (double)D);
+      put(p, row, Q_LABEL, i2d(label));
+      put(p, row, Q_IMAGE, i2d(bimg));
+      put(p, row, Q_AREA, i2d(n));
+      put(p, row, Q_BB_X, i2d(r.x0));
+      put(p, row, Q_BB_Y, i2d(r.y0));
+      put(p, row, Q_BB_Z, i2d(r.z0));
+      put(p, row, Q_BB_W, i2d(W));
+      put(p, row, Q_BB_H, i2d(H));
+      put(p, row, Q_BB_D, i2d(D));
+      if (Enc<T>::INTEGER) {
+        const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
+        put(p, row, Q_STATS + S_MIN, i2d((long long)vmin - bias));
+        put(p, row, Q_STATS + S_MAX, i2d((long long)vmax - bias));
+        put(p, row, Q_STATS + S_RANGE, i2d((long long)vmax - (long long)vmin));
+      } else {
+        put(p, row, Q_STATS + S_MIN, f2d(fmn));
+        put(p, row, Q_STATS + S_MAX, f2d(fmx));
+        put(p, row, Q_STATS + S_RANGE, __dsub_rn(f2d(fmx), f2d(fmn)));  // as the FP64 definition
+      }
     }
 
     // ---- pass 1: exact sums (integers) --------------------------------------
-    const unsigned need = p.need;
-    const float fbias = std::is_same<T, int16_t>::value ? 32768.f : 0.f;
+    const int ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
     {
       // [0] sum I, [1] sum x I, [2] sum y I, [3] sum z I, [4] sum x, [5] sum y, [6] sum z, [7] sum I^2
       long long s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -647,14 +780,14 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         s[5] += y;
         s[6] += z;
         if (Enc<T>::INTEGER) {
-          const int v = (int)pv[i] - (int)fbias;
+          const int v = (int)pv[i] - ibias;
           s[0] += v;
           s[1] += (long long)x * v;
           s[2] += (long long)y * v;
           s[3] += (long long)z * v;
           s[7] += (long long)v * v;
         } else {
-          const A v = (A)Enc<T>::decf(pv[i]);
+          const A v = decA<T, A>(pv[i]);
           fs[0] += v;
           fs[1] += (A)x * v;
           fs[2] += (A)y * v;
@@ -663,38 +796,75 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         }
       }
       block_sum_i64<C, 8>(s, red, s_i64);
-      if (!Enc<T>::INTEGER) {
-        block_sum<C, A, 5>(fs, red, s_sc);
-      } else if (tid == 0) {
-        for (int i = 0; i < 4; ++i) s_sc[i] = (double)s_i64[i];
-        s_sc[4] = (double)s_i64[7];
-      }
-      __syncthreads();
+      if (!Enc<T>::INTEGER) block_sum<C, A, 5>(fs, red, s_sc);
     }
-    const double sumI = s_sc[0];
-    const double energy = s_sc[4];
-    const double mean = sumI / n;
+    // per-ROI scalars by one thread, broadcast through shared memory: mean
+    // (as hi + lo so that I - mean keeps its accuracy in FP32), the centre of
+    // the intensity-weighted sums (the exact centroid, or the binary centroid
+    // when the weights sum to zero) and the binary centroid
+    if (tid == 0) {
+      const A nA = (A)n;
+      A sI, sxI, syI, szI, en, mhi, mlo;
+      if (Enc<T>::INTEGER) {
+        const long long si = s_i64[0];
+        sI = (A)si;
+        sxI = (A)s_i64[1];
+        syI = (A)s_i64[2];
+        szI = (A)s_i64[3];
+        en = (A)s_i64[7];
+        if constexpr (std::is_same<A, float>::value) {
+          const long long q = si / n, rm = si - q * n;  // mean = q + rm / n exactly
+          mhi = (A)q;
+          mlo = (A)rm / nA;
+        } else {
+          mhi = (A)si / nA;
+          mlo = 0;
+        }
+        put(p, row, Q_STATS + S_II, i2d(si));
+        put(p, row, Q_STATS + S_ENERGY, i2d(s_i64[7]));
+      } else {
+        sI = s_sc[0];
+        sxI = s_sc[1];
+        syI = s_sc[2];
+        szI = s_sc[3];
+        en = s_sc[4];
+        mhi = sI / nA;
+        mlo = 0;
+        putA(p, row, Q_STATS + S_II, sI);
+        putA(p, row, Q_STATS + S_ENERGY, en);
+      }
+      const A bx_ = (A)s_i64[4] / nA, by_ = (A)s_i64[5] / nA, bz_ = (A)s_i64[6] / nA;
+      const bool wv = sI != 0;
+      s_pa[0] = mhi;
+      s_pa[1] = mlo;
+      s_pa[2] = wv ? sxI / sI : bx_;
+      s_pa[3] = wv ? syI / sI : by_;
+      s_pa[4] = wv ? szI / sI : bz_;
+      s_pa[5] = bx_;
+      s_pa[6] = by_;
+      s_pa[7] = bz_;
+      s_pa[8] = sI;
+      s_pa[9] = en;
+    }
+    __syncthreads();
+    const A mu_hi = s_pa[0], mu_lo = s_pa[1];
+    const A cx = s_pa[2], cy = s_pa[3], cz = s_pa[4], bx = s_pa[5], by = s_pa[6], bz = s_pa[7];
+    const A sumI = s_pa[8], energy = s_pa[9];
     const bool wvalid = sumI != 0;
-    // centre of the intensity-weighted sums (exact centroid, or the binary
-    // centroid when the weights sum to zero) and the binary centroid
-    const double bx = (double)s_i64[4] / n, by = (double)s_i64[5] / n, bz = (double)s_i64[6] / n;
-    const double cx = wvalid ? s_sc[1] / sumI : bx, cy = wvalid ? s_sc[2] / sumI : by,
-                 cz = wvalid ? s_sc[3] / sumI : bz;
 
     // ---- pass 2: centred sums (one loop per feature group keeps the live
     // accumulators few) -------------------------------------------------------
     constexpr int NM = NDIM == 3 ? 20 : 10;
-    double* res_st = res;            // [8]  statistics
-    double* res_mi = res + 8;        // [NM] intensity-weighted moments
-    double* res_mb = res + 8 + NM;   // [NM] binary moments
+    A* res_st = res;            // [8]  statistics
+    A* res_mi = res + 8;        // [NM] intensity-weighted moments
+    A* res_mb = res + 8 + NM;   // [NM] binary moments
     if (need & (NEED_STATS | NEED_SAVE)) {
       A acc[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) acc[i] = 0;
-      const A mu_hi = (A)mean, mu_lo = (A)(mean - (double)mu_hi);
 #pragma unroll 1
       for (int i = tid; i < n; i += C::NT) {
-        const A v = Enc<T>::INTEGER ? (A)((int)pv[i] - (int)fbias) : (A)Enc<T>::decf(pv[i]);
+        const A v = Enc<T>::INTEGER ? (A)((int)pv[i] - ibias) : decA<T, A>(pv[i]);
         const A d = (v - mu_hi) - mu_lo;
         const A d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
         acc[0] += d;
@@ -714,14 +884,14 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
       A acc[NM];
 #pragma unroll
       for (int i = 0; i < NM; ++i) acc[i] = 0;
-      const A c0 = (A)(w ? bx : cx), c1 = (A)(w ? by : cy), c2 = (A)(w ? bz : cz);
+      const A c0 = w ? bx : cx, c1 = w ? by : cy, c2 = w ? bz : cz;
 #pragma unroll 1
       for (int i = tid; i < n; i += C::NT) {
         const unsigned c = pc[i];
         const A u0 = (A)(NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu)) - c0;
         const A u1 = (A)(NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16)) - c1;
         const A u2 = (A)(NDIM == 3 ? (int)(c >> 22) : 0) - c2;
-        const A wt = w ? (A)1 : (Enc<T>::INTEGER ? (A)((int)pv[i] - (int)fbias) : (A)Enc<T>::decf(pv[i]));
+        const A wt = w ? (A)1 : (Enc<T>::INTEGER ? (A)((int)pv[i] - ibias) : decA<T, A>(pv[i]));
         A px[4], py[4], pz[4];
         px[0] = wt;
         py[0] = pz[0] = 1;
@@ -742,17 +912,15 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
       block_sum<C, A, NM>(acc, red, w ? res_mb : res_mi);
     }
 
-    // ---- finalise statistics and moments (FP64, one thread per group) -------
+    // ---- finalise statistics and moments (one warp per group) ---------------
     double* save = (need & NEED_SAVE) ? p.saved + (int64_t)item * SV_WORDS : nullptr;
     if (tid == 0)
-      finalize_stats<T, NDIM>(p, row, res_st, n, mean, sumI, energy, vmin, vmax, bimg, r.x0, r.y0, r.z0, cx, cy, cz,
-                              bx, by, bz, wvalid, save);
-    if (tid == 32 && (need & (NEED_MOM_INT | NEED_SAVE)))
-      finalize_moments<NDIM>(p, row, 0, res_mi, (double)(A)cx, (double)(A)cy, (double)(A)cz, cx, cy, cz, wvalid,
-                             save ? save + SV_MU : nullptr);
-    if (tid == 64 && (need & NEED_MOM_BIN))
-      finalize_moments<NDIM>(p, row, 5, res_mb, (double)(A)bx, (double)(A)by, (double)(A)bz, bx, by, bz, true,
-                             nullptr);
+      finalize_stats<T, NDIM, A>(p, row, res_st, n, mu_hi + mu_lo, sumI, energy, vmin, vmax, bimg, r.x0, r.y0, r.z0,
+                                 cx, cy, cz, bx, by, bz, wvalid, save);
+    if (warp == 1 && (need & (NEED_MOM_INT | NEED_SAVE)))
+      finalize_moments_warp<NDIM, A>(p, row, 0, res_mi, cx, cy, cz, wvalid, save ? save + SV_MU : nullptr);
+    if (warp == 2 && (need & NEED_MOM_BIN))
+      finalize_moments_warp<NDIM, A>(p, row, 5, res_mb, bx, by, bz, true, nullptr);
     __syncthreads();
 
     // ---- histogram features -------------------------------------------------
@@ -769,8 +937,8 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
       }
       block_sum<C, A, 2>(hv, red, s_sc + 8);
       if (tid == 0) {
-        put(p, row, Q_STATS + S_ENTROPY, s_sc[8]);
-        put(p, row, Q_STATS + S_UNIFORMITY, s_sc[9]);
+        putA(p, row, Q_STATS + S_ENTROPY, s_sc[8]);
+        putA(p, row, Q_STATS + S_UNIFORMITY, s_sc[9]);
       }
     }
 
@@ -802,7 +970,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
               const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
               const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
               const int z = NDIM == 3 ? (int)(c >> 22) : 0;
-              const int ci = ((z + pad) * Hp + (y + pad)) * Wp + (x + pad);
+              const int ci = ((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad);
               const unsigned a = raster[ci], b = raster[ci + olin];
               if (b != 0xFFFFu) key = a < b ? (a << 8) | b : (b << 8) | a;
             }
@@ -858,65 +1026,79 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           const long long Ti = s_i64[8];
           if (Ti == 0) {  // no pair for this offset: every feature NaN
             if (tid == 0 && p.per_offset)
-              for (int g = 0; g < NGLCM; ++g) put(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, nan);
+              for (int g = 0; g < NGLCM; ++g) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, nan);
             __syncthreads();
             continue;
           }
-          const double Td = (double)Ti;
-          const double mu = (double)s_i64[9] / Td, sumave = (double)s_i64[10] / Td, difave = (double)s_i64[11] / Td;
-          // centred / entropy sums in the accumulation type
-          A gv[17];
+          // first moments from exact 32-bit sums (T <= 2^17, sums <= 2^26)
+          const A Ta = (A)(int)Ti;
+          const A invT = (A)1 / Ta, muA = (A)(int)s_i64[9] / Ta, saA = (A)(int)s_i64[10] / Ta,
+                  daA = (A)(int)s_i64[11] / Ta, ngA = (A)ng;
+          const float Tf = (float)(int)Ti;
+          // sums over the marginals
+          A gv[14];
 #pragma unroll
-          for (int k = 0; k < 17; ++k) gv[k] = 0;
-          float jmax = 0.f;
-          const A invT = (A)1 / (A)Td, muA = (A)mu, saA = (A)sumave, daA = (A)difave, ngA = (A)ng;
+          for (int k = 0; k < 14; ++k) gv[k] = 0;
           for (int a = tid; a < ng; a += C::NT) {
             if (!px[a]) continue;
             const A pr = (A)px[a] * invT, di_ = (A)(a + 1) - muA;
             gv[0] -= pr * alog2(pr);  // HX
-            gv[1] += di_ * di_ * pr;            // sigma^2
+            gv[1] += di_ * di_ * pr;  // sigma^2
           }
           for (int s = tid; s < 2 * ng - 1; s += C::NT) {
             if (!psum[s]) continue;
             const A pr = (A)psum[s] * invT, dk = (A)(s + 2) - saA;
-            gv[2] -= pr * alog2(pr);  // SUMENT
-            gv[3] += dk * dk * pr;              // SUMVAR = CLUTEND
-            gv[4] += dk * dk * dk * pr;         // CLUSHADE
-            gv[5] += dk * dk * dk * dk * pr;    // CLUPROM
+            gv[2] -= pr * alog2(pr);          // SUMENT
+            gv[3] += dk * dk * pr;            // SUMVAR = CLUTEND
+            gv[4] += dk * dk * dk * pr;       // CLUSHADE
+            gv[5] += dk * dk * dk * dk * pr;  // CLUPROM
           }
           for (int k = tid; k < ng; k += C::NT) {
             if (!pdiff[k]) continue;
             const A pr = (A)pdiff[k] * invT, kk = (A)k, dk = kk - daA;
-            gv[6] += kk * kk * pr;                     // CONTRAST
-            gv[7] += pr / ((A)1 + kk);                 // ID = HOM1
-            gv[8] += pr / ((A)1 + kk * kk);            // IDM = HOM2
-            gv[9] += pr / ((A)1 + kk / ngA);           // IDN
+            gv[6] += kk * kk * pr;                          // CONTRAST
+            gv[7] += pr / ((A)1 + kk);                      // ID = HOM1
+            gv[8] += pr / ((A)1 + kk * kk);                 // IDM = HOM2
+            gv[9] += pr / ((A)1 + kk / ngA);                // IDN
             gv[10] += pr / ((A)1 + kk * kk / (ngA * ngA));  // IDMN
-            if (k >= 1) gv[11] += pr / (kk * kk);      // IV
-            gv[12] += dk * dk * pr;                    // DIFVAR
-            gv[13] -= pr * alog2(pr);        // DIFENTRO
+            if (k >= 1) gv[11] += pr / (kk * kk);           // IV
+            gv[12] += dk * dk * pr;                         // DIFVAR
+            gv[13] -= pr * alog2(pr);                       // DIFENTRO
           }
+          // sums over the non-zero cells, exact in 64-bit integers (fixed
+          // point 2^-24 for the logarithmic terms) so that they do not depend
+          // on the order in which the hash table was filled:
+          //   [0] sum C^2, [1] sum C log2 C, [2] sum C log2(C T / (P_a P_b))
+          // with C the count of a cell of the symmetric matrix
+          long long cs[3] = {0, 0, 0};
+          unsigned long long cmax = 0;
           for (int s = tid; s < cap; s += C::NT) {
             const unsigned wv = tab[s];
             if (!wv) continue;
             const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
             const unsigned a = key >> 8, b = key & 255u;
-            const A mult = a == b ? (A)1 : (A)2;          // cells (a,b) and (b,a)
-            const A pr = (A)(a == b ? 2 * cnt : cnt) * invT;
-            gv[14] += mult * pr * pr;                                       // ASM
-            gv[15] -= mult * pr * alog2(pr);                                // JE
-            const A ratio = (A)(a == b ? 2 * cnt : cnt) * (A)Td / ((A)px[a] * (A)px[b]);
-            gv[16] += mult * pr * alog2(ratio);                             // mutual information
-            jmax = fmaxf(jmax, (float)pr);
+            const long long mult = a == b ? 1 : 2;  // cells (a,b) and (b,a)
+            const unsigned Cc = a == b ? 2 * cnt : cnt;
+            cs[0] += mult * (long long)Cc * Cc;
+            cs[1] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
+            const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[b]);
+            cs[2] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
+            cmax = Cc > cmax ? Cc : cmax;
           }
-          block_sum<C, A, 17>(gv, red, res);
-          jmax = block_max<C>(jmax, red);
-          if (tid == 0) finalize_glcm(p, row, res, mu, sumave, difave, jmax, di, dir, s_gsum);
+          block_sum<C, A, 14>(gv, red, res);
+          block_sum_i64<C, 3>(cs, red, s_i64 + 12);
+          cmax = block_max_u64<C>(cmax, red);
+          if (tid == 0) {
+            res[14] = (A)s_i64[12] * invT * invT;                                  // ASM
+            res[15] = alog2(Ta) - (A)s_i64[13] * ((A)(1.0 / 16777216.0) * invT);  // JE
+            res[16] = (A)s_i64[14] * ((A)(1.0 / 16777216.0) * invT);              // MI
+            finalize_glcm<A>(p, row, res, muA, saA, daA, (A)(int)cmax * invT, di, dir, s_gsum);
+          }
           __syncthreads();
         }
         if (tid == 0)
           for (int g = 0; g < NGLCM; ++g)
-            put(p, row, Q_GLCM_D + di * NGLCM + g, s_gsum[NGLCM] > 0 ? s_gsum[g] / s_gsum[NGLCM] : nan);
+            putA(p, row, Q_GLCM_D + di * NGLCM + g, s_gsum[NGLCM] > 0 ? s_gsum[g] / s_gsum[NGLCM] : nan);
       }
     }
 
@@ -976,7 +1158,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         dst = t;
       }
       const unsigned* v = src;  // sorted, ascending
-      if (tid == 0) finalize_percentiles<T>(p, row, v, n, s_sc, s_idx);
+      if (warp == 0) finalize_percentiles<T>(p, row, v, n, s_sd, s_idx);
       __syncthreads();
       // mode: longest run of equal values, ties -> smallest value.  Each
       // thread owns a contiguous segment; runs entering a segment get their
@@ -987,16 +1169,23 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
       for (int i = s0; i < s1; ++i)
         if (i == 0 || v[i] != v[i - 1]) last_start = i;
       {
-        // exclusive max-scan of last_start over threads
         int* sc = (int*)red;
         sc[tid] = last_start;
         __syncthreads();
-        if (tid == 0) {
-          int run = -1;
-          for (int t = 0; t < C::NT; ++t) {
-            const int x = sc[t];
-            sc[t] = run;
-            if (x > run) run = x;
+        if (warp == 0) {  // exclusive max-scan over the C::NT entries
+          int carry = -1;
+          for (int base = 0; base < C::NT; base += 32) {
+            const int x = sc[base + lane];
+            int incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+              if (lane >= o) incl = max(incl, y);
+            }
+            const int prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);  // every lane executes the shuffle
+            const int excl = lane == 0 ? carry : max(carry, prev);
+            sc[base + lane] = excl;
+            carry = max(carry, __shfl_sync(0xFFFFFFFFu, incl, 31));
           }
         }
         __syncthreads();
@@ -1013,32 +1202,36 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         }
       }
       best = block_max_u64<C>(best, red);
-      // robust mean, median absolute deviation
+      // robust mean over [P10, P90], mean absolute deviation from the median
       const int i10 = s_idx[0], i90 = s_idx[1];
-      const double med = s_sc[0];
-      const A medA = (A)med;
+      if (tid == 0) s_sc[10] = (A)s_sd[0];  // median in the accumulation type
+      __syncthreads();
+      const A medA = s_sc[10];
       A rv[2] = {0, 0};
       for (int i = tid; i < n; i += C::NT) {
-        const A x = (A)Enc<T>::dec(v[i]);
+        const A x = decA<T, A>(v[i]);
         if (i >= i10 && i < i90) rv[0] += x;
         rv[1] += x > medA ? x - medA : medA - x;
       }
       block_sum<C, A, 2>(rv, red, s_sc + 4);
       const int cntV = i90 - i10;
-      const double rmean = s_sc[4] / cntV;
-      const A rmA = (A)rmean;
+      if (tid == 0) s_sc[11] = cntV > 0 ? s_sc[4] / (A)cntV : nan;
+      __syncthreads();
+      const A rmA = s_sc[11];
       A ra[1] = {0};
       for (int i = i10 + tid; i < i90; i += C::NT) {
-        const A x = (A)Enc<T>::dec(v[i]);
+        const A x = decA<T, A>(v[i]);
         ra[0] += x > rmA ? x - rmA : rmA - x;
       }
       block_sum<C, A, 1>(ra, red, s_sc + 6);
       if (tid == 0) {
-        put(p, row, Q_STATS + S_MODE, Enc<T>::dec(~(unsigned)(best & 0xFFFFFFFFu)));
-        put(p, row, Q_STATS + S_MODE_PROB, (double)(best >> 32) / n);
-        put(p, row, Q_STATS + S_RMEAN, cntV > 0 ? rmean : nan);
-        put(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[6] / cntV : nan);
-        put(p, row, Q_STATS + S_MEDAD, s_sc[5] / n);
+        const unsigned mode_e = ~(unsigned)(best & 0xFFFFFFFFu);
+        if (Enc<T>::INTEGER) put(p, row, Q_STATS + S_MODE, i2d((long long)mode_e - ibias));
+        else put(p, row, Q_STATS + S_MODE, f2d(Enc<T>::decf(mode_e)));
+        putA(p, row, Q_STATS + S_MODE_PROB, (A)(int)(best >> 32) / (A)n);
+        putA(p, row, Q_STATS + S_RMEAN, rmA);
+        putA(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[6] / (A)cntV : nan);
+        putA(p, row, Q_STATS + S_MEDAD, s_sc[5] / (A)n);
       }
     }
     __syncthreads();

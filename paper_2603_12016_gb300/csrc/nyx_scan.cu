@@ -153,11 +153,24 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t ty = t / ntx, tx = t - ty * ntx;
     const int64_t x0 = tx * TX;
+    // decompose the warp's first row once; later rows step incrementally
+    // (no 64-bit division per row)
+    int64_t row = ty * TY + warp;
+    int64_t y = row % p.ny, zb = row / p.ny;
+    int64_t z = zb % p.nz, b = zb / p.nz;
     for (int rr = warp; rr < TY; rr += SCAN_NT / 32) {
-      const int64_t row = ty * TY + rr;
+      if (rr != warp) {
+        row += SCAN_NT / 32;
+        y += SCAN_NT / 32;
+        while (y >= p.ny) {
+          y -= p.ny;
+          if (++z == p.nz) {
+            z = 0;
+            ++b;
+          }
+        }
+      }
       if (row >= p.rows_total) break;
-      const int64_t y = row % p.ny, zb = row / p.ny;
-      const int64_t z = zb % p.nz, b = zb / p.nz;
       if (b != im_b) {  // warp-uniform: flush the running image range
         unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
         if (lane == 0 && im_b >= 0) {

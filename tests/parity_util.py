@@ -3,7 +3,7 @@
 Tolerances (stated by the build target; natural scales per feature so that
 values that are zero by symmetry are compared against their scale):
   exact     : counts, bounding boxes, min/max/range, labels, order statistics
-              (same FP64 operations on the same sorted values), mode
+              (same FP64 operations on the same sorted values), mode value
   RTOL_STAT : 1e-5 for first-order statistics and moments
   RTOL_GLCM : 1e-4 for GLCM features (scale floor 1)
 |gpu - oracle| <= rtol * max(|oracle|, scale).
@@ -19,9 +19,8 @@ RTOL_STAT = 1e-5
 RTOL_GLCM = 1e-4
 
 EXACT = {"LABEL", "IMAGE", "AREA", "BBOX_XMIN", "BBOX_YMIN", "BBOX_ZMIN", "BBOX_WIDTH", "BBOX_HEIGHT", "BBOX_DEPTH",
-         "MIN", "MAX", "RANGE", "MEDIAN", "P01", "P10", "P25", "P75", "P90", "P99", "INTERQUARTILE_RANGE", "MODE",
-         "MODE_PROBABILITY"}
-DIMENSIONLESS = {"SKEWNESS", "KURTOSIS", "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENTROPY",
+         "MIN", "MAX", "RANGE", "MEDIAN", "P01", "P10", "P25", "P75", "P90", "P99", "INTERQUARTILE_RANGE", "MODE"}
+DIMENSIONLESS = {"MODE_PROBABILITY", "SKEWNESS", "KURTOSIS", "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENTROPY",
                  "UNIFORMITY", "COV", "QCOD", "COVERED_IMAGE_INTENSITY_RANGE", "UNIFORMITY_PIU"}
 
 
