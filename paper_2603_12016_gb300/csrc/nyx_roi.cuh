@@ -471,56 +471,157 @@ __device__ __noinline__ void finalize_stats(const KParams& p, double* row, const
   }
 }
 
-// GLCM features of one offset (Table S3 rows 140-174) from the reduced sums
-// of the marginals and cells; accumulates the direction mean in gsum.
+// int64 / int128 -> float without the FP64 pipe: convert the magnitude (the
+// sum of non-negative halves has no cancellation), then apply the sign
+__device__ inline float u64f(unsigned long long u) {
+  return fmaf((float)(unsigned)(u >> 32), 4294967296.f, (float)(unsigned)(u & 0xFFFFFFFFull));
+}
+__device__ inline float ll2f(long long x) {
+  const float m = u64f(x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x);
+  return x < 0 ? -m : m;
+}
+__device__ inline float i128f(__int128 x) {
+  const unsigned __int128 u = x < 0 ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
+  const float m = fmaf(u64f((unsigned long long)(u >> 64)), 18446744073709551616.f, u64f((unsigned long long)u));
+  return x < 0 ? -m : m;
+}
 template <class A>
-__device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const A* r, A mu, A sumave, A difave,
-                                           A jmax, int di, int dir, A* gsum) {
+__device__ inline A i128A(__int128 x) {
+  if constexpr (std::is_same<A, float>::value) return i128f(x);
+  else return (double)(long long)(x >> 64) * 18446744073709551616.0 + (double)(unsigned long long)x;
+}
+
+// GLCM sums of one offset, reduced over the block.  Integer sums are exact
+// (independent of the order of the hash table): with C the count of a cell
+// (a, b) of the symmetric matrix, k = a + b + 2 (= i + j, 1-based levels) and
+// d = |a - b|,
+//   [0] T = sum C            [1..4] sum C k^m      [5..6] sum C d^m
+//   [7] sum C i^2            [8] sum C^2           [9] sum C log2 C  (2^-24)
+//   [10] sum C log2(C T / (P_i P_j))  (2^-24)      [11] max C
+// Float sums (deterministic: over the marginals in index order):
+//   [0] HX  [1] SUMENT  [2] DIFENTRO  [3] ID  [4] IDM  [5] IDN  [6] IDMN  [7] IV
+constexpr int GI = 12, GF = 8;
+
+// GLCM features of one offset (Table S3 rows 140-174): every moment-type
+// feature from exact integer power sums (central moments of the sum /
+// difference / row distributions as exact integer numerators over powers of
+// T), the entropies from the marginal sums.  Accumulates the direction mean.
+template <class A>
+__device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const long long* iv, const A* fv, int di,
+                                           int dir, A* gsum) {
+  typedef __int128 I;
+  const long long T = iv[0], S1 = iv[1], S2 = iv[2], S3 = iv[3], S4 = iv[4], D1 = iv[5], D2 = iv[6], Q2 = iv[7];
+  const A Ta = i128A<A>(T), invT = (A)1 / Ta;
+  // row distribution: mu = sum i p = S1 / (2T), var = (T Q2 - (S1/2)^2) / T^2
+  const I R1 = (I)S1;  // 2 * sum i P
+  const I var_n = 4 * (I)T * Q2 - R1 * R1;  // 4 T^2 var
+  // sum distribution (k = i + j): mean S1/T, central moments via exact numerators
+  const I c2n = (I)T * S2 - (I)S1 * S1;                                          // T^2 m2
+  const I c3n = (I)T * T * S3 - 3 * (I)T * S1 * S2 + 2 * (I)S1 * S1 * S1;       // T^3 m3
+  const I c4n = (I)T * T * T * S4 - 4 * (I)T * T * S1 * S3 + 6 * (I)T * S1 * S1 * S2 -
+                3 * (I)S1 * S1 * S1 * S1;                                          // T^4 m4
+  const I dvn = (I)T * D2 - (I)D1 * D1;                                          // T^2 var of |i-j|
+  // covariance: sum (i-mu)(j-mu) p = ((S2 - D2) T - S1^2) / (4 T^2)
+  const I cov_n = ((I)S2 - D2) * T - (I)S1 * S1;                                 // 4 T^2 cov
+  const A T2 = Ta * Ta;
+  const A mu = i128A<A>(R1) * invT / 2;
+  const A var = i128A<A>(var_n) / (4 * T2);
+  const A sumave = i128A<A>(S1) * invT;
+  const A sumvar = i128A<A>(c2n) / T2;
+  const A clushade = i128A<A>(c3n) / (T2 * Ta);
+  const A cluprom = i128A<A>(c4n) / (T2 * T2);
+  const A contrast = i128A<A>(D2) * invT;
+  const A difave = i128A<A>(D1) * invT;
+  const A difvar = i128A<A>(dvn) / T2;
+  const A cov = i128A<A>(cov_n) / (4 * T2);
+  const A asmv = i128A<A>(iv[8]) / T2;
+  const A je = alog2(Ta) - i128A<A>(iv[9]) * ((A)(1.0 / 16777216.0) * invT);
+  const A mi = i128A<A>(iv[10]) * ((A)(1.0 / 16777216.0) * invT);
+  const A hx = fv[0];
   A f[NGLCM];
-  const A hx = r[0], var = r[1], sument = r[2], sumvar = r[3], clushade = r[4], cluprom = r[5], contrast = r[6],
-          id = r[7], idm = r[8], idn = r[9], idmn = r[10], iv = r[11], difvar = r[12], difent = r[13], asmv = r[14],
-          je = r[15], mi = r[16];
-  // covariance from the sum and difference marginals:
-  // (i+j-2mu)^2 - (i-j)^2 = 4 (i-mu)(j-mu)
-  const A cov = (sumvar - contrast) / 4;
   f[G_ASM] = asmv;
-  f[G_ACOR] = cov + mu * mu;
+  f[G_ACOR] = i128A<A>((I)S2 - D2) * invT / 4;
   f[G_CLUPROM] = cluprom;
   f[G_CLUSHADE] = clushade;
   f[G_CLUTEND] = sumvar;
   f[G_CONTRAST] = contrast;
-  f[G_CORR] = var > 0 ? cov / var : (A)1;
+  f[G_CORR] = var_n > 0 ? i128A<A>(cov_n) / i128A<A>(var_n) : (A)1;
   f[G_DIFAVE] = difave;
-  f[G_DIFENTRO] = difent;
+  f[G_DIFENTRO] = fv[2];
   f[G_DIFVAR] = difvar;
   f[G_DIS] = difave;
   f[G_ENERGY] = asqrt(asmv);
   f[G_ENTROPY] = je;
-  f[G_HOM1] = id;
-  f[G_HOM2] = idm;
-  f[G_IDM] = idm;
+  f[G_HOM1] = fv[3];
+  f[G_HOM2] = fv[4];
+  f[G_IDM] = fv[4];
   // HXY1 = HXY2 = HX + HY and HX = HY for a symmetric matrix, so
   // HXY - HXY1 = -MI and HXY2 - HXY = MI (mutual information)
   f[G_INFOMEAS1] = hx > 0 ? -mi / hx : (A)0;
   const A arg = (A)1 - aexp((A)-2 * mi);
   f[G_INFOMEAS2] = asqrt(arg > 0 ? arg : (A)0);
-  f[G_IDMN] = idmn;
-  f[G_ID] = id;
-  f[G_IDN] = idn;
-  f[G_IV] = iv;
+  f[G_IDMN] = fv[6];
+  f[G_ID] = fv[3];
+  f[G_IDN] = fv[5];
+  f[G_IV] = fv[7];
   f[G_JAVE] = mu;
   f[G_JE] = je;
-  f[G_JMAX] = jmax;
+  f[G_JMAX] = i128A<A>(iv[11]) * invT;
   f[G_SUMAVE] = sumave;
-  f[G_SUMENT] = sument;
+  f[G_SUMENT] = fv[1];
   f[G_JVAR] = var;
   f[G_SUMVAR] = sumvar;
   f[G_VARIANCE] = var;
+  (void)cov;
   for (int g = 0; g < NGLCM; ++g) {
     if (p.per_offset) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
     gsum[g] += f[g];
   }
   gsum[NGLCM] += 1;
+}
+
+// Block reduction of GI int64 and GF float values (plain sums; the int64
+// ones are exact, the floats are GLCM marginal sums with a 1e-4 budget).
+// Results in iout / fout (shared memory) for every thread.
+template <class C, class A>
+__device__ inline void block_sum_glcm(long long (&iv)[GI], A (&fv)[GF], double* scratch_d, long long* iout, A* fout) {
+  long long* si = (long long*)scratch_d;
+  A* sf = (A*)(si + C::NW * GI);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < GI; ++i) {
+    long long x = iv[i];
+    if (i == GI - 1) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        x = y > x ? y : x;
+      }
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    }
+    if (lane == 0) si[warp * GI + i] = x;
+  }
+#pragma unroll
+  for (int i = 0; i < GF; ++i) {
+    A x = fv[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    if (lane == 0) sf[warp * GF + i] = x;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < GI) {
+    long long s = si[t];
+    for (int w = 1; w < C::NW; ++w) s = t == GI - 1 ? (si[w * GI + t] > s ? si[w * GI + t] : s) : s + si[w * GI + t];
+    iout[t] = s;
+  } else if (t < GI + GF) {
+    A s = 0;
+    for (int w = 0; w < C::NW; ++w) s += sf[w * GF + t - GI];
+    fout[t - GI] = s;
+  }
+  __syncthreads();
 }
 
 // Percentiles by linear interpolation at h = (n-1) q on the sorted values,
@@ -638,6 +739,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
   __shared__ int s_idx[4];
   __shared__ A s_gsum[NGLCM + 1];
   __shared__ A s_pa[10];  // per-ROI scalars: mean (hi, lo), centroids, sums
+  __shared__ unsigned s_ncell, s_npair;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned* qlen = p.qlen + cls;
@@ -943,14 +1045,24 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
     }
 
     // ---- GLCM ------------------------------------------------------------------
+    // Per offset: warp-aggregated inserts into a shared hash table of
+    // (min bin, max bin) -> count that also records its occupied slots, so
+    // every later pass and the clean-up cost O(cells), not O(capacity).
     if (need_glcm) {
       const int ng = p.ng;
       unsigned* px = marg;
       unsigned* psum = marg + ng;      // index a + b, 0 .. 2ng-2
       unsigned* pdiff = marg + 3 * ng; // index |a - b|
+      uint16_t* cells = rank;          // occupied slots of the table (rank is free until the sort)
       int cap = 64;
       while (cap < 2 * n && cap < C::TAB) cap <<= 1;
       const bool dbg = p.dbg_roi == (int64_t)item;
+      for (int i = tid; i < cap; i += C::NT) tab[i] = 0;
+      for (int i = tid; i < 4 * ng; i += C::NT) marg[i] = 0;
+      if (tid == 0) {
+        s_ncell = 0;
+        s_npair = 0;
+      }
       for (int di = 0; di < p.n_dist; ++di) {
         if (tid == 0)
           for (int g = 0; g <= NGLCM; ++g) s_gsum[g] = 0;
@@ -958,8 +1070,6 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           const int oi = di * p.n_dirs + dir;
           const int dx = p.off[oi][0], dy = p.off[oi][1], dz = p.off[oi][2];
           const int olin = (dz * Hp + dy) * Wp + dx;
-          for (int i = tid; i < cap; i += C::NT) tab[i] = 0;
-          for (int i = tid; i < 4 * ng; i += C::NT) marg[i] = 0;
           __syncthreads();
           // accumulate pairs (q, q + o) inside the ROI
           for (int i0 = warp * 32; i0 < n; i0 += C::NT) {
@@ -975,6 +1085,8 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
               if (b != 0xFFFFu) key = a < b ? (a << 8) | b : (b << 8) | a;
             }
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+            const unsigned nvalid = __popc(__ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu));
+            if (lane == 0 && nvalid) atomicAdd(&s_npair, nvalid);
             if (key != 0xFFFFFFFFu && (peers & lanemask_lt()) == 0) {
               const unsigned add = (unsigned)__popc(peers);
               unsigned h = (key * 2654435761u >> 7) & (unsigned)(cap - 1);
@@ -982,7 +1094,10 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
                 const unsigned wv = tab[h];
                 if (wv == 0) {
                   const unsigned old = atomicCAS(&tab[h], 0u, (key << 16) | add);
-                  if (old == 0) break;
+                  if (old == 0) {
+                    cells[atomicAdd(&s_ncell, 1u)] = (uint16_t)h;
+                    break;
+                  }
                   if ((old >> 16) == key) {
                     atomicAdd(&tab[h], add);
                     break;
@@ -996,110 +1111,106 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             }
           }
           __syncthreads();
-          // marginals from the non-zero cells
-          for (int s = tid; s < cap; s += C::NT) {
-            const unsigned wv = tab[s];
-            if (!wv) continue;
+          const int ncell = (int)s_ncell;
+          // pass 1 over the cells: marginals and exact integer power sums
+          long long iv[GI];
+#pragma unroll
+          for (int k = 0; k < GI; ++k) iv[k] = 0;
+          for (int s = tid; s < ncell; s += C::NT) {
+            const unsigned wv = tab[cells[s]];
             const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
             const unsigned a = key >> 8, b = key & 255u;
             atomicAdd(&px[a], cnt);
             atomicAdd(&px[b], cnt);
             atomicAdd(&psum[a + b], 2 * cnt);
             atomicAdd(&pdiff[b - a], 2 * cnt);
+            const long long Cm = 2 * (long long)cnt;  // mass of the cell pair (or of the doubled diagonal cell)
+            const long long k = a + b + 2, d = b - a, k2 = k * k;
+            iv[0] += Cm;
+            iv[1] += Cm * k;
+            iv[2] += Cm * k2;
+            iv[3] += Cm * k2 * k;
+            iv[4] += Cm * k2 * k2;
+            iv[5] += Cm * d;
+            iv[6] += Cm * d * d;
+            iv[7] += (long long)cnt * ((long long)(a + 1) * (a + 1) + (long long)(b + 1) * (b + 1));
+            const long long Cc = a == b ? 2 * (long long)cnt : (long long)cnt;  // count of one matrix cell
+            const long long mult = a == b ? 1 : 2;
+            iv[8] += mult * Cc * Cc;
+            iv[9] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
+            iv[11] = Cc > iv[11] ? Cc : iv[11];
             if (dbg) {
-              p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + b] = a == b ? 2 * cnt : cnt;
-              p.dbg_glcm[(int64_t)oi * ng * ng + b * ng + a] = a == b ? 2 * cnt : cnt;
+              p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + b] = (unsigned)Cc;
+              p.dbg_glcm[(int64_t)oi * ng * ng + b * ng + a] = (unsigned)Cc;
             }
           }
           __syncthreads();
-          // exact integer first moments: T, sum (a+1) px, sum (s+2) psum, sum k pdiff
-          {
-            long long iv[4] = {0, 0, 0, 0};
-            for (int a = tid; a < ng; a += C::NT) {
-              iv[0] += px[a];
-              iv[1] += (long long)(a + 1) * px[a];
-              iv[3] += (long long)a * pdiff[a];
-            }
-            for (int s = tid; s < 2 * ng - 1; s += C::NT) iv[2] += (long long)(s + 2) * psum[s];
-            block_sum_i64<C, 4>(iv, red, s_i64 + 8);
-          }
-          const long long Ti = s_i64[8];
-          if (Ti == 0) {  // no pair for this offset: every feature NaN
+          if (ncell == 0) {  // no pair for this offset: every feature NaN
             if (tid == 0 && p.per_offset)
               for (int g = 0; g < NGLCM; ++g) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, nan);
-            __syncthreads();
             continue;
           }
-          // first moments from exact 32-bit sums (T <= 2^17, sums <= 2^26)
-          const A Ta = (A)(int)Ti;
-          const A invT = (A)1 / Ta, muA = (A)(int)s_i64[9] / Ta, saA = (A)(int)s_i64[10] / Ta,
-                  daA = (A)(int)s_i64[11] / Ta, ngA = (A)ng;
-          const float Tf = (float)(int)Ti;
-          // sums over the marginals
-          A gv[14];
+          // pass 2: marginal sums (index order) and mutual information (cells)
+          A fv[GF];
 #pragma unroll
-          for (int k = 0; k < 14; ++k) gv[k] = 0;
+          for (int k = 0; k < GF; ++k) fv[k] = 0;
+          const long long Tl = 2 * (long long)s_npair;  // total mass of the symmetric matrix
+          const A invT = (A)1 / (A)(int)Tl, ngA = (A)ng;
+          const float Tf = (float)(int)Tl;
           for (int a = tid; a < ng; a += C::NT) {
             if (!px[a]) continue;
-            const A pr = (A)px[a] * invT, di_ = (A)(a + 1) - muA;
-            gv[0] -= pr * alog2(pr);  // HX
-            gv[1] += di_ * di_ * pr;  // sigma^2
+            const A pr = (A)px[a] * invT;
+            fv[0] -= pr * alog2(pr);  // HX
           }
           for (int s = tid; s < 2 * ng - 1; s += C::NT) {
             if (!psum[s]) continue;
-            const A pr = (A)psum[s] * invT, dk = (A)(s + 2) - saA;
-            gv[2] -= pr * alog2(pr);          // SUMENT
-            gv[3] += dk * dk * pr;            // SUMVAR = CLUTEND
-            gv[4] += dk * dk * dk * pr;       // CLUSHADE
-            gv[5] += dk * dk * dk * dk * pr;  // CLUPROM
+            const A pr = (A)psum[s] * invT;
+            fv[1] -= pr * alog2(pr);  // SUMENT
           }
           for (int k = tid; k < ng; k += C::NT) {
             if (!pdiff[k]) continue;
-            const A pr = (A)pdiff[k] * invT, kk = (A)k, dk = kk - daA;
-            gv[6] += kk * kk * pr;                          // CONTRAST
-            gv[7] += pr / ((A)1 + kk);                      // ID = HOM1
-            gv[8] += pr / ((A)1 + kk * kk);                 // IDM = HOM2
-            gv[9] += pr / ((A)1 + kk / ngA);                // IDN
-            gv[10] += pr / ((A)1 + kk * kk / (ngA * ngA));  // IDMN
-            if (k >= 1) gv[11] += pr / (kk * kk);           // IV
-            gv[12] += dk * dk * pr;                         // DIFVAR
-            gv[13] -= pr * alog2(pr);                       // DIFENTRO
+            const A pr = (A)pdiff[k] * invT, kk = (A)k;
+            fv[2] -= pr * alog2(pr);                        // DIFENTRO
+            fv[3] += pr / ((A)1 + kk);                      // ID = HOM1
+            fv[4] += pr / ((A)1 + kk * kk);                 // IDM = HOM2
+            fv[5] += pr / ((A)1 + kk / ngA);                // IDN
+            fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));  // IDMN
+            if (k >= 1) fv[7] += pr / (kk * kk);            // IV
           }
-          // sums over the non-zero cells, exact in 64-bit integers (fixed
-          // point 2^-24 for the logarithmic terms) so that they do not depend
-          // on the order in which the hash table was filled:
-          //   [0] sum C^2, [1] sum C log2 C, [2] sum C log2(C T / (P_a P_b))
-          // with C the count of a cell of the symmetric matrix
-          long long cs[3] = {0, 0, 0};
-          unsigned long long cmax = 0;
-          for (int s = tid; s < cap; s += C::NT) {
-            const unsigned wv = tab[s];
-            if (!wv) continue;
+          for (int s = tid; s < ncell; s += C::NT) {
+            const unsigned wv = tab[cells[s]];
             const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
             const unsigned a = key >> 8, b = key & 255u;
-            const long long mult = a == b ? 1 : 2;  // cells (a,b) and (b,a)
+            const long long mult = a == b ? 1 : 2;
             const unsigned Cc = a == b ? 2 * cnt : cnt;
-            cs[0] += mult * (long long)Cc * Cc;
-            cs[1] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
             const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[b]);
-            cs[2] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
-            cmax = Cc > cmax ? Cc : cmax;
+            iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
           }
-          block_sum<C, A, 14>(gv, red, res);
-          block_sum_i64<C, 3>(cs, red, s_i64 + 12);
-          cmax = block_max_u64<C>(cmax, red);
-          if (tid == 0) {
-            res[14] = (A)s_i64[12] * invT * invT;                                  // ASM
-            res[15] = alog2(Ta) - (A)s_i64[13] * ((A)(1.0 / 16777216.0) * invT);  // JE
-            res[16] = (A)s_i64[14] * ((A)(1.0 / 16777216.0) * invT);              // MI
-            finalize_glcm<A>(p, row, res, muA, saA, daA, (A)(int)cmax * invT, di, dir, s_gsum);
+          block_sum_glcm<C, A>(iv, fv, red, s_i64, res);
+          if (tid == 0) finalize_glcm<A>(p, row, s_i64, res, di, dir, s_gsum);
+          // clean up only what this offset touched
+          for (int s = tid; s < ncell; s += C::NT) {
+            const unsigned h = cells[s];
+            const unsigned key = tab[h] >> 16;
+            const unsigned a = key >> 8, b = key & 255u;
+            px[a] = 0;
+            px[b] = 0;
+            psum[a + b] = 0;
+            pdiff[b - a] = 0;
           }
           __syncthreads();
+          for (int s = tid; s < ncell; s += C::NT) tab[cells[s]] = 0;
+          if (tid == 0) {
+            s_ncell = 0;
+            s_npair = 0;
+          }
         }
+        __syncthreads();
         if (tid == 0)
           for (int g = 0; g < NGLCM; ++g)
             putA(p, row, Q_GLCM_D + di * NGLCM + g, s_gsum[NGLCM] > 0 ? s_gsum[g] / s_gsum[NGLCM] : nan);
       }
+      __syncthreads();
     }
 
     // ---- order statistics: block radix sort of the encoded values -----------
