@@ -1084,11 +1084,13 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
               const unsigned a = raster[ci], b = raster[ci + olin];
               if (b != 0xFFFFu) key = a < b ? (a << 8) | b : (b << 8) | a;
             }
-            const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+            // one insert per pair: with up to Ng^2/2 keys the pairs of a warp
+            // are mostly distinct, so aggregating them first costs more than
+            // the shared-memory atomics it would save
             const unsigned nvalid = __popc(__ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu));
             if (lane == 0 && nvalid) atomicAdd(&s_npair, nvalid);
-            if (key != 0xFFFFFFFFu && (peers & lanemask_lt()) == 0) {
-              const unsigned add = (unsigned)__popc(peers);
+            if (key != 0xFFFFFFFFu) {
+              const unsigned add = 1u;
               unsigned h = (key * 2654435761u >> 7) & (unsigned)(cap - 1);
               for (int probe = 0; probe < cap; ++probe) {
                 const unsigned wv = tab[h];
@@ -1228,8 +1230,15 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         for (int i0 = lo; i0 < hi; i0 += 32) {
           const int i = i0 + lane;
           const bool act = i < hi;
-          const unsigned dg = act ? (src[i] >> shift) & 255u : 256u + lane;
-          const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+          const unsigned dg = act ? (src[i] >> shift) & 255u : 0u;
+          // lanes holding the same digit, from 8 ballots (constant cost, unlike
+          // a match over up to 32 distinct values)
+          unsigned peers = __ballot_sync(0xFFFFFFFFu, act);
+#pragma unroll
+          for (int bit = 0; bit < 8; ++bit) {
+            const unsigned bb = __ballot_sync(0xFFFFFFFFu, (dg >> bit) & 1u);
+            peers &= ((dg >> bit) & 1u) ? bb : ~bb;
+          }
           const unsigned before = __popc(peers & lanemask_lt());
           unsigned b0 = 0;
           if (act) b0 = cnt[warp * 256 + dg];

@@ -216,9 +216,10 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
             xe = q;
           }
         }
-        const unsigned long long k =
-            act ? (((unsigned long long)b << 32) | (unsigned)L[j]) : (0xFFFFFFFF00000000ull | (unsigned)lane);
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+        // the image index b is uniform across the row, so the 32-bit label
+        // identifies the ROI; inactive lanes share the background label 0
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, act ? (unsigned)L[j] : 0u);
+        const unsigned long long k = ((unsigned long long)b << 32) | (unsigned)L[j];
         const unsigned cnt = __reduce_add_sync(peers, act ? c : 0u);
         const unsigned vmn = __reduce_min_sync(peers, act ? mn : 0xFFFFFFFFu);
         const unsigned vmx = __reduce_max_sync(peers, act ? mx : 0u);
