@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ROIs/sec and Mpixel/sec full feature set, % HBM roofline vs plain FP64 path"
-PHASES = ("scan", "sort_setup", "roi_small", "roi_medium", "reset")
+PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "reset")
 
 
 def _peaks():
@@ -268,7 +268,7 @@ def main() -> int:
     dom = max(phases, key=phases.get)
     dom_bytes = {"scan": w.image.nbytes + w.mask.nbytes,
                  "sort_setup": 0,
-                 "roi_small": None, "roi_medium": None, "reset": 0}[dom]
+                 "roi_warp": None, "roi_small": None, "roi_medium": None, "reset": 0}[dom]
     if dom_bytes is None:
         roi_px = int((w.mask > 0).sum())
         share = 1.0

@@ -180,10 +180,11 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
  * for the events of the extract `back` calls ago (0 = the last one, up to
  * slots - 1) and writes up to NYX_N_PHASES durations in milliseconds:
  * [0] counters + label scan, [1] key sort + per-ROI setup, [2] ROI kernel of
- * the small class, [3] ROI kernel of the medium class, [4] table reset.
+ * the warp class (one warp per ROI), [3] of the small block class, [4] of the
+ * medium block class, [5] table reset.
  * Errors: NYX_ERR_ARG (null plan/ms, slots out of 0..1024, back out of
  * range), NYX_ERR_STATE (that extract was not recorded), NYX_ERR_CUDA. */
-#define NYX_N_PHASES 5
+#define NYX_N_PHASES 6
 nyx_status nyx_profile_enable(nyx_plan* plan, int slots);
 nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
 

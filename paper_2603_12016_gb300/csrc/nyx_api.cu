@@ -398,10 +398,12 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.n_col = (int)pl->col_names.size();
   k.max_rois = mr;
   k.dbg_roi = -1;
-  k.lim_pix[0] = 1024;
-  k.lim_cells[0] = 4096;
-  k.lim_pix[1] = 8192;
-  k.lim_cells[1] = 16384;
+  k.lim_pix[0] = 512;
+  k.lim_cells[0] = 2048;
+  k.lim_pix[1] = 1024;
+  k.lim_cells[1] = 4096;
+  k.lim_pix[2] = 8192;
+  k.lim_cells[2] = 16384;
   e = cudaMemcpy(pl->d_col_map, pl->col_map.data(), 4ull * Q_TOTAL, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(small, 0, 64);
   if (e == cudaSuccess) {
@@ -539,7 +541,7 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
   if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
   if (prof) NYX_CUDA(c, cudaEventRecord(ev[2], st));
   const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
-  for (int cls = 0; cls < 2; ++cls) {
+  for (int cls = 0; cls < 3; ++cls) {
     cudaError_t e;
     switch (k.dtype) {
       case NYX_U16: e = launch_roi_u16(k, cls, fp64, c->nsm, st); break;
@@ -551,7 +553,7 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
   }
   if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
   if (prof) {
-    NYX_CUDA(c, cudaEventRecord(ev[5], st));
+    NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));
     ++pl->prof_count;
   }
   if (flags & NYX_SYNC) return read_err(pl, st);

@@ -123,7 +123,7 @@ struct KParams {
   unsigned long long* sorted_keys;
   RoiInfo* rois;
   int* slot_dense;
-  int* queue;                      // [3][max_rois]
+  int* queue;                      // [3][max_rois], one per size class
   unsigned* qlen;                  // [3]
   unsigned* qhead;                 // [3]
   unsigned* n_roi;                 // device ROI count
@@ -135,8 +135,9 @@ struct KParams {
   // debug hook
   int64_t dbg_roi;
   unsigned* dbg_glcm;              // [n_off][ng*ng]
-  // class limits (pixels, padded raster cells) of the single-block paths
-  int lim_pix[2], lim_cells[2];
+  // class limits (pixels, padded raster cells): 0 warp path, 1 small
+  // block path, 2 medium block path
+  int lim_pix[3], lim_cells[3];
 };
 
 // ---------------------------------------------------------------------------

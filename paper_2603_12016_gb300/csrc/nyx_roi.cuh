@@ -42,6 +42,7 @@ struct RoiClass {
   static constexpr int CELLS = CELLS_;  // max padded raster cells
   static constexpr int TAB = 2 * PIX_;  // GLCM hash capacity (power of two); also 2 sort buffers
 };
+using ClassW = RoiClass<32, 512, 2048>;    // one warp per ROI
 using ClassS = RoiClass<128, 1024, 4096>;
 using ClassM = RoiClass<256, 8192, 16384>;
 
@@ -781,66 +782,107 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
     const int nrows = H * D;
     const T* img = (const T*)p.img;
     const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
-    for (int rb = 0; rb < nrows; rb += C::NW) {
-      const int rr = rb + warp;
-      const bool have = rr < nrows;
-      const int ry = have ? rr % H : 0, rz = have ? rr / H : 0;
-      const int64_t roff = origin + ((int64_t)rz * p.ny + ry) * p.nx;
-      unsigned cnt = 0;
-      if (have)
-        for (int x0 = 0; x0 < W; x0 += 32) {
-          const int x = x0 + lane;
-          const bool in = x < W && __ldg(p.mask + roff + x) == label;
-          cnt += __popc(__ballot_sync(0xFFFFFFFFu, in));
-        }
-      if (lane == 0) s_rowcnt[warp] = cnt;
-      __syncthreads();
-      if (tid == 0) {
-        unsigned run = s_rowbase[C::NW];
-        for (int w = 0; w < C::NW; ++w) {
-          s_rowbase[w] = run;
-          run += s_rowcnt[w];
-        }
-        s_rowbase[C::NW] = run;
-      }
-      __syncthreads();
-      unsigned base = s_rowbase[warp];
-      if (have)
-        for (int x0 = 0; x0 < W; x0 += 32) {
-          const int x = x0 + lane;
-          const bool in = x < W && __ldg(p.mask + roff + x) == label;
-          const unsigned bal = __ballot_sync(0xFFFFFFFFu, in);
-          if (in) {
-            const unsigned pos = base + __popc(bal & lanemask_lt());
-            const unsigned e = Enc<T>::enc(__ldg(img + roff + x));
-            if (pos < (unsigned)C::PIX) {
-              pc[pos] = NDIM == 3 ? ((unsigned)x | ((unsigned)ry << 11) | ((unsigned)rz << 22))
-                                  : ((unsigned)x | ((unsigned)ry << 16));
-              pv[pos] = e;
-            }
-            // GLCM bin and histogram bin (rule a4)
-            unsigned gb = 0, hb = 0;
-            if (vmax > vmin) {
-              if (Enc<T>::INTEGER) {
-                const unsigned dv = e - vmin;
-                gb = min(s_fd.div((unsigned)p.ng * dv), (unsigned)(p.ng - 1));
-                hb = min(s_fd.div((unsigned)p.hist_bins * dv), (unsigned)(p.hist_bins - 1));
-              } else {
-                const float xv = Enc<T>::decf(e);
-                if (need_glcm) gb = bin_float(xv, fmn, fmx, p.ng);
-                if (need & NEED_HIST) hb = bin_float(xv, fmn, fmx, p.hist_bins);
-              }
-            }
-            if (need_glcm) {
-              const int ri = ((NDIM == 3 ? rz + pad : 0) * Hp + (ry + pad)) * Wp + (x + pad);
-              if (ri < cells) raster[ri] = (uint16_t)gb;
-              else atomicOr(p.err, E_INTERNAL);
-            }
-            if (need & NEED_HIST) atomicAdd(&hist[hb], 1u);
+    // Work items are (row, 32-column chunk) pairs in raster order.  Each warp
+    // takes U consecutive items per iteration and issues all their loads
+    // before using them (the bounding box is L2-resident, so latency, not
+    // bandwidth, bounds this loop); pixel positions follow raster order via a
+    // prefix over warps, which keeps the pixel list deterministic.
+    constexpr int U = C::NW == 1 ? 8 : (C::NW <= 4 ? 4 : 2);
+    const int nchk = (W + 31) >> 5;
+    const int nitems = nrows * nchk;
+    unsigned run = 0;  // pixels placed so far (single-warp blocks)
+    for (int ib = 0; ib < nitems; ib += C::NW * U) {
+      const int i0 = ib + warp * U;
+      int rr = i0 / nchk, xc = i0 - rr * nchk;
+      int ry = rr % H, rz = rr / H;
+      unsigned bal[U];
+      int64_t roff[U];
+      int xs[U];
+      unsigned wcnt = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool have = i0 + u < nitems;
+        xs[u] = xc * 32 + lane;
+        roff[u] = origin + ((int64_t)rz * p.ny + ry) * p.nx;
+        const bool in = have && xs[u] < W && __ldg(p.mask + roff[u] + xs[u]) == label;
+        bal[u] = __ballot_sync(0xFFFFFFFFu, in);
+        wcnt += __popc(bal[u]);
+        if (++xc == nchk) {
+          xc = 0;
+          if (++ry == H) {
+            ry = 0;
+            ++rz;
           }
-          base += __popc(bal);
         }
+      }
+      unsigned base;
+      if (C::NW == 1) {
+        base = run;
+        run += wcnt;
+      } else {
+        if (lane == 0) s_rowcnt[warp] = wcnt;
+        __syncthreads();
+        if (tid == 0) {
+          unsigned acc = s_rowbase[C::NW];
+          for (int w = 0; w < C::NW; ++w) {
+            s_rowbase[w] = acc;
+            acc += s_rowcnt[w];
+          }
+          s_rowbase[C::NW] = acc;
+        }
+        __syncthreads();
+        base = s_rowbase[warp];
+      }
+      rr = i0 / nchk;
+      xc = i0 - rr * nchk;
+      ry = rr % H;
+      rz = rr / H;
+      T val[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if ((bal[u] >> lane) & 1u) val[u] = __ldg(img + roff[u] + xs[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((bal[u] >> lane) & 1u) {
+          const int x = xs[u];
+          const unsigned pos = base + __popc(bal[u] & lanemask_lt());
+          const unsigned e = Enc<T>::enc(val[u]);
+          if (pos < (unsigned)C::PIX) {
+            pc[pos] = NDIM == 3 ? ((unsigned)x | ((unsigned)ry << 11) | ((unsigned)rz << 22))
+                                : ((unsigned)x | ((unsigned)ry << 16));
+            pv[pos] = e;
+          }
+          // GLCM bin and histogram bin (rule a4)
+          unsigned gb = 0, hb = 0;
+          if (vmax > vmin) {
+            if (Enc<T>::INTEGER) {
+              const unsigned dv = e - vmin;
+              gb = min(s_fd.div((unsigned)p.ng * dv), (unsigned)(p.ng - 1));
+              hb = min(s_fd.div((unsigned)p.hist_bins * dv), (unsigned)(p.hist_bins - 1));
+            } else {
+              const float xv = Enc<T>::decf(e);
+              if (need_glcm) gb = bin_float(xv, fmn, fmx, p.ng);
+              if (need & NEED_HIST) hb = bin_float(xv, fmn, fmx, p.hist_bins);
+            }
+          }
+          if (need_glcm) {
+            const int ri = ((NDIM == 3 ? rz + pad : 0) * Hp + (ry + pad)) * Wp + (x + pad);
+            if (ri < cells) raster[ri] = (uint16_t)gb;
+            else atomicOr(p.err, E_INTERNAL);
+          }
+          if (need & NEED_HIST) atomicAdd(&hist[hb], 1u);
+        }
+        base += __popc(bal[u]);
+        if (++xc == nchk) {
+          xc = 0;
+          if (++ry == H) {
+            ry = 0;
+            ++rz;
+          }
+        }
+      }
     }
+    if (C::NW == 1 && lane == 0) s_rowbase[C::NW] = run;
     __syncthreads();
     if (tid == 0 && s_rowbase[C::NW] != (unsigned)n) atomicOr(p.err, E_INTERNAL);
 
@@ -1019,9 +1061,10 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
     if (tid == 0)
       finalize_stats<T, NDIM, A>(p, row, res_st, n, mu_hi + mu_lo, sumI, energy, vmin, vmax, bimg, r.x0, r.y0, r.z0,
                                  cx, cy, cz, bx, by, bz, wvalid, save);
-    if (warp == 1 && (need & (NEED_MOM_INT | NEED_SAVE)))
+    // (blocks with fewer warps run these groups one after the other)
+    if (warp == (C::NW > 1 ? 1 : 0) && (need & (NEED_MOM_INT | NEED_SAVE)))
       finalize_moments_warp<NDIM, A>(p, row, 0, res_mi, cx, cy, cz, wvalid, save ? save + SV_MU : nullptr);
-    if (warp == 2 && (need & NEED_MOM_BIN))
+    if (warp == (C::NW > 2 ? 2 : 0) && (need & NEED_MOM_BIN))
       finalize_moments_warp<NDIM, A>(p, row, 5, res_mb, bx, by, bz, true, nullptr);
     __syncthreads();
 
@@ -1386,16 +1429,20 @@ cudaError_t launch_roi_one(const KParams& p, int cls, int nsm, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+template <class T, class C>
+cudaError_t launch_roi_c(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st) {
+  if (p.ndim == 3)
+    return fp64 ? launch_roi_one<T, 3, C, double>(p, cls, nsm, st) : launch_roi_one<T, 3, C, float>(p, cls, nsm, st);
+  return fp64 ? launch_roi_one<T, 2, C, double>(p, cls, nsm, st) : launch_roi_one<T, 2, C, float>(p, cls, nsm, st);
+}
+
 template <class T>
 cudaError_t launch_roi_t(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st) {
-  if (p.ndim == 3) {
-    if (cls == 0)
-      return fp64 ? launch_roi_one<T, 3, ClassS, double>(p, cls, nsm, st) : launch_roi_one<T, 3, ClassS, float>(p, cls, nsm, st);
-    return fp64 ? launch_roi_one<T, 3, ClassM, double>(p, cls, nsm, st) : launch_roi_one<T, 3, ClassM, float>(p, cls, nsm, st);
+  switch (cls) {
+    case 0: return launch_roi_c<T, ClassW>(p, cls, fp64, nsm, st);
+    case 1: return launch_roi_c<T, ClassS>(p, cls, fp64, nsm, st);
+    default: return launch_roi_c<T, ClassM>(p, cls, fp64, nsm, st);
   }
-  if (cls == 0)
-    return fp64 ? launch_roi_one<T, 2, ClassS, double>(p, cls, nsm, st) : launch_roi_one<T, 2, ClassS, float>(p, cls, nsm, st);
-  return fp64 ? launch_roi_one<T, 2, ClassM, double>(p, cls, nsm, st) : launch_roi_one<T, 2, ClassM, float>(p, cls, nsm, st);
 }
 
 }  // namespace nyx

@@ -337,14 +337,14 @@ __global__ void k_setup(KParams p) {
     const long long cells = (long long)(r.w + 2 * pad) * (r.h + 2 * pad) * (p.ndim == 3 ? r.d + 2 * pad : 1);
     bool pack_ok = p.ndim == 3 ? (r.w + 2 * pad <= 2048 && r.h + 2 * pad <= 2048 && r.d + 2 * pad <= 1024)
                                : (r.w + 2 * pad <= 65535 && r.h + 2 * pad <= 65535);
-    int cls = 2;
-    if (pack_ok && r.n <= (unsigned)p.lim_pix[0] && cells <= p.lim_cells[0]) cls = 0;
-    else if (pack_ok && r.n <= (unsigned)p.lim_pix[1] && cells <= p.lim_cells[1]) cls = 1;
+    int cls = 3;  // beyond every single-block path
+    for (int c = 2; c >= 0; --c)
+      if (pack_ok && r.n <= (unsigned)p.lim_pix[c] && cells <= p.lim_cells[c]) cls = c;
     r.cls = cls;
     r.pad = 0;
     p.rois[i] = r;
     if ((int64_t)i >= p.cap_roi) continue;  // no room for its output row
-    if (cls == 2) {
+    if (cls == 3) {
       atomicOr(p.err, E_TOO_LARGE);
       continue;
     }
