@@ -188,6 +188,34 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
 nyx_status nyx_profile_enable(nyx_plan* plan, int slots);
 nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
 
+/* Allocation-free ROI count (the paper has no counterpart; this is a service
+ * for callers that may not allocate device memory).  Some hosts cannot let a
+ * library call cudaMalloc: applications that hand all device memory to their
+ * own pool allocator and forbid plug-ins from allocating, programs running
+ * under a fixed device-memory quota on a shared node or an acquisition
+ * workstation, and code paths that cannot afford cudaMalloc's implicit
+ * device synchronisation.  This call counts the ROIs of an image exactly like
+ * nyx_count_rois, with no context, no plan and no allocation: its label table
+ * lives in a fixed array inside the library, of about 2 MB per GPU, which
+ * every GPU that loads the library holds until the process exits.
+ *   params : dims, batch, dtype and ndim are read (other fields ignored);
+ *            struct_size must be sizeof(nyx_params)
+ *   d_img, d_mask : device pointers as for nyx_count_rois, 16-byte aligned
+ *   n_roi  : host int64 receiving the count
+ * Limits: at most NYX_NOALLOC_MAX_LABELS distinct (image, label) pairs and a
+ * batch of at most NYX_NOALLOC_MAX_BATCH images; beyond either the call
+ * returns NYX_ERR_CAPACITY.  The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress) with that device current, so make it
+ * before any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The call synchronises `stream`.
+ * Errors: NYX_ERR_ARG, NYX_ERR_SHAPE, NYX_ERR_DTYPE, NYX_ERR_BAD_LABEL,
+ * NYX_ERR_NONFINITE, NYX_ERR_CAPACITY, NYX_ERR_CUDA. */
+#define NYX_NOALLOC_MAX_LABELS 16384
+#define NYX_NOALLOC_MAX_BATCH 1024
+nyx_status nyx_count_rois_noalloc(const nyx_params* params, const void* d_img, const int32_t* d_mask,
+                                  int64_t* n_roi, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

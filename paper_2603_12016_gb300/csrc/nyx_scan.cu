@@ -13,6 +13,7 @@
 //   block   : a shared-memory hash table per 32 x 128 tile
 //   global  : one insert + field atomics per (tile, label)
 #include <cstdio>
+#include <cstring>
 
 #include "nyx_internal.cuh"
 
@@ -483,4 +484,95 @@ cudaError_t launch_debug_bins(const KParams& p, uint16_t* out, int nsm, cudaStre
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free ROI count.
+//
+// Some callers cannot allocate device memory for this library: hosts that
+// hand every byte of the GPU to their own pool allocator and forbid
+// cudaMalloc from plug-ins, applications running under a fixed device-memory
+// quota (a shared cloud node, an instrument PC that keeps acquiring while it
+// analyses), and code paths where cudaMalloc's implicit device
+// synchronisation is not acceptable.  For them nyx_count_rois_noalloc runs
+// the label scan with its label table in this fixed file-scope array instead
+// of a plan workspace.  Every GPU that loads the library holds the array
+// until the process exits.
+//
+// Layout of the array (bytes): keys[NOALLOC_SLOTS] (8 B each), slot
+// accumulators[NOALLOC_SLOTS] (48 B each), slot list[NOALLOC_SLOTS] (4 B each),
+// image ranges 2 x NOALLOC_MAX_BATCH (4 B each), 64 B of counters.
+constexpr unsigned NOALLOC_SLOTS = 2u * NYX_NOALLOC_MAX_LABELS;  // load factor <= 0.5
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_SLOTS * (8 + sizeof(SlotAcc) + 4) +
+                                 2ull * 4 * NYX_NOALLOC_MAX_BATCH + 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, made once per device with that device current.
+static void* g_noalloc_ptr[64] = {nullptr};
+
+extern "C" nyx_status nyx_count_rois_noalloc(const nyx_params* prm, const void* d_img, const int32_t* d_mask,
+                                             int64_t* n_roi, void* stream) {
+  if (!prm || !d_img || !d_mask || !n_roi) return NYX_ERR_ARG;
+  if (prm->struct_size != sizeof(nyx_params)) return NYX_ERR_ARG;
+  if (((uintptr_t)d_img & 15) || ((uintptr_t)d_mask & 15)) return NYX_ERR_ARG;
+  if (prm->ndim != 2 && prm->ndim != 3) return NYX_ERR_SHAPE;
+  for (int i = 0; i < 3; ++i)
+    if (prm->dims[i] < 1 || prm->dims[i] > (1ll << 31)) return NYX_ERR_SHAPE;
+  if (prm->ndim == 2 && prm->dims[2] != 1) return NYX_ERR_SHAPE;
+  if (prm->batch < 1) return NYX_ERR_SHAPE;
+  if (prm->batch > NYX_NOALLOC_MAX_BATCH) return NYX_ERR_CAPACITY;  // image ranges do not fit the array
+  if (prm->dtype < 0 || prm->dtype > 2) return NYX_ERR_DTYPE;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return NYX_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NYX_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return NYX_ERR_CUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  unsigned char* w = (unsigned char*)g_noalloc_ptr[dev];
+  KParams k;
+  memset(&k, 0, sizeof k);
+  k.img = d_img;
+  k.mask = d_mask;
+  k.nx = prm->dims[0];
+  k.ny = prm->dims[1];
+  k.nz = prm->dims[2];
+  k.batch = prm->batch;
+  k.rows_total = (int64_t)prm->batch * prm->dims[2] * prm->dims[1];
+  k.ndim = prm->ndim;
+  k.dtype = prm->dtype;
+  k.vec = (k.nx % 4) == 0;
+  k.keys = (unsigned long long*)w;
+  k.slots = (SlotAcc*)(w + 8ull * NOALLOC_SLOTS);
+  k.slot_list = (int*)(w + (8ull + sizeof(SlotAcc)) * NOALLOC_SLOTS);
+  k.hmask = NOALLOC_SLOTS - 1;
+  unsigned char* tail = w + (8ull + sizeof(SlotAcc) + 4) * NOALLOC_SLOTS;
+  k.img_vmin = (unsigned*)tail;
+  k.img_vmax = (unsigned*)(tail + 4ull * NYX_NOALLOC_MAX_BATCH);
+  unsigned* small = (unsigned*)(tail + 8ull * NYX_NOALLOC_MAX_BATCH);
+  k.n_used = small + 0;
+  k.n_roi = small + 1;
+  k.err = small + 2;
+  k.qlen = small + 4;
+  k.qhead = small + 8;
+  k.max_rois = NYX_NOALLOC_MAX_LABELS;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: start from an empty table
+  // and zero counters every time
+  if (cudaMemsetAsync(small, 0, 64, st) != cudaSuccess) return NYX_ERR_CUDA;
+  k_init_table<<<2 * nsm, 256, 0, st>>>(k, NOALLOC_SLOTS);
+  if (cudaGetLastError() != cudaSuccess) return NYX_ERR_CUDA;
+  if (launch_front(k, nsm, st) != cudaSuccess) return NYX_ERR_CUDA;
+  unsigned h[3] = {0, 0, 0};  // n_used, n_roi (unused), error word
+  if (cudaMemcpyAsync(h, small, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return NYX_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NYX_ERR_CUDA;
+  if (h[2] & E_BAD_LABEL) return NYX_ERR_BAD_LABEL;
+  if (h[2] & E_NONFINITE) return NYX_ERR_NONFINITE;
+  if ((h[2] & E_HASH_FULL) || h[0] > (unsigned)NYX_NOALLOC_MAX_LABELS) return NYX_ERR_CAPACITY;
+  if (h[2]) return NYX_ERR_STATE;
+  *n_roi = h[0];
+  return NYX_OK;
+}
 }  // namespace nyx

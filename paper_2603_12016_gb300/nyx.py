@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
     L.nyx_debug_select.argtypes = [vp, ctypes.c_int64]
     L.nyx_debug_glcm.argtypes = [vp, ctypes.c_int, vp]
     L.nyx_debug_bins.argtypes = [vp, vp, vp, vp, vp]
+    L.nyx_count_rois_noalloc.argtypes = [P(NyxParams), vp, vp, P(ctypes.c_int64), vp]
+    L.nyx_count_rois_noalloc.restype = ctypes.c_int
     L.nyx_profile_enable.argtypes = [vp, ctypes.c_int]
     L.nyx_phase_times.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), ctypes.c_int]
     for f in ("nyx_params_default", "nyx_create", "nyx_plan_create", "nyx_num_columns", "nyx_column_name",
