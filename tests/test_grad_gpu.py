@@ -1,0 +1,116 @@
+"""Backward pass of the smooth intensity features on the GPU (nyx_backward
+through the C ABI, and FeatureLayer through autograd) against the oracle's
+analytic FP64 gradient and against central finite differences (h = 1e-3) of
+the FP64 oracle forward on sampled pixels; tolerance rel 1e-3."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_12016_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SMOOTH = ["MEAN", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS", "KURTOSIS", "EXCESS_KURTOSIS",
+          "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED", "STANDARD_ERROR", "MEAN_ABSOLUTE_DEVIATION",
+          "INTEGRATED_INTENSITY", "WEIGHTED_CENTROID_X", "WEIGHTED_CENTROID_Y", "WEIGHTED_CENTROID_Z",
+          "MASS_DISPLACEMENT", "COV"]
+FAMILIES = ["INT_M", "INT_MU", "INT_ETA", "INT_NU", "INT_HU"]
+RTOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_12016_gb300 import build
+
+    build.build()
+
+
+def _upstream(cols, table, rng):
+    """Random dL/dF scaled by 1/|F| per column (first-order central moments,
+    identically zero, get no gradient)."""
+    g = np.zeros_like(table)
+    for j, c in enumerate(cols):
+        if c in ("LABEL", "IMAGE", "AREA") or c.startswith("BBOX") or c.startswith("CENTROID"):
+            continue
+        if c in ("INT_MU10", "INT_MU01", "INT_MU100", "INT_MU010", "INT_MU001"):
+            continue
+        col = table[:, j]
+        scale = np.where(np.isfinite(col), np.abs(col), 1.0) + 1e-3
+        g[:, j] = rng.normal(size=len(col)) / scale
+    return g
+
+
+def _check(w, ndim, n_fd=24):
+    from paper_2603_12016_gb300 import nyx
+
+    rng = np.random.default_rng(11)
+    img = torch.from_numpy(w.image).cuda()
+    mask = torch.from_numpy(w.mask).cuda()
+    layer = nyx.FeatureLayer(w.image.shape, ndim=ndim, max_rois=4096, features=SMOOTH + FAMILIES)
+    x = img.clone().requires_grad_(True)
+    table = layer(x, mask)
+    cols = layer.columns
+    tab = table.detach().cpu().numpy()
+    g = _upstream(cols, tab, rng)
+    table.backward(torch.from_numpy(g).cuda())
+    got = x.grad.detach().cpu().numpy().astype(np.float64)
+    gtab = {c: g[:, j] for j, c in enumerate(cols)}
+    ref = oracle.grad(w.image.astype(np.float64), w.mask, ndim, gtab)
+    inroi = w.mask > 0
+    assert np.all(got[~inroi] == 0)
+    # per-ROI scale: the largest reference gradient magnitude in that ROI
+    labels = w.mask.astype(np.int64)
+    if labels.ndim == 3 and ndim == 2:
+        bidx = np.broadcast_to(np.arange(labels.shape[0], dtype=np.int64)[:, None, None], labels.shape)
+    else:
+        bidx = np.zeros_like(labels)
+    keyarr = (bidx << 32) + labels
+    worst = 0.0
+    for k in np.unique(keyarr[labels > 0]):
+        sel = keyarr == k
+        r = ref[sel]
+        err = np.max(np.abs(got[sel] - r)) / (np.max(np.abs(r)) + 1e-30)
+        worst = max(worst, err)
+        assert err <= RTOL, (k >> 32, k & 0xFFFFFFFF, err)
+    # finite differences of the FP64 oracle forward on sampled ROI pixels
+    names = [c for c in cols if np.any(gtab[c] != 0)]
+    img64 = w.image.astype(np.float64)
+
+    def loss(im):
+        t = oracle.extract(im, w.mask, ndim, ng=0)
+        return sum(float(np.sum(gtab[c] * t[c])) for c in names)
+
+    idx = rng.choice(np.flatnonzero(inroi.ravel()), size=n_fd, replace=False)
+    for i in idx:
+        ip, im_ = img64.copy(), img64.copy()
+        ip.flat[i] += 1e-3
+        im_.flat[i] -= 1e-3
+        fd = (loss(ip) - loss(im_)) / 2e-3
+        assert abs(got.flat[i] - fd) <= RTOL * max(abs(fd), 1e-3 * np.max(np.abs(ref))), (i, got.flat[i], fd)
+    return worst
+
+
+def test_backward_blob_batch_f32():
+    w = W.config("blobbatch_small")
+    _check(w, 2)
+
+
+def test_backward_3d_volume_f32():
+    v = W.ct_3d(shape=(16, 40, 40), n_roi=5, seed=99, vol_range=(150, 2000))
+    w = W.Workload("ct_small_f32", v.image.astype(np.float32), v.mask, 3, params=v.params, meta=v.meta)
+    _check(w, 3, n_fd=12)
+
+
+def test_backward_requires_saved_forward():
+    from paper_2603_12016_gb300 import nyx
+
+    ex = nyx.Extractor((16, 16), torch.float32, glcm_levels=0, max_rois=64)
+    img = torch.zeros((16, 16), dtype=torch.float32, device="cuda")
+    mask = torch.ones((16, 16), dtype=torch.int32, device="cuda")
+    ex(img, mask)  # forward without save_for_backward
+    with pytest.raises(nyx.NyxError) as e:
+        ex.backward(img, mask, torch.zeros((64, len(ex.columns)), dtype=torch.float64, device="cuda"))
+    assert e.value.status == 10
