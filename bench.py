@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ROIs/sec and Mpixel/sec full feature set, % HBM roofline vs plain FP64 path"
-PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "reset")
+PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "reset")
 
 
 def _peaks():

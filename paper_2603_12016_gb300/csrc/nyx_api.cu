@@ -20,6 +20,9 @@ namespace nyx {
 cudaError_t launch_roi_u16(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_roi_i16(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_roi_f32(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_big_u16(const KParams& p, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_big_i16(const KParams& p, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_big_f32(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_reset(const KParams& p, int nsm, cudaStream_t st);
@@ -329,7 +332,14 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   const size_t o_keys = take(8ull * hcap), o_slots = take(sizeof(SlotAcc) * hcap), o_slist = take(4ull * hcap),
                o_sdense = take(4ull * hcap), o_sorted = take(8ull * mr), o_rois = take(sizeof(RoiInfo) * mr),
                o_queue = take(4ull * 3 * mr), o_small = take(64), o_imin = take(4ull * p.batch),
-               o_imax = take(4ull * p.batch), o_cmap = take(4ull * Q_TOTAL);
+               o_imax = take(4ull * p.batch), o_cmap = take(4ull * Q_TOTAL), o_big = take(sizeof(BigRoi) * mr),
+               o_bigctr = take(64);
+  // big-ROI arena: the per-ROI regions of the multi-block class (value
+  // histograms, co-occurrence triangles, partial sums, float sort buffers).
+  // Sorting needs 2 words per ROI pixel; the rest is per-ROI bookkeeping.
+  const unsigned long long total_px = (unsigned long long)p.batch * p.dims[0] * p.dims[1] * p.dims[2];
+  const unsigned long long arena_words = 3ull * total_px + (1ull << 24);
+  const size_t o_arena = take(4ull * arena_words);
   cudaError_t e = cudaMalloc(&pl->ws, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -393,6 +403,11 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.qhead = small + 8;
   k.img_vmin = (unsigned*)(w + o_imin);
   k.img_vmax = (unsigned*)(w + o_imax);
+  k.big = (BigRoi*)(w + o_big);
+  k.big_ctr = (unsigned long long*)(w + o_bigctr);
+  k.big_used = k.big_ctr + 1;
+  k.arena = (unsigned*)(w + o_arena);
+  k.arena_cap = arena_words;
   pl->d_col_map = (int*)(w + o_cmap);
   k.col_map = pl->d_col_map;
   k.n_col = (int)pl->col_names.size();
@@ -550,6 +565,16 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
     }
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
     if (prof) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
+  }
+  {
+    cudaError_t e;
+    switch (k.dtype) {
+      case NYX_U16: e = launch_big_u16(k, fp64, c->nsm, st); break;
+      case NYX_I16: e = launch_big_i16(k, fp64, c->nsm, st); break;
+      default: e = launch_big_f32(k, fp64, c->nsm, st); break;
+    }
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
+    if (prof) NYX_CUDA(c, cudaEventRecord(ev[6], st));
   }
   if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
   if (prof) {

@@ -47,6 +47,22 @@ struct RoiInfo {
   int pad;
 };
 
+// Per ROI of the multi-block class (class 3), registered by k_setup.  The
+// ROI's bounding box is cut into chunks of BIG_CHUNK raster cells; pass units
+// are (ROI, chunk), GLCM units (ROI, chunk, offset).  Everything the ROI
+// needs in global memory (counters, histograms, per-offset co-occurrence
+// triangles, per-chunk partial sums, sort buffers) is one region of the big
+// arena starting at word `arena`.
+constexpr int BIG_CHUNK = 65536;
+struct BigRoi {
+  int item;                 // ROI index (output row)
+  int nch;                  // bounding-box chunks
+  unsigned u1;              // first pass unit (prefix over the big ROIs)
+  unsigned range;           // value-histogram words (16-bit order statistics), else 0
+  unsigned long long arena; // word offset of the ROI's arena region
+  double st[10];            // pass-1 scalars: mean (hi, lo), centroids, sum I, energy
+};
+
 // ---------------------------------------------------------------------------
 // output quantity index space.  The host maps each quantity to an output
 // column (or -1) in col_map[].
@@ -138,7 +154,40 @@ struct KParams {
   // class limits (pixels, padded raster cells): 0 warp path, 1 small
   // block path, 2 medium block path
   int lim_pix[3], lim_cells[3];
+  // multi-block class
+  BigRoi* big;                     // [max_rois]
+  unsigned long long* big_ctr;     // (n_big << 32) | n_pass_units
+  unsigned long long* big_used;    // arena words handed out
+  unsigned* arena;
+  unsigned long long arena_cap;    // words
 };
+
+// Word offsets (u32 units) of the parts of one big ROI's arena region.  The
+// prefix [0, zero_end) must be zero when the passes start.
+constexpr int BIG_P1 = 28;   // pass-1 partial per chunk: 9 int64 + 5 doubles
+constexpr int BIG_P2 = 96;   // pass-2 partial per chunk: 48 doubles
+struct BigLayout {
+  unsigned long long ctr, hist, vhist, tri, zero_end, gfeat, part1, part2, fsort, total;
+};
+__host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, unsigned range, unsigned n) {
+  const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
+  const bool glcm = (p.need & NEED_GLCM) != 0;
+  const unsigned long long tri = glcm ? (unsigned long long)p.ng * (p.ng + 1) / 2 : 0;
+  const bool fsort = p.dtype == NYX_F32 && (p.need & NEED_ORDER);
+  BigLayout L;
+  unsigned long long o = 0;
+  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [2] GLCM, [4 + k] offset k
+  L.hist = o;     o = (o + ((p.need & NEED_HIST) ? p.hist_bins : 0) + 3) & ~3ull;
+  L.vhist = o;    o = (o + range + 3) & ~3ull;
+  L.tri = o;      o = (o + (nch > 1 ? n_off * tri : 0) + 3) & ~3ull;
+  L.zero_end = o;
+  L.gfeat = o;    o += glcm ? n_off * 64 : 0;       // 32 doubles per offset
+  L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
+  L.part2 = o;    o += (unsigned long long)nch * BIG_P2;
+  L.fsort = o;    o += fsort ? 2ull * n : 0;
+  L.total = (o + 3) & ~3ull;
+  return L;
+}
 
 // ---------------------------------------------------------------------------
 // order-preserving encodings of pixel values

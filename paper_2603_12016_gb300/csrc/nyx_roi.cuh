@@ -714,6 +714,94 @@ __device__ inline unsigned bin_float(float x, float mn, float mx, int nb) {
   return min(b, (unsigned)(nb - 1));
 }
 
+// Order statistics of Table S1 from the sorted encoded values v[0..n) (in
+// shared or global memory): percentiles, mode (longest run, ties to the
+// smallest value), robust mean and mean absolute deviation over [P10, P90],
+// and the mean absolute deviation from the median.  Called by every thread of
+// the block; uses s_sc[4..6] and s_sc[10..11].
+template <class T, class C, class A>
+__device__ inline void order_tail(const KParams& p, double* row, const unsigned* v, int n, double* red,
+                                  double* s_sd, int* s_idx, A* s_sc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const A nan = anan<A>();
+  const int ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
+  if (warp == 0) finalize_percentiles<T>(p, row, v, n, s_sd, s_idx);
+  __syncthreads();
+  // mode: longest run of equal values, ties -> smallest value.  Each
+  // thread owns a contiguous segment; runs entering a segment get their
+  // start from an exclusive max-scan of the previous segments.
+  const int per_t = (n + C::NT - 1) / C::NT;
+  const int s0 = min(n, tid * per_t), s1 = min(n, s0 + per_t);
+  int last_start = -1;
+  for (int i = s0; i < s1; ++i)
+    if (i == 0 || v[i] != v[i - 1]) last_start = i;
+  {
+    int* sc = (int*)red;
+    sc[tid] = last_start;
+    __syncthreads();
+    if (warp == 0) {  // exclusive max-scan over the C::NT entries
+      int carry = -1;
+      for (int base = 0; base < C::NT; base += 32) {
+        const int x = sc[base + lane];
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+          if (lane >= o) incl = max(incl, y);
+        }
+        const int prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);  // every lane executes the shuffle
+        const int excl = lane == 0 ? carry : max(carry, prev);
+        sc[base + lane] = excl;
+        carry = max(carry, __shfl_sync(0xFFFFFFFFu, incl, 31));
+      }
+    }
+    __syncthreads();
+    last_start = sc[tid];
+    __syncthreads();
+  }
+  unsigned long long best = 0;  // (length << 32) | ~value: max = longest, then smallest
+  int start = last_start;
+  for (int i = s0; i < s1; ++i) {
+    if (i == 0 || v[i] != v[i - 1]) start = i;
+    if (i == n - 1 || v[i] != v[i + 1]) {
+      const unsigned long long cand = ((unsigned long long)(i - start + 1) << 32) | (unsigned)(~v[i]);
+      if (cand > best) best = cand;
+    }
+  }
+  best = block_max_u64<C>(best, red);
+  // robust mean over [P10, P90], mean absolute deviation from the median
+  const int i10 = s_idx[0], i90 = s_idx[1];
+  if (tid == 0) s_sc[10] = (A)s_sd[0];  // median in the accumulation type
+  __syncthreads();
+  const A medA = s_sc[10];
+  A rv[2] = {0, 0};
+  for (int i = tid; i < n; i += C::NT) {
+    const A x = decA<T, A>(v[i]);
+    if (i >= i10 && i < i90) rv[0] += x;
+    rv[1] += x > medA ? x - medA : medA - x;
+  }
+  block_sum<C, A, 2>(rv, red, s_sc + 4);
+  const int cntV = i90 - i10;
+  if (tid == 0) s_sc[11] = cntV > 0 ? s_sc[4] / (A)cntV : nan;
+  __syncthreads();
+  const A rmA = s_sc[11];
+  A ra[1] = {0};
+  for (int i = i10 + tid; i < i90; i += C::NT) {
+    const A x = decA<T, A>(v[i]);
+    ra[0] += x > rmA ? x - rmA : rmA - x;
+  }
+  block_sum<C, A, 1>(ra, red, s_sc + 6);
+  if (tid == 0) {
+    const unsigned mode_e = ~(unsigned)(best & 0xFFFFFFFFu);
+    if (Enc<T>::INTEGER) put(p, row, Q_STATS + S_MODE, i2d((long long)mode_e - ibias));
+    else put(p, row, Q_STATS + S_MODE, f2d(Enc<T>::decf(mode_e)));
+    putA(p, row, Q_STATS + S_MODE_PROB, (A)(int)(best >> 32) / (A)n);
+    putA(p, row, Q_STATS + S_RMEAN, rmA);
+    putA(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[6] / (A)cntV : nan);
+    putA(p, row, Q_STATS + S_MEDAD, s_sc[5] / (A)n);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // the kernel
 
@@ -1321,81 +1409,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         dst = t;
       }
       const unsigned* v = src;  // sorted, ascending
-      if (warp == 0) finalize_percentiles<T>(p, row, v, n, s_sd, s_idx);
-      __syncthreads();
-      // mode: longest run of equal values, ties -> smallest value.  Each
-      // thread owns a contiguous segment; runs entering a segment get their
-      // start from an exclusive max-scan of the previous segments.
-      const int per_t = (n + C::NT - 1) / C::NT;
-      const int s0 = min(n, tid * per_t), s1 = min(n, s0 + per_t);
-      int last_start = -1;
-      for (int i = s0; i < s1; ++i)
-        if (i == 0 || v[i] != v[i - 1]) last_start = i;
-      {
-        int* sc = (int*)red;
-        sc[tid] = last_start;
-        __syncthreads();
-        if (warp == 0) {  // exclusive max-scan over the C::NT entries
-          int carry = -1;
-          for (int base = 0; base < C::NT; base += 32) {
-            const int x = sc[base + lane];
-            int incl = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-              if (lane >= o) incl = max(incl, y);
-            }
-            const int prev = __shfl_up_sync(0xFFFFFFFFu, incl, 1);  // every lane executes the shuffle
-            const int excl = lane == 0 ? carry : max(carry, prev);
-            sc[base + lane] = excl;
-            carry = max(carry, __shfl_sync(0xFFFFFFFFu, incl, 31));
-          }
-        }
-        __syncthreads();
-        last_start = sc[tid];
-        __syncthreads();
-      }
-      unsigned long long best = 0;  // (length << 32) | ~value: max = longest, then smallest
-      int start = last_start;
-      for (int i = s0; i < s1; ++i) {
-        if (i == 0 || v[i] != v[i - 1]) start = i;
-        if (i == n - 1 || v[i] != v[i + 1]) {
-          const unsigned long long cand = ((unsigned long long)(i - start + 1) << 32) | (unsigned)(~v[i]);
-          if (cand > best) best = cand;
-        }
-      }
-      best = block_max_u64<C>(best, red);
-      // robust mean over [P10, P90], mean absolute deviation from the median
-      const int i10 = s_idx[0], i90 = s_idx[1];
-      if (tid == 0) s_sc[10] = (A)s_sd[0];  // median in the accumulation type
-      __syncthreads();
-      const A medA = s_sc[10];
-      A rv[2] = {0, 0};
-      for (int i = tid; i < n; i += C::NT) {
-        const A x = decA<T, A>(v[i]);
-        if (i >= i10 && i < i90) rv[0] += x;
-        rv[1] += x > medA ? x - medA : medA - x;
-      }
-      block_sum<C, A, 2>(rv, red, s_sc + 4);
-      const int cntV = i90 - i10;
-      if (tid == 0) s_sc[11] = cntV > 0 ? s_sc[4] / (A)cntV : nan;
-      __syncthreads();
-      const A rmA = s_sc[11];
-      A ra[1] = {0};
-      for (int i = i10 + tid; i < i90; i += C::NT) {
-        const A x = decA<T, A>(v[i]);
-        ra[0] += x > rmA ? x - rmA : rmA - x;
-      }
-      block_sum<C, A, 1>(ra, red, s_sc + 6);
-      if (tid == 0) {
-        const unsigned mode_e = ~(unsigned)(best & 0xFFFFFFFFu);
-        if (Enc<T>::INTEGER) put(p, row, Q_STATS + S_MODE, i2d((long long)mode_e - ibias));
-        else put(p, row, Q_STATS + S_MODE, f2d(Enc<T>::decf(mode_e)));
-        putA(p, row, Q_STATS + S_MODE_PROB, (A)(int)(best >> 32) / (A)n);
-        putA(p, row, Q_STATS + S_RMEAN, rmA);
-        putA(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[6] / (A)cntV : nan);
-        putA(p, row, Q_STATS + S_MEDAD, s_sc[5] / (A)n);
-      }
+      order_tail<T, C, A>(p, row, v, n, red, s_sd, s_idx, s_sc);
     }
     __syncthreads();
   }

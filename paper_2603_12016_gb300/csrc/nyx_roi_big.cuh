@@ -1,0 +1,961 @@
+// nyx_roi_big.cuh -- the multi-block path (class 3) for ROIs beyond the
+// single-block classes (more pixels or bounding-box cells than a block stages
+// in shared memory, up to ~1e6-voxel ROIs).  Included by nyx_big_<dtype>.cu;
+// reuses the finalisers of nyx_roi.cuh so both paths compute every feature
+// with the same arithmetic.
+//
+// The bounding box of a big ROI is cut into chunks of BIG_CHUNK raster
+// cells.  Each kernel streams chunk cells straight from global memory (the
+// image and mask are L2-resident after the label scan for all but the largest
+// inputs), with one 512-thread block per unit:
+//   k_big_zero   clear each big ROI's counters and histograms
+//   k_big_p1     units (ROI, chunk): exact pass-1 sums (int64 for integer
+//                images, Kahan-compensated otherwise), the hist_bins
+//                histogram, and for 16-bit images the value histogram over
+//                [min, max]; the last unit of an ROI merges the per-chunk
+//                partials in chunk order and derives the mean, centroids,
+//                histogram features and the order statistics
+//   k_big_p2     units (ROI, chunk): centred power sums and central moments
+//                (Kahan per thread, compensated across the block); the last
+//                unit merges and finalises statistics and moments
+//   k_big_glcm   units (ROI, chunk, offset): a dense upper-triangular
+//                co-occurrence matrix in shared memory (Ng(Ng+1)/2 counts,
+//                diagonal counted twice); multi-chunk ROIs add it into a
+//                global triangle and the last chunk of the offset computes
+//                the features; the last offset forms the direction means
+//   k_big_order_f  float images: one block per ROI compacts the values in
+//                raster order and sorts them (LSD radix, global memory)
+// "Last unit" is decided with a counter in the ROI's arena region after a
+// __threadfence, and every merge runs in chunk order, so results do not
+// depend on which block ran which unit.
+#pragma once
+
+#include "nyx_roi.cuh"
+
+namespace nyx {
+
+constexpr int BIG_NT = 512;
+constexpr int VH_SMEM = 8192;  // value-histogram words kept in shared memory per chunk
+using ClassBig = RoiClass<BIG_NT, 1, 1>;  // thread geometry for the block reductions
+
+// the big ROI owning pass unit u (u1 grows with the big-ROI index)
+__device__ inline int big_of_unit(const KParams& p, int n_big, unsigned u) {
+  int lo = 0, hi = n_big - 1;
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    if (p.big[m].u1 <= u) lo = m;
+    else hi = m - 1;
+  }
+  return lo;
+}
+
+// Kahan-compensated running sum (per thread)
+template <class A>
+struct KSum {
+  A s, c;
+  __device__ KSum() : s(0), c(0) {}
+  __device__ void add(A x) {
+    const A y = x - c;
+    const A t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// block sum of Kahan pairs: sums and negated corrections reduced separately
+// (each compensated), then added; out[] in shared memory for every thread
+template <class C, class A, int NV>
+__device__ inline void block_sum_k(KSum<A> (&v)[NV], double* scratch, A* out) {
+  A hi[NV], lo[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    hi[i] = v[i].s;
+    lo[i] = -v[i].c;
+  }
+  block_sum<C, A, NV>(lo, scratch, out);
+  A lo_i = 0;
+  if (threadIdx.x < NV) lo_i = out[threadIdx.x];
+  __syncthreads();
+  block_sum<C, A, NV>(hi, scratch, out);
+  if (threadIdx.x < NV) out[threadIdx.x] += lo_i;
+  __syncthreads();
+}
+
+// Bounding box of one big ROI and the cell -> (x, y, z) decomposition.
+struct BigBox {
+  int W, H, D;
+  unsigned cells;
+  FastDiv dw, dh;
+  int64_t origin;  // linear index of the box origin in the image batch
+  int label;
+  __device__ void init(const KParams& p, const RoiInfo& r, int ndim) {
+    W = r.w;
+    H = r.h;
+    D = ndim == 3 ? r.d : 1;
+    cells = (unsigned)W * (unsigned)H * (unsigned)D;
+    dw.init((unsigned)W);
+    dh.init((unsigned)H);
+    const int64_t per = p.nx * p.ny * p.nz;
+    origin = (int64_t)(r.key >> 32) * per + ((int64_t)r.z0 * p.ny + r.y0) * p.nx + r.x0;
+    label = (int)(r.key & 0xFFFFFFFFu);
+  }
+  __device__ int64_t offset(unsigned c, int& x, int& y, int& z, const KParams& p) const {
+    const unsigned zy = dw.div(c);
+    x = (int)(c - zy * (unsigned)W);
+    const unsigned zz = dh.div(zy);
+    y = (int)(zy - zz * (unsigned)H);
+    z = (int)zz;
+    return origin + ((int64_t)z * p.ny + y) * p.nx + x;
+  }
+};
+
+// Visit the ROI pixels of cells [c0, c1): f(x, y, z, encoded value).
+template <class T, class F>
+__device__ inline void chunk_pixels(const KParams& p, const BigBox& bx, unsigned c0, unsigned c1, F f) {
+  const T* img = (const T*)p.img;
+#pragma unroll 1
+  for (unsigned c = c0 + threadIdx.x; c < c1; c += BIG_NT) {
+    int x, y, z;
+    const int64_t off = bx.offset(c, x, y, z, p);
+    if (__ldg(p.mask + off) != bx.label) continue;
+    f(x, y, z, Enc<T>::enc(__ldg(img + off)));
+  }
+}
+
+// true in every thread of the one block that finishes last among `total`
+// (counter in global memory; the caller's global writes are fenced first)
+__device__ inline bool last_arrival(unsigned* counter, unsigned total, int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_flag = atomicAdd(counter, 1u) == total - 1;
+  __syncthreads();
+  const bool last = *s_flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// ---------------------------------------------------------------------------
+
+template <class T>  // (templated so each dtype's translation unit owns its copy)
+__global__ void __launch_bounds__(BIG_NT) k_big_zero(KParams p) {
+  const int n_big = (int)(*p.big_ctr >> 32);
+  for (int b = blockIdx.x; b < n_big; b += gridDim.x) {
+    const BigRoi br = p.big[b];
+    const RoiInfo r = p.rois[br.item];
+    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    uint4* z = (uint4*)(p.arena + br.arena);
+    const unsigned long long n4 = L.zero_end / 4;
+    for (unsigned long long i = threadIdx.x; i < n4; i += BIG_NT) z[i] = make_uint4(0, 0, 0, 0);
+  }
+}
+
+// Percentiles, mode, robust mean / MAD and median MAD of a 16-bit ROI from its
+// value histogram h[0..range) (bin k = encoded value vmin + k).  Every thread
+// of the block calls it.  The percentile arithmetic is the FP64 definition
+// on the two order statistics around h = (n-1) q, as in finalize_percentiles.
+template <class T, class A>
+__device__ void hist_order_stats(const KParams& p, double* row, const unsigned* h, unsigned range, unsigned vmin,
+                                 int n, double* red, A* s_sc) {
+  using C = ClassBig;
+  const int tid = threadIdx.x;
+  const long long ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
+  const A nan = anan<A>();
+  __shared__ long long s_rank[14], s_val[14];
+  __shared__ long long s_thr[3];
+  __shared__ unsigned long long s_best;
+  __shared__ long long s_iv[3];
+  if (tid < 14) {
+    const double qs[7] = {0.01, 0.10, 0.25, 0.50, 0.75, 0.90, 0.99};
+    const double hq = __dmul_rn((double)(n - 1), qs[tid >> 1]);
+    const long long rk = (long long)floor(hq) + (tid & 1);
+    s_rank[tid] = rk > n - 1 ? n - 1 : rk;
+  }
+  const unsigned seg = (range + BIG_NT - 1) / BIG_NT;
+  const unsigned b0 = min(range, tid * seg), b1 = min(range, b0 + seg);
+  unsigned segtot = 0;
+  unsigned long long best = 0;  // (count << 32) | ~bin: most frequent, then smallest value
+  for (unsigned k = b0; k < b1; ++k) {
+    const unsigned c = __ldcg(h + k);
+    segtot += c;
+    const unsigned long long cand = ((unsigned long long)c << 32) | (unsigned)~k;
+    if (c && cand > best) best = cand;
+  }
+  unsigned* scan = (unsigned*)red;
+  scan[tid] = segtot;
+  __syncthreads();
+  if (tid < 32) warp_exclusive_scan(scan, BIG_NT);
+  __syncthreads();
+  const unsigned long long segbase = scan[tid];
+  __syncthreads();
+  best = block_max_u64<C>(best, red);
+  for (int k = 0; k < 14; ++k) {
+    const unsigned long long rk = (unsigned long long)s_rank[k];
+    if (rk >= segbase && rk < segbase + segtot) {
+      unsigned long long acc = segbase;
+      for (unsigned q = b0; q < b1; ++q) {
+        acc += __ldcg(h + q);
+        if (rk < acc) {
+          s_val[k] = (long long)(vmin + q) - ibias;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double qs[7] = {0.01, 0.10, 0.25, 0.50, 0.75, 0.90, 0.99};
+    const int qcol[7] = {S_P01, S_P10, S_P25, S_MEDIAN, S_P75, S_P90, S_P99};
+    double pv_[7];
+    for (int k = 0; k < 7; ++k) {
+      const double hq = __dmul_rn((double)(n - 1), qs[k]);
+      const long long lo = (long long)floor(hq);
+      const double a = (double)s_val[2 * k], b = (double)s_val[2 * k + 1];
+      pv_[k] = lo >= n - 1 ? a : __dadd_rn(a, __dmul_rn(__dsub_rn(hq, (double)lo), __dsub_rn(b, a)));
+      put(p, row, Q_STATS + qcol[k], pv_[k]);
+    }
+    put(p, row, Q_STATS + S_IQR, __dsub_rn(pv_[4], pv_[2]));
+    const float qa = (float)pv_[4], qb = (float)pv_[2];
+    put(p, row, Q_STATS + S_QCOD, (qa + qb) != 0.f ? f2d((qa - qb) / (qa + qb)) : f2d(__int_as_float(0x7FC00000)));
+    s_thr[0] = (long long)ceil(pv_[1]);    // values >= P10
+    s_thr[1] = (long long)floor(pv_[5]);   // values <= P90
+    s_thr[2] = (long long)(2.0 * pv_[3]);  // twice the median: an integer (h - floor(h) is 0 or 1/2)
+    s_best = best;
+  }
+  __syncthreads();
+  const long long t10 = s_thr[0], t90 = s_thr[1], med2 = s_thr[2];
+  // exact integer sums: [0] sum c v over [P10, P90], [1] count there, [2] sum c |2v - 2 median|
+  long long iv[3] = {0, 0, 0};
+  for (unsigned k = b0; k < b1; ++k) {
+    const unsigned c = __ldcg(h + k);
+    if (!c) continue;
+    const long long v = (long long)(vmin + k) - ibias;
+    if (v >= t10 && v <= t90) {
+      iv[0] += (long long)c * v;
+      iv[1] += c;
+    }
+    const long long d2 = 2 * v - med2;
+    iv[2] += (long long)c * (d2 < 0 ? -d2 : d2);
+  }
+  block_sum_i64<C, 3>(iv, red, s_iv);
+  const long long cntV = s_iv[1];
+  const A rmA = cntV > 0 ? (A)s_iv[0] / (A)cntV : nan;
+  KSum<A> ra[1];
+  for (unsigned k = b0; k < b1; ++k) {
+    const unsigned c = __ldcg(h + k);
+    if (!c) continue;
+    const long long v = (long long)(vmin + k) - ibias;
+    if (v < t10 || v > t90) continue;
+    const A vA = (A)v;
+    ra[0].add((A)c * (vA > rmA ? vA - rmA : rmA - vA));
+  }
+  block_sum_k<C, A, 1>(ra, red, s_sc + 12);
+  if (tid == 0) {
+    const unsigned long long bb = s_best;
+    put(p, row, Q_STATS + S_MODE, i2d((long long)(vmin + ~(unsigned)(bb & 0xFFFFFFFFu)) - ibias));
+    putA(p, row, Q_STATS + S_MODE_PROB, (A)(int)(bb >> 32) / (A)n);
+    putA(p, row, Q_STATS + S_RMEAN, rmA);
+    putA(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[12] / (A)cntV : nan);
+    putA(p, row, Q_STATS + S_MEDAD, (A)s_iv[2] / ((A)2 * (A)n));
+  }
+  __syncthreads();
+}
+
+template <class T, int NDIM, class A>
+__global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
+  using C = ClassBig;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned* hist = (unsigned*)smem;                // [hist_bins]
+  unsigned* vh = hist + ((p.hist_bins + 3) & ~3);  // [VH_SMEM]
+  __shared__ double red[C::NW * RED_MAX];
+  __shared__ long long s_i64[16];
+  __shared__ A s_sc[16];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  const unsigned long long ctr = *p.big_ctr;
+  const int n_big = (int)(ctr >> 32);
+  const unsigned n_units = (unsigned)ctr;
+  const unsigned need = p.need;
+  constexpr bool integer = Enc<T>::INTEGER;
+  const long long ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
+  for (unsigned u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int b = big_of_unit(p, n_big, u);
+    const BigRoi br = p.big[b];
+    const int chunk = (int)(u - br.u1);
+    const RoiInfo r = p.rois[br.item];
+    BigBox bx;
+    bx.init(p, r, NDIM);
+    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    unsigned* reg = p.arena + br.arena;
+    const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
+    const unsigned vmin = r.vmin, vmax = r.vmax;
+    const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
+    const bool do_hist = (need & NEED_HIST) != 0;
+    const unsigned range = br.range;
+    const bool vh_smem = range > 0 && range <= (unsigned)VH_SMEM;
+    FastDiv fd;
+    fd.init(vmax > vmin ? vmax - vmin : 1u);
+    if (do_hist)
+      for (int i = tid; i < p.hist_bins; i += BIG_NT) hist[i] = 0;
+    if (vh_smem)
+      for (unsigned i = tid; i < range; i += BIG_NT) vh[i] = 0;
+    __syncthreads();
+    // [0] sum I, [1] sum x I, [2] sum y I, [3] sum z I, [4] sum x, [5] sum y, [6] sum z, [7] sum I^2, [8] count
+    long long s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    KSum<A> fs[5];  // float images: sum I, x I, y I, z I, I^2
+    unsigned* gvh = reg + L.vhist;
+    chunk_pixels<T>(p, bx, c0, c1, [&](int x, int y, int z, unsigned e) {
+      s[4] += x;
+      s[5] += y;
+      s[6] += z;
+      s[8] += 1;
+      if constexpr (integer) {
+        const long long v = (long long)e - ibias;
+        s[0] += v;
+        s[1] += x * v;
+        s[2] += y * v;
+        s[3] += z * v;
+        s[7] += v * v;
+      } else {
+        const A v = decA<T, A>(e);
+        fs[0].add(v);
+        fs[1].add((A)x * v);
+        fs[2].add((A)y * v);
+        fs[3].add((A)z * v);
+        fs[4].add(v * v);
+      }
+      if (do_hist) {
+        unsigned hb = 0;
+        if (vmax > vmin) {
+          if constexpr (integer) hb = min(fd.div((unsigned)p.hist_bins * (e - vmin)), (unsigned)(p.hist_bins - 1));
+          else hb = bin_float(Enc<T>::decf(e), fmn, fmx, p.hist_bins);
+        }
+        atomicAdd(&hist[hb], 1u);
+      }
+      if (range) {
+        if (vh_smem) atomicAdd(&vh[e - vmin], 1u);
+        else atomicAdd(&gvh[e - vmin], 1u);
+      }
+    });
+    block_sum_i64<C, 9>(s, red, s_i64);
+    if constexpr (!integer) block_sum_k<C, A, 5>(fs, red, s_sc);
+    if (do_hist)
+      for (int i = tid; i < p.hist_bins; i += BIG_NT)
+        if (hist[i]) atomicAdd(reg + L.hist + i, hist[i]);
+    if (vh_smem)
+      for (unsigned i = tid; i < range; i += BIG_NT)
+        if (vh[i]) atomicAdd(gvh + i, vh[i]);
+    if (tid == 0) {
+      long long* pt = (long long*)(reg + L.part1) + (size_t)chunk * (BIG_P1 / 2);
+      for (int k = 0; k < 9; ++k) pt[k] = s_i64[k];
+      double* pf = (double*)(pt + 9);
+      for (int k = 0; k < 5; ++k) pf[k] = integer ? 0.0 : to_d(s_sc[k]);
+    }
+    if (!last_arrival(reg + L.ctr + 0, (unsigned)br.nch, &s_flag)) continue;
+
+    // ---- last chunk of this ROI: merge in chunk order, per-ROI scalars ----
+    const int n = (int)r.n;
+    double* row = p.table + (int64_t)br.item * p.n_col;
+    const int64_t bimg = (int64_t)(r.key >> 32);
+    if (tid == 0) {
+      long long t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      A fh[5] = {0, 0, 0, 0, 0}, fl[5] = {0, 0, 0, 0, 0};
+      for (int ch = 0; ch < br.nch; ++ch) {
+        const long long* pt = (const long long*)(reg + L.part1) + (size_t)ch * (BIG_P1 / 2);
+        for (int k = 0; k < 9; ++k) t[k] += __ldcg(pt + k);
+        if constexpr (!integer) {
+          const double* pf = (const double*)(pt + 9);
+          for (int k = 0; k < 5; ++k) {
+            const A x = (A)__ldcg(pf + k);
+            if constexpr (std::is_same<A, float>::value) {
+              float sum, err;
+              two_sum(fh[k], x, sum, err);
+              fh[k] = sum;
+              fl[k] += err;
+            } else {
+              fh[k] += x;
+            }
+          }
+        }
+      }
+      if (t[8] != (long long)n) atomicOr(p.err, E_INTERNAL);
+      const A nA = (A)n;
+      A sI, sxI, syI, szI, en, mhi, mlo;
+      if constexpr (integer) {
+        const long long si = t[0];
+        sI = (A)si;
+        sxI = (A)t[1];
+        syI = (A)t[2];
+        szI = (A)t[3];
+        en = (A)t[7];
+        if constexpr (std::is_same<A, float>::value) {
+          const long long q = si / n, rm = si - q * n;  // mean = q + rm / n exactly
+          mhi = (A)q;
+          mlo = (A)rm / nA;
+        } else {
+          mhi = (A)si / nA;
+          mlo = 0;
+        }
+        put(p, row, Q_STATS + S_II, i2d(si));
+        put(p, row, Q_STATS + S_ENERGY, i2d(t[7]));
+      } else {
+        sI = fh[0] + fl[0];
+        sxI = fh[1] + fl[1];
+        syI = fh[2] + fl[2];
+        szI = fh[3] + fl[3];
+        en = fh[4] + fl[4];
+        mhi = sI / nA;
+        mlo = 0;
+        putA(p, row, Q_STATS + S_II, sI);
+        putA(p, row, Q_STATS + S_ENERGY, en);
+      }
+      const A bx_ = (A)t[4] / nA, by_ = (A)t[5] / nA, bz_ = (A)t[6] / nA;
+      const bool wv = sI != 0;
+      double* st = p.big[b].st;
+      st[0] = to_d(mhi);
+      st[1] = to_d(mlo);
+      st[2] = to_d(wv ? sxI / sI : bx_);
+      st[3] = to_d(wv ? syI / sI : by_);
+      st[4] = to_d(wv ? szI / sI : bz_);
+      st[5] = to_d(bx_);
+      st[6] = to_d(by_);
+      st[7] = to_d(bz_);
+      st[8] = to_d(sI);
+      st[9] = to_d(en);
+      put(p, row, Q_LABEL, i2d(bx.label));
+      put(p, row, Q_IMAGE, i2d(bimg));
+      put(p, row, Q_AREA, i2d(n));
+      put(p, row, Q_BB_X, i2d(r.x0));
+      put(p, row, Q_BB_Y, i2d(r.y0));
+      put(p, row, Q_BB_Z, i2d(r.z0));
+      put(p, row, Q_BB_W, i2d(bx.W));
+      put(p, row, Q_BB_H, i2d(bx.H));
+      put(p, row, Q_BB_D, i2d(bx.D));
+      if constexpr (integer) {
+        put(p, row, Q_STATS + S_MIN, i2d((long long)vmin - ibias));
+        put(p, row, Q_STATS + S_MAX, i2d((long long)vmax - ibias));
+        put(p, row, Q_STATS + S_RANGE, i2d((long long)vmax - (long long)vmin));
+      } else {
+        put(p, row, Q_STATS + S_MIN, f2d(fmn));
+        put(p, row, Q_STATS + S_MAX, f2d(fmx));
+        put(p, row, Q_STATS + S_RANGE, __dsub_rn(f2d(fmx), f2d(fmn)));
+      }
+    }
+    // histogram features
+    if (do_hist) {
+      A hv[2] = {0, 0};
+      const A inv = (A)1 / (A)n;
+      for (int i = tid; i < p.hist_bins; i += BIG_NT) {
+        const unsigned hc = __ldcg(reg + L.hist + i);
+        if (hc) {
+          const A pr = (A)hc * inv;
+          hv[0] -= pr * alog2(pr);
+          hv[1] += pr * pr;
+        }
+      }
+      block_sum<C, A, 2>(hv, red, s_sc + 8);
+      if (tid == 0) {
+        putA(p, row, Q_STATS + S_ENTROPY, s_sc[8]);
+        putA(p, row, Q_STATS + S_UNIFORMITY, s_sc[9]);
+      }
+    }
+    if (range) hist_order_stats<T, A>(p, row, gvh, range, vmin, n, red, s_sc);
+    __syncthreads();
+  }
+}
+
+template <class T, int NDIM, class A>
+__global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
+  using C = ClassBig;
+  constexpr int NM = NDIM == 3 ? 20 : 10;
+  constexpr int NV = 8 + 2 * NM;
+  __shared__ double red[C::NW * RED_MAX];
+  __shared__ A res[NV + 16];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const unsigned long long ctr = *p.big_ctr;
+  const int n_big = (int)(ctr >> 32);
+  const unsigned n_units = (unsigned)ctr;
+  const unsigned need = p.need;
+  const long long ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
+  const bool do_st = (need & (NEED_STATS | NEED_SAVE)) != 0;
+  const bool do_mi = (need & (NEED_MOM_INT | NEED_SAVE)) != 0;
+  const bool do_mb = (need & NEED_MOM_BIN) != 0;
+  for (unsigned u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int b = big_of_unit(p, n_big, u);
+    const BigRoi br = p.big[b];
+    const int chunk = (int)(u - br.u1);
+    const RoiInfo r = p.rois[br.item];
+    BigBox bx;
+    bx.init(p, r, NDIM);
+    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    unsigned* reg = p.arena + br.arena;
+    const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
+    const double* st = p.big[b].st;
+    const A mu_hi = (A)__ldcg(st + 0), mu_lo = (A)__ldcg(st + 1);
+    const A cx = (A)__ldcg(st + 2), cy = (A)__ldcg(st + 3), cz = (A)__ldcg(st + 4);
+    const A bcx = (A)__ldcg(st + 5), bcy = (A)__ldcg(st + 6), bcz = (A)__ldcg(st + 7);
+    double* part = (double*)(reg + L.part2) + (size_t)chunk * (BIG_P2 / 2);
+    if (do_st) {
+      KSum<A> acc[8];
+      chunk_pixels<T>(p, bx, c0, c1, [&](int, int, int, unsigned e) {
+        const A v = Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e);
+        const A d = (v - mu_hi) - mu_lo;
+        const A d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
+        acc[0].add(d);
+        acc[1].add(d2);
+        acc[2].add(d3);
+        acc[3].add(d4);
+        acc[4].add(d4 * d);
+        acc[5].add(d3 * d3);
+        acc[6].add(d < 0 ? -d : d);
+        acc[7].add(d > 0 ? (A)1 : (d < 0 ? (A)-1 : (A)0));
+      });
+      block_sum_k<C, A, 8>(acc, red, res);
+      if (tid < 8) part[tid] = to_d(res[tid]);
+      __syncthreads();
+    } else if (tid < 8) {
+      part[tid] = 0.0;  // unselected group: defined zeros for the merge
+    }
+#pragma unroll 1
+    for (int w = 0; w < 2; ++w) {
+      if (!(w ? do_mb : do_mi)) {
+        if (tid < NM) part[8 + w * NM + tid] = 0.0;
+        continue;
+      }
+      KSum<A> acc[NM];
+      const A k0 = w ? bcx : cx, k1 = w ? bcy : cy, k2 = w ? bcz : cz;
+      chunk_pixels<T>(p, bx, c0, c1, [&](int x, int y, int z, unsigned e) {
+        const A u0 = (A)x - k0, u1 = (A)y - k1, u2 = (A)z - k2;
+        const A wt = w ? (A)1 : (Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e));
+        A px[4], py[4], pz[4];
+        px[0] = wt;
+        py[0] = pz[0] = 1;
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+          px[q] = px[q - 1] * u0;
+          py[q] = py[q - 1] * u1;
+          pz[q] = pz[q - 1] * u2;
+        }
+#pragma unroll
+        for (int a = 0; a <= 3; ++a)
+#pragma unroll
+          for (int bb = 0; a + bb <= 3; ++bb)
+#pragma unroll
+            for (int cc = 0; cc <= (NDIM == 3 ? 3 - a - bb : 0); ++cc)
+              acc[midx<NDIM>(a, bb, cc)].add(px[a] * py[bb] * pz[cc]);
+      });
+      block_sum_k<C, A, NM>(acc, red, res);
+      if (tid < NM) part[8 + w * NM + tid] = to_d(res[tid]);
+      __syncthreads();
+    }
+    if (!last_arrival(reg + L.ctr + 1, (unsigned)br.nch, &s_flag)) continue;
+
+    // ---- last chunk: merge the partials in chunk order, finalise ----------
+    if (tid < NV) {
+      A hi = 0, lo = 0;
+      for (int ch = 0; ch < br.nch; ++ch) {
+        const A x = (A)__ldcg((const double*)(reg + L.part2) + (size_t)ch * (BIG_P2 / 2) + tid);
+        if constexpr (std::is_same<A, float>::value) {
+          float sum, err;
+          two_sum(hi, x, sum, err);
+          hi = sum;
+          lo += err;
+        } else {
+          hi += x;
+        }
+      }
+      res[tid] = hi + lo;
+    }
+    __syncthreads();
+    const int n = (int)r.n;
+    double* row = p.table + (int64_t)br.item * p.n_col;
+    const int64_t bimg = (int64_t)(r.key >> 32);
+    const A sumI = (A)__ldcg(st + 8), energy = (A)__ldcg(st + 9);
+    const bool wvalid = sumI != 0;
+    double* save = (need & NEED_SAVE) ? p.saved + (int64_t)br.item * SV_WORDS : nullptr;
+    if (tid == 0)  // also writes the centroid columns
+      finalize_stats<T, NDIM, A>(p, row, res, n, mu_hi + mu_lo, sumI, energy, r.vmin, r.vmax, bimg, r.x0, r.y0, r.z0,
+                                 cx, cy, cz, bcx, bcy, bcz, wvalid, save);
+    if (warp == 1 && do_mi)
+      finalize_moments_warp<NDIM, A>(p, row, 0, res + 8, cx, cy, cz, wvalid, save ? save + SV_MU : nullptr);
+    if (warp == 2 && do_mb) finalize_moments_warp<NDIM, A>(p, row, 5, res + 8 + NM, bcx, bcy, bcz, true, nullptr);
+    __syncthreads();
+  }
+}
+
+// cell (a, b), a <= b, of the upper-triangular co-occurrence matrix
+__device__ inline unsigned tri_idx(unsigned a, unsigned b) { return b * (b + 1) / 2 + a; }
+__device__ inline void tri_ab(unsigned f, unsigned& a, unsigned& b) {
+  unsigned r = (unsigned)((sqrtf(8.f * (float)f + 1.f) - 1.f) * 0.5f);
+  while (r * (r + 1) / 2 > f) --r;
+  while ((r + 1) * (r + 2) / 2 <= f) ++r;
+  b = r;
+  a = f - r * (r + 1) / 2;
+}
+
+template <class T, int NDIM, class A>
+__global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
+  using C = ClassBig;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ng = p.ng;
+  const unsigned ntri = (unsigned)ng * (ng + 1) / 2;
+  unsigned* tri = (unsigned*)smem;
+  unsigned* marg = tri + ((ntri + 3) & ~3u);
+  unsigned* px = marg;
+  unsigned* psum = marg + ng;       // index a + b
+  unsigned* pdiff = marg + 3 * ng;  // index b - a
+  __shared__ double red[C::NW * RED_MAX];
+  __shared__ long long s_i64[16];
+  __shared__ A s_res[RED_MAX];
+  __shared__ A s_gsum[NGLCM + 1];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  const unsigned long long ctr = *p.big_ctr;
+  const int n_big = (int)(ctr >> 32);
+  const int n_off = p.n_dist * p.n_dirs;
+  const unsigned long long n_units = (unsigned long long)(unsigned)ctr * n_off;
+  const A nan = anan<A>();
+  const T* img = (const T*)p.img;
+  for (unsigned long long g = blockIdx.x; g < n_units; g += gridDim.x) {
+    const unsigned u = (unsigned)(g / n_off);
+    const int oi = (int)(g - (unsigned long long)u * n_off);
+    const int di = oi / p.n_dirs, dir = oi - di * p.n_dirs;
+    const int b = big_of_unit(p, n_big, u);
+    const BigRoi br = p.big[b];
+    const int chunk = (int)(u - br.u1);
+    const RoiInfo r = p.rois[br.item];
+    BigBox bx;
+    bx.init(p, r, NDIM);
+    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    unsigned* reg = p.arena + br.arena;
+    const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
+    const unsigned vmin = r.vmin, vmax = r.vmax;
+    const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
+    FastDiv fd;
+    fd.init(vmax > vmin ? vmax - vmin : 1u);
+    auto gbin = [&](unsigned e) -> unsigned {  // rule a4 with n = Ng
+      if (vmax <= vmin) return 0u;
+      if constexpr (Enc<T>::INTEGER) return min(fd.div((unsigned)ng * (e - vmin)), (unsigned)(ng - 1));
+      else return bin_float(Enc<T>::decf(e), fmn, fmx, ng);
+    };
+    const int dx = p.off[oi][0], dy = p.off[oi][1], dz = p.off[oi][2];
+    const int64_t olin = ((int64_t)dz * p.ny + dy) * p.nx + dx;
+    for (unsigned i = tid; i < ntri; i += BIG_NT) tri[i] = 0;
+    __syncthreads();
+    chunk_pixels<T>(p, bx, c0, c1, [&](int x, int y, int z, unsigned e) {
+      const int X = x + dx, Y = y + dy, Z = z + dz;
+      if (X < 0 || Y < 0 || Z < 0 || X >= bx.W || Y >= bx.H || Z >= bx.D) return;
+      const int64_t off = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x + olin;
+      if (__ldg(p.mask + off) != bx.label) return;
+      const unsigned a = gbin(e), bb = gbin(Enc<T>::enc(__ldg(img + off)));
+      atomicAdd(&tri[a < bb ? tri_idx(a, bb) : tri_idx(bb, a)], 1u);
+    });
+    __syncthreads();
+    if (br.nch > 1) {
+      unsigned* gt = reg + L.tri + (size_t)oi * ntri;
+      for (unsigned i = tid; i < ntri; i += BIG_NT)
+        if (tri[i]) atomicAdd(gt + i, tri[i]);
+      if (!last_arrival(reg + L.ctr + 4 + oi, (unsigned)br.nch, &s_flag)) continue;
+      for (unsigned i = tid; i < ntri; i += BIG_NT) tri[i] = __ldcg(gt + i);
+      __syncthreads();
+    }
+
+    // ---- features of this offset from the complete triangle ---------------
+    double* row = p.table + (int64_t)br.item * p.n_col;
+    double* gf = (double*)(reg + L.gfeat) + (size_t)oi * 32;
+    const bool dbg = p.dbg_roi == (int64_t)br.item;
+    for (int i = tid; i < 4 * ng; i += BIG_NT) marg[i] = 0;
+    if (tid == 0)
+      for (int k = 0; k <= NGLCM; ++k) s_gsum[k] = 0;
+    __syncthreads();
+    long long iv[GI];
+#pragma unroll
+    for (int k = 0; k < GI; ++k) iv[k] = 0;
+    for (unsigned f = tid; f < ntri; f += BIG_NT) {
+      const unsigned cnt = tri[f];
+      if (!cnt) continue;
+      unsigned a, bb;
+      tri_ab(f, a, bb);
+      atomicAdd(&px[a], cnt);
+      atomicAdd(&px[bb], cnt);
+      atomicAdd(&psum[a + bb], 2 * cnt);
+      atomicAdd(&pdiff[bb - a], 2 * cnt);
+      const long long Cm = 2 * (long long)cnt;
+      const long long k = a + bb + 2, d = bb - a, k2 = k * k;
+      iv[0] += Cm;
+      iv[1] += Cm * k;
+      iv[2] += Cm * k2;
+      iv[3] += Cm * k2 * k;
+      iv[4] += Cm * k2 * k2;
+      iv[5] += Cm * d;
+      iv[6] += Cm * d * d;
+      iv[7] += (long long)cnt * ((long long)(a + 1) * (a + 1) + (long long)(bb + 1) * (bb + 1));
+      const long long Cc = a == bb ? 2 * (long long)cnt : (long long)cnt;
+      const long long mult = a == bb ? 1 : 2;
+      iv[8] += mult * Cc * Cc;
+      iv[9] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
+      iv[11] = Cc > iv[11] ? Cc : iv[11];
+      if (dbg) {
+        p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + bb] = (unsigned)Cc;
+        p.dbg_glcm[(int64_t)oi * ng * ng + bb * ng + a] = (unsigned)Cc;
+      }
+    }
+    __syncthreads();
+    long long Tl;
+    {
+      long long t1[1] = {0};
+      for (int a = tid; a < ng; a += BIG_NT) t1[0] += px[a];
+      block_sum_i64<C, 1>(t1, red, s_i64 + 13);
+      Tl = s_i64[13];
+    }
+    if (Tl == 0) {  // no pair for this offset: every feature NaN
+      if (tid == 0) {
+        if (p.per_offset)
+          for (int k = 0; k < NGLCM; ++k) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + k, nan);
+        gf[NGLCM] = 0.0;
+      }
+    } else {
+      A fv[GF];
+#pragma unroll
+      for (int k = 0; k < GF; ++k) fv[k] = 0;
+      const float Tf = (float)Tl;
+      const A invT = (A)1 / (A)Tl, ngA = (A)ng;
+      for (int a = tid; a < ng; a += BIG_NT) {
+        if (!px[a]) continue;
+        const A pr = (A)px[a] * invT;
+        fv[0] -= pr * alog2(pr);
+      }
+      for (int s = tid; s < 2 * ng - 1; s += BIG_NT) {
+        if (!psum[s]) continue;
+        const A pr = (A)psum[s] * invT;
+        fv[1] -= pr * alog2(pr);
+      }
+      for (int k = tid; k < ng; k += BIG_NT) {
+        if (!pdiff[k]) continue;
+        const A pr = (A)pdiff[k] * invT, kk = (A)k;
+        fv[2] -= pr * alog2(pr);
+        fv[3] += pr / ((A)1 + kk);
+        fv[4] += pr / ((A)1 + kk * kk);
+        fv[5] += pr / ((A)1 + kk / ngA);
+        fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));
+        if (k >= 1) fv[7] += pr / (kk * kk);
+      }
+      for (unsigned f = tid; f < ntri; f += BIG_NT) {
+        const unsigned cnt = tri[f];
+        if (!cnt) continue;
+        unsigned a, bb;
+        tri_ab(f, a, bb);
+        const long long mult = a == bb ? 1 : 2;
+        const unsigned Cc = a == bb ? 2 * cnt : cnt;
+        const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
+        iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
+      }
+      block_sum_glcm<C, A>(iv, fv, red, s_i64, s_res);
+      if (tid == 0) {
+        finalize_glcm<A>(p, row, s_i64, s_res, di, dir, s_gsum);
+        for (int k = 0; k < NGLCM; ++k) gf[k] = to_d(s_gsum[k]);
+        gf[NGLCM] = 1.0;
+      }
+    }
+    // the last offset of the ROI forms the direction means (offset order)
+    if (!last_arrival(reg + L.ctr + 2, (unsigned)n_off, &s_flag)) continue;
+    if (tid == 0) {
+      const double* gfa = (const double*)(reg + L.gfeat);
+      for (int d2 = 0; d2 < p.n_dist; ++d2) {
+        A gs[NGLCM];
+        for (int k = 0; k < NGLCM; ++k) gs[k] = 0;
+        A cnt = 0;
+        for (int o = 0; o < p.n_dirs; ++o) {
+          const double* q = gfa + (size_t)(d2 * p.n_dirs + o) * 32;
+          if (__ldcg(q + NGLCM) == 0.0) continue;
+          for (int k = 0; k < NGLCM; ++k) gs[k] += (A)__ldcg(q + k);
+          cnt += 1;
+        }
+        for (int k = 0; k < NGLCM; ++k) putA(p, row, Q_GLCM_D + d2 * NGLCM + k, cnt > 0 ? gs[k] / cnt : nan);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Float images: order statistics of one big ROI per block from its values
+// compacted in raster order and sorted by an LSD radix sort in the ROI's
+// arena region (stable ranks from 8 ballots per digit, as in the block path).
+template <class A>
+__global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
+  using C = ClassBig;
+  __shared__ unsigned cnt[C::NW * 256];
+  __shared__ unsigned dtot[256];
+  __shared__ double red[C::NW * RED_MAX];
+  __shared__ unsigned s_wc[C::NW], s_wb[C::NW + 1];
+  __shared__ double s_sd[4];
+  __shared__ int s_idx[4];
+  __shared__ A s_sc[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n_big = (int)(*p.big_ctr >> 32);
+  const float* img = (const float*)p.img;
+  for (int b = blockIdx.x; b < n_big; b += gridDim.x) {
+    const BigRoi br = p.big[b];
+    const RoiInfo r = p.rois[br.item];
+    BigBox bx;
+    bx.init(p, r, ndim);
+    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    const int n = (int)r.n;
+    unsigned* src = p.arena + br.arena + L.fsort;
+    unsigned* dst = src + n;
+    // compaction in raster order
+    if (tid == 0) s_wb[C::NW] = 0;
+    __syncthreads();
+    for (unsigned base = 0; base < bx.cells; base += BIG_NT) {
+      const unsigned c = base + tid;
+      bool in = false;
+      unsigned e = 0;
+      if (c < bx.cells) {
+        int x, y, z;
+        const int64_t off = bx.offset(c, x, y, z, p);
+        in = __ldg(p.mask + off) == bx.label;
+        if (in) e = Enc<float>::enc(__ldg(img + off));
+      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, in);
+      if (lane == 0) s_wc[warp] = __popc(bal);
+      __syncthreads();
+      if (tid == 0) {
+        unsigned acc = s_wb[C::NW];
+        for (int w = 0; w < C::NW; ++w) {
+          s_wb[w] = acc;
+          acc += s_wc[w];
+        }
+        s_wb[C::NW] = acc;
+      }
+      __syncthreads();
+      if (in) {
+        const unsigned pos = s_wb[warp] + __popc(bal & lanemask_lt());
+        if (pos < (unsigned)n) src[pos] = e;
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && s_wb[C::NW] != (unsigned)n) atomicOr(p.err, E_INTERNAL);
+    __threadfence_block();
+    __syncthreads();
+    // LSD radix sort, 8-bit digits; warp w owns the segment [w seg, (w+1) seg)
+    const int seg = (((n + C::NW - 1) / C::NW) + 31) & ~31;
+    const int lo = min(n, warp * seg), hi = min(n, lo + seg);
+    for (int shift = 0; shift < 32; shift += 8) {
+      for (int i = tid; i < C::NW * 256; i += BIG_NT) cnt[i] = 0;
+      __syncthreads();
+      for (int i0 = lo; i0 < hi; i0 += 32) {  // digit counts per warp
+        const int i = i0 + lane;
+        const bool act = i < hi;
+        const unsigned dg = act ? (src[i] >> shift) & 255u : 0u;
+        unsigned peers = __ballot_sync(0xFFFFFFFFu, act);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+          const unsigned bb = __ballot_sync(0xFFFFFFFFu, (dg >> bit) & 1u);
+          peers &= ((dg >> bit) & 1u) ? bb : ~bb;
+        }
+        if (act && __popc(peers & lanemask_lt()) == 0) cnt[warp * 256 + dg] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      for (int d = tid; d < 256; d += BIG_NT) {
+        unsigned t = 0;
+        for (int w = 0; w < C::NW; ++w) t += cnt[w * 256 + d];
+        dtot[d] = t;
+      }
+      __syncthreads();
+      if (warp == 0) warp_exclusive_scan(dtot, 256);
+      __syncthreads();
+      for (int d = tid; d < 256; d += BIG_NT) {
+        unsigned run = dtot[d];
+        for (int w = 0; w < C::NW; ++w) {
+          const unsigned c = cnt[w * 256 + d];
+          cnt[w * 256 + d] = run;
+          run += c;
+        }
+      }
+      __syncthreads();
+      for (int i0 = lo; i0 < hi; i0 += 32) {  // stable scatter, same walk
+        const int i = i0 + lane;
+        const bool act = i < hi;
+        const unsigned k = act ? src[i] : 0u;
+        const unsigned dg = (k >> shift) & 255u;
+        unsigned peers = __ballot_sync(0xFFFFFFFFu, act);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+          const unsigned bb = __ballot_sync(0xFFFFFFFFu, (dg >> bit) & 1u);
+          peers &= ((dg >> bit) & 1u) ? bb : ~bb;
+        }
+        const unsigned before = __popc(peers & lanemask_lt());
+        unsigned b0 = 0;
+        if (act) b0 = cnt[warp * 256 + dg];
+        __syncwarp();
+        if (act) {
+          dst[b0 + before] = k;
+          if (before == 0) cnt[warp * 256 + dg] = b0 + __popc(peers);
+        }
+        __syncwarp();
+      }
+      __threadfence_block();
+      __syncthreads();
+      unsigned* t = src;
+      src = dst;
+      dst = t;
+    }
+    double* row = p.table + (int64_t)br.item * p.n_col;
+    order_tail<float, C, A>(p, row, src, n, red, s_sd, s_idx, s_sc);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers (kernel templates are launched only from the translation unit
+// that instantiates them)
+
+template <auto K>
+static cudaError_t big_launch(int smem, int nsm, const KParams& p, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static int configured[64] = {0};
+  if (smem > 0 && (dev >= 64 || configured[dev] < smem)) {
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured[dev] = smem;
+  }
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K, BIG_NT, smem);
+  if (e != cudaSuccess) return e;
+  if (nb < 1) return cudaErrorInvalidConfiguration;
+  K<<<nb * nsm, BIG_NT, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <class T, int NDIM, class A>
+cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
+  cudaError_t e = big_launch<k_big_zero<T>>(0, nsm, p, st);
+  if (e != cudaSuccess) return e;
+  const int smem1 = 4 * (((p.hist_bins + 3) & ~3) + VH_SMEM);
+  if ((e = big_launch<k_big_p1<T, NDIM, A>>(smem1, nsm, p, st)) != cudaSuccess) return e;
+  if ((e = big_launch<k_big_p2<T, NDIM, A>>(0, nsm, p, st)) != cudaSuccess) return e;
+  if (p.need & NEED_GLCM) {
+    const int ntri = p.ng * (p.ng + 1) / 2;
+    const int smemg = 4 * (((ntri + 3) & ~3) + 4 * p.ng);
+    if ((e = big_launch<k_big_glcm<T, NDIM, A>>(smemg, nsm, p, st)) != cudaSuccess) return e;
+  }
+  if (!Enc<T>::INTEGER && (p.need & NEED_ORDER)) {
+    auto kern = k_big_order_f<A>;
+    int nb = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BIG_NT, 0)) != cudaSuccess) return e;
+    kern<<<(nb > 0 ? nb : 1) * nsm, BIG_NT, 0, st>>>(p, NDIM);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t launch_big_t(const KParams& p, int fp64, int nsm, cudaStream_t st) {
+  if (p.ndim == 3) return fp64 ? launch_big_one<T, 3, double>(p, nsm, st) : launch_big_one<T, 3, float>(p, nsm, st);
+  return fp64 ? launch_big_one<T, 2, double>(p, nsm, st) : launch_big_one<T, 2, float>(p, nsm, st);
+}
+
+}  // namespace nyx

@@ -345,8 +345,30 @@ __global__ void k_setup(KParams p) {
     r.pad = 0;
     p.rois[i] = r;
     if ((int64_t)i >= p.cap_roi) continue;  // no room for its output row
-    if (cls == 3) {
-      atomicOr(p.err, E_TOO_LARGE);
+    if (cls == 3) {  // multi-block class: register the ROI and its arena region
+      const unsigned long long cells3 = (unsigned long long)r.w * r.h * (p.ndim == 3 ? r.d : 1);
+      if (!p.big || cells3 >= (1ull << 32)) {
+        atomicOr(p.err, E_TOO_LARGE);
+        continue;
+      }
+      const int nch = (int)((cells3 + BIG_CHUNK - 1) / BIG_CHUNK);
+      const unsigned range = (p.dtype != NYX_F32 && (p.need & NEED_ORDER)) ? r.vmax - r.vmin + 1 : 0u;
+      const BigLayout L = big_layout(p, nch, range, r.n);
+      const unsigned long long a = atomicAdd(p.big_used, L.total);
+      if (a + L.total > p.arena_cap) {
+        atomicOr(p.err, E_TOO_LARGE);
+        continue;
+      }
+      // one atomic hands out the big-ROI index and the first pass unit, so
+      // u1 grows with the index
+      const unsigned long long old = atomicAdd(p.big_ctr, (1ull << 32) | (unsigned long long)nch);
+      BigRoi br;
+      br.item = (int)i;
+      br.nch = nch;
+      br.u1 = (unsigned)old;
+      br.range = range;
+      br.arena = a;
+      p.big[old >> 32] = br;
       continue;
     }
     unsigned q = atomicAdd(&p.qlen[cls], 1u);
@@ -415,6 +437,10 @@ __global__ void k_begin(KParams p) {
   if (t < 3) {
     p.qlen[t] = 0;
     p.qhead[t] = 0;
+  }
+  if (t == 0 && p.big_ctr) {
+    *p.big_ctr = 0;
+    *p.big_used = 0;
   }
   for (int b = t; b < p.batch; b += blockDim.x) {
     p.img_vmin[b] = 0xFFFFFFFFu;
