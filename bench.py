@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ROIs/sec and Mpixel/sec full feature set, % HBM roofline vs plain FP64 path"
-PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "reset")
+PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final", "reset")
 
 
 def _peaks():
@@ -321,7 +321,10 @@ def main() -> int:
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, 20.0)
-    launches_per_step = 7
+    # begin, scan, key sort, setup, 3 block classes, reset; multi-block class:
+    # zero, pass 1, pass 2 (+ GLCM, + float sort); GLCM features
+    glcm = w.params["glcm_levels"] > 0
+    launches_per_step = 8 + 3 + (1 if glcm else 0) + (1 if str(w.image.dtype) == "float32" else 0) + (1 if glcm else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "ROIs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",

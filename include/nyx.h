@@ -182,10 +182,10 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
  * [0] counters + label scan, [1] key sort + per-ROI setup, [2] ROI kernel of
  * the warp class (one warp per ROI), [3] of the small block class, [4] of the
  * medium block class, [5] the multi-block class (ROIs larger than a block
- * stages), [6] table reset.
+ * stages), [6] GLCM features from the per-offset sums, [7] table reset.
  * Errors: NYX_ERR_ARG (null plan/ms, slots out of 0..1024, back out of
  * range), NYX_ERR_STATE (that extract was not recorded), NYX_ERR_CUDA. */
-#define NYX_N_PHASES 7
+#define NYX_N_PHASES 8
 nyx_status nyx_profile_enable(nyx_plan* plan, int slots);
 nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
 

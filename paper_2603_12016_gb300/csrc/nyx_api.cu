@@ -23,6 +23,7 @@ cudaError_t launch_roi_f32(const KParams& p, int cls, int fp64, int nsm, cudaStr
 cudaError_t launch_big_u16(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_big_i16(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_big_f32(const KParams& p, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_glcm_final(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_reset(const KParams& p, int nsm, cudaStream_t st);
@@ -340,6 +341,10 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   const unsigned long long total_px = (unsigned long long)p.batch * p.dims[0] * p.dims[1] * p.dims[2];
   const unsigned long long arena_words = 3ull * total_px + (1ull << 24);
   const size_t o_arena = take(4ull * arena_words);
+  // per (ROI, offset) GLCM accumulators (GI int64 + GF sums in 8-byte slots)
+  const int64_t grows = mr < SORT_CAP ? mr : SORT_CAP;
+  const int n_off_all = p.glcm_levels > 0 ? p.n_dist * (p.ndim == 3 ? 13 : 4) : 0;
+  const size_t o_gacc = take((size_t)grows * n_off_all * (8 * (GI_HOST + GF_HOST)));
   cudaError_t e = cudaMalloc(&pl->ws, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -408,6 +413,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.big_used = k.big_ctr + 1;
   k.arena = (unsigned*)(w + o_arena);
   k.arena_cap = arena_words;
+  k.gacc = (unsigned char*)(w + o_gacc);
   pl->d_col_map = (int*)(w + o_cmap);
   k.col_map = pl->d_col_map;
   k.n_col = (int)pl->col_names.size();
@@ -576,6 +582,11 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
     if (prof) NYX_CUDA(c, cudaEventRecord(ev[6], st));
   }
+  if (k.need & NEED_GLCM) {
+    cudaError_t e = launch_glcm_final(k, fp64, c->nsm, st);
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
+  }
+  if (prof) NYX_CUDA(c, cudaEventRecord(ev[7], st));
   if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
   if (prof) {
     NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));

@@ -27,6 +27,7 @@ constexpr int MAX_DIST = 8;
 constexpr int MAX_DIRS = 13;
 constexpr int NGLCM = 30;
 constexpr int SORT_CAP = 16384;  // ROIs sortable by the single-block label sort
+constexpr int GI_HOST = 12, GF_HOST = 8;  // GLCM accumulator sizes (int64 sums, float sums)
 
 // Per (image, label) accumulator filled by the label scan.  Intensities use
 // an order-preserving uint32 encoding so that min/max are integer atomics.
@@ -160,14 +161,17 @@ struct KParams {
   unsigned long long* big_used;    // arena words handed out
   unsigned* arena;
   unsigned long long arena_cap;    // words
+  unsigned char* gacc;             // [max rows][n_off] GLCM accumulators
 };
 
-// Word offsets (u32 units) of the parts of one big ROI's arena region.  The
-// prefix [0, zero_end) must be zero when the passes start.
+// Word offsets (u32 units) of the parts of one big ROI's arena region: pass
+// counters, histograms, per-offset co-occurrence triangles (multi-chunk ROIs),
+// per-chunk partial sums, float sort buffers.  The prefix [0, zero_end) must
+// be zero when the passes start.
 constexpr int BIG_P1 = 28;   // pass-1 partial per chunk: 9 int64 + 5 doubles
 constexpr int BIG_P2 = 96;   // pass-2 partial per chunk: 48 doubles
 struct BigLayout {
-  unsigned long long ctr, hist, vhist, tri, zero_end, gfeat, part1, part2, fsort, total;
+  unsigned long long ctr, hist, vhist, tri, zero_end, part1, part2, fsort, total;
 };
 __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, unsigned range, unsigned n) {
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
@@ -176,12 +180,11 @@ __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, unsig
   const bool fsort = p.dtype == NYX_F32 && (p.need & NEED_ORDER);
   BigLayout L;
   unsigned long long o = 0;
-  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [2] GLCM, [4 + k] offset k
+  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [4 + k] offset k
   L.hist = o;     o = (o + ((p.need & NEED_HIST) ? p.hist_bins : 0) + 3) & ~3ull;
   L.vhist = o;    o = (o + range + 3) & ~3ull;
   L.tri = o;      o = (o + (nch > 1 ? n_off * tri : 0) + 3) & ~3ull;
   L.zero_end = o;
-  L.gfeat = o;    o += glcm ? n_off * 64 : 0;       // 32 doubles per offset
   L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
   L.part2 = o;    o += (unsigned long long)nch * BIG_P2;
   L.fsort = o;    o += fsort ? 2ull * n : 0;

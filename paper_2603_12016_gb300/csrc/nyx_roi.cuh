@@ -501,7 +501,7 @@ __device__ inline A i128A(__int128 x) {
 //   [10] sum C log2(C T / (P_i P_j))  (2^-24)      [11] max C
 // Float sums (deterministic: over the marginals in index order):
 //   [0] HX  [1] SUMENT  [2] DIFENTRO  [3] ID  [4] IDM  [5] IDN  [6] IDMN  [7] IV
-constexpr int GI = 12, GF = 8;
+constexpr int GI = GI_HOST, GF = GF_HOST;
 
 // GLCM features of one offset (Table S3 rows 140-174): every moment-type
 // feature from exact integer power sums (central moments of the sum /
@@ -623,6 +623,19 @@ __device__ inline void block_sum_glcm(long long (&iv)[GI], A (&fv)[GF], double* 
     fout[t - GI] = s;
   }
   __syncthreads();
+}
+
+// Per (ROI, offset) GLCM accumulator handed from the accumulation kernels to
+// k_glcm_final: the GI exact integer sums, then GF sums in the accumulation
+// type.  An all-zero record (T = 0) marks an offset without pairs.
+constexpr int GACC_BYTES = 8 * GI + 8 * GF;
+template <class A>
+__device__ inline void store_gacc(const KParams& p, int64_t item, int oi, const long long* iv, const A* fv,
+                                  bool empty) {
+  unsigned char* g = p.gacc + ((size_t)item * (p.n_dist * p.n_dirs) + oi) * GACC_BYTES;
+  const int t = threadIdx.x;
+  if (t < GI) ((long long*)g)[t] = empty ? 0ll : iv[t];
+  else if (t < GI + GF && !empty) ((A*)(g + 8 * GI))[t - GI] = fv[t - GI];
 }
 
 // Percentiles by linear interpolation at h = (n-1) q on the sorted values,
@@ -826,7 +839,6 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
   __shared__ double s_sd[4];
   __shared__ long long s_i64[16];  // [0..7] pass 1, [8..11] GLCM moments, [12..14] GLCM cells
   __shared__ int s_idx[4];
-  __shared__ A s_gsum[NGLCM + 1];
   __shared__ A s_pa[10];  // per-ROI scalars: mean (hi, lo), centroids, sums
   __shared__ unsigned s_ncell, s_npair;
 
@@ -1195,8 +1207,6 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         s_npair = 0;
       }
       for (int di = 0; di < p.n_dist; ++di) {
-        if (tid == 0)
-          for (int g = 0; g <= NGLCM; ++g) s_gsum[g] = 0;
         for (int dir = 0; dir < p.n_dirs; ++dir) {
           const int oi = di * p.n_dirs + dir;
           const int dx = p.off[oi][0], dy = p.off[oi][1], dz = p.off[oi][2];
@@ -1279,8 +1289,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           }
           __syncthreads();
           if (ncell == 0) {  // no pair for this offset: every feature NaN
-            if (tid == 0 && p.per_offset)
-              for (int g = 0; g < NGLCM; ++g) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, nan);
+            store_gacc<A>(p, item, oi, s_i64, res, true);
             continue;
           }
           // pass 2: marginal sums (index order) and mutual information (cells)
@@ -1320,7 +1329,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
           }
           block_sum_glcm<C, A>(iv, fv, red, s_i64, res);
-          if (tid == 0) finalize_glcm<A>(p, row, s_i64, res, di, dir, s_gsum);
+          store_gacc<A>(p, item, oi, s_i64, res, false);  // features: k_glcm_final
           // clean up only what this offset touched
           for (int s = tid; s < ncell; s += C::NT) {
             const unsigned h = cells[s];
@@ -1338,10 +1347,6 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             s_npair = 0;
           }
         }
-        __syncthreads();
-        if (tid == 0)
-          for (int g = 0; g < NGLCM; ++g)
-            putA(p, row, Q_GLCM_D + di * NGLCM + g, s_gsum[NGLCM] > 0 ? s_gsum[g] / s_gsum[NGLCM] : nan);
       }
       __syncthreads();
     }

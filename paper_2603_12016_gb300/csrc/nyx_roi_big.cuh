@@ -21,8 +21,8 @@
 //   k_big_glcm   units (ROI, chunk, offset): a dense upper-triangular
 //                co-occurrence matrix in shared memory (Ng(Ng+1)/2 counts,
 //                diagonal counted twice); multi-chunk ROIs add it into a
-//                global triangle and the last chunk of the offset computes
-//                the features; the last offset forms the direction means
+//                global triangle and the last chunk of the offset reduces it
+//                to the per-offset sums that k_glcm_final turns into features
 //   k_big_order_f  float images: one block per ROI compacts the values in
 //                raster order and sorts them (LSD radix, global memory)
 // "Last unit" is decided with a counter in the ROI's arena region after a
@@ -607,14 +607,12 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   __shared__ double red[C::NW * RED_MAX];
   __shared__ long long s_i64[16];
   __shared__ A s_res[RED_MAX];
-  __shared__ A s_gsum[NGLCM + 1];
   __shared__ int s_flag;
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
   const int n_big = (int)(ctr >> 32);
   const int n_off = p.n_dist * p.n_dirs;
   const unsigned long long n_units = (unsigned long long)(unsigned)ctr * n_off;
-  const A nan = anan<A>();
   const T* img = (const T*)p.img;
   for (unsigned long long g = blockIdx.x; g < n_units; g += gridDim.x) {
     const unsigned u = (unsigned)(g / n_off);
@@ -660,13 +658,9 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       __syncthreads();
     }
 
-    // ---- features of this offset from the complete triangle ---------------
-    double* row = p.table + (int64_t)br.item * p.n_col;
-    double* gf = (double*)(reg + L.gfeat) + (size_t)oi * 32;
+    // ---- GLCM sums of this offset from the complete triangle ---------------
     const bool dbg = p.dbg_roi == (int64_t)br.item;
     for (int i = tid; i < 4 * ng; i += BIG_NT) marg[i] = 0;
-    if (tid == 0)
-      for (int k = 0; k <= NGLCM; ++k) s_gsum[k] = 0;
     __syncthreads();
     long long iv[GI];
 #pragma unroll
@@ -709,71 +703,47 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       Tl = s_i64[13];
     }
     if (Tl == 0) {  // no pair for this offset: every feature NaN
-      if (tid == 0) {
-        if (p.per_offset)
-          for (int k = 0; k < NGLCM; ++k) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + k, nan);
-        gf[NGLCM] = 0.0;
-      }
-    } else {
-      A fv[GF];
+      store_gacc<A>(p, br.item, oi, s_i64, s_res, true);
+      __syncthreads();
+      continue;
+    }
+    A fv[GF];
 #pragma unroll
-      for (int k = 0; k < GF; ++k) fv[k] = 0;
-      const float Tf = (float)Tl;
-      const A invT = (A)1 / (A)Tl, ngA = (A)ng;
-      for (int a = tid; a < ng; a += BIG_NT) {
-        if (!px[a]) continue;
-        const A pr = (A)px[a] * invT;
-        fv[0] -= pr * alog2(pr);
-      }
-      for (int s = tid; s < 2 * ng - 1; s += BIG_NT) {
-        if (!psum[s]) continue;
-        const A pr = (A)psum[s] * invT;
-        fv[1] -= pr * alog2(pr);
-      }
-      for (int k = tid; k < ng; k += BIG_NT) {
-        if (!pdiff[k]) continue;
-        const A pr = (A)pdiff[k] * invT, kk = (A)k;
-        fv[2] -= pr * alog2(pr);
-        fv[3] += pr / ((A)1 + kk);
-        fv[4] += pr / ((A)1 + kk * kk);
-        fv[5] += pr / ((A)1 + kk / ngA);
-        fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));
-        if (k >= 1) fv[7] += pr / (kk * kk);
-      }
-      for (unsigned f = tid; f < ntri; f += BIG_NT) {
-        const unsigned cnt = tri[f];
-        if (!cnt) continue;
-        unsigned a, bb;
-        tri_ab(f, a, bb);
-        const long long mult = a == bb ? 1 : 2;
-        const unsigned Cc = a == bb ? 2 * cnt : cnt;
-        const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
-        iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
-      }
-      block_sum_glcm<C, A>(iv, fv, red, s_i64, s_res);
-      if (tid == 0) {
-        finalize_glcm<A>(p, row, s_i64, s_res, di, dir, s_gsum);
-        for (int k = 0; k < NGLCM; ++k) gf[k] = to_d(s_gsum[k]);
-        gf[NGLCM] = 1.0;
-      }
+    for (int k = 0; k < GF; ++k) fv[k] = 0;
+    const float Tf = (float)Tl;
+    const A invT = (A)1 / (A)Tl, ngA = (A)ng;
+    for (int a = tid; a < ng; a += BIG_NT) {
+      if (!px[a]) continue;
+      const A pr = (A)px[a] * invT;
+      fv[0] -= pr * alog2(pr);
     }
-    // the last offset of the ROI forms the direction means (offset order)
-    if (!last_arrival(reg + L.ctr + 2, (unsigned)n_off, &s_flag)) continue;
-    if (tid == 0) {
-      const double* gfa = (const double*)(reg + L.gfeat);
-      for (int d2 = 0; d2 < p.n_dist; ++d2) {
-        A gs[NGLCM];
-        for (int k = 0; k < NGLCM; ++k) gs[k] = 0;
-        A cnt = 0;
-        for (int o = 0; o < p.n_dirs; ++o) {
-          const double* q = gfa + (size_t)(d2 * p.n_dirs + o) * 32;
-          if (__ldcg(q + NGLCM) == 0.0) continue;
-          for (int k = 0; k < NGLCM; ++k) gs[k] += (A)__ldcg(q + k);
-          cnt += 1;
-        }
-        for (int k = 0; k < NGLCM; ++k) putA(p, row, Q_GLCM_D + d2 * NGLCM + k, cnt > 0 ? gs[k] / cnt : nan);
-      }
+    for (int s = tid; s < 2 * ng - 1; s += BIG_NT) {
+      if (!psum[s]) continue;
+      const A pr = (A)psum[s] * invT;
+      fv[1] -= pr * alog2(pr);
     }
+    for (int k = tid; k < ng; k += BIG_NT) {
+      if (!pdiff[k]) continue;
+      const A pr = (A)pdiff[k] * invT, kk = (A)k;
+      fv[2] -= pr * alog2(pr);
+      fv[3] += pr / ((A)1 + kk);
+      fv[4] += pr / ((A)1 + kk * kk);
+      fv[5] += pr / ((A)1 + kk / ngA);
+      fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));
+      if (k >= 1) fv[7] += pr / (kk * kk);
+    }
+    for (unsigned f = tid; f < ntri; f += BIG_NT) {
+      const unsigned cnt = tri[f];
+      if (!cnt) continue;
+      unsigned a, bb;
+      tri_ab(f, a, bb);
+      const long long mult = a == bb ? 1 : 2;
+      const unsigned Cc = a == bb ? 2 * cnt : cnt;
+      const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
+      iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
+    }
+    block_sum_glcm<C, A>(iv, fv, red, s_i64, s_res);
+    store_gacc<A>(p, br.item, oi, s_i64, s_res, false);  // features: k_glcm_final
     __syncthreads();
   }
 }

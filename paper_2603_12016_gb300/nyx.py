@@ -224,7 +224,7 @@ class Extractor:
                                        _stream_ptr(self.device)))
         return out
 
-    PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "reset")
+    PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final", "reset")
 
     def profile(self, slots: int = 1):
         """Record per-phase CUDA events for the next extracts (ring of
