@@ -93,6 +93,39 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# DRAM bytes (read + write) per launch of a phase's kernel from one ncu
+# capture of the same command; None once the kernel has changed since.
+TRAFFIC = {}
+
+
+def roi_classes(w):
+    """Pixels and ROI count per size class (warp, small, medium, multi-block)
+    by the library's class rule: pixel count and padded bounding-box cells
+    against (512, 2048), (1024, 4096), (8192, 16384)."""
+    import numpy as np
+    from scipy import ndimage
+
+    pad = max(w.params["dists"]) if w.params["glcm_levels"] > 0 else 0
+    lims = ((512, 2048), (1024, 4096), (8192, 16384))
+    px, rows = [0, 0, 0, 0], [0, 0, 0, 0]
+    masks = w.mask if (w.mask.ndim == 3 and w.ndim == 2) else w.mask[None]
+    for m in masks:
+        cnt = np.bincount(m.ravel())
+        for lab, sl in enumerate(ndimage.find_objects(m), start=1):
+            if sl is None:
+                continue
+            ext = [s.stop - s.start + 2 * pad for s in sl]
+            cells = int(np.prod(ext))
+            n = int(cnt[lab])
+            k = 3
+            for i in (2, 1, 0):
+                if n <= lims[i][0] and cells <= lims[i][1]:
+                    k = i
+            px[k] += n
+            rows[k] += 1
+    return px, rows
+
+
 def make_workload(name: str, rank: int):
     from paper_2603_12016_gb300 import workloads as W
 
@@ -174,6 +207,9 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison path")
     ap.add_argument("--ref-rois", type=int, default=800)
+    ap.add_argument("--backward", dest="backward", action="store_true", default=None,
+                    help="time forward + backward (default for the blobbatch workloads)")
+    ap.add_argument("--no-backward", dest="backward", action="store_false")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -215,10 +251,22 @@ def main() -> int:
     table = torch.empty((max_rois, len(ex.columns)), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # differentiation workload: a step is the forward pass plus the backward
+    # pass for a fixed random upstream gradient dL/dtable
+    bwd = args.backward if args.backward is not None else args.workload.startswith("blobbatch")
+    gen = torch.Generator(device=dev).manual_seed(5)
+    gtab = torch.randn((max_rois, len(ex.columns)), dtype=torch.float64, device=dev, generator=gen) if bwd else None
+    gimg = torch.empty(img.shape, dtype=torch.float32, device=dev) if bwd else None
+
+    def one_step(e, im, mk):
+        n = e.extract_into(im, mk, table, save_for_backward=bwd)
+        if bwd:
+            e.backward(im, mk, gtab, out=gimg)
+        return n
 
     def timed(e, steps, warmup, profile=False):
         for _ in range(warmup):
-            e.extract_into(img, mask, table)
+            one_step(e, img, mask)
         e.sync_status()
         if profile:
             e.profile(steps)
@@ -230,7 +278,7 @@ def main() -> int:
         for i in range(steps):
             flush.zero_()
             starts[i].record(stream)
-            n = e.extract_into(img, mask, table)
+            n = one_step(e, img, mask)
             ends[i].record(stream)
         torch.cuda.synchronize(dev)
         e.sync_status()
@@ -262,25 +310,31 @@ def main() -> int:
     alg = algorithmic_bytes(w, n_roi, n_col)
     pipe_gbs = alg / (t_step * 1e-3) / 1e9
 
-    # dominant kernel and its roofline (the ROI feature kernels read the ROI
-    # bounding boxes, L2-resident after the scan, and write the table; the
-    # label scan streams image + mask from HBM)
+    # dominant kernel and its roofline: algorithmic bytes of the phase that
+    # takes longest (the scan streams image + mask once; a ROI class reads
+    # its ROIs' pixels and mask once and writes their table rows; the GLCM
+    # feature kernel reads the per-offset sums and writes the GLCM columns)
     dom = max(phases, key=phases.get)
+    cls_px, cls_rows = roi_classes(w)
+    n_off = len(prm["dists"]) * (13 if w.ndim == 3 else 4) if prm["glcm_levels"] > 0 else 0
+    per_px = w.image.itemsize + 4
     dom_bytes = {"scan": w.image.nbytes + w.mask.nbytes,
-                 "sort_setup": 0,
-                 "roi_warp": None, "roi_small": None, "roi_medium": None, "reset": 0}[dom]
-    if dom_bytes is None:
-        roi_px = int((w.mask > 0).sum())
-        share = 1.0
-        dom_bytes = int(roi_px * (w.image.itemsize + 4) * share + 8 * n_roi * n_col)
+                 "roi_warp": cls_px[0] * per_px + 8 * cls_rows[0] * n_col,
+                 "roi_small": cls_px[1] * per_px + 8 * cls_rows[1] * n_col,
+                 "roi_medium": cls_px[2] * per_px + 8 * cls_rows[2] * n_col,
+                 "roi_big": cls_px[3] * per_px + 8 * cls_rows[3] * n_col,
+                 "glcm_final": n_roi * n_off * (160 + 8 * 30)}.get(dom, 0)
     dom_gbs = dom_bytes / (phases[dom] * 1e-3) / 1e9
+    traffic = TRAFFIC.get((w.name, dom))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
-                "frac": dom_gbs / peak, "traffic": None, "peak_kind": peak_kind}
+                "frac": dom_gbs / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes": int(dom_bytes)}
 
     # end to end through the public API: pinned host inputs -> H2D -> extract -> D2H
     h_img = torch.from_numpy(w.image).pin_memory()
     h_mask = torch.from_numpy(w.mask).pin_memory()
     h_table = torch.empty((max_rois, n_col), dtype=torch.float64).pin_memory()
+    h_grad = torch.empty(img.shape, dtype=torch.float32).pin_memory() if bwd else None
     d_img = torch.empty_like(img)
     d_mask = torch.empty_like(mask)
     e2e_ms = []
@@ -290,8 +344,10 @@ def main() -> int:
         s.record(stream)
         d_img.copy_(h_img, non_blocking=True)
         d_mask.copy_(h_mask, non_blocking=True)
-        n = ex.extract_into(d_img, d_mask, table)
+        n = one_step(ex, d_img, d_mask)
         h_table[:n_roi].copy_(table[:n_roi], non_blocking=True)
+        if bwd:
+            h_grad.copy_(gimg, non_blocking=True)
         t.record(stream)
         t.synchronize()
         if i >= args.warmup:
@@ -303,7 +359,7 @@ def main() -> int:
         e2e_t = float(tt.item())
     e2e = {"value": n_total / (e2e_t * 1e-3), "unit": "ROIs/s",
            "h2d_bytes_per_step": int(w.image.nbytes + w.mask.nbytes),
-           "d2h_bytes_per_step": int(8 * n_roi * n_col), "ms_per_step": e2e_t}
+           "d2h_bytes_per_step": int(8 * n_roi * n_col + (4 * w.image.size if bwd else 0)), "ms_per_step": e2e_t}
 
     fp64 = None
     if not args.no_fp64:
@@ -325,13 +381,16 @@ def main() -> int:
     # zero, pass 1, pass 2 (+ GLCM, + float sort); GLCM features
     glcm = w.params["glcm_levels"] > 0
     launches_per_step = 8 + 3 + (1 if glcm else 0) + (1 if str(w.image.dtype) == "float32" else 0) + (1 if glcm else 0)
+    if bwd:  # begin, scan, key sort, setup, coefficients, per-pixel gradient, reset
+        launches_per_step += 7
     line = {
         "metric": METRIC, "value": value, "unit": "ROIs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": w.name, "image": list(w.image.shape), "pixel_dtype": str(w.image.dtype),
                    "n_roi": n_roi, "n_col": n_col, "glcm_levels": prm["glcm_levels"], "dists": list(prm["dists"]),
-                   "hist_bins": prm["hist_bins"], "features": "all", "l2": "flushed (256 MB write) between steps",
+                   "hist_bins": prm["hist_bins"], "features": "all", "step": "forward + backward" if bwd else "forward",
+                   "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas{world}"},
         "mpix_per_s": px_total / (t_step * 1e-3) / 1e6,
         "roi_mpix_per_s": float((w.mask > 0).sum()) * world / (t_step * 1e-3) / 1e6,

@@ -216,10 +216,16 @@ class Extractor:
     def sync_status(self):
         self._check(lib().nyx_sync_status(self._plan, _stream_ptr(self.device)))
 
-    def backward(self, img: torch.Tensor, mask: torch.Tensor, grad_table: torch.Tensor) -> torch.Tensor:
+    def backward(self, img: torch.Tensor, mask: torch.Tensor, grad_table: torch.Tensor,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """dL/dimage (float32, image shape) of the last forward pass saved for
+        backward, given dL/dtable (FP64 [rows, n_col]); asynchronous."""
         img, mask = self._inputs(img, mask)
         g = grad_table.to(dtype=torch.float64).contiguous()
-        out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        elif out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != tuple(self.shape):
+            raise NyxError(1, "out must be a contiguous float32 tensor of the image shape")
         self._check(lib().nyx_backward(self._plan, img.data_ptr(), mask.data_ptr(), g.data_ptr(), out.data_ptr(),
                                        _stream_ptr(self.device)))
         return out

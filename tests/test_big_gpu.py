@@ -146,3 +146,39 @@ def test_big_repeatable():
     ex.sync_status()
     k = int(n.item())
     assert torch.equal(torch.nan_to_num(t1[:k], nan=-7.0), torch.nan_to_num(t2[:k], nan=-7.0))
+
+
+def _sampled(w, ndim, rng_seed, n_random=8, features=None):
+    """Full-size workload in the launch configuration of the benchmark,
+    checked on a sample of ROIs the oracle computes one by one (the largest,
+    the smallest and random ones)."""
+    from paper_2603_12016_gb300 import nyx
+
+    prm = w.params
+    ng = prm["glcm_levels"]
+    ex = nyx.Extractor(w.image.shape, _dtype(w.image), ndim=ndim, glcm_levels=ng, dists=prm["dists"],
+                       glcm_per_offset_cols=False, hist_bins=prm["hist_bins"], max_rois=8192, features=features)
+    g = gpu_table(ex, to_torch(w.image), to_torch(w.mask))
+    keys = (g["IMAGE"].astype(np.int64) << 32) | g["LABEL"].astype(np.int64)
+    order = np.argsort(g["AREA"])
+    rng = np.random.default_rng(rng_seed)
+    pick = set(order[:3].tolist()) | set(order[-3:].tolist()) | set(rng.choice(len(keys), n_random, replace=False).tolist())
+    rows = np.array(sorted(pick))
+    o = oracle.extract(w.image, w.mask, ndim, ng=max(ng, 2), dists=prm["dists"], hist_bins=prm["hist_bins"],
+                       rois=[int(keys[i]) for i in rows], threads=8)
+    g = {k: v[rows] for k, v in g.items()}
+    return g, o
+
+
+def test_ct3d_512x512x128_sampled():
+    w = W.config("ct3d")
+    g, o = _sampled(w, 3, 31)
+    assert o["AREA"].max() > 5e5
+    _assert_parity(g, o, 3)
+
+
+def test_blobbatch_64x512_sampled():
+    w = W.config("blobbatch")
+    g, o = _sampled(w, 2, 32, n_random=16)
+    assert o["AREA"].max() > 8192
+    _assert_parity(g, o, 2)

@@ -114,3 +114,11 @@ def test_backward_requires_saved_forward():
     with pytest.raises(nyx.NyxError) as e:
         ex.backward(img, mask, torch.zeros((64, len(ex.columns)), dtype=torch.float64, device="cuda"))
     assert e.value.status == 10
+
+
+def test_backward_big_rois_f32():
+    """ROIs above 8192 px take the multi-block path; their saved state feeds
+    the same backward kernels."""
+    w = W.blob_batch_f32(batch=2, size=256, seed=2305, roi_range=(3, 5), px_range=(9000, 20000))
+    assert np.bincount(w.mask.ravel())[1:].max() > 8192
+    _check(w, 2, n_fd=8)
