@@ -200,7 +200,7 @@ def cpu_baseline(w, budget_s: float):
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nuclei2d")
@@ -210,6 +210,7 @@ def main() -> int:
     ap.add_argument("--backward", dest="backward", action="store_true", default=None,
                     help="time forward + backward (default for the blobbatch workloads)")
     ap.add_argument("--no-backward", dest="backward", action="store_false")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default class limits")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -264,12 +265,12 @@ def main() -> int:
             e.backward(im, mk, gtab, out=gimg)
         return n
 
-    def timed(e, steps, warmup, profile=False):
+    def timed(e, steps, warmup):
+        """Per-step device times (CUDA events on the launching stream) of
+        back-to-back steps; the extraction replays its captured CUDA graph."""
         for _ in range(warmup):
             one_step(e, img, mask)
         e.sync_status()
-        if profile:
-            e.profile(steps)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         if dist is not None:
@@ -282,18 +283,28 @@ def main() -> int:
             ends[i].record(stream)
         torch.cuda.synchronize(dev)
         e.sync_status()
-        ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-        phases = None
-        if profile:
-            per = [e.phase_times(back=b) for b in range(steps)]
-            phases = {k: sum(p[k] for p in per) / steps for k in PHASES}
-            e.profile(0)
-        return ms, int(n.item()), phases
+        return [s.elapsed_time(t) for s, t in zip(starts, ends)], int(n.item())
 
+    def phase_profile(e, steps):
+        """Per-phase times from the library's event ring (direct launches)."""
+        e.profile(steps)
+        for _ in range(steps):
+            flush.zero_()
+            one_step(e, img, mask)
+        torch.cuda.synchronize(dev)
+        e.sync_status()
+        per = [e.phase_times(back=b) for b in range(steps)]
+        e.profile(0)
+        return {k: sum(p[k] for p in per) / steps for k in PHASES}
+
+    limits = None
+    if not args.no_autotune:
+        limits = ex.autotune(img, mask, reps=3)
     with ClockSampler(local) as clk:
-        ms, n_roi, phases = timed(ex, args.steps, args.warmup, profile=True)
+        ms, n_roi = timed(ex, args.steps, args.warmup)
     clocks = clk.summary()
-    t_step = sum(ms) / len(ms)
+    phases = phase_profile(ex, min(args.steps, 10))
+    t_step = statistics.median(ms)
     if dist is not None:
         tt = torch.tensor([t_step], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -352,7 +363,7 @@ def main() -> int:
         t.synchronize()
         if i >= args.warmup:
             e2e_ms.append(s.elapsed_time(t))
-    e2e_t = sum(e2e_ms) / len(e2e_ms)
+    e2e_t = statistics.median(e2e_ms)
     if dist is not None:
         tt = torch.tensor([e2e_t], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -364,8 +375,10 @@ def main() -> int:
     fp64 = None
     if not args.no_fp64:
         ex64 = extractor("fp64")
-        ms64, _, _ = timed(ex64, max(3, args.steps // 4), 3)
-        t64 = sum(ms64) / len(ms64)
+        if limits is not None:
+            ex64.set_class_limits(*limits)
+        ms64, _ = timed(ex64, max(3, args.steps // 4), 3)
+        t64 = statistics.median(ms64)
         fp64 = {"value": n_roi / (t64 * 1e-3), "unit": "ROIs/s", "ms_per_step": t64,
                 "speedup_fp32_over_fp64": t64 / t_step}
 
@@ -390,7 +403,8 @@ def main() -> int:
         "config": {"workload": w.name, "image": list(w.image.shape), "pixel_dtype": str(w.image.dtype),
                    "n_roi": n_roi, "n_col": n_col, "glcm_levels": prm["glcm_levels"], "dists": list(prm["dists"]),
                    "hist_bins": prm["hist_bins"], "features": "all", "step": "forward + backward" if bwd else "forward",
-                   "l2": "flushed (256 MB write) between steps",
+                   "l2": "flushed (256 MB write) between steps", "class_limits_px": list(limits) if limits else None,
+                   "timing": "median of per-step CUDA-event times, CUDA-graph replay",
                    "parallelism": f"replicas{world}"},
         "mpix_per_s": px_total / (t_step * 1e-3) / 1e6,
         "roi_mpix_per_s": float((w.mask > 0).sum()) * world / (t_step * 1e-3) / 1e6,

@@ -142,6 +142,36 @@ nyx_status nyx_count_rois(nyx_plan* plan, const void* d_img, const int32_t* d_ma
 nyx_status nyx_extract(nyx_plan* plan, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                        int64_t* d_n_roi, uint32_t flags, void* stream);
 
+/* CUDA graphs.  By default a plan captures its extraction launch sequence
+ * (label scan, key sort, the size-class kernels, GLCM features, table reset)
+ * into a CUDA graph the first time it sees a given set of arguments (device
+ * pointers, cap_roi, flags, class limits) and replays it on later calls with
+ * the same arguments; new arguments trigger a new capture.  Capture uses a
+ * stream owned by the plan, so `stream` may be the legacy default stream; the
+ * graph is launched on `stream`.  Calls with profiling enabled launch
+ * directly.  nyx_use_graphs(plan, 0) switches to direct launches;
+ * nyx_graph_captures reports how many captures the plan has made.  Not in
+ * the paper.  Errors: NYX_ERR_ARG (null plan / n). */
+nyx_status nyx_use_graphs(nyx_plan* plan, int enable);
+nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
+
+/* Size classes (the paper, "Results, Scalability": how much the GPU helps
+ * depends on ROI size and count, Fig. 3f/g).  Every ROI
+ * goes to the first class whose pixel limit and padded bounding-box cell
+ * capacity it fits: one warp per ROI (capacity 512 px / 2,048 cells), one
+ * 128-thread block (1,024 / 4,096), one 256-thread block (8,192 / 16,384),
+ * else the multi-block path.  lim_pix[3] sets the pixel limits of the first
+ * three classes (0 disables a class; each at most its capacity above).
+ * nyx_autotune times the extraction of (d_img, d_mask) under a grid of
+ * limits (warp 0/128/256/512, small 0/1024, medium 4096/8192; `reps` timed
+ * calls each after one synchronised warm-up), keeps the fastest and returns
+ * it in h_lim_pix (host int32[3], may be NULL).  d_table / cap_roi as in
+ * nyx_extract.  Synchronises.  Results do not depend on the limits beyond
+ * floating-point rounding.  Errors: NYX_ERR_ARG, and those of nyx_extract. */
+nyx_status nyx_set_class_limits(nyx_plan* plan, const int32_t* lim_pix);
+nyx_status nyx_autotune(nyx_plan* plan, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
+                        int reps, void* stream, int32_t* h_lim_pix);
+
 /* Synchronise `stream` and return the device error word of the plan's last
  * calls as a status (NYX_OK if clean); clears the word. */
 nyx_status nyx_sync_status(nyx_plan* plan, void* stream);

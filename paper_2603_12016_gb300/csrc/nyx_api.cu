@@ -88,7 +88,25 @@ struct nyx_plan {
   int prof_slots = 0;                // ring of event sets, 0 = off
   int64_t prof_count = 0;            // profiled extracts so far
   std::vector<cudaEvent_t> ev;       // prof_slots * (NYX_N_PHASES + 1)
+  // CUDA graphs of the extraction sequence, keyed by its kernel parameters
+  // (a few entries, least recently used replaced)
+  static constexpr int NGRAPH = 4;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;  // capture only; graphs launch on the caller's stream
+  cudaGraphExec_t graph_exec[NGRAPH] = {};
+  KParams graph_key[NGRAPH];
+  int64_t graph_used[NGRAPH] = {};
+  int64_t graph_clock = 0;
+  int64_t graph_captures = 0;
 };
+
+static void drop_graph(nyx_plan* pl) {
+  for (int i = 0; i < nyx_plan::NGRAPH; ++i) {
+    if (pl->graph_exec[i]) cudaGraphExecDestroy(pl->graph_exec[i]);
+    pl->graph_exec[i] = nullptr;
+  }
+}
+
 
 static nyx_status fail(nyx_ctx* c, nyx_status s, const char* fmt, ...) {
   if (c) {
@@ -431,6 +449,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
     e = launch_init_table(k, hcap, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaFree(pl->ws);
     delete pl;
@@ -444,6 +463,8 @@ void nyx_plan_destroy(nyx_plan* pl) {
   if (!pl) return;
   cudaSetDevice(pl->ctx->device);
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+  drop_graph(pl);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   cudaFree(pl->ws);
   if (pl->d_saved) cudaFree(pl->d_saved);
   if (pl->d_dbg) cudaFree(pl->d_dbg);
@@ -516,6 +537,87 @@ nyx_status nyx_count_rois(nyx_plan* pl, const void* d_img, const int32_t* d_mask
   return s;
 }
 
+// The launch sequence of one extraction (label scan, key sort + setup, the
+// four size classes, GLCM features, table reset).  `ev` (profiling) records
+// the phase boundaries; it is null when the sequence is captured.
+static nyx_status enqueue_extract(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st) {
+  nyx_ctx* c = pl->ctx;
+  nyx_status s;
+  if (k.dbg_glcm) NYX_CUDA(c, cudaMemsetAsync(pl->d_dbg, 0, 4ull * pl->n_off * k.ng * k.ng, st));
+  if (ev) NYX_CUDA(c, cudaEventRecord(ev[0], st));
+  if ((s = run_front(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  if (ev) NYX_CUDA(c, cudaEventRecord(ev[1], st));
+  if ((s = run_sort_setup(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  if (ev) NYX_CUDA(c, cudaEventRecord(ev[2], st));
+  const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
+  for (int cls = 0; cls < 3; ++cls) {
+    cudaError_t e;
+    switch (k.dtype) {
+      case NYX_U16: e = launch_roi_u16(k, cls, fp64, c->nsm, st); break;
+      case NYX_I16: e = launch_roi_i16(k, cls, fp64, c->nsm, st); break;
+      default: e = launch_roi_f32(k, cls, fp64, c->nsm, st); break;
+    }
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
+    if (ev) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
+  }
+  {
+    cudaError_t e;
+    switch (k.dtype) {
+      case NYX_U16: e = launch_big_u16(k, fp64, c->nsm, st); break;
+      case NYX_I16: e = launch_big_i16(k, fp64, c->nsm, st); break;
+      default: e = launch_big_f32(k, fp64, c->nsm, st); break;
+    }
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
+    if (ev) NYX_CUDA(c, cudaEventRecord(ev[6], st));
+  }
+  if (k.need & NEED_GLCM) {
+    cudaError_t e = launch_glcm_final(k, fp64, c->nsm, st);
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
+  }
+  if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
+  if ((s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  if (ev) NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));
+  return NYX_OK;
+}
+
+// Replay the cached graph of this exact launch sequence (same kernel
+// parameters, byte for byte), or capture it on the plan's own stream first.
+// The instantiated graph is then launched on the caller's stream, which may
+// be the legacy default stream.
+static nyx_status launch_graph(nyx_plan* pl, const KParams& k, cudaStream_t st) {
+  nyx_ctx* c = pl->ctx;
+  int slot = -1, victim = 0;
+  for (int i = 0; i < nyx_plan::NGRAPH; ++i) {
+    if (pl->graph_exec[i] && memcmp(&pl->graph_key[i], &k, sizeof(KParams)) == 0) slot = i;
+    if (!pl->graph_exec[i] || (pl->graph_exec[victim] && pl->graph_used[i] < pl->graph_used[victim])) victim = i;
+  }
+  if (slot < 0) {
+    slot = victim;
+    if (pl->graph_exec[slot]) cudaGraphExecDestroy(pl->graph_exec[slot]);
+    pl->graph_exec[slot] = nullptr;
+    NYX_CUDA(c, cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
+    const nyx_status s = enqueue_extract(pl, k, nullptr, pl->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+    if (s != NYX_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&pl->graph_exec[slot], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      pl->graph_exec[slot] = nullptr;
+      return fail(c, NYX_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    memcpy(&pl->graph_key[slot], &k, sizeof(KParams));
+    ++pl->graph_captures;
+  }
+  pl->graph_used[slot] = ++pl->graph_clock;
+  NYX_CUDA(c, cudaGraphLaunch(pl->graph_exec[slot], st));
+  return NYX_OK;
+}
+
 nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                        int64_t* d_n_roi, uint32_t flags, void* stream) {
   if (!pl) return NYX_ERR_ARG;
@@ -527,7 +629,10 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
   cudaStream_t st = (cudaStream_t)stream;
   nyx_ctx* c = pl->ctx;
   NYX_CUDA(c, cudaSetDevice(c->device));
-  KParams k = pl->kp;
+  // kernel parameters: a byte copy of the plan's (zero-padded) template, so
+  // that equal launches compare equal byte for byte
+  KParams k;
+  memcpy(&k, &pl->kp, sizeof k);
   k.img = d_img;
   k.mask = d_mask;
   k.vec = (k.nx % 4) == 0;
@@ -552,47 +657,92 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
   if (pl->dbg_roi >= 0 && pl->d_dbg && (k.need & NEED_GLCM)) {
     k.dbg_roi = pl->dbg_roi;
     k.dbg_glcm = pl->d_dbg;
-    NYX_CUDA(c, cudaMemsetAsync(pl->d_dbg, 0, 4ull * pl->n_off * k.ng * k.ng, st));
   }
-  const bool prof = pl->prof_slots > 0;
-  cudaEvent_t* ev = prof ? &pl->ev[(size_t)(pl->prof_count % pl->prof_slots) * (NYX_N_PHASES + 1)] : nullptr;
-  if (prof) NYX_CUDA(c, cudaEventRecord(ev[0], st));
-  if ((s = run_front(pl, k, st)) != NYX_OK) return s;
-  if (prof) NYX_CUDA(c, cudaEventRecord(ev[1], st));
-  if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
-  if (prof) NYX_CUDA(c, cudaEventRecord(ev[2], st));
-  const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
-  for (int cls = 0; cls < 3; ++cls) {
-    cudaError_t e;
-    switch (k.dtype) {
-      case NYX_U16: e = launch_roi_u16(k, cls, fp64, c->nsm, st); break;
-      case NYX_I16: e = launch_roi_i16(k, cls, fp64, c->nsm, st); break;
-      default: e = launch_roi_f32(k, cls, fp64, c->nsm, st); break;
-    }
-    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
-    if (prof) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
-  }
-  {
-    cudaError_t e;
-    switch (k.dtype) {
-      case NYX_U16: e = launch_big_u16(k, fp64, c->nsm, st); break;
-      case NYX_I16: e = launch_big_i16(k, fp64, c->nsm, st); break;
-      default: e = launch_big_f32(k, fp64, c->nsm, st); break;
-    }
-    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
-    if (prof) NYX_CUDA(c, cudaEventRecord(ev[6], st));
-  }
-  if (k.need & NEED_GLCM) {
-    cudaError_t e = launch_glcm_final(k, fp64, c->nsm, st);
-    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
-  }
-  if (prof) NYX_CUDA(c, cudaEventRecord(ev[7], st));
-  if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
-  if (prof) {
-    NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));
+  if (pl->prof_slots > 0) {  // profiled: direct launches with phase events
+    cudaEvent_t* ev = &pl->ev[(size_t)(pl->prof_count % pl->prof_slots) * (NYX_N_PHASES + 1)];
+    if ((s = enqueue_extract(pl, k, ev, st)) != NYX_OK) return s;
     ++pl->prof_count;
+  } else if (pl->use_graphs) {
+    if ((s = launch_graph(pl, k, st)) != NYX_OK) return s;
+  } else {
+    if ((s = enqueue_extract(pl, k, nullptr, st)) != NYX_OK) return s;
   }
   if (flags & NYX_SYNC) return read_err(pl, st);
+  return NYX_OK;
+}
+
+nyx_status nyx_use_graphs(nyx_plan* pl, int enable) {
+  if (!pl) return NYX_ERR_ARG;
+  pl->use_graphs = enable != 0;
+  if (!pl->use_graphs) drop_graph(pl);
+  return NYX_OK;
+}
+
+nyx_status nyx_graph_captures(const nyx_plan* pl, int64_t* n) {
+  if (!pl || !n) return NYX_ERR_ARG;
+  *n = pl->graph_captures;
+  return NYX_OK;
+}
+
+nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
+                        int reps, void* stream, int32_t* h_lim_pix) {
+  if (!pl || reps < 1 || reps > 100) return NYX_ERR_ARG;
+  nyx_status s = check_ptrs(pl, d_img, d_mask);
+  if (s != NYX_OK) return s;
+  nyx_ctx* c = pl->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  NYX_CUDA(c, cudaSetDevice(c->device));
+  // candidate pixel thresholds of the warp, small and medium classes (0 =
+  // class unused); the cell limits stay at each class's staging capacity
+  static const int cw[] = {0, 128, 256, 512}, cs[] = {0, 1024}, cm[] = {4096, 8192};
+  const int saved_prof = pl->prof_slots;
+  pl->prof_slots = 0;
+  int best[3] = {pl->kp.lim_pix[0], pl->kp.lim_pix[1], pl->kp.lim_pix[2]};
+  float best_ms = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  NYX_CUDA(c, cudaEventCreate(&e0));
+  NYX_CUDA(c, cudaEventCreate(&e1));
+  for (int a : cw)
+    for (int b : cs)
+      for (int m : cm) {
+        pl->kp.lim_pix[0] = a;
+        pl->kp.lim_pix[1] = b;
+        pl->kp.lim_pix[2] = m;
+        s = nyx_extract(pl, d_img, d_mask, d_table, cap_roi, nullptr, NYX_SYNC, stream);  // warm-up + check
+        if (s == NYX_OK) {
+          cudaEventRecord(e0, st);
+          for (int r = 0; r < reps && s == NYX_OK; ++r) s = nyx_extract(pl, d_img, d_mask, d_table, cap_roi, nullptr, 0, stream);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+        }
+        if (s != NYX_OK) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best[0] = a;
+          best[1] = b;
+          best[2] = m;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = best[i];
+  drop_graph(pl);
+  pl->prof_slots = saved_prof;
+  if (s != NYX_OK) return s;
+  if (h_lim_pix)
+    for (int i = 0; i < 3; ++i) h_lim_pix[i] = best[i];
+  return NYX_OK;
+}
+
+nyx_status nyx_set_class_limits(nyx_plan* pl, const int32_t* lim_pix) {
+  if (!pl || !lim_pix) return NYX_ERR_ARG;
+  const int cap[3] = {512, 1024, 8192};
+  for (int i = 0; i < 3; ++i)
+    if (lim_pix[i] < 0 || lim_pix[i] > cap[i]) return fail(pl->ctx, NYX_ERR_ARG, "class limit %d out of 0..%d", i, cap[i]);
+  for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = lim_pix[i];
+  drop_graph(pl);
   return NYX_OK;
 }
 

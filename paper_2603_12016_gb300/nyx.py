@@ -84,9 +84,14 @@ def lib() -> ctypes.CDLL:
     L.nyx_count_rois_noalloc.restype = ctypes.c_int
     L.nyx_profile_enable.argtypes = [vp, ctypes.c_int]
     L.nyx_phase_times.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), ctypes.c_int]
+    L.nyx_use_graphs.argtypes = [vp, ctypes.c_int]
+    L.nyx_graph_captures.argtypes = [vp, P(ctypes.c_int64)]
+    L.nyx_set_class_limits.argtypes = [vp, P(ctypes.c_int32)]
+    L.nyx_autotune.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, vp, P(ctypes.c_int32)]
     for f in ("nyx_params_default", "nyx_create", "nyx_plan_create", "nyx_num_columns", "nyx_column_name",
               "nyx_count_rois", "nyx_extract", "nyx_sync_status", "nyx_backward", "nyx_debug_select",
-              "nyx_debug_glcm", "nyx_debug_bins", "nyx_profile_enable", "nyx_phase_times"):
+              "nyx_debug_glcm", "nyx_debug_bins", "nyx_profile_enable", "nyx_phase_times", "nyx_use_graphs",
+              "nyx_graph_captures", "nyx_set_class_limits", "nyx_autotune"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -231,6 +236,29 @@ class Extractor:
         return out
 
     PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final", "reset")
+
+    def use_graphs(self, enable: bool = True):
+        """Replay the extraction as a captured CUDA graph (default on)."""
+        self._check(lib().nyx_use_graphs(self._plan, int(bool(enable))))
+
+    def graph_captures(self) -> int:
+        n = ctypes.c_int64(0)
+        self._check(lib().nyx_graph_captures(self._plan, ctypes.byref(n)))
+        return int(n.value)
+
+    def set_class_limits(self, warp: int, small: int, medium: int):
+        """Pixel limits of the warp / small / medium classes (0 disables one)."""
+        lim = (ctypes.c_int32 * 3)(warp, small, medium)
+        self._check(lib().nyx_set_class_limits(self._plan, lim))
+
+    def autotune(self, img: torch.Tensor, mask: torch.Tensor, reps: int = 3) -> Tuple[int, int, int]:
+        """Time a grid of class limits on this input, keep the fastest."""
+        img, mask = self._inputs(img, mask)
+        table = torch.empty((self.max_rois, len(self.columns)), dtype=torch.float64, device=self.device)
+        lim = (ctypes.c_int32 * 3)()
+        self._check(lib().nyx_autotune(self._plan, img.data_ptr(), mask.data_ptr(), table.data_ptr(), table.shape[0],
+                                       int(reps), _stream_ptr(self.device), lim))
+        return tuple(int(v) for v in lim)
 
     def profile(self, slots: int = 1):
         """Record per-phase CUDA events for the next extracts (ring of

@@ -207,3 +207,48 @@ def test_repeatable_and_sync_free_launches():
     ex.sync_status()
     k = int(n.item())
     assert torch.equal(torch.nan_to_num(t1[:k], nan=-7.0), torch.nan_to_num(t2[:k], nan=-7.0))
+
+
+# ---------------------------------------------------------------------------
+# CUDA-graph replay and size-class limits
+
+def test_graph_replay_matches_direct_launches():
+    nyx = _nyx()
+    w = W.config("nuclei2d_small")
+    img, mask = to_torch(w.image), to_torch(w.mask)
+    ex = nyx.Extractor(w.image.shape, torch.uint16, glcm_levels=256, dists=(1, 2), max_rois=1024)
+    t = [torch.full((1024, len(ex.columns)), -1.0, dtype=torch.float64, device="cuda") for _ in range(3)]
+    n = ex.extract_into(img, mask, t[0])
+    ex.extract_into(img, mask, t[0])          # same arguments: replay
+    assert ex.graph_captures() == 1
+    ex.extract_into(img, mask, t[1])          # new table pointer: second graph
+    assert ex.graph_captures() == 2
+    ex.extract_into(img, mask, t[0])          # both stay cached
+    assert ex.graph_captures() == 2
+    ex.sync_status()
+    ex.use_graphs(False)
+    ex.extract_into(img, mask, t[2])
+    ex.sync_status()
+    k = int(n.item())
+    ref = torch.nan_to_num(t[2][:k], nan=-7.0)
+    for tt in t[:2]:
+        assert torch.equal(torch.nan_to_num(tt[:k], nan=-7.0), ref)
+
+
+@pytest.mark.parametrize("limits", [None, (0, 0, 4096), (128, 0, 8192), (512, 1024, 0)])
+def test_class_limits_and_autotune_keep_parity(limits):
+    """Any class limits (autotuned or set) route ROIs to other kernels; the
+    table must still match the oracle.  (512, 1024, 0) sends every ROI above
+    1,024 px to the multi-block path."""
+    nyx = _nyx()
+    w = W.config("nuclei2d_small")
+    img, mask = to_torch(w.image), to_torch(w.mask)
+    ex = nyx.Extractor(w.image.shape, torch.uint16, glcm_levels=256, dists=(1, 2), max_rois=1024)
+    if limits is None:
+        lim = ex.autotune(img, mask, reps=2)
+        assert lim[0] in (0, 128, 256, 512) and lim[1] in (0, 1024) and lim[2] in (4096, 8192)
+    else:
+        ex.set_class_limits(*limits)
+    g = gpu_table(ex, img, mask)
+    o = oracle.extract(w.image, w.mask, 2, ng=256, dists=(1, 2), hist_bins=256, threads=8)
+    _assert_parity(g, o, 2)
