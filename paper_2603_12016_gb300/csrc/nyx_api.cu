@@ -428,7 +428,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.img_vmax = (unsigned*)(w + o_imax);
   k.big = (BigRoi*)(w + o_big);
   k.big_ctr = (unsigned long long*)(w + o_bigctr);
-  k.big_used = k.big_ctr + 1;
+  k.big_used = k.big_ctr + 1;  // three counters (the block holds 8 words)
   k.arena = (unsigned*)(w + o_arena);
   k.arena_cap = arena_words;
   k.gacc = (unsigned char*)(w + o_gacc);

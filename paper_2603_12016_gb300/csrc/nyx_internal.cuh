@@ -50,17 +50,41 @@ struct RoiInfo {
 
 // Per ROI of the multi-block class (class 3), registered by k_setup.  The
 // ROI's bounding box is cut into chunks of BIG_CHUNK raster cells; pass units
-// are (ROI, chunk), GLCM units (ROI, chunk, offset).  Everything the ROI
-// needs in global memory (counters, histograms, per-offset co-occurrence
+// are (ROI, chunk), GLCM units (ROI, BIG_GSPAN chunks, group of offsets whose
+// triangles fit in shared memory together).  Everything the ROI needs in
+// global memory (counters, histograms, per-offset co-occurrence
 // triangles, per-chunk partial sums, sort buffers) is one region of the big
 // arena starting at word `arena`.
-constexpr int BIG_CHUNK = 65536;
+constexpr int BIG_CHUNK = 16384;   // pass-unit cells (32 per thread of a 512-thread block)
+constexpr int BIG_GSPAN = 4;       // fallback GLCM unit: this many pass chunks
+constexpr int GLCM_TRI_WORDS = 30720;   // shared-memory words for the co-occurrence triangles of a GLCM unit
+constexpr int GLCM_SMEM_BYTES = 200 * 1024;  // dynamic shared memory of a GLCM unit (triangles, marginals, raster)
+
+// Offsets whose triangles fit in one GLCM unit's shared memory together.
+__host__ __device__ inline int glcm_group(int ng, int n_off) {
+  const int tri = ng * (ng + 1) / 2;
+  const int padded = (tri + 3) & ~3;
+  int g = padded > 0 ? GLCM_TRI_WORDS / padded : n_off;
+  if (g < 1) g = 1;
+  return g < n_off ? g : n_off;
+}
+
+// u16 raster cells left for a GLCM unit next to its triangles and marginals.
+__host__ __device__ inline int glcm_raster_cells(int ng, int n_off) {
+  const int g = glcm_group(ng, n_off);
+  const int tstride = ((ng * (ng + 1) / 2) + 3) & ~3;
+  return (GLCM_SMEM_BYTES - 4 * g * tstride - 16 * ng) / 2;
+}
 struct BigRoi {
   int item;                 // ROI index (output row)
   int nch;                  // bounding-box chunks
   unsigned u1;              // first pass unit (prefix over the big ROIs)
   unsigned range;           // value-histogram words (16-bit order statistics), else 0
   unsigned long long arena; // word offset of the ROI's arena region
+  unsigned u2;              // first GLCM unit (prefix over the big ROIs)
+  int nsp;                  // GLCM spans
+  int gsp;                  // padded raster cells per GLCM span; 0 = global-memory neighbours
+  int hal;                  // raster halo: the largest neighbour displacement in padded cells
   double st[10];            // pass-1 scalars: mean (hi, lo), centroids, sum I, energy
 };
 
@@ -157,12 +181,18 @@ struct KParams {
   int lim_pix[3], lim_cells[3];
   // multi-block class
   BigRoi* big;                     // [max_rois]
-  unsigned long long* big_ctr;     // (n_big << 32) | n_pass_units
-  unsigned long long* big_used;    // arena words handed out
+  unsigned long long* big_ctr;     // (n_big << 44) | (n_pass_units << 22) | n_glcm_units
+  unsigned long long* big_used;    // [0] arena words handed out, [1] pass units, [2] GLCM units
   unsigned* arena;
   unsigned long long arena_cap;    // words
   unsigned char* gacc;             // [max rows][n_off] GLCM accumulators
 };
+
+// Fields of the packed big-ROI counter (one atomic hands out the big-ROI
+// index, its first pass unit and its first GLCM unit together).
+__host__ __device__ inline int big_count(unsigned long long c) { return (int)(c >> 44); }
+__host__ __device__ inline unsigned big_units1(unsigned long long c) { return (unsigned)(c >> 22) & 0x3FFFFFu; }
+__host__ __device__ inline unsigned big_units2(unsigned long long c) { return (unsigned)c & 0x3FFFFFu; }
 
 // Word offsets (u32 units) of the parts of one big ROI's arena region: pass
 // counters, histograms, per-offset co-occurrence triangles (multi-chunk ROIs),
@@ -173,17 +203,17 @@ constexpr int BIG_P2 = 96;   // pass-2 partial per chunk: 48 doubles
 struct BigLayout {
   unsigned long long ctr, hist, vhist, tri, zero_end, part1, part2, fsort, total;
 };
-__host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, unsigned range, unsigned n) {
+__host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int nsp, unsigned range, unsigned n) {
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
   const bool glcm = (p.need & NEED_GLCM) != 0;
   const unsigned long long tri = glcm ? (unsigned long long)p.ng * (p.ng + 1) / 2 : 0;
   const bool fsort = p.dtype == NYX_F32 && (p.need & NEED_ORDER);
   BigLayout L;
   unsigned long long o = 0;
-  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [4 + k] offset k
+  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [4 + k] offset group k
   L.hist = o;     o = (o + ((p.need & NEED_HIST) ? p.hist_bins : 0) + 3) & ~3ull;
   L.vhist = o;    o = (o + range + 3) & ~3ull;
-  L.tri = o;      o = (o + (nch > 1 ? n_off * tri : 0) + 3) & ~3ull;
+  L.tri = o;      o = (o + (nsp > 1 ? n_off * tri : 0) + 3) & ~3ull;
   L.zero_end = o;
   L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
   L.part2 = o;    o += (unsigned long long)nch * BIG_P2;

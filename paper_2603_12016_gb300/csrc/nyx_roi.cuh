@@ -265,6 +265,21 @@ __device__ inline void warp_exclusive_scan(unsigned* a, int n) {
   }
 }
 
+// Run-length merge of equal keys held by consecutive lanes (every lane of the
+// warp calls it; `invalid` marks lanes without a key).  Returns the run length
+// in the first lane of each run of valid keys, 0 elsewhere.  Smooth images
+// give long runs of equal co-occurrence cells or histogram bins along x; one
+// atomic per run replaces up to 32 conflicting ones on the same address.
+__device__ inline unsigned run_leader(unsigned key, unsigned invalid) {
+  const int lane = threadIdx.x & 31;
+  const unsigned prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+  const bool lead = lane == 0 || key != prev;
+  const unsigned leads = __ballot_sync(0xFFFFFFFFu, lead);
+  if (!lead || key == invalid) return 0u;
+  const unsigned above = lane == 31 ? 0u : (leads & (0xFFFFFFFFu << (lane + 1)));
+  return (unsigned)((above ? __ffs(above) - 1 : 32) - lane);
+}
+
 // ----------------------------------------------------------------------------
 // moments helpers
 
@@ -1225,13 +1240,13 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
               const unsigned a = raster[ci], b = raster[ci + olin];
               if (b != 0xFFFFu) key = a < b ? (a << 8) | b : (b << 8) | a;
             }
-            // one insert per pair: with up to Ng^2/2 keys the pairs of a warp
-            // are mostly distinct, so aggregating them first costs more than
-            // the shared-memory atomics it would save
+            // one insert per run of equal keys in consecutive lanes (noisy
+            // images give runs of 1; smooth ones long runs that would
+            // otherwise serialise on one address)
             const unsigned nvalid = __popc(__ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu));
             if (lane == 0 && nvalid) atomicAdd(&s_npair, nvalid);
-            if (key != 0xFFFFFFFFu) {
-              const unsigned add = 1u;
+            const unsigned add = run_leader(key, 0xFFFFFFFFu);
+            if (add) {
               unsigned h = (key * 2654435761u >> 7) & (unsigned)(cap - 1);
               for (int probe = 0; probe < cap; ++probe) {
                 const unsigned wv = tab[h];

@@ -15,14 +15,21 @@
 //                [min, max]; the last unit of an ROI merges the per-chunk
 //                partials in chunk order and derives the mean, centroids,
 //                histogram features and the order statistics
-//   k_big_p2     units (ROI, chunk): centred power sums and central moments
-//                (Kahan per thread, compensated across the block); the last
-//                unit merges and finalises statistics and moments
-//   k_big_glcm   units (ROI, chunk, offset): a dense upper-triangular
-//                co-occurrence matrix in shared memory (Ng(Ng+1)/2 counts,
-//                diagonal counted twice); multi-chunk ROIs add it into a
-//                global triangle and the last chunk of the offset reduces it
-//                to the per-offset sums that k_glcm_final turns into features
+//   k_big_p2     units (ROI, chunk): one pass for the centred power sums
+//                (Kahan per thread) and both sets of central moments,
+//                compensated across the block; the last unit merges and
+//                finalises statistics and moments
+//   k_big_glcm   units (ROI, span, group of offsets): one dense upper-
+//                triangular co-occurrence matrix per offset of the group in
+//                shared memory (Ng(Ng+1)/2 counts, diagonal counted twice).
+//                A span is a range of the ROI's padded bounding box staged
+//                as a raster of bins (plus a forward halo of the largest
+//                neighbour displacement), so neighbours are shared-memory
+//                loads; ROIs whose halo does not fit read neighbours from
+//                global memory.  ROIs of several spans add the triangles
+//                into global ones and the last span of the group reduces
+//                them to the per-offset sums that k_glcm_final turns into
+//                features
 //   k_big_order_f  float images: one block per ROI compacts the values in
 //                raster order and sorts them (LSD radix, global memory)
 // "Last unit" is decided with a counter in the ROI's arena region after a
@@ -38,12 +45,13 @@ constexpr int BIG_NT = 512;
 constexpr int VH_SMEM = 8192;  // value-histogram words kept in shared memory per chunk
 using ClassBig = RoiClass<BIG_NT, 1, 1>;  // thread geometry for the block reductions
 
-// the big ROI owning pass unit u (u1 grows with the big-ROI index)
-__device__ inline int big_of_unit(const KParams& p, int n_big, unsigned u) {
+// the big ROI owning pass unit u (GLCM unit u with glcm = true); the first
+// units u1 and u2 grow with the big-ROI index
+__device__ inline int big_of_unit(const KParams& p, int n_big, unsigned u, bool glcm = false) {
   int lo = 0, hi = n_big - 1;
   while (lo < hi) {
     const int m = (lo + hi + 1) >> 1;
-    if (p.big[m].u1 <= u) lo = m;
+    if ((glcm ? p.big[m].u2 : p.big[m].u1) <= u) lo = m;
     else hi = m - 1;
   }
   return lo;
@@ -109,16 +117,36 @@ struct BigBox {
   }
 };
 
-// Visit the ROI pixels of cells [c0, c1): f(x, y, z, encoded value).
+// Visit cells [c0, c1) with every thread of the block making the same number
+// of iterations, so that f may use warp-synchronous operations:
+// f(in, x, y, z, encoded value), in = the cell belongs to the ROI.  Each
+// thread issues the mask and image loads of BIG_U cells before using them (a
+// cell of the bounding box is always inside the image, so the image load
+// needs no mask test): the loop is bound by L2 latency, not bandwidth.
+constexpr int BIG_U = 4;
 template <class T, class F>
-__device__ inline void chunk_pixels(const KParams& p, const BigBox& bx, unsigned c0, unsigned c1, F f) {
+__device__ inline void chunk_cells(const KParams& p, const BigBox& bx, unsigned c0, unsigned c1, F f) {
   const T* img = (const T*)p.img;
 #pragma unroll 1
-  for (unsigned c = c0 + threadIdx.x; c < c1; c += BIG_NT) {
-    int x, y, z;
-    const int64_t off = bx.offset(c, x, y, z, p);
-    if (__ldg(p.mask + off) != bx.label) continue;
-    f(x, y, z, Enc<T>::enc(__ldg(img + off)));
+  for (unsigned cb = c0; cb < c1; cb += BIG_U * BIG_NT) {
+    int xs[BIG_U], ys[BIG_U], zs[BIG_U], lab[BIG_U];
+    T val[BIG_U];
+#pragma unroll
+    for (int u = 0; u < BIG_U; ++u) {
+      const unsigned c = cb + u * BIG_NT + threadIdx.x;
+      lab[u] = 0;
+      xs[u] = ys[u] = zs[u] = 0;
+      if (c < c1) {
+        const int64_t off = bx.offset(c, xs[u], ys[u], zs[u], p);
+        lab[u] = __ldg(p.mask + off);
+        val[u] = __ldg(img + off);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BIG_U; ++u) {
+      const bool in = cb + u * BIG_NT + threadIdx.x < c1 && lab[u] == bx.label;
+      f(in, xs[u], ys[u], zs[u], in ? Enc<T>::enc(val[u]) : 0u);
+    }
   }
 }
 
@@ -138,11 +166,11 @@ __device__ inline bool last_arrival(unsigned* counter, unsigned total, int* s_fl
 
 template <class T>  // (templated so each dtype's translation unit owns its copy)
 __global__ void __launch_bounds__(BIG_NT) k_big_zero(KParams p) {
-  const int n_big = (int)(*p.big_ctr >> 32);
+  const int n_big = big_count(*p.big_ctr);
   for (int b = blockIdx.x; b < n_big; b += gridDim.x) {
     const BigRoi br = p.big[b];
     const RoiInfo r = p.rois[br.item];
-    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
     uint4* z = (uint4*)(p.arena + br.arena);
     const unsigned long long n4 = L.zero_end / 4;
     for (unsigned long long i = threadIdx.x; i < n4; i += BIG_NT) z[i] = make_uint4(0, 0, 0, 0);
@@ -272,8 +300,8 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
   __shared__ int s_flag;
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
-  const int n_big = (int)(ctr >> 32);
-  const unsigned n_units = (unsigned)ctr;
+  const int n_big = big_count(ctr);
+  const unsigned n_units = big_units1(ctr);
   const unsigned need = p.need;
   constexpr bool integer = Enc<T>::INTEGER;
   const long long ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
@@ -284,7 +312,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
     const RoiInfo r = p.rois[br.item];
     BigBox bx;
     bx.init(p, r, NDIM);
-    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
     unsigned* reg = p.arena + br.arena;
     const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
     const unsigned vmin = r.vmin, vmax = r.vmax;
@@ -303,37 +331,45 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
     long long s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     KSum<A> fs[5];  // float images: sum I, x I, y I, z I, I^2
     unsigned* gvh = reg + L.vhist;
-    chunk_pixels<T>(p, bx, c0, c1, [&](int x, int y, int z, unsigned e) {
-      s[4] += x;
-      s[5] += y;
-      s[6] += z;
-      s[8] += 1;
-      if constexpr (integer) {
-        const long long v = (long long)e - ibias;
-        s[0] += v;
-        s[1] += x * v;
-        s[2] += y * v;
-        s[3] += z * v;
-        s[7] += v * v;
-      } else {
-        const A v = decA<T, A>(e);
-        fs[0].add(v);
-        fs[1].add((A)x * v);
-        fs[2].add((A)y * v);
-        fs[3].add((A)z * v);
-        fs[4].add(v * v);
-      }
-      if (do_hist) {
-        unsigned hb = 0;
+    chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e) {
+      unsigned hb = 0xFFFFFFFFu, vb = 0xFFFFFFFFu;
+      if (in) {
+        s[4] += x;
+        s[5] += y;
+        s[6] += z;
+        s[8] += 1;
+        if constexpr (integer) {
+          const long long v = (long long)e - ibias;
+          s[0] += v;
+          s[1] += x * v;
+          s[2] += y * v;
+          s[3] += z * v;
+          s[7] += v * v;
+        } else {
+          const A v = decA<T, A>(e);
+          fs[0].add(v);
+          fs[1].add((A)x * v);
+          fs[2].add((A)y * v);
+          fs[3].add((A)z * v);
+          fs[4].add(v * v);
+        }
+        hb = 0;
         if (vmax > vmin) {
           if constexpr (integer) hb = min(fd.div((unsigned)p.hist_bins * (e - vmin)), (unsigned)(p.hist_bins - 1));
           else hb = bin_float(Enc<T>::decf(e), fmn, fmx, p.hist_bins);
         }
-        atomicAdd(&hist[hb], 1u);
+        vb = e - vmin;
+      }
+      if (do_hist) {  // one atomic per run of equal bins in consecutive lanes
+        const unsigned len = run_leader(hb, 0xFFFFFFFFu);
+        if (len) atomicAdd(&hist[hb], len);
       }
       if (range) {
-        if (vh_smem) atomicAdd(&vh[e - vmin], 1u);
-        else atomicAdd(&gvh[e - vmin], 1u);
+        const unsigned len = run_leader(vb, 0xFFFFFFFFu);
+        if (len) {
+          if (vh_smem) atomicAdd(&vh[vb], len);
+          else atomicAdd(&gvh[vb], len);
+        }
       }
     });
     block_sum_i64<C, 9>(s, red, s_i64);
@@ -473,8 +509,8 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
   __shared__ int s_flag;
   const int tid = threadIdx.x, warp = tid >> 5;
   const unsigned long long ctr = *p.big_ctr;
-  const int n_big = (int)(ctr >> 32);
-  const unsigned n_units = (unsigned)ctr;
+  const int n_big = big_count(ctr);
+  const unsigned n_units = big_units1(ctr);
   const unsigned need = p.need;
   const long long ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
   const bool do_st = (need & (NEED_STATS | NEED_SAVE)) != 0;
@@ -487,7 +523,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
     const RoiInfo r = p.rois[br.item];
     BigBox bx;
     bx.init(p, r, NDIM);
-    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
     unsigned* reg = p.arena + br.arena;
     const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
     const double* st = p.big[b].st;
@@ -495,40 +531,35 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
     const A cx = (A)__ldcg(st + 2), cy = (A)__ldcg(st + 3), cz = (A)__ldcg(st + 4);
     const A bcx = (A)__ldcg(st + 5), bcy = (A)__ldcg(st + 6), bcz = (A)__ldcg(st + 7);
     double* part = (double*)(reg + L.part2) + (size_t)chunk * (BIG_P2 / 2);
-    if (do_st) {
-      KSum<A> acc[8];
-      chunk_pixels<T>(p, bx, c0, c1, [&](int, int, int, unsigned e) {
-        const A v = Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e);
+    // one pass: centred power sums and both moment sets, plain per-thread
+    // sums over at most BIG_CHUNK / BIG_NT = 32 cells (as in the block
+    // classes), then compensated block sums and two-sum chunk merges
+    A acc[8], mi[NM], mb[NM];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) mi[i] = mb[i] = 0;
+    chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e) {
+      if (!in) return;
+      const A v = Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e);
+      if (do_st) {
         const A d = (v - mu_hi) - mu_lo;
         const A d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
-        acc[0].add(d);
-        acc[1].add(d2);
-        acc[2].add(d3);
-        acc[3].add(d4);
-        acc[4].add(d4 * d);
-        acc[5].add(d3 * d3);
-        acc[6].add(d < 0 ? -d : d);
-        acc[7].add(d > 0 ? (A)1 : (d < 0 ? (A)-1 : (A)0));
-      });
-      block_sum_k<C, A, 8>(acc, red, res);
-      if (tid < 8) part[tid] = to_d(res[tid]);
-      __syncthreads();
-    } else if (tid < 8) {
-      part[tid] = 0.0;  // unselected group: defined zeros for the merge
-    }
-#pragma unroll 1
-    for (int w = 0; w < 2; ++w) {
-      if (!(w ? do_mb : do_mi)) {
-        if (tid < NM) part[8 + w * NM + tid] = 0.0;
-        continue;
+        acc[0] += d;
+        acc[1] += d2;
+        acc[2] += d3;
+        acc[3] += d4;
+        acc[4] += d4 * d;
+        acc[5] += d3 * d3;
+        acc[6] += d < 0 ? -d : d;
+        acc[7] += d > 0 ? (A)1 : (d < 0 ? (A)-1 : (A)0);
       }
-      KSum<A> acc[NM];
-      const A k0 = w ? bcx : cx, k1 = w ? bcy : cy, k2 = w ? bcz : cz;
-      chunk_pixels<T>(p, bx, c0, c1, [&](int x, int y, int z, unsigned e) {
-        const A u0 = (A)x - k0, u1 = (A)y - k1, u2 = (A)z - k2;
-        const A wt = w ? (A)1 : (Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e));
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        if (!(w ? do_mb : do_mi)) continue;
+        const A u0 = (A)x - (w ? bcx : cx), u1 = (A)y - (w ? bcy : cy), u2 = (A)z - (w ? bcz : cz);
         A px[4], py[4], pz[4];
-        px[0] = wt;
+        px[0] = w ? (A)1 : v;
         py[0] = pz[0] = 1;
 #pragma unroll
         for (int q = 1; q < 4; ++q) {
@@ -541,13 +572,21 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
 #pragma unroll
           for (int bb = 0; a + bb <= 3; ++bb)
 #pragma unroll
-            for (int cc = 0; cc <= (NDIM == 3 ? 3 - a - bb : 0); ++cc)
-              acc[midx<NDIM>(a, bb, cc)].add(px[a] * py[bb] * pz[cc]);
-      });
-      block_sum_k<C, A, NM>(acc, red, res);
-      if (tid < NM) part[8 + w * NM + tid] = to_d(res[tid]);
-      __syncthreads();
-    }
+            for (int cc = 0; cc <= (NDIM == 3 ? 3 - a - bb : 0); ++cc) {
+              const A t = px[a] * py[bb] * pz[cc];
+              if (w) mb[midx<NDIM>(a, bb, cc)] += t;
+              else mi[midx<NDIM>(a, bb, cc)] += t;
+            }
+      }
+    });
+    block_sum<C, A, 8>(acc, red, res);
+    if (tid < 8) part[tid] = do_st ? to_d(res[tid]) : 0.0;
+    __syncthreads();
+    block_sum<C, A, NM>(mi, red, res);
+    if (tid < NM) part[8 + tid] = do_mi ? to_d(res[tid]) : 0.0;
+    __syncthreads();
+    block_sum<C, A, NM>(mb, red, res);
+    if (tid < NM) part[8 + NM + tid] = do_mb ? to_d(res[tid]) : 0.0;
     if (!last_arrival(reg + L.ctr + 1, (unsigned)br.nch, &s_flag)) continue;
 
     // ---- last chunk: merge the partials in chunk order, finalise ----------
@@ -598,35 +637,36 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   using C = ClassBig;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ng = p.ng;
-  const unsigned ntri = (unsigned)ng * (ng + 1) / 2;
-  unsigned* tri = (unsigned*)smem;
-  unsigned* marg = tri + ((ntri + 3) & ~3u);
+  const int n_off = p.n_dist * p.n_dirs;
+  const int G = glcm_group(ng, n_off), n_grp = (n_off + G - 1) / G;
+  const unsigned ntri = (unsigned)ng * (ng + 1) / 2, tstride = (ntri + 3) & ~3u;
+  unsigned* tris = (unsigned*)smem;  // [G][tstride]
+  unsigned* marg = tris + (size_t)G * tstride;
   unsigned* px = marg;
   unsigned* psum = marg + ng;       // index a + b
   unsigned* pdiff = marg + 3 * ng;  // index b - a
+  uint16_t* rast = (uint16_t*)(marg + 4 * ng);  // [glcm_raster_cells] bins of padded cells
   __shared__ double red[C::NW * RED_MAX];
   __shared__ long long s_i64[16];
   __shared__ A s_res[RED_MAX];
   __shared__ int s_flag;
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
-  const int n_big = (int)(ctr >> 32);
-  const int n_off = p.n_dist * p.n_dirs;
-  const unsigned long long n_units = (unsigned long long)(unsigned)ctr * n_off;
+  const int n_big = big_count(ctr);
+  const unsigned n_units = big_units2(ctr);
   const T* img = (const T*)p.img;
-  for (unsigned long long g = blockIdx.x; g < n_units; g += gridDim.x) {
-    const unsigned u = (unsigned)(g / n_off);
-    const int oi = (int)(g - (unsigned long long)u * n_off);
-    const int di = oi / p.n_dirs, dir = oi - di * p.n_dirs;
-    const int b = big_of_unit(p, n_big, u);
+  constexpr uint16_t SENT = 0xFFFF;  // padded cell outside the ROI
+  for (unsigned g = blockIdx.x; g < n_units; g += gridDim.x) {
+    const int b = big_of_unit(p, n_big, g, true);
     const BigRoi br = p.big[b];
-    const int chunk = (int)(u - br.u1);
+    const int loc = (int)(g - br.u2);
+    const int sp = loc / n_grp, grp = loc - sp * n_grp;
     const RoiInfo r = p.rois[br.item];
     BigBox bx;
     bx.init(p, r, NDIM);
-    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
     unsigned* reg = p.arena + br.arena;
-    const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
+    const int o0 = grp * G, og = min(G, n_off - o0);
     const unsigned vmin = r.vmin, vmax = r.vmax;
     const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
     FastDiv fd;
@@ -636,115 +676,215 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       if constexpr (Enc<T>::INTEGER) return min(fd.div((unsigned)ng * (e - vmin)), (unsigned)(ng - 1));
       else return bin_float(Enc<T>::decf(e), fmn, fmx, ng);
     };
-    const int dx = p.off[oi][0], dy = p.off[oi][1], dz = p.off[oi][2];
-    const int64_t olin = ((int64_t)dz * p.ny + dy) * p.nx + dx;
-    for (unsigned i = tid; i < ntri; i += BIG_NT) tri[i] = 0;
-    __syncthreads();
-    chunk_pixels<T>(p, bx, c0, c1, [&](int x, int y, int z, unsigned e) {
-      const int X = x + dx, Y = y + dy, Z = z + dz;
-      if (X < 0 || Y < 0 || Z < 0 || X >= bx.W || Y >= bx.H || Z >= bx.D) return;
-      const int64_t off = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x + olin;
-      if (__ldg(p.mask + off) != bx.label) return;
-      const unsigned a = gbin(e), bb = gbin(Enc<T>::enc(__ldg(img + off)));
-      atomicAdd(&tri[a < bb ? tri_idx(a, bb) : tri_idx(bb, a)], 1u);
-    });
-    __syncthreads();
-    if (br.nch > 1) {
-      unsigned* gt = reg + L.tri + (size_t)oi * ntri;
-      for (unsigned i = tid; i < ntri; i += BIG_NT)
-        if (tri[i]) atomicAdd(gt + i, tri[i]);
-      if (!last_arrival(reg + L.ctr + 4 + oi, (unsigned)br.nch, &s_flag)) continue;
-      for (unsigned i = tid; i < ntri; i += BIG_NT) tri[i] = __ldcg(gt + i);
-      __syncthreads();
-    }
-
-    // ---- GLCM sums of this offset from the complete triangle ---------------
-    const bool dbg = p.dbg_roi == (int64_t)br.item;
-    for (int i = tid; i < 4 * ng; i += BIG_NT) marg[i] = 0;
-    __syncthreads();
-    long long iv[GI];
+    for (unsigned i = tid; i < (unsigned)og * tstride; i += BIG_NT) tris[i] = 0;
+    if (br.gsp > 0) {
+      // ---- raster path: the span's padded cells plus a forward halo ----------
+      // Padded box (W + 2d) x (H + 2d) [x (D + 2d)]; every unordered pair of
+      // positions at offset +-o is counted once from its earlier cell in
+      // raster order, at displacement |o| (the matrix is symmetric).
+      const int dd = p.pad;
+      const int Wp = bx.W + 2 * dd, Hp = bx.H + 2 * dd, Dp = NDIM == 3 ? bx.D + 2 * dd : 1;
+      const unsigned pcells = (unsigned)Wp * (unsigned)Hp * (unsigned)Dp;
+      const unsigned P0 = (unsigned)sp * (unsigned)br.gsp;
+      const unsigned span = min((unsigned)br.gsp, pcells - P0);
+      const unsigned len = min((unsigned)br.gsp + (unsigned)br.hal, pcells - P0);
+      FastDiv fwp, fhp;
+      fwp.init((unsigned)Wp);
+      fhp.init((unsigned)Hp);
+      int disp[MAX_DIRS];
 #pragma unroll
-    for (int k = 0; k < GI; ++k) iv[k] = 0;
-    for (unsigned f = tid; f < ntri; f += BIG_NT) {
-      const unsigned cnt = tri[f];
-      if (!cnt) continue;
-      unsigned a, bb;
-      tri_ab(f, a, bb);
-      atomicAdd(&px[a], cnt);
-      atomicAdd(&px[bb], cnt);
-      atomicAdd(&psum[a + bb], 2 * cnt);
-      atomicAdd(&pdiff[bb - a], 2 * cnt);
-      const long long Cm = 2 * (long long)cnt;
-      const long long k = a + bb + 2, d = bb - a, k2 = k * k;
-      iv[0] += Cm;
-      iv[1] += Cm * k;
-      iv[2] += Cm * k2;
-      iv[3] += Cm * k2 * k;
-      iv[4] += Cm * k2 * k2;
-      iv[5] += Cm * d;
-      iv[6] += Cm * d * d;
-      iv[7] += (long long)cnt * ((long long)(a + 1) * (a + 1) + (long long)(bb + 1) * (bb + 1));
-      const long long Cc = a == bb ? 2 * (long long)cnt : (long long)cnt;
-      const long long mult = a == bb ? 1 : 2;
-      iv[8] += mult * Cc * Cc;
-      iv[9] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
-      iv[11] = Cc > iv[11] ? Cc : iv[11];
-      if (dbg) {
-        p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + bb] = (unsigned)Cc;
-        p.dbg_glcm[(int64_t)oi * ng * ng + bb * ng + a] = (unsigned)Cc;
+      for (int j = 0; j < MAX_DIRS; ++j) {
+        const int oj = o0 + (j < og ? j : 0);
+        const int ds = (p.off[oj][2] * Hp + p.off[oj][1]) * Wp + p.off[oj][0];
+        disp[j] = ds < 0 ? -ds : ds;
       }
-    }
-    __syncthreads();
-    long long Tl;
-    {
-      long long t1[1] = {0};
-      for (int a = tid; a < ng; a += BIG_NT) t1[0] += px[a];
-      block_sum_i64<C, 1>(t1, red, s_i64 + 13);
-      Tl = s_i64[13];
-    }
-    if (Tl == 0) {  // no pair for this offset: every feature NaN
-      store_gacc<A>(p, br.item, oi, s_i64, s_res, true);
-      __syncthreads();
-      continue;
-    }
-    A fv[GF];
+      // stage: bins of the ROI's cells, SENT elsewhere (loads of BIG_U cells in flight)
+      for (unsigned ib = 0; ib < len; ib += BIG_U * BIG_NT) {
+        int lab[BIG_U];
+        T val[BIG_U];
 #pragma unroll
-    for (int k = 0; k < GF; ++k) fv[k] = 0;
-    const float Tf = (float)Tl;
-    const A invT = (A)1 / (A)Tl, ngA = (A)ng;
-    for (int a = tid; a < ng; a += BIG_NT) {
-      if (!px[a]) continue;
-      const A pr = (A)px[a] * invT;
-      fv[0] -= pr * alog2(pr);
+        for (int u = 0; u < BIG_U; ++u) {
+          const unsigned i = ib + u * BIG_NT + tid;
+          lab[u] = 0;
+          if (i < len) {
+            const unsigned P = P0 + i;
+            const unsigned q = fwp.div(P), zq = fhp.div(q);
+            const int x = (int)(P - q * (unsigned)Wp) - dd, y = (int)(q - zq * (unsigned)Hp) - dd;
+            const int z = NDIM == 3 ? (int)zq - dd : 0;
+            if (x >= 0 && y >= 0 && z >= 0 && x < bx.W && y < bx.H && z < bx.D) {
+              const int64_t off = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
+              lab[u] = __ldg(p.mask + off);
+              val[u] = __ldg(img + off);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < BIG_U; ++u) {
+          const unsigned i = ib + u * BIG_NT + tid;
+          if (i < len) rast[i] = lab[u] == bx.label ? (uint16_t)gbin(Enc<T>::enc(val[u])) : SENT;
+        }
+      }
+      __syncthreads();
+      // count: every ROI cell of the span with its neighbour at each offset of
+      // the group; equal cells in consecutive lanes merge into one atomic
+      for (unsigned ib = 0; ib < span; ib += BIG_NT) {
+        const unsigned i = ib + tid;
+        const unsigned a = i < span ? rast[i] : SENT;
+#pragma unroll
+        for (int j = 0; j < MAX_DIRS; ++j) {
+          if (j >= og) break;  // uniform
+          unsigned key = 0xFFFFFFFFu;
+          if (a != SENT) {
+            const unsigned bb = rast[i + disp[j]];
+            if (bb != SENT) key = a < bb ? tri_idx(a, bb) : tri_idx(bb, a);
+          }
+          const unsigned n = run_leader(key, 0xFFFFFFFFu);
+          if (n) atomicAdd(&tris[(size_t)j * tstride + key], n);
+        }
+      }
+      __syncthreads();
+    } else {
+      // ---- global-memory path (the halo does not fit): BIG_GSPAN chunks ------
+      __syncthreads();
+      const unsigned c0 = (unsigned)sp * BIG_GSPAN * BIG_CHUNK;
+      const unsigned c1 = (unsigned)min((unsigned long long)bx.cells,
+                                        (unsigned long long)c0 + (unsigned long long)BIG_GSPAN * BIG_CHUNK);
+      chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e) {
+        const unsigned a = in ? gbin(e) : 0u;
+        const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
+        int nl[MAX_DIRS];
+        T nv[MAX_DIRS];
+#pragma unroll
+        for (int j = 0; j < MAX_DIRS; ++j) {
+          nl[j] = 0;
+          if (j < og && in) {
+            const int dx = p.off[o0 + j][0], dy = p.off[o0 + j][1], dz = p.off[o0 + j][2];
+            const int X = x + dx, Y = y + dy, Z = z + dz;
+            if (X >= 0 && Y >= 0 && Z >= 0 && X < bx.W && Y < bx.H && Z < bx.D) {
+              const int64_t off = here + ((int64_t)dz * p.ny + dy) * p.nx + dx;
+              nl[j] = __ldg(p.mask + off);
+              nv[j] = __ldg(img + off);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < MAX_DIRS; ++j) {
+          if (j >= og) break;  // uniform
+          unsigned key = 0xFFFFFFFFu;
+          if (nl[j] == bx.label) {
+            const unsigned bb = gbin(Enc<T>::enc(nv[j]));
+            key = a < bb ? tri_idx(a, bb) : tri_idx(bb, a);
+          }
+          const unsigned n = run_leader(key, 0xFFFFFFFFu);
+          if (n) atomicAdd(&tris[(size_t)j * tstride + key], n);
+        }
+      });
+      __syncthreads();
     }
-    for (int s = tid; s < 2 * ng - 1; s += BIG_NT) {
-      if (!psum[s]) continue;
-      const A pr = (A)psum[s] * invT;
-      fv[1] -= pr * alog2(pr);
+    if (br.nsp > 1) {  // add into the ROI's global triangles; the last span reduces them
+      for (int j = 0; j < og; ++j) {
+        unsigned* gt = reg + L.tri + (size_t)(o0 + j) * ntri;
+        for (unsigned i = tid; i < ntri; i += BIG_NT)
+          if (tris[(size_t)j * tstride + i]) atomicAdd(gt + i, tris[(size_t)j * tstride + i]);
+      }
+      if (!last_arrival(reg + L.ctr + 4 + grp, (unsigned)br.nsp, &s_flag)) continue;
+      for (int j = 0; j < og; ++j) {
+        const unsigned* gt = reg + L.tri + (size_t)(o0 + j) * ntri;
+        for (unsigned i = tid; i < ntri; i += BIG_NT) tris[(size_t)j * tstride + i] = __ldcg(gt + i);
+      }
+      __syncthreads();
     }
-    for (int k = tid; k < ng; k += BIG_NT) {
-      if (!pdiff[k]) continue;
-      const A pr = (A)pdiff[k] * invT, kk = (A)k;
-      fv[2] -= pr * alog2(pr);
-      fv[3] += pr / ((A)1 + kk);
-      fv[4] += pr / ((A)1 + kk * kk);
-      fv[5] += pr / ((A)1 + kk / ngA);
-      fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));
-      if (k >= 1) fv[7] += pr / (kk * kk);
+    for (int j = 0; j < og; ++j) {
+      const int oi = o0 + j;
+      const unsigned* tri = tris + (size_t)j * tstride;
+      // ---- GLCM sums of this offset from the complete triangle ---------------
+      const bool dbg = p.dbg_roi == (int64_t)br.item;
+      for (int i = tid; i < 4 * ng; i += BIG_NT) marg[i] = 0;
+      __syncthreads();
+      long long iv[GI];
+#pragma unroll
+      for (int k = 0; k < GI; ++k) iv[k] = 0;
+      for (unsigned f = tid; f < ntri; f += BIG_NT) {
+        const unsigned cnt = tri[f];
+        if (!cnt) continue;
+        unsigned a, bb;
+        tri_ab(f, a, bb);
+        atomicAdd(&px[a], cnt);
+        atomicAdd(&px[bb], cnt);
+        atomicAdd(&psum[a + bb], 2 * cnt);
+        atomicAdd(&pdiff[bb - a], 2 * cnt);
+        const long long Cm = 2 * (long long)cnt;
+        const long long k = a + bb + 2, d = bb - a, k2 = k * k;
+        iv[0] += Cm;
+        iv[1] += Cm * k;
+        iv[2] += Cm * k2;
+        iv[3] += Cm * k2 * k;
+        iv[4] += Cm * k2 * k2;
+        iv[5] += Cm * d;
+        iv[6] += Cm * d * d;
+        iv[7] += (long long)cnt * ((long long)(a + 1) * (a + 1) + (long long)(bb + 1) * (bb + 1));
+        const long long Cc = a == bb ? 2 * (long long)cnt : (long long)cnt;
+        const long long mult = a == bb ? 1 : 2;
+        iv[8] += mult * Cc * Cc;
+        iv[9] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
+        iv[11] = Cc > iv[11] ? Cc : iv[11];
+        if (dbg) {
+          p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + bb] = (unsigned)Cc;
+          p.dbg_glcm[(int64_t)oi * ng * ng + bb * ng + a] = (unsigned)Cc;
+        }
+      }
+      __syncthreads();
+      long long Tl;
+      {
+        long long t1[1] = {0};
+        for (int a = tid; a < ng; a += BIG_NT) t1[0] += px[a];
+        block_sum_i64<C, 1>(t1, red, s_i64 + 13);
+        Tl = s_i64[13];
+      }
+      if (Tl == 0) {  // no pair for this offset: every feature NaN
+        store_gacc<A>(p, br.item, oi, s_i64, s_res, true);
+        __syncthreads();
+        continue;
+      }
+      A fv[GF];
+#pragma unroll
+      for (int k = 0; k < GF; ++k) fv[k] = 0;
+      const float Tf = (float)Tl;
+      const A invT = (A)1 / (A)Tl, ngA = (A)ng;
+      for (int a = tid; a < ng; a += BIG_NT) {
+        if (!px[a]) continue;
+        const A pr = (A)px[a] * invT;
+        fv[0] -= pr * alog2(pr);
+      }
+      for (int s = tid; s < 2 * ng - 1; s += BIG_NT) {
+        if (!psum[s]) continue;
+        const A pr = (A)psum[s] * invT;
+        fv[1] -= pr * alog2(pr);
+      }
+      for (int k = tid; k < ng; k += BIG_NT) {
+        if (!pdiff[k]) continue;
+        const A pr = (A)pdiff[k] * invT, kk = (A)k;
+        fv[2] -= pr * alog2(pr);
+        fv[3] += pr / ((A)1 + kk);
+        fv[4] += pr / ((A)1 + kk * kk);
+        fv[5] += pr / ((A)1 + kk / ngA);
+        fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));
+        if (k >= 1) fv[7] += pr / (kk * kk);
+      }
+      for (unsigned f = tid; f < ntri; f += BIG_NT) {
+        const unsigned cnt = tri[f];
+        if (!cnt) continue;
+        unsigned a, bb;
+        tri_ab(f, a, bb);
+        const long long mult = a == bb ? 1 : 2;
+        const unsigned Cc = a == bb ? 2 * cnt : cnt;
+        const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
+        iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
+      }
+      block_sum_glcm<C, A>(iv, fv, red, s_i64, s_res);
+      store_gacc<A>(p, br.item, oi, s_i64, s_res, false);  // features: k_glcm_final
+      __syncthreads();
     }
-    for (unsigned f = tid; f < ntri; f += BIG_NT) {
-      const unsigned cnt = tri[f];
-      if (!cnt) continue;
-      unsigned a, bb;
-      tri_ab(f, a, bb);
-      const long long mult = a == bb ? 1 : 2;
-      const unsigned Cc = a == bb ? 2 * cnt : cnt;
-      const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
-      iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
-    }
-    block_sum_glcm<C, A>(iv, fv, red, s_i64, s_res);
-    store_gacc<A>(p, br.item, oi, s_i64, s_res, false);  // features: k_glcm_final
-    __syncthreads();
   }
 }
 
@@ -762,14 +902,14 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
   __shared__ int s_idx[4];
   __shared__ A s_sc[16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n_big = (int)(*p.big_ctr >> 32);
+  const int n_big = big_count(*p.big_ctr);
   const float* img = (const float*)p.img;
   for (int b = blockIdx.x; b < n_big; b += gridDim.x) {
     const BigRoi br = p.big[b];
     const RoiInfo r = p.rois[br.item];
     BigBox bx;
     bx.init(p, r, ndim);
-    const BigLayout L = big_layout(p, br.nch, br.range, r.n);
+    const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
     const int n = (int)r.n;
     unsigned* src = p.arena + br.arena + L.fsort;
     unsigned* dst = src + n;
@@ -908,9 +1048,7 @@ cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
   if ((e = big_launch<k_big_p1<T, NDIM, A>>(smem1, nsm, p, st)) != cudaSuccess) return e;
   if ((e = big_launch<k_big_p2<T, NDIM, A>>(0, nsm, p, st)) != cudaSuccess) return e;
   if (p.need & NEED_GLCM) {
-    const int ntri = p.ng * (p.ng + 1) / 2;
-    const int smemg = 4 * (((ntri + 3) & ~3) + 4 * p.ng);
-    if ((e = big_launch<k_big_glcm<T, NDIM, A>>(smemg, nsm, p, st)) != cudaSuccess) return e;
+    if ((e = big_launch<k_big_glcm<T, NDIM, A>>(GLCM_SMEM_BYTES, nsm, p, st)) != cudaSuccess) return e;
   }
   if (!Enc<T>::INTEGER && (p.need & NEED_ORDER)) {
     auto kern = k_big_order_f<A>;

@@ -347,28 +347,59 @@ __global__ void k_setup(KParams p) {
     if ((int64_t)i >= p.cap_roi) continue;  // no room for its output row
     if (cls == 3) {  // multi-block class: register the ROI and its arena region
       const unsigned long long cells3 = (unsigned long long)r.w * r.h * (p.ndim == 3 ? r.d : 1);
-      if (!p.big || cells3 >= (1ull << 32)) {
+      if (!p.big || cells3 >= (1ull << 30)) {
         atomicOr(p.err, E_TOO_LARGE);
         continue;
       }
       const int nch = (int)((cells3 + BIG_CHUNK - 1) / BIG_CHUNK);
       const unsigned range = (p.dtype != NYX_F32 && (p.need & NEED_ORDER)) ? r.vmax - r.vmin + 1 : 0u;
-      const BigLayout L = big_layout(p, nch, range, r.n);
+      // GLCM spans: a raster of padded cells in shared memory when the largest
+      // neighbour displacement leaves room for at least 2,048 cells, else
+      // spans of BIG_GSPAN chunks reading neighbours from global memory
+      int gsp = 0, nsp = 0, hal = 0, n_g = 0;
+      if (p.need & NEED_GLCM) {
+        const int dd = p.pad, n_off = p.n_dist * p.n_dirs;
+        const long long Wp = r.w + 2 * dd, Hp = r.h + 2 * dd, Dp = p.ndim == 3 ? r.d + 2 * dd : 1;
+        long long hmax = 0;
+        for (int o = 0; o < n_off; ++o) {
+          long long ds = ((long long)p.off[o][2] * Hp + p.off[o][1]) * Wp + p.off[o][0];
+          ds = ds < 0 ? -ds : ds;
+          hmax = ds > hmax ? ds : hmax;
+        }
+        const long long rc = glcm_raster_cells(p.ng, n_off), pcells = Wp * Hp * Dp;
+        if (rc - hmax >= 2048 && pcells < (1ll << 31)) {
+          gsp = (int)(((rc - hmax) / 512) * 512);
+          hal = (int)hmax;
+          nsp = (int)((pcells + gsp - 1) / gsp);
+        } else {
+          nsp = (nch + BIG_GSPAN - 1) / BIG_GSPAN;
+        }
+        const int G = glcm_group(p.ng, n_off);
+        n_g = nsp * ((n_off + G - 1) / G);
+      }
+      const BigLayout L = big_layout(p, nch, nsp, range, r.n);
       const unsigned long long a = atomicAdd(p.big_used, L.total);
-      if (a + L.total > p.arena_cap) {
+      const unsigned long long u1c = atomicAdd(p.big_used + 1, (unsigned long long)nch);
+      const unsigned long long u2c = atomicAdd(p.big_used + 2, (unsigned long long)n_g);
+      if (a + L.total > p.arena_cap || u1c + nch > 0x3FFFFFull || u2c + n_g > 0x3FFFFFull) {
         atomicOr(p.err, E_TOO_LARGE);
         continue;
       }
-      // one atomic hands out the big-ROI index and the first pass unit, so
-      // u1 grows with the index
-      const unsigned long long old = atomicAdd(p.big_ctr, (1ull << 32) | (unsigned long long)nch);
+      // one atomic hands out the big-ROI index and its first pass and GLCM
+      // units, so both grow with the index
+      const unsigned long long old =
+          atomicAdd(p.big_ctr, (1ull << 44) | ((unsigned long long)nch << 22) | (unsigned long long)n_g);
       BigRoi br;
       br.item = (int)i;
       br.nch = nch;
-      br.u1 = (unsigned)old;
+      br.u1 = big_units1(old);
+      br.u2 = big_units2(old);
+      br.nsp = nsp;
+      br.gsp = gsp;
+      br.hal = hal;
       br.range = range;
       br.arena = a;
-      p.big[old >> 32] = br;
+      p.big[big_count(old)] = br;
       continue;
     }
     unsigned q = atomicAdd(&p.qlen[cls], 1u);
@@ -438,9 +469,9 @@ __global__ void k_begin(KParams p) {
     p.qlen[t] = 0;
     p.qhead[t] = 0;
   }
-  if (t == 0 && p.big_ctr) {
-    *p.big_ctr = 0;
-    *p.big_used = 0;
+  if (t < 3 && p.big_ctr) {
+    if (t == 0) *p.big_ctr = 0;
+    p.big_used[t] = 0;
   }
   for (int b = t; b < p.batch; b += blockDim.x) {
     p.img_vmin[b] = 0xFFFFFFFFu;

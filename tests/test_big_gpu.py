@@ -182,3 +182,20 @@ def test_blobbatch_64x512_sampled():
     g, o = _sampled(w, 2, 32, n_random=16)
     assert o["AREA"].max() > 8192
     _assert_parity(g, o, 2)
+
+
+def test_big_3d_wide_plane_global_neighbours():
+    """A slab ROI with 300x300 planes: its one-plane halo does not fit beside
+    the co-occurrence triangles in shared memory, so its spans read
+    neighbours from global memory; a smaller ROI in the same volume takes the
+    shared-memory raster path."""
+    rng = np.random.default_rng(2306)
+    img = rng.integers(-200, 1800, size=(8, 320, 320)).astype(np.int16)
+    mask = np.zeros(img.shape, dtype=np.int32)
+    mask[2:6, 10:310, 12:312] = 3
+    zz, yy, xx = np.ogrid[0:8, 0:320, 0:320]
+    mask[((zz - 4) / 3.5) ** 2 + ((yy - 160) / 60.0) ** 2 + ((xx - 160) / 70.0) ** 2 <= 1.0] = 9
+    w = W.Workload("slab3d", img, mask, 3, params=dict(glcm_levels=64, dists=(1,), hist_bins=256), meta={"n_roi": 2})
+    ex, g, o = _run(w)
+    assert list(g["LABEL"]) == [3, 9]
+    _assert_parity(g, o, 3)
