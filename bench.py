@@ -126,6 +126,21 @@ def roi_classes(w):
     return px, rows
 
 
+def reduce_over_ranks(dist, device, t_ms: float, units: int):
+    """Whole-job figures of independent per-rank problems (weak scaling, no
+    collective on the data path): the slowest rank's time and the units that
+    all ranks processed."""
+    if dist is None:
+        return t_ms, units
+    import torch
+
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    nn = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(nn)
+    return float(tt.item()), int(nn.item())
+
+
 def make_workload(name: str, rank: int):
     from paper_2603_12016_gb300 import workloads as W
 
@@ -304,16 +319,7 @@ def main() -> int:
         ms, n_roi = timed(ex, args.steps, args.warmup)
     clocks = clk.summary()
     phases = phase_profile(ex, min(args.steps, 10))
-    t_step = statistics.median(ms)
-    if dist is not None:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-        nn = torch.tensor([n_roi], device=dev, dtype=torch.int64)
-        dist.all_reduce(nn)
-        n_total = int(nn.item())
-    else:
-        n_total = n_roi
+    t_step, n_total = reduce_over_ranks(dist, dev, statistics.median(ms), n_roi)
     value = n_total / (t_step * 1e-3)
     px_total = w.image.size * world
     n_col = len(ex.columns)
@@ -363,11 +369,7 @@ def main() -> int:
         t.synchronize()
         if i >= args.warmup:
             e2e_ms.append(s.elapsed_time(t))
-    e2e_t = statistics.median(e2e_ms)
-    if dist is not None:
-        tt = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+    e2e_t, _ = reduce_over_ranks(dist, dev, statistics.median(e2e_ms), n_roi)
     e2e = {"value": n_total / (e2e_t * 1e-3), "unit": "ROIs/s",
            "h2d_bytes_per_step": int(w.image.nbytes + w.mask.nbytes),
            "d2h_bytes_per_step": int(8 * n_roi * n_col + (4 * w.image.size if bwd else 0)), "ms_per_step": e2e_t}
