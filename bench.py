@@ -393,9 +393,9 @@ def main() -> int:
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, 20.0)
     # begin, scan, key sort, setup, 3 block classes, reset; multi-block class:
-    # zero, pass 1, pass 2 (+ GLCM, + float sort); GLCM features
+    # zero, pass 1, pass 2, sorted order statistics (+ GLCM); GLCM features
     glcm = w.params["glcm_levels"] > 0
-    launches_per_step = 8 + 3 + (1 if glcm else 0) + (1 if str(w.image.dtype) == "float32" else 0) + (1 if glcm else 0)
+    launches_per_step = 8 + 4 + (1 if glcm else 0) + (1 if glcm else 0)
     if bwd:  # begin, scan, key sort, setup, coefficients, per-pixel gradient, reset
         launches_per_step += 7
     line = {

@@ -172,6 +172,34 @@ nyx_status nyx_set_class_limits(nyx_plan* plan, const int32_t* lim_pix);
 nyx_status nyx_autotune(nyx_plan* plan, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                         int reps, void* stream, int32_t* h_lim_pix);
 
+/* Source of one tile of a mosaic for nyx_extract_tiles: fill h_img (w x h
+ * pixels of the plan's dtype, row-major dense) and h_mask (int32, w x h) with
+ * the tile whose top-left pixel is (x0, y0).  Both buffers are pinned host
+ * memory owned by the library, valid during the call only.  Return 0 on
+ * success; any other value aborts the extraction. */
+typedef int (*nyx_tile_fn)(void* user, int64_t x0, int64_t y0, int64_t w, int64_t h, void* h_img, int32_t* h_mask);
+
+/* Streamed extraction of a large 2D mosaic (the plan's dims; batch 1), the
+ * whole-slide regime of "Results, Scalability" where host-to-device traffic
+ * decides GPU benefit.  Tiles of tile_w x tile_h (edge tiles smaller) are
+ * requested from `fn` in row-major tile order into two pinned staging
+ * buffers, copied into d_img / d_mask (caller-allocated device buffers of
+ * the whole mosaic, 16-byte aligned, filled by this call), and every band of
+ * tile rows is label-scanned as soon as its tiles are in, while the host
+ * produces the next tiles.  After the last band the per-ROI kernels run on
+ * the device-resident mosaic, so ROIs crossing tile borders are merged in the
+ * label table (counts, bounding boxes, intensity ranges) and processed whole.
+ * Output as nyx_extract (d_table FP64 [cap_roi x n_col], rows in ascending
+ * label order; d_n_roi device int64 or NULL).  flags: NYX_SYNC only.  The
+ * call returns once every tile has been handed to the stream.  Plans above
+ * 16,384 ROIs sort their keys with a multi-block merge sort.  Errors:
+ * NYX_ERR_ARG (null fn/pointers, bad tile extent, the source failed),
+ * NYX_ERR_SHAPE (plan not 2D or batch > 1), NYX_ERR_OOM (staging), and with
+ * NYX_SYNC the device-detected codes. */
+nyx_status nyx_extract_tiles(nyx_plan* plan, int64_t tile_w, int64_t tile_h, nyx_tile_fn fn, void* user, void* d_img,
+                             int32_t* d_mask, double* d_table, int64_t cap_roi, int64_t* d_n_roi, uint32_t flags,
+                             void* stream);
+
 /* Synchronise `stream` and return the device error word of the plan's last
  * calls as a status (NYX_OK if clean); clears the word. */
 nyx_status nyx_sync_status(nyx_plan* plan, void* stream);

@@ -25,6 +25,8 @@ cudaError_t launch_big_i16(const KParams& p, int fp64, int nsm, cudaStream_t st)
 cudaError_t launch_big_f32(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_glcm_final(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_begin(const KParams& p, cudaStream_t st);
+cudaError_t launch_scan(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_reset(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_init_table(const KParams& p, unsigned cap, cudaStream_t st);
@@ -98,6 +100,10 @@ struct nyx_plan {
   int64_t graph_used[NGRAPH] = {};
   int64_t graph_clock = 0;
   int64_t graph_captures = 0;
+  // pinned staging buffers of the streamed mosaic path (two tiles in flight)
+  void* stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
 };
 
 static void drop_graph(nyx_plan* pl) {
@@ -357,12 +363,14 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   // histograms, co-occurrence triangles, partial sums, float sort buffers).
   // Sorting needs 2 words per ROI pixel; the rest is per-ROI bookkeeping.
   const unsigned long long total_px = (unsigned long long)p.batch * p.dims[0] * p.dims[1] * p.dims[2];
-  const unsigned long long arena_words = 3ull * total_px + (1ull << 24);
+  unsigned long long arena_words = 3ull * total_px + (1ull << 24);
+  if (arena_words > (1ull << 30)) arena_words = 1ull << 30;  // 4 GiB: large mosaics hold few multi-block ROIs
   const size_t o_arena = take(4ull * arena_words);
   // per (ROI, offset) GLCM accumulators (GI int64 + GF sums in 8-byte slots)
-  const int64_t grows = mr < SORT_CAP ? mr : SORT_CAP;
   const int n_off_all = p.glcm_levels > 0 ? p.n_dist * (p.ndim == 3 ? 13 : 4) : 0;
-  const size_t o_gacc = take((size_t)grows * n_off_all * (8 * (GI_HOST + GF_HOST)));
+  const size_t o_gacc = take((size_t)mr * n_off_all * (8 * (GI_HOST + GF_HOST)));
+  // second key buffer of the multi-block key sort
+  const size_t o_sorttmp = take(mr > SORT_CAP ? 8ull * mr : 0);
   cudaError_t e = cudaMalloc(&pl->ws, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -432,6 +440,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.arena = (unsigned*)(w + o_arena);
   k.arena_cap = arena_words;
   k.gacc = (unsigned char*)(w + o_gacc);
+  k.sort_tmp = mr > SORT_CAP ? (unsigned long long*)(w + o_sorttmp) : nullptr;
   pl->d_col_map = (int*)(w + o_cmap);
   k.col_map = pl->d_col_map;
   k.n_col = (int)pl->col_names.size();
@@ -465,6 +474,10 @@ void nyx_plan_destroy(nyx_plan* pl) {
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   drop_graph(pl);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (pl->stage[i]) cudaFreeHost(pl->stage[i]);
+    if (pl->stage_ev[i]) cudaEventDestroy(pl->stage_ev[i]);
+  }
   cudaFree(pl->ws);
   if (pl->d_saved) cudaFree(pl->d_saved);
   if (pl->d_dbg) cudaFree(pl->d_dbg);
@@ -540,6 +553,8 @@ nyx_status nyx_count_rois(nyx_plan* pl, const void* d_img, const int32_t* d_mask
 // The launch sequence of one extraction (label scan, key sort + setup, the
 // four size classes, GLCM features, table reset).  `ev` (profiling) records
 // the phase boundaries; it is null when the sequence is captured.
+static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st);
+
 static nyx_status enqueue_extract(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st) {
   nyx_ctx* c = pl->ctx;
   nyx_status s;
@@ -547,6 +562,14 @@ static nyx_status enqueue_extract(nyx_plan* pl, const KParams& k, cudaEvent_t* e
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[0], st));
   if ((s = run_front(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[1], st));
+  return enqueue_back(pl, k, ev, st);
+}
+
+// Everything after the label scan: key sort + setup, the four size classes,
+// GLCM features, table reset.
+static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st) {
+  nyx_ctx* c = pl->ctx;
+  nyx_status s;
   if ((s = run_sort_setup(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[2], st));
   const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
@@ -667,6 +690,90 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
   } else {
     if ((s = enqueue_extract(pl, k, nullptr, st)) != NYX_OK) return s;
   }
+  if (flags & NYX_SYNC) return read_err(pl, st);
+  return NYX_OK;
+}
+
+nyx_status nyx_extract_tiles(nyx_plan* pl, int64_t tile_w, int64_t tile_h, nyx_tile_fn fn, void* user, void* d_img,
+                             int32_t* d_mask, double* d_table, int64_t cap_roi, int64_t* d_n_roi, uint32_t flags,
+                             void* stream) {
+  if (!pl || !fn) return NYX_ERR_ARG;
+  nyx_ctx* c = pl->ctx;
+  const nyx_params& prm = pl->prm;
+  if (prm.ndim != 2 || prm.batch != 1) return fail(c, NYX_ERR_SHAPE, "tiled extraction needs a 2D plan with batch 1");
+  if (tile_w < 1 || tile_h < 1) return fail(c, NYX_ERR_ARG, "tile extent must be positive");
+  nyx_status s = check_ptrs(pl, d_img, d_mask);
+  if (s != NYX_OK) return s;
+  if (!d_table && cap_roi > 0) return fail(c, NYX_ERR_ARG, "null table");
+  if (cap_roi < 0 || ((uintptr_t)d_table & 7)) return fail(c, NYX_ERR_ARG, "bad table or cap_roi");
+  if (flags & NYX_SAVE_FOR_BACKWARD) return fail(c, NYX_ERR_ARG, "tiled extraction does not keep backward state");
+  cudaStream_t st = (cudaStream_t)stream;
+  NYX_CUDA(c, cudaSetDevice(c->device));
+  const int64_t W = prm.dims[0], H = prm.dims[1];
+  const size_t isz = prm.dtype == NYX_F32 ? 4 : 2;
+  const int64_t tw = tile_w < W ? tile_w : W, th = tile_h < H ? tile_h : H;
+  const size_t need = (((size_t)tw * th * isz + 15) & ~(size_t)15) + (size_t)tw * th * 4;
+  if (pl->stage_bytes < need) {
+    for (int i = 0; i < 2; ++i) {
+      if (pl->stage[i]) cudaFreeHost(pl->stage[i]);
+      pl->stage[i] = nullptr;
+    }
+    pl->stage_bytes = 0;
+    for (int i = 0; i < 2; ++i)
+      if (cudaHostAlloc(&pl->stage[i], need, cudaHostAllocDefault) != cudaSuccess) {
+        pl->stage[i] = nullptr;
+        return fail(c, NYX_ERR_OOM, "pinned staging allocation of %zu bytes failed", need);
+      }
+    pl->stage_bytes = need;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!pl->stage_ev[i]) NYX_CUDA(c, cudaEventCreateWithFlags(&pl->stage_ev[i], cudaEventDisableTiming));
+  KParams k;
+  memcpy(&k, &pl->kp, sizeof k);
+  k.img = d_img;
+  k.mask = d_mask;
+  k.vec = (k.nx % 4) == 0;
+  k.table = d_table;
+  k.cap_roi = cap_roi < prm.max_rois ? cap_roi : prm.max_rois;
+  k.n_roi_out = d_n_roi;
+  pl->have_saved = false;
+  NYX_CUDA(c, launch_begin(k, st));
+  // make sure both staging buffers are free before the first fill
+  for (int i = 0; i < 2; ++i) NYX_CUDA(c, cudaEventRecord(pl->stage_ev[i], st));
+  int slot = 0;
+  bool failed = false;
+  for (int64_t y0 = 0; y0 < H && !failed; y0 += tile_h) {
+    const int64_t h = H - y0 < tile_h ? H - y0 : tile_h;
+    for (int64_t x0 = 0; x0 < W; x0 += tile_w) {
+      const int64_t w = W - x0 < tile_w ? W - x0 : tile_w;
+      NYX_CUDA(c, cudaEventSynchronize(pl->stage_ev[slot]));  // its previous copy is done
+      unsigned char* himg = (unsigned char*)pl->stage[slot];
+      int32_t* hmask = (int32_t*)(himg + (((size_t)w * h * isz + 15) & ~(size_t)15));
+      if (fn(user, x0, y0, w, h, himg, hmask) != 0) {
+        failed = true;
+        break;
+      }
+      NYX_CUDA(c, cudaMemcpy2DAsync((unsigned char*)d_img + ((size_t)y0 * W + x0) * isz, (size_t)W * isz, himg,
+                                    (size_t)w * isz, (size_t)w * isz, (size_t)h, cudaMemcpyHostToDevice, st));
+      NYX_CUDA(c, cudaMemcpy2DAsync(d_mask + (size_t)y0 * W + x0, (size_t)W * 4, hmask, (size_t)w * 4, (size_t)w * 4,
+                                    (size_t)h, cudaMemcpyHostToDevice, st));
+      NYX_CUDA(c, cudaEventRecord(pl->stage_ev[slot], st));
+      slot ^= 1;
+    }
+    if (failed) break;
+    // the band's tiles are in: label-scan its rows while the next band streams
+    k.scan_row0 = y0;
+    k.scan_row1 = y0 + h;
+    NYX_CUDA(c, launch_scan(k, c->nsm, st));
+  }
+  k.scan_row0 = 0;
+  k.scan_row1 = 0;
+  if (failed) {  // return the label table to its empty state
+    run_reset(pl, k, st);
+    cudaStreamSynchronize(st);
+    return fail(c, NYX_ERR_ARG, "tile source reported an error");
+  }
+  if ((s = enqueue_back(pl, k, nullptr, st)) != NYX_OK) return s;
   if (flags & NYX_SYNC) return read_err(pl, st);
   return NYX_OK;
 }

@@ -84,8 +84,7 @@ static cudaError_t launch_final_t(const KParams& p, int nsm, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (dev < 64) configured[dev] = smem;
   }
-  int64_t rows = p.cap_roi < p.max_rois ? p.cap_roi : p.max_rois;
-  if (rows > SORT_CAP) rows = SORT_CAP;
+  const int64_t rows = p.cap_roi < p.max_rois ? p.cap_roi : p.max_rois;
   int64_t nb = (rows + rpb - 1) / rpb;
   if (nb > 8ll * nsm) nb = 8ll * nsm;
   if (nb < 1) nb = 1;

@@ -186,6 +186,10 @@ struct KParams {
   unsigned* arena;
   unsigned long long arena_cap;    // words
   unsigned char* gacc;             // [max rows][n_off] GLCM accumulators
+  // label scan over rows [scan_row0, scan_row1) of the batch (scan_row1 = 0:
+  // all rows); the mosaic path scans each band of tiles as it arrives
+  int64_t scan_row0, scan_row1;
+  unsigned long long* sort_tmp;    // second key buffer of the multi-block key sort (plans above SORT_CAP)
 };
 
 // Fields of the packed big-ROI counter (one atomic hands out the big-ROI
@@ -207,7 +211,7 @@ __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int n
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
   const bool glcm = (p.need & NEED_GLCM) != 0;
   const unsigned long long tri = glcm ? (unsigned long long)p.ng * (p.ng + 1) / 2 : 0;
-  const bool fsort = p.dtype == NYX_F32 && (p.need & NEED_ORDER);
+  const bool fsort = (p.need & NEED_ORDER) && range == 0;  // sorted values instead of a value histogram
   BigLayout L;
   unsigned long long o = 0;
   L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [4 + k] offset group k

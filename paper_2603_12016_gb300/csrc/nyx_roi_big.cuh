@@ -30,8 +30,10 @@
 //                into global ones and the last span of the group reduces
 //                them to the per-offset sums that k_glcm_final turns into
 //                features
-//   k_big_order_f  float images: one block per ROI compacts the values in
-//                raster order and sorts them (LSD radix, global memory)
+//   k_big_order  ROIs without a value histogram (float images, 16-bit ROIs
+//                whose value range exceeds their pixel count): one block
+//                per ROI compacts the values in raster order and sorts them
+//                (LSD radix, global memory)
 // "Last unit" is decided with a counter in the ROI's arena region after a
 // __threadfence, and every merge runs in chunk order, so results do not
 // depend on which block ran which unit.
@@ -888,11 +890,13 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   }
 }
 
-// Float images: order statistics of one big ROI per block from its values
-// compacted in raster order and sorted by an LSD radix sort in the ROI's
-// arena region (stable ranks from 8 ballots per digit, as in the block path).
-template <class A>
-__global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
+// Order statistics of big ROIs without a value histogram (float images, and
+// 16-bit ROIs whose value range exceeds their pixel count): one block per ROI
+// compacts the values in raster order and sorts them with an LSD radix sort
+// in the ROI's arena region (stable ranks from 8 ballots per digit, as in the
+// block path).
+template <class T, class A>
+__global__ void __launch_bounds__(BIG_NT) k_big_order(KParams p, int ndim) {
   using C = ClassBig;
   __shared__ unsigned cnt[C::NW * 256];
   __shared__ unsigned dtot[256];
@@ -903,9 +907,10 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
   __shared__ A s_sc[16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_big = big_count(*p.big_ctr);
-  const float* img = (const float*)p.img;
+  const T* img = (const T*)p.img;
   for (int b = blockIdx.x; b < n_big; b += gridDim.x) {
     const BigRoi br = p.big[b];
+    if (br.range) continue;  // value histogram path (pass 1)
     const RoiInfo r = p.rois[br.item];
     BigBox bx;
     bx.init(p, r, ndim);
@@ -924,7 +929,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
         int x, y, z;
         const int64_t off = bx.offset(c, x, y, z, p);
         in = __ldg(p.mask + off) == bx.label;
-        if (in) e = Enc<float>::enc(__ldg(img + off));
+        if (in) e = Enc<T>::enc(__ldg(img + off));
       }
       const unsigned bal = __ballot_sync(0xFFFFFFFFu, in);
       if (lane == 0) s_wc[warp] = __popc(bal);
@@ -950,7 +955,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
     // LSD radix sort, 8-bit digits; warp w owns the segment [w seg, (w+1) seg)
     const int seg = (((n + C::NW - 1) / C::NW) + 31) & ~31;
     const int lo = min(n, warp * seg), hi = min(n, lo + seg);
-    for (int shift = 0; shift < 32; shift += 8) {
+    for (int shift = 0; shift < Enc<T>::BITS; shift += 8) {
       for (int i = tid; i < C::NW * 256; i += BIG_NT) cnt[i] = 0;
       __syncthreads();
       for (int i0 = lo; i0 < hi; i0 += 32) {  // digit counts per warp
@@ -1012,7 +1017,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order_f(KParams p, int ndim) {
       dst = t;
     }
     double* row = p.table + (int64_t)br.item * p.n_col;
-    order_tail<float, C, A>(p, row, src, n, red, s_sd, s_idx, s_sc);
+    order_tail<T, C, A>(p, row, src, n, red, s_sd, s_idx, s_sc);
     __syncthreads();
   }
 }
@@ -1050,8 +1055,8 @@ cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
   if (p.need & NEED_GLCM) {
     if ((e = big_launch<k_big_glcm<T, NDIM, A>>(GLCM_SMEM_BYTES, nsm, p, st)) != cudaSuccess) return e;
   }
-  if (!Enc<T>::INTEGER && (p.need & NEED_ORDER)) {
-    auto kern = k_big_order_f<A>;
+  if (p.need & NEED_ORDER) {
+    auto kern = k_big_order<T, A>;
     int nb = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BIG_NT, 0)) != cudaSuccess) return e;
     kern<<<(nb > 0 ? nb : 1) * nsm, BIG_NT, 0, st>>>(p, NDIM);

@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (p.rows_total + TY - 1) / TY;
+  const int64_t r0 = p.scan_row0, r1 = p.scan_row1 > 0 ? p.scan_row1 : p.rows_total;
+  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (r1 - r0 + TY - 1) / TY;
   const int64_t ntiles = ntx * nty;
   unsigned im_mn = 0xFFFFFFFFu, im_mx = 0;
   int64_t im_b = -1;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
     const int64_t x0 = tx * TX;
     // decompose the warp's first row once; later rows step incrementally
     // (no 64-bit division per row)
-    int64_t row = ty * TY + warp;
+    int64_t row = r0 + ty * TY + warp;
     int64_t y = row % p.ny, zb = row / p.ny;
     int64_t z = zb % p.nz, b = zb / p.nz;
     for (int rr = warp; rr < TY; rr += SCAN_NT / 32) {
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
           }
         }
       }
-      if (row >= p.rows_total) break;
+      if (row >= r1) break;
       if (b != im_b) {  // warp-uniform: flush the running image range
         unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
         if (lane == 0 && im_b >= 0) {
@@ -307,6 +308,77 @@ __global__ void __launch_bounds__(1024) k_sort_keys(KParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-block key sort for plans above SORT_CAP ROIs: chunks of MSORT_CH keys
+// sorted in shared memory (bitonic), then merge passes doubling the run width
+// (merge path: each thread finds its split of the two runs by binary search
+// and writes MSORT_PT outputs).  Keys are distinct, so no tie rule is needed.
+constexpr int MSORT_CH = 4096;
+constexpr int MSORT_PT = 8;
+
+__global__ void __launch_bounds__(1024) k_msort_chunks(KParams p, unsigned long long* out) {
+  __shared__ unsigned long long s[MSORT_CH];
+  const unsigned n = *p.n_used;
+  if ((int64_t)n > p.max_rois) return;  // reported by k_msort_done
+  for (unsigned c0 = blockIdx.x * MSORT_CH; c0 < n; c0 += gridDim.x * MSORT_CH) {
+    for (unsigned i = threadIdx.x; i < MSORT_CH; i += blockDim.x)
+      s[i] = c0 + i < n ? p.keys[p.slot_list[c0 + i]] : EMPTY_KEY;
+    __syncthreads();
+    for (unsigned k = 2; k <= MSORT_CH; k <<= 1) {
+      for (unsigned j = k >> 1; j > 0; j >>= 1) {
+        for (unsigned i = threadIdx.x; i < MSORT_CH; i += blockDim.x) {
+          const unsigned ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long a = s[i], c = s[ixj];
+            if ((a > c) == ((i & k) == 0)) {
+              s[i] = c;
+              s[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (unsigned i = threadIdx.x; i < MSORT_CH && c0 + i < n; i += blockDim.x) out[c0 + i] = s[i];
+    __syncthreads();
+  }
+}
+
+__global__ void k_msort_merge(KParams p, const unsigned long long* src, unsigned long long* dst, unsigned w) {
+  const unsigned n = *p.n_used;
+  if ((int64_t)n > p.max_rois) return;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t * MSORT_PT < n;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned k0 = (unsigned)(t * MSORT_PT);
+    const unsigned base = k0 / (2 * w) * (2 * w);
+    const unsigned la = min(w, n - base), lb = n - base > w ? min(w, n - base - w) : 0u;
+    const unsigned long long* A = src + base;
+    const unsigned long long* B = src + base + la;
+    const unsigned d = k0 - base;
+    unsigned lo = d > lb ? d - lb : 0u, hi = min(d, la);
+    while (lo < hi) {  // number of A elements among the first d outputs
+      const unsigned a = (lo + hi) >> 1;
+      if (A[a] < B[d - a - 1]) lo = a + 1;
+      else hi = a;
+    }
+    unsigned ia = lo, ib = d - lo;
+    const unsigned end = min(base + la + lb, k0 + MSORT_PT);
+    for (unsigned k = k0; k < end; ++k) {
+      const bool takeA = ib >= lb || (ia < la && A[ia] < B[ib]);
+      dst[k] = takeA ? A[ia++] : B[ib++];
+    }
+  }
+}
+
+__global__ void k_msort_done(KParams p) {
+  const unsigned n = *p.n_used;
+  const bool over = (int64_t)n > p.max_rois;
+  *p.n_roi = over ? 0u : n;
+  if (p.n_roi_out) *p.n_roi_out = (int64_t)n;
+  if (over) atomicOr(p.err, E_ROI_CAP);
+  else if ((int64_t)n > p.cap_roi) atomicOr(p.err, E_ROI_CAP);
+}
+
 // Per ROI: gather its scan accumulator, decide the processing class and
 // append it to that class's work queue.
 __global__ void k_setup(KParams p) {
@@ -352,7 +424,10 @@ __global__ void k_setup(KParams p) {
         continue;
       }
       const int nch = (int)((cells3 + BIG_CHUNK - 1) / BIG_CHUNK);
-      const unsigned range = (p.dtype != NYX_F32 && (p.need & NEED_ORDER)) ? r.vmax - r.vmin + 1 : 0u;
+      // 16-bit order statistics from a value histogram when it is dense
+      // (range <= pixels), else from sorted values like float images
+      const unsigned span_v = r.vmax - r.vmin + 1;
+      const unsigned range = (p.dtype != NYX_F32 && (p.need & NEED_ORDER) && span_v <= r.n) ? span_v : 0u;
       // GLCM spans: a raster of padded cells in shared memory when the largest
       // neighbour displacement leaves room for at least 2,048 cells, else
       // spans of BIG_GSPAN chunks reading neighbours from global memory
@@ -500,26 +575,61 @@ cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st) {
   }
 }
 
-// key sort (one block) + per-ROI setup
+// key sort (one block up to SORT_CAP keys, else multi-block) + per-ROI setup
 cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st) {
-  unsigned np2 = 1;
-  while (np2 < (unsigned)p.max_rois && np2 < (unsigned)SORT_CAP) np2 <<= 1;
-  const int smem = (int)(8 * np2);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  static int configured[64] = {0};
-  if (dev < 64 && configured[dev] < smem) {
-    e = cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e;
+  if (p.max_rois <= SORT_CAP) {
+    unsigned np2 = 1;
+    while (np2 < (unsigned)p.max_rois) np2 <<= 1;
+    const int smem = (int)(8 * np2);
+    int dev = 0;
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    configured[dev] = smem;
+    static int configured[64] = {0};
+    if (dev < 64 && configured[dev] < smem) {
+      e = cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      configured[dev] = smem;
+    }
+    k_sort_keys<<<1, 1024, smem, st>>>(p);
+  } else {
+    // passes until the run width covers max_rois; the chunk sort writes to
+    // whichever buffer makes the last pass land in sorted_keys
+    int npass = 0;
+    for (int64_t w = MSORT_CH; w < p.max_rois; w <<= 1) ++npass;
+    unsigned long long* bufs[2] = {p.sorted_keys, p.sort_tmp};
+    int cur = npass & 1;
+    int64_t nchunk = (p.max_rois + MSORT_CH - 1) / MSORT_CH;
+    k_msort_chunks<<<(int)(nchunk < 4 * nsm ? nchunk : 4 * nsm), 1024, 0, st>>>(p, bufs[cur]);
+    int64_t nthr = (p.max_rois + MSORT_PT - 1) / MSORT_PT, nb = (nthr + 255) / 256;
+    if (nb > 8 * nsm) nb = 8 * nsm;
+    unsigned w = MSORT_CH;
+    for (int i = 0; i < npass; ++i, w <<= 1) {
+      k_msort_merge<<<(int)nb, 256, 0, st>>>(p, bufs[cur], bufs[cur ^ 1], w);
+      cur ^= 1;
+    }
+    k_msort_done<<<1, 1, 0, st>>>(p);
   }
-  k_sort_keys<<<1, 1024, smem, st>>>(p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int g = (int)((p.max_rois + 255) / 256);
   if (g > 4 * nsm) g = 4 * nsm;
   k_setup<<<g, 256, 0, st>>>(p);
   return cudaGetLastError();
+}
+
+// pieces of the front for the streamed mosaic: counter reset, and the label
+// scan of rows [scan_row0, scan_row1)
+cudaError_t launch_begin(const KParams& p, cudaStream_t st) {
+  k_begin<<<1, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const KParams& p, int nsm, cudaStream_t st) {
+  switch (p.dtype) {
+    case NYX_U16: return launch_scan_t<uint16_t>(p, nsm, st);
+    case NYX_I16: return launch_scan_t<int16_t>(p, nsm, st);
+    default: return launch_scan_t<float>(p, nsm, st);
+  }
 }
 
 cudaError_t launch_reset(const KParams& p, int nsm, cudaStream_t st) {

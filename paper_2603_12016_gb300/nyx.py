@@ -51,6 +51,11 @@ class NyxError(RuntimeError):
 _lib = None
 
 
+# int (*)(void* user, int64 x0, int64 y0, int64 w, int64 h, void* h_img, int32* h_mask)
+TILE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p)
+
+
 def lib() -> ctypes.CDLL:
     """Load libnyxgpu.so (built in-tree by build.build()); raises if absent."""
     global _lib
@@ -84,6 +89,9 @@ def lib() -> ctypes.CDLL:
     L.nyx_count_rois_noalloc.restype = ctypes.c_int
     L.nyx_profile_enable.argtypes = [vp, ctypes.c_int]
     L.nyx_phase_times.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), ctypes.c_int]
+    L.nyx_extract_tiles.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, TILE_FN, vp, vp, vp, vp, ctypes.c_int64, vp,
+                                    ctypes.c_uint32, vp]
+    L.nyx_extract_tiles.restype = ctypes.c_int
     L.nyx_use_graphs.argtypes = [vp, ctypes.c_int]
     L.nyx_graph_captures.argtypes = [vp, P(ctypes.c_int64)]
     L.nyx_set_class_limits.argtypes = [vp, P(ctypes.c_int32)]
@@ -236,6 +244,41 @@ class Extractor:
         return out
 
     PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final", "reset")
+
+    def extract_tiles(self, source, tile: Tuple[int, int], d_img: torch.Tensor, d_mask: torch.Tensor,
+                      table: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Streamed extraction of a 2D mosaic: source(x0, y0, w, h) returns the
+        (image, mask) numpy arrays of one tile; d_img / d_mask are the device
+        buffers of the whole mosaic (filled here).  Returns the table rows."""
+        import numpy as np
+
+        img_dt = {torch.uint16: np.uint16, torch.int16: np.int16, torch.float32: np.float32}[self.dtype]
+        err = []
+
+        def cb(user, x0, y0, w, h, p_img, p_mask):
+            try:
+                ti, tm = source(int(x0), int(y0), int(w), int(h))
+                ti = np.ascontiguousarray(ti, dtype=img_dt)
+                tm = np.ascontiguousarray(tm, dtype=np.int32)
+                if ti.shape != (h, w) or tm.shape != (h, w):
+                    raise ValueError(f"tile ({x0},{y0}) has shape {ti.shape}/{tm.shape}, expected {(h, w)}")
+                ctypes.memmove(p_img, ti.ctypes.data, ti.nbytes)
+                ctypes.memmove(p_mask, tm.ctypes.data, tm.nbytes)
+                return 0
+            except Exception as e:  # reported after the call
+                err.append(e)
+                return 1
+
+        fn = TILE_FN(cb)
+        if table is None:
+            table = torch.empty((self.max_rois, len(self.columns)), dtype=torch.float64, device=self.device)
+        st = lib().nyx_extract_tiles(self._plan, int(tile[0]), int(tile[1]), fn, None, d_img.data_ptr(),
+                                     d_mask.data_ptr(), table.data_ptr(), table.shape[0], self._n_roi.data_ptr(),
+                                     SYNC, _stream_ptr(self.device))
+        if err:
+            raise err[0]
+        self._check(st)
+        return table[: int(self._n_roi.item())]
 
     def use_graphs(self, enable: bool = True):
         """Replay the extraction as a captured CUDA graph (default on)."""

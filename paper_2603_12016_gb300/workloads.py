@@ -233,6 +233,97 @@ def blob_batch_f32(batch: int = 64, size: int = 512, seed: int = 1004, roi_range
 
 
 # ---------------------------------------------------------------------------
+# streamed mosaic: generated tile by tile from one global ROI placement
+
+@dataclass
+class Mosaic:
+    """A size x size uint16 mosaic produced tile by tile.  tile(x0, y0, w, h)
+    returns (image, mask) of that window; windows agree where they overlap,
+    so ROIs crossing tile borders are consistent."""
+    name: str
+    size: int
+    tile_size: int
+    n_roi: int
+    params: Dict
+    _cy: np.ndarray = field(repr=False, default=None)
+    _cx: np.ndarray = field(repr=False, default=None)
+    _a: np.ndarray = field(repr=False, default=None)
+    _b: np.ndarray = field(repr=False, default=None)
+    _th: np.ndarray = field(repr=False, default=None)
+    _bright: np.ndarray = field(repr=False, default=None)
+    _labels: np.ndarray = field(repr=False, default=None)
+    _order: np.ndarray = field(repr=False, default=None)
+    _seed: int = 0
+
+    def tile(self, x0: int, y0: int, w: int, h: int):
+        # background and texture depend on the pixel position only (a hash of
+        # (seed, y, x)), so overlapping windows agree
+        yy, xx = np.mgrid[y0:y0 + h, x0:x0 + w].astype(np.uint64)
+        hsh = (yy * np.uint64(0x9E3779B97F4A7C15) ^ xx * np.uint64(0xC2B2AE3D27D4EB4F) ^
+               np.uint64(self._seed * 0x165667B19E3779F9 % (1 << 63)))
+        hsh ^= hsh >> np.uint64(29)
+        hsh *= np.uint64(0xBF58476D1CE4E5B9)
+        hsh ^= hsh >> np.uint64(32)
+        u1 = ((hsh & np.uint64(0xFFFFFF)).astype(np.float64) + 0.5) / float(1 << 24)
+        u2 = (((hsh >> np.uint64(24)) & np.uint64(0xFFFFFF)).astype(np.float64) + 0.5) / float(1 << 24)
+        img = -300.0 * np.log(u1 * u2)          # Gamma(2, 300): sum of two exponentials
+        mask = np.zeros((h, w), dtype=np.int32)
+        # ellipses touching the window, painted in the global order
+        r = np.maximum(self._a, self._b)
+        hit = np.flatnonzero((self._cy + r >= y0) & (self._cy - r < y0 + h) &
+                             (self._cx + r >= x0) & (self._cx - r < x0 + w))
+        hit = hit[np.argsort(self._order[hit], kind="stable")]
+        for k in hit:
+            ry0, ry1 = max(y0, int(self._cy[k] - r[k]) - 1), min(y0 + h, int(self._cy[k] + r[k]) + 2)
+            rx0, rx1 = max(x0, int(self._cx[k] - r[k]) - 1), min(x0 + w, int(self._cx[k] + r[k]) + 2)
+            if ry1 <= ry0 or rx1 <= rx0:
+                continue
+            gy, gx = np.mgrid[ry0:ry1, rx0:rx1].astype(np.float64)
+            dy, dx = gy - self._cy[k], gx - self._cx[k]
+            c, s_ = math.cos(self._th[k]), math.sin(self._th[k])
+            u = (dx * c + dy * s_) / self._a[k]
+            v = (-dx * s_ + dy * c) / self._b[k]
+            inside = u * u + v * v <= 1.0
+            sub = mask[ry0 - y0:ry1 - y0, rx0 - x0:rx1 - x0]
+            sub[inside] = self._labels[k]
+            isub = img[ry0 - y0:ry1 - y0, rx0 - x0:rx1 - x0]
+            isub[inside] = isub[inside] + self._bright[k]
+        salt = u1 < 0.01
+        img[salt] = 65535
+        return np.clip(np.rint(img), 0, 65535).astype(np.uint16), mask
+
+    def assemble(self):
+        """The whole mosaic (for tests on small mosaics)."""
+        img = np.empty((self.size, self.size), dtype=np.uint16)
+        mask = np.empty((self.size, self.size), dtype=np.int32)
+        t = self.tile_size
+        for y0 in range(0, self.size, t):
+            for x0 in range(0, self.size, t):
+                h, w = min(t, self.size - y0), min(t, self.size - x0)
+                img[y0:y0 + h, x0:x0 + w], mask[y0:y0 + h, x0:x0 + w] = self.tile(x0, y0, w, h)
+        return img, mask
+
+
+def mosaic_2d(size: int = 32768, tile: int = 4096, n_roi: int = 500_000, seed: int = 1005, ng: int = 64,
+              area_range=(20.0, 1e4)) -> Mosaic:
+    """size x size uint16 mosaic (whole-slide stand-in): Gamma(2, 300)
+    background, 1% salt, n_roi ellipses placed once over the whole mosaic
+    (areas log-uniform in area_range, aspect 1-2, random angle, lognormal
+    brightness), painted in a random global order so that later ones
+    overwrite earlier ones; many cross tile borders."""
+    rng = _rng(seed)
+    area = np.exp(rng.uniform(math.log(area_range[0]), math.log(area_range[1]), n_roi))
+    asp = rng.uniform(1.0, 2.0, n_roi)
+    b = np.sqrt(area / (math.pi * asp))
+    a = b * asp
+    return Mosaic(name=f"mosaic_{size}_u16_{n_roi}roi", size=size, tile_size=tile, n_roi=n_roi,
+                  params=dict(glcm_levels=ng, dists=(1,), hist_bins=256),
+                  _cy=rng.uniform(0, size, n_roi), _cx=rng.uniform(0, size, n_roi), _a=a, _b=b,
+                  _th=rng.uniform(0, math.pi, n_roi), _bright=rng.lognormal(8.0, 0.6, n_roi),
+                  _labels=rng.permutation(n_roi).astype(np.int32) + 1, _order=rng.permutation(n_roi), _seed=seed)
+
+
+# ---------------------------------------------------------------------------
 # named configurations (sizes of the benchmark table) and small variants
 
 def config(name: str, seed_offset: int = 0) -> Workload:

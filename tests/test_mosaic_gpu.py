@@ -1,0 +1,125 @@
+"""Streamed mosaic extraction (tiles delivered by a host callback, ROIs
+crossing tile borders merged on the device) and the multi-block key sort of
+plans above 16,384 ROIs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_12016_gb300 import workloads as W
+from parity_util import compare, to_torch
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_12016_gb300 import build
+
+    build.build()
+
+
+def _table(ex, t):
+    t = t.cpu().numpy()
+    return {c: t[:, i] for i, c in enumerate(ex.columns)}
+
+
+def _crossing(mask, tw, th):
+    """Labels present on both sides of some tile border."""
+    out = set()
+    for x in range(tw, mask.shape[1], tw):
+        a, b = mask[:, x - 1], mask[:, x]
+        out |= set(np.unique(a[(a == b) & (a > 0)]).tolist())
+    for y in range(th, mask.shape[0], th):
+        a, b = mask[y - 1], mask[y]
+        out |= set(np.unique(a[(a == b) & (a > 0)]).tolist())
+    return out
+
+
+def test_tiles_match_whole_image_and_oracle():
+    from paper_2603_12016_gb300 import nyx
+
+    m = W.mosaic_2d(size=2048, tile=512, n_roi=3000, seed=2401)
+    img, mask = m.assemble()
+    tw, th = 700, 450  # ragged edge tiles
+    ex = nyx.Extractor(img.shape, torch.uint16, glcm_levels=64, dists=(1,), max_rois=8192)
+    d_img = torch.empty(img.shape, dtype=torch.uint16, device="cuda")
+    d_mask = torch.empty(mask.shape, dtype=torch.int32, device="cuda")
+    calls = []
+
+    def source(x0, y0, w, h):
+        calls.append((x0, y0, w, h))
+        return m.tile(x0, y0, w, h)
+
+    got = ex.extract_tiles(source, (tw, th), d_img, d_mask)
+    assert len(calls) == 3 * 5
+    assert np.array_equal(d_img.cpu().numpy(), img)
+    assert np.array_equal(d_mask.cpu().numpy(), mask)
+    whole = ex(to_torch(img), to_torch(mask))
+    assert got.shape == whole.shape
+    assert torch.equal(torch.nan_to_num(got, nan=-7.0), torch.nan_to_num(whole, nan=-7.0))
+    g = _table(ex, got)
+    cross = sorted(_crossing(mask, tw, th))
+    assert len(cross) > 50
+    rng = np.random.default_rng(1)
+    pick = sorted(set(rng.choice(cross, 24, replace=False).tolist()) |
+                  set(rng.choice(g["LABEL"].astype(np.int64), 8, replace=False).tolist()))
+    o = oracle.extract(img, mask, 2, ng=64, dists=(1,), hist_bins=256, rois=[oracle.roi_key(0, l) for l in pick],
+                       threads=8)
+    sel = np.isin(g["LABEL"].astype(np.int64), pick)
+    fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
+    assert not fails, "\n".join(fails[:30])
+
+
+def test_tile_source_error_leaves_plan_usable():
+    from paper_2603_12016_gb300 import nyx
+
+    m = W.mosaic_2d(size=512, tile=256, n_roi=200, seed=2402)
+    img, mask = m.assemble()
+    ex = nyx.Extractor(img.shape, torch.uint16, glcm_levels=16, max_rois=1024)
+    d_img = torch.empty(img.shape, dtype=torch.uint16, device="cuda")
+    d_mask = torch.empty(mask.shape, dtype=torch.int32, device="cuda")
+
+    def bad(x0, y0, w, h):
+        if y0 > 0:
+            raise RuntimeError("source failed")
+        return m.tile(x0, y0, w, h)
+
+    with pytest.raises(RuntimeError):
+        ex.extract_tiles(bad, (256, 256), d_img, d_mask)
+    t = ex.extract_tiles(m.tile, (256, 256), d_img, d_mask)
+    assert np.array_equal(t[:, 0].cpu().numpy().astype(np.int64), np.unique(mask[mask > 0]))
+
+
+@pytest.mark.parametrize("n_roi", [16385, 40000])
+def test_multiblock_key_sort_above_single_block_capacity(n_roi):
+    """More ROIs than one block sorts: sparse random labels up to 2^31 - 1 in
+    an irregular order; the table must list them in ascending order with
+    their exact pixel counts and bounding boxes."""
+    from paper_2603_12016_gb300 import nyx
+
+    rng = np.random.default_rng(n_roi)
+    side = 4 * int(np.ceil(np.sqrt(n_roi)))
+    labels = rng.choice(np.arange(1, 2**31 - 1, dtype=np.int64), size=n_roi, replace=False).astype(np.int32)
+    mask = np.zeros((side, side), dtype=np.int32)
+    k = 0
+    for y in range(0, side, 4):
+        for x in range(0, side, 4):
+            if k < n_roi:
+                mask[y:y + 3, x:x + 2 + (k % 2)] = labels[k]
+                k += 1
+    img = rng.integers(0, 5000, size=mask.shape).astype(np.uint16)
+    ex = nyx.Extractor(mask.shape, torch.uint16, glcm_levels=8, max_rois=65536,
+                       features=["MEAN", "MEDIAN", "GLCM_CONTRAST"])
+    g = _table(ex, ex(to_torch(img), to_torch(mask)))
+    assert np.array_equal(g["LABEL"].astype(np.int64), np.sort(labels.astype(np.int64)))
+    lab, cnt = np.unique(mask[mask > 0], return_counts=True)
+    assert np.array_equal(g["AREA"].astype(np.int64), cnt)
+    pick = [int(lab[i]) for i in rng.choice(len(lab), 16, replace=False)] + [int(lab[0]), int(lab[-1])]
+    o = oracle.extract(img, mask, 2, ng=8, dists=(1,), hist_bins=256, rois=[oracle.roi_key(0, l) for l in pick],
+                       threads=8)
+    sel = np.isin(g["LABEL"].astype(np.int64), pick)
+    fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
+    assert not fails, "\n".join(fails[:30])
