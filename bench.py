@@ -21,6 +21,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -144,6 +146,16 @@ def reduce_over_ranks(dist, device, t_ms: float, units: int):
 def make_workload(name: str, rank: int):
     from paper_2603_12016_gb300 import workloads as W
 
+    if name.startswith("mosaic"):
+        # whole-slide stand-in generated tile by tile; the assembled arrays are
+        # what the host would stream
+        big = name == "mosaic"
+        m = W.mosaic_2d(size=32768 if big else 8192, tile=4096 if big else 1024,
+                        n_roi=500_000 if big else 32_000, seed=1005 + rank)
+        img, mask = m.assemble()
+        n_roi = int(np.count_nonzero(np.bincount(mask.ravel())[1:]))
+        return W.Workload(m.name, img, mask, 2, params=dict(m.params),
+                          meta={"n_roi": n_roi, "tile": m.tile_size})
     return W.config(name, seed_offset=rank)
 
 
@@ -162,14 +174,15 @@ def run_reference(args) -> int:
 
     w = make_workload(args.workload, 0)
     cores = os.cpu_count() or 1
-    labels = np.unique(w.mask[w.mask > 0])
+    image, mask, where = _oracle_view(w)
+    labels = np.unique(mask[mask > 0])
     sample = labels[: min(len(labels), args.ref_rois)]
     keys = [oracle.roi_key(0, int(l)) for l in sample]
     prm = w.params
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.extract(w.image, w.mask, w.ndim, ng=prm["glcm_levels"], dists=prm["dists"],
+        oracle.extract(image, mask, w.ndim, ng=prm["glcm_levels"], dists=prm["dists"],
                        hist_bins=prm["hist_bins"], rois=keys, threads=cores)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
@@ -182,10 +195,19 @@ def run_reference(args) -> int:
             "config": {"workload": w.name, "sample_rois": int(len(sample)), "n_roi_total": int(len(labels)),
                        "glcm_levels": prm["glcm_levels"], "dists": list(prm["dists"])},
             "cpu_baseline": {"value": v, "unit": "ROIs/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {len(sample)} of {len(labels)} ROIs of {w.name}"},
+                             "sample": f"first {len(sample)} of {len(labels)} ROIs of {w.name}{where}"},
             "e2e": {"value": v, "unit": "ROIs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def _oracle_view(w):
+    """Arrays the oracle samples from: the first 4096 x 4096 tile of a
+    streamed mosaic (the oracle separates every pixel of its input first),
+    else the whole workload."""
+    if w.meta.get("tile"):
+        return w.image[:4096, :4096], w.mask[:4096, :4096], " (first 4096x4096 tile)"
+    return w.image, w.mask, ""
 
 
 def cpu_baseline(w, budget_s: float):
@@ -194,21 +216,22 @@ def cpu_baseline(w, budget_s: float):
     import oracle
 
     cores = os.cpu_count() or 1
-    labels = np.unique(w.mask[w.mask > 0])
+    image, mask, where = _oracle_view(w)
+    labels = np.unique(mask[mask > 0])
     prm = w.params
     n = 32
     while True:
         sample = labels[: min(n, len(labels))]
         keys = [oracle.roi_key(0, int(l)) for l in sample]
         t0 = time.perf_counter()
-        oracle.extract(w.image, w.mask, w.ndim, ng=prm["glcm_levels"], dists=prm["dists"],
+        oracle.extract(image, mask, w.ndim, ng=prm["glcm_levels"], dists=prm["dists"],
                        hist_bins=prm["hist_bins"], rois=keys, threads=cores)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or len(sample) == len(labels):
             break
         n = int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3))))
     return {"value": len(sample) / dt, "unit": "ROIs/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {len(sample)} of {len(labels)} ROIs of {w.name}, {dt:.1f} s",
+            "sample": f"first {len(sample)} of {len(labels)} ROIs of {w.name}{where}, {dt:.1f} s",
             "seconds": dt}
 
 
@@ -256,6 +279,7 @@ def main() -> int:
     prm = w.params
     dtype = {np.uint16: torch.uint16, np.int16: torch.int16, np.float32: torch.float32}[w.image.dtype.type]
     max_rois = 8192 if w.meta["n_roi"] <= 8192 else 2 * w.meta["n_roi"]
+    tile = w.meta.get("tile")  # streamed mosaic: e2e goes through nyx_extract_tiles
 
     def extractor(precision):
         return nyx.Extractor(w.image.shape, dtype, ndim=w.ndim, glcm_levels=prm["glcm_levels"], dists=prm["dists"],
@@ -355,13 +379,22 @@ def main() -> int:
     d_img = torch.empty_like(img)
     d_mask = torch.empty_like(mask)
     e2e_ms = []
-    for i in range(args.warmup + args.steps):
+    h_img_np, h_mask_np = h_img.numpy(), h_mask.numpy()
+
+    def tile_source(x0, y0, tw, th):
+        return h_img_np[y0:y0 + th, x0:x0 + tw], h_mask_np[y0:y0 + th, x0:x0 + tw]
+
+    e2e_steps = args.steps if tile is None else min(args.steps, 3)
+    for i in range(args.warmup + e2e_steps):
         torch.cuda.synchronize(dev)
         s, t = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        d_img.copy_(h_img, non_blocking=True)
-        d_mask.copy_(h_mask, non_blocking=True)
-        n = one_step(ex, d_img, d_mask)
+        if tile is None:
+            d_img.copy_(h_img, non_blocking=True)
+            d_mask.copy_(h_mask, non_blocking=True)
+            n = one_step(ex, d_img, d_mask)
+        else:  # tiles streamed from host memory, band scans overlapping the host
+            ex.extract_tiles(tile_source, (tile, tile), d_img, d_mask, table=table)
         h_table[:n_roi].copy_(table[:n_roi], non_blocking=True)
         if bwd:
             h_grad.copy_(gimg, non_blocking=True)
@@ -371,7 +404,7 @@ def main() -> int:
             e2e_ms.append(s.elapsed_time(t))
     e2e_t, _ = reduce_over_ranks(dist, dev, statistics.median(e2e_ms), n_roi)
     e2e = {"value": n_total / (e2e_t * 1e-3), "unit": "ROIs/s",
-           "h2d_bytes_per_step": int(w.image.nbytes + w.mask.nbytes),
+           "h2d_bytes_per_step": int(w.image.nbytes + w.mask.nbytes), "api": "nyx_extract_tiles" if tile else "nyx_extract",
            "d2h_bytes_per_step": int(8 * n_roi * n_col + (4 * w.image.size if bwd else 0)), "ms_per_step": e2e_t}
 
     fp64 = None
