@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ROIs/sec and Mpixel/sec full feature set, % HBM roofline vs plain FP64 path"
-PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final", "reset")
+PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "final", "reset")
 
 
 def _peaks():
@@ -100,15 +100,17 @@ class ClockSampler:
 TRAFFIC = {}
 
 
-def roi_classes(w):
+def roi_classes(w, lim_pix=None):
     """Pixels and ROI count per size class (warp, small, medium, multi-block)
-    by the library's class rule: pixel count and padded bounding-box cells
-    against (512, 2048), (1024, 4096), (8192, 16384)."""
+    by the library's class rule: pixel count against the class limits
+    (default 256 / 1,024 / 8,192) and padded bounding-box cells against the
+    class capacities 1,024 / 4,096 / 16,384."""
     import numpy as np
     from scipy import ndimage
 
     pad = max(w.params["dists"]) if w.params["glcm_levels"] > 0 else 0
-    lims = ((512, 2048), (1024, 4096), (8192, 16384))
+    lp = tuple(lim_pix) if lim_pix else (256, 1024, 8192)
+    lims = ((lp[0], 1024), (lp[1], 4096), (lp[2], 16384))
     px, rows = [0, 0, 0, 0], [0, 0, 0, 0]
     masks = w.mask if (w.mask.ndim == 3 and w.ndim == 2) else w.mask[None]
     for m in masks:
@@ -356,7 +358,7 @@ def main() -> int:
     # its ROIs' pixels and mask once and writes their table rows; the GLCM
     # feature kernel reads the per-offset sums and writes the GLCM columns)
     dom = max(phases, key=phases.get)
-    cls_px, cls_rows = roi_classes(w)
+    cls_px, cls_rows = roi_classes(w, limits)
     n_off = len(prm["dists"]) * (13 if w.ndim == 3 else 4) if prm["glcm_levels"] > 0 else 0
     per_px = w.image.itemsize + 4
     dom_bytes = {"scan": w.image.nbytes + w.mask.nbytes,
@@ -364,7 +366,7 @@ def main() -> int:
                  "roi_small": cls_px[1] * per_px + 8 * cls_rows[1] * n_col,
                  "roi_medium": cls_px[2] * per_px + 8 * cls_rows[2] * n_col,
                  "roi_big": cls_px[3] * per_px + 8 * cls_rows[3] * n_col,
-                 "glcm_final": n_roi * n_off * (160 + 8 * 30)}.get(dom, 0)
+                 "final": n_roi * (512 + n_off * 160 + 8 * n_col)}.get(dom, 0)
     dom_gbs = dom_bytes / (phases[dom] * 1e-3) / 1e9
     traffic = TRAFFIC.get((w.name, dom))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
@@ -426,9 +428,10 @@ def main() -> int:
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, 20.0)
     # begin, scan, key sort, setup, 3 block classes, reset; multi-block class:
-    # zero, pass 1, pass 2, sorted order statistics (+ GLCM); GLCM features
+    # zero, pass 1, pass 2, sorted order statistics (+ GLCM); statistics
+    # final (+ GLCM features)
     glcm = w.params["glcm_levels"] > 0
-    launches_per_step = 8 + 4 + (1 if glcm else 0) + (1 if glcm else 0)
+    launches_per_step = 8 + 4 + (1 if glcm else 0) + 1 + (1 if glcm else 0)
     if bwd:  # begin, scan, key sort, setup, coefficients, per-pixel gradient, reset
         launches_per_step += 7
     line = {

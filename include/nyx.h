@@ -158,12 +158,12 @@ nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
 /* Size classes (the paper, "Results, Scalability": how much the GPU helps
  * depends on ROI size and count, Fig. 3f/g).  Every ROI
  * goes to the first class whose pixel limit and padded bounding-box cell
- * capacity it fits: one warp per ROI (capacity 512 px / 2,048 cells), one
+ * capacity it fits: one warp per ROI (capacity 256 px / 1,024 cells), one
  * 128-thread block (1,024 / 4,096), one 256-thread block (8,192 / 16,384),
  * else the multi-block path.  lim_pix[3] sets the pixel limits of the first
  * three classes (0 disables a class; each at most its capacity above).
  * nyx_autotune times the extraction of (d_img, d_mask) under a grid of
- * limits (warp 0/128/256/512, small 0/1024, medium 4096/8192; `reps` timed
+ * limits (warp 0/128/256, small 0/512/1024, medium 4096/8192; `reps` timed
  * calls each after one synchronised warm-up), keeps the fastest and returns
  * it in h_lim_pix (host int32[3], may be NULL).  d_table / cap_roi as in
  * nyx_extract.  Synchronises.  Results do not depend on the limits beyond
@@ -240,7 +240,8 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
  * [0] counters + label scan, [1] key sort + per-ROI setup, [2] ROI kernel of
  * the warp class (one warp per ROI), [3] of the small block class, [4] of the
  * medium block class, [5] the multi-block class (ROIs larger than a block
- * stages), [6] GLCM features from the per-offset sums, [7] table reset.
+ * stages), [6] statistics, moments and GLCM features from the per-ROI sums,
+ * [7] table reset.
  * Errors: NYX_ERR_ARG (null plan/ms, slots out of 0..1024, back out of
  * range), NYX_ERR_STATE (that extract was not recorded), NYX_ERR_CUDA. */
 #define NYX_N_PHASES 8

@@ -369,6 +369,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   // per (ROI, offset) GLCM accumulators (GI int64 + GF sums in 8-byte slots)
   const int n_off_all = p.glcm_levels > 0 ? p.n_dist * (p.ndim == 3 ? 13 : 4) : 0;
   const size_t o_gacc = take((size_t)mr * n_off_all * (8 * (GI_HOST + GF_HOST)));
+  // per-ROI statistics / moment sums (64 eight-byte slots)
+  const size_t o_sacc = take((size_t)mr * 512);
   // second key buffer of the multi-block key sort
   const size_t o_sorttmp = take(mr > SORT_CAP ? 8ull * mr : 0);
   cudaError_t e = cudaMalloc(&pl->ws, off);
@@ -440,14 +442,15 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.arena = (unsigned*)(w + o_arena);
   k.arena_cap = arena_words;
   k.gacc = (unsigned char*)(w + o_gacc);
+  k.sacc = (unsigned char*)(w + o_sacc);
   k.sort_tmp = mr > SORT_CAP ? (unsigned long long*)(w + o_sorttmp) : nullptr;
   pl->d_col_map = (int*)(w + o_cmap);
   k.col_map = pl->d_col_map;
   k.n_col = (int)pl->col_names.size();
   k.max_rois = mr;
   k.dbg_roi = -1;
-  k.lim_pix[0] = 512;
-  k.lim_cells[0] = 2048;
+  k.lim_pix[0] = 256;
+  k.lim_cells[0] = 1024;
   k.lim_pix[1] = 1024;
   k.lim_cells[1] = 4096;
   k.lim_pix[2] = 8192;
@@ -592,6 +595,15 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     }
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[6], st));
+  }
+  {  // statistics, moments and Hu invariants from the per-ROI sums
+    cudaError_t e;
+    switch (k.dtype) {
+      case NYX_U16: e = launch_roi_u16(k, 3, fp64, c->nsm, st); break;
+      case NYX_I16: e = launch_roi_i16(k, 3, fp64, c->nsm, st); break;
+      default: e = launch_roi_f32(k, 3, fp64, c->nsm, st); break;
+    }
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "statistics kernel launch failed: %s", cudaGetErrorString(e));
   }
   if (k.need & NEED_GLCM) {
     cudaError_t e = launch_glcm_final(k, fp64, c->nsm, st);
@@ -801,7 +813,7 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   NYX_CUDA(c, cudaSetDevice(c->device));
   // candidate pixel thresholds of the warp, small and medium classes (0 =
   // class unused); the cell limits stay at each class's staging capacity
-  static const int cw[] = {0, 128, 256, 512}, cs[] = {0, 1024}, cm[] = {4096, 8192};
+  static const int cw[] = {0, 128, 256}, cs[] = {0, 512, 1024}, cm[] = {4096, 8192};
   const int saved_prof = pl->prof_slots;
   pl->prof_slots = 0;
   int best[3] = {pl->kp.lim_pix[0], pl->kp.lim_pix[1], pl->kp.lim_pix[2]};
@@ -845,7 +857,7 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
 
 nyx_status nyx_set_class_limits(nyx_plan* pl, const int32_t* lim_pix) {
   if (!pl || !lim_pix) return NYX_ERR_ARG;
-  const int cap[3] = {512, 1024, 8192};
+  const int cap[3] = {256, 1024, 8192};
   for (int i = 0; i < 3; ++i)
     if (lim_pix[i] < 0 || lim_pix[i] > cap[i]) return fail(pl->ctx, NYX_ERR_ARG, "class limit %d out of 0..%d", i, cap[i]);
   for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = lim_pix[i];

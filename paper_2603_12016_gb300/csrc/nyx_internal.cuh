@@ -186,6 +186,7 @@ struct KParams {
   unsigned* arena;
   unsigned long long arena_cap;    // words
   unsigned char* gacc;             // [max rows][n_off] GLCM accumulators
+  unsigned char* sacc;             // [max rows] statistics / moment sums for k_stats_final
   // label scan over rows [scan_row0, scan_row1) of the batch (scan_row1 = 0:
   // all rows); the mosaic path scans each band of tiles as it arrives
   int64_t scan_row0, scan_row1;

@@ -42,7 +42,7 @@ struct RoiClass {
   static constexpr int CELLS = CELLS_;  // max padded raster cells
   static constexpr int TAB = 2 * PIX_;  // GLCM hash capacity (power of two); also 2 sort buffers
 };
-using ClassW = RoiClass<32, 512, 2048>;    // one warp per ROI
+using ClassW = RoiClass<32, 256, 1024>;    // one warp per ROI
 using ClassS = RoiClass<128, 1024, 4096>;
 using ClassM = RoiClass<256, 8192, 16384>;
 
@@ -653,6 +653,28 @@ __device__ inline void store_gacc(const KParams& p, int64_t item, int oi, const 
   else if (t < GI + GF && !empty) ((A*)(g + 8 * GI))[t - GI] = fv[t - GI];
 }
 
+// Per-ROI statistics and moment sums handed from the accumulation kernels to
+// k_stats_final (8-byte slots): [0..7] centred power sums, [8..27] intensity
+// moments, [28..47] binary moments, [48] mean, [49] sum I, [50] energy,
+// [51..53] intensity centroid, [54..56] binary centroid (ROI-local).
+constexpr int SACC_SLOTS = 64, SACC_BYTES = 8 * SACC_SLOTS;
+template <class A>
+__device__ inline void store_sacc(const KParams& p, int64_t item, int nm, const A* st, const A* mi, const A* mb,
+                                  A mean, A sumI, A energy, A cx, A cy, A cz, A bx, A by, A bz) {
+  A* g = (A*)(p.sacc + (size_t)item * SACC_BYTES);
+  for (int i = threadIdx.x; i < 57; i += blockDim.x) {
+    A v;
+    if (i < 8) v = st[i];
+    else if (i < 28) v = i - 8 < nm ? mi[i - 8] : (A)0;
+    else if (i < 48) v = i - 28 < nm ? mb[i - 28] : (A)0;
+    else {
+      const A sc[9] = {mean, sumI, energy, cx, cy, cz, bx, by, bz};
+      v = sc[i - 48];
+    }
+    g[i] = v;
+  }
+}
+
 // Percentiles by linear interpolation at h = (n-1) q on the sorted values,
 // computed in FP64 with separately rounded operations like the definition,
 // one lane per percentile.  Lane 0 also finds the index range of the values
@@ -1171,17 +1193,11 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
       block_sum<C, A, NM>(acc, red, w ? res_mb : res_mi);
     }
 
-    // ---- finalise statistics and moments (one warp per group) ---------------
-    double* save = (need & NEED_SAVE) ? p.saved + (int64_t)item * SV_WORDS : nullptr;
-    if (tid == 0)
-      finalize_stats<T, NDIM, A>(p, row, res_st, n, mu_hi + mu_lo, sumI, energy, vmin, vmax, bimg, r.x0, r.y0, r.z0,
-                                 cx, cy, cz, bx, by, bz, wvalid, save);
-    // (blocks with fewer warps run these groups one after the other)
-    if (warp == (C::NW > 1 ? 1 : 0) && (need & (NEED_MOM_INT | NEED_SAVE)))
-      finalize_moments_warp<NDIM, A>(p, row, 0, res_mi, cx, cy, cz, wvalid, save ? save + SV_MU : nullptr);
-    if (warp == (C::NW > 2 ? 2 : 0) && (need & NEED_MOM_BIN))
-      finalize_moments_warp<NDIM, A>(p, row, 5, res_mb, bx, by, bz, true, nullptr);
-    __syncthreads();
+    // ---- the sums go to k_stats_final (one warp per ROI), which derives the
+    // statistics, moments and Hu invariants, so no block waits on that
+    // serial arithmetic
+    store_sacc<A>(p, item, NM, res_st, res_mi, res_mb, mu_hi + mu_lo, sumI, energy, cx, cy, cz, bx, by, bz);
+    (void)wvalid;
 
     // ---- histogram features -------------------------------------------------
     if (need & NEED_HIST) {
@@ -1463,6 +1479,39 @@ cudaError_t launch_roi_one(const KParams& p, int cls, int nsm, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+// First-order statistics (Table S1/S5), moments and Hu invariants (Table S2,
+// S5) of every ROI from the sums its accumulation kernel left in sacc: one
+// warp per ROI (lane 0 the statistics, lanes 0..NM-1 the moments).
+template <class T, int NDIM, class A>
+__global__ void __launch_bounds__(256) k_stats_final(KParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nroi = min((int64_t)*p.n_roi, p.cap_roi);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < nroi; item += nw) {
+    const A* g = (const A*)(p.sacc + (size_t)item * SACC_BYTES);
+    const RoiInfo r = p.rois[item];
+    double* row = p.table + item * p.n_col;
+    double* save = (p.need & NEED_SAVE) ? p.saved + item * SV_WORDS : nullptr;
+    const bool wvalid = g[49] != (A)0;
+    if (lane == 0)
+      finalize_stats<T, NDIM, A>(p, row, g, (int)r.n, g[48], g[49], g[50], r.vmin, r.vmax, (int64_t)(r.key >> 32),
+                                 r.x0, r.y0, r.z0, g[51], g[52], g[53], g[54], g[55], g[56], wvalid, save);
+    if (p.need & (NEED_MOM_INT | NEED_SAVE))
+      finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], wvalid, save ? save + SV_MU : nullptr);
+    if (p.need & NEED_MOM_BIN) finalize_moments_warp<NDIM, A>(p, row, 5, g + 28, g[54], g[55], g[56], true, nullptr);
+  }
+}
+
+template <class T, int NDIM, class A>
+cudaError_t launch_stats_final(const KParams& p, int nsm, cudaStream_t st) {
+  const int64_t rows = p.cap_roi < p.max_rois ? p.cap_roi : p.max_rois;
+  int64_t nb = (rows + 7) / 8;
+  if (nb > 16ll * nsm) nb = 16ll * nsm;
+  if (nb < 1) nb = 1;
+  k_stats_final<T, NDIM, A><<<(int)nb, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
 template <class T, class C>
 cudaError_t launch_roi_c(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st) {
   if (p.ndim == 3)
@@ -1470,12 +1519,17 @@ cudaError_t launch_roi_c(const KParams& p, int cls, int fp64, int nsm, cudaStrea
   return fp64 ? launch_roi_one<T, 2, C, double>(p, cls, nsm, st) : launch_roi_one<T, 2, C, float>(p, cls, nsm, st);
 }
 
+// cls 0..2: the block classes; cls 3: k_stats_final over all ROIs
 template <class T>
 cudaError_t launch_roi_t(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st) {
   switch (cls) {
     case 0: return launch_roi_c<T, ClassW>(p, cls, fp64, nsm, st);
     case 1: return launch_roi_c<T, ClassS>(p, cls, fp64, nsm, st);
-    default: return launch_roi_c<T, ClassM>(p, cls, fp64, nsm, st);
+    case 2: return launch_roi_c<T, ClassM>(p, cls, fp64, nsm, st);
+    default:
+      if (p.ndim == 3)
+        return fp64 ? launch_stats_final<T, 3, double>(p, nsm, st) : launch_stats_final<T, 3, float>(p, nsm, st);
+      return fp64 ? launch_stats_final<T, 2, double>(p, nsm, st) : launch_stats_final<T, 2, float>(p, nsm, st);
   }
 }
 

@@ -16,9 +16,9 @@
 //                partials in chunk order and derives the mean, centroids,
 //                histogram features and the order statistics
 //   k_big_p2     units (ROI, chunk): one pass for the centred power sums
-//                (Kahan per thread) and both sets of central moments,
-//                compensated across the block; the last unit merges and
-//                finalises statistics and moments
+//                and both sets of central moments, compensated across the
+//                block; the last unit merges them in chunk order and hands
+//                them to k_stats_final
 //   k_big_glcm   units (ROI, span, group of offsets): one dense upper-
 //                triangular co-occurrence matrix per offset of the group in
 //                shared memory (Ng(Ng+1)/2 counts, diagonal counted twice).
@@ -613,13 +613,12 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
     const int64_t bimg = (int64_t)(r.key >> 32);
     const A sumI = (A)__ldcg(st + 8), energy = (A)__ldcg(st + 9);
     const bool wvalid = sumI != 0;
-    double* save = (need & NEED_SAVE) ? p.saved + (int64_t)br.item * SV_WORDS : nullptr;
-    if (tid == 0)  // also writes the centroid columns
-      finalize_stats<T, NDIM, A>(p, row, res, n, mu_hi + mu_lo, sumI, energy, r.vmin, r.vmax, bimg, r.x0, r.y0, r.z0,
-                                 cx, cy, cz, bcx, bcy, bcz, wvalid, save);
-    if (warp == 1 && do_mi)
-      finalize_moments_warp<NDIM, A>(p, row, 0, res + 8, cx, cy, cz, wvalid, save ? save + SV_MU : nullptr);
-    if (warp == 2 && do_mb) finalize_moments_warp<NDIM, A>(p, row, 5, res + 8 + NM, bcx, bcy, bcz, true, nullptr);
+    // the merged sums go to k_stats_final like those of the block classes
+    store_sacc<A>(p, br.item, NM, res, res + 8, res + 8 + NM, mu_hi + mu_lo, sumI, energy, cx, cy, cz, bcx, bcy, bcz);
+    (void)n;
+    (void)row;
+    (void)bimg;
+    (void)wvalid;
     __syncthreads();
   }
 }

@@ -243,7 +243,7 @@ class Extractor:
                                        _stream_ptr(self.device)))
         return out
 
-    PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final", "reset")
+    PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "final", "reset")
 
     def extract_tiles(self, source, tile: Tuple[int, int], d_img: torch.Tensor, d_mask: torch.Tensor,
                       table: Optional[torch.Tensor] = None) -> torch.Tensor:
