@@ -29,21 +29,17 @@ __global__ void __launch_bounds__(256) k_glcm_final(KParams p, int rpb) {
       const long long* g = (const long long*)(p.gacc + ((size_t)item * n_off + oi) * GACC_BYTES);
       double* row = p.table + item * p.n_col;
       const int di = oi / p.n_dirs, dir = oi - di * p.n_dirs;
-      long long iv[GI];
+      long long iv[GN];
 #pragma unroll
-      for (int k = 0; k < GI; ++k) iv[k] = g[k];
+      for (int k = 0; k < GN; ++k) iv[k] = g[k];
       if (iv[0] == 0) {  // offset without pairs
         if (p.per_offset)
           for (int k = 0; k < NGLCM; ++k) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + k, nan);
         f[NGLCM] = 0;
       } else {
-        const A* gf = (const A*)(g + GI);
-        A fv[GF];
-#pragma unroll
-        for (int k = 0; k < GF; ++k) fv[k] = gf[k];
         A gs[NGLCM + 1];
         for (int k = 0; k <= NGLCM; ++k) gs[k] = 0;
-        finalize_glcm<A>(p, row, iv, fv, di, dir, gs);
+        finalize_glcm<A>(p, row, iv, di, dir, gs);
         for (int k = 0; k < NGLCM; ++k) f[k] = gs[k];
         f[NGLCM] = 1;
       }

@@ -507,24 +507,49 @@ __device__ inline A i128A(__int128 x) {
   else return (double)(long long)(x >> 64) * 18446744073709551616.0 + (double)(unsigned long long)x;
 }
 
-// GLCM sums of one offset, reduced over the block.  Integer sums are exact
-// (independent of the order of the hash table): with C the count of a cell
-// (a, b) of the symmetric matrix, k = a + b + 2 (= i + j, 1-based levels) and
-// d = |a - b|,
+// GLCM sums of one offset, reduced over the block; all are integers, so they
+// do not depend on the order of the hash table or of the reduction.  With C
+// the count of a cell (a, b) of the symmetric matrix, k = a + b + 2 (= i + j,
+// 1-based levels) and d = |a - b|:
 //   [0] T = sum C            [1..4] sum C k^m      [5..6] sum C d^m
 //   [7] sum C i^2            [8] sum C^2           [9] sum C log2 C  (2^-24)
 //   [10] sum C log2(C T / (P_i P_j))  (2^-24)      [11] max C
-// Float sums (deterministic: over the marginals in index order):
-//   [0] HX  [1] SUMENT  [2] DIFENTRO  [3] ID  [4] IDM  [5] IDN  [6] IDMN  [7] IV
-constexpr int GI = GI_HOST, GF = GF_HOST;
+// and over the marginals (c = count of one entry, e = c log2 c):
+//   [12] sum e over p_x      [13] over p_{x+y}     [14] over p_{x-y}  (2^-24)
+//   [15..19] sum_k c_k w(k) over p_{x-y} for w = 1/(1+k), 1/(1+k^2),
+//            1/(1+k/Ng), 1/(1+k^2/Ng^2), 1/k^2 (k >= 1)  (2^-32)
+// Each fixed-point term is one rounding of a value computed in A.
+constexpr int GI = GI_HOST, GF = GF_HOST, GN = GI + GF;
+
+template <class A>
+__device__ inline long long a2ll(A x) {
+  if constexpr (std::is_same<A, float>::value) return __float2ll_rn(x);
+  else return __double2ll_rn(x);
+}
+// c log2 c in units of 2^-24
+template <class A>
+__device__ inline long long ent_fx(unsigned c) {
+  const A ca = (A)c;
+  return a2ll(ca * alog2(ca) * (A)16777216);
+}
+// the inverse-difference family of one difference-marginal entry (c at k)
+template <class A>
+__device__ inline void invdiff_fx(unsigned c, int k, int ng, long long* s) {
+  const A ca = (A)c, kk = (A)k, ngA = (A)ng, sc = (A)4294967296.0;
+  s[15] += a2ll(ca / ((A)1 + kk) * sc);
+  s[16] += a2ll(ca / ((A)1 + kk * kk) * sc);
+  s[17] += a2ll(ca / ((A)1 + kk / ngA) * sc);
+  s[18] += a2ll(ca / ((A)1 + kk * kk / (ngA * ngA)) * sc);
+  if (k >= 1) s[19] += a2ll(ca / (kk * kk) * sc);
+}
 
 // GLCM features of one offset (Table S3 rows 140-174): every moment-type
 // feature from exact integer power sums (central moments of the sum /
 // difference / row distributions as exact integer numerators over powers of
 // T), the entropies from the marginal sums.  Accumulates the direction mean.
 template <class A>
-__device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const long long* iv, const A* fv, int di,
-                                           int dir, A* gsum) {
+__device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const long long* iv, int di, int dir,
+                                           A* gsum) {
   typedef __int128 I;
   const long long T = iv[0], S1 = iv[1], S2 = iv[2], S3 = iv[3], S4 = iv[4], D1 = iv[5], D2 = iv[6], Q2 = iv[7];
   const A Ta = i128A<A>(T), invT = (A)1 / Ta;
@@ -553,6 +578,12 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
   const A asmv = i128A<A>(iv[8]) / T2;
   const A je = alog2(Ta) - i128A<A>(iv[9]) * ((A)(1.0 / 16777216.0) * invT);
   const A mi = i128A<A>(iv[10]) * ((A)(1.0 / 16777216.0) * invT);
+  const A E = (A)(1.0 / 16777216.0), Q = (A)(1.0 / 4294967296.0), lT = alog2(Ta);
+  A fv[GF];
+  fv[0] = lT - i128A<A>(iv[12]) * E * invT;  // HX
+  fv[1] = lT - i128A<A>(iv[13]) * E * invT;  // SUMENT
+  fv[2] = lT - i128A<A>(iv[14]) * E * invT;  // DIFENTRO
+  for (int k = 3; k < GF; ++k) fv[k] = i128A<A>(iv[12 + k]) * Q * invT;  // ID, IDM, IDN, IDMN, IV
   const A hx = fv[0];
   A f[NGLCM];
   f[G_ASM] = asmv;
@@ -596,18 +627,16 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
   gsum[NGLCM] += 1;
 }
 
-// Block reduction of GI int64 and GF float values (plain sums; the int64
-// ones are exact, the floats are GLCM marginal sums with a 1e-4 budget).
-// Results in iout / fout (shared memory) for every thread.
-template <class C, class A>
-__device__ inline void block_sum_glcm(long long (&iv)[GI], A (&fv)[GF], double* scratch_d, long long* iout, A* fout) {
+// Block reduction of the GN GLCM sums (index 11 is a maximum); results in
+// out (shared memory) for every thread.
+template <class C>
+__device__ inline void block_sum_glcm(long long (&iv)[GN], double* scratch_d, long long* out) {
   long long* si = (long long*)scratch_d;
-  A* sf = (A*)(si + C::NW * GI);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < GI; ++i) {
+  for (int i = 0; i < GN; ++i) {
     long long x = iv[i];
-    if (i == GI - 1) {
+    if (i == 11) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const long long y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
@@ -617,40 +646,26 @@ __device__ inline void block_sum_glcm(long long (&iv)[GI], A (&fv)[GF], double* 
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
     }
-    if (lane == 0) si[warp * GI + i] = x;
-  }
-#pragma unroll
-  for (int i = 0; i < GF; ++i) {
-    A x = fv[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-    if (lane == 0) sf[warp * GF + i] = x;
+    if (lane == 0) si[warp * GN + i] = x;
   }
   __syncthreads();
   const int t = threadIdx.x;
-  if (t < GI) {
-    long long s = si[t];
-    for (int w = 1; w < C::NW; ++w) s = t == GI - 1 ? (si[w * GI + t] > s ? si[w * GI + t] : s) : s + si[w * GI + t];
-    iout[t] = s;
-  } else if (t < GI + GF) {
-    A s = 0;
-    for (int w = 0; w < C::NW; ++w) s += sf[w * GF + t - GI];
-    fout[t - GI] = s;
+  if (t < GN) {
+    long long v = si[t];
+    for (int w = 1; w < C::NW; ++w) v = t == 11 ? (si[w * GN + t] > v ? si[w * GN + t] : v) : v + si[w * GN + t];
+    out[t] = v;
   }
   __syncthreads();
 }
 
 // Per (ROI, offset) GLCM accumulator handed from the accumulation kernels to
-// k_glcm_final: the GI exact integer sums, then GF sums in the accumulation
-// type.  An all-zero record (T = 0) marks an offset without pairs.
-constexpr int GACC_BYTES = 8 * GI + 8 * GF;
-template <class A>
-__device__ inline void store_gacc(const KParams& p, int64_t item, int oi, const long long* iv, const A* fv,
-                                  bool empty) {
-  unsigned char* g = p.gacc + ((size_t)item * (p.n_dist * p.n_dirs) + oi) * GACC_BYTES;
+// k_glcm_final: the GN integer sums.  An all-zero record (T = 0) marks an
+// offset without pairs.
+constexpr int GACC_BYTES = 8 * GN;
+__device__ inline void store_gacc(const KParams& p, int64_t item, int oi, const long long* iv, bool empty) {
+  long long* g = (long long*)(p.gacc + ((size_t)item * (p.n_dist * p.n_dirs) + oi) * GACC_BYTES);
   const int t = threadIdx.x;
-  if (t < GI) ((long long*)g)[t] = empty ? 0ll : iv[t];
-  else if (t < GI + GF && !empty) ((A*)(g + 8 * GI))[t - GI] = fv[t - GI];
+  if (t < GN) g[t] = empty ? 0ll : iv[t];
 }
 
 // Per-ROI statistics and moment sums handed from the accumulation kernels to
@@ -874,7 +889,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
   __shared__ FastDiv s_fd;
   __shared__ A s_sc[16];
   __shared__ double s_sd[4];
-  __shared__ long long s_i64[16];  // [0..7] pass 1, [8..11] GLCM moments, [12..14] GLCM cells
+  __shared__ long long s_i64[GN + 4];  // pass-1 sums, then the GLCM sums of an offset
   __shared__ int s_idx[4];
   __shared__ A s_pa[10];  // per-ROI scalars: mean (hi, lo), centroids, sums
   __shared__ unsigned s_ncell, s_npair;
@@ -1287,9 +1302,9 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           __syncthreads();
           const int ncell = (int)s_ncell;
           // pass 1 over the cells: marginals and exact integer power sums
-          long long iv[GI];
+          long long iv[GN];
 #pragma unroll
-          for (int k = 0; k < GI; ++k) iv[k] = 0;
+          for (int k = 0; k < GN; ++k) iv[k] = 0;
           for (int s = tid; s < ncell; s += C::NT) {
             const unsigned wv = tab[cells[s]];
             const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
@@ -1320,36 +1335,22 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           }
           __syncthreads();
           if (ncell == 0) {  // no pair for this offset: every feature NaN
-            store_gacc<A>(p, item, oi, s_i64, res, true);
+            store_gacc(p, item, oi, iv, true);
             continue;
           }
-          // pass 2: marginal sums (index order) and mutual information (cells)
-          A fv[GF];
-#pragma unroll
-          for (int k = 0; k < GF; ++k) fv[k] = 0;
+          // pass 2: marginal entropies and inverse differences (exact
+          // fixed-point sums), mutual information over the cells
           const long long Tl = 2 * (long long)s_npair;  // total mass of the symmetric matrix
-          const A invT = (A)1 / (A)(int)Tl, ngA = (A)ng;
           const float Tf = (float)(int)Tl;
-          for (int a = tid; a < ng; a += C::NT) {
-            if (!px[a]) continue;
-            const A pr = (A)px[a] * invT;
-            fv[0] -= pr * alog2(pr);  // HX
-          }
-          for (int s = tid; s < 2 * ng - 1; s += C::NT) {
-            if (!psum[s]) continue;
-            const A pr = (A)psum[s] * invT;
-            fv[1] -= pr * alog2(pr);  // SUMENT
-          }
-          for (int k = tid; k < ng; k += C::NT) {
-            if (!pdiff[k]) continue;
-            const A pr = (A)pdiff[k] * invT, kk = (A)k;
-            fv[2] -= pr * alog2(pr);                        // DIFENTRO
-            fv[3] += pr / ((A)1 + kk);                      // ID = HOM1
-            fv[4] += pr / ((A)1 + kk * kk);                 // IDM = HOM2
-            fv[5] += pr / ((A)1 + kk / ngA);                // IDN
-            fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));  // IDMN
-            if (k >= 1) fv[7] += pr / (kk * kk);            // IV
-          }
+          for (int a = tid; a < ng; a += C::NT)
+            if (px[a]) iv[12] += ent_fx<A>(px[a]);
+          for (int k = tid; k < 2 * ng - 1; k += C::NT)
+            if (psum[k]) iv[13] += ent_fx<A>(psum[k]);
+          for (int k = tid; k < ng; k += C::NT)
+            if (pdiff[k]) {
+              iv[14] += ent_fx<A>(pdiff[k]);
+              invdiff_fx<A>(pdiff[k], k, ng, iv);
+            }
           for (int s = tid; s < ncell; s += C::NT) {
             const unsigned wv = tab[cells[s]];
             const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
@@ -1359,8 +1360,8 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[b]);
             iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
           }
-          block_sum_glcm<C, A>(iv, fv, red, s_i64, res);
-          store_gacc<A>(p, item, oi, s_i64, res, false);  // features: k_glcm_final
+          block_sum_glcm<C>(iv, red, s_i64);
+          store_gacc(p, item, oi, s_i64, false);  // features: k_glcm_final
           // clean up only what this offset touched
           for (int s = tid; s < ncell; s += C::NT) {
             const unsigned h = cells[s];

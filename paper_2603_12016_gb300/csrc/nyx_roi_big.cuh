@@ -648,8 +648,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   unsigned* pdiff = marg + 3 * ng;  // index b - a
   uint16_t* rast = (uint16_t*)(marg + 4 * ng);  // [glcm_raster_cells] bins of padded cells
   __shared__ double red[C::NW * RED_MAX];
-  __shared__ long long s_i64[16];
-  __shared__ A s_res[RED_MAX];
+  __shared__ long long s_i64[GN + 4];
   __shared__ int s_flag;
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
@@ -802,9 +801,9 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       const bool dbg = p.dbg_roi == (int64_t)br.item;
       for (int i = tid; i < 4 * ng; i += BIG_NT) marg[i] = 0;
       __syncthreads();
-      long long iv[GI];
+      long long iv[GN];
 #pragma unroll
-      for (int k = 0; k < GI; ++k) iv[k] = 0;
+      for (int k = 0; k < GN; ++k) iv[k] = 0;
       for (unsigned f = tid; f < ntri; f += BIG_NT) {
         const unsigned cnt = tri[f];
         if (!cnt) continue;
@@ -839,39 +838,26 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       {
         long long t1[1] = {0};
         for (int a = tid; a < ng; a += BIG_NT) t1[0] += px[a];
-        block_sum_i64<C, 1>(t1, red, s_i64 + 13);
-        Tl = s_i64[13];
+        block_sum_i64<C, 1>(t1, red, s_i64 + GN);
+        Tl = s_i64[GN];
       }
       if (Tl == 0) {  // no pair for this offset: every feature NaN
-        store_gacc<A>(p, br.item, oi, s_i64, s_res, true);
+        store_gacc(p, br.item, oi, iv, true);
         __syncthreads();
         continue;
       }
-      A fv[GF];
-#pragma unroll
-      for (int k = 0; k < GF; ++k) fv[k] = 0;
+      // marginal entropies and inverse differences (exact fixed-point sums),
+      // mutual information over the cells
       const float Tf = (float)Tl;
-      const A invT = (A)1 / (A)Tl, ngA = (A)ng;
-      for (int a = tid; a < ng; a += BIG_NT) {
-        if (!px[a]) continue;
-        const A pr = (A)px[a] * invT;
-        fv[0] -= pr * alog2(pr);
-      }
-      for (int s = tid; s < 2 * ng - 1; s += BIG_NT) {
-        if (!psum[s]) continue;
-        const A pr = (A)psum[s] * invT;
-        fv[1] -= pr * alog2(pr);
-      }
-      for (int k = tid; k < ng; k += BIG_NT) {
-        if (!pdiff[k]) continue;
-        const A pr = (A)pdiff[k] * invT, kk = (A)k;
-        fv[2] -= pr * alog2(pr);
-        fv[3] += pr / ((A)1 + kk);
-        fv[4] += pr / ((A)1 + kk * kk);
-        fv[5] += pr / ((A)1 + kk / ngA);
-        fv[6] += pr / ((A)1 + kk * kk / (ngA * ngA));
-        if (k >= 1) fv[7] += pr / (kk * kk);
-      }
+      for (int a = tid; a < ng; a += BIG_NT)
+        if (px[a]) iv[12] += ent_fx<A>(px[a]);
+      for (int k = tid; k < 2 * ng - 1; k += BIG_NT)
+        if (psum[k]) iv[13] += ent_fx<A>(psum[k]);
+      for (int k = tid; k < ng; k += BIG_NT)
+        if (pdiff[k]) {
+          iv[14] += ent_fx<A>(pdiff[k]);
+          invdiff_fx<A>(pdiff[k], k, ng, iv);
+        }
       for (unsigned f = tid; f < ntri; f += BIG_NT) {
         const unsigned cnt = tri[f];
         if (!cnt) continue;
@@ -882,8 +868,8 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
         const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
         iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
       }
-      block_sum_glcm<C, A>(iv, fv, red, s_i64, s_res);
-      store_gacc<A>(p, br.item, oi, s_i64, s_res, false);  // features: k_glcm_final
+      block_sum_glcm<C>(iv, red, s_i64);
+      store_gacc(p, br.item, oi, s_i64, false);  // features: k_glcm_final
       __syncthreads();
     }
   }
