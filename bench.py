@@ -96,8 +96,12 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) per launch of a phase's kernel from one ncu
-# capture of the same command; None once the kernel has changed since.
-TRAFFIC = {}
+# capture (profiles/roi_kernels_nuclei2d_2048.md), keyed by workload, phase
+# and class limits; entries are removed when the kernel changes.
+TRAFFIC = {
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 8192)): 18.45e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 8192)): 13.58e6,
+}
 
 
 def roi_classes(w, lim_pix=None):
@@ -251,6 +255,7 @@ def main() -> int:
                     help="time forward + backward (default for the blobbatch workloads)")
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default class limits")
+    ap.add_argument("--class-limits", default=None, help="warp,small,medium pixel limits instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -339,7 +344,10 @@ def main() -> int:
         return {k: sum(p[k] for p in per) / steps for k in PHASES}
 
     limits = None
-    if not args.no_autotune:
+    if args.class_limits:
+        limits = tuple(int(v) for v in args.class_limits.split(","))
+        ex.set_class_limits(*limits)
+    elif not args.no_autotune:
         limits = ex.autotune(img, mask, reps=3)
     with ClockSampler(local) as clk:
         ms, n_roi = timed(ex, args.steps, args.warmup)
@@ -368,7 +376,7 @@ def main() -> int:
                  "roi_big": cls_px[3] * per_px + 8 * cls_rows[3] * n_col,
                  "final": n_roi * (512 + n_off * 160 + 8 * n_col)}.get(dom, 0)
     dom_gbs = dom_bytes / (phases[dom] * 1e-3) / 1e9
-    traffic = TRAFFIC.get((w.name, dom))
+    traffic = TRAFFIC.get((w.name, dom, tuple(limits) if limits else None))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                 "frac": dom_gbs / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes": int(dom_bytes)}
