@@ -371,8 +371,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   const size_t o_gacc = take((size_t)mr * n_off_all * (8 * (GI_HOST + GF_HOST)));
   // per-ROI statistics / moment sums (64 eight-byte slots)
   const size_t o_sacc = take((size_t)mr * 512);
-  // second key buffer of the multi-block key sort
-  const size_t o_sorttmp = take(mr > SORT_CAP ? 8ull * mr : 0);
+  // key buffer of the key sorts (gathered keys; second run buffer of the multi-block sort)
+  const size_t o_sorttmp = take(8ull * mr);
   cudaError_t e = cudaMalloc(&pl->ws, off);
   if (e != cudaSuccess) {
     delete pl;
@@ -443,7 +443,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.arena_cap = arena_words;
   k.gacc = (unsigned char*)(w + o_gacc);
   k.sacc = (unsigned char*)(w + o_sacc);
-  k.sort_tmp = mr > SORT_CAP ? (unsigned long long*)(w + o_sorttmp) : nullptr;
+  k.sort_tmp = (unsigned long long*)(w + o_sorttmp);
   pl->d_col_map = (int*)(w + o_cmap);
   k.col_map = pl->d_col_map;
   k.n_col = (int)pl->col_names.size();

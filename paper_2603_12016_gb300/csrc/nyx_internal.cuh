@@ -190,7 +190,7 @@ struct KParams {
   // label scan over rows [scan_row0, scan_row1) of the batch (scan_row1 = 0:
   // all rows); the mosaic path scans each band of tiles as it arrives
   int64_t scan_row0, scan_row1;
-  unsigned long long* sort_tmp;    // second key buffer of the multi-block key sort (plans above SORT_CAP)
+  unsigned long long* sort_tmp;    // key buffer of the key sorts [max_rois]
 };
 
 // Fields of the packed big-ROI counter (one atomic hands out the big-ROI
@@ -304,6 +304,24 @@ __device__ inline void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// exclusive scan of `n` unsigned values in shared memory (single warp)
+__device__ inline void warp_exclusive_scan(unsigned* a, int n) {
+  const int lane = threadIdx.x & 31;
+  unsigned carry = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const unsigned v = i < n ? a[i] : 0u;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < n) a[i] = carry + x - v;
+    carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+  }
 }
 
 __device__ inline unsigned lanemask_lt() {

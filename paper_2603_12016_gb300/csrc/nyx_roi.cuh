@@ -247,24 +247,6 @@ __device__ inline unsigned long long block_max_u64(unsigned long long v, double*
   return m;
 }
 
-// exclusive scan of `n` unsigned values in shared memory (single warp)
-__device__ inline void warp_exclusive_scan(unsigned* a, int n) {
-  const int lane = threadIdx.x & 31;
-  unsigned carry = 0;
-  for (int base = 0; base < n; base += 32) {
-    const int i = base + lane;
-    const unsigned v = i < n ? a[i] : 0u;
-    unsigned x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (i < n) a[i] = carry + x - v;
-    carry += __shfl_sync(0xFFFFFFFFu, x, 31);
-  }
-}
-
 // Run-length merge of equal keys held by consecutive lanes (every lane of the
 // warp calls it; `invalid` marks lanes without a key).  Returns the run length
 // in the first lane of each run of valid keys, 0 elsewhere.  Smooth images

@@ -265,43 +265,100 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
   if (lane == 0 && errbits) atomicOr(p.err, errbits);
 }
 
-// Sort the distinct keys ascending (bitonic, one block, shared memory):
-// dense ROI id = rank of its (image, label) key.
+// Sort the distinct keys ascending (one block): dense ROI id = rank of its
+// (image, label) key.  LSD radix sort of 16-bit indices by 8-bit digits over
+// the key bits that differ at all (2 passes for labels below 65,536 in one
+// image), with stable ranks from 8 ballots per digit; the keys are gathered
+// once into sort_tmp.
 __global__ void __launch_bounds__(1024) k_sort_keys(KParams p) {
-  extern __shared__ unsigned long long s_sort[];
+  extern __shared__ unsigned s_sm[];
+  constexpr int NW = 32;
+  unsigned* cnt = s_sm;                     // [NW][256]
+  unsigned* dtot = cnt + NW * 256;          // [256]
+  uint16_t* ix0 = (uint16_t*)(dtot + 256);  // [2][max_rois]
+  __shared__ unsigned long long s_or[NW];
   const unsigned n = *p.n_used;
-  // the host sized s_sort for min(max_rois, SORT_CAP) keys
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (n > (unsigned)SORT_CAP || (int64_t)n > p.max_rois) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       atomicOr(p.err, n > (unsigned)SORT_CAP ? E_SORT_CAP : E_ROI_CAP);
       *p.n_roi = 0;
       if (p.n_roi_out) *p.n_roi_out = (int64_t)n;
     }
     return;
   }
-  unsigned np2 = 1;
-  while (np2 < n) np2 <<= 1;
-  for (unsigned i = threadIdx.x; i < np2; i += blockDim.x)
-    s_sort[i] = i < n ? p.keys[p.slot_list[i]] : EMPTY_KEY;
+  unsigned long long* kv = p.sort_tmp;
+  uint16_t* src = ix0;
+  uint16_t* dst = ix0 + p.max_rois;
+  const unsigned long long k0 = n ? p.keys[p.slot_list[0]] : 0ull;
+  unsigned long long diff = 0;
+  for (unsigned i = tid; i < n; i += blockDim.x) {
+    const unsigned long long k = p.keys[p.slot_list[i]];
+    kv[i] = k;
+    src[i] = (uint16_t)i;
+    diff |= k ^ k0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) diff |= __shfl_xor_sync(0xFFFFFFFFu, diff, o);
+  if (lane == 0) s_or[warp] = diff;
   __syncthreads();
-  for (unsigned k = 2; k <= np2; k <<= 1) {
-    for (unsigned j = k >> 1; j > 0; j >>= 1) {
-      for (unsigned i = threadIdx.x; i < np2; i += blockDim.x) {
-        unsigned ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long a = s_sort[i], c = s_sort[ixj];
-          bool up = (i & k) == 0;
-          if ((a > c) == up) {
-            s_sort[i] = c;
-            s_sort[ixj] = a;
-          }
+  diff = 0;
+  for (int w = 0; w < NW; ++w) diff |= s_or[w];
+  const int nbits = diff ? 64 - __clzll((long long)diff) : 0;
+  const int seg = (((int)(n + NW - 1) / NW) + 31) & ~31;
+  const int lo = min((int)n, warp * seg), hi = min((int)n, lo + seg);
+  for (int shift = 0; shift < nbits; shift += 8) {
+    for (int i = tid; i < NW * 256; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {  // 0: digit counts per warp, 1: stable scatter
+      for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        const bool act = i < hi;
+        const unsigned id = act ? src[i] : 0u;
+        const unsigned dg = act ? (unsigned)(kv[id] >> shift) & 255u : 0u;
+        unsigned peers = __ballot_sync(0xFFFFFFFFu, act);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+          const unsigned bb = __ballot_sync(0xFFFFFFFFu, (dg >> bit) & 1u);
+          peers &= ((dg >> bit) & 1u) ? bb : ~bb;
         }
+        const unsigned before = __popc(peers & lanemask_lt());
+        unsigned base = 0;
+        if (act) base = cnt[warp * 256 + dg];
+        __syncwarp();
+        if (act) {
+          if (pass) dst[base + before] = (uint16_t)id;
+          if (before == 0) cnt[warp * 256 + dg] = base + __popc(peers);
+        }
+        __syncwarp();
       }
       __syncthreads();
+      if (pass == 0) {  // digit-major, then warp, exclusive offsets
+        for (int d = tid; d < 256; d += blockDim.x) {
+          unsigned t = 0;
+          for (int w = 0; w < NW; ++w) t += cnt[w * 256 + d];
+          dtot[d] = t;
+        }
+        __syncthreads();
+        if (warp == 0) warp_exclusive_scan(dtot, 256);
+        __syncthreads();
+        for (int d = tid; d < 256; d += blockDim.x) {
+          unsigned run = dtot[d];
+          for (int w = 0; w < NW; ++w) {
+            const unsigned c = cnt[w * 256 + d];
+            cnt[w * 256 + d] = run;
+            run += c;
+          }
+        }
+        __syncthreads();
+      }
     }
+    uint16_t* t = src;
+    src = dst;
+    dst = t;
   }
-  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) p.sorted_keys[i] = s_sort[i];
-  if (threadIdx.x == 0) {
+  for (unsigned i = tid; i < n; i += blockDim.x) p.sorted_keys[i] = kv[src[i]];
+  if (tid == 0) {
     *p.n_roi = n;
     if (p.n_roi_out) *p.n_roi_out = (int64_t)n;
     if ((int64_t)n > p.cap_roi) atomicOr(p.err, E_ROI_CAP);
@@ -579,9 +636,7 @@ cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st) {
 cudaError_t launch_sort_setup(const KParams& p, int nsm, cudaStream_t st) {
   cudaError_t e;
   if (p.max_rois <= SORT_CAP) {
-    unsigned np2 = 1;
-    while (np2 < (unsigned)p.max_rois) np2 <<= 1;
-    const int smem = (int)(8 * np2);
+    const int smem = (int)(4 * (32 * 256 + 256) + 4 * p.max_rois);  // counts + two u16 index buffers
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
