@@ -146,10 +146,52 @@ __device__ inline void chunk_cells(const KParams& p, const BigBox& bx, unsigned 
     }
 #pragma unroll
     for (int u = 0; u < BIG_U; ++u) {
-      const bool in = cb + u * BIG_NT + threadIdx.x < c1 && lab[u] == bx.label;
-      f(in, xs[u], ys[u], zs[u], in ? Enc<T>::enc(val[u]) : 0u);
+      const unsigned c = cb + u * BIG_NT + threadIdx.x;
+      const bool in = c < c1 && lab[u] == bx.label;
+      f(in, xs[u], ys[u], zs[u], in ? Enc<T>::enc(val[u]) : 0u, c);
     }
   }
+}
+
+// Visit the ROI voxels of cells [c0, c1) in full warps: cells are streamed
+// as in chunk_cells, each warp compacts its ROI cells into a 64-entry queue
+// in shared memory (qc: cell index, qe: encoded value) and calls
+// f(valid, x, y, z, e) once per 32 queued voxels, then once for the remainder
+// (lanes past it have valid = false).  Work per voxel runs on full warps
+// instead of on every lane of partly filled ones.
+template <class T, class F>
+__device__ inline void chunk_voxels(const KParams& p, const BigBox& bx, unsigned c0, unsigned c1, unsigned* qc,
+                                    unsigned* qe, F f) {
+  const int lane = threadIdx.x & 31;
+  int qn = 0;  // warp-uniform queue length (< 32 between flushes)
+  auto flush32 = [&]() {
+    const unsigned c = qc[lane], e = qe[lane];
+    int x, y, z;
+    bx.offset(c, x, y, z, p);
+    f(true, x, y, z, e);
+    __syncwarp();
+    if (lane < qn - 32) {
+      qc[lane] = qc[32 + lane];
+      qe[lane] = qe[32 + lane];
+    }
+    __syncwarp();
+    qn -= 32;
+  };
+  chunk_cells<T>(p, bx, c0, c1, [&](bool in, int, int, int, unsigned e, unsigned c) {
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, in);
+    if (in) {
+      const unsigned pos = qn + __popc(bal & lanemask_lt());
+      qc[pos] = c;
+      qe[pos] = e;
+    }
+    qn += __popc(bal);
+    __syncwarp();
+    if (qn >= 32) flush32();
+  });
+  int x = 0, y = 0, z = 0;
+  const bool v = lane < qn;
+  if (v) bx.offset(qc[lane], x, y, z, p);
+  f(v, x, y, z, v ? qe[lane] : 0u);
 }
 
 // true in every thread of the one block that finishes last among `total`
@@ -333,7 +375,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
     long long s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     KSum<A> fs[5];  // float images: sum I, x I, y I, z I, I^2
     unsigned* gvh = reg + L.vhist;
-    chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e) {
+    chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e, unsigned) {
       unsigned hb = 0xFFFFFFFFu, vb = 0xFFFFFFFFu;
       if (in) {
         s[4] += x;
@@ -509,6 +551,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
   __shared__ double red[C::NW * RED_MAX];
   __shared__ A res[NV + 16];
   __shared__ int s_flag;
+  __shared__ unsigned s_qc[C::NW * 64], s_qe[C::NW * 64];  // per-warp voxel queues
   const int tid = threadIdx.x, warp = tid >> 5;
   const unsigned long long ctr = *p.big_ctr;
   const int n_big = big_count(ctr);
@@ -541,7 +584,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
     for (int i = 0; i < 8; ++i) acc[i] = 0;
 #pragma unroll
     for (int i = 0; i < NM; ++i) mi[i] = mb[i] = 0;
-    chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e) {
+    chunk_voxels<T>(p, bx, c0, c1, s_qc + warp * 64, s_qe + warp * 64, [&](bool in, int x, int y, int z, unsigned e) {
       if (!in) return;
       const A v = Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e);
       if (do_st) {
@@ -650,6 +693,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   __shared__ double red[C::NW * RED_MAX];
   __shared__ long long s_i64[GN + 4];
   __shared__ int s_flag;
+  __shared__ unsigned s_qc[C::NW * 64];  // per-warp queues of ROI raster cells
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
   const int n_big = big_count(ctr);
@@ -726,10 +770,14 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       }
       __syncthreads();
       // count: every ROI cell of the span with its neighbour at each offset of
-      // the group; equal cells in consecutive lanes merge into one atomic
-      for (unsigned ib = 0; ib < span; ib += BIG_NT) {
-        const unsigned i = ib + tid;
-        const unsigned a = i < span ? rast[i] : SENT;
+      // the group.  Each warp queues its ROI cells (raster indices) and runs
+      // the offset loop on full warps of them; equal cells in consecutive
+      // lanes merge into one atomic.
+      unsigned* q = s_qc + (tid >> 5) * 64;
+      const int lane = tid & 31;
+      int qn = 0;  // warp-uniform
+      auto count = [&](bool v, unsigned i) {
+        const unsigned a = v ? rast[i] : SENT;
 #pragma unroll
         for (int j = 0; j < MAX_DIRS; ++j) {
           if (j >= og) break;  // uniform
@@ -741,7 +789,23 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
           const unsigned n = run_leader(key, 0xFFFFFFFFu);
           if (n) atomicAdd(&tris[(size_t)j * tstride + key], n);
         }
+      };
+      for (unsigned ib = 0; ib < span; ib += BIG_NT) {
+        const unsigned i = ib + tid;
+        const bool in = i < span && rast[i] != SENT;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, in);
+        if (in) q[qn + __popc(bal & lanemask_lt())] = i;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+          count(true, q[lane]);
+          __syncwarp();
+          if (lane < qn - 32) q[lane] = q[32 + lane];
+          __syncwarp();
+          qn -= 32;
+        }
       }
+      count(lane < qn, lane < qn ? q[lane] : 0u);
       __syncthreads();
     } else {
       // ---- global-memory path (the halo does not fit): BIG_GSPAN chunks ------
@@ -749,7 +813,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       const unsigned c0 = (unsigned)sp * BIG_GSPAN * BIG_CHUNK;
       const unsigned c1 = (unsigned)min((unsigned long long)bx.cells,
                                         (unsigned long long)c0 + (unsigned long long)BIG_GSPAN * BIG_CHUNK);
-      chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e) {
+      chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e, unsigned) {
         const unsigned a = in ? gbin(e) : 0u;
         const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
         int nl[MAX_DIRS];
