@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
   __shared__ long long s_i64[16];
   __shared__ A s_sc[16];
   __shared__ int s_flag;
+  __shared__ unsigned s_qc[C::NW * 64], s_qe[C::NW * 64];  // per-warp voxel queues
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
   const int n_big = big_count(ctr);
@@ -375,7 +376,8 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
     long long s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     KSum<A> fs[5];  // float images: sum I, x I, y I, z I, I^2
     unsigned* gvh = reg + L.vhist;
-    chunk_cells<T>(p, bx, c0, c1, [&](bool in, int x, int y, int z, unsigned e, unsigned) {
+    chunk_voxels<T>(p, bx, c0, c1, s_qc + (tid >> 5) * 64, s_qe + (tid >> 5) * 64,
+                    [&](bool in, int x, int y, int z, unsigned e) {
       unsigned hb = 0xFFFFFFFFu, vb = 0xFFFFFFFFu;
       if (in) {
         s[4] += x;
