@@ -62,7 +62,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -99,8 +99,10 @@ class ClockSampler:
 # capture (profiles/roi_kernels_nuclei2d_2048.md), keyed by workload, phase
 # and class limits; entries are removed when the kernel changes.
 TRAFFIC = {
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 8192)): 18.45e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 8192)): 18.49e6,
     ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 8192)): 13.58e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 4096)): 18.46e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 4096)): 13.58e6,
 }
 
 
