@@ -44,7 +44,7 @@ struct RoiClass {
 };
 using ClassW = RoiClass<32, 256, 1024>;    // one warp per ROI
 using ClassS = RoiClass<128, 1024, 4096>;
-using ClassM = RoiClass<256, 8192, 16384>;
+using ClassM = RoiClass<512, 8192, 16384>;
 
 constexpr int RED_MAX = 64;  // max values per block reduction
 
