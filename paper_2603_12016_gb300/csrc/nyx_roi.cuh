@@ -610,32 +610,43 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
 }
 
 // Block reduction of the GN GLCM sums (index 11 is a maximum); results in
-// out (shared memory) for every thread.
+// out (shared memory) for every thread.  Within a warp the sums use recursive
+// halving (reduce-scatter): at lane bit o each lane keeps half of its values
+// and swaps the other half with lane ^ o, so 32 slots cost 16 + 8 + 4 + 2 + 1
+// exchanges instead of 5 per value; lane l ends with the warp total of slot
+// l.  The maximum takes a plain butterfly.
 template <class C>
 __device__ inline void block_sum_glcm(long long (&iv)[GN], double* scratch_d, long long* out) {
   long long* si = (long long*)scratch_d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long mx = iv[11];
 #pragma unroll
-  for (int i = 0; i < GN; ++i) {
-    long long x = iv[i];
-    if (i == 11) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
-        x = y > x ? y : x;
-      }
-    } else {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-    }
-    if (lane == 0) si[warp * GN + i] = x;
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+    mx = y > mx ? y : mx;
   }
+  long long v[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = i < GN && i != 11 ? iv[i] : 0ll;
+#pragma unroll
+  for (int h = 16, o = 16; h > 0; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const long long send = up ? v[i] : v[i + h];
+      const long long keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+    }
+  }
+  // lane l holds slot l: at bit o the lane kept the half selected by its bit o
+  if (lane < GN && lane != 11) si[warp * GN + lane] = v[0];
+  if (lane == 0) si[warp * GN + 11] = mx;
   __syncthreads();
   const int t = threadIdx.x;
   if (t < GN) {
-    long long v = si[t];
-    for (int w = 1; w < C::NW; ++w) v = t == 11 ? (si[w * GN + t] > v ? si[w * GN + t] : v) : v + si[w * GN + t];
-    out[t] = v;
+    long long r = si[t];
+    for (int w = 1; w < C::NW; ++w) r = t == 11 ? (si[w * GN + t] > r ? si[w * GN + t] : r) : r + si[w * GN + t];
+    out[t] = r;
   }
   __syncthreads();
 }
