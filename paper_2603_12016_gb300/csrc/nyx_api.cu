@@ -369,6 +369,9 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   // per (ROI, offset) GLCM accumulators (GI int64 + GF sums in 8-byte slots)
   const int n_off_all = p.glcm_levels > 0 ? p.n_dist * (p.ndim == 3 ? 13 : 4) : 0;
   const size_t o_gacc = take((size_t)mr * n_off_all * (8 * (GI_HOST + GF_HOST)));
+  // inverse-difference weights per difference level (float and double)
+  const int ngw = p.glcm_levels > 0 ? p.glcm_levels : 1;
+  const size_t o_wtab_f = take(4ull * 5 * ngw), o_wtab_d = take(8ull * 5 * ngw);
   // per-ROI statistics / moment sums (64 eight-byte slots)
   const size_t o_sacc = take((size_t)mr * 512);
   // key buffer of the key sorts (gathered keys; second run buffer of the multi-block sort)
@@ -443,6 +446,19 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.arena_cap = arena_words;
   k.gacc = (unsigned char*)(w + o_gacc);
   k.sacc = (unsigned char*)(w + o_sacc);
+  k.wtab_f = (const float*)(w + o_wtab_f);
+  k.wtab_d = (const double*)(w + o_wtab_d);
+  std::vector<float> wf(5ull * ngw);
+  std::vector<double> wd(5ull * ngw);
+  for (int kk = 0; kk < ngw; ++kk) {
+    const double d = kk, g = ngw;
+    const double ww[5] = {1.0 / (1.0 + d), 1.0 / (1.0 + d * d), 1.0 / (1.0 + d / g), 1.0 / (1.0 + d * d / (g * g)),
+                          kk >= 1 ? 1.0 / (d * d) : 0.0};
+    for (int i = 0; i < 5; ++i) {
+      wd[5 * kk + i] = ww[i];
+      wf[5 * kk + i] = (float)ww[i];
+    }
+  }
   k.sort_tmp = (unsigned long long*)(w + o_sorttmp);
   pl->d_col_map = (int*)(w + o_cmap);
   k.col_map = pl->d_col_map;
@@ -456,6 +472,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.lim_pix[2] = 8192;
   k.lim_cells[2] = 16384;
   e = cudaMemcpy(pl->d_col_map, pl->col_map.data(), 4ull * Q_TOTAL, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w + o_wtab_f, wf.data(), 4ull * 5 * ngw, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w + o_wtab_d, wd.data(), 8ull * 5 * ngw, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(small, 0, 64);
   if (e == cudaSuccess) {
     e = launch_init_table(k, hcap, 0);

@@ -187,6 +187,8 @@ struct KParams {
   unsigned long long arena_cap;    // words
   unsigned char* gacc;             // [max rows][n_off] GLCM accumulators
   unsigned char* sacc;             // [max rows] statistics / moment sums for k_stats_final
+  const float* wtab_f;             // [Ng][5] inverse-difference weights 1/(1+k), 1/(1+k^2),
+  const double* wtab_d;            //   1/(1+k/Ng), 1/(1+k^2/Ng^2), 1/k^2 (0 at k = 0)
   // label scan over rows [scan_row0, scan_row1) of the batch (scan_row1 = 0:
   // all rows); the mosaic path scans each band of tiles as it arrives
   int64_t scan_row0, scan_row1;

@@ -514,15 +514,16 @@ __device__ inline long long ent_fx(unsigned c) {
   const A ca = (A)c;
   return a2ll(ca * alog2(ca) * (A)16777216);
 }
-// the inverse-difference family of one difference-marginal entry (c at k)
+// the inverse-difference family of one difference-marginal entry (c at k),
+// with the weights from the plan's table (rounded once on the host)
 template <class A>
-__device__ inline void invdiff_fx(unsigned c, int k, int ng, long long* s) {
-  const A ca = (A)c, kk = (A)k, ngA = (A)ng, sc = (A)4294967296.0;
-  s[15] += a2ll(ca / ((A)1 + kk) * sc);
-  s[16] += a2ll(ca / ((A)1 + kk * kk) * sc);
-  s[17] += a2ll(ca / ((A)1 + kk / ngA) * sc);
-  s[18] += a2ll(ca / ((A)1 + kk * kk / (ngA * ngA)) * sc);
-  if (k >= 1) s[19] += a2ll(ca / (kk * kk) * sc);
+__device__ inline void invdiff_fx(const KParams& p, unsigned c, int k, long long* s) {
+  const A* w;
+  if constexpr (std::is_same<A, float>::value) w = p.wtab_f + 5 * k;
+  else w = p.wtab_d + 5 * k;
+  const A ca = (A)c * (A)4294967296.0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) s[15 + i] += a2ll(ca * __ldg(w + i));
 }
 
 // GLCM features of one offset (Table S3 rows 140-174): every moment-type
@@ -1342,7 +1343,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           for (int k = tid; k < ng; k += C::NT)
             if (pdiff[k]) {
               iv[14] += ent_fx<A>(pdiff[k]);
-              invdiff_fx<A>(pdiff[k], k, ng, iv);
+              invdiff_fx<A>(p, pdiff[k], k, iv);
             }
           for (int s = tid; s < ncell; s += C::NT) {
             const unsigned wv = tab[cells[s]];

@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       for (int k = tid; k < ng; k += BIG_NT)
         if (pdiff[k]) {
           iv[14] += ent_fx<A>(pdiff[k]);
-          invdiff_fx<A>(pdiff[k], k, ng, iv);
+          invdiff_fx<A>(p, pdiff[k], k, iv);
         }
       for (unsigned f = tid; f < ntri; f += BIG_NT) {
         const unsigned cnt = tri[f];
