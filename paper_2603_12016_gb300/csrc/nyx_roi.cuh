@@ -1246,6 +1246,15 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         s_ncell = 0;
         s_npair = 0;
       }
+      // the pixel list's coordinates are not needed after the moments: keep
+      // each pixel's padded raster index there instead of decoding it per offset
+      for (int i = tid; i < n; i += C::NT) {
+        const unsigned c = pc[i];
+        const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
+        const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
+        const int z = NDIM == 3 ? (int)(c >> 22) : 0;
+        pc[i] = (unsigned)(((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad));
+      }
       for (int di = 0; di < p.n_dist; ++di) {
         for (int dir = 0; dir < p.n_dirs; ++dir) {
           const int oi = di * p.n_dirs + dir;
@@ -1257,11 +1266,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             const int i = i0 + lane;
             unsigned key = 0xFFFFFFFFu;
             if (i < n) {
-              const unsigned c = pc[i];
-              const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
-              const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
-              const int z = NDIM == 3 ? (int)(c >> 22) : 0;
-              const int ci = ((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad);
+              const unsigned ci = pc[i];
               const unsigned a = raster[ci], b = raster[ci + olin];
               if (b != 0xFFFFu) key = a < b ? (a << 8) | b : (b << 8) | a;
             }
