@@ -61,7 +61,7 @@ typedef enum { NYX_U16 = 0, NYX_I16 = 1, NYX_F32 = 2 } nyx_dtype;
 typedef enum { NYX_PREC_FP32_COMP = 0, NYX_PREC_FP64_PLAIN = 1 } nyx_prec;
 
 /* Flags of nyx_extract. */
-#define NYX_SAVE_FOR_BACKWARD 1u /* keep per-ROI state for nyx_backward */
+#define NYX_SAVE_FOR_BACKWARD 1u /* keep per-ROI state (and the label -> ROI map) for nyx_backward */
 #define NYX_SYNC 2u              /* synchronise the stream and return the device error word */
 
 /* Hyperparameters of one plan.  POD; set struct_size = sizeof(nyx_params)
@@ -213,8 +213,11 @@ nyx_status nyx_sync_status(nyx_plan* plan, void* stream);
  * Non-smooth columns (min/max, order statistics, histogram, GLCM, binary
  * moments, geometry) contribute nothing.  Not in the paper: it makes the
  * features usable as a differentiable layer for the AI/ML use the paper's
- * introduction motivates.  Errors: NYX_ERR_STATE (no saved forward),
- * NYX_ERR_ARG, NYX_ERR_CUDA. */
+ * introduction motivates.  When d_img / d_mask are the buffers of that
+ * forward pass, its label -> ROI map is reused (the forward pass kept it);
+ * otherwise the map is rebuilt by a label scan of d_mask.  Any other call on
+ * the plan releases a kept map first.  Errors: NYX_ERR_STATE (no saved
+ * forward), NYX_ERR_ARG, NYX_ERR_CUDA. */
 nyx_status nyx_backward(nyx_plan* plan, const void* d_img, const int32_t* d_mask, const double* d_grad_table,
                         float* d_grad_img, void* stream);
 

@@ -84,6 +84,11 @@ struct nyx_plan {
   double* d_saved = nullptr;
   unsigned* d_dbg = nullptr;
   bool have_saved = false;
+  // after a forward pass saved for backward, the label table (label -> ROI
+  // map) stays filled for the backward pass on the same image and mask
+  bool table_live = false;
+  const void* live_img = nullptr;
+  const int32_t* live_mask = nullptr;
   int64_t saved_rows = 0;
   int n_off = 0;
   int64_t dbg_roi = -1;
@@ -552,12 +557,23 @@ static nyx_status read_err(nyx_plan* pl, cudaStream_t st) {
   return NYX_OK;
 }
 
+// Empty the label table left filled by a forward pass saved for backward
+// (stream-ordered before the caller's next scan).
+static nyx_status flush_live(nyx_plan* pl, cudaStream_t st) {
+  if (!pl->table_live) return NYX_OK;
+  pl->table_live = false;
+  KParams k;
+  memcpy(&k, &pl->kp, sizeof k);
+  return run_reset(pl, k, st);
+}
+
 nyx_status nyx_count_rois(nyx_plan* pl, const void* d_img, const int32_t* d_mask, int64_t* n_roi, void* stream) {
   if (!pl || !n_roi) return NYX_ERR_ARG;
   nyx_status s = check_ptrs(pl, d_img, d_mask);
   if (s != NYX_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+  if ((s = flush_live(pl, st)) != NYX_OK) return s;
   KParams k = pl->kp;
   k.img = d_img;
   k.mask = d_mask;
@@ -628,7 +644,8 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
   }
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
-  if ((s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  // a forward pass saved for backward keeps the label table for nyx_backward
+  if (!(k.need & NEED_SAVE) && (s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));
   return NYX_OK;
 }
@@ -711,6 +728,7 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
     k.dbg_roi = pl->dbg_roi;
     k.dbg_glcm = pl->d_dbg;
   }
+  if ((s = flush_live(pl, st)) != NYX_OK) return s;
   if (pl->prof_slots > 0) {  // profiled: direct launches with phase events
     cudaEvent_t* ev = &pl->ev[(size_t)(pl->prof_count % pl->prof_slots) * (NYX_N_PHASES + 1)];
     if ((s = enqueue_extract(pl, k, ev, st)) != NYX_OK) return s;
@@ -719,6 +737,11 @@ nyx_status nyx_extract(nyx_plan* pl, const void* d_img, const int32_t* d_mask, d
     if ((s = launch_graph(pl, k, st)) != NYX_OK) return s;
   } else {
     if ((s = enqueue_extract(pl, k, nullptr, st)) != NYX_OK) return s;
+  }
+  if (k.need & NEED_SAVE) {
+    pl->table_live = true;
+    pl->live_img = d_img;
+    pl->live_mask = d_mask;
   }
   if (flags & NYX_SYNC) return read_err(pl, st);
   return NYX_OK;
@@ -767,6 +790,7 @@ nyx_status nyx_extract_tiles(nyx_plan* pl, int64_t tile_w, int64_t tile_h, nyx_t
   k.cap_roi = cap_roi < prm.max_rois ? cap_roi : prm.max_rois;
   k.n_roi_out = d_n_roi;
   pl->have_saved = false;
+  if ((s = flush_live(pl, st)) != NYX_OK) return s;
   NYX_CUDA(c, launch_begin(k, st));
   // make sure both staging buffers are free before the first fill
   for (int i = 0; i < 2; ++i) NYX_CUDA(c, cudaEventRecord(pl->stage_ev[i], st));
@@ -943,6 +967,7 @@ nyx_status nyx_debug_bins(nyx_plan* pl, const void* d_img, const int32_t* d_mask
   k.mask = d_mask;
   k.vec = (k.nx % 4) == 0;
   k.cap_roi = pl->prm.max_rois;
+  if ((s = flush_live(pl, st)) != NYX_OK) return s;
   if ((s = run_front(pl, k, st)) != NYX_OK) return s;
   if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
   NYX_CUDA(c, launch_debug_bins(k, d_bins, c->nsm, st));
@@ -965,9 +990,14 @@ nyx_status nyx_backward(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   k.vec = (k.nx % 4) == 0;
   k.saved = pl->d_saved;
   k.cap_roi = pl->prm.max_rois;
-  // rebuild the label -> ROI map of this image (the forward pass released it)
-  if ((s = run_front(pl, k, st)) != NYX_OK) return s;
-  if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
+  // the label -> ROI map of the saved forward pass is still in the table when
+  // the image and mask are the same buffers; otherwise rebuild it
+  if (!(pl->table_live && pl->live_img == d_img && pl->live_mask == d_mask)) {
+    if ((s = flush_live(pl, st)) != NYX_OK) return s;
+    if ((s = run_front(pl, k, st)) != NYX_OK) return s;
+    if ((s = run_sort_setup(pl, k, st)) != NYX_OK) return s;
+  }
+  pl->table_live = false;
   cudaError_t e = launch_backward(k, d_grad_table, d_grad_img, c->nsm, st);
   if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "backward launch failed: %s", cudaGetErrorString(e));
   return run_reset(pl, k, st);

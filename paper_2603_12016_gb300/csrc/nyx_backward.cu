@@ -56,9 +56,13 @@ __device__ inline double choose(int n, int k) {
   return r;
 }
 
+// m00^(1 + o/2) (2D) or m00^(1 + o/3) (3D) for o = 0..3, from one square or
+// cube root (no pow on the FP64 pipe)
 template <int NDIM>
-__device__ inline double gnorm(double m00, int o) {
-  return NDIM == 2 ? pow(m00, 1.0 + o / 2.0) : pow(m00, 1.0 + o / 3.0);
+__device__ inline void gnorm_table(double m00, double t[4]) {
+  const double r = NDIM == 2 ? sqrt(m00) : cbrt(m00);
+  t[0] = m00;
+  for (int o = 1; o < 4; ++o) t[o] = t[o - 1] * r;
 }
 
 // partial derivatives of Hu's invariants with respect to
@@ -143,19 +147,22 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
       }
     }
     if (m2 > 0) {
-      c[2] += gget(p, g, Q_STATS + S_STD_B) / (2 * sqrt(m2));
+      // powers m2^(-k/2) from one reciprocal and one square root
+      const double sq = sqrt(m2), ri = 1.0 / m2, rh = ri / sq;  // m2^-1, m2^-1.5
+      const double r2 = ri * ri, r25 = r2 / sq, r3 = r2 * ri, r35 = r3 / sq, r4 = r2 * r2;
+      c[2] += gget(p, g, Q_STATS + S_STD_B) / (2 * sq);
       const double gs = gget(p, g, Q_STATS + S_SKEW);
-      c[3] += gs * pow(m2, -1.5);
-      c[2] -= 1.5 * gs * m3 * pow(m2, -2.5);
+      c[3] += gs * rh;
+      c[2] -= 1.5 * gs * m3 * r25;
       const double gk = gget(p, g, Q_STATS + S_KURT) + gget(p, g, Q_STATS + S_EXKURT);
-      c[4] += gk * pow(m2, -2.0);
-      c[2] -= 2.0 * gk * m4 * pow(m2, -3.0);
+      c[4] += gk * r2;
+      c[2] -= 2.0 * gk * m4 * r3;
       const double gh = gget(p, g, Q_STATS + S_HSKEW);
-      c[5] += gh * pow(m2, -2.5);
-      c[2] -= 2.5 * gh * m5 * pow(m2, -3.5);
+      c[5] += gh * r25;
+      c[2] -= 2.5 * gh * m5 * r35;
       const double gf = gget(p, g, Q_STATS + S_HFLAT);
-      c[6] += gf * pow(m2, -3.0);
-      c[2] -= 3.0 * gf * m6 * pow(m2, -4.0);
+      c[6] += gf * r3;
+      c[2] -= 3.0 * gf * m6 * r4;
     }
     for (int j = 2; j <= 6; ++j) {  // c_j (j/N) (d^(j-1) - m_(j-1))
       a[j - 1] += c[j] * j / N;
@@ -191,6 +198,9 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
       double geta[NM];
       for (int k = 0; k < NM; ++k) geta[k] = 0;
       const double mu00 = MU[0];
+      double nmu[4], nM[4];  // normalisations of the central and raw moments by order
+      gnorm_table<NDIM>(mu00, nmu);
+      gnorm_table<NDIM>(M00, nM);
       for (int pp = 0; pp <= 3; ++pp)
         for (int qq = 0; pp + qq <= 3; ++qq)
           for (int rr = 0; rr <= (NDIM == 3 ? 3 - pp - qq : 0); ++rr) {
@@ -201,7 +211,7 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
         const int ie[7] = {bidx<2>(2, 0, 0), bidx<2>(0, 2, 0), bidx<2>(1, 1, 0), bidx<2>(3, 0, 0),
                            bidx<2>(2, 1, 0), bidx<2>(1, 2, 0), bidx<2>(0, 3, 0)};
         double e[7], dh[7][7];
-        for (int t = 0; t < 7; ++t) e[t] = MU[ie[t]] / gnorm<2>(mu00, t < 3 ? 2 : 3);
+        for (int t = 0; t < 7; ++t) e[t] = MU[ie[t]] / nmu[t < 3 ? 2 : 3];
         hu_partials(e, dh);
         for (int h = 0; h < 7; ++h) {
           const double gh = gget(p, g, Q_MOM + F_HU * 20 + h);
@@ -219,7 +229,7 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
             const int k = bidx<NDIM>(pp, qq, rr), o = pp + qq + rr;
             if (o >= 2 && geta[k] != 0) {
               const double gam = NDIM == 2 ? 1.0 + o / 2.0 : 1.0 + o / 3.0;
-              const double den = gnorm<NDIM>(mu00, o);
+              const double den = nmu[o];
               gmu[k] += geta[k] / den;
               cst -= geta[k] * gam * (MU[k] / den) / mu00;
             }
@@ -244,7 +254,7 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
             if (NDIM == 2) {
               const double gn = gget(p, g, Q_MOM + F_NU * 20 + k);
               if (gn != 0) {
-                const double den = gnorm<NDIM>(M00, o), gam = 1.0 + o / 2.0;
+                const double den = nM[o], gam = 1.0 + o / 2.0;
                 double Mk = 0;  // raw moment from the central ones
                 for (int i2 = 0; i2 <= pp; ++i2)
                   for (int j2 = 0; j2 <= qq; ++j2)

@@ -946,9 +946,12 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
 // compacts the values in raster order and sorts them with an LSD radix sort
 // in the ROI's arena region (stable ranks from 8 ballots per digit, as in the
 // block path).
+constexpr int BIG_SORT_SMEM = 23552;  // values sorted in shared memory (two buffers, 188 KB)
+
 template <class T, class A>
 __global__ void __launch_bounds__(BIG_NT) k_big_order(KParams p, int ndim) {
   using C = ClassBig;
+  extern __shared__ __align__(16) unsigned char smem_o[];
   __shared__ unsigned cnt[C::NW * 256];
   __shared__ unsigned dtot[256];
   __shared__ double red[C::NW * RED_MAX];
@@ -967,8 +970,11 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order(KParams p, int ndim) {
     bx.init(p, r, ndim);
     const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
     const int n = (int)r.n;
-    unsigned* src = p.arena + br.arena + L.fsort;
-    unsigned* dst = src + n;
+    // ping-pong buffers in shared memory when the values fit, else in the
+    // ROI's arena region
+    const bool in_smem = n <= BIG_SORT_SMEM;
+    unsigned* src = in_smem ? (unsigned*)smem_o : p.arena + br.arena + L.fsort;
+    unsigned* dst = in_smem ? src + BIG_SORT_SMEM : src + n;
     // compaction in raster order
     if (tid == 0) s_wb[C::NW] = 0;
     __syncthreads();
@@ -1108,9 +1114,17 @@ cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
   }
   if (p.need & NEED_ORDER) {
     auto kern = k_big_order<T, A>;
+    const int smem = 8 * BIG_SORT_SMEM;
+    static int configured[64] = {0};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev >= 64 || !configured[dev]) {
+      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+      if (dev < 64) configured[dev] = 1;
+    }
     int nb = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BIG_NT, 0)) != cudaSuccess) return e;
-    kern<<<(nb > 0 ? nb : 1) * nsm, BIG_NT, 0, st>>>(p, NDIM);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BIG_NT, smem)) != cudaSuccess) return e;
+    kern<<<(nb > 0 ? nb : 1) * nsm, BIG_NT, smem, st>>>(p, NDIM);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
