@@ -122,3 +122,26 @@ def test_backward_big_rois_f32():
     w = W.blob_batch_f32(batch=2, size=256, seed=2305, roi_range=(3, 5), px_range=(9000, 20000))
     assert np.bincount(w.mask.ravel())[1:].max() > 8192
     _check(w, 2, n_fd=8)
+
+
+def test_backward_label_map_kept_or_rebuilt():
+    """The forward pass saved for backward keeps its label -> ROI map: a
+    backward on the same buffers reuses it, one on copies of them (or after
+    another call released it) rebuilds it; all three give the same gradient."""
+    from paper_2603_12016_gb300 import nyx
+
+    w = W.config("blobbatch_small")
+    img = torch.from_numpy(w.image).cuda()
+    mask = torch.from_numpy(w.mask).cuda()
+    ex = nyx.Extractor(w.image.shape, torch.float32, glcm_levels=0, max_rois=1024, features=SMOOTH + FAMILIES)
+    table = ex(img, mask, save_for_backward=True)
+    g = torch.randn(table.shape, dtype=torch.float64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    g_same = ex.backward(img, mask, g)                       # kept map
+    ex(img, mask, save_for_backward=True)
+    g_copy = ex.backward(img.clone(), mask.clone(), g)       # other buffers: rebuilt map
+    ex(img, mask, save_for_backward=True)
+    assert ex.count_rois(img, mask) == table.shape[0]        # releases the kept map
+    g_after = ex.backward(img, mask, g)
+    torch.cuda.synchronize()
+    assert torch.equal(g_same, g_copy) and torch.equal(g_same, g_after)
+    assert torch.count_nonzero(g_same[mask == 0]) == 0 and torch.count_nonzero(g_same) > 0
