@@ -66,6 +66,7 @@ __host__ __device__ inline int glcm_group(int ng, int n_off) {
   const int padded = (tri + 3) & ~3;
   int g = padded > 0 ? GLCM_TRI_WORDS / padded : n_off;
   if (g < 1) g = 1;
+  if (g > MAX_DIRS) g = MAX_DIRS;  // per-lane neighbour arrays hold one direction set
   return g < n_off ? g : n_off;
 }
 

@@ -140,6 +140,8 @@ __device__ inline float asqrt(float x) { return sqrtf(x); }
 __device__ inline double asqrt(double x) { return sqrt(x); }
 __device__ inline float aexp(float x) { return expf(x); }
 __device__ inline double aexp(double x) { return exp(x); }
+__device__ inline float aexpm1(float x) { return expm1f(x); }
+__device__ inline double aexpm1(double x) { return expm1(x); }
 __device__ inline float acbrt(float x) { return cbrtf(x); }
 __device__ inline double acbrt(double x) { return cbrt(x); }
 
@@ -485,8 +487,13 @@ __device__ inline float i128f(__int128 x) {
 }
 template <class A>
 __device__ inline A i128A(__int128 x) {
-  if constexpr (std::is_same<A, float>::value) return i128f(x);
-  else return (double)(long long)(x >> 64) * 18446744073709551616.0 + (double)(unsigned long long)x;
+  if constexpr (std::is_same<A, float>::value) {
+    return i128f(x);
+  } else {  // magnitude first (its two halves are non-negative), then the sign
+    const unsigned __int128 u = x < 0 ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
+    const double m = (double)(unsigned long long)(u >> 64) * 18446744073709551616.0 + (double)(unsigned long long)u;
+    return x < 0 ? -m : m;
+  }
 }
 
 // GLCM sums of one offset, reduced over the block; all are integers, so they
@@ -495,7 +502,7 @@ __device__ inline A i128A(__int128 x) {
 // 1-based levels) and d = |a - b|:
 //   [0] T = sum C            [1..4] sum C k^m      [5..6] sum C d^m
 //   [7] sum C i^2            [8] sum C^2           [9] sum C log2 C  (2^-24)
-//   [10] sum C log2(C T / (P_i P_j))  (2^-24)      [11] max C
+//   [10] sum C log2(C T / (P_i P_j))  (2^-32)      [11] max C
 // and over the marginals (c = count of one entry, e = c log2 c):
 //   [12] sum e over p_x      [13] over p_{x+y}     [14] over p_{x-y}  (2^-24)
 //   [15..19] sum_k c_k w(k) over p_{x-y} for w = 1/(1+k), 1/(1+k^2),
@@ -524,6 +531,19 @@ __device__ inline void invdiff_fx(const KParams& p, unsigned c, int k, long long
   const A ca = (A)c * (A)4294967296.0;
 #pragma unroll
   for (int i = 0; i < 5; ++i) s[15 + i] += a2ll(ca * __ldg(w + i));
+}
+
+// C log2(C T / (P_i P_j)) in units of 2^-32, from the exact integer excess
+// C T - P_i P_j through log1p, so that cells of a nearly independent matrix
+// (ratio close to 1, mutual information ~1e-7) keep their precision
+template <class A>
+__device__ inline long long mi_fx(unsigned Cc, long long T, unsigned pa, unsigned pb) {
+  const long long pp = (long long)pa * (long long)pb;
+  const long long ex = (long long)Cc * T - pp;
+  if constexpr (std::is_same<A, float>::value)
+    return a2ll<float>((float)Cc * log1pf((float)ex / (float)pp) * 6196328018.7194805f);  // 2^32 / ln 2
+  else
+    return a2ll<double>((double)Cc * log1p((double)ex / (double)pp) * 6196328018.7194805);
 }
 
 // GLCM features of one offset (Table S3 rows 140-174): every moment-type
@@ -560,7 +580,7 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
   const A cov = i128A<A>(cov_n) / (4 * T2);
   const A asmv = i128A<A>(iv[8]) / T2;
   const A je = alog2(Ta) - i128A<A>(iv[9]) * ((A)(1.0 / 16777216.0) * invT);
-  const A mi = i128A<A>(iv[10]) * ((A)(1.0 / 16777216.0) * invT);
+  const A mi = i128A<A>(iv[10]) * ((A)(1.0 / 4294967296.0) * invT);
   const A E = (A)(1.0 / 16777216.0), Q = (A)(1.0 / 4294967296.0), lT = alog2(Ta);
   A fv[GF];
   fv[0] = lT - i128A<A>(iv[12]) * E * invT;  // HX
@@ -588,7 +608,7 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
   // HXY1 = HXY2 = HX + HY and HX = HY for a symmetric matrix, so
   // HXY - HXY1 = -MI and HXY2 - HXY = MI (mutual information)
   f[G_INFOMEAS1] = hx > 0 ? -mi / hx : (A)0;
-  const A arg = (A)1 - aexp((A)-2 * mi);
+  const A arg = -aexpm1((A)-2 * mi);  // 1 - exp(-2 MI) without cancellation for small MI
   f[G_INFOMEAS2] = asqrt(arg > 0 ? arg : (A)0);
   f[G_IDMN] = fv[6];
   f[G_ID] = fv[3];
@@ -1340,7 +1360,6 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           // pass 2: marginal entropies and inverse differences (exact
           // fixed-point sums), mutual information over the cells
           const long long Tl = 2 * (long long)s_npair;  // total mass of the symmetric matrix
-          const float Tf = (float)(int)Tl;
           for (int a = tid; a < ng; a += C::NT)
             if (px[a]) iv[12] += ent_fx<A>(px[a]);
           for (int k = tid; k < 2 * ng - 1; k += C::NT)
@@ -1356,8 +1375,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             const unsigned a = key >> 8, b = key & 255u;
             const long long mult = a == b ? 1 : 2;
             const unsigned Cc = a == b ? 2 * cnt : cnt;
-            const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[b]);
-            iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
+            iv[10] += mult * mi_fx<A>(Cc, Tl, px[a], px[b]);
           }
           block_sum_glcm<C>(iv, red, s_i64);
           store_gacc(p, item, oi, s_i64, false);  // features: k_glcm_final

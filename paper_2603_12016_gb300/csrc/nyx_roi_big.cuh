@@ -914,7 +914,6 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       }
       // marginal entropies and inverse differences (exact fixed-point sums),
       // mutual information over the cells
-      const float Tf = (float)Tl;
       for (int a = tid; a < ng; a += BIG_NT)
         if (px[a]) iv[12] += ent_fx<A>(px[a]);
       for (int k = tid; k < 2 * ng - 1; k += BIG_NT)
@@ -931,8 +930,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
         tri_ab(f, a, bb);
         const long long mult = a == bb ? 1 : 2;
         const unsigned Cc = a == bb ? 2 * cnt : cnt;
-        const float ratio = (float)Cc * Tf / ((float)px[a] * (float)px[bb]);
-        iv[10] += mult * __float2ll_rn((float)Cc * log2f(ratio) * 16777216.f);
+        iv[10] += mult * mi_fx<A>(Cc, Tl, px[a], px[bb]);
       }
       block_sum_glcm<C>(iv, red, s_i64);
       store_gacc(p, br.item, oi, s_i64, false);  // features: k_glcm_final
