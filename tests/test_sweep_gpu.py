@@ -74,3 +74,43 @@ def test_fp64_path_3d_and_float():
     _check(w.image, w.mask, 3, 32, (1,), 256, per_offset=False, precision="fp64")
     b = W.config("blobbatch_small")
     _check(b.image, b.mask, 2, 16, (1,), 256, per_offset=False, precision="fp64")
+
+
+def _disc_image(size, rois, seed, dtype=np.uint16):
+    """Discs of given (cy, cx, r, lo, hi): uniform values in [lo, hi)."""
+    rng = np.random.default_rng(seed)
+    img = rng.integers(0, 1000, size=(size, size)).astype(np.int64)
+    mask = np.zeros((size, size), dtype=np.int32)
+    yy, xx = np.mgrid[0:size, 0:size]
+    for k, (cy, cx, r, lo, hi) in enumerate(rois, start=1):
+        inside = (yy - cy) ** 2 + (xx - cx) ** 2 <= r * r
+        mask[inside] = k
+        img[inside] = rng.integers(lo, hi, size=int(inside.sum()))
+    return img.astype(dtype), mask
+
+
+def test_big_value_histogram_global_and_sorted_paths():
+    """uint16 multi-block ROIs: a dense value range above the shared-memory
+    histogram (global histogram), a range wider than the pixel count (sorted
+    values), and a narrow one (shared-memory histogram)."""
+    img, mask = _disc_image(512, [(130, 130, 110, 0, 20000),      # ~38K px, range 20K: global histogram
+                                  (380, 380, 100, 0, 65536),      # ~31K px, range 65K > n: sorted values
+                                  (130, 390, 80, 5000, 5300)], 2601)  # ~20K px, range 300: shared histogram
+    _check(img, mask, 2, 64, (1, 2), 256, max_rois=64)
+
+
+def test_big_2d_long_distances_multispan():
+    img, mask = _disc_image(768, [(380, 380, 300, 0, 4000), (80, 80, 60, 100, 900)], 2602)
+    _check(img, mask, 2, 32, (1, 4, 8), 64, per_offset=True, max_rois=64)
+
+
+def test_big_float_3d():
+    w = W.ct_3d(shape=(32, 96, 96), n_roi=5, seed=2603, vol_range=(9000, 40000))
+    img = (w.image.astype(np.float32) * np.float32(0.37) + np.float32(12.5))
+    _check(img, w.mask, 3, 24, (1,), 100, per_offset=False, max_rois=64)
+
+
+def test_int16_big_2d_negative():
+    img, mask = _disc_image(512, [(250, 250, 200, -30000, 30000)], 2604, dtype=np.int64)
+    img = img.astype(np.int16)
+    _check(img, mask, 2, 48, (1,), 256, max_rois=64)
