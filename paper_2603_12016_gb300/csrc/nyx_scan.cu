@@ -8,7 +8,8 @@
 // distinct (image, label > 0) pair and accumulates its pixel count, bounding
 // box and intensity range, plus the intensity range of every image.
 // Aggregation is hierarchical so that few atomics reach global memory:
-//   lane    : its 4 contiguous pixels collapse into runs
+//   lane    : a register accumulator for the open label of its 4-column
+//             strip, carried down the warp's rows
 //   warp    : lanes holding the same label merge with match/reduce intrinsics
 //   block   : a shared-memory hash table per 32 x 128 tile
 //   global  : one insert + field atomics per (tile, label)
@@ -22,7 +23,10 @@ namespace nyx {
 namespace {
 
 constexpr int TX = 128;   // tile columns (32 lanes x 4 pixels)
-constexpr int TY = 32;    // tile rows
+constexpr int SCAN_RPT = 32; // tallest tile: rows per warp
+// resident blocks per SM the register budget is set for (4-byte pixels need
+// more registers for the rows in flight)
+template <class T> constexpr int scan_minb() { return sizeof(T) == 4 ? 3 : 4; }
 constexpr int SCAP = 256; // shared table capacity (labels per tile)
 constexpr int SCAN_NT = 256;
 
@@ -68,19 +72,7 @@ __device__ int s_find_insert(unsigned long long* s_key, unsigned long long key) 
   return -1;
 }
 
-// Merge one run / group into an accumulator (shared or global memory).
-__device__ inline void acc_merge(SlotAcc* a, unsigned cnt, unsigned vmn, unsigned vmx, int xmn, int xmx, int y, int z) {
-  atomicAdd(&a->count, cnt);
-  atomicMin(&a->vmin, vmn);
-  atomicMax(&a->vmax, vmx);
-  atomicMin(&a->xmin, xmn);
-  atomicMax(&a->xmax, xmx);
-  atomicMin(&a->ymin, y);
-  atomicMax(&a->ymax, y);
-  atomicMin(&a->zmin, z);
-  atomicMax(&a->zmax, z);
-}
-
+// Merge a tile-table accumulator into a global one.
 __device__ inline void acc_merge_acc(SlotAcc* a, const SlotAcc& s) {
   atomicAdd(&a->count, s.count);
   atomicMin(&a->vmin, s.vmin);
@@ -111,23 +103,29 @@ template <class T> __device__ inline void unpack4(uint4 v, unsigned ev[4]) {
   ev[3] = Enc<T>::enc(__uint_as_float(v.w));
 }
 
+// Raw 4-pixel image word: two 32-bit words of 16-bit pixels, four of floats.
 template <class T>
-__device__ inline void load4(const KParams& p, int64_t base, int64_t xs, int lab[4], unsigned ev[4], bool valid[4]) {
+__device__ inline void load_raw(const KParams& p, int64_t base, int64_t xs, int nvalid, int4& m,
+                                typename Vec4<T>::V& v) {
   const T* img = (const T*)p.img;
-  if (p.vec && xs + 3 < p.nx) {
-    int4 m = __ldg((const int4*)(p.mask + base + xs));
-    lab[0] = m.x; lab[1] = m.y; lab[2] = m.z; lab[3] = m.w;
-    const typename Vec4<T>::V v = __ldg((const typename Vec4<T>::V*)(img + base + xs));
-    unpack4<T>(v, ev);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) valid[j] = true;
+  if (p.vec && nvalid == 4) {
+    m = __ldg((const int4*)(p.mask + base + xs));
+    v = __ldg((const typename Vec4<T>::V*)(img + base + xs));
   } else {
+    int l[4];
+    unsigned w[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      valid[j] = xs + j < p.nx;
-      lab[j] = valid[j] ? p.mask[base + xs + j] : 0;
-      ev[j] = valid[j] ? Enc<T>::enc(img[base + xs + j]) : 0;
+      l[j] = j < nvalid ? p.mask[base + xs + j] : 0;
+      w[j] = 0;
+      if (j < nvalid) {
+        if constexpr (sizeof(T) == 2) w[j] = (unsigned)(uint16_t)img[base + xs + j];
+        else w[j] = __float_as_uint((float)img[base + xs + j]);
+      }
     }
+    m = make_int4(l[0], l[1], l[2], l[3]);
+    if constexpr (sizeof(T) == 2) v = make_uint2(w[0] | w[1] << 16, w[2] | w[3] << 16);
+    else v = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -136,8 +134,115 @@ template <> __device__ inline bool finite_enc<float>(unsigned e) { return isfini
 
 }  // namespace
 
+namespace {
+
+// One open label of a lane: the pixels of its 4-column strip seen so far in
+// the current tile and plane.
+struct Slot {
+  int lab;  // 0: empty
+  unsigned cnt, vmn, vmx;
+  unsigned xb;  // which of the lane's 4 columns the label covers
+  int ymn, ymx;
+};
+
+// A slot is opened on a row where it receives pixels.
+__device__ inline void slot_open(Slot& s, int lab, int y) {
+  s.lab = lab;
+  s.cnt = 0;
+  s.vmn = 0xFFFFFFFFu;
+  s.vmx = 0;
+  s.xb = 0;
+  s.ymn = s.ymx = y;
+}
+
+// Adds pixels j of one row (bit j of m) to the slot.
+__device__ inline void slot_add(Slot& s, unsigned m, const unsigned ev[4], int y) {
+  s.cnt += __popc(m);
+  s.xb |= m;
+  if (m) s.ymx = y;  // rows arrive in ascending y within a plane
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool in = m >> j & 1;
+    s.vmn = min(s.vmn, in ? ev[j] : 0xFFFFFFFFu);
+    s.vmx = max(s.vmx, in ? ev[j] : 0u);
+  }
+}
+
+__device__ inline int slot_xmin(const Slot& s, int xs) { return s.xb ? xs + __ffs(s.xb) - 1 : 0x7FFFFFFF; }
+__device__ inline int slot_xmax(const Slot& s, int xs) { return s.xb ? xs + 31 - __clz(s.xb) : (int)0x80000000; }
+
+__device__ inline void acc_merge_run(SlotAcc* s, unsigned cnt, unsigned vmn, unsigned vmx, int xmn, int xmx, int ymn,
+                                     int ymx, int z) {
+  atomicAdd(&s->count, cnt);
+  atomicMin(&s->vmin, vmn);
+  atomicMax(&s->vmax, vmx);
+  atomicMin(&s->xmin, xmn);
+  atomicMax(&s->xmax, xmx);
+  atomicMin(&s->ymin, ymn);
+  atomicMax(&s->ymax, ymx);
+  atomicMin(&s->zmin, z);
+  atomicMax(&s->zmax, z);
+}
+
+// One label's pixels of one plane into the tile table (the global table when
+// the tile holds more than SCAP labels).
+__device__ void run_insert(const KParams& p, unsigned long long* s_key, SlotAcc* s_acc, int lab, long long b,
+                           unsigned cnt, unsigned vmn, unsigned vmx, int xmn, int xmx, int ymn, int ymx, int z,
+                           unsigned& errbits) {
+  const unsigned long long k = ((unsigned long long)b << 32) | (unsigned)lab;
+  const int s = s_find_insert(s_key, k);
+  if (s >= 0) {
+    acc_merge_run(&s_acc[s], cnt, vmn, vmx, xmn, xmx, ymn, ymx, z);
+  } else {
+    const int g = g_find_insert(p, k);
+    if (g >= 0) acc_merge_run(&p.slots[g], cnt, vmn, vmx, xmn, xmx, ymn, ymx, z);
+    else errbits |= E_HASH_FULL;
+  }
+}
+
+__device__ inline void slot_insert(const KParams& p, unsigned long long* s_key, SlotAcc* s_acc, const Slot& s, int xs,
+                                   int z, long long b, unsigned& errbits) {
+  run_insert(p, s_key, s_acc, s.lab, b, s.cnt, s.vmn, s.vmx, slot_xmin(s, xs), slot_xmax(s, xs), s.ymn, s.ymx, z,
+             errbits);
+}
+
+// Whole warp: lanes whose slot holds the same label merge it with
+// match/reduce, and the lowest such lane inserts the result once.
+__device__ inline void slot_flush_warp(const KParams& p, unsigned long long* s_key, SlotAcc* s_acc, Slot& s, int xs,
+                                       int z, long long b, unsigned& errbits) {
+  if (!__any_sync(0xFFFFFFFFu, s.lab > 0)) return;
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, (unsigned)s.lab);
+  const unsigned cnt = __reduce_add_sync(peers, s.cnt);
+  const unsigned vmn = __reduce_min_sync(peers, s.vmn);
+  const unsigned vmx = __reduce_max_sync(peers, s.vmx);
+  const int xmn = __reduce_min_sync(peers, slot_xmin(s, xs));
+  const int xmx = __reduce_max_sync(peers, slot_xmax(s, xs));
+  const int ymn = __reduce_min_sync(peers, s.ymn);
+  const int ymx = __reduce_max_sync(peers, s.ymx);
+  if (s.lab > 0 && (peers & lanemask_lt()) == 0)
+    run_insert(p, s_key, s_acc, s.lab, b, cnt, vmn, vmx, xmn, xmx, ymn, ymx, z, errbits);
+  s.lab = 0;
+}
+
+template <class T> __device__ inline bool nonfinite_raw(const typename Vec4<T>::V&) { return false; }
+template <> __device__ inline bool nonfinite_raw<float>(const uint4& v) {
+  const unsigned E = 0x7F800000u;
+  return ((v.x & E) == E) | ((v.y & E) == E) | ((v.z & E) == E) | ((v.w & E) == E);
+}
+
+}  // namespace
+
+// Each warp takes rpt consecutive rows of a 128-column tile (tile height
+// 8 * rpt) and each lane a 4-pixel column strip of them.  Blob-shaped ROIs
+// keep the labels in a strip the same from row to row, so a lane keeps two
+// open labels (two, so that a strip on the border of two touching ROIs
+// stays cheap) in registers: a row whose 4 pixels are background or one
+// open label costs a few min/max operations, and the shared table is only
+// touched when a third label displaces one.  At the end of the tile or of a
+// plane the warp merges equal labels with match/reduce and inserts each
+// once.  Loads run two rows ahead of the row being processed.
 template <class T>
-__global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
+__global__ void __launch_bounds__(SCAN_NT, scan_minb<T>()) k_scan(KParams p, int rpt) {
   __shared__ unsigned long long s_key[SCAP];
   __shared__ SlotAcc s_acc[SCAP];
   for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
@@ -145,35 +250,52 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
     acc_identity(s_acc[i]);
   }
   __syncthreads();
+  using V = typename Vec4<T>::V;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ty_rows = 8ll * rpt;
   const int64_t r0 = p.scan_row0, r1 = p.scan_row1 > 0 ? p.scan_row1 : p.rows_total;
-  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (r1 - r0 + TY - 1) / TY;
+  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (r1 - r0 + ty_rows - 1) / ty_rows;
   const int64_t ntiles = ntx * nty;
   unsigned im_mn = 0xFFFFFFFFu, im_mx = 0;
   int64_t im_b = -1;
   unsigned errbits = 0;
+  Slot A, B;
+  A.lab = B.lab = 0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t ty = t / ntx, tx = t - ty * ntx;
-    const int64_t x0 = tx * TX;
-    // decompose the warp's first row once; later rows step incrementally
-    // (no 64-bit division per row)
-    int64_t row = r0 + ty * TY + warp;
-    int64_t y = row % p.ny, zb = row / p.ny;
-    int64_t z = zb % p.nz, b = zb / p.nz;
-    for (int rr = warp; rr < TY; rr += SCAN_NT / 32) {
-      if (rr != warp) {
-        row += SCAN_NT / 32;
-        y += SCAN_NT / 32;
-        while (y >= p.ny) {
-          y -= p.ny;
-          if (++z == p.nz) {
-            z = 0;
-            ++b;
-          }
+    const int64_t xs64 = tx * TX + 4 * lane;
+    const int xs = (int)xs64;
+    const int nvalid = (int)max((int64_t)0, min((int64_t)4, p.nx - xs64));
+    const int64_t rw0 = r0 + ty * ty_rows + (int64_t)warp * rpt;
+    const int nr = (int)max((int64_t)0, min((int64_t)rpt, r1 - rw0));
+    int y = 0, z = 0;
+    int64_t b = 0;
+    int4 m0, m1;
+    V v0, v1;
+    if (nr > 0) {
+      y = (int)(rw0 % p.ny);
+      const int64_t zb = rw0 / p.ny;
+      z = (int)(zb % p.nz);
+      b = zb / p.nz;
+      load_raw<T>(p, rw0 * p.nx, xs64, nvalid, m0, v0);
+    }
+    if (nr > 1) load_raw<T>(p, (rw0 + 1) * p.nx, xs64, nvalid, m1, v1);
+    for (int i = 0; i < nr; ++i) {
+      const int4 mc = m0;
+      const V vc = v0;
+      m0 = m1;
+      v0 = v1;
+      if (i + 2 < nr) load_raw<T>(p, (rw0 + i + 2) * p.nx, xs64, nvalid, m1, v1);
+      if (i > 0 && ++y == p.ny) {  // warp-uniform: a new plane (or image) starts
+        slot_flush_warp(p, s_key, s_acc, A, xs, z, b, errbits);
+        slot_flush_warp(p, s_key, s_acc, B, xs, z, b, errbits);
+        y = 0;
+        if (++z == p.nz) {
+          z = 0;
+          ++b;
         }
       }
-      if (row >= r1) break;
-      if (b != im_b) {  // warp-uniform: flush the running image range
+      if (b != im_b) {  // warp-uniform: close the previous image's range
         unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
         if (lane == 0 && im_b >= 0) {
           atomicMin(&p.img_vmin[im_b], mn);
@@ -183,62 +305,94 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(KParams p) {
         im_mn = 0xFFFFFFFFu;
         im_mx = 0;
       }
-      const int64_t xs = x0 + 4 * lane;
-      int lab[4];
+      int L[4] = {mc.x, mc.y, mc.z, mc.w};
       unsigned ev[4];
-      bool valid[4];
-      load4<T>(p, row * p.nx, xs, lab, ev, valid);
-      // lane-local runs of equal label; a run is identified by its first
-      // pixel j, and round j merges the runs that start at pixel j
-      int L[4];
+      unpack4<T>(vc, ev);
+      bool uni;
+      unsigned rmn, rmx;
+      if (nvalid == 4) {
+        rmn = min(min(ev[0], ev[1]), min(ev[2], ev[3]));
+        rmx = max(max(ev[0], ev[1]), max(ev[2], ev[3]));
+        uni = (L[0] == L[1]) & (L[1] == L[2]) & (L[2] == L[3]);
+      } else {  // right edge of the image: pixels past it are background
+        rmn = 0xFFFFFFFFu;
+        rmx = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        L[j] = valid[j] ? lab[j] : 0;
-        if (valid[j]) {
-          im_mn = min(im_mn, ev[j]);
-          im_mx = max(im_mx, ev[j]);
-          if (L[j] < 0) errbits |= E_BAD_LABEL;
-          if (L[j] > 0 && !finite_enc<T>(ev[j])) errbits |= E_NONFINITE;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool act = L[j] > 0 && (j == 0 || L[j - 1] != L[j]);
-        if (!__any_sync(0xFFFFFFFFu, act)) continue;
-        unsigned c = 0, mn = 0xFFFFFFFFu, mx = 0;
-        int xe = j;
-        bool cont = true;
-#pragma unroll
-        for (int q = j; q < 4; ++q) {
-          cont = cont && L[q] == L[j];
-          if (cont) {
-            ++c;
-            mn = min(mn, ev[q]);
-            mx = max(mx, ev[q]);
-            xe = q;
-          }
-        }
-        // the image index b is uniform across the row, so the 32-bit label
-        // identifies the ROI; inactive lanes share the background label 0
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, act ? (unsigned)L[j] : 0u);
-        const unsigned long long k = ((unsigned long long)b << 32) | (unsigned)L[j];
-        const unsigned cnt = __reduce_add_sync(peers, act ? c : 0u);
-        const unsigned vmn = __reduce_min_sync(peers, act ? mn : 0xFFFFFFFFu);
-        const unsigned vmx = __reduce_max_sync(peers, act ? mx : 0u);
-        const int xmn = (int)__reduce_min_sync(peers, act ? (unsigned)(xs + j) : 0x7FFFFFFFu);
-        const int xmx = (int)__reduce_max_sync(peers, act ? (unsigned)(xs + xe) : 0u);
-        if (act && (peers & lanemask_lt()) == 0) {
-          const int s = s_find_insert(s_key, k);
-          if (s >= 0) {
-            acc_merge(&s_acc[s], cnt, vmn, vmx, xmn, xmx, (int)y, (int)z);
+        for (int j = 0; j < 4; ++j) {
+          if (j < nvalid) {
+            rmn = min(rmn, ev[j]);
+            rmx = max(rmx, ev[j]);
           } else {
-            const int g = g_find_insert(p, k);
-            if (g >= 0) acc_merge(&p.slots[g], cnt, vmn, vmx, xmn, xmx, (int)y, (int)z);
-            else errbits |= E_HASH_FULL;
+            L[j] = 0;
           }
         }
+        uni = false;
       }
+      im_mn = min(im_mn, rmn);
+      im_mx = max(im_mx, rmx);
+      if ((L[0] | L[1] | L[2] | L[3]) < 0) errbits |= E_BAD_LABEL;
+      if (nonfinite_raw<T>(vc)) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (L[j] > 0 && !finite_enc<T>(ev[j])) errbits |= E_NONFINITE;
+      }
+      if (uni && L[0] <= 0) continue;  // background row segment
+      if (uni && L[0] == A.lab) {
+        A.cnt += 4;
+        A.xb = 0xFu;
+        A.vmn = min(A.vmn, rmn);
+        A.vmx = max(A.vmx, rmx);
+        A.ymx = y;
+        continue;
+      }
+      if (uni && L[0] == B.lab) {
+        B.cnt += 4;
+        B.xb = 0xFu;
+        B.vmn = min(B.vmn, rmn);
+        B.vmx = max(B.vmx, rmx);
+        B.ymx = y;
+        continue;
+      }
+      unsigned mA = 0, mB = 0, mo = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (L[j] > 0) {
+          if (L[j] == A.lab) mA |= 1u << j;
+          else if (L[j] == B.lab) mB |= 1u << j;
+          else mo |= 1u << j;
+        }
+      while (mo) {  // a label in neither slot: give it a slot
+        const int j = __ffs(mo) - 1;
+        const int nl = j == 0 ? L[0] : j == 1 ? L[1] : j == 2 ? L[2] : L[3];
+        // an empty slot, else one without pixels on this row, else B; the
+        // displaced label keeps the pixels it has on this row
+        const bool useA = A.lab == 0 || (B.lab != 0 && mA == 0);
+        if (useA) {
+          if (A.lab > 0) {
+            slot_add(A, mA, ev, y);
+            slot_insert(p, s_key, s_acc, A, xs, z, b, errbits);
+          }
+          slot_open(A, nl, y);
+        } else {
+          if (B.lab > 0) {
+            slot_add(B, mB, ev, y);
+            slot_insert(p, s_key, s_acc, B, xs, z, b, errbits);
+          }
+          slot_open(B, nl, y);
+        }
+        unsigned mn = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if ((mo >> q & 1) && L[q] == nl) mn |= 1u << q;
+        mo &= ~mn;
+        if (useA) mA = mn;
+        else mB = mn;
+      }
+      slot_add(A, mA, ev, y);
+      slot_add(B, mB, ev, y);
     }
+    slot_flush_warp(p, s_key, s_acc, A, xs, z, b, errbits);
+    slot_flush_warp(p, s_key, s_acc, B, xs, z, b, errbits);
     __syncthreads();
     // flush the tile table to the global label table
     for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
@@ -616,7 +770,18 @@ static cudaError_t launch_scan_t(const KParams& p, int nsm, cudaStream_t st) {
   int nb = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<T>, SCAN_NT, 0);
   if (e != cudaSuccess) return e;
-  k_scan<T><<<(nb > 0 ? nb : 1) * nsm, SCAN_NT, 0, st>>>(p);
+  const int64_t grid = (int64_t)(nb > 0 ? nb : 1) * nsm;
+  // rows per warp and tile: the tallest tile that still gives every block
+  // two tiles (taller tiles spread the per-tile table flush over more rows)
+  const int64_t rows = (p.scan_row1 > 0 ? p.scan_row1 : p.rows_total) - p.scan_row0;
+  const int64_t ntx = (p.nx + TX - 1) / TX;
+  int rpt = SCAN_RPT / 4;
+  for (int c = SCAN_RPT; c > SCAN_RPT / 4; c /= 2)
+    if (ntx * ((rows + 8ll * c - 1) / (8ll * c)) >= 2 * grid) {
+      rpt = c;
+      break;
+    }
+  k_scan<T><<<(int)grid, SCAN_NT, 0, st>>>(p, rpt);
   return cudaGetLastError();
 }
 
