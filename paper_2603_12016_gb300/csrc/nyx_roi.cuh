@@ -706,11 +706,12 @@ __device__ inline void store_sacc(const KParams& p, int64_t item, int nm, const 
 
 // Percentiles by linear interpolation at h = (n-1) q on the sorted values,
 // computed in FP64 with separately rounded operations like the definition,
-// one lane per percentile.  Lane 0 also finds the index range of the values
-// inside [P10, P90].  Writes median, P10, P90 to sc[] (FP64).
+// one lane per percentile.  Lane 0 also turns [P10, P90] into an inclusive
+// range of encoded values (bnd[0], bnd[1]): a value lies in [P10, P90] exactly
+// when its code lies in that range.  Writes median, P10, P90 to sc[] (FP64).
 template <class T>
 __device__ __noinline__ void finalize_percentiles(const KParams& p, double* row, const unsigned* v, int n, double* sc,
-                                                  int* idx) {
+                                                  unsigned* bnd) {
   const int lane = threadIdx.x & 31;
   const double qs[7] = {0.01, 0.10, 0.25, 0.50, 0.75, 0.90, 0.99};
   const int qcol[7] = {S_P01, S_P10, S_P25, S_MEDIAN, S_P75, S_P90, S_P99};
@@ -738,40 +739,22 @@ __device__ __noinline__ void finalize_percentiles(const KParams& p, double* row,
   sc[0] = med;
   sc[1] = p10;
   sc[2] = p90;
-  int lo = 0, hi = n;
-  if (Enc<T>::INTEGER) {
+  if constexpr (Enc<T>::INTEGER) {
     // integer values: v >= P10 <=> v >= ceil(P10); v <= P90 <=> v <= floor(P90)
-    const long long t10 = (long long)ceil(p10), t90 = (long long)floor(p90);
     const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
-    while (lo < hi) {
-      const int m = (lo + hi) >> 1;
-      if ((long long)v[m] - bias < t10) lo = m + 1;
-      else hi = m;
-    }
-    idx[0] = lo;
-    lo = 0;
-    hi = n;
-    while (lo < hi) {
-      const int m = (lo + hi) >> 1;
-      if ((long long)v[m] - bias <= t90) lo = m + 1;
-      else hi = m;
-    }
-    idx[1] = lo;
+    bnd[0] = (unsigned)((long long)ceil(p10) + bias);
+    bnd[1] = (unsigned)((long long)floor(p90) + bias);
   } else {
-    while (lo < hi) {
-      const int m = (lo + hi) >> 1;
-      if (Enc<T>::dec(v[m]) < p10) lo = m + 1;
-      else hi = m;
-    }
-    idx[0] = lo;  // first value >= P10
-    lo = 0;
-    hi = n;
-    while (lo < hi) {
-      const int m = (lo + hi) >> 1;
-      if (Enc<T>::dec(v[m]) <= p90) lo = m + 1;
-      else hi = m;
-    }
-    idx[1] = lo;  // one past the last value <= P90
+    // float values: v >= P10 <=> v >= the smallest float not below P10, and
+    // v <= P90 <=> v <= the largest float not above P90; a zero bound admits
+    // both signed zeros, which compare equal to it
+    float lo = (float)p10, hi = (float)p90;
+    if ((double)lo < p10) lo = nextafterf(lo, INFINITY);
+    if ((double)hi > p90) hi = nextafterf(hi, -INFINITY);
+    if (lo == 0.f) lo = -0.f;
+    if (hi == 0.f) hi = 0.f;
+    bnd[0] = Enc<T>::enc(lo);
+    bnd[1] = Enc<T>::enc(hi);
   }
 }
 
@@ -797,14 +780,14 @@ __device__ inline unsigned bin_float(float x, float mn, float mx, int nb) {
 // shared or global memory): percentiles, mode (longest run, ties to the
 // smallest value), robust mean and mean absolute deviation over [P10, P90],
 // and the mean absolute deviation from the median.  Called by every thread of
-// the block; uses s_sc[4..6] and s_sc[10..11].
+// the block; uses s_sc[4..7] and s_sc[10..11].
 template <class T, class C, class A>
 __device__ inline void order_tail(const KParams& p, double* row, const unsigned* v, int n, double* red,
-                                  double* s_sd, int* s_idx, A* s_sc) {
+                                  double* s_sd, unsigned* s_bnd, A* s_sc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const A nan = anan<A>();
   const int ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
-  if (warp == 0) finalize_percentiles<T>(p, row, v, n, s_sd, s_idx);
+  if (warp == 0) finalize_percentiles<T>(p, row, v, n, s_sd, s_bnd);
   __syncthreads();
   // mode: longest run of equal values, ties -> smallest value.  Each
   // thread owns a contiguous segment; runs entering a segment get their
@@ -849,34 +832,41 @@ __device__ inline void order_tail(const KParams& p, double* row, const unsigned*
   }
   best = block_max_u64<C>(best, red);
   // robust mean over [P10, P90], mean absolute deviation from the median
-  const int i10 = s_idx[0], i90 = s_idx[1];
+  const unsigned b10 = s_bnd[0], b90 = s_bnd[1];
   if (tid == 0) s_sc[10] = (A)s_sd[0];  // median in the accumulation type
   __syncthreads();
   const A medA = s_sc[10];
-  A rv[2] = {0, 0};
+  A rv[3] = {0, 0, 0};  // sum over [P10, P90], sum |x - median|, count in [P10, P90] (exact)
   for (int i = tid; i < n; i += C::NT) {
-    const A x = decA<T, A>(v[i]);
-    if (i >= i10 && i < i90) rv[0] += x;
+    const unsigned e = v[i];
+    const A x = decA<T, A>(e);
+    if (e >= b10 && e <= b90) {
+      rv[0] += x;
+      rv[2] += (A)1;
+    }
     rv[1] += x > medA ? x - medA : medA - x;
   }
-  block_sum<C, A, 2>(rv, red, s_sc + 4);
-  const int cntV = i90 - i10;
+  block_sum<C, A, 3>(rv, red, s_sc + 4);
+  const int cntV = (int)s_sc[6];
   if (tid == 0) s_sc[11] = cntV > 0 ? s_sc[4] / (A)cntV : nan;
   __syncthreads();
   const A rmA = s_sc[11];
   A ra[1] = {0};
-  for (int i = i10 + tid; i < i90; i += C::NT) {
-    const A x = decA<T, A>(v[i]);
-    ra[0] += x > rmA ? x - rmA : rmA - x;
+  for (int i = tid; i < n; i += C::NT) {
+    const unsigned e = v[i];
+    if (e >= b10 && e <= b90) {
+      const A x = decA<T, A>(e);
+      ra[0] += x > rmA ? x - rmA : rmA - x;
+    }
   }
-  block_sum<C, A, 1>(ra, red, s_sc + 6);
+  block_sum<C, A, 1>(ra, red, s_sc + 7);
   if (tid == 0) {
     const unsigned mode_e = ~(unsigned)(best & 0xFFFFFFFFu);
     if (Enc<T>::INTEGER) put(p, row, Q_STATS + S_MODE, i2d((long long)mode_e - ibias));
     else put(p, row, Q_STATS + S_MODE, f2d(Enc<T>::decf(mode_e)));
     putA(p, row, Q_STATS + S_MODE_PROB, (A)(int)(best >> 32) / (A)n);
     putA(p, row, Q_STATS + S_RMEAN, rmA);
-    putA(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[6] / (A)cntV : nan);
+    putA(p, row, Q_STATS + S_RMAD, cntV > 0 ? s_sc[7] / (A)cntV : nan);
     putA(p, row, Q_STATS + S_MEDAD, s_sc[5] / (A)n);
   }
 }
@@ -904,7 +894,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
   __shared__ A s_sc[16];
   __shared__ double s_sd[4];
   __shared__ long long s_i64[GN + 4];  // pass-1 sums, then the GLCM sums of an offset
-  __shared__ int s_idx[4];
+  __shared__ unsigned s_bnd[4];
   __shared__ A s_pa[10];  // per-ROI scalars: mean (hi, lo), centroids, sums
   __shared__ unsigned s_ncell, s_npair;
 
@@ -1282,6 +1272,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
           const int olin = (dz * Hp + dy) * Wp + dx;
           __syncthreads();
           // accumulate pairs (q, q + o) inside the ROI
+          unsigned npair = 0;  // this lane's pairs
           for (int i0 = warp * 32; i0 < n; i0 += C::NT) {
             const int i = i0 + lane;
             unsigned key = 0xFFFFFFFFu;
@@ -1293,8 +1284,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             // one insert per run of equal keys in consecutive lanes (noisy
             // images give runs of 1; smooth ones long runs that would
             // otherwise serialise on one address)
-            const unsigned nvalid = __popc(__ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu));
-            if (lane == 0 && nvalid) atomicAdd(&s_npair, nvalid);
+            npair += key != 0xFFFFFFFFu;
             const unsigned add = run_leader(key, 0xFFFFFFFFu);
             if (add) {
               unsigned h = (key * 2654435761u >> 7) & (unsigned)(cap - 1);
@@ -1318,6 +1308,8 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
               }
             }
           }
+          npair = __reduce_add_sync(0xFFFFFFFFu, npair);
+          if (lane == 0 && npair) atomicAdd(&s_npair, npair);
           __syncthreads();
           const int ncell = (int)s_ncell;
           // pass 1 over the cells: marginals and exact integer power sums
@@ -1463,7 +1455,7 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
         dst = t;
       }
       const unsigned* v = src;  // sorted, ascending
-      order_tail<T, C, A>(p, row, v, n, red, s_sd, s_idx, s_sc);
+      order_tail<T, C, A>(p, row, v, n, red, s_sd, s_bnd, s_sc);
     }
     __syncthreads();
   }

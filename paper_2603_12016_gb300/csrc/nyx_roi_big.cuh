@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order(KParams p, int ndim) {
   __shared__ double red[C::NW * RED_MAX];
   __shared__ unsigned s_wc[C::NW], s_wb[C::NW + 1];
   __shared__ double s_sd[4];
-  __shared__ int s_idx[4];
+  __shared__ unsigned s_bnd[4];
   __shared__ A s_sc[16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_big = big_count(*p.big_ctr);
@@ -1072,7 +1072,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_order(KParams p, int ndim) {
       dst = t;
     }
     double* row = p.table + (int64_t)br.item * p.n_col;
-    order_tail<T, C, A>(p, row, src, n, red, s_sd, s_idx, s_sc);
+    order_tail<T, C, A>(p, row, src, n, red, s_sd, s_bnd, s_sc);
     __syncthreads();
   }
 }
