@@ -34,16 +34,17 @@
 
 namespace nyx {
 
-template <int NT_, int PIX_, int CELLS_>
+template <int NT_, int PIX_, int CELLS_, int MINB_ = 1>
 struct RoiClass {
   static constexpr int NT = NT_;
+  static constexpr int MINB = MINB_;    // resident blocks per SM the register budget is set for
   static constexpr int NW = NT_ / 32;
   static constexpr int PIX = PIX_;      // max pixels of an ROI
   static constexpr int CELLS = CELLS_;  // max padded raster cells
   static constexpr int TAB = 2 * PIX_;  // GLCM hash capacity (power of two); also 2 sort buffers
 };
 using ClassW = RoiClass<32, 256, 1024>;    // one warp per ROI
-using ClassS = RoiClass<128, 1024, 4096>;
+using ClassS = RoiClass<128, 1024, 4096, 6>;  // 6 blocks of ~37 KB shared memory fit an SM
 using ClassM = RoiClass<512, 8192, 16384>;
 
 constexpr int RED_MAX = 64;  // max values per block reduction
@@ -636,7 +637,7 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
 // and swaps the other half with lane ^ o, so 32 slots cost 16 + 8 + 4 + 2 + 1
 // exchanges instead of 5 per value; lane l ends with the warp total of slot
 // l.  The maximum takes a plain butterfly.
-template <class C>
+template <class C, bool TRAILING_SYNC = true>
 __device__ inline void block_sum_glcm(long long (&iv)[GN], double* scratch_d, long long* out) {
   long long* si = (long long*)scratch_d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -669,7 +670,7 @@ __device__ inline void block_sum_glcm(long long (&iv)[GN], double* scratch_d, lo
     for (int w = 1; w < C::NW; ++w) r = t == 11 ? (si[w * GN + t] > r ? si[w * GN + t] : r) : r + si[w * GN + t];
     out[t] = r;
   }
-  __syncthreads();
+  if (TRAILING_SYNC) __syncthreads();
 }
 
 // Per (ROI, offset) GLCM accumulator handed from the accumulation kernels to
@@ -875,7 +876,7 @@ __device__ inline void order_tail(const KParams& p, double* row, const unsigned*
 // the kernel
 
 template <class T, int NDIM, class C, class A>
-__global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
+__global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = SmemLayout::make<C>(p.ng, p.hist_bins);
   uint16_t* raster = (uint16_t*)(smem + L.raster);
@@ -1369,9 +1370,12 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             const unsigned Cc = a == b ? 2 * cnt : cnt;
             iv[10] += mult * mi_fx<A>(Cc, Tl, px[a], px[b]);
           }
-          block_sum_glcm<C>(iv, red, s_i64);
+          // thread t < GN reads back only the sum it wrote itself, and the
+          // next offset starts with a barrier: no trailing one needed
+          block_sum_glcm<C, false>(iv, red, s_i64);
           store_gacc(p, item, oi, s_i64, false);  // features: k_glcm_final
-          // clean up only what this offset touched
+          // clean up only what this offset touched (each table slot is read
+          // and cleared by the thread that owns its cell)
           for (int s = tid; s < ncell; s += C::NT) {
             const unsigned h = cells[s];
             const unsigned key = tab[h] >> 16;
@@ -1380,9 +1384,8 @@ __global__ void __launch_bounds__(C::NT) k_roi(KParams p, int cls) {
             px[b] = 0;
             psum[a + b] = 0;
             pdiff[b - a] = 0;
+            tab[h] = 0;
           }
-          __syncthreads();
-          for (int s = tid; s < ncell; s += C::NT) tab[cells[s]] = 0;
           if (tid == 0) {
             s_ncell = 0;
             s_npair = 0;
