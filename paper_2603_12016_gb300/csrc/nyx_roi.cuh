@@ -877,6 +877,7 @@ __device__ inline void order_tail(const KParams& p, double* row, const unsigned*
 
 template <class T, int NDIM, class C, class A>
 __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
+  static_assert(C::CELLS <= 65536, "GLCM pixel words hold a 16-bit raster index");
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = SmemLayout::make<C>(p.ng, p.hist_bins);
   uint16_t* raster = (uint16_t*)(smem + L.raster);
@@ -1258,13 +1259,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         s_npair = 0;
       }
       // the pixel list's coordinates are not needed after the moments: keep
-      // each pixel's padded raster index there instead of decoding it per offset
+      // each pixel's padded raster index (low 16 bits; cells <= 16,384) and
+      // its own bin (high 16 bits) there instead of decoding them per offset
       for (int i = tid; i < n; i += C::NT) {
         const unsigned c = pc[i];
         const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
         const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
         const int z = NDIM == 3 ? (int)(c >> 22) : 0;
-        pc[i] = (unsigned)(((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad));
+        const unsigned ci = (unsigned)(((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad));
+        pc[i] = ci | ((unsigned)raster[ci] << 16);
       }
       for (int di = 0; di < p.n_dist; ++di) {
         for (int dir = 0; dir < p.n_dirs; ++dir) {
@@ -1278,8 +1281,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
             const int i = i0 + lane;
             unsigned key = 0xFFFFFFFFu;
             if (i < n) {
-              const unsigned ci = pc[i];
-              const unsigned a = raster[ci], b = raster[ci + olin];
+              const unsigned w = pc[i];
+              const unsigned a = w >> 16, b = raster[(w & 0xFFFFu) + olin];
               if (b != 0xFFFFu) key = a < b ? (a << 8) | b : (b << 8) | a;
             }
             // one insert per run of equal keys in consecutive lanes (noisy

@@ -44,6 +44,9 @@
 namespace nyx {
 
 constexpr int BIG_NT = 512;
+// resident blocks per SM of the pass kernels: two (64 registers a thread) on
+// the float path, one on the FP64 path, whose wider state would spill
+template <class A> constexpr int big_pass_minb() { return std::is_same<A, float>::value ? 2 : 1; }
 constexpr int VH_SMEM = 8192;  // value-histogram words kept in shared memory per chunk
 using ClassBig = RoiClass<BIG_NT, 1, 1>;  // thread geometry for the block reductions
 
@@ -333,7 +336,7 @@ __device__ void hist_order_stats(const KParams& p, double* row, const unsigned* 
 }
 
 template <class T, int NDIM, class A>
-__global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
+__global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p) {
   using C = ClassBig;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned* hist = (unsigned*)smem;                // [hist_bins]
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_p1(KParams p) {
 }
 
 template <class T, int NDIM, class A>
-__global__ void __launch_bounds__(BIG_NT) k_big_p2(KParams p) {
+__global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p2(KParams p) {
   using C = ClassBig;
   constexpr int NM = NDIM == 3 ? 20 : 10;
   constexpr int NV = 8 + 2 * NM;
