@@ -100,6 +100,11 @@ struct nyx_plan {
   static constexpr int NGRAPH = 4;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;  // capture only; graphs launch on the caller's stream
+  // branches of the extraction that run beside the caller's stream (the
+  // medium class, the multi-block path, the GLCM feature kernel), with the
+  // events that fork and join them
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev[6] = {};
   cudaGraphExec_t graph_exec[NGRAPH] = {};
   KParams graph_key[NGRAPH];
   int64_t graph_used[NGRAPH] = {};
@@ -485,6 +490,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->side[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->fork_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(pl->ws);
     delete pl;
@@ -500,6 +507,10 @@ void nyx_plan_destroy(nyx_plan* pl) {
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   drop_graph(pl);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  for (int i = 0; i < 2; ++i)
+    if (pl->side[i]) cudaStreamDestroy(pl->side[i]);
+  for (int i = 0; i < 6; ++i)
+    if (pl->fork_ev[i]) cudaEventDestroy(pl->fork_ev[i]);
   for (int i = 0; i < 2; ++i) {
     if (pl->stage[i]) cudaFreeHost(pl->stage[i]);
     if (pl->stage_ev[i]) cudaEventDestroy(pl->stage_ev[i]);
@@ -602,46 +613,78 @@ static nyx_status enqueue_extract(nyx_plan* pl, const KParams& k, cudaEvent_t* e
   return enqueue_back(pl, k, ev, st);
 }
 
+static cudaError_t launch_class(const KParams& k, int cls, int fp64, int nsm, cudaStream_t st) {
+  switch (k.dtype) {
+    case NYX_U16: return launch_roi_u16(k, cls, fp64, nsm, st);
+    case NYX_I16: return launch_roi_i16(k, cls, fp64, nsm, st);
+    default: return launch_roi_f32(k, cls, fp64, nsm, st);
+  }
+}
+
+static cudaError_t launch_big(const KParams& k, int fp64, int nsm, cudaStream_t st) {
+  switch (k.dtype) {
+    case NYX_U16: return launch_big_u16(k, fp64, nsm, st);
+    case NYX_I16: return launch_big_i16(k, fp64, nsm, st);
+    default: return launch_big_f32(k, fp64, nsm, st);
+  }
+}
+
 // Everything after the label scan: key sort + setup, the four size classes,
-// GLCM features, table reset.
+// GLCM features, table reset.  The size classes work on disjoint ROIs, and
+// the GLCM feature and statistics kernels on disjoint sums, so outside
+// profiling they run as parallel branches: the medium class and the
+// multi-block path on the plan's side streams, the warp and small classes on
+// `st`, joined before the kernels that read every ROI's sums; then the GLCM
+// feature kernel beside the statistics kernel.  Blocks of one class fill the
+// SMs that another class's tail leaves idle.  A class whose pixel limit is 0
+// receives no ROI and is not launched.
 static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st) {
   nyx_ctx* c = pl->ctx;
   nyx_status s;
   if ((s = run_sort_setup(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[2], st));
   const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
+  const bool fork = ev == nullptr && pl->side[0] != nullptr;
+  cudaStream_t s_med = st, s_big = st;
+  if (fork) {
+    NYX_CUDA(c, cudaEventRecord(pl->fork_ev[0], st));
+    for (int i = 0; i < 2; ++i) NYX_CUDA(c, cudaStreamWaitEvent(pl->side[i], pl->fork_ev[0], 0));
+    s_med = pl->side[0];
+    s_big = pl->side[1];
+  }
   for (int cls = 0; cls < 3; ++cls) {
-    cudaError_t e;
-    switch (k.dtype) {
-      case NYX_U16: e = launch_roi_u16(k, cls, fp64, c->nsm, st); break;
-      case NYX_I16: e = launch_roi_i16(k, cls, fp64, c->nsm, st); break;
-      default: e = launch_roi_f32(k, cls, fp64, c->nsm, st); break;
-    }
+    const cudaError_t e = k.lim_pix[cls] > 0 ? launch_class(k, cls, fp64, c->nsm, cls == 2 ? s_med : st) : cudaSuccess;
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
   }
   {
-    cudaError_t e;
-    switch (k.dtype) {
-      case NYX_U16: e = launch_big_u16(k, fp64, c->nsm, st); break;
-      case NYX_I16: e = launch_big_i16(k, fp64, c->nsm, st); break;
-      default: e = launch_big_f32(k, fp64, c->nsm, st); break;
-    }
+    const cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[6], st));
   }
-  {  // statistics, moments and Hu invariants from the per-ROI sums
-    cudaError_t e;
-    switch (k.dtype) {
-      case NYX_U16: e = launch_roi_u16(k, 3, fp64, c->nsm, st); break;
-      case NYX_I16: e = launch_roi_i16(k, 3, fp64, c->nsm, st); break;
-      default: e = launch_roi_f32(k, 3, fp64, c->nsm, st); break;
-    }
-    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "statistics kernel launch failed: %s", cudaGetErrorString(e));
+  if (fork) {  // join, then fork the GLCM feature kernel
+    NYX_CUDA(c, cudaEventRecord(pl->fork_ev[1], s_med));
+    NYX_CUDA(c, cudaEventRecord(pl->fork_ev[2], s_big));
+    NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[1], 0));
+    NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[2], 0));
+  }
+  cudaStream_t s_gl = st;
+  if (fork && (k.need & NEED_GLCM)) {
+    NYX_CUDA(c, cudaEventRecord(pl->fork_ev[3], st));
+    NYX_CUDA(c, cudaStreamWaitEvent(pl->side[0], pl->fork_ev[3], 0));
+    s_gl = pl->side[0];
   }
   if (k.need & NEED_GLCM) {
-    cudaError_t e = launch_glcm_final(k, fp64, c->nsm, st);
+    cudaError_t e = launch_glcm_final(k, fp64, c->nsm, s_gl);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
+  }
+  {  // statistics, moments and Hu invariants from the per-ROI sums
+    const cudaError_t e = launch_class(k, 3, fp64, c->nsm, st);
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "statistics kernel launch failed: %s", cudaGetErrorString(e));
+  }
+  if (s_gl != st) {
+    NYX_CUDA(c, cudaEventRecord(pl->fork_ev[4], s_gl));
+    NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[4], 0));
   }
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
   // a forward pass saved for backward keeps the label table for nyx_backward
