@@ -420,10 +420,11 @@ __global__ void __launch_bounds__(SCAN_NT, scan_minb<T>()) k_scan(KParams p, int
 }
 
 // Sort the distinct keys ascending (one block): dense ROI id = rank of its
-// (image, label) key.  LSD radix sort of 16-bit indices by 8-bit digits over
-// the key bits that differ at all (2 passes for labels below 65,536 in one
-// image), with stable ranks from 8 ballots per digit; the keys are gathered
-// once into sort_tmp.
+// (image, label) key.  Keys that differ only in their low 16 bits (one
+// image, labels within a 65,536 range) are ranked through a presence bitmap;
+// other key sets by an LSD radix sort of 16-bit indices by 8-bit digits over
+// the digits that differ at all, with stable ranks from 8 ballots per digit.
+// The keys are gathered once into sort_tmp.
 __global__ void __launch_bounds__(1024) k_sort_keys(KParams p) {
   extern __shared__ unsigned s_sm[];
   constexpr int NW = 32;
@@ -459,9 +460,54 @@ __global__ void __launch_bounds__(1024) k_sort_keys(KParams p) {
   diff = 0;
   for (int w = 0; w < NW; ++w) diff |= s_or[w];
   const int nbits = diff ? 64 - __clzll((long long)diff) : 0;
+  if (nbits <= 16) {
+    // Keys differ only in their low nbits bits (one image, labels within a
+    // 65,536 range): the rank of a key is the number of keys below it, read
+    // from a presence bitmap over that range and a prefix of its popcounts.
+    const unsigned long long kb = k0 & ~((1ull << nbits) - 1ull);
+    const int nwd = nbits > 5 ? 1 << (nbits - 5) : 1;  // bitmap words (<= 2048)
+    unsigned* bm = cnt;           // [nwd] presence bits
+    unsigned* pre = cnt + 2048;   // [nwd] exclusive prefix of popcounts
+    for (int i = tid; i < nwd; i += blockDim.x) bm[i] = 0;
+    __syncthreads();
+    for (unsigned i = tid; i < n; i += blockDim.x) {
+      const unsigned o = (unsigned)(kv[i] - kb);
+      atomicOr(&bm[o >> 5], 1u << (o & 31));
+    }
+    __syncthreads();
+    // block-wide exclusive scan, two words per thread
+    const int w0 = 2 * tid;
+    const unsigned c0 = w0 < nwd ? __popc(bm[w0]) : 0u, c1 = w0 + 1 < nwd ? __popc(bm[w0 + 1]) : 0u;
+    unsigned x = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) dtot[warp] = x;
+    __syncthreads();
+    if (warp == 0) warp_exclusive_scan(dtot, NW);
+    __syncthreads();
+    const unsigned ex = dtot[warp] + x - (c0 + c1);
+    if (w0 < nwd) pre[w0] = ex;
+    if (w0 + 1 < nwd) pre[w0 + 1] = ex + c0;
+    __syncthreads();
+    for (unsigned i = tid; i < n; i += blockDim.x) {
+      const unsigned long long k = kv[i];
+      const unsigned o = (unsigned)(k - kb);
+      p.sorted_keys[pre[o >> 5] + __popc(bm[o >> 5] & ((1u << (o & 31)) - 1u))] = k;
+    }
+    if (tid == 0) {
+      *p.n_roi = n;
+      if (p.n_roi_out) *p.n_roi_out = (int64_t)n;
+      if ((int64_t)n > p.cap_roi) atomicOr(p.err, E_ROI_CAP);
+    }
+    return;
+  }
   const int seg = (((int)(n + NW - 1) / NW) + 31) & ~31;
   const int lo = min((int)n, warp * seg), hi = min((int)n, lo + seg);
   for (int shift = 0; shift < nbits; shift += 8) {
+    if (((diff >> shift) & 255ull) == 0) continue;  // a digit every key shares: no reordering
     for (int i = tid; i < NW * 256; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {  // 0: digit counts per warp, 1: stable scatter
