@@ -252,3 +252,42 @@ def test_class_limits_and_autotune_keep_parity(limits):
     g = gpu_table(ex, img, mask)
     o = oracle.extract(w.image, w.mask, 2, ng=256, dists=(1, 2), hist_bins=256, threads=8)
     _assert_parity(g, o, 2)
+
+
+@pytest.mark.parametrize("case", ["bitmap_high_base", "bit16_boundary", "wide_31bit", "batch2"])
+def test_key_sort_paths(case):
+    """ROI rows come out in ascending (image, label) order on both key-sort
+    paths: the presence bitmap (keys differing in their low 16 bits only,
+    here based at 0x30000) and the radix sort (wider label ranges, batches).
+    Areas and bounding boxes are checked against numpy, the full feature
+    set against the oracle."""
+    rng = np.random.default_rng({"bitmap_high_base": 41, "bit16_boundary": 42, "wide_31bit": 43, "batch2": 44}[case])
+    nb = 2 if case == "batch2" else 1
+    img = rng.integers(0, 3000, size=(nb, 96, 96)).astype(np.uint16)
+    mask = np.zeros(img.shape, dtype=np.int32)
+    n = 180
+    if case == "bitmap_high_base":
+        labels = rng.choice(np.arange(0x30000, 0x40000), size=n, replace=False)
+        labels[:2] = [0x30000, 0x3FFFF]
+    elif case == "bit16_boundary":
+        labels = rng.choice(np.arange(60000, 70000), size=n, replace=False)
+        labels[:2] = [65535, 65536]
+    else:
+        labels = rng.choice(np.arange(1, 2**31 - 1, 9973), size=n, replace=False)
+    slots = rng.permutation(32 * 32)[:n]
+    for lab, sl in zip(labels, slots):
+        b = int(rng.integers(0, nb))
+        y, x = 3 * (sl // 32), 3 * (sl % 32)
+        mask[b, y:y + 2, x:x + 1 + int(rng.integers(1, 3))] = lab
+    if nb == 1:
+        img, mask = img[0], mask[0]
+    w = W.Workload(case, img, mask, 2, params=dict(glcm_levels=16, dists=(1,), hist_bins=16), meta={"n_roi": n})
+    ex, g, o = _run(w, max_rois=1024)
+    bi = np.nonzero(mask)[0] if nb > 1 else np.zeros(np.count_nonzero(mask), dtype=np.int64)
+    keys = np.unique((bi.astype(np.int64) << 32) | mask[mask > 0].astype(np.int64))
+    got = (g["IMAGE"].astype(np.int64) << 32) | g["LABEL"].astype(np.int64)
+    assert np.array_equal(got, keys)
+    for k, area in zip(keys, g["AREA"]):
+        m = (mask[k >> 32] if nb > 1 else mask) == (k & 0xFFFFFFFF)
+        assert area == m.sum()
+    _assert_parity(g, o, 2)
