@@ -101,8 +101,8 @@ struct nyx_plan {
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;  // capture only; graphs launch on the caller's stream
   // branches of the extraction that run beside the caller's stream (the
-  // medium class, the multi-block path, the GLCM feature kernel), with the
-  // events that fork and join them
+  // medium class, the multi-block path, the GLCM feature kernel, the label
+  // table reset), with the events that fork and join them
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t fork_ev[6] = {};
   cudaGraphExec_t graph_exec[NGRAPH] = {};
@@ -668,16 +668,26 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[1], 0));
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[2], 0));
   }
-  cudaStream_t s_gl = st;
-  if (fork && (k.need & NEED_GLCM)) {
+  // the GLCM feature kernel, the statistics kernel and the label-table reset
+  // touch disjoint data: three branches
+  const bool reset = !(k.need & NEED_SAVE);  // a pass saved for backward keeps the label table
+  cudaStream_t s_gl = st, s_rs = st;
+  if (fork) {
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[3], st));
-    NYX_CUDA(c, cudaStreamWaitEvent(pl->side[0], pl->fork_ev[3], 0));
-    s_gl = pl->side[0];
+    if (k.need & NEED_GLCM) {
+      NYX_CUDA(c, cudaStreamWaitEvent(pl->side[0], pl->fork_ev[3], 0));
+      s_gl = pl->side[0];
+    }
+    if (reset) {
+      NYX_CUDA(c, cudaStreamWaitEvent(pl->side[1], pl->fork_ev[3], 0));
+      s_rs = pl->side[1];
+    }
   }
   if (k.need & NEED_GLCM) {
     cudaError_t e = launch_glcm_final(k, fp64, c->nsm, s_gl);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
   }
+  if (reset && s_rs != st && (s = run_reset(pl, const_cast<KParams&>(k), s_rs)) != NYX_OK) return s;
   {  // statistics, moments and Hu invariants from the per-ROI sums
     const cudaError_t e = launch_class(k, 3, fp64, c->nsm, st);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "statistics kernel launch failed: %s", cudaGetErrorString(e));
@@ -686,9 +696,12 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[4], s_gl));
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[4], 0));
   }
+  if (s_rs != st) {
+    NYX_CUDA(c, cudaEventRecord(pl->fork_ev[5], s_rs));
+    NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[5], 0));
+  }
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
-  // a forward pass saved for backward keeps the label table for nyx_backward
-  if (!(k.need & NEED_SAVE) && (s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  if (reset && s_rs == st && (s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));
   return NYX_OK;
 }
