@@ -227,6 +227,9 @@ typedef struct {
   /* Table S3 rows 140-174 (GLCM), per offset and mean per distance */
   double glcm_off[ORC_MAX_DIST][ORC_MAX_DIR][ORC_NGLCM];
   double glcm_mean[ORC_MAX_DIST][ORC_NGLCM];
+  /* Table S1 rows 3-7 / Table S5 IIE, Max IE, Min IE, Mean IE, std IE:
+   * intensity statistics over the ROI's edge pixels (reading c14) */
+  double edge_ii, edge_max, edge_min, edge_mean, edge_std;
 } feat_t;
 
 static const char* GLCM_NAMES[ORC_NGLCM] = {
@@ -391,6 +394,12 @@ static void emit_all(const orc_cfg* c, const feat_t* f, emitter* e) {
         if (d3) emit(e, f->glcm_off[di][o][g], "GLCM_%s_D%d_O%d", GLCM_NAMES[g], c->dist[di], o);
         else emit(e, f->glcm_off[di][o][g], "GLCM_%s_D%d_A%d", GLCM_NAMES[g], c->dist[di], 45 * o);
       }
+
+  emit(e, f->edge_ii, "EDGE_INTEGRATED_INTENSITY");
+  emit(e, f->edge_max, "EDGE_MAX_INTENSITY");
+  emit(e, f->edge_min, "EDGE_MIN_INTENSITY");
+  emit(e, f->edge_mean, "EDGE_MEAN_INTENSITY");
+  emit(e, f->edge_std, "EDGE_STDDEV_INTENSITY");
 }
 
 /* ------------------------------------------------------------------------ */
@@ -639,6 +648,40 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
   f->cov = mean != 0 ? f->std / mean : NAN;
   f->covered = img_max != img_min ? (mx - mn) / (img_max - img_min) : NAN;
   f->piu = (mx + mn) != 0 ? 100.0 * (1.0 - (mx - mn) / (mx + mn)) : NAN;
+
+  /* edge intensity statistics (Table S1 rows 3-7, Table S5): a pixel of the
+   * ROI is an edge pixel when one of its 4 (2D) / 6 (3D) face neighbours is
+   * outside the image or carries another label (reading c14).  Two-pass
+   * mean and unbiased standard deviation over the edge pixels. */
+  {
+    const int nnb = d3 ? 6 : 4;
+    const int nb[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+    int64_t ne = 0;
+    double es = 0, emn = INFINITY, emx = -INFINITY;
+    char* edge = (char*)calloc((size_t)N, 1);
+    for (int64_t k = 0; k < N; ++k) {
+      for (int q = 0; q < nnb && !edge[k]; ++q) {
+        const int64_t x = X[k][0] + nb[q][0], y = X[k][1] + nb[q][1], z = X[k][2] + nb[q][2];
+        if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) edge[k] = 1;
+        else if (mask[base + (z * c->ny + y) * c->nx + x] != r->label) edge[k] = 1;
+      }
+      if (!edge[k]) continue;
+      ++ne;
+      es += I[k];
+      if (I[k] < emn) emn = I[k];
+      if (I[k] > emx) emx = I[k];
+    }
+    const double em = es / ne;  /* every finite ROI has an edge pixel */
+    double ev = 0;
+    for (int64_t k = 0; k < N; ++k)
+      if (edge[k]) ev += (I[k] - em) * (I[k] - em);
+    free(edge);
+    f->edge_ii = es;
+    f->edge_max = emx;
+    f->edge_min = emn;
+    f->edge_mean = em;
+    f->edge_std = ne > 1 ? sqrt(ev / (ne - 1)) : 0.0;
+  }
 
   /* order statistics on the sorted values (reading c11) */
   double* v = (double*)malloc(sizeof(double) * (size_t)N);

@@ -19,7 +19,8 @@ RTOL_STAT = 1e-5
 RTOL_GLCM = 1e-4
 
 EXACT = {"LABEL", "IMAGE", "AREA", "BBOX_XMIN", "BBOX_YMIN", "BBOX_ZMIN", "BBOX_WIDTH", "BBOX_HEIGHT", "BBOX_DEPTH",
-         "MIN", "MAX", "RANGE", "MEDIAN", "P01", "P10", "P25", "P75", "P90", "P99", "INTERQUARTILE_RANGE", "MODE"}
+         "MIN", "MAX", "RANGE", "MEDIAN", "P01", "P10", "P25", "P75", "P90", "P99", "INTERQUARTILE_RANGE", "MODE",
+         "EDGE_MIN_INTENSITY", "EDGE_MAX_INTENSITY"}
 DIMENSIONLESS = {"MODE_PROBABILITY", "SKEWNESS", "KURTOSIS", "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENTROPY",
                  "UNIFORMITY", "COV", "QCOD", "COVERED_IMAGE_INTENSITY_RANGE", "UNIFORMITY_PIU"}
 
@@ -40,15 +41,17 @@ def scales(t: Dict[str, np.ndarray], name: str, ndim: int) -> np.ndarray:
         return one
     if name in DIMENSIONLESS:
         return one
-    if name in ("MEAN", "ROBUST_MEAN", "MEDIAN"):
+    if name in ("MEAN", "ROBUST_MEAN", "MEDIAN", "EDGE_MEAN_INTENSITY"):
         return np.maximum(std, amax * 1e-3)
     if name in ("MEAN_ABSOLUTE_DEVIATION", "MEDIAN_ABSOLUTE_DEVIATION", "ROBUST_MEAN_ABSOLUTE_DEVIATION",
-                "STDDEV", "STDDEV_BIASED", "STANDARD_ERROR"):
+                "STDDEV", "STDDEV_BIASED", "STANDARD_ERROR", "EDGE_STDDEV_INTENSITY"):
         return np.maximum(std, amax * 1e-3)
     if name in ("VARIANCE", "VARIANCE_BIASED"):
         return np.maximum(std ** 2, (amax * 1e-3) ** 2)
     if name.startswith("WEIGHTED_CENTROID") or name.startswith("CENTROID") or name == "MASS_DISPLACEMENT":
         return np.maximum(ext[0], ext[1])
+    if name == "EDGE_INTEGRATED_INTENSITY":
+        return np.abs(t["AREA"]) * amax
     if name in ("ENERGY", "ROOT_MEAN_SQUARED", "INTEGRATED_INTENSITY"):
         return np.abs(t["AREA"]) * amax ** (2 if name == "ENERGY" else 1) * (1 if name != "ROOT_MEAN_SQUARED" else
                                                                                1 / np.maximum(t["AREA"], 1))

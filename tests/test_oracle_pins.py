@@ -537,3 +537,82 @@ def test_small_closed_forms_dispersion(orc):
     assert (t["P25"], t["P75"], t["QCOD"]) == (1.5, 2.5, 0.25)
     assert t["MEAN_ABSOLUTE_DEVIATION"] == 1.0 and t["RANGE"] == 2.0
     assert t["ROBUST_MEAN"] != t["ROBUST_MEAN"]  # no value inside [P10, P90] = [1.2, 2.8]: NaN
+
+
+# --------------------------------------------------------------------------
+# Edge intensity statistics (Table S1 rows 3-7, Table S5): edge pixels are
+# the ROI pixels a face-connected erosion removes (scipy.ndimage, with the
+# image border counted as outside), statistics by NumPy over them.
+
+def _edge_ref(img, mask, label):
+    import scipy.ndimage as ndi
+
+    m = mask == label
+    cross = ndi.generate_binary_structure(m.ndim, 1)
+    inner = ndi.binary_erosion(m, structure=cross, border_value=0)
+    v = img[m & ~inner].astype(np.float64)
+    return {"EDGE_INTEGRATED_INTENSITY": v.sum(), "EDGE_MAX_INTENSITY": v.max(), "EDGE_MIN_INTENSITY": v.min(),
+            "EDGE_MEAN_INTENSITY": v.mean(), "EDGE_STDDEV_INTENSITY": v.std(ddof=1) if v.size > 1 else 0.0}, v.size
+
+
+def test_edge_rectangle_ring(orc):
+    """A 3 x 4 rectangle inside the image: 10 ring pixels, 2 interior ones."""
+    img = np.arange(1, 8 * 9 + 1, dtype=np.uint16).reshape(8, 9) * 7
+    mask = np.zeros(img.shape, dtype=np.int32)
+    mask[2:5, 3:7] = 4
+    t = _single(orc, img, mask, ng=4)
+    ring = np.concatenate([img[2, 3:7], img[4, 3:7], img[3, [3, 6]]]).astype(np.float64)
+    assert ring.size == 10
+    assert t["EDGE_INTEGRATED_INTENSITY"] == ring.sum()
+    assert t["EDGE_MIN_INTENSITY"] == ring.min() and t["EDGE_MAX_INTENSITY"] == ring.max()
+    assert t["EDGE_MEAN_INTENSITY"] == pytest.approx(ring.mean(), rel=1e-15)
+    assert t["EDGE_STDDEV_INTENSITY"] == pytest.approx(ring.std(ddof=1), rel=1e-14)
+
+
+def test_edge_single_pixel_and_line(orc):
+    img = np.full((5, 6), 9, dtype=np.uint16)
+    img[1, 1] = 321
+    mask = np.zeros(img.shape, dtype=np.int32)
+    mask[1, 1] = 1          # one pixel: its own edge, deviation 0
+    mask[3, 0:6] = 2        # full-width line: every pixel is an edge pixel
+    img[3, :] = [5, 1, 4, 1, 5, 9]
+    t = orc.extract(img, mask, 2, ng=4)
+    assert t["EDGE_INTEGRATED_INTENSITY"][0] == 321 and t["EDGE_STDDEV_INTENSITY"][0] == 0
+    assert t["EDGE_INTEGRATED_INTENSITY"][1] == 25 and t["EDGE_MEAN_INTENSITY"][1] == pytest.approx(25 / 6)
+    assert t["EDGE_STDDEV_INTENSITY"][1] == pytest.approx(np.std([5, 1, 4, 1, 5, 9], ddof=1), rel=1e-14)
+
+
+def test_edge_cube_3d_face_neighbours(orc):
+    """3 x 3 x 3 cube: with face neighbours only the centre voxel is inner."""
+    img = np.random.default_rng(7).integers(-500, 500, size=(5, 5, 5)).astype(np.int16)
+    mask = np.zeros(img.shape, dtype=np.int32)
+    mask[1:4, 1:4, 1:4] = 3
+    t = _single(orc, img, mask, ndim=3, ng=4)
+    ref, n = _edge_ref(img, mask, 3)
+    assert n == 26
+    sel = np.ones((3, 3, 3), bool)
+    sel[1, 1, 1] = False
+    assert ref["EDGE_INTEGRATED_INTENSITY"] == img[1:4, 1:4, 1:4][sel].astype(np.float64).sum()
+    for k, v in ref.items():
+        assert t[k] == pytest.approx(v, rel=1e-13)
+
+
+@pytest.mark.parametrize("ndim,seed", [(2, 1), (2, 2), (3, 3)])
+def test_edge_touching_rois_and_border_vs_erosion(orc, ndim, seed):
+    """Random touching blobs, some cut by the image border: a pixel next to
+    another label or to the border is an edge pixel."""
+    rng = np.random.default_rng(seed)
+    shape = (24, 29) if ndim == 2 else (9, 12, 13)
+    img = rng.gamma(2.0, 300.0, size=shape).astype(np.float32)
+    mask = np.zeros(shape, dtype=np.int32)
+    grids = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    for lab in range(1, 7):
+        c = [rng.uniform(-2, s + 2) for s in shape]
+        r = rng.uniform(2.5, 6.0)
+        d2 = sum((g - ci) ** 2 for g, ci in zip(grids, c))
+        mask[d2 <= r * r] = lab
+    t = orc.extract(img, mask, ndim, ng=4)
+    for row, lab in enumerate(t["LABEL"].astype(int)):
+        ref, _ = _edge_ref(img, mask, lab)
+        for k, v in ref.items():
+            assert t[k][row] == pytest.approx(v, rel=1e-12, abs=1e-9), (lab, k)
