@@ -119,8 +119,15 @@ nyx_status nyx_num_columns(const nyx_plan* plan, int* n_col);
 nyx_status nyx_column_name(const nyx_plan* plan, int col, char* buf, size_t cap);
 
 /* Feature id of a feature name (e.g. "MEAN", "INT_HU", "GLCM_CONTRAST"), -1
- * if unknown.  Moment families are one id each (INT_M, INT_MU, INT_ETA,
- * INT_NU, INT_HU and the BIN_ variants). */
+ * if unknown.  Ids: 0..40 first-order statistics (Table S1 / S5), 41..50
+ * moment families, one id each (INT_M, INT_MU, INT_ETA, INT_NU, INT_HU and
+ * the BIN_ variants; Table S2 rows 123-135), 51..80 GLCM features (Table S3
+ * rows 140-174), 81..85 edge intensity statistics (Table S1 rows 3-7,
+ * Table S5): EDGE_INTEGRATED_INTENSITY, EDGE_MAX_INTENSITY,
+ * EDGE_MIN_INTENSITY, EDGE_MEAN_INTENSITY, EDGE_STDDEV_INTENSITY over the
+ * ROI's edge pixels, those with a face neighbour (4 in 2D, 6 in 3D) outside
+ * the ROI or the image; the deviation is the unbiased one (0 for a single
+ * edge pixel). */
 int nyx_feature_id(const char* name);
 
 /* Run the label scan only and return the number of ROIs (distinct

@@ -37,7 +37,8 @@ cudaError_t launch_backward(const KParams& p, const double* gtab, float* gimg, i
 using namespace nyx;
 
 // ---------------------------------------------------------------------------
-// feature registry: ids 0..40 statistics, 41..50 moment families, 51..80 GLCM
+// feature registry: ids 0..40 statistics, 41..50 moment families, 51..80 GLCM,
+// 81..85 edge intensity statistics
 
 namespace {
 
@@ -53,9 +54,12 @@ const char* GLCM_NAMES[NGLCM] = {
     "ASM", "ACOR", "CLUPROM", "CLUSHADE", "CLUTEND", "CONTRAST", "CORR", "DIFAVE", "DIFENTRO", "DIFVAR",
     "DIS", "ENERGY", "ENTROPY", "HOM1", "HOM2", "IDM", "INFOMEAS1", "INFOMEAS2", "IDMN", "ID",
     "IDN", "IV", "JAVE", "JE", "JMAX", "SUMAVE", "SUMENT", "JVAR", "SUMVAR", "VARIANCE"};
+const char* EDGE_NAMES[N_EDGE] = {"EDGE_INTEGRATED_INTENSITY", "EDGE_MAX_INTENSITY", "EDGE_MIN_INTENSITY",
+                                  "EDGE_MEAN_INTENSITY", "EDGE_STDDEV_INTENSITY"};
 constexpr int FID_MOM = N_STATS;         // 41
 constexpr int FID_GLCM = N_STATS + 10;   // 51
-constexpr int N_FID = FID_GLCM + NGLCM;  // 81
+constexpr int FID_EDGE = FID_GLCM + NGLCM;  // 81
+constexpr int N_FID = FID_EDGE + N_EDGE;    // 86
 
 bool is_order_stat(int s) {
   return s == S_MEDIAN || s == S_P01 || s == S_P10 || s == S_P25 || s == S_P75 || s == S_P90 || s == S_P99 ||
@@ -214,6 +218,8 @@ int nyx_feature_id(const char* name) {
     snprintf(b, sizeof b, "GLCM_%s", GLCM_NAMES[g]);
     if (!strcmp(name, b)) return FID_GLCM + g;
   }
+  for (int e = 0; e < N_EDGE; ++e)
+    if (!strcmp(name, EDGE_NAMES[e])) return FID_EDGE + e;
   return -1;
 }
 
@@ -310,6 +316,8 @@ static void build_columns(nyx_plan* pl) {
                   std::string("GLCM_") + GLCM_NAMES[g] + "_D" + std::to_string(p.dists[di]) +
                       (d3 ? "_O" + std::to_string(o) : "_A" + std::to_string(45 * o)));
   }
+  for (int e = 0; e < N_EDGE; ++e)
+    if (fbit(p, FID_EDGE + e)) add(Q_EDGE + e, EDGE_NAMES[e]);
 }
 
 // GLCM unit directions: 2D angles 0/45/90/135 degrees as (dx,dy) = (1,0),
@@ -432,6 +440,10 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   if (p.glcm_levels > 0)
     for (int g = 0; g < NGLCM; ++g)
       if (fbit(p, FID_GLCM + g)) need |= NEED_GLCM;
+  for (int e = 0; e < N_EDGE; ++e)
+    if (fbit(p, FID_EDGE + e)) need |= NEED_EDGE;
+  // the edge test reads face neighbours from the padded bin raster
+  if ((need & NEED_EDGE) && k.pad < 1) k.pad = 1;
   k.need = need;
   k.keys = (unsigned long long*)(w + o_keys);
   k.slots = (SlotAcc*)(w + o_slots);

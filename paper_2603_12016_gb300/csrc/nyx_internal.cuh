@@ -87,6 +87,7 @@ struct BigRoi {
   int gsp;                  // padded raster cells per GLCM span; 0 = global-memory neighbours
   int hal;                  // raster halo: the largest neighbour displacement in padded cells
   double st[10];            // pass-1 scalars: mean (hi, lo), centroids, sum I, energy
+  double est[2];            // edge pixels: mean, count (float images finish their deviation in pass 2)
 };
 
 // ---------------------------------------------------------------------------
@@ -99,8 +100,13 @@ enum : int {
   Q_MOM = Q_STATS + N_STATS,          // + (weighting*5 + family)*20 + k
   Q_GLCM_D = Q_MOM + 200,             // + di*30 + g
   Q_GLCM_O = Q_GLCM_D + MAX_DIST * NGLCM,  // + (di*13 + dir)*30 + g
-  Q_TOTAL = Q_GLCM_O + MAX_DIST * MAX_DIRS * NGLCM
+  Q_EDGE = Q_GLCM_O + MAX_DIST * MAX_DIRS * NGLCM,  // + e (edge intensity statistics)
+  N_EDGE = 5,
+  Q_TOTAL = Q_EDGE + N_EDGE
 };
+
+// edge intensity statistics (Table S1 rows 3-7, Table S5), index within Q_EDGE
+enum : int { E_II = 0, E_MAX, E_MIN, E_MEAN, E_STD };
 
 // first-order statistics (Table S1 / S5), index within Q_STATS
 enum : int {
@@ -129,6 +135,7 @@ enum : unsigned {
   NEED_MOM_BIN = 16u, // binary moments
   NEED_GLCM = 32u,
   NEED_SAVE = 64u,    // keep per-ROI state for the backward pass
+  NEED_EDGE = 128u,   // edge intensity statistics
 };
 
 // saved per-ROI state for the backward pass (FP64 words per ROI)
@@ -206,8 +213,8 @@ __host__ __device__ inline unsigned big_units2(unsigned long long c) { return (u
 // counters, histograms, per-offset co-occurrence triangles (multi-chunk ROIs),
 // per-chunk partial sums, float sort buffers.  The prefix [0, zero_end) must
 // be zero when the passes start.
-constexpr int BIG_P1 = 28;   // pass-1 partial per chunk: 9 int64 + 5 doubles
-constexpr int BIG_P2 = 96;   // pass-2 partial per chunk: 48 doubles
+constexpr int BIG_P1 = 38;   // pass-1 partial per chunk: 9 int64 + 5 doubles + 5 edge words (8 bytes each)
+constexpr int BIG_P2 = 98;   // pass-2 partial per chunk: 48 doubles + the edge squared deviations
 struct BigLayout {
   unsigned long long ctr, hist, vhist, tri, zero_end, part1, part2, fsort, total;
 };

@@ -159,6 +159,21 @@ __device__ inline A decA(unsigned e) {
   else return Enc<T>::dec(e);
 }
 
+// Edge test of one ROI pixel (packed bbox-local coordinates c, as in the
+// pixel list) on the padded raster (pad >= 1): true when a face neighbour is
+// not a cell of the ROI.
+template <int NDIM>
+__device__ inline bool edge_pixel(const uint16_t* raster, unsigned c, int pad, int Wp, int Hp, int plane) {
+  const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
+  const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
+  const int z = NDIM == 3 ? (int)(c >> 22) : 0;
+  const int ri = ((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad);
+  bool e = raster[ri - 1] == 0xFFFFu || raster[ri + 1] == 0xFFFFu || raster[ri - Wp] == 0xFFFFu ||
+           raster[ri + Wp] == 0xFFFFu;
+  if (NDIM == 3) e = e || raster[ri - plane] == 0xFFFFu || raster[ri + plane] == 0xFFFFu;
+  return e;
+}
+
 // ----------------------------------------------------------------------------
 // block reductions (results are left in shared memory for every thread)
 
@@ -905,7 +920,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
   const int* queue = p.queue + (int64_t)cls * p.max_rois;
   const int64_t per = p.nx * p.ny * p.nz;
   const bool need_glcm = (p.need & NEED_GLCM) != 0;
-  const int pad = need_glcm ? p.pad : 0;
+  const bool need_raster = (p.need & (NEED_GLCM | NEED_EDGE)) != 0;  // padded raster of the ROI's cells
+  const int pad = need_raster ? p.pad : 0;
   const A nan = anan<A>();
 
   for (;;) {
@@ -1023,7 +1039,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
               if (need & NEED_HIST) hb = bin_float(xv, fmn, fmx, p.hist_bins);
             }
           }
-          if (need_glcm) {
+          if (need_raster) {
             const int ri = ((NDIM == 3 ? rz + pad : 0) * Hp + (ry + pad)) * Wp + (x + pad);
             if (ri < cells) raster[ri] = (uint16_t)gb;
             else atomicOr(p.err, E_INTERNAL);
@@ -1153,6 +1169,69 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     const A cx = s_pa[2], cy = s_pa[3], cz = s_pa[4], bx = s_pa[5], by = s_pa[6], bz = s_pa[7];
     const A sumI = s_pa[8], energy = s_pa[9];
     const bool wvalid = sumI != 0;
+
+    // ---- edge intensity statistics (Table S1 rows 3-7, Table S5) ------------
+    // An edge pixel has a face neighbour (4 in 2D, 6 in 3D) outside the ROI:
+    // in the padded raster every cell that is not one of the ROI's pixels
+    // (another label, background, beyond the image) holds the sentinel.
+    if (need & NEED_EDGE) {
+      const int plane = Wp * Hp;
+      // count, sum d, sum d^2 with d = code - vmin (exact for integer images)
+      long long es[3] = {0, 0, 0};
+      A ef[1] = {0};  // float images: sum of (x - min)
+      unsigned emn = 0xFFFFFFFFu, emx = 0;
+      for (int i = tid; i < n; i += C::NT) {
+        if (!edge_pixel<NDIM>(raster, pc[i], pad, Wp, Hp, plane)) continue;
+        const unsigned e = pv[i];
+        es[0] += 1;
+        emn = min(emn, e);
+        emx = max(emx, e);
+        if (Enc<T>::INTEGER) {
+          const long long d = (long long)(e - vmin);
+          es[1] += d;
+          es[2] += d * d;
+        } else {
+          ef[0] += decA<T, A>(e) - (A)fmn;
+        }
+      }
+      block_sum_i64<C, 3>(es, red, s_i64);
+      if (!Enc<T>::INTEGER) block_sum<C, A, 1>(ef, red, s_sc + 12);
+      const unsigned bmx = (unsigned)block_max_u64<C>(emx, red);
+      const unsigned bmn = 0xFFFFFFFFu - (unsigned)block_max_u64<C>(0xFFFFFFFFu - emn, red);
+      const long long ne = s_i64[0];  // >= 1: a finite ROI has an edge pixel
+      A emean, estd;
+      if (Enc<T>::INTEGER) {
+        const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
+        const long long s1 = s_i64[1];
+        const __int128 num = (__int128)ne * s_i64[2] - (__int128)s1 * s1;  // n^2 var_biased, exact
+        emean = (A)(s1 + ne * ((long long)vmin - bias)) / (A)ne;
+        estd = ne > 1 ? asqrt(i128A<A>(num) / ((A)ne * (A)(ne - 1))) : (A)0;
+        if (tid == 0) put(p, row, Q_EDGE + E_II, i2d(s1 + ne * ((long long)vmin - bias)));
+      } else {
+        emean = (A)fmn + s_sc[12] / (A)ne;
+        A ev[1] = {0};
+        for (int i = tid; i < n; i += C::NT) {
+          if (!edge_pixel<NDIM>(raster, pc[i], pad, Wp, Hp, plane)) continue;
+          const A d = decA<T, A>(pv[i]) - emean;
+          ev[0] += d * d;
+        }
+        block_sum<C, A, 1>(ev, red, s_sc + 13);
+        estd = ne > 1 ? asqrt(s_sc[13] / (A)(ne - 1)) : (A)0;
+        if (tid == 0) putA(p, row, Q_EDGE + E_II, (A)fmn * (A)ne + s_sc[12]);
+      }
+      if (tid == 0) {
+        if (Enc<T>::INTEGER) {
+          const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
+          put(p, row, Q_EDGE + E_MAX, i2d((long long)bmx - bias));
+          put(p, row, Q_EDGE + E_MIN, i2d((long long)bmn - bias));
+        } else {
+          put(p, row, Q_EDGE + E_MAX, f2d(Enc<T>::decf(bmx)));
+          put(p, row, Q_EDGE + E_MIN, f2d(Enc<T>::decf(bmn)));
+        }
+        putA(p, row, Q_EDGE + E_MEAN, emean);
+        putA(p, row, Q_EDGE + E_STD, estd);
+      }
+    }
 
     // ---- pass 2: centred sums (one loop per feature group keeps the live
     // accumulators few) -------------------------------------------------------

@@ -128,6 +128,23 @@ struct BigBox {
 // thread issues the mask and image loads of BIG_U cells before using them (a
 // cell of the bounding box is always inside the image, so the image load
 // needs no mask test): the loop is bound by L2 latency, not bandwidth.
+// Edge test of an ROI voxel at bbox-local (x, y, z): a face neighbour
+// (4 in 2D, 6 in 3D) outside the bounding box, or inside it under another
+// label, makes it an edge voxel.  Neighbour labels are read from the mask.
+template <int NDIM>
+__device__ inline bool big_edge(const KParams& p, const BigBox& bx, int x, int y, int z) {
+  const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
+  if (x == 0 || x == bx.W - 1 || y == 0 || y == bx.H - 1) return true;
+  if (NDIM == 3 && (z == 0 || z == bx.D - 1)) return true;
+  bool e = __ldg(p.mask + here - 1) != bx.label || __ldg(p.mask + here + 1) != bx.label ||
+           __ldg(p.mask + here - p.nx) != bx.label || __ldg(p.mask + here + p.nx) != bx.label;
+  if (NDIM == 3) {
+    const int64_t pl = p.nx * p.ny;
+    e = e || __ldg(p.mask + here - pl) != bx.label || __ldg(p.mask + here + pl) != bx.label;
+  }
+  return e;
+}
+
 constexpr int BIG_U = 4;
 template <class T, class F>
 __device__ inline void chunk_cells(const KParams& p, const BigBox& bx, unsigned c0, unsigned c1, F f) {
@@ -378,10 +395,28 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
     // [0] sum I, [1] sum x I, [2] sum y I, [3] sum z I, [4] sum x, [5] sum y, [6] sum z, [7] sum I^2, [8] count
     long long s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     KSum<A> fs[5];  // float images: sum I, x I, y I, z I, I^2
+    // edge voxels: count, sum d, sum d^2 with d = code - vmin (exact for
+    // integer images); float images sum d compensated
+    const bool do_edge = (need & NEED_EDGE) != 0;
+    long long es[3] = {0, 0, 0};
+    KSum<A> ef[1];
+    unsigned emn = 0xFFFFFFFFu, emx = 0;
     unsigned* gvh = reg + L.vhist;
     chunk_voxels<T>(p, bx, c0, c1, s_qc + (tid >> 5) * 64, s_qe + (tid >> 5) * 64,
                     [&](bool in, int x, int y, int z, unsigned e) {
       unsigned hb = 0xFFFFFFFFu, vb = 0xFFFFFFFFu;
+      if (in && do_edge && big_edge<NDIM>(p, bx, x, y, z)) {
+        es[0] += 1;
+        emn = min(emn, e);
+        emx = max(emx, e);
+        if constexpr (integer) {
+          const long long d = (long long)(e - vmin);
+          es[1] += d;
+          es[2] += d * d;
+        } else {
+          ef[0].add(decA<T, A>(e) - (A)fmn);
+        }
+      }
       if (in) {
         s[4] += x;
         s[5] += y;
@@ -423,6 +458,13 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
     });
     block_sum_i64<C, 9>(s, red, s_i64);
     if constexpr (!integer) block_sum_k<C, A, 5>(fs, red, s_sc);
+    unsigned bmn = 0xFFFFFFFFu, bmx = 0;
+    if (do_edge) {
+      block_sum_i64<C, 3>(es, red, s_i64 + 9);
+      if constexpr (!integer) block_sum_k<C, A, 1>(ef, red, s_sc + 5);
+      bmx = (unsigned)block_max_u64<C>(emx, red);
+      bmn = 0xFFFFFFFFu - (unsigned)block_max_u64<C>(0xFFFFFFFFu - emn, red);
+    }
     if (do_hist)
       for (int i = tid; i < p.hist_bins; i += BIG_NT)
         if (hist[i]) atomicAdd(reg + L.hist + i, hist[i]);
@@ -434,6 +476,13 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
       for (int k = 0; k < 9; ++k) pt[k] = s_i64[k];
       double* pf = (double*)(pt + 9);
       for (int k = 0; k < 5; ++k) pf[k] = integer ? 0.0 : to_d(s_sc[k]);
+      // [14] edge count, [15] sum d (float images: as a double), [16] sum d^2, [17] min code, [18] max code
+      pt[14] = do_edge ? s_i64[9] : 0;
+      if constexpr (integer) pt[15] = do_edge ? s_i64[10] : 0;
+      else ((double*)pt)[15] = do_edge ? to_d(s_sc[5]) : 0.0;
+      pt[16] = do_edge ? s_i64[11] : 0;
+      pt[17] = bmn;
+      pt[18] = bmx;
     }
     if (!last_arrival(reg + L.ctr + 0, (unsigned)br.nch, &s_flag)) continue;
 
@@ -524,6 +573,50 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
         put(p, row, Q_STATS + S_MAX, f2d(fmx));
         put(p, row, Q_STATS + S_RANGE, __dsub_rn(f2d(fmx), f2d(fmn)));
       }
+      if (do_edge) {  // edge intensity statistics, merged in chunk order
+        long long ne = 0, e1 = 0, e2 = 0;
+        unsigned lo_c = 0xFFFFFFFFu, hi_c = 0;
+        A eh = 0, el = 0;
+        for (int ch = 0; ch < br.nch; ++ch) {
+          const long long* pt = (const long long*)(reg + L.part1) + (size_t)ch * (BIG_P1 / 2);
+          ne += __ldcg(pt + 14);
+          if constexpr (integer) {
+            e1 += __ldcg(pt + 15);
+          } else {
+            const A x = (A)__ldcg((const double*)pt + 15);
+            if constexpr (std::is_same<A, float>::value) {
+              float sum, err;
+              two_sum(eh, x, sum, err);
+              eh = sum;
+              el += err;
+            } else {
+              eh += x;
+            }
+          }
+          e2 += __ldcg(pt + 16);
+          lo_c = min(lo_c, (unsigned)__ldcg(pt + 17));
+          hi_c = max(hi_c, (unsigned)__ldcg(pt + 18));
+        }
+        A emean;
+        if constexpr (integer) {
+          const long long sumx = e1 + ne * ((long long)vmin - ibias);
+          const __int128 num = (__int128)ne * e2 - (__int128)e1 * e1;  // n^2 var_biased, exact
+          emean = (A)sumx / (A)ne;
+          put(p, row, Q_EDGE + E_II, i2d(sumx));
+          put(p, row, Q_EDGE + E_MAX, i2d((long long)hi_c - ibias));
+          put(p, row, Q_EDGE + E_MIN, i2d((long long)lo_c - ibias));
+          putA(p, row, Q_EDGE + E_STD, ne > 1 ? asqrt(i128A<A>(num) / ((A)ne * (A)(ne - 1))) : (A)0);
+        } else {
+          const A sd = eh + el;
+          emean = (A)fmn + sd / (A)ne;
+          putA(p, row, Q_EDGE + E_II, (A)fmn * (A)ne + sd);
+          put(p, row, Q_EDGE + E_MAX, f2d(Enc<T>::decf(hi_c)));
+          put(p, row, Q_EDGE + E_MIN, f2d(Enc<T>::decf(lo_c)));
+        }
+        putA(p, row, Q_EDGE + E_MEAN, emean);
+        p.big[b].est[0] = to_d(emean);
+        p.big[b].est[1] = (double)ne;
+      }
     }
     // histogram features
     if (do_hist) {
@@ -589,9 +682,15 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p2(KParams p
     for (int i = 0; i < 8; ++i) acc[i] = 0;
 #pragma unroll
     for (int i = 0; i < NM; ++i) mi[i] = mb[i] = 0;
+    // float images: squared deviations of the edge voxels from their mean
+    // (integer images finish their edge statistics exactly in pass 1)
+    const bool do_edge = !Enc<T>::INTEGER && (need & NEED_EDGE) != 0;
+    const A emean = do_edge ? (A)__ldcg(p.big[b].est + 0) : (A)0;
+    A ev[1] = {0};
     chunk_voxels<T>(p, bx, c0, c1, s_qc + warp * 64, s_qe + warp * 64, [&](bool in, int x, int y, int z, unsigned e) {
       if (!in) return;
       const A v = Enc<T>::INTEGER ? (A)((long long)e - ibias) : decA<T, A>(e);
+      if (do_edge && big_edge<NDIM>(p, bx, x, y, z)) ev[0] += (v - emean) * (v - emean);
       if (do_st) {
         const A d = (v - mu_hi) - mu_lo;
         const A d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
@@ -637,9 +736,31 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p2(KParams p
     __syncthreads();
     block_sum<C, A, NM>(mb, red, res);
     if (tid < NM) part[8 + NM + tid] = do_mb ? to_d(res[tid]) : 0.0;
+    __syncthreads();
+    if (do_edge) {
+      block_sum<C, A, 1>(ev, red, res);
+      if (tid == 0) part[48] = to_d(res[0]);
+    }
     if (!last_arrival(reg + L.ctr + 1, (unsigned)br.nch, &s_flag)) continue;
 
     // ---- last chunk: merge the partials in chunk order, finalise ----------
+    if (do_edge && tid == 0) {
+      A hi = 0, lo = 0;
+      for (int ch = 0; ch < br.nch; ++ch) {
+        const A x = (A)__ldcg((const double*)(reg + L.part2) + (size_t)ch * (BIG_P2 / 2) + 48);
+        if constexpr (std::is_same<A, float>::value) {
+          float sum, err;
+          two_sum(hi, x, sum, err);
+          hi = sum;
+          lo += err;
+        } else {
+          hi += x;
+        }
+      }
+      const double ne = __ldcg(p.big[b].est + 1);
+      putA(p, p.table + (int64_t)br.item * p.n_col, Q_EDGE + E_STD,
+           ne > 1.5 ? asqrt((hi + lo) / (A)(ne - 1.0)) : (A)0);
+    }
     if (tid < NV) {
       A hi = 0, lo = 0;
       for (int ch = 0; ch < br.nch; ++ch) {
