@@ -562,6 +562,20 @@ static double ipow(double x, int k) {
 }
 
 /* All features of one ROI. */
+/* Edge test (reading c14): pixel (x, y, z) of ROI `label` in image `base`
+ * has a face neighbour (4 in 2D, 6 in 3D) outside the image or under
+ * another label. */
+static int is_edge(const orc_cfg* c, const int32_t* mask, int64_t base, const int64_t* X, int32_t label) {
+  static const int nb[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  const int nnb = c->ndim == 3 ? 6 : 4;
+  for (int q = 0; q < nnb; ++q) {
+    const int64_t x = X[0] + nb[q][0], y = X[1] + nb[q][1], z = X[2] + nb[q][2];
+    if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) return 1;
+    if (mask[base + (z * c->ny + y) * c->nx + x] != label) return 1;
+  }
+  return 0;
+}
+
 static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, const roi_t* r, double img_min,
                         double img_max, feat_t* f) {
   const int64_t per = c->nx * c->ny * c->nz;
@@ -654,17 +668,11 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
    * outside the image or carries another label (reading c14).  Two-pass
    * mean and unbiased standard deviation over the edge pixels. */
   {
-    const int nnb = d3 ? 6 : 4;
-    const int nb[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
     int64_t ne = 0;
     double es = 0, emn = INFINITY, emx = -INFINITY;
     char* edge = (char*)calloc((size_t)N, 1);
     for (int64_t k = 0; k < N; ++k) {
-      for (int q = 0; q < nnb && !edge[k]; ++q) {
-        const int64_t x = X[k][0] + nb[q][0], y = X[k][1] + nb[q][1], z = X[k][2] + nb[q][2];
-        if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) edge[k] = 1;
-        else if (mask[base + (z * c->ny + y) * c->nx + x] != r->label) edge[k] = 1;
-      }
+      edge[k] = (char)is_edge(c, mask, base, X[k], r->label);
       if (!edge[k]) continue;
       ++ne;
       es += I[k];
@@ -1019,6 +1027,17 @@ static int find_name(char (*names)[ORC_NAME], int nf, const char* s) {
 /* gtab: [n_roi x n_features] upstream gradient rows in the order of
  * orc_extract (ascending (image, label) key).  grad: image-shaped FP64
  * output (zero outside ROIs).  Returns the ROI count or a negative error. */
+/* number of edge pixels of ROI R (reading c14) */
+static int64_t edge_count(const orc_cfg* c, const int32_t* mask, const roi_t* R, int64_t per) {
+  int64_t ne = 0;
+  for (int64_t k = 0; k < R->n; ++k) {
+    const int64_t lin = R->lin[k];
+    const int64_t xi[3] = {lin % c->nx, (lin / c->nx) % c->ny, lin / (c->nx * c->ny)};
+    ne += is_edge(c, mask, R->b * per, xi, R->label);
+  }
+  return ne;
+}
+
 int64_t orc_grad(const orc_cfg* c, const void* img, const int32_t* mask, const double* gtab, double* grad) {
   roi_t* r = NULL;
   int64_t n = separate(c, mask, NULL, 0, &r);
@@ -1055,6 +1074,11 @@ int64_t orc_grad(const orc_cfg* c, const void* img, const int32_t* mask, const d
                  ghf = G("HYPERFLATNESS"), gen = G("ENERGY"), grms = G("ROOT_MEAN_SQUARED"),
                  gse = G("STANDARD_ERROR"), gmad = G("MEAN_ABSOLUTE_DEVIATION"), gcov = G("COV"),
                  gmd = G("MASS_DISPLACEMENT");
+    /* edge statistics over the fixed edge set E (reading c14): d II_E = 1,
+     * d mean_E = 1/n_E, d std_E = (I - mean_E) / ((n_E - 1) std_E) on E */
+    const double geii = G("EDGE_INTEGRATED_INTENSITY"), gemean = G("EDGE_MEAN_INTENSITY"),
+                 gestd = G("EDGE_STDDEV_INTENSITY");
+    const int64_t ne_e = (geii != 0 || gemean != 0 || gestd != 0) ? edge_count(c, mask, R, per) : 0;
     double gwc[3];
     for (int a = 0; a < 3; ++a) {
       char s[48];
@@ -1150,6 +1174,10 @@ int64_t orc_grad(const orc_cfg* c, const void* img, const int32_t* mask, const d
         acc += gM[kk] * dM + gMU[kk] * dMU;
         if (o >= 2) acc += gETA[kk] * (dMU / pow(mu00, gam) - gam * f->ETA[0][kk] * dmu00 / mu00);
         if (!d3) acc += gNU[kk] * (dM / pow(M00, gam) - gam * f->NU[0][kk] / M00);
+      }
+      if (ne_e > 0 && is_edge(c, mask, R->b * per, xi, R->label)) {
+        acc += geii + gemean / ne_e;
+        if (f->edge_std > 0) acc += gestd * (Ik - f->edge_mean) / ((ne_e - 1) * f->edge_std);
       }
       grad[R->b * per + lin] = acc;
     }

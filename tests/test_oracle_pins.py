@@ -451,7 +451,7 @@ def test_3d_box_moments(orc):
 SMOOTH = ["MEAN", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS", "KURTOSIS",
           "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED", "STANDARD_ERROR",
           "MEAN_ABSOLUTE_DEVIATION", "INTEGRATED_INTENSITY", "WEIGHTED_CENTROID_X", "WEIGHTED_CENTROID_Y",
-          "MASS_DISPLACEMENT", "COV"]
+          "MASS_DISPLACEMENT", "COV", "EDGE_INTEGRATED_INTENSITY", "EDGE_MEAN_INTENSITY", "EDGE_STDDEV_INTENSITY"]
 
 
 def _moment_names(ndim):
@@ -616,3 +616,23 @@ def test_edge_touching_rois_and_border_vs_erosion(orc, ndim, seed):
         ref, _ = _edge_ref(img, mask, lab)
         for k, v in ref.items():
             assert t[k][row] == pytest.approx(v, rel=1e-12, abs=1e-9), (lab, k)
+
+
+def test_gradient_edge_features_closed_forms(orc):
+    """Edge mean and integrated intensity: constant gradient on the edge
+    ring, zero inside; edge deviation: (I - mean_E) / ((n_E - 1) std_E)."""
+    rng = np.random.default_rng(41)
+    img = rng.uniform(10, 20, size=(6, 7))
+    mask = np.zeros((6, 7), dtype=np.int32)
+    mask[1:5, 1:6] = 1
+    ring = mask.astype(bool).copy()
+    ring[2:4, 2:5] = False
+    ne = ring.sum()
+    g = orc.grad(img, mask, 2, {"EDGE_MEAN_INTENSITY": np.array([1.0])})
+    assert np.allclose(g[ring], 1.0 / ne, rtol=1e-14) and np.all(g[~ring] == 0)
+    g = orc.grad(img, mask, 2, {"EDGE_INTEGRATED_INTENSITY": np.array([2.5])})
+    assert np.allclose(g[ring], 2.5, rtol=1e-14) and np.all(g[~ring] == 0)
+    v = img[ring]
+    g = orc.grad(img, mask, 2, {"EDGE_STDDEV_INTENSITY": np.array([1.0])})
+    assert np.allclose(g[ring], (v - v.mean()) / ((ne - 1) * v.std(ddof=1)), rtol=1e-12)
+    assert np.all(g[~ring] == 0)
