@@ -212,8 +212,10 @@ nyx_status nyx_extract_tiles(nyx_plan* plan, int64_t tile_w, int64_t tile_h, nyx
 nyx_status nyx_sync_status(nyx_plan* plan, void* stream);
 
 /* Backward pass of the smooth intensity features (first-order statistics
- * except order statistics, weighted centroids, mass displacement and every
- * intensity-weighted moment) with respect to the pixel intensities: given
+ * except order statistics, weighted centroids, mass displacement, every
+ * intensity-weighted moment, and the edge integrated intensity, mean and
+ * deviation, differentiated on the fixed edge set) with respect to the pixel
+ * intensities: given
  * dL/dF for every output cell (d_grad_table, FP64 [n_roi x n_col], same
  * layout as the last nyx_extract made with NYX_SAVE_FOR_BACKWARD), write
  * dL/dI for every pixel to d_grad_img (FP32, image shape; 0 outside ROIs).

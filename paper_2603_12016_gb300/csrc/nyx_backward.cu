@@ -30,6 +30,7 @@ namespace nyx {
 namespace {
 
 constexpr int CW = 40;  // floats per ROI of coefficients
+constexpr int EC0 = 37; // edge-statistics coefficients e0, e1, mean_E (after 17 + 20 moment ones)
 
 __device__ inline double gget(const KParams& p, const double* g, int q) {
   const int c = __ldg(p.col_map + q);
@@ -303,6 +304,15 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
           cf[17 + k] = (float)(b[k] * dpow(L, pp + qq + rr));
         }
     for (int k = 17 + NM; k < CW; ++k) cf[k] = 0.f;
+    // ---- edge statistics, on edge pixels only: e0 + e1 (I - mean_E)
+    const double geii = gget(p, g, Q_EDGE + E_II), gem = gget(p, g, Q_EDGE + E_MEAN),
+                 ges = gget(p, g, Q_EDGE + E_STD);
+    if (geii != 0 || gem != 0 || ges != 0) {
+      const double ne = sv[SV_ECNT], es = sv[SV_ESTD];
+      cf[EC0] = (float)(geii + gem / ne);
+      cf[EC0 + 1] = (float)(es > 0 && ne > 1 ? ges / ((ne - 1) * es) : 0.0);
+      cf[EC0 + 2] = (float)sv[SV_EMEAN];
+    }
   }
 }
 
@@ -329,6 +339,19 @@ __global__ void k_bwd_pixel(KParams p, const float* coef, float* gimg) {
         poly += t > 0 ? cf[9] : (t < 0 ? -cf[9] : 0.f);
         const int64_t rem = i - b * per;
         const int x = (int)(rem % p.nx), y = (int)((rem / p.nx) % p.ny), z = (int)(rem / (p.nx * p.ny));
+        const float e0 = cf[EC0], e1 = cf[EC0 + 1];
+        if (e0 != 0.f || e1 != 0.f) {  // edge statistics: face-neighbour test on the mask
+          bool edge = x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1;
+          if (NDIM == 3) edge = edge || z == 0 || z == p.nz - 1;
+          if (!edge)
+            edge = __ldg(p.mask + i - 1) != L || __ldg(p.mask + i + 1) != L || __ldg(p.mask + i - p.nx) != L ||
+                   __ldg(p.mask + i + p.nx) != L;
+          if (NDIM == 3 && !edge) {
+            const int64_t pl = p.nx * p.ny;
+            edge = __ldg(p.mask + i - pl) != L || __ldg(p.mask + i + pl) != L;
+          }
+          if (edge) poly += e0 + e1 * (I - cf[EC0 + 2]);
+        }
         const float il = cf[16];
         const float u = ((float)x - cf[13] - cf[10]) * il, v = ((float)y - cf[14] - cf[11]) * il,
                     w = ((float)z - cf[15] - cf[12]) * il;

@@ -145,7 +145,9 @@ enum : int {
   SV_BX, SV_BY, SV_BZ,          // binary centroid, image coordinates
   SV_X0, SV_Y0, SV_Z0,          // bounding-box origin
   SV_MU = 19,                   // 20 central intensity moments
-  SV_WORDS = SV_MU + 20
+  SV_EMEAN = SV_MU + 20,        // edge pixels: mean, unbiased deviation, count
+  SV_ESTD, SV_ECNT,
+  SV_WORDS
 };
 
 // Kernel parameters (by value).

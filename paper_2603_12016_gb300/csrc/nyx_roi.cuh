@@ -1230,6 +1230,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         }
         putA(p, row, Q_EDGE + E_MEAN, emean);
         putA(p, row, Q_EDGE + E_STD, estd);
+        if (need & NEED_SAVE) {
+          double* sv = p.saved + (size_t)item * SV_WORDS;
+          sv[SV_EMEAN] = to_d(emean);
+          sv[SV_ESTD] = to_d(estd);
+          sv[SV_ECNT] = i2d(ne);
+        }
       }
     }
 

@@ -598,14 +598,17 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
           hi_c = max(hi_c, (unsigned)__ldcg(pt + 18));
         }
         A emean;
+        double* sv = (need & NEED_SAVE) ? p.saved + (size_t)br.item * SV_WORDS : nullptr;
         if constexpr (integer) {
           const long long sumx = e1 + ne * ((long long)vmin - ibias);
           const __int128 num = (__int128)ne * e2 - (__int128)e1 * e1;  // n^2 var_biased, exact
           emean = (A)sumx / (A)ne;
+          const A estd = ne > 1 ? asqrt(i128A<A>(num) / ((A)ne * (A)(ne - 1))) : (A)0;
           put(p, row, Q_EDGE + E_II, i2d(sumx));
           put(p, row, Q_EDGE + E_MAX, i2d((long long)hi_c - ibias));
           put(p, row, Q_EDGE + E_MIN, i2d((long long)lo_c - ibias));
-          putA(p, row, Q_EDGE + E_STD, ne > 1 ? asqrt(i128A<A>(num) / ((A)ne * (A)(ne - 1))) : (A)0);
+          putA(p, row, Q_EDGE + E_STD, estd);
+          if (sv) sv[SV_ESTD] = to_d(estd);
         } else {
           const A sd = eh + el;
           emean = (A)fmn + sd / (A)ne;
@@ -615,7 +618,11 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
         }
         putA(p, row, Q_EDGE + E_MEAN, emean);
         p.big[b].est[0] = to_d(emean);
-        p.big[b].est[1] = (double)ne;
+        p.big[b].est[1] = i2d(ne);
+        if (sv) {
+          sv[SV_EMEAN] = to_d(emean);
+          sv[SV_ECNT] = i2d(ne);
+        }
       }
     }
     // histogram features
@@ -758,8 +765,9 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p2(KParams p
         }
       }
       const double ne = __ldcg(p.big[b].est + 1);
-      putA(p, p.table + (int64_t)br.item * p.n_col, Q_EDGE + E_STD,
-           ne > 1.5 ? asqrt((hi + lo) / (A)(ne - 1.0)) : (A)0);
+      const A estd = ne > 1.5 ? asqrt((hi + lo) / (A)(ne - 1.0)) : (A)0;
+      putA(p, p.table + (int64_t)br.item * p.n_col, Q_EDGE + E_STD, estd);
+      if (need & NEED_SAVE) p.saved[(size_t)br.item * SV_WORDS + SV_ESTD] = to_d(estd);
     }
     if (tid < NV) {
       A hi = 0, lo = 0;

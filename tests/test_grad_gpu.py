@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 SMOOTH = ["MEAN", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS", "KURTOSIS", "EXCESS_KURTOSIS",
           "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED", "STANDARD_ERROR", "MEAN_ABSOLUTE_DEVIATION",
           "INTEGRATED_INTENSITY", "WEIGHTED_CENTROID_X", "WEIGHTED_CENTROID_Y", "WEIGHTED_CENTROID_Z",
-          "MASS_DISPLACEMENT", "COV"]
+          "MASS_DISPLACEMENT", "COV", "EDGE_INTEGRATED_INTENSITY", "EDGE_MEAN_INTENSITY", "EDGE_STDDEV_INTENSITY"]
 FAMILIES = ["INT_M", "INT_MU", "INT_ETA", "INT_NU", "INT_HU"]
 RTOL = 1e-3
 
