@@ -343,12 +343,15 @@ __global__ void k_bwd_pixel(KParams p, const float* coef, float* gimg) {
         if (e0 != 0.f || e1 != 0.f) {  // edge statistics: face-neighbour test on the mask
           bool edge = x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1;
           if (NDIM == 3) edge = edge || z == 0 || z == p.nz - 1;
-          if (!edge)
-            edge = __ldg(p.mask + i - 1) != L || __ldg(p.mask + i + 1) != L || __ldg(p.mask + i - p.nx) != L ||
-                   __ldg(p.mask + i + p.nx) != L;
-          if (NDIM == 3 && !edge) {
-            const int64_t pl = p.nx * p.ny;
-            edge = __ldg(p.mask + i - pl) != L || __ldg(p.mask + i + pl) != L;
+          if (!edge) {  // all neighbours inside the image: issue the loads together
+            const int l0 = __ldg(p.mask + i - 1), l1 = __ldg(p.mask + i + 1);
+            const int l2 = __ldg(p.mask + i - p.nx), l3 = __ldg(p.mask + i + p.nx);
+            edge = (l0 != L) | (l1 != L) | (l2 != L) | (l3 != L);
+            if (NDIM == 3) {
+              const int64_t pl = p.nx * p.ny;
+              const int l4 = __ldg(p.mask + i - pl), l5 = __ldg(p.mask + i + pl);
+              edge |= (l4 != L) | (l5 != L);
+            }
           }
           if (edge) poly += e0 + e1 * (I - cf[EC0 + 2]);
         }

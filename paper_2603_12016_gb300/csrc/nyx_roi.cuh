@@ -168,9 +168,12 @@ __device__ inline bool edge_pixel(const uint16_t* raster, unsigned c, int pad, i
   const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
   const int z = NDIM == 3 ? (int)(c >> 22) : 0;
   const int ri = ((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad);
-  bool e = raster[ri - 1] == 0xFFFFu || raster[ri + 1] == 0xFFFFu || raster[ri - Wp] == 0xFFFFu ||
-           raster[ri + Wp] == 0xFFFFu;
-  if (NDIM == 3) e = e || raster[ri - plane] == 0xFFFFu || raster[ri + plane] == 0xFFFFu;
+  const unsigned a0 = raster[ri - 1], a1 = raster[ri + 1], a2 = raster[ri - Wp], a3 = raster[ri + Wp];
+  bool e = (a0 == 0xFFFFu) | (a1 == 0xFFFFu) | (a2 == 0xFFFFu) | (a3 == 0xFFFFu);
+  if (NDIM == 3) {
+    const unsigned a4 = raster[ri - plane], a5 = raster[ri + plane];
+    e |= (a4 == 0xFFFFu) | (a5 == 0xFFFFu);
+  }
   return e;
 }
 

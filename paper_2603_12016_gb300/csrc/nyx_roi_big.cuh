@@ -136,11 +136,14 @@ __device__ inline bool big_edge(const KParams& p, const BigBox& bx, int x, int y
   const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
   if (x == 0 || x == bx.W - 1 || y == 0 || y == bx.H - 1) return true;
   if (NDIM == 3 && (z == 0 || z == bx.D - 1)) return true;
-  bool e = __ldg(p.mask + here - 1) != bx.label || __ldg(p.mask + here + 1) != bx.label ||
-           __ldg(p.mask + here - p.nx) != bx.label || __ldg(p.mask + here + p.nx) != bx.label;
+  // every neighbour is inside the box here: issue all loads, then combine
+  const int l0 = __ldg(p.mask + here - 1), l1 = __ldg(p.mask + here + 1);
+  const int l2 = __ldg(p.mask + here - p.nx), l3 = __ldg(p.mask + here + p.nx);
+  bool e = (l0 != bx.label) | (l1 != bx.label) | (l2 != bx.label) | (l3 != bx.label);
   if (NDIM == 3) {
     const int64_t pl = p.nx * p.ny;
-    e = e || __ldg(p.mask + here - pl) != bx.label || __ldg(p.mask + here + pl) != bx.label;
+    const int l4 = __ldg(p.mask + here - pl), l5 = __ldg(p.mask + here + pl);
+    e |= (l4 != bx.label) | (l5 != bx.label);
   }
   return e;
 }
