@@ -251,6 +251,26 @@ __device__ inline void block_sum_i64(long long (&v)[NV], double* scratch_d, long
   __syncthreads();
 }
 
+// Block minimum and maximum of two unsigned values; results in mn / mx of
+// every thread.
+template <class C>
+__device__ inline void block_minmax_u32(unsigned& mn, unsigned& mx, double* scratch_d) {
+  unsigned* scratch = (unsigned*)scratch_d;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  if (lane == 0) {
+    scratch[2 * warp] = mn;
+    scratch[2 * warp + 1] = mx;
+  }
+  __syncthreads();
+  for (int w = 0; w < C::NW; ++w) {
+    mn = min(mn, scratch[2 * w]);
+    mx = max(mx, scratch[2 * w + 1]);
+  }
+  __syncthreads();
+}
+
 template <class C>
 __device__ inline unsigned long long block_max_u64(unsigned long long v, double* scratch_d) {
   unsigned long long* scratch = (unsigned long long*)scratch_d;
@@ -915,7 +935,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
   __shared__ double s_sd[4];
   __shared__ long long s_i64[GN + 4];  // pass-1 sums, then the GLCM sums of an offset
   __shared__ unsigned s_bnd[4];
-  __shared__ A s_pa[10];  // per-ROI scalars: mean (hi, lo), centroids, sums
+  __shared__ A s_pa[12];  // per-ROI scalars: mean (hi, lo), centroids, sums, edge mean
   __shared__ unsigned s_ncell, s_npair;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1087,11 +1107,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     }
 
     // ---- pass 1: exact sums (integers) --------------------------------------
+    // Edge intensity statistics (Table S1 rows 3-7, Table S5) ride along: an
+    // edge pixel has a face neighbour (4 in 2D, 6 in 3D) outside the ROI, and
+    // in the padded raster every cell that is not one of the ROI's pixels
+    // (another label, background, beyond the image) holds the sentinel.
     const int ibias = std::is_same<T, int16_t>::value ? 32768 : 0;
+    const bool do_edge = (need & NEED_EDGE) != 0;
+    const int plane = Wp * Hp;
+    unsigned emn = 0xFFFFFFFFu, emx = 0;  // edge codes (block-reduced below)
     {
-      // [0] sum I, [1] sum x I, [2] sum y I, [3] sum z I, [4] sum x, [5] sum y, [6] sum z, [7] sum I^2
-      long long s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      A fs[5] = {0, 0, 0, 0, 0};  // float images: sum I, x I, y I, z I, I^2
+      // [0] sum I, [1] sum x I, [2] sum y I, [3] sum z I, [4] sum x, [5] sum y, [6] sum z, [7] sum I^2,
+      // [8] edge count, [9] edge sum d, [10] edge sum d^2 with d = code - vmin (exact for integer images)
+      long long s[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      A fs[6] = {0, 0, 0, 0, 0, 0};  // float images: sum I, x I, y I, z I, I^2, edge sum (I - min)
       for (int i = tid; i < n; i += C::NT) {
         const unsigned c = pc[i];
         const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
@@ -1100,6 +1128,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         s[4] += x;
         s[5] += y;
         s[6] += z;
+        const bool edge = do_edge && edge_pixel<NDIM>(raster, c, pad, Wp, Hp, plane);
+        if (edge) {
+          s[8] += 1;
+          emn = min(emn, pv[i]);
+          emx = max(emx, pv[i]);
+        }
         if (Enc<T>::INTEGER) {
           const int v = (int)pv[i] - ibias;
           s[0] += v;
@@ -1107,6 +1141,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
           s[2] += (long long)y * v;
           s[3] += (long long)z * v;
           s[7] += (long long)v * v;
+          if (edge) {
+            const long long d = (long long)(pv[i] - vmin);
+            s[9] += d;
+            s[10] += d * d;
+          }
         } else {
           const A v = decA<T, A>(pv[i]);
           fs[0] += v;
@@ -1114,10 +1153,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
           fs[2] += (A)y * v;
           fs[3] += (A)z * v;
           fs[4] += v * v;
+          if (edge) fs[5] += v - (A)fmn;
         }
       }
-      block_sum_i64<C, 8>(s, red, s_i64);
-      if (!Enc<T>::INTEGER) block_sum<C, A, 5>(fs, red, s_sc);
+      block_sum_i64<C, 11>(s, red, s_i64);
+      if (!Enc<T>::INTEGER) block_sum<C, A, 6>(fs, red, s_sc);
+      if (do_edge) block_minmax_u32<C>(emn, emx, red);
     }
     // per-ROI scalars by one thread, broadcast through shared memory: mean
     // (as hi + lo so that I - mean keeps its accuracy in FP32), the centre of
@@ -1166,73 +1207,27 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
       s_pa[7] = bz_;
       s_pa[8] = sI;
       s_pa[9] = en;
-    }
-    __syncthreads();
-    const A mu_hi = s_pa[0], mu_lo = s_pa[1];
-    const A cx = s_pa[2], cy = s_pa[3], cz = s_pa[4], bx = s_pa[5], by = s_pa[6], bz = s_pa[7];
-    const A sumI = s_pa[8], energy = s_pa[9];
-    const bool wvalid = sumI != 0;
-
-    // ---- edge intensity statistics (Table S1 rows 3-7, Table S5) ------------
-    // An edge pixel has a face neighbour (4 in 2D, 6 in 3D) outside the ROI:
-    // in the padded raster every cell that is not one of the ROI's pixels
-    // (another label, background, beyond the image) holds the sentinel.
-    if (need & NEED_EDGE) {
-      const int plane = Wp * Hp;
-      // count, sum d, sum d^2 with d = code - vmin (exact for integer images)
-      long long es[3] = {0, 0, 0};
-      A ef[1] = {0};  // float images: sum of (x - min)
-      unsigned emn = 0xFFFFFFFFu, emx = 0;
-      for (int i = tid; i < n; i += C::NT) {
-        if (!edge_pixel<NDIM>(raster, pc[i], pad, Wp, Hp, plane)) continue;
-        const unsigned e = pv[i];
-        es[0] += 1;
-        emn = min(emn, e);
-        emx = max(emx, e);
-        if (Enc<T>::INTEGER) {
-          const long long d = (long long)(e - vmin);
-          es[1] += d;
-          es[2] += d * d;
-        } else {
-          ef[0] += decA<T, A>(e) - (A)fmn;
-        }
-      }
-      block_sum_i64<C, 3>(es, red, s_i64);
-      if (!Enc<T>::INTEGER) block_sum<C, A, 1>(ef, red, s_sc + 12);
-      const unsigned bmx = (unsigned)block_max_u64<C>(emx, red);
-      const unsigned bmn = 0xFFFFFFFFu - (unsigned)block_max_u64<C>(0xFFFFFFFFu - emn, red);
-      const long long ne = s_i64[0];  // >= 1: a finite ROI has an edge pixel
-      A emean, estd;
-      if (Enc<T>::INTEGER) {
-        const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
-        const long long s1 = s_i64[1];
-        const __int128 num = (__int128)ne * s_i64[2] - (__int128)s1 * s1;  // n^2 var_biased, exact
-        emean = (A)(s1 + ne * ((long long)vmin - bias)) / (A)ne;
-        estd = ne > 1 ? asqrt(i128A<A>(num) / ((A)ne * (A)(ne - 1))) : (A)0;
-        if (tid == 0) put(p, row, Q_EDGE + E_II, i2d(s1 + ne * ((long long)vmin - bias)));
-      } else {
-        emean = (A)fmn + s_sc[12] / (A)ne;
-        A ev[1] = {0};
-        for (int i = tid; i < n; i += C::NT) {
-          if (!edge_pixel<NDIM>(raster, pc[i], pad, Wp, Hp, plane)) continue;
-          const A d = decA<T, A>(pv[i]) - emean;
-          ev[0] += d * d;
-        }
-        block_sum<C, A, 1>(ev, red, s_sc + 13);
-        estd = ne > 1 ? asqrt(s_sc[13] / (A)(ne - 1)) : (A)0;
-        if (tid == 0) putA(p, row, Q_EDGE + E_II, (A)fmn * (A)ne + s_sc[12]);
-      }
-      if (tid == 0) {
+      if (do_edge) {  // edge statistics (the float deviation follows in pass 2)
+        const long long ne = s_i64[8];  // >= 1: a finite ROI has an edge pixel
+        A emean, estd = 0;
         if (Enc<T>::INTEGER) {
           const long long bias = std::is_same<T, int16_t>::value ? 32768 : 0;
-          put(p, row, Q_EDGE + E_MAX, i2d((long long)bmx - bias));
-          put(p, row, Q_EDGE + E_MIN, i2d((long long)bmn - bias));
+          const long long s1 = s_i64[9], sumx = s1 + ne * ((long long)vmin - bias);
+          const __int128 num = (__int128)ne * s_i64[10] - (__int128)s1 * s1;  // n^2 var_biased, exact
+          emean = (A)sumx / (A)ne;
+          estd = ne > 1 ? asqrt(i128A<A>(num) / ((A)ne * (A)(ne - 1))) : (A)0;
+          put(p, row, Q_EDGE + E_II, i2d(sumx));
+          put(p, row, Q_EDGE + E_MAX, i2d((long long)emx - bias));
+          put(p, row, Q_EDGE + E_MIN, i2d((long long)emn - bias));
+          putA(p, row, Q_EDGE + E_STD, estd);
         } else {
-          put(p, row, Q_EDGE + E_MAX, f2d(Enc<T>::decf(bmx)));
-          put(p, row, Q_EDGE + E_MIN, f2d(Enc<T>::decf(bmn)));
+          emean = (A)fmn + s_sc[5] / (A)ne;
+          putA(p, row, Q_EDGE + E_II, (A)fmn * (A)ne + s_sc[5]);
+          put(p, row, Q_EDGE + E_MAX, f2d(Enc<T>::decf(emx)));
+          put(p, row, Q_EDGE + E_MIN, f2d(Enc<T>::decf(emn)));
         }
         putA(p, row, Q_EDGE + E_MEAN, emean);
-        putA(p, row, Q_EDGE + E_STD, estd);
+        s_pa[10] = emean;
         if (need & NEED_SAVE) {
           double* sv = p.saved + (size_t)item * SV_WORDS;
           sv[SV_EMEAN] = to_d(emean);
@@ -1241,6 +1236,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         }
       }
     }
+    __syncthreads();
+    const A mu_hi = s_pa[0], mu_lo = s_pa[1];
+    const A cx = s_pa[2], cy = s_pa[3], cz = s_pa[4], bx = s_pa[5], by = s_pa[6], bz = s_pa[7];
+    const A sumI = s_pa[8], energy = s_pa[9];
+    const bool wvalid = sumI != 0;
 
     // ---- pass 2: centred sums (one loop per feature group keeps the live
     // accumulators few) -------------------------------------------------------
@@ -1248,10 +1248,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     A* res_st = res;            // [8]  statistics
     A* res_mi = res + 8;        // [NM] intensity-weighted moments
     A* res_mb = res + 8 + NM;   // [NM] binary moments
-    if (need & (NEED_STATS | NEED_SAVE)) {
-      A acc[8];
+    // float images add the squared deviations of the edge pixels from their
+    // mean as a ninth sum
+    constexpr int NP2 = Enc<T>::INTEGER ? 8 : 9;
+    const bool edge_p2 = !Enc<T>::INTEGER && do_edge;
+    if ((need & (NEED_STATS | NEED_SAVE)) || edge_p2) {
+      const A emean = s_pa[10];
+      A acc[NP2];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) acc[i] = 0;
+      for (int i = 0; i < NP2; ++i) acc[i] = 0;
 #pragma unroll 1
       for (int i = tid; i < n; i += C::NT) {
         const A v = Enc<T>::INTEGER ? (A)((int)pv[i] - ibias) : decA<T, A>(pv[i]);
@@ -1265,8 +1270,22 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         acc[5] += d3 * d3;
         acc[6] += d < 0 ? -d : d;
         acc[7] += d > 0 ? (A)1 : (d < 0 ? (A)-1 : (A)0);
+        if constexpr (NP2 == 9)
+          if (edge_p2 && edge_pixel<NDIM>(raster, pc[i], pad, Wp, Hp, plane)) acc[8] += (v - emean) * (v - emean);
       }
-      block_sum<C, A, 8>(acc, red, res_st);
+      if constexpr (NP2 == 8) {
+        block_sum<C, A, 8>(acc, red, res_st);
+      } else {
+        block_sum<C, A, 9>(acc, red, s_sc + 4);  // s_sc[4..12]
+        if (tid < 8) res_st[tid] = s_sc[4 + tid];
+        if (edge_p2 && tid == 0) {
+          const long long ne = s_i64[8];
+          const A estd = ne > 1 ? asqrt(s_sc[12] / (A)(ne - 1)) : (A)0;
+          putA(p, row, Q_EDGE + E_STD, estd);
+          if (need & NEED_SAVE) p.saved[(size_t)item * SV_WORDS + SV_ESTD] = to_d(estd);
+        }
+        __syncthreads();
+      }
     }
 #pragma unroll 1
     for (int w = 0; w < 2; ++w) {
