@@ -243,6 +243,35 @@ def cpu_baseline(w, budget_s: float):
             "seconds": dt}
 
 
+def run_soft_sweep(args) -> int:
+    """GLCM soft-feature grid: compute time over grey depth (Eq. 2) x nested
+    distance sets (Eq. 3), checked for the ordering of Eq. 5, and the Eq. 8
+    separability ratio of every GLCM feature over the same grid on labelled
+    synthetic texture classes."""
+    import torch
+
+    from paper_2603_12016_gb300 import softgrid
+    from paper_2603_12016_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    levels = [16, 32, 64, 128, 256]
+    dist_sets = [[1], [1, 2], [1, 2, 3], [1, 2, 3, 4]]
+    w = W.config("nuclei2d")
+    t = softgrid.timing_grid(w, levels, dist_sets, steps=max(args.steps // 10, 10), warmup=args.warmup)
+    mono = softgrid.monotone_report(t)
+    tw = W.texture_classes_2d()
+    sep = softgrid.separability_grid(tw, tw.meta["classes"], levels, dist_sets)
+    top = sorted(sep["best_point"].items(), key=lambda kv: -kv[1]["ratio"])[:5]
+    print(json.dumps({
+        "metric": "GLCM soft-feature grid (Eqs. 2-5) and Eq. 8 separability", "unit": "ms",
+        "workload": w.name, "features": "GLCM only", "levels": levels, "dist_sets": dist_sets,
+        "ms": [[round(x, 4) for x in row] for row in t.tolist()],
+        "monotone": {"steps": mono["steps"], "holds": mono["holds"], "violations": mono["violations"]},
+        "separability_workload": tw.name, "top_features": [{"feature": f, **v} for f, v in top],
+        "best_feature_by_point": sep["best_feature"]}))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,10 +287,15 @@ def main() -> int:
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default class limits")
     ap.add_argument("--class-limits", default=None, help="warp,small,medium pixel limits instead of autotuning")
+    ap.add_argument("--sweep", default=None, choices=["soft"],
+                    help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
+                         "separability grid on labelled texture classes (one JSON line, not a bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep == "soft":
+        return run_soft_sweep(args)
 
     import numpy as np
     import torch

@@ -141,6 +141,56 @@ def nuclei_2d(size: int = 2048, n_roi: int = 4000, seed: int = 1002, ng: int = 2
                     params=dict(glcm_levels=ng, dists=tuple(dists), hist_bins=256), meta=_meta(mask))
 
 
+def texture_classes_2d(size: int = 1024, n_roi: int = 600, n_classes: int = 3, seed: int = 1006, ng: int = 64,
+                       dists=(1,)) -> Workload:
+    """Labelled texture classes for the separability ratio of Eq. 8: uint16
+    ellipses (log-uniform semi-axes in [8, 24]) on a Gamma(2, 100)
+    background.  Every ROI draws a class c in [0, n_classes) and a brightness
+    ~ lognormal(mu=7.5, sigma=0.3) shared by all classes; its texture is
+    Gaussian noise of 15% of the brightness smoothed with sigma = c (c = 0:
+    unsmoothed), so the classes differ in texture coarseness, not in level.
+    meta["classes"][label] is the class of each label (-1 for none)."""
+    from scipy.ndimage import gaussian_filter
+
+    rng = _rng(seed)
+    img = rng.gamma(2.0, 100.0, size=(size, size))
+    mask = np.zeros((size, size), dtype=np.int32)
+    lo, hi = math.log(8.0), math.log(24.0)
+    a = np.exp(rng.uniform(lo, hi, n_roi))
+    b = np.exp(rng.uniform(lo, hi, n_roi))
+    th = rng.uniform(0, math.pi, n_roi)
+    cy = rng.uniform(0, size, n_roi)
+    cx = rng.uniform(0, size, n_roi)
+    bright = rng.lognormal(7.5, 0.3, n_roi)
+    cls = rng.integers(0, n_classes, n_roi)
+    labels = rng.permutation(n_roi).astype(np.int32) + 1
+    fields = []
+    for c in range(n_classes):
+        f = rng.normal(size=(size, size))
+        if c > 0:
+            f = gaussian_filter(f, sigma=float(c))
+            f /= f.std()
+        fields.append(f)
+
+    def val(k, n, cur):
+        return cur * 0 + bright[k]
+
+    _paint_ellipses(mask, img, cy, cx, a, b, th, labels, val)
+    classes = np.full(n_roi + 1, -1, dtype=np.int64)
+    classes[labels] = cls
+    inroi = mask > 0
+    cmap = classes[mask]
+    for c in range(n_classes):
+        sel = inroi & (cmap == c)
+        img[sel] = img[sel] * (1.0 + 0.15 * fields[c][sel])
+    mask = _relabel_drop_small(mask, 60)
+    img = np.clip(np.rint(img), 0, 65535).astype(np.uint16)
+    meta = _meta(mask)
+    meta["classes"] = classes
+    return Workload(f"textures2d_{size}_u16_{n_roi}roi_{n_classes}cls", img, mask, 2,
+                    params=dict(glcm_levels=ng, dists=tuple(dists), hist_bins=256), meta=meta)
+
+
 # ---------------------------------------------------------------------------
 # 3D CT-like volume: smoothed random field + ellipsoids
 
