@@ -243,6 +243,60 @@ def cpu_baseline(w, budget_s: float):
             "seconds": dt}
 
 
+def _oracle_ms(w, budget_s: float):
+    """CPU oracle time for all of w's ROIs, extrapolated from a bounded
+    sample of them (all host cores); the sample size is returned too."""
+    import numpy as np
+    import oracle
+
+    cores = os.cpu_count() or 1
+    labels = np.unique(w.mask[w.mask > 0])
+    prm = w.params
+    n = min(8, len(labels))
+    while True:
+        keys = [oracle.roi_key(0, int(l)) for l in labels[:n]]
+        t0 = time.perf_counter()
+        oracle.extract(w.image, w.mask, w.ndim, ng=prm["glcm_levels"], dists=prm["dists"],
+                       hist_bins=prm["hist_bins"], rois=keys, threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n == len(labels):
+            break
+        n = min(len(labels), int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3)))))
+    return 1e3 * dt * len(labels) / n, n, cores
+
+
+def run_scalability_sweep(args) -> int:
+    """Time over ROI size x ROI count (the study of Fig. 3f): GPU with inputs
+    in HBM, GPU end to end from pinned host buffers, and the CPU oracle on a
+    bounded sample scaled to all ROIs; then the per-group cost structure of
+    an image of 100 ROIs of 100,000 px (Fig. 3g)."""
+    import torch
+
+    from paper_2603_12016_gb300 import scalability as S
+    from paper_2603_12016_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    rows = []
+    for n_roi in (10, 100, 1000):
+        for px in (100, 500, 1000, 5000, 20000, 100000):
+            w = W.scalability_2d(px, n_roi)
+            dev = S.time_device(w, steps=10)
+            e2e = S.time_end_to_end(w)
+            ora, ns, cores = _oracle_ms(w, budget_s=2.0)
+            rows.append({"roi_px": px, "n_roi": w.meta["n_roi"], "image": list(w.image.shape),
+                         "gpu_ms": round(dev, 4), "gpu_e2e_ms": round(e2e["ms"], 4), "h2d_bytes": e2e["h2d_bytes"],
+                         "oracle_ms": round(ora, 2), "oracle_sample_rois": ns, "oracle_cores": cores})
+    w = W.scalability_2d(100000, 100)
+    groups = S.group_costs(w)
+    ora, ns, cores = _oracle_ms(w, budget_s=6.0)
+    print(json.dumps({"metric": "scalability over ROI size x count; feature-group cost of 100 x 100,000 px",
+                      "unit": "ms", "features": "all", "rows": rows,
+                      "cost_100x100k": {"gpu_ms": {k: round(v, 4) for k, v in groups.items()},
+                                        "oracle_ms": round(ora, 1), "oracle_sample_rois": ns,
+                                        "oracle_cores": cores}}))
+    return 0
+
+
 def run_soft_sweep(args) -> int:
     """GLCM soft-feature grid: compute time over grey depth (Eq. 2) x nested
     distance sets (Eq. 3), checked for the ordering of Eq. 5, and the Eq. 8
@@ -287,15 +341,19 @@ def main() -> int:
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default class limits")
     ap.add_argument("--class-limits", default=None, help="warp,small,medium pixel limits instead of autotuning")
-    ap.add_argument("--sweep", default=None, choices=["soft"],
+    ap.add_argument("--sweep", default=None, choices=["soft", "scalability"],
                     help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
-                         "separability grid on labelled texture classes (one JSON line, not a bench line)")
+                         "separability grid on labelled texture classes; scalability: time over ROI size x ROI "
+                         "count (GPU device, GPU end to end, CPU oracle) and the feature-group cost of an image "
+                         "of 100 ROIs of 100,000 px (one JSON line each, not bench lines)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     if args.sweep == "soft":
         return run_soft_sweep(args)
+    if args.sweep == "scalability":
+        return run_scalability_sweep(args)
 
     import numpy as np
     import torch

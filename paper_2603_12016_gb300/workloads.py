@@ -191,6 +191,37 @@ def texture_classes_2d(size: int = 1024, n_roi: int = 600, n_classes: int = 3, s
                     params=dict(glcm_levels=ng, dists=tuple(dists), hist_bins=256), meta=meta)
 
 
+def scalability_2d(roi_px: int, n_roi: int, seed: int = 1007, ng: int = 64, dists=(1,)) -> Workload:
+    """n_roi disks of about roi_px pixels each on a jittered square grid
+    (cell side 1.5 diameters, so disks never touch), uint16: Gamma(2, 300)
+    background, per-disk brightness ~ lognormal(mu=8, sigma=0.6) with +-20%
+    per-pixel texture.  Image side = grid cells x cell side."""
+    rng = _rng(seed)
+    r = math.sqrt(roi_px / math.pi)
+    cell = int(math.ceil(3.0 * r)) + 2
+    g = int(math.ceil(math.sqrt(n_roi)))
+    size = g * cell
+    img = rng.gamma(2.0, 300.0, size=(size, size))
+    mask = np.zeros((size, size), dtype=np.int32)
+    slots = rng.permutation(g * g)[:n_roi]
+    bright = rng.lognormal(8.0, 0.6, n_roi)
+    span = max(cell - 2 * r - 2, 0.0)
+    for k, sl in enumerate(slots):
+        cy = (sl // g) * cell + r + 1 + rng.uniform(0, span)
+        cx = (sl % g) * cell + r + 1 + rng.uniform(0, span)
+        y0, y1 = max(0, int(cy - r) - 1), min(size, int(cy + r) + 2)
+        x0, x1 = max(0, int(cx - r) - 1), min(size, int(cx + r) + 2)
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        inside = (yy - cy) ** 2 + (xx - cx) ** 2 <= r * r
+        mask[y0:y1, x0:x1][inside] = k + 1
+        img[y0:y1, x0:x1][inside] += bright[k]
+    inroi = mask > 0
+    img[inroi] *= rng.uniform(0.8, 1.2, size=int(inroi.sum()))
+    img = np.clip(np.rint(img), 0, 65535).astype(np.uint16)
+    return Workload(f"disks2d_{roi_px}px_x{n_roi}", img, mask, 2,
+                    params=dict(glcm_levels=ng, dists=tuple(dists), hist_bins=256), meta=_meta(mask))
+
+
 # ---------------------------------------------------------------------------
 # 3D CT-like volume: smoothed random field + ellipsoids
 
