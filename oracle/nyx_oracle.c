@@ -230,6 +230,9 @@ typedef struct {
   /* Table S1 rows 3-7 / Table S5 IIE, Max IE, Min IE, Mean IE, std IE:
    * intensity statistics over the ROI's edge pixels (reading c14) */
   double edge_ii, edge_max, edge_min, edge_mean, edge_std;
+  /* Table S3 rows 246-250 (NGTDM): coarseness, contrast, busyness,
+   * complexity, strength (reading c17) */
+  double ngtdm[5];
 } feat_t;
 
 static const char* GLCM_NAMES[ORC_NGLCM] = {
@@ -395,6 +398,10 @@ static void emit_all(const orc_cfg* c, const feat_t* f, emitter* e) {
         else emit(e, f->glcm_off[di][o][g], "GLCM_%s_D%d_A%d", GLCM_NAMES[g], c->dist[di], 45 * o);
       }
 
+  if (c->ng > 0) {
+    static const char* NG_NAMES[5] = {"COARSENESS", "CONTRAST", "BUSYNESS", "COMPLEXITY", "STRENGTH"};
+    for (int q = 0; q < 5; ++q) emit(e, f->ngtdm[q], "NGTDM_%s", NG_NAMES[q]);
+  }
   emit(e, f->edge_ii, "EDGE_INTEGRATED_INTENSITY");
   emit(e, f->edge_max, "EDGE_MAX_INTENSITY");
   emit(e, f->edge_min, "EDGE_MIN_INTENSITY");
@@ -822,6 +829,73 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
       for (int g = 0; g < ORC_NGLCM; ++g) f->glcm_mean[di][g] = used ? acc[g] / used : NAN;
     }
     free(P);
+  }
+
+  /* ---- NGTDM, Table S3 rows 246-250 (reading c17): for every ROI pixel
+   * with grey level L (1-based GLCM bin) and at least one neighbour in the
+   * ROI among its 8 (2D) / 26 (3D) Chebyshev-1 neighbours, the mean level
+   * A of those neighbours; n_L counts such pixels and s_L sums |L - A|.
+   * With p_L = n_L / N (N = number of such pixels) and the sums over the
+   * levels with p_L > 0: coarseness 1 / sum p s; contrast
+   * [sum_i sum_j p_i p_j (i-j)^2 / (G (G-1))] [sum s / N] (G levels present);
+   * busyness sum p s / sum_i sum_j |i p_i - j p_j|; complexity
+   * (1/N) sum_i sum_j |i - j| (p_i s_i + p_j s_j) / (p_i + p_j); strength
+   * sum_i sum_j (p_i + p_j) (i-j)^2 / sum s. ---- */
+  if (c->ng > 0) {
+    double* nL = (double*)calloc((size_t)c->ng, sizeof(double));
+    double* sL = (double*)calloc((size_t)c->ng, sizeof(double));
+    for (int64_t k = 0; k < N; ++k) {
+      const int L = bin_of(c, I[k], mn, mx, c->ng) + 1;
+      double sum = 0;
+      int cnt = 0;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            if (!d3 && dz != 0) continue;
+            const int64_t x = X[k][0] + dx, y = X[k][1] + dy, z = X[k][2] + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) continue;
+            const int64_t nl = (z * c->ny + y) * c->nx + x;
+            if (mask[base + nl] != r->label) continue;
+            sum += bin_of(c, pixel(c, img, base + nl), mn, mx, c->ng) + 1;
+            ++cnt;
+          }
+      if (cnt == 0) continue;
+      nL[L - 1] += 1;
+      sL[L - 1] += fabs(L - sum / cnt);
+    }
+    double Nv = 0;
+    for (int i = 0; i < c->ng; ++i) Nv += nL[i];
+    for (int q = 0; q < 5; ++q) f->ngtdm[q] = NAN;
+    if (Nv > 0) {
+      double ps = 0, ssum = 0, G = 0;
+      for (int i = 0; i < c->ng; ++i) {
+        if (nL[i] == 0) continue;
+        ps += nL[i] / Nv * sL[i];
+        ssum += sL[i];
+        G += 1;
+      }
+      double pair_c = 0, busy_den = 0, cplx = 0, str_num = 0;
+      for (int i = 0; i < c->ng; ++i) {
+        if (nL[i] == 0) continue;
+        const double pi = nL[i] / Nv, li = i + 1;
+        for (int j = 0; j < c->ng; ++j) {
+          if (nL[j] == 0) continue;
+          const double pj = nL[j] / Nv, lj = j + 1;
+          pair_c += pi * pj * (li - lj) * (li - lj);
+          busy_den += fabs(li * pi - lj * pj);
+          cplx += fabs(li - lj) * (pi * sL[i] + pj * sL[j]) / (pi + pj);
+          str_num += (pi + pj) * (li - lj) * (li - lj);
+        }
+      }
+      f->ngtdm[0] = ps > 0 ? 1.0 / ps : NAN;
+      f->ngtdm[1] = G > 1 ? pair_c / (G * (G - 1)) * (ssum / Nv) : 0.0;
+      f->ngtdm[2] = busy_den > 0 ? ps / busy_den : 0.0;
+      f->ngtdm[3] = cplx / Nv;
+      f->ngtdm[4] = ssum > 0 ? str_num / ssum : 0.0;
+    }
+    free(nL);
+    free(sL);
   }
   free(I);
   free(X);

@@ -636,3 +636,96 @@ def test_gradient_edge_features_closed_forms(orc):
     g = orc.grad(img, mask, 2, {"EDGE_STDDEV_INTENSITY": np.array([1.0])})
     assert np.allclose(g[ring], (v - v.mean()) / ((ne - 1) * v.std(ddof=1)), rtol=1e-12)
     assert np.all(g[~ring] == 0)
+
+
+# --------------------------------------------------------------------------
+# NGTDM (Table S3 rows 246-250): an independent NumPy construction of the
+# neighbourhood means (scipy.ndimage correlation with the 8- / 26-neighbour
+# kernel) and of the five features with explicit pair arrays.
+
+def _ngtdm_ref(img, mask, label, ng):
+    import scipy.ndimage as ndi
+
+    m = mask == label
+    v = img[m].astype(np.int64)
+    mn, mx = v.min(), v.max()
+    lev = np.zeros(img.shape, dtype=np.int64)
+    if mx > mn:
+        lev[m] = np.minimum(ng * (img[m].astype(np.int64) - mn) // (mx - mn), ng - 1) + 1
+    else:
+        lev[m] = 1
+    k = np.ones((3,) * img.ndim)
+    k[(1,) * img.ndim] = 0
+    s_nb = ndi.correlate(lev.astype(np.float64), k, mode="constant", cval=0.0)
+    c_nb = ndi.correlate(m.astype(np.float64), k, mode="constant", cval=0.0)
+    valid = m & (c_nb > 0)
+    if not valid.any():
+        return [np.nan] * 5
+    L = lev[valid]
+    A = s_nb[valid] / c_nb[valid]
+    n = np.bincount(L, minlength=ng + 1)[1:].astype(np.float64)
+    s = np.bincount(L, weights=np.abs(L - A), minlength=ng + 1)[1:]
+    N = n.sum()
+    z = n > 0
+    p, sz, li = n[z] / N, s[z], np.arange(1, ng + 1, dtype=np.float64)[z]
+    G = z.sum()
+    ps = np.sum(p * sz)
+    dl = li[:, None] - li[None, :]
+    coarse = 1.0 / ps if ps > 0 else np.nan
+    contrast = np.sum(p[:, None] * p[None, :] * dl ** 2) / (G * (G - 1)) * s.sum() / N if G > 1 else 0.0
+    den = np.sum(np.abs((li * p)[:, None] - (li * p)[None, :]))
+    busy = ps / den if den > 0 else 0.0
+    cplx = np.sum(np.abs(dl) * ((p * sz)[:, None] + (p * sz)[None, :]) / (p[:, None] + p[None, :])) / N
+    strength = np.sum((p[:, None] + p[None, :]) * dl ** 2) / s.sum() if s.sum() > 0 else 0.0
+    return [coarse, contrast, busy, cplx, strength]
+
+
+NGTDM_COLS = ["NGTDM_COARSENESS", "NGTDM_CONTRAST", "NGTDM_BUSYNESS", "NGTDM_COMPLEXITY", "NGTDM_STRENGTH"]
+
+
+@pytest.mark.parametrize("ndim,seed,ng", [(2, 1, 8), (2, 2, 32), (3, 3, 16)])
+def test_ngtdm_vs_numpy_construction(orc, ndim, seed, ng):
+    rng = np.random.default_rng(50 + seed)
+    shape = (30, 33) if ndim == 2 else (10, 12, 13)
+    img = rng.integers(0, 4000, size=shape).astype(np.uint16)
+    mask = np.zeros(shape, dtype=np.int32)
+    grids = np.meshgrid(*[np.arange(sh) for sh in shape], indexing="ij")
+    for lab in range(1, 6):  # touching blobs, some cut by the border
+        c = [rng.uniform(-1, sh + 1) for sh in shape]
+        r = rng.uniform(2.5, 7.0)
+        mask[sum((g - ci) ** 2 for g, ci in zip(grids, c)) <= r * r] = lab
+    t = orc.extract(img, mask, ndim, ng=ng)
+    for row, lab in enumerate(t["LABEL"].astype(int)):
+        ref = _ngtdm_ref(img, mask, lab, ng)
+        for name, v in zip(NGTDM_COLS, ref):
+            if np.isnan(v):
+                assert np.isnan(t[name][row]), (lab, name)
+            else:
+                assert t[name][row] == pytest.approx(v, rel=1e-12, abs=1e-12), (lab, name)
+
+
+def test_ngtdm_degenerate_cases(orc):
+    img = np.full((6, 7), 100, dtype=np.uint16)
+    img[0, 0] = 7
+    mask = np.zeros((6, 7), dtype=np.int32)
+    mask[0, 0] = 1           # single pixel: no neighbour, every NGTDM feature NaN
+    mask[2:5, 2:6] = 2       # constant ROI: one grey level, no difference
+    t = orc.extract(img, mask, 2, ng=8)
+    assert all(np.isnan(t[c][0]) for c in NGTDM_COLS)
+    assert np.isnan(t["NGTDM_COARSENESS"][1])
+    assert t["NGTDM_CONTRAST"][1] == 0 and t["NGTDM_BUSYNESS"][1] == 0
+    assert t["NGTDM_COMPLEXITY"][1] == 0 and t["NGTDM_STRENGTH"][1] == 0
+
+
+def test_ngtdm_two_level_stripes_closed_form(orc):
+    """Vertical stripes of width 1 alternating levels 1 and 2 in a 4 x 6 ROI
+    filling the image (Ng = 2, min 0, max 1): every pixel is valid, and an
+    interior pixel sees 6 neighbours of the other level and 2 of its own, so
+    |L - A| = 3/4 there.  Checked against the NumPy construction."""
+    img = np.tile(np.array([0, 1], dtype=np.uint16), (4, 3))
+    mask = np.ones(img.shape, dtype=np.int32)
+    t = _single(orc, img, mask, ng=2)
+    ref = _ngtdm_ref(img, mask, 1, 2)
+    for name, v in zip(NGTDM_COLS, ref):
+        assert t[name] == pytest.approx(v, rel=1e-13)
+    assert t["NGTDM_CONTRAST"] > 0 and t["NGTDM_BUSYNESS"] > 0
