@@ -529,11 +529,12 @@ def main() -> int:
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, 20.0)
-    # begin, scan, key sort, setup, 3 block classes, reset; multi-block class:
-    # zero, pass 1, pass 2, sorted order statistics (+ GLCM); statistics
-    # final (+ GLCM features)
+    # begin, scan, key sort, setup, the block classes whose pixel limit is
+    # above 0, reset; multi-block class: zero, pass 1, pass 2, sorted order
+    # statistics (+ GLCM, + NGTDM); statistics final (+ GLCM features)
     glcm = w.params["glcm_levels"] > 0
-    launches_per_step = 8 + 4 + (1 if glcm else 0) + 1 + (1 if glcm else 0)
+    n_cls = sum(1 for v in (limits or (256, 1024, 8192)) if v > 0)
+    launches_per_step = 5 + n_cls + 4 + (2 if glcm else 0) + 1 + (1 if glcm else 0)
     if bwd:  # begin, scan, key sort, setup, coefficients, per-pixel gradient, reset
         launches_per_step += 7
     line = {

@@ -127,7 +127,10 @@ nyx_status nyx_column_name(const nyx_plan* plan, int col, char* buf, size_t cap)
  * EDGE_MIN_INTENSITY, EDGE_MEAN_INTENSITY, EDGE_STDDEV_INTENSITY over the
  * ROI's edge pixels, those with a face neighbour (4 in 2D, 6 in 3D) outside
  * the ROI or the image; the deviation is the unbiased one (0 for a single
- * edge pixel). */
+ * edge pixel); 86..90 NGTDM features (Table S3 rows 246-250, need
+ * glcm_levels > 0): NGTDM_COARSENESS, NGTDM_CONTRAST, NGTDM_BUSYNESS,
+ * NGTDM_COMPLEXITY, NGTDM_STRENGTH on the GLCM grey levels, over the pixels
+ * with at least one ROI pixel among their 8 (2D) / 26 (3D) neighbours. */
 int nyx_feature_id(const char* name);
 
 /* Run the label scan only and return the number of ROIs (distinct

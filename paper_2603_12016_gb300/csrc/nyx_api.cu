@@ -38,7 +38,7 @@ using namespace nyx;
 
 // ---------------------------------------------------------------------------
 // feature registry: ids 0..40 statistics, 41..50 moment families, 51..80 GLCM,
-// 81..85 edge intensity statistics
+// 81..85 edge intensity statistics, 86..90 NGTDM
 
 namespace {
 
@@ -58,8 +58,11 @@ const char* EDGE_NAMES[N_EDGE] = {"EDGE_INTEGRATED_INTENSITY", "EDGE_MAX_INTENSI
                                   "EDGE_MEAN_INTENSITY", "EDGE_STDDEV_INTENSITY"};
 constexpr int FID_MOM = N_STATS;         // 41
 constexpr int FID_GLCM = N_STATS + 10;   // 51
+const char* NGTDM_NAMES[N_NGTDM] = {"NGTDM_COARSENESS", "NGTDM_CONTRAST", "NGTDM_BUSYNESS", "NGTDM_COMPLEXITY",
+                                    "NGTDM_STRENGTH"};
 constexpr int FID_EDGE = FID_GLCM + NGLCM;  // 81
-constexpr int N_FID = FID_EDGE + N_EDGE;    // 86
+constexpr int FID_NGTDM = FID_EDGE + N_EDGE;  // 86
+constexpr int N_FID = FID_NGTDM + N_NGTDM;    // 91
 
 bool is_order_stat(int s) {
   return s == S_MEDIAN || s == S_P01 || s == S_P10 || s == S_P25 || s == S_P75 || s == S_P90 || s == S_P99 ||
@@ -220,6 +223,8 @@ int nyx_feature_id(const char* name) {
   }
   for (int e = 0; e < N_EDGE; ++e)
     if (!strcmp(name, EDGE_NAMES[e])) return FID_EDGE + e;
+  for (int q = 0; q < N_NGTDM; ++q)
+    if (!strcmp(name, NGTDM_NAMES[q])) return FID_NGTDM + q;
   return -1;
 }
 
@@ -318,6 +323,9 @@ static void build_columns(nyx_plan* pl) {
   }
   for (int e = 0; e < N_EDGE; ++e)
     if (fbit(p, FID_EDGE + e)) add(Q_EDGE + e, EDGE_NAMES[e]);
+  if (p.glcm_levels > 0)
+    for (int q = 0; q < N_NGTDM; ++q)
+      if (fbit(p, FID_NGTDM + q)) add(Q_NGTDM + q, NGTDM_NAMES[q]);
 }
 
 // GLCM unit directions: 2D angles 0/45/90/135 degrees as (dx,dy) = (1,0),
@@ -442,8 +450,12 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
       if (fbit(p, FID_GLCM + g)) need |= NEED_GLCM;
   for (int e = 0; e < N_EDGE; ++e)
     if (fbit(p, FID_EDGE + e)) need |= NEED_EDGE;
-  // the edge test reads face neighbours from the padded bin raster
-  if ((need & NEED_EDGE) && k.pad < 1) k.pad = 1;
+  if (p.glcm_levels > 0)  // NGTDM grey levels are the GLCM bins
+    for (int q = 0; q < N_NGTDM; ++q)
+      if (fbit(p, FID_NGTDM + q)) need |= NEED_NGTDM;
+  // the edge test and the NGTDM neighbourhood read neighbours from the
+  // padded bin raster
+  if ((need & (NEED_EDGE | NEED_NGTDM)) && k.pad < 1) k.pad = 1;
   k.need = need;
   k.keys = (unsigned long long*)(w + o_keys);
   k.slots = (SlotAcc*)(w + o_slots);

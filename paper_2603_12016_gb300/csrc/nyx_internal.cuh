@@ -102,8 +102,13 @@ enum : int {
   Q_GLCM_O = Q_GLCM_D + MAX_DIST * NGLCM,  // + (di*13 + dir)*30 + g
   Q_EDGE = Q_GLCM_O + MAX_DIST * MAX_DIRS * NGLCM,  // + e (edge intensity statistics)
   N_EDGE = 5,
-  Q_TOTAL = Q_EDGE + N_EDGE
+  Q_NGTDM = Q_EDGE + N_EDGE,          // + k (NGTDM features)
+  N_NGTDM = 5,
+  Q_TOTAL = Q_NGTDM + N_NGTDM
 };
+
+// NGTDM features (Table S3 rows 246-250), index within Q_NGTDM
+enum : int { NT_COARSENESS = 0, NT_CONTRAST, NT_BUSYNESS, NT_COMPLEXITY, NT_STRENGTH };
 
 // edge intensity statistics (Table S1 rows 3-7, Table S5), index within Q_EDGE
 enum : int { E_II = 0, E_MAX, E_MIN, E_MEAN, E_STD };
@@ -136,6 +141,7 @@ enum : unsigned {
   NEED_GLCM = 32u,
   NEED_SAVE = 64u,    // keep per-ROI state for the backward pass
   NEED_EDGE = 128u,   // edge intensity statistics
+  NEED_NGTDM = 256u,  // neighbourhood grey-tone difference matrix
 };
 
 // saved per-ROI state for the backward pass (FP64 words per ROI)
@@ -218,7 +224,7 @@ __host__ __device__ inline unsigned big_units2(unsigned long long c) { return (u
 constexpr int BIG_P1 = 38;   // pass-1 partial per chunk: 9 int64 + 5 doubles + 5 edge words (8 bytes each)
 constexpr int BIG_P2 = 98;   // pass-2 partial per chunk: 48 doubles + the edge squared deviations
 struct BigLayout {
-  unsigned long long ctr, hist, vhist, tri, zero_end, part1, part2, fsort, total;
+  unsigned long long ctr, hist, vhist, tri, ngt, zero_end, part1, part2, fsort, total;
 };
 __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int nsp, unsigned range, unsigned n) {
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
@@ -227,10 +233,11 @@ __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int n
   const bool fsort = (p.need & NEED_ORDER) && range == 0;  // sorted values instead of a value histogram
   BigLayout L;
   unsigned long long o = 0;
-  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [4 + k] offset group k
+  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [2] NGTDM, [4 + k] offset group k
   L.hist = o;     o = (o + ((p.need & NEED_HIST) ? p.hist_bins : 0) + 3) & ~3ull;
   L.vhist = o;    o = (o + range + 3) & ~3ull;
   L.tri = o;      o = (o + (nsp > 1 ? n_off * tri : 0) + 3) & ~3ull;
+  L.ngt = o;      o = (o + ((p.need & NEED_NGTDM) ? 3ull * p.ng : 0) + 3) & ~3ull;  // S[ng] int64, then n[ng] u32
   L.zero_end = o;
   L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
   L.part2 = o;    o += (unsigned long long)nch * BIG_P2;

@@ -711,6 +711,108 @@ __device__ inline void block_sum_glcm(long long (&iv)[GN], double* scratch_d, lo
   if (TRAILING_SYNC) __syncthreads();
 }
 
+// ----------------------------------------------------------------------------
+// NGTDM (Table S3 rows 246-250).  For a pixel of grey level L (1-based bin)
+// whose Chebyshev-1 neighbourhood holds cnt > 0 ROI pixels with level sum
+// `sum`, the term |L - sum / cnt| in units of 2^-32: the FP32 quotient of the
+// two integers is correctly rounded and the power-of-two scaling exact, so
+// the per-level sums do not depend on the order of the atomics.
+__device__ inline unsigned long long ngtdm_term(int L, int sum, int cnt) {
+  const int num = L * cnt - sum;
+  const float q = (float)(num < 0 ? -num : num) / (float)cnt;
+  return __float2ull_rn(q * 4294967296.f);
+}
+
+// The five NGTDM features from the per-level counts nL[0..ng) and sums
+// S[0..ng) (2^-32 units) in shared memory; every thread of the block calls
+// it, thread 0 writes the columns.  lst: shared scratch of ng words.  With
+// p = n / N (N valid pixels), G levels present, mu = sum p L, m = mean of
+// the present levels: coarseness 1 / sum p s; contrast
+// 2 sum p (L - mu)^2 / (G (G - 1)) * sum s / N; busyness sum p s /
+// sum_i sum_j |L_i p_i - L_j p_j|; complexity (1/N) sum_i sum_j |L_i - L_j|
+// (p_i s_i + p_j s_j) / (p_i + p_j); strength 2 (G sum p (L - m)^2 +
+// sum (L - m)^2) / sum s (the double sums over the present levels, written
+// about the means so that they do not cancel).
+template <class C, class A>
+__device__ void ngtdm_features(const KParams& p, double* row, int ng, const unsigned* nL,
+                               const unsigned long long* S, unsigned* lst, double* red, A* sc, long long* s64) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const A nan = anan<A>();
+  const A fx = (A)(1.0 / 4294967296.0);
+  if (warp == 0) {  // levels present, ascending
+    int cnt = 0;
+    for (int b = 0; b < ng; b += 32) {
+      const bool v = b + lane < ng && nL[b + lane] > 0;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, v);
+      if (v) lst[cnt + __popc(bal & lanemask_lt())] = (unsigned)(b + lane);
+      cnt += __popc(bal);
+    }
+    if (lane == 0) s64[0] = cnt;
+  }
+  {
+    long long t[1] = {0};
+    for (int i = tid; i < ng; i += C::NT) t[0] += nL[i];
+    block_sum_i64<C, 1>(t, red, s64 + 1);  // ends with a barrier: lst and s64[0] are visible
+  }
+  const int G = (int)s64[0];
+  const long long Nv = s64[1];
+  if (Nv == 0) {
+    if (tid == 0)
+      for (int q = 0; q < N_NGTDM; ++q) putA(p, row, Q_NGTDM + q, nan);
+    return;
+  }
+  const A invN = (A)1 / (A)Nv;
+  {  // ps = sum p s, ssum = sum s, mu = sum p L, T1 = sum L
+    A v[4] = {0, 0, 0, 0};
+    for (int k = tid; k < G; k += C::NT) {
+      const int i = (int)lst[k];
+      const A pi = (A)nL[i] * invN, si = (A)ll2f((long long)S[i]) * fx, L = (A)(i + 1);
+      v[0] += pi * si;
+      v[1] += si;
+      v[2] += pi * L;
+      v[3] += L;
+    }
+    block_sum<C, A, 4>(v, red, sc);
+  }
+  const A ps = sc[0], ssum = sc[1], mu = sc[2], m = sc[3] / (A)G;
+  {  // centred sums, then the pair sums over i < j (rows paired for balance)
+    A v[5] = {0, 0, 0, 0, 0};
+    for (int k = tid; k < G; k += C::NT) {
+      const int i = (int)lst[k];
+      const A pi = (A)nL[i] * invN, L = (A)(i + 1);
+      v[0] += pi * (L - mu) * (L - mu);
+      v[1] += pi * (L - m) * (L - m);
+      v[2] += (L - m) * (L - m);
+    }
+    for (int a = tid; a < (G + 1) / 2; a += C::NT) {
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int r = h ? G - 1 - a : a;
+        if (h && r == a) break;
+        const int i = (int)lst[r];
+        const A pi = (A)nL[i] * invN, si = (A)ll2f((long long)S[i]) * fx, Li = (A)(i + 1);
+        for (int c = r + 1; c < G; ++c) {
+          const int j = (int)lst[c];
+          const A pj = (A)nL[j] * invN, sj = (A)ll2f((long long)S[j]) * fx, Lj = (A)(j + 1);
+          const A dv = Li * pi - Lj * pj;
+          v[3] += dv < 0 ? -dv : dv;
+          v[4] += (Lj - Li) * (pi * si + pj * sj) / (pi + pj);  // Lj > Li
+        }
+      }
+    }
+    block_sum<C, A, 5>(v, red, sc + 4);
+  }
+  if (tid == 0) {
+    const A V1 = sc[4], V2 = sc[5], V3 = sc[6], bden = 2 * sc[7], cplx = 2 * sc[8];
+    putA(p, row, Q_NGTDM + NT_COARSENESS, ps > 0 ? (A)1 / ps : nan);
+    putA(p, row, Q_NGTDM + NT_CONTRAST, G > 1 ? (A)2 * V1 / ((A)G * (A)(G - 1)) * ssum * invN : (A)0);
+    putA(p, row, Q_NGTDM + NT_BUSYNESS, bden > 0 ? ps / bden : (A)0);
+    putA(p, row, Q_NGTDM + NT_COMPLEXITY, cplx * invN);
+    putA(p, row, Q_NGTDM + NT_STRENGTH, ssum > 0 ? (A)2 * ((A)G * V2 + V3) / ssum : (A)0);
+  }
+  __syncthreads();
+}
+
 // Per (ROI, offset) GLCM accumulator handed from the accumulation kernels to
 // k_glcm_final: the GN integer sums.  An all-zero record (T = 0) marks an
 // offset without pairs.
@@ -943,7 +1045,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
   const int* queue = p.queue + (int64_t)cls * p.max_rois;
   const int64_t per = p.nx * p.ny * p.nz;
   const bool need_glcm = (p.need & NEED_GLCM) != 0;
-  const bool need_raster = (p.need & (NEED_GLCM | NEED_EDGE)) != 0;  // padded raster of the ROI's cells
+  const bool need_ngtdm = (p.need & NEED_NGTDM) != 0;
+  const bool need_raster = (p.need & (NEED_GLCM | NEED_EDGE | NEED_NGTDM)) != 0;  // padded raster of the ROI's cells
   const int pad = need_raster ? p.pad : 0;
   const A nan = anan<A>();
 
@@ -1058,7 +1161,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
               hb = min(s_fd.div((unsigned)p.hist_bins * dv), (unsigned)(p.hist_bins - 1));
             } else {
               const float xv = Enc<T>::decf(e);
-              if (need_glcm) gb = bin_float(xv, fmn, fmx, p.ng);
+              if (need_glcm || need_ngtdm) gb = bin_float(xv, fmn, fmx, p.ng);
               if (need & NEED_HIST) hb = bin_float(xv, fmn, fmx, p.hist_bins);
             }
           }
@@ -1346,6 +1449,60 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
       }
     }
 
+    // the pixel list's coordinates are not needed after the moments: keep
+    // each pixel's padded raster index (low 16 bits; cells <= 16,384) and its
+    // own bin (high 16 bits) there instead of decoding them per neighbour
+    if (need_glcm || need_ngtdm)
+      for (int i = tid; i < n; i += C::NT) {
+        const unsigned c = pc[i];
+        const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
+        const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
+        const int z = NDIM == 3 ? (int)(c >> 22) : 0;
+        const unsigned ci = (unsigned)(((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad));
+        pc[i] = ci | ((unsigned)raster[ci] << 16);
+      }
+
+    // ---- NGTDM (Table S3 rows 246-250) ---------------------------------------
+    // Per pixel the level sum and count of its Chebyshev-1 neighbours in the
+    // ROI (raster cells that are not the sentinel), then n_L and the fixed-
+    // point s_L per level in shared memory.
+    if (need_ngtdm) {
+      const int ng = p.ng;
+      unsigned long long* S = (unsigned long long*)marg;  // [ng] sums of |L - A|, 2^-32 units
+      unsigned* nL = (unsigned*)(S + ng);                  // [ng] valid pixels per level
+      unsigned* lst = nL + ng;                             // [ng] levels present
+      for (int i = tid; i < ng; i += C::NT) {
+        S[i] = 0;
+        nL[i] = 0;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += C::NT) {
+        const unsigned w = pc[i];
+        const int ci = (int)(w & 0xFFFFu);
+        int sum = 0, cnt = 0;
+#pragma unroll
+        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (dx == 0 && dy == 0 && dz == 0) continue;
+              const unsigned b = raster[ci + (dz * Hp + dy) * Wp + dx];
+              if (b != 0xFFFFu) {
+                sum += (int)b + 1;
+                ++cnt;
+              }
+            }
+        if (cnt) {
+          const unsigned a = w >> 16;
+          atomicAdd(&nL[a], 1u);
+          atomicAdd(&S[a], ngtdm_term((int)a + 1, sum, cnt));
+        }
+      }
+      __syncthreads();
+      ngtdm_features<C, A>(p, row, ng, nL, S, lst, red, s_sc, s_i64);
+    }
+
     // ---- GLCM ------------------------------------------------------------------
     // Per offset: warp-aggregated inserts into a shared hash table of
     // (min bin, max bin) -> count that also records its occupied slots, so
@@ -1364,17 +1521,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
       if (tid == 0) {
         s_ncell = 0;
         s_npair = 0;
-      }
-      // the pixel list's coordinates are not needed after the moments: keep
-      // each pixel's padded raster index (low 16 bits; cells <= 16,384) and
-      // its own bin (high 16 bits) there instead of decoding them per offset
-      for (int i = tid; i < n; i += C::NT) {
-        const unsigned c = pc[i];
-        const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
-        const int y = NDIM == 3 ? (int)((c >> 11) & 2047u) : (int)(c >> 16);
-        const int z = NDIM == 3 ? (int)(c >> 22) : 0;
-        const unsigned ci = (unsigned)(((NDIM == 3 ? z + pad : 0) * Hp + (y + pad)) * Wp + (x + pad));
-        pc[i] = ci | ((unsigned)raster[ci] << 16);
       }
       for (int di = 0; di < p.n_dist; ++di) {
         for (int dir = 0; dir < p.n_dirs; ++dir) {

@@ -30,6 +30,8 @@
 //                into global ones and the last span of the group reduces
 //                them to the per-offset sums that k_glcm_final turns into
 //                features
+//   k_big_ngtdm  units (ROI, chunk): NGTDM neighbourhood sums from global
+//                memory; the last unit of an ROI derives the features
 //   k_big_order  ROIs without a value histogram (float images, 16-bit ROIs
 //                whose value range exceeds their pixel count): one block
 //                per ROI compacts the values in raster order and sorts them
@@ -1074,6 +1076,104 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   }
 }
 
+// NGTDM of big ROIs (Table S3 rows 246-250): units (ROI, chunk) as in the
+// pass kernels.  The Chebyshev-1 neighbours of a voxel come from the mask and
+// image in global memory, one plane of up to 9 loads of each issued together;
+// per-level counts and fixed-point sums gather in shared memory, go to the
+// ROI's arena arrays, and the last chunk of the ROI derives the features.
+template <class T, int NDIM, class A>
+__global__ void __launch_bounds__(BIG_NT) k_big_ngtdm(KParams p) {
+  using C = ClassBig;
+  __shared__ unsigned long long sS[256];
+  __shared__ unsigned snL[256], slst[256];
+  __shared__ double red[C::NW * RED_MAX];
+  __shared__ long long s_i64[4];
+  __shared__ A s_sc[16];
+  __shared__ int s_flag;
+  __shared__ unsigned s_qc[C::NW * 64], s_qe[C::NW * 64];  // per-warp voxel queues
+  const int tid = threadIdx.x;
+  const unsigned long long ctr = *p.big_ctr;
+  const int n_big = big_count(ctr);
+  const unsigned n_units = big_units1(ctr);
+  const int ng = p.ng;
+  const T* img = (const T*)p.img;
+  for (unsigned u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int b = big_of_unit(p, n_big, u);
+    const BigRoi br = p.big[b];
+    const int chunk = (int)(u - br.u1);
+    const RoiInfo r = p.rois[br.item];
+    BigBox bx;
+    bx.init(p, r, NDIM);
+    const BigLayout L = big_layout(p, br.nch, br.nsp, br.range, r.n);
+    unsigned* reg = p.arena + br.arena;
+    unsigned long long* gS = (unsigned long long*)(reg + L.ngt);
+    unsigned* gn = (unsigned*)(gS + ng);
+    const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
+    const unsigned vmin = r.vmin, vmax = r.vmax;
+    const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
+    FastDiv fd;
+    fd.init(vmax > vmin ? vmax - vmin : 1u);
+    auto gbin = [&](unsigned e) -> int {  // rule a4 with n = Ng
+      if (vmax <= vmin) return 0;
+      if constexpr (Enc<T>::INTEGER) return (int)min(fd.div((unsigned)ng * (e - vmin)), (unsigned)(ng - 1));
+      else return (int)bin_float(Enc<T>::decf(e), fmn, fmx, ng);
+    };
+    for (int i = tid; i < ng; i += BIG_NT) {
+      sS[i] = 0;
+      snL[i] = 0;
+    }
+    __syncthreads();
+    chunk_voxels<T>(p, bx, c0, c1, s_qc + (tid >> 5) * 64, s_qe + (tid >> 5) * 64,
+                    [&](bool in, int x, int y, int z, unsigned e) {
+      if (!in) return;
+      const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
+      int sum = 0, cnt = 0;
+#pragma unroll 1
+      for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
+        if (z + dz < 0 || z + dz >= bx.D) continue;
+        int lab[9];
+        T val[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {  // every load of the plane first
+          const int dy = q / 3 - 1, dx = q % 3 - 1;
+          lab[q] = 0;
+          const bool inb = !(dz == 0 && dy == 0 && dx == 0) && y + dy >= 0 && y + dy < bx.H && x + dx >= 0 &&
+                           x + dx < bx.W;
+          if (inb) {
+            const int64_t o = here + ((int64_t)dz * p.ny + dy) * p.nx + dx;
+            lab[q] = __ldg(p.mask + o);
+            val[q] = __ldg(img + o);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          if (lab[q] == bx.label) {
+            sum += gbin(Enc<T>::enc(val[q])) + 1;
+            ++cnt;
+          }
+      }
+      if (cnt) {
+        const int a = gbin(e);
+        atomicAdd(&snL[a], 1u);
+        atomicAdd(&sS[a], ngtdm_term(a + 1, sum, cnt));
+      }
+    });
+    __syncthreads();
+    for (int i = tid; i < ng; i += BIG_NT)
+      if (snL[i]) {
+        atomicAdd(gn + i, snL[i]);
+        atomicAdd(gS + i, sS[i]);
+      }
+    if (!last_arrival(reg + L.ctr + 2, (unsigned)br.nch, &s_flag)) continue;
+    for (int i = tid; i < ng; i += BIG_NT) {
+      snL[i] = __ldcg(gn + i);
+      sS[i] = __ldcg(gS + i);
+    }
+    __syncthreads();
+    ngtdm_features<C, A>(p, p.table + (int64_t)br.item * p.n_col, ng, snL, sS, slst, red, s_sc, s_i64);
+  }
+}
+
 // Order statistics of big ROIs without a value histogram (float images, and
 // 16-bit ROIs whose value range exceeds their pixel count): one block per ROI
 // compacts the values in raster order and sorts them with an LSD radix sort
@@ -1244,6 +1344,9 @@ cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
   if ((e = big_launch<k_big_p2<T, NDIM, A>>(0, nsm, p, st)) != cudaSuccess) return e;
   if (p.need & NEED_GLCM) {
     if ((e = big_launch<k_big_glcm<T, NDIM, A>>(GLCM_SMEM_BYTES, nsm, p, st)) != cudaSuccess) return e;
+  }
+  if (p.need & NEED_NGTDM) {
+    if ((e = big_launch<k_big_ngtdm<T, NDIM, A>>(0, nsm, p, st)) != cudaSuccess) return e;
   }
   if (p.need & NEED_ORDER) {
     auto kern = k_big_order<T, A>;
