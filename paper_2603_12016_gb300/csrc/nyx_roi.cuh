@@ -734,8 +734,8 @@ __device__ inline unsigned long long ngtdm_term(int L, int sum, int cnt) {
 // sum (L - m)^2) / sum s (the double sums over the present levels, written
 // about the means so that they do not cancel).
 template <class C, class A>
-__device__ void ngtdm_features(const KParams& p, double* row, int ng, const unsigned* nL,
-                               const unsigned long long* S, unsigned* lst, double* red, A* sc, long long* s64) {
+__device__ void ngtdm_features(const KParams& p, double* row, int ng, unsigned* nL, unsigned long long* S,
+                               unsigned* lst, double* red, A* sc, long long* s64) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const A nan = anan<A>();
   const A fx = (A)(1.0 / 4294967296.0);
@@ -762,13 +762,56 @@ __device__ void ngtdm_features(const KParams& p, double* row, int ng, const unsi
     return;
   }
   const A invN = (A)1 / (A)Nv;
+  // FP32: p, p s and L p of the present levels, compacted in level order into
+  // the storage of S (float2 per level) and nL, read by the pair sums below
+  constexpr bool F32 = std::is_same<A, float>::value;
+  float2* PA = (float2*)S;
+  float* V = (float*)nL;
+  if constexpr (F32) {
+    constexpr int MAXK = 256 / C::NT + 1;
+    float2 pa[MAXK];
+    float vv[MAXK];
+#pragma unroll
+    for (int q = 0; q < MAXK; ++q) {
+      const int k = tid + q * C::NT;
+      if (k < G) {
+        const int i = (int)lst[k];
+        const float pi = (float)nL[i] * invN;
+        pa[q] = make_float2(pi, pi * (ll2f((long long)S[i]) * fx));
+        vv[q] = (float)(i + 1) * pi;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MAXK; ++q) {
+      const int k = tid + q * C::NT;
+      if (k < G) {
+        PA[k] = pa[q];
+        V[k] = vv[q];
+      }
+    }
+    __syncthreads();
+  }
+  auto level = [&](int k, A& pi, A& ai, A& L) {  // p, p s, L of the k-th present level
+    if constexpr (F32) {
+      const float2 x = PA[k];
+      pi = x.x;
+      ai = x.y;
+      L = (A)(lst[k] + 1);
+    } else {
+      const int i = (int)lst[k];
+      pi = (A)nL[i] * invN;
+      ai = pi * ((A)ll2f((long long)S[i]) * fx);
+      L = (A)(i + 1);
+    }
+  };
   {  // ps = sum p s, ssum = sum s, mu = sum p L, T1 = sum L
     A v[4] = {0, 0, 0, 0};
     for (int k = tid; k < G; k += C::NT) {
-      const int i = (int)lst[k];
-      const A pi = (A)nL[i] * invN, si = (A)ll2f((long long)S[i]) * fx, L = (A)(i + 1);
-      v[0] += pi * si;
-      v[1] += si;
+      A pi, ai, L;
+      level(k, pi, ai, L);
+      v[0] += ai;
+      v[1] += ai / pi;
       v[2] += pi * L;
       v[3] += L;
     }
@@ -778,8 +821,8 @@ __device__ void ngtdm_features(const KParams& p, double* row, int ng, const unsi
   {  // centred sums, then the pair sums over i < j (rows paired for balance)
     A v[5] = {0, 0, 0, 0, 0};
     for (int k = tid; k < G; k += C::NT) {
-      const int i = (int)lst[k];
-      const A pi = (A)nL[i] * invN, L = (A)(i + 1);
+      A pi, ai, L;
+      level(k, pi, ai, L);
       v[0] += pi * (L - mu) * (L - mu);
       v[1] += pi * (L - m) * (L - m);
       v[2] += (L - m) * (L - m);
@@ -789,15 +832,29 @@ __device__ void ngtdm_features(const KParams& p, double* row, int ng, const unsi
       for (int h = 0; h < 2; ++h) {
         const int r = h ? G - 1 - a : a;
         if (h && r == a) break;
-        const int i = (int)lst[r];
-        const A pi = (A)nL[i] * invN, si = (A)ll2f((long long)S[i]) * fx, Li = (A)(i + 1);
+        A pi, ai, Li;
+        level(r, pi, ai, Li);
+        const A vi = Li * pi;
+        A b0 = 0, b1 = 0;
         for (int c = r + 1; c < G; ++c) {
-          const int j = (int)lst[c];
-          const A pj = (A)nL[j] * invN, sj = (A)ll2f((long long)S[j]) * fx, Lj = (A)(j + 1);
-          const A dv = Li * pi - Lj * pj;
-          v[3] += dv < 0 ? -dv : dv;
-          v[4] += (Lj - Li) * (pi * si + pj * sj) / (pi + pj);  // Lj > Li
+          A pj, aj, Lj;
+          if constexpr (F32) {
+            const float2 x = PA[c];
+            pj = x.x;
+            aj = x.y;
+            Lj = (A)(lst[c] + 1);
+            const float dv = vi - V[c];
+            b0 += fabsf(dv);
+            b1 += __fdividef((Lj - Li) * (ai + aj), pi + pj);  // Lj > Li
+          } else {
+            level(c, pj, aj, Lj);
+            const A dv = vi - Lj * pj;
+            b0 += dv < 0 ? -dv : dv;
+            b1 += (Lj - Li) * (ai + aj) / (pi + pj);
+          }
         }
+        v[3] += b0;
+        v[4] += b1;
       }
     }
     block_sum<C, A, 5>(v, red, sc + 4);

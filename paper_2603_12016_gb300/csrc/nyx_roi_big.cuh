@@ -30,8 +30,9 @@
 //                into global ones and the last span of the group reduces
 //                them to the per-offset sums that k_glcm_final turns into
 //                features
-//   k_big_ngtdm  units (ROI, chunk): NGTDM neighbourhood sums from global
-//                memory; the last unit of an ROI derives the features
+//   k_big_ngtdm  units (ROI, chunk): NGTDM neighbourhood sums over a shared-
+//                memory window of bins (chunk plus a plane-and-row halo);
+//                the last unit of an ROI derives the features
 //   k_big_order  ROIs without a value histogram (float images, 16-bit ROIs
 //                whose value range exceeds their pixel count): one block
 //                per ROI compacts the values in raster order and sorts them
@@ -1077,13 +1078,21 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
 }
 
 // NGTDM of big ROIs (Table S3 rows 246-250): units (ROI, chunk) as in the
-// pass kernels.  The Chebyshev-1 neighbours of a voxel come from the mask and
-// image in global memory, one plane of up to 9 loads of each issued together;
-// per-level counts and fixed-point sums gather in shared memory, go to the
-// ROI's arena arrays, and the last chunk of the ROI derives the features.
+// pass kernels.  A unit stages the bins of its chunk plus a halo of one plane
+// and one row on each side (the Chebyshev-1 reach), in the raster of the box
+// padded by one sentinel cell, in shared memory, then sums each ROI voxel's
+// neighbour levels there at fixed displacements; when
+// the window exceeds NGT_WIN cells (very wide planes) the neighbours come
+// from global memory instead, one plane of up to 9 loads of each issued
+// together.  Per-level counts and fixed-point sums gather in shared memory,
+// go to the ROI's arena arrays, and the last chunk derives the features.
+constexpr int NGT_WIN = 49152;  // window cells (2-byte bins) in dynamic shared memory
+
 template <class T, int NDIM, class A>
-__global__ void __launch_bounds__(BIG_NT) k_big_ngtdm(KParams p) {
+__global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParams p) {
   using C = ClassBig;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* rast = (uint16_t*)smem;  // [NGT_WIN]
   __shared__ unsigned long long sS[256];
   __shared__ unsigned snL[256], slst[256];
   __shared__ double red[C::NW * RED_MAX];
@@ -1091,6 +1100,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_ngtdm(KParams p) {
   __shared__ A s_sc[16];
   __shared__ int s_flag;
   __shared__ unsigned s_qc[C::NW * 64], s_qe[C::NW * 64];  // per-warp voxel queues
+  constexpr uint16_t SENT = 0xFFFF;
   const int tid = threadIdx.x;
   const unsigned long long ctr = *p.big_ctr;
   const int n_big = big_count(ctr);
@@ -1122,42 +1132,110 @@ __global__ void __launch_bounds__(BIG_NT) k_big_ngtdm(KParams p) {
       sS[i] = 0;
       snL[i] = 0;
     }
-    __syncthreads();
-    chunk_voxels<T>(p, bx, c0, c1, s_qc + (tid >> 5) * 64, s_qe + (tid >> 5) * 64,
-                    [&](bool in, int x, int y, int z, unsigned e) {
-      if (!in) return;
-      const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
-      int sum = 0, cnt = 0;
-#pragma unroll 1
-      for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
-        if (z + dz < 0 || z + dz >= bx.D) continue;
-        int lab[9];
-        T val[9];
+    // window in the padded box (one sentinel cell around the bounding box),
+    // so that every neighbour is a fixed displacement without bounds tests
+    const int Wp = bx.W + 2, Hp = bx.H + 2;
+    const unsigned plane = (unsigned)Wp * (unsigned)Hp;
+    const unsigned pcells = plane * (unsigned)(NDIM == 3 ? bx.D + 2 : 1);
+    auto pidx = [&](unsigned c) -> unsigned {  // padded index of bounding-box cell c
+      int x, y, z;
+      bx.offset(c, x, y, z, p);
+      return ((unsigned)(NDIM == 3 ? z + 1 : 0) * (unsigned)Hp + (unsigned)(y + 1)) * (unsigned)Wp + (unsigned)(x + 1);
+    };
+    const unsigned halo = (NDIM == 3 ? plane : 0u) + (unsigned)Wp + 1u;
+    const unsigned p_lo = pidx(c0), p_hi = pidx(c1 - 1) + 1u;
+    const unsigned w0 = p_lo > halo ? p_lo - halo : 0u, w1 = min(pcells, p_hi + halo);
+    if (w1 - w0 <= (unsigned)NGT_WIN) {
+      // ---- shared-memory window: bins of padded cells [w0, w1), SENT off the ROI ----
+      FastDiv fwp, fhp;
+      fwp.init((unsigned)Wp);
+      fhp.init((unsigned)Hp);
+      for (unsigned ib = w0; ib < w1; ib += BIG_U * BIG_NT) {
+        int lab[BIG_U];
+        T val[BIG_U];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {  // every load of the plane first
-          const int dy = q / 3 - 1, dx = q % 3 - 1;
+        for (int q = 0; q < BIG_U; ++q) {  // loads of BIG_U cells in flight
+          const unsigned P = ib + q * BIG_NT + tid;
           lab[q] = 0;
-          const bool inb = !(dz == 0 && dy == 0 && dx == 0) && y + dy >= 0 && y + dy < bx.H && x + dx >= 0 &&
-                           x + dx < bx.W;
-          if (inb) {
-            const int64_t o = here + ((int64_t)dz * p.ny + dy) * p.nx + dx;
-            lab[q] = __ldg(p.mask + o);
-            val[q] = __ldg(img + o);
+          if (P < w1) {
+            const unsigned rq = fwp.div(P), zq = fhp.div(rq);
+            const int x = (int)(P - rq * (unsigned)Wp) - 1, y = (int)(rq - zq * (unsigned)Hp) - 1;
+            const int z = NDIM == 3 ? (int)zq - 1 : 0;
+            if (x >= 0 && y >= 0 && z >= 0 && x < bx.W && y < bx.H && z < bx.D) {
+              const int64_t off = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
+              lab[q] = __ldg(p.mask + off);
+              val[q] = __ldg(img + off);
+            }
           }
         }
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-          if (lab[q] == bx.label) {
-            sum += gbin(Enc<T>::enc(val[q])) + 1;
-            ++cnt;
+        for (int q = 0; q < BIG_U; ++q) {
+          const unsigned P = ib + q * BIG_NT + tid;
+          if (P < w1) rast[P - w0] = lab[q] == bx.label ? (uint16_t)gbin(Enc<T>::enc(val[q])) : SENT;
+        }
+      }
+      __syncthreads();
+      for (unsigned c = c0 + tid; c < c1; c += BIG_NT) {
+        const int here = (int)(pidx(c) - w0);
+        const unsigned a = rast[here];
+        if (a == SENT) continue;
+        int sum = 0, cnt = 0;
+#pragma unroll
+        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (dx == 0 && dy == 0 && dz == 0) continue;
+              const unsigned bnb = rast[here + (dz * Hp + dy) * Wp + dx];
+              if (bnb != SENT) {
+                sum += (int)bnb + 1;
+                ++cnt;
+              }
+            }
+        if (cnt) {
+          atomicAdd(&snL[a], 1u);
+          atomicAdd(&sS[a], ngtdm_term((int)a + 1, sum, cnt));
+        }
+      }
+    } else {
+      // ---- neighbours from global memory ----
+      __syncthreads();
+      chunk_voxels<T>(p, bx, c0, c1, s_qc + (tid >> 5) * 64, s_qe + (tid >> 5) * 64,
+                      [&](bool in, int x, int y, int z, unsigned e) {
+        const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
+        int sum = 0, cnt = 0;
+#pragma unroll 1
+        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
+          if (!in || z + dz < 0 || z + dz >= bx.D) continue;
+          int lab[9];
+          T val[9];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {  // every load of the plane first
+            const int dy = q / 3 - 1, dx = q % 3 - 1;
+            lab[q] = 0;
+            const bool inb = !(dz == 0 && dy == 0 && dx == 0) && y + dy >= 0 && y + dy < bx.H && x + dx >= 0 &&
+                             x + dx < bx.W;
+            if (inb) {
+              const int64_t o = here + ((int64_t)dz * p.ny + dy) * p.nx + dx;
+              lab[q] = __ldg(p.mask + o);
+              val[q] = __ldg(img + o);
+            }
           }
-      }
-      if (cnt) {
-        const int a = gbin(e);
-        atomicAdd(&snL[a], 1u);
-        atomicAdd(&sS[a], ngtdm_term(a + 1, sum, cnt));
-      }
-    });
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            if (lab[q] == bx.label) {
+              sum += gbin(Enc<T>::enc(val[q])) + 1;
+              ++cnt;
+            }
+        }
+        if (cnt) {
+          const int a = gbin(e);
+          atomicAdd(&snL[a], 1u);
+          atomicAdd(&sS[a], ngtdm_term(a + 1, sum, cnt));
+        }
+      });
+    }
     __syncthreads();
     for (int i = tid; i < ng; i += BIG_NT)
       if (snL[i]) {
@@ -1346,7 +1424,7 @@ cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
     if ((e = big_launch<k_big_glcm<T, NDIM, A>>(GLCM_SMEM_BYTES, nsm, p, st)) != cudaSuccess) return e;
   }
   if (p.need & NEED_NGTDM) {
-    if ((e = big_launch<k_big_ngtdm<T, NDIM, A>>(0, nsm, p, st)) != cudaSuccess) return e;
+    if ((e = big_launch<k_big_ngtdm<T, NDIM, A>>(2 * NGT_WIN, nsm, p, st)) != cudaSuccess) return e;
   }
   if (p.need & NEED_ORDER) {
     auto kern = k_big_order<T, A>;
