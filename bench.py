@@ -99,10 +99,10 @@ class ClockSampler:
 # capture (profiles/roi_kernels_nuclei2d_2048.md), keyed by workload, phase
 # and class limits; entries are removed when the kernel changes.
 TRAFFIC = {
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 8192)): 18.48e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 8192)): 13.61e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 4096)): 18.48e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 4096)): 13.62e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 8192)): 18.51e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 8192)): 13.64e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 4096)): 18.70e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 4096)): 13.64e6,
 }
 
 
