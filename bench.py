@@ -103,6 +103,9 @@ TRAFFIC = {
     ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 8192)): 13.64e6,
     ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 4096)): 18.70e6,
     ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 4096)): 13.64e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_warp", (256, 1024, 8192)): 5.81e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (256, 1024, 8192)): 16.53e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_medium", (256, 1024, 8192)): 13.63e6,
 }
 
 
