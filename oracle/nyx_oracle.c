@@ -12,7 +12,8 @@
  *     table out; ROI separation into per-ROI pixel sets ("Nyxus architecture"
  *     section, pixel-cloud paragraph);
  *   - feature inventory: Table S1 (2D intensity), Table S2 (shape/geometric
- *     and intensity moments, rows 123-135), Table S3 (GLCM rows 140-174),
+ *     and intensity moments, rows 123-135), Table S3 (GLCM rows 140-174,
+ *     NGTDM rows 246-250, GLDM rows 251-264),
  *     Table S5 (3D intensity, 3D GLCM row 361, 3D raw/central moments rows
  *     368/370);
  *   - the paper states IBSI compliance ("IBSI profile", Fig. 5) and defers
@@ -233,6 +234,8 @@ typedef struct {
   /* Table S3 rows 246-250 (NGTDM): coarseness, contrast, busyness,
    * complexity, strength (reading c17) */
   double ngtdm[5];
+  /* Table S3 rows 251-264 (GLDM), reading c18 */
+  double gldm[14];
 } feat_t;
 
 static const char* GLCM_NAMES[ORC_NGLCM] = {
@@ -401,6 +404,9 @@ static void emit_all(const orc_cfg* c, const feat_t* f, emitter* e) {
   if (c->ng > 0) {
     static const char* NG_NAMES[5] = {"COARSENESS", "CONTRAST", "BUSYNESS", "COMPLEXITY", "STRENGTH"};
     for (int q = 0; q < 5; ++q) emit(e, f->ngtdm[q], "NGTDM_%s", NG_NAMES[q]);
+    static const char* GD_NAMES[14] = {"SDE", "LDE", "GLN", "DN", "DNN", "GLV", "DV",
+                                       "DE", "LGLE", "HGLE", "SDLGLE", "SDHGLE", "LDLGLE", "LDHGLE"};
+    for (int q = 0; q < 14; ++q) emit(e, f->gldm[q], "GLDM_%s", GD_NAMES[q]);
   }
   emit(e, f->edge_ii, "EDGE_INTEGRATED_INTENSITY");
   emit(e, f->edge_max, "EDGE_MAX_INTENSITY");
@@ -896,6 +902,77 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     }
     free(nL);
     free(sL);
+  }
+
+  /* ---- GLDM, Table S3 rows 251-264 (reading c18): the dependence of a
+   * pixel of grey level i (1-based GLCM bin) is j = 1 + the number of its 8
+   * (2D) / 26 (3D) Chebyshev-1 neighbours in the ROI with the same level;
+   * P(i, j) counts the pixels, N = sum P = the ROI's pixel count, p = P / N.
+   * SDE sum P / j^2 / N, LDE sum P j^2 / N, GLN sum_i (sum_j P)^2 / N, DN
+   * sum_j (sum_i P)^2 / N, DNN DN / N, GLV sum p (i - mu_i)^2, DV
+   * sum p (j - mu_j)^2, DE -sum p log2 p (cells with P > 0), LGLE
+   * sum P / i^2 / N, HGLE sum P i^2 / N, SDLGLE sum P / (i^2 j^2) / N,
+   * SDHGLE sum P i^2 / j^2 / N, LDLGLE sum P j^2 / i^2 / N, LDHGLE
+   * sum P i^2 j^2 / N. ---- */
+  if (c->ng > 0) {
+    const int nj = d3 ? 27 : 9;
+    double* P = (double*)calloc((size_t)c->ng * nj, sizeof(double));
+    for (int64_t k = 0; k < N; ++k) {
+      const int L = bin_of(c, I[k], mn, mx, c->ng);
+      int dep = 1;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            if (!d3 && dz != 0) continue;
+            const int64_t x = X[k][0] + dx, y = X[k][1] + dy, z = X[k][2] + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) continue;
+            const int64_t nl = (z * c->ny + y) * c->nx + x;
+            if (mask[base + nl] != r->label) continue;
+            if (bin_of(c, pixel(c, img, base + nl), mn, mx, c->ng) == L) ++dep;
+          }
+      P[L * nj + (dep - 1)] += 1;
+    }
+    const double Nz = (double)N;
+    double g[14] = {0};
+    double mui = 0, muj = 0;
+    for (int i = 0; i < c->ng; ++i)
+      for (int j = 0; j < nj; ++j) {
+        const double pij = P[i * nj + j] / Nz;
+        mui += pij * (i + 1);
+        muj += pij * (j + 1);
+      }
+    for (int i = 0; i < c->ng; ++i) {
+      double rowsum = 0;
+      const double ii = i + 1.0, i2 = ii * ii;
+      for (int j = 0; j < nj; ++j) {
+        const double v = P[i * nj + j];
+        rowsum += v;
+        if (v == 0) continue;
+        const double jj = j + 1.0, j2 = jj * jj, pij = v / Nz;
+        g[0] += v / j2;
+        g[1] += v * j2;
+        g[5] += pij * (ii - mui) * (ii - mui);
+        g[6] += pij * (jj - muj) * (jj - muj);
+        g[7] -= pij * log2(pij);
+        g[8] += v / i2;
+        g[9] += v * i2;
+        g[10] += v / (i2 * j2);
+        g[11] += v * i2 / j2;
+        g[12] += v * j2 / i2;
+        g[13] += v * i2 * j2;
+      }
+      g[2] += rowsum * rowsum;
+    }
+    for (int j = 0; j < nj; ++j) {
+      double colsum = 0;
+      for (int i = 0; i < c->ng; ++i) colsum += P[i * nj + j];
+      g[3] += colsum * colsum;
+    }
+    const int per_n[14] = {1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
+    for (int q = 0; q < 14; ++q) f->gldm[q] = per_n[q] ? g[q] / Nz : g[q];
+    f->gldm[4] = g[3] / (Nz * Nz);
+    free(P);
   }
   free(I);
   free(X);

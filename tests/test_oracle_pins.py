@@ -729,3 +729,113 @@ def test_ngtdm_two_level_stripes_closed_form(orc):
     for name, v in zip(NGTDM_COLS, ref):
         assert t[name] == pytest.approx(v, rel=1e-13)
     assert t["NGTDM_CONTRAST"] > 0 and t["NGTDM_BUSYNESS"] > 0
+
+
+# --------------------------------------------------------------------------
+# GLDM (Table S3 rows 251-264): the dependence matrix built independently
+# with one scipy.ndimage correlation per grey level (same-level neighbour
+# counts), the fourteen features from the explicit matrix, and a constant
+# square whose matrix is known by hand.
+
+GLDM_COLS = ["GLDM_" + n for n in ("SDE", "LDE", "GLN", "DN", "DNN", "GLV", "DV", "DE", "LGLE", "HGLE", "SDLGLE",
+                                   "SDHGLE", "LDLGLE", "LDHGLE")]
+
+
+def _gldm_matrix(img, mask, label, ng):
+    import scipy.ndimage as ndi
+
+    m = mask == label
+    v = img[m].astype(np.int64)
+    mn, mx = v.min(), v.max()
+    lev = np.zeros(img.shape, dtype=np.int64)
+    if mx > mn:
+        lev[m] = np.minimum(ng * (img[m].astype(np.int64) - mn) // (mx - mn), ng - 1) + 1
+    else:
+        lev[m] = 1
+    k = np.ones((3,) * img.ndim)
+    k[(1,) * img.ndim] = 0
+    nj = 3 ** img.ndim
+    P = np.zeros((ng, nj))
+    for i in range(1, ng + 1):
+        ind = (lev == i) & m
+        if not ind.any():
+            continue
+        same = ndi.correlate(ind.astype(np.int64), k.astype(np.int64), mode="constant", cval=0)
+        P[i - 1] = np.bincount(same[ind] + 1, minlength=nj + 1)[1:]
+    return P
+
+
+def _gldm_features(P):
+    N = P.sum()
+    i = np.arange(1, P.shape[0] + 1, dtype=np.float64)[:, None]
+    j = np.arange(1, P.shape[1] + 1, dtype=np.float64)[None, :]
+    p = P / N
+    mui, muj = np.sum(p * i), np.sum(p * j)
+    nz = p > 0
+    return [np.sum(P / j ** 2) / N, np.sum(P * j ** 2) / N, np.sum(P.sum(1) ** 2) / N, np.sum(P.sum(0) ** 2) / N,
+            np.sum(P.sum(0) ** 2) / N ** 2, np.sum(p * (i - mui) ** 2), np.sum(p * (j - muj) ** 2),
+            -np.sum(p[nz] * np.log2(p[nz])), np.sum(P / i ** 2) / N, np.sum(P * i ** 2) / N,
+            np.sum(P / (i ** 2 * j ** 2)) / N, np.sum(P * i ** 2 / j ** 2) / N, np.sum(P * j ** 2 / i ** 2) / N,
+            np.sum(P * i ** 2 * j ** 2) / N]
+
+
+@pytest.mark.parametrize("ndim,seed,ng", [(2, 1, 8), (2, 2, 32), (3, 3, 16)])
+def test_gldm_vs_numpy_construction(orc, ndim, seed, ng):
+    rng = np.random.default_rng(70 + seed)
+    shape = (30, 33) if ndim == 2 else (10, 12, 13)
+    # few distinct values so that same-level neighbours are common
+    img = (rng.integers(0, 6, size=shape) * 700).astype(np.uint16)
+    mask = np.zeros(shape, dtype=np.int32)
+    grids = np.meshgrid(*[np.arange(sh) for sh in shape], indexing="ij")
+    for lab in range(1, 6):  # touching blobs, some cut by the border
+        c = [rng.uniform(-1, sh + 1) for sh in shape]
+        r = rng.uniform(2.5, 7.0)
+        mask[sum((g - ci) ** 2 for g, ci in zip(grids, c)) <= r * r] = lab
+    t = orc.extract(img, mask, ndim, ng=ng)
+    for row, lab in enumerate(t["LABEL"].astype(int)):
+        P = _gldm_matrix(img, mask, lab, ng)
+        assert P.sum() == np.count_nonzero(mask == lab)
+        for name, v in zip(GLDM_COLS, _gldm_features(P)):
+            assert t[name][row] == pytest.approx(v, rel=1e-12, abs=1e-12), (lab, name)
+
+
+def test_gldm_constant_square_closed_form(orc):
+    """A constant 3 x 3 ROI in 2D: one grey level; 4 corners with 3
+    neighbours (dependence 4), 4 edge centres with 5 (dependence 6), the
+    centre with 8 (dependence 9), so P(1, 4) = P(1, 6) = 4, P(1, 9) = 1."""
+    img = np.full((5, 5), 300, dtype=np.uint16)
+    mask = np.zeros((5, 5), dtype=np.int32)
+    mask[1:4, 1:4] = 1
+    t = _single(orc, img, mask, ng=16)
+    n, deps = 9.0, {4: 4.0, 6: 4.0, 9: 1.0}
+    sde = sum(c / d ** 2 for d, c in deps.items()) / n
+    lde = sum(c * d ** 2 for d, c in deps.items()) / n
+    muj = sum(c * d for d, c in deps.items()) / n
+    want = {"SDE": sde, "LDE": lde, "GLN": n, "DN": 33.0 / n, "DNN": 33.0 / n ** 2, "GLV": 0.0,
+            "DV": sum(c * (d - muj) ** 2 for d, c in deps.items()) / n,
+            "DE": -sum((c / n) * np.log2(c / n) for c in deps.values()), "LGLE": 1.0, "HGLE": 1.0,
+            "SDLGLE": sde, "SDHGLE": sde, "LDLGLE": lde, "LDHGLE": lde}
+    for k, v in want.items():
+        assert t["GLDM_" + k] == pytest.approx(v, rel=1e-14, abs=1e-15), k
+    assert lde == pytest.approx(289.0 / 9.0)
+
+
+def test_gldm_checkerboard_and_isolated_pixels(orc):
+    """A two-level checkerboard: in 2D every same-level neighbour is
+    diagonal, so each of the 36 interior pixels has dependence 5.  Isolated
+    pixels have dependence 1 at any level: SDE = LDE = 1, DN = N, DNN = 1,
+    DV = 0."""
+    yy, xx = np.mgrid[0:8, 0:8]
+    img = ((xx + yy) % 2).astype(np.uint16)
+    mask = np.ones((8, 8), dtype=np.int32)
+    t = _single(orc, img, mask, ng=2)
+    P = _gldm_matrix(img, mask, 1, 2)
+    assert P[:, 4].sum() == 36  # the 6 x 6 interior
+    for name, v in zip(GLDM_COLS, _gldm_features(P)):
+        assert t[name] == pytest.approx(v, rel=1e-13), name
+    mask = np.zeros((9, 9), dtype=np.int32)
+    mask[::3, ::3] = 1       # 9 pixels, no two adjacent
+    img = (np.arange(81).reshape(9, 9) * 5).astype(np.uint16)
+    t = _single(orc, img, mask, ng=4)
+    assert t["GLDM_SDE"] == 1.0 and t["GLDM_LDE"] == 1.0
+    assert t["GLDM_DN"] == 9.0 and t["GLDM_DNN"] == 1.0 and t["GLDM_DV"] == 0.0
