@@ -99,13 +99,9 @@ class ClockSampler:
 # capture (profiles/roi_kernels_nuclei2d_2048.md), keyed by workload, phase
 # and class limits; entries are removed when the kernel changes.
 TRAFFIC = {
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 8192)): 18.51e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 8192)): 13.64e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (0, 1024, 4096)): 18.70e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_medium", (0, 1024, 4096)): 13.64e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_warp", (256, 1024, 8192)): 5.81e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (256, 1024, 8192)): 16.53e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_medium", (256, 1024, 8192)): 13.63e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_warp", (256, 1024, 8192)): 5.88e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_small", (256, 1024, 8192)): 16.58e6,
+    ("nuclei2d_2048_u16_4000roi", "roi_medium", (256, 1024, 8192)): 13.68e6,
 }
 
 

@@ -130,7 +130,13 @@ nyx_status nyx_column_name(const nyx_plan* plan, int col, char* buf, size_t cap)
  * edge pixel); 86..90 NGTDM features (Table S3 rows 246-250, need
  * glcm_levels > 0): NGTDM_COARSENESS, NGTDM_CONTRAST, NGTDM_BUSYNESS,
  * NGTDM_COMPLEXITY, NGTDM_STRENGTH on the GLCM grey levels, over the pixels
- * with at least one ROI pixel among their 8 (2D) / 26 (3D) neighbours. */
+ * with at least one ROI pixel among their 8 (2D) / 26 (3D) neighbours;
+ * 91..104 GLDM features (Table S3 rows 251-264, need glcm_levels > 0):
+ * GLDM_SDE, GLDM_LDE, GLDM_GLN, GLDM_DN, GLDM_DNN, GLDM_GLV, GLDM_DV,
+ * GLDM_DE, GLDM_LGLE, GLDM_HGLE, GLDM_SDLGLE, GLDM_SDHGLE, GLDM_LDLGLE,
+ * GLDM_LDHGLE of the grey-level dependence matrix on the GLCM grey levels,
+ * the dependence of a pixel being 1 + the number of its 8 / 26 neighbours
+ * in the ROI at its own level. */
 int nyx_feature_id(const char* name);
 
 /* Run the label scan only and return the number of ROIs (distinct
@@ -222,10 +228,10 @@ nyx_status nyx_sync_status(nyx_plan* plan, void* stream);
  * dL/dF for every output cell (d_grad_table, FP64 [n_roi x n_col], same
  * layout as the last nyx_extract made with NYX_SAVE_FOR_BACKWARD), write
  * dL/dI for every pixel to d_grad_img (FP32, image shape; 0 outside ROIs).
- * Non-smooth columns (min/max, order statistics, histogram, GLCM, binary
- * moments, geometry) contribute nothing.  Not in the paper: it makes the
- * features usable as a differentiable layer for the AI/ML use the paper's
- * introduction motivates.  When d_img / d_mask are the buffers of that
+ * Non-smooth columns (min/max, order statistics, histogram, GLCM, NGTDM,
+ * GLDM, binary moments, geometry) contribute nothing.  Not in the paper: it
+ * makes the features usable as a differentiable layer for the AI/ML use the
+ * paper's introduction motivates.  When d_img / d_mask are the buffers of that
  * forward pass, its label -> ROI map is reused (the forward pass kept it);
  * otherwise the map is rebuilt by a label scan of d_mask.  Any other call on
  * the plan releases a kept map first.  Errors: NYX_ERR_STATE (no saved

@@ -38,7 +38,7 @@ using namespace nyx;
 
 // ---------------------------------------------------------------------------
 // feature registry: ids 0..40 statistics, 41..50 moment families, 51..80 GLCM,
-// 81..85 edge intensity statistics, 86..90 NGTDM
+// 81..85 edge intensity statistics, 86..90 NGTDM, 91..104 GLDM
 
 namespace {
 
@@ -61,8 +61,12 @@ constexpr int FID_GLCM = N_STATS + 10;   // 51
 const char* NGTDM_NAMES[N_NGTDM] = {"NGTDM_COARSENESS", "NGTDM_CONTRAST", "NGTDM_BUSYNESS", "NGTDM_COMPLEXITY",
                                     "NGTDM_STRENGTH"};
 constexpr int FID_EDGE = FID_GLCM + NGLCM;  // 81
+const char* GLDM_NAMES[N_GLDM] = {"GLDM_SDE",    "GLDM_LDE",  "GLDM_GLN",    "GLDM_DN",     "GLDM_DNN",
+                                  "GLDM_GLV",    "GLDM_DV",   "GLDM_DE",     "GLDM_LGLE",   "GLDM_HGLE",
+                                  "GLDM_SDLGLE", "GLDM_SDHGLE", "GLDM_LDLGLE", "GLDM_LDHGLE"};
 constexpr int FID_NGTDM = FID_EDGE + N_EDGE;  // 86
-constexpr int N_FID = FID_NGTDM + N_NGTDM;    // 91
+constexpr int FID_GLDM = FID_NGTDM + N_NGTDM; // 91
+constexpr int N_FID = FID_GLDM + N_GLDM;      // 105
 
 bool is_order_stat(int s) {
   return s == S_MEDIAN || s == S_P01 || s == S_P10 || s == S_P25 || s == S_P75 || s == S_P90 || s == S_P99 ||
@@ -225,6 +229,8 @@ int nyx_feature_id(const char* name) {
     if (!strcmp(name, EDGE_NAMES[e])) return FID_EDGE + e;
   for (int q = 0; q < N_NGTDM; ++q)
     if (!strcmp(name, NGTDM_NAMES[q])) return FID_NGTDM + q;
+  for (int q = 0; q < N_GLDM; ++q)
+    if (!strcmp(name, GLDM_NAMES[q])) return FID_GLDM + q;
   return -1;
 }
 
@@ -326,6 +332,9 @@ static void build_columns(nyx_plan* pl) {
   if (p.glcm_levels > 0)
     for (int q = 0; q < N_NGTDM; ++q)
       if (fbit(p, FID_NGTDM + q)) add(Q_NGTDM + q, NGTDM_NAMES[q]);
+  if (p.glcm_levels > 0)
+    for (int q = 0; q < N_GLDM; ++q)
+      if (fbit(p, FID_GLDM + q)) add(Q_GLDM + q, GLDM_NAMES[q]);
 }
 
 // GLCM unit directions: 2D angles 0/45/90/135 degrees as (dx,dy) = (1,0),
@@ -453,9 +462,12 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   if (p.glcm_levels > 0)  // NGTDM grey levels are the GLCM bins
     for (int q = 0; q < N_NGTDM; ++q)
       if (fbit(p, FID_NGTDM + q)) need |= NEED_NGTDM;
-  // the edge test and the NGTDM neighbourhood read neighbours from the
-  // padded bin raster
-  if ((need & (NEED_EDGE | NEED_NGTDM)) && k.pad < 1) k.pad = 1;
+  if (p.glcm_levels > 0)  // so are the GLDM grey levels
+    for (int q = 0; q < N_GLDM; ++q)
+      if (fbit(p, FID_GLDM + q)) need |= NEED_GLDM;
+  // the edge test and the NGTDM / GLDM neighbourhoods read neighbours from
+  // the padded bin raster
+  if ((need & (NEED_EDGE | NEED_NGTDM | NEED_GLDM)) && k.pad < 1) k.pad = 1;
   k.need = need;
   k.keys = (unsigned long long*)(w + o_keys);
   k.slots = (SlotAcc*)(w + o_slots);

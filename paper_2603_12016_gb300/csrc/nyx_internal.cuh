@@ -104,11 +104,19 @@ enum : int {
   N_EDGE = 5,
   Q_NGTDM = Q_EDGE + N_EDGE,          // + k (NGTDM features)
   N_NGTDM = 5,
-  Q_TOTAL = Q_NGTDM + N_NGTDM
+  Q_GLDM = Q_NGTDM + N_NGTDM,         // + k (GLDM features)
+  N_GLDM = 14,
+  Q_TOTAL = Q_GLDM + N_GLDM
 };
 
 // NGTDM features (Table S3 rows 246-250), index within Q_NGTDM
 enum : int { NT_COARSENESS = 0, NT_CONTRAST, NT_BUSYNESS, NT_COMPLEXITY, NT_STRENGTH };
+
+// GLDM features (Table S3 rows 251-264), index within Q_GLDM
+enum : int {
+  GD_SDE = 0, GD_LDE, GD_GLN, GD_DN, GD_DNN, GD_GLV, GD_DV, GD_DE, GD_LGLE, GD_HGLE, GD_SDLGLE, GD_SDHGLE,
+  GD_LDLGLE, GD_LDHGLE
+};
 
 // edge intensity statistics (Table S1 rows 3-7, Table S5), index within Q_EDGE
 enum : int { E_II = 0, E_MAX, E_MIN, E_MEAN, E_STD };
@@ -142,6 +150,7 @@ enum : unsigned {
   NEED_SAVE = 64u,    // keep per-ROI state for the backward pass
   NEED_EDGE = 128u,   // edge intensity statistics
   NEED_NGTDM = 256u,  // neighbourhood grey-tone difference matrix
+  NEED_GLDM = 512u,   // grey-level dependence matrix
 };
 
 // saved per-ROI state for the backward pass (FP64 words per ROI)
@@ -219,12 +228,13 @@ __host__ __device__ inline unsigned big_units2(unsigned long long c) { return (u
 
 // Word offsets (u32 units) of the parts of one big ROI's arena region: pass
 // counters, histograms, per-offset co-occurrence triangles (multi-chunk ROIs),
+// NGTDM per-level sums, GLDM counts (level-major, 9 / 27 dependences),
 // per-chunk partial sums, float sort buffers.  The prefix [0, zero_end) must
 // be zero when the passes start.
 constexpr int BIG_P1 = 38;   // pass-1 partial per chunk: 9 int64 + 5 doubles + 5 edge words (8 bytes each)
 constexpr int BIG_P2 = 98;   // pass-2 partial per chunk: 48 doubles + the edge squared deviations
 struct BigLayout {
-  unsigned long long ctr, hist, vhist, tri, ngt, zero_end, part1, part2, fsort, total;
+  unsigned long long ctr, hist, vhist, tri, ngt, gld, zero_end, part1, part2, fsort, total;
 };
 __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int nsp, unsigned range, unsigned n) {
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
@@ -233,11 +243,12 @@ __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int n
   const bool fsort = (p.need & NEED_ORDER) && range == 0;  // sorted values instead of a value histogram
   BigLayout L;
   unsigned long long o = 0;
-  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [2] NGTDM, [4 + k] offset group k
+  L.ctr = o;      o = (o + 4 + n_off + 3) & ~3ull;  // [0] pass 1, [1] pass 2, [2] NGTDM / GLDM, [4 + k] offset group k
   L.hist = o;     o = (o + ((p.need & NEED_HIST) ? p.hist_bins : 0) + 3) & ~3ull;
   L.vhist = o;    o = (o + range + 3) & ~3ull;
   L.tri = o;      o = (o + (nsp > 1 ? n_off * tri : 0) + 3) & ~3ull;
   L.ngt = o;      o = (o + ((p.need & NEED_NGTDM) ? 3ull * p.ng : 0) + 3) & ~3ull;  // S[ng] int64, then n[ng] u32
+  L.gld = o;      o = (o + ((p.need & NEED_GLDM) ? (unsigned long long)p.ng * (p.ndim == 3 ? 27 : 9) : 0) + 3) & ~3ull;
   L.zero_end = o;
   L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
   L.part2 = o;    o += (unsigned long long)nch * BIG_P2;

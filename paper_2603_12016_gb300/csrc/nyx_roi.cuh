@@ -63,7 +63,7 @@ struct SmemLayout {
     L.tab = o;    o = align16(o + 4 * C::TAB);
     L.rank = o;   o = align16(o + 2 * C::PIX);
     L.hist = o;   o = align16(o + 4 * (hist_bins > 0 ? hist_bins : 1));
-    int marg = 4 * (4 * (ng > 0 ? ng : 1));
+    int marg = 4 * (4 * (ng > 0 ? ng : 1) + 32);  // 4 words per grey level + the GLDM column sums
     int cnts = 4 * (C::NW * 256 + 256);
     L.marg = o;   o = align16(o + (marg > cnts ? marg : cnts));
     L.red = o;    o = align16(o + 8 * C::NW * RED_MAX);
@@ -301,6 +301,32 @@ __device__ inline unsigned run_leader(unsigned key, unsigned invalid) {
   if (!lead || key == invalid) return 0u;
   const unsigned above = lane == 31 ? 0u : (leads & (0xFFFFFFFFu << (lane + 1)));
   return (unsigned)((above ? __ffs(above) - 1 : 32) - lane);
+}
+
+// Add `add` to the count of 16-bit `key` in a shared open-addressing table of
+// (key << 16 | count) words (cap a power of two, at most half full, so the
+// probe ends); a newly occupied slot is appended to cells[].
+__device__ __forceinline__ void tab_add(unsigned* tab, int cap, unsigned key, unsigned add, uint16_t* cells,
+                                        unsigned* ncell) {
+  unsigned h = (key * 2654435761u >> 7) & (unsigned)(cap - 1);
+  for (int probe = 0; probe < cap; ++probe) {
+    const unsigned wv = tab[h];
+    if (wv == 0) {
+      const unsigned old = atomicCAS(&tab[h], 0u, (key << 16) | add);
+      if (old == 0) {
+        cells[atomicAdd(ncell, 1u)] = (uint16_t)h;
+        return;
+      }
+      if ((old >> 16) == key) {
+        atomicAdd(&tab[h], add);
+        return;
+      }
+    } else if ((wv >> 16) == key) {
+      atomicAdd(&tab[h], add);
+      return;
+    }
+    h = (h + 1) & (unsigned)(cap - 1);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -870,6 +896,107 @@ __device__ void ngtdm_features(const KParams& p, double* row, int ng, unsigned* 
   __syncthreads();
 }
 
+// 2^32 / j^2 rounded to nearest (j <= 27), exact in integers
+__device__ inline unsigned long long inv_sq_fx(unsigned j) {
+  const unsigned long long d = (unsigned long long)j * j;
+  return ((1ull << 32) + d / 2) / d;
+}
+
+// GLDM (Table S3 rows 251-264) from per-level sums over the levels a < ng
+// (grey level i = a + 1): lv(a, r, c2, cm) gives the level's pixel count r,
+// sum_j P(i, j) j^2 (c2) and sum_j P(i, j) round(2^32 / j^2) (cm, 2^-32
+// units); col[0..nj) counts the pixels of each dependence j = 1..nj; ent is
+// this thread's share of sum over the cells of P log2 P (2^-24 units).  With
+// N the ROI's pixel count: SDE sum P / j^2 / N, LDE sum P j^2 / N, GLN
+// sum_i r_i^2 / N, DN sum_j col_j^2 / N, DNN DN / N, GLV and DV the
+// variances of i and j under P / N, DE log2 N - sum P log2 P / N, and the
+// grey-level emphases sum P i^{+-2} (j^{+-2}) / N.  Every thread of the block
+// calls it; thread 0 writes the columns.
+template <class C, class A, class LV>
+__device__ void gldm_features(const KParams& p, double* row, int ng, int nj, LV lv, const unsigned* col, long long ent,
+                              double* red, A* sc, long long* s64) {
+  const int tid = threadIdx.x;
+  {
+    long long t[2] = {0, ent};
+    for (int a = tid; a < ng; a += C::NT) {
+      unsigned long long r, c2, cm;
+      lv(a, r, c2, cm);
+      t[0] += (long long)r;
+    }
+    block_sum_i64<C, 2>(t, red, s64);  // ends with a barrier
+  }
+  const long long N = s64[0], E = s64[1];
+  if (N == 0) {
+    if (tid == 0)
+      for (int q = 0; q < N_GLDM; ++q) putA(p, row, Q_GLDM + q, anan<A>());
+    __syncthreads();
+    return;
+  }
+  const A invN = (A)1 / (A)N, Q = (A)(1.0 / 4294967296.0);
+  {
+    A v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = tid; a < ng; a += C::NT) {
+      unsigned long long r, c2, cm;
+      lv(a, r, c2, cm);
+      if (!r) continue;
+      const A i = (A)(a + 1), i2 = i * i, ii2 = (A)1 / i2;
+      const A ra = (A)r, c2a = (A)c2, cma = (A)cm * Q;
+      v[0] += cma;
+      v[1] += c2a;
+      v[2] += ra * ra;
+      v[3] += ra * i;
+      v[4] += ra * i2;
+      v[5] += ra * ii2;
+      v[6] += cma * ii2;
+      v[7] += cma * i2;
+      v[8] += c2a * ii2;
+      v[9] += c2a * i2;
+    }
+    block_sum<C, A, 10>(v, red, sc);
+  }
+  const A mui = sc[3] * invN;
+  {
+    A v[1] = {0};
+    for (int a = tid; a < ng; a += C::NT) {
+      unsigned long long r, c2, cm;
+      lv(a, r, c2, cm);
+      const A d = (A)(a + 1) - mui;
+      v[0] += (A)r * d * d;
+    }
+    block_sum<C, A, 1>(v, red, sc + 10);
+  }
+  if (tid == 0) {
+    A dn = 0, sj = 0;
+    for (int j = 0; j < nj; ++j) {
+      const A c = (A)col[j];
+      dn += c * c;
+      sj += c * (A)(j + 1);
+    }
+    const A muj = sj * invN;
+    A dv = 0;
+    for (int j = 0; j < nj; ++j) {
+      const A d = (A)(j + 1) - muj;
+      dv += (A)col[j] * d * d;
+    }
+    putA(p, row, Q_GLDM + GD_SDE, sc[0] * invN);
+    putA(p, row, Q_GLDM + GD_LDE, sc[1] * invN);
+    putA(p, row, Q_GLDM + GD_GLN, sc[2] * invN);
+    putA(p, row, Q_GLDM + GD_DN, dn * invN);
+    putA(p, row, Q_GLDM + GD_DNN, dn * invN * invN);
+    putA(p, row, Q_GLDM + GD_GLV, sc[10] * invN);
+    putA(p, row, Q_GLDM + GD_DV, dv * invN);
+    // one thread per ROI: the difference of two terms near log2 N in FP64
+    put(p, row, Q_GLDM + GD_DE, log2((double)N) - (double)E * (1.0 / 16777216.0) / (double)N);
+    putA(p, row, Q_GLDM + GD_LGLE, sc[5] * invN);
+    putA(p, row, Q_GLDM + GD_HGLE, sc[4] * invN);
+    putA(p, row, Q_GLDM + GD_SDLGLE, sc[6] * invN);
+    putA(p, row, Q_GLDM + GD_SDHGLE, sc[7] * invN);
+    putA(p, row, Q_GLDM + GD_LDLGLE, sc[8] * invN);
+    putA(p, row, Q_GLDM + GD_LDHGLE, sc[9] * invN);
+  }
+  __syncthreads();
+}
+
 // Per (ROI, offset) GLCM accumulator handed from the accumulation kernels to
 // k_glcm_final: the GN integer sums.  An all-zero record (T = 0) marks an
 // offset without pairs.
@@ -1103,7 +1230,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
   const int64_t per = p.nx * p.ny * p.nz;
   const bool need_glcm = (p.need & NEED_GLCM) != 0;
   const bool need_ngtdm = (p.need & NEED_NGTDM) != 0;
-  const bool need_raster = (p.need & (NEED_GLCM | NEED_EDGE | NEED_NGTDM)) != 0;  // padded raster of the ROI's cells
+  const bool need_gldm = (p.need & NEED_GLDM) != 0;
+  const bool need_levels = need_glcm || need_ngtdm || need_gldm;  // grey levels (GLCM bins) of the pixels
+  const bool need_raster = need_levels || (p.need & NEED_EDGE) != 0;  // padded raster of the ROI's cells
   const int pad = need_raster ? p.pad : 0;
   const A nan = anan<A>();
 
@@ -1218,7 +1347,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
               hb = min(s_fd.div((unsigned)p.hist_bins * dv), (unsigned)(p.hist_bins - 1));
             } else {
               const float xv = Enc<T>::decf(e);
-              if (need_glcm || need_ngtdm) gb = bin_float(xv, fmn, fmx, p.ng);
+              if (need_levels) gb = bin_float(xv, fmn, fmx, p.ng);
               if (need & NEED_HIST) hb = bin_float(xv, fmn, fmx, p.hist_bins);
             }
           }
@@ -1509,7 +1638,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     // the pixel list's coordinates are not needed after the moments: keep
     // each pixel's padded raster index (low 16 bits; cells <= 16,384) and its
     // own bin (high 16 bits) there instead of decoding them per neighbour
-    if (need_glcm || need_ngtdm)
+    if (need_levels)
       for (int i = tid; i < n; i += C::NT) {
         const unsigned c = pc[i];
         const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
@@ -1519,45 +1648,100 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         pc[i] = ci | ((unsigned)raster[ci] << 16);
       }
 
-    // ---- NGTDM (Table S3 rows 246-250) ---------------------------------------
-    // Per pixel the level sum and count of its Chebyshev-1 neighbours in the
-    // ROI (raster cells that are not the sentinel), then n_L and the fixed-
-    // point s_L per level in shared memory.
-    if (need_ngtdm) {
+    // ---- NGTDM (Table S3 rows 246-250) and GLDM (rows 251-264) ----------------
+    // One visit of each pixel's Chebyshev-1 neighbours (raster cells that are
+    // not the sentinel) gives the NGTDM level sum and count and the GLDM
+    // dependence (1 + the neighbours at the pixel's own level).  NGTDM: n_L
+    // and the fixed-point s_L per level in shared memory.  GLDM: the
+    // (level, dependence) cells counted in the shared hash table, with runs of
+    // equal cells in consecutive lanes added once, then per-level sums.
+    if (need_ngtdm || need_gldm) {
       const int ng = p.ng;
       unsigned long long* S = (unsigned long long*)marg;  // [ng] sums of |L - A|, 2^-32 units
       unsigned* nL = (unsigned*)(S + ng);                  // [ng] valid pixels per level
       unsigned* lst = nL + ng;                             // [ng] levels present
-      for (int i = tid; i < ng; i += C::NT) {
-        S[i] = 0;
-        nL[i] = 0;
+      uint16_t* cells = rank;                              // occupied slots of the GLDM table
+      int cap = 64;
+      while (cap < 2 * n && cap < C::TAB) cap <<= 1;
+      if (need_ngtdm)
+        for (int i = tid; i < ng; i += C::NT) {
+          S[i] = 0;
+          nL[i] = 0;
+        }
+      if (need_gldm) {
+        for (int i = tid; i < cap; i += C::NT) tab[i] = 0;
+        if (tid == 0) s_ncell = 0;
       }
       __syncthreads();
-      for (int i = tid; i < n; i += C::NT) {
-        const unsigned w = pc[i];
-        const int ci = (int)(w & 0xFFFFu);
-        int sum = 0, cnt = 0;
-#pragma unroll
-        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz)
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-              if (dx == 0 && dy == 0 && dz == 0) continue;
-              const unsigned b = raster[ci + (dz * Hp + dy) * Wp + dx];
-              if (b != 0xFFFFu) {
-                sum += (int)b + 1;
-                ++cnt;
-              }
-            }
-        if (cnt) {
+      for (int i0 = warp * 32; i0 < n; i0 += C::NT) {
+        const int i = i0 + lane;
+        unsigned key = 0xFFFFFFFFu;
+        if (i < n) {
+          const unsigned w = pc[i];
+          const int ci = (int)(w & 0xFFFFu);
           const unsigned a = w >> 16;
-          atomicAdd(&nL[a], 1u);
-          atomicAdd(&S[a], ngtdm_term((int)a + 1, sum, cnt));
+          int sum = 0, cnt = 0, same = 0;
+#pragma unroll
+          for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+              for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                const unsigned b = raster[ci + (dz * Hp + dy) * Wp + dx];
+                if (b != 0xFFFFu) {
+                  sum += (int)b + 1;
+                  ++cnt;
+                }
+                same += b == a;
+              }
+          if (need_ngtdm && cnt) {
+            atomicAdd(&nL[a], 1u);
+            atomicAdd(&S[a], ngtdm_term((int)a + 1, sum, cnt));
+          }
+          key = (a << 5) | (unsigned)same;  // level, dependence - 1
+        }
+        if (need_gldm) {
+          const unsigned add = run_leader(key, 0xFFFFFFFFu);
+          if (add) tab_add(tab, cap, key, add, cells, &s_ncell);
         }
       }
       __syncthreads();
-      ngtdm_features<C, A>(p, row, ng, nL, S, lst, red, s_sc, s_i64);
+      if (need_ngtdm) ngtdm_features<C, A>(p, row, ng, nL, S, lst, red, s_sc, s_i64);  // ends with a barrier
+      if (need_gldm) {
+        unsigned long long* Cm = (unsigned long long*)marg;  // [ng] sum_j P round(2^32 / j^2)
+        unsigned* R = (unsigned*)(Cm + ng);                   // [ng] pixels per level
+        unsigned* C2 = R + ng;                                // [ng] sum_j P j^2
+        unsigned* col = C2 + ng;                              // [27] pixels per dependence
+        for (int i = tid; i < ng; i += C::NT) {
+          Cm[i] = 0;
+          R[i] = 0;
+          C2[i] = 0;
+        }
+        if (tid < 27) col[tid] = 0;
+        __syncthreads();
+        const int ncell = (int)s_ncell;
+        long long ent = 0;
+        for (int k = tid; k < ncell; k += C::NT) {
+          const unsigned wv = tab[cells[k]];
+          const unsigned cnt = wv & 0xFFFFu, key = wv >> 16;
+          const unsigned a = key >> 5, j = (key & 31u) + 1u;
+          atomicAdd(&R[a], cnt);
+          atomicAdd(&C2[a], cnt * j * j);
+          atomicAdd(&Cm[a], (unsigned long long)cnt * inv_sq_fx(j));
+          atomicAdd(&col[j - 1], cnt);
+          ent += ent_fx<A>(cnt);
+        }
+        __syncthreads();
+        gldm_features<C, A>(
+            p, row, ng, NDIM == 3 ? 27 : 9,
+            [&](int a, unsigned long long& r, unsigned long long& c2, unsigned long long& cm) {
+              r = R[a];
+              c2 = C2[a];
+              cm = Cm[a];
+            },
+            col, ent, red, s_sc, s_i64);
+      }
     }
 
     // ---- GLCM ------------------------------------------------------------------
@@ -1600,27 +1784,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
             // otherwise serialise on one address)
             npair += key != 0xFFFFFFFFu;
             const unsigned add = run_leader(key, 0xFFFFFFFFu);
-            if (add) {
-              unsigned h = (key * 2654435761u >> 7) & (unsigned)(cap - 1);
-              for (int probe = 0; probe < cap; ++probe) {
-                const unsigned wv = tab[h];
-                if (wv == 0) {
-                  const unsigned old = atomicCAS(&tab[h], 0u, (key << 16) | add);
-                  if (old == 0) {
-                    cells[atomicAdd(&s_ncell, 1u)] = (uint16_t)h;
-                    break;
-                  }
-                  if ((old >> 16) == key) {
-                    atomicAdd(&tab[h], add);
-                    break;
-                  }
-                } else if ((wv >> 16) == key) {
-                  atomicAdd(&tab[h], add);
-                  break;
-                }
-                h = (h + 1) & (unsigned)(cap - 1);
-              }
-            }
+            if (add) tab_add(tab, cap, key, add, cells, &s_ncell);
           }
           npair = __reduce_add_sync(0xFFFFFFFFu, npair);
           if (lane == 0 && npair) atomicAdd(&s_npair, npair);

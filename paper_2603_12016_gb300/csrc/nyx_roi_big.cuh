@@ -1077,8 +1077,8 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
   }
 }
 
-// NGTDM of big ROIs (Table S3 rows 246-250): units (ROI, chunk) as in the
-// pass kernels.  A unit stages the bins of its chunk plus a halo of one plane
+// NGTDM (Table S3 rows 246-250) and GLDM (rows 251-264) of big ROIs: units
+// (ROI, chunk) as in the pass kernels.  A unit stages the bins of its chunk plus a halo of one plane
 // and one row on each side (the Chebyshev-1 reach), in the raster of the box
 // padded by one sentinel cell, in shared memory, then sums each ROI voxel's
 // neighbour levels there at fixed displacements; when
@@ -1086,6 +1086,9 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
 // from global memory instead, one plane of up to 9 loads of each issued
 // together.  Per-level counts and fixed-point sums gather in shared memory,
 // go to the ROI's arena arrays, and the last chunk derives the features.
+// The GLDM dependence of a voxel (1 + its neighbours at its own level) comes
+// from the same neighbour visit; the (level, dependence) counts gather in a
+// dense shared array after the window and are added to the ROI's arena.
 constexpr int NGT_WIN = 49152;  // window cells (2-byte bins) in dynamic shared memory
 
 template <class T, int NDIM, class A>
@@ -1093,6 +1096,7 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
   using C = ClassBig;
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* rast = (uint16_t*)smem;  // [NGT_WIN]
+  unsigned* sP = (unsigned*)(smem + 2 * NGT_WIN);  // [ng * nj] GLDM counts (launched with them when needed)
   __shared__ unsigned long long sS[256];
   __shared__ unsigned snL[256], slst[256];
   __shared__ double red[C::NW * RED_MAX];
@@ -1106,6 +1110,8 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
   const int n_big = big_count(ctr);
   const unsigned n_units = big_units1(ctr);
   const int ng = p.ng;
+  const int nj = NDIM == 3 ? 27 : 9;
+  const bool do_ngtdm = (p.need & NEED_NGTDM) != 0, do_gldm = (p.need & NEED_GLDM) != 0;
   const T* img = (const T*)p.img;
   for (unsigned u = blockIdx.x; u < n_units; u += gridDim.x) {
     const int b = big_of_unit(p, n_big, u);
@@ -1118,6 +1124,7 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
     unsigned* reg = p.arena + br.arena;
     unsigned long long* gS = (unsigned long long*)(reg + L.ngt);
     unsigned* gn = (unsigned*)(gS + ng);
+    unsigned* gP = reg + L.gld;  // [ng * nj]
     const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
     const unsigned vmin = r.vmin, vmax = r.vmax;
     const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
@@ -1132,6 +1139,8 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
       sS[i] = 0;
       snL[i] = 0;
     }
+    if (do_gldm)
+      for (int i = tid; i < ng * nj; i += BIG_NT) sP[i] = 0;
     // window in the padded box (one sentinel cell around the bounding box),
     // so that every neighbour is a fixed displacement without bounds tests
     const int Wp = bx.W + 2, Hp = bx.H + 2;
@@ -1179,7 +1188,7 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
         const int here = (int)(pidx(c) - w0);
         const unsigned a = rast[here];
         if (a == SENT) continue;
-        int sum = 0, cnt = 0;
+        int sum = 0, cnt = 0, same = 0;
 #pragma unroll
         for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz)
 #pragma unroll
@@ -1192,11 +1201,13 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
                 sum += (int)bnb + 1;
                 ++cnt;
               }
+              same += bnb == a;
             }
-        if (cnt) {
+        if (do_ngtdm && cnt) {
           atomicAdd(&snL[a], 1u);
           atomicAdd(&sS[a], ngtdm_term((int)a + 1, sum, cnt));
         }
+        if (do_gldm) atomicAdd(&sP[a * nj + same], 1u);
       }
     } else {
       // ---- neighbours from global memory ----
@@ -1204,7 +1215,8 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
       chunk_voxels<T>(p, bx, c0, c1, s_qc + (tid >> 5) * 64, s_qe + (tid >> 5) * 64,
                       [&](bool in, int x, int y, int z, unsigned e) {
         const int64_t here = bx.origin + ((int64_t)z * p.ny + y) * p.nx + x;
-        int sum = 0, cnt = 0;
+        const int a = in ? gbin(e) : -1;
+        int sum = 0, cnt = 0, same = 0;
 #pragma unroll 1
         for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
           if (!in || z + dz < 0 || z + dz >= bx.D) continue;
@@ -1225,30 +1237,69 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
 #pragma unroll
           for (int q = 0; q < 9; ++q)
             if (lab[q] == bx.label) {
-              sum += gbin(Enc<T>::enc(val[q])) + 1;
+              const int lq = gbin(Enc<T>::enc(val[q]));
+              sum += lq + 1;
               ++cnt;
+              same += lq == a;
             }
         }
-        if (cnt) {
-          const int a = gbin(e);
+        if (do_ngtdm && cnt) {
           atomicAdd(&snL[a], 1u);
           atomicAdd(&sS[a], ngtdm_term(a + 1, sum, cnt));
         }
+        if (do_gldm && in) atomicAdd(&sP[a * nj + same], 1u);
       });
     }
     __syncthreads();
-    for (int i = tid; i < ng; i += BIG_NT)
-      if (snL[i]) {
-        atomicAdd(gn + i, snL[i]);
-        atomicAdd(gS + i, sS[i]);
-      }
+    if (do_ngtdm)
+      for (int i = tid; i < ng; i += BIG_NT)
+        if (snL[i]) {
+          atomicAdd(gn + i, snL[i]);
+          atomicAdd(gS + i, sS[i]);
+        }
+    if (do_gldm)
+      for (int i = tid; i < ng * nj; i += BIG_NT)
+        if (sP[i]) atomicAdd(gP + i, sP[i]);
     if (!last_arrival(reg + L.ctr + 2, (unsigned)br.nch, &s_flag)) continue;
-    for (int i = tid; i < ng; i += BIG_NT) {
-      snL[i] = __ldcg(gn + i);
-      sS[i] = __ldcg(gS + i);
+    double* row = p.table + (int64_t)br.item * p.n_col;
+    if (do_ngtdm) {
+      for (int i = tid; i < ng; i += BIG_NT) {
+        snL[i] = __ldcg(gn + i);
+        sS[i] = __ldcg(gS + i);
+      }
+      __syncthreads();
+      ngtdm_features<C, A>(p, row, ng, snL, sS, slst, red, s_sc, s_i64);  // ends with a barrier
     }
-    __syncthreads();
-    ngtdm_features<C, A>(p, p.table + (int64_t)br.item * p.n_col, ng, snL, sS, slst, red, s_sc, s_i64);
+    if (do_gldm) {
+      // column sums and the entropy share from the ROI's dense counts, then
+      // the per-level sums read back by the feature pass
+      unsigned* scol = slst;  // [nj]
+      if (tid < nj) scol[tid] = 0;
+      __syncthreads();
+      long long ent = 0;
+      for (int i = tid; i < ng * nj; i += BIG_NT) {
+        const unsigned c = __ldcg(gP + i);
+        if (c) {
+          atomicAdd(&scol[i % nj], c);
+          ent += ent_fx<A>(c);
+        }
+      }
+      __syncthreads();
+      gldm_features<C, A>(
+          p, row, ng, nj,
+          [&](int a, unsigned long long& r, unsigned long long& c2, unsigned long long& cm) {
+            r = 0;
+            c2 = 0;
+            cm = 0;
+            for (int j = 0; j < nj; ++j) {
+              const unsigned long long c = __ldcg(gP + a * nj + j);
+              r += c;
+              c2 += c * (unsigned long long)((j + 1) * (j + 1));
+              cm += c * inv_sq_fx((unsigned)(j + 1));
+            }
+          },
+          scol, ent, red, s_sc, s_i64);
+    }
   }
 }
 
@@ -1423,8 +1474,9 @@ cudaError_t launch_big_one(const KParams& p, int nsm, cudaStream_t st) {
   if (p.need & NEED_GLCM) {
     if ((e = big_launch<k_big_glcm<T, NDIM, A>>(GLCM_SMEM_BYTES, nsm, p, st)) != cudaSuccess) return e;
   }
-  if (p.need & NEED_NGTDM) {
-    if ((e = big_launch<k_big_ngtdm<T, NDIM, A>>(2 * NGT_WIN, nsm, p, st)) != cudaSuccess) return e;
+  if (p.need & (NEED_NGTDM | NEED_GLDM)) {
+    const int smem = 2 * NGT_WIN + ((p.need & NEED_GLDM) ? 4 * p.ng * (NDIM == 3 ? 27 : 9) : 0);
+    if ((e = big_launch<k_big_ngtdm<T, NDIM, A>>(smem, nsm, p, st)) != cudaSuccess) return e;
   }
   if (p.need & NEED_ORDER) {
     auto kern = k_big_order<T, A>;

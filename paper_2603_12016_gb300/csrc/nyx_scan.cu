@@ -640,7 +640,7 @@ __global__ void k_msort_done(KParams p) {
 // append it to that class's work queue.
 __global__ void k_setup(KParams p) {
   const unsigned n = *p.n_roi;
-  const int pad = (p.need & (NEED_GLCM | NEED_EDGE | NEED_NGTDM)) ? p.pad : 0;
+  const int pad = (p.need & (NEED_GLCM | NEED_EDGE | NEED_NGTDM | NEED_GLDM)) ? p.pad : 0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned long long key = p.sorted_keys[i];
     const int s = g_find(p.keys, p.hmask, key);

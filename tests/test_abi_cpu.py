@@ -45,6 +45,7 @@ def test_feature_ids(nyxlib):
     assert fid("GLCM_ASM") == 51 and fid("GLCM_VARIANCE") == 80
     assert fid("EDGE_INTEGRATED_INTENSITY") == 81 and fid("EDGE_STDDEV_INTENSITY") == 85
     assert fid("NGTDM_COARSENESS") == 86 and fid("NGTDM_STRENGTH") == 90
+    assert fid("GLDM_SDE") == 91 and fid("GLDM_LDHGLE") == 104
     assert fid("NOPE") == -1
     ids = [fid(n) for n in ("MEAN", "INT_HU", "GLCM_CORR")]
     assert len(set(ids)) == 3
