@@ -108,6 +108,20 @@ def test_big_targeted_subset():
     _assert_parity(g, o, 3)
 
 
+@pytest.mark.parametrize("features", [
+    ["GLDM_SDE", "GLDM_GLN", "GLDM_DV", "GLDM_DE", "GLDM_LDHGLE"],
+    ["GLDM_DN", "GLDM_GLV", "GLDM_SDLGLE", "NGTDM_COARSENESS", "NGTDM_STRENGTH"],
+])
+def test_big_gldm_without_glcm(features):
+    """GLDM alone, and GLDM with NGTDM, on multi-block 3D ROIs: the
+    neighbour kernel runs without the GLCM kernels."""
+    w = _ct()
+    ex, g, o = _run(w, features=features, per_offset=False)
+    assert not any(c.startswith("GLCM_") for c in ex.columns)
+    assert all(f in ex.columns for f in features)
+    _assert_parity(g, o, 3)
+
+
 @pytest.mark.parametrize("cfg", ["2d", "3d"])
 def test_big_glcm_counts_bit_exact(cfg):
     from paper_2603_12016_gb300 import nyx

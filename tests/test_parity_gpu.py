@@ -103,6 +103,23 @@ def test_targeted_subset_columns():
     _assert_parity(g, o, 2)
 
 
+GLDM_FEATURES = ["GLDM_" + f for f in ("SDE", "LDE", "GLN", "DN", "DNN", "GLV", "DV", "DE", "LGLE", "HGLE",
+                                          "SDLGLE", "SDHGLE", "LDLGLE", "LDHGLE")]
+
+
+@pytest.mark.parametrize("cfg,ng", [("blobs2d", 8), ("blobs2d", 256), ("blobbatch_small", 16)])
+def test_gldm_only_selection(cfg, ng):
+    """The GLDM selected alone (no GLCM, no NGTDM columns): the neighbour
+    visit and the dependence counts run without the other texture groups,
+    on integer and float images."""
+    w = W.config(cfg)
+    w.params["glcm_levels"] = ng
+    ex, g, o = _run(w, features=GLDM_FEATURES, per_offset=False)
+    assert [c for c in ex.columns if c.startswith("GLDM_")] == GLDM_FEATURES
+    assert not any(c.startswith(("GLCM_", "NGTDM_")) for c in ex.columns)
+    _assert_parity(g, o, w.ndim)
+
+
 # ---------------------------------------------------------------------------
 # bit-exact integer intermediates
 
