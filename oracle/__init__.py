@@ -37,6 +37,7 @@ class OrcCfg(ctypes.Structure):
         ("n_dist", ctypes.c_int),
         ("dist", ctypes.c_int * 8),
         ("hist_bins", ctypes.c_int),
+        ("families", ctypes.c_int),
     ]
 
 
@@ -88,8 +89,14 @@ GLCM_NAMES = ["ASM", "ACOR", "CLUPROM", "CLUSHADE", "CLUTEND", "CONTRAST", "CORR
               "JAVE", "JE", "JMAX", "SUMAVE", "SUMENT", "JVAR", "SUMVAR", "VARIANCE"]
 
 
-def make_cfg(img: np.ndarray, ndim: int, ng: int = 0, dists: Sequence[int] = (1,), hist_bins: int = 256) -> OrcCfg:
-    """img: [batch,] [z,] y, x array.  ndim = 2 or 3 (spatial dims)."""
+FAMILIES = {"glrlm": 1, "glszm": 2}
+
+
+def make_cfg(img: np.ndarray, ndim: int, ng: int = 0, dists: Sequence[int] = (1,), hist_bins: int = 256,
+             families: Sequence[str] = ()) -> OrcCfg:
+    """img: [batch,] [z,] y, x array.  ndim = 2 or 3 (spatial dims).
+    families: optional texture families ("glrlm", "glszm") beyond the ones
+    always computed; they need ng > 0."""
     shape = img.shape
     if ndim == 2:
         if img.ndim == 2:
@@ -111,6 +118,7 @@ def make_cfg(img: np.ndarray, ndim: int, ng: int = 0, dists: Sequence[int] = (1,
     for i, d in enumerate(dists):
         c.dist[i] = int(d)
     c.hist_bins = hist_bins
+    c.families = sum(FAMILIES[f] for f in set(families))
     return c
 
 
@@ -127,14 +135,16 @@ def roi_key(image: int, label: int) -> int:
 
 
 def extract(img: np.ndarray, mask: np.ndarray, ndim: int, ng: int = 0, dists: Sequence[int] = (1,),
-            hist_bins: int = 256, rois: Optional[Iterable[int]] = None, threads: int = 1) -> Dict[str, np.ndarray]:
+            hist_bins: int = 256, rois: Optional[Iterable[int]] = None, threads: int = 1,
+            families: Sequence[str] = ()) -> Dict[str, np.ndarray]:
     """Compute every feature of every ROI (or of the ROI keys in ``rois``,
-    key = image << 32 | label).  Returns {feature name: FP64 array [n_roi]} in
+    key = image << 32 | label), plus the optional texture ``families``
+    ("glrlm", "glszm").  Returns {feature name: FP64 array [n_roi]} in
     ascending key order."""
     img = np.ascontiguousarray(img)
     mask = np.ascontiguousarray(mask, dtype=np.int32)
     assert img.shape == mask.shape
-    cfg = make_cfg(img, ndim, ng, dists, hist_bins)
+    cfg = make_cfg(img, ndim, ng, dists, hist_bins, families)
     names = feature_names(cfg)
     if rois is not None:
         sub = np.ascontiguousarray(np.array(sorted(set(int(r) for r in rois)), dtype=np.int64))

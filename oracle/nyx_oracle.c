@@ -13,7 +13,8 @@
  *     section, pixel-cloud paragraph);
  *   - feature inventory: Table S1 (2D intensity), Table S2 (shape/geometric
  *     and intensity moments, rows 123-135), Table S3 (GLCM rows 140-174,
- *     NGTDM rows 246-250, GLDM rows 251-264),
+ *     NGTDM rows 246-250, GLDM rows 251-264; GLRLM rows from 193 with the
+ *     acronyms of its note, GLSZM rows 228-245, both on request),
  *     Table S5 (3D intensity, 3D GLCM row 361, 3D raw/central moments rows
  *     368/370);
  *   - the paper states IBSI compliance ("IBSI profile", Fig. 5) and defers
@@ -53,6 +54,7 @@ typedef struct {
   int n_dist;            /* number of GLCM distances */
   int dist[ORC_MAX_DIST];
   int hist_bins;         /* bins of the entropy / uniformity histogram */
+  int families;          /* optional texture families: 1 = GLRLM, 2 = GLSZM (0 = neither) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -236,6 +238,10 @@ typedef struct {
   double ngtdm[5];
   /* Table S3 rows 251-264 (GLDM), reading c18 */
   double gldm[14];
+  /* GLRLM (Table S3 rows from 193, acronyms of its note) and GLSZM (rows
+   * 228-245), readings c19 / c20, in the order of SZ_NAMES below */
+  double glrlm[16];
+  double glszm[18];
 } feat_t;
 
 static const char* GLCM_NAMES[ORC_NGLCM] = {
@@ -407,6 +413,14 @@ static void emit_all(const orc_cfg* c, const feat_t* f, emitter* e) {
     static const char* GD_NAMES[14] = {"SDE", "LDE", "GLN", "DN", "DNN", "GLV", "DV",
                                        "DE", "LGLE", "HGLE", "SDLGLE", "SDHGLE", "LDLGLE", "LDHGLE"};
     for (int q = 0; q < 14; ++q) emit(e, f->gldm[q], "GLDM_%s", GD_NAMES[q]);
+    static const char* RL_NAMES[16] = {"SRE", "LRE", "GLNU", "GLNUN", "RLNU", "RLNUN", "RP", "GLV",
+                                       "RV", "RE", "LGLRE", "HGLRE", "SRLGLE", "SRHGLE", "LRLGLE", "LRHGLE"};
+    static const char* SZ_NAMES[18] = {"SAE", "LAE", "GLNU", "GLNUN", "SZNU", "SZNUN", "ZP", "GLV", "ZV",
+                                       "ZE", "LGLZE", "HGLZE", "SALGLE", "SAHGLE", "LALGLE", "LAHGLE", "GLM", "ZSM"};
+    if (c->families & 1)
+      for (int q = 0; q < 16; ++q) emit(e, f->glrlm[q], "GLRLM_%s", RL_NAMES[q]);
+    if (c->families & 2)
+      for (int q = 0; q < 18; ++q) emit(e, f->glszm[q], "GLSZM_%s", SZ_NAMES[q]);
   }
   emit(e, f->edge_ii, "EDGE_INTEGRATED_INTENSITY");
   emit(e, f->edge_max, "EDGE_MAX_INTENSITY");
@@ -587,6 +601,168 @@ static int is_edge(const orc_cfg* c, const int32_t* mask, int64_t base, const in
     if (mask[base + (z * c->ny + y) * c->nx + x] != label) return 1;
   }
   return 0;
+}
+
+/* ---- run-length and size-zone matrices (readings c19, c20) ----
+ * Both matrices count items (runs or zones) by grey level i (1-based GLCM
+ * bin) and size s (run length or zone area).  With M items over Np ROI
+ * pixels, p = count(i, s) / M, and sums over the items:
+ *   [0] small emphasis  sum 1/s^2 / M      [1] large emphasis  sum s^2 / M
+ *   [2] grey-level non-uniformity  sum_i n_i^2 / M,  [3] the same / M
+ *   [4] size non-uniformity  sum_s n_s^2 / M,        [5] the same / M
+ *   [6] percentage M / Np
+ *   [7] grey-level variance  sum p (i - mu_i)^2,  [8] size variance  sum p (s - mu_s)^2
+ *   [9] entropy -sum p log2 p over the non-empty (i, s) cells
+ *   [10] low grey  sum 1/i^2 / M   [11] high grey  sum i^2 / M
+ *   [12] small-low  sum 1/(i^2 s^2) / M   [13] small-high  sum i^2/s^2 / M
+ *   [14] large-low  sum s^2/i^2 / M       [15] large-high  sum i^2 s^2 / M
+ *   [16] grey-level mean mu_i             [17] size mean mu_s
+ * n_i = items of level i, n_s = items of size s. */
+typedef struct {
+  int64_t i, s;
+} item_t;
+
+static int cmp_item(const void* a, const void* b) {
+  const item_t* x = (const item_t*)a;
+  const item_t* y = (const item_t*)b;
+  if (x->i != y->i) return x->i < y->i ? -1 : 1;
+  if (x->s != y->s) return x->s < y->s ? -1 : 1;
+  return 0;
+}
+
+static void size_matrix_features(item_t* it, int64_t M, int ng, int64_t smax, int64_t Np, double* o) {
+  for (int q = 0; q < 18; ++q) o[q] = 0;
+  const double Md = (double)M;
+  double* ni = (double*)calloc((size_t)ng + 1, sizeof(double));
+  double* ns = (double*)calloc((size_t)smax + 1, sizeof(double));
+  double mui = 0, mus = 0;
+  for (int64_t k = 0; k < M; ++k) {
+    const double i = (double)it[k].i, sz = (double)it[k].s, i2 = i * i, s2 = sz * sz;
+    ni[it[k].i] += 1;
+    ns[it[k].s] += 1;
+    o[0] += 1 / s2;
+    o[1] += s2;
+    o[10] += 1 / i2;
+    o[11] += i2;
+    o[12] += 1 / (i2 * s2);
+    o[13] += i2 / s2;
+    o[14] += s2 / i2;
+    o[15] += i2 * s2;
+    mui += i;
+    mus += sz;
+  }
+  mui /= Md;
+  mus /= Md;
+  for (int64_t k = 0; k < M; ++k) {
+    o[7] += ((double)it[k].i - mui) * ((double)it[k].i - mui);
+    o[8] += ((double)it[k].s - mus) * ((double)it[k].s - mus);
+  }
+  for (int a = 0; a <= ng; ++a) o[2] += ni[a] * ni[a];
+  for (int64_t a = 0; a <= smax; ++a) o[4] += ns[a] * ns[a];
+  qsort(it, (size_t)M, sizeof(item_t), cmp_item);
+  for (int64_t k = 0; k < M;) {
+    int64_t e = k;
+    while (e < M && it[e].i == it[k].i && it[e].s == it[k].s) ++e;
+    const double pc = (double)(e - k) / Md;
+    o[9] -= pc * log2(pc);
+    k = e;
+  }
+  const int per_m[18] = {1, 1, 1, 0, 1, 0, 0, 1, 1, 0, 1, 1, 1, 1, 1, 1, 0, 0};
+  for (int q = 0; q < 18; ++q)
+    if (per_m[q]) o[q] /= Md;
+  o[3] = o[2] / Md;
+  o[5] = o[4] / Md;
+  o[6] = Md / (double)Np;
+  o[16] = mui;
+  o[17] = mus;
+  free(ni);
+  free(ns);
+}
+
+/* GLRLM (reading c19) and GLSZM (reading c20) of one ROI.  lev[] holds the
+ * 1-based level of each cell of the ROI's bounding box (W x H x D, x
+ * fastest), 0 outside the ROI; Np is the ROI's pixel count.  GLRLM: for
+ * each GLCM unit direction v, a run is a maximal chain p, p + v, ... of
+ * ROI cells with one level; the 16 features of each direction's matrix are
+ * averaged over the directions.  GLSZM: a zone is a maximal set of ROI
+ * cells of one level connected through their 8 (2D) / 26 (3D) Chebyshev-1
+ * neighbours. */
+static void run_zone_features(const orc_cfg* c, const int* lev, int64_t W, int64_t H, int64_t D, int64_t Np,
+                              feat_t* f) {
+  const int64_t cells = W * H * D;
+  int64_t smax = W > H ? W : H;
+  if (D > smax) smax = D;
+  if (c->families & 1) {
+    item_t* it = (item_t*)malloc(sizeof(item_t) * (size_t)Np);
+    double acc[18] = {0}, o[18];
+    const int nd = n_dirs(c);
+    for (int k = 0; k < nd; ++k) {
+      int dx, dy, dz;
+      unit_dir(c, k, &dx, &dy, &dz);
+      int64_t M = 0;
+      for (int64_t z = 0; z < D; ++z)
+        for (int64_t y = 0; y < H; ++y)
+          for (int64_t x = 0; x < W; ++x) {
+            const int L = lev[(z * H + y) * W + x];
+            if (!L) continue;
+            /* a run starts here when the cell before it is not of level L */
+            const int64_t px = x - dx, py = y - dy, pz = z - dz;
+            if (px >= 0 && py >= 0 && pz >= 0 && px < W && py < H && pz < D && lev[(pz * H + py) * W + px] == L)
+              continue;
+            int64_t len = 0, qx = x, qy = y, qz = z;
+            while (qx >= 0 && qy >= 0 && qz >= 0 && qx < W && qy < H && qz < D && lev[(qz * H + qy) * W + qx] == L) {
+              ++len;
+              qx += dx;
+              qy += dy;
+              qz += dz;
+            }
+            it[M].i = L;
+            it[M].s = len;
+            ++M;
+          }
+      size_matrix_features(it, M, c->ng, smax, Np, o);
+      for (int q = 0; q < 16; ++q) acc[q] += o[q];
+    }
+    for (int q = 0; q < 16; ++q) f->glrlm[q] = acc[q] / nd;
+    free(it);
+  }
+  if (c->families & 2) {
+    item_t* it = (item_t*)malloc(sizeof(item_t) * (size_t)Np);
+    char* seen = (char*)calloc((size_t)cells, 1);
+    int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)Np);
+    int64_t M = 0;
+    const int d3 = c->ndim == 3;
+    for (int64_t start = 0; start < cells; ++start) {
+      if (!lev[start] || seen[start]) continue;
+      const int L = lev[start];
+      int64_t top = 0, size = 0;
+      stack[top++] = start;
+      seen[start] = 1;
+      while (top > 0) {
+        const int64_t q = stack[--top];
+        ++size;
+        const int64_t x = q % W, y = (q / W) % H, z = q / (W * H);
+        for (int ez = -1; ez <= 1; ++ez)
+          for (int ey = -1; ey <= 1; ++ey)
+            for (int ex = -1; ex <= 1; ++ex) {
+              if (!d3 && ez != 0) continue;
+              const int64_t nx = x + ex, ny = y + ey, nz = z + ez;
+              if (nx < 0 || ny < 0 || nz < 0 || nx >= W || ny >= H || nz >= D) continue;
+              const int64_t nb = (nz * H + ny) * W + nx;
+              if (seen[nb] || lev[nb] != L) continue;
+              seen[nb] = 1;
+              stack[top++] = nb;
+            }
+      }
+      it[M].i = L;
+      it[M].s = size;
+      ++M;
+    }
+    size_matrix_features(it, M, c->ng, Np, Np, f->glszm);
+    free(seen);
+    free(stack);
+    free(it);
+  }
 }
 
 static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, const roi_t* r, double img_min,
@@ -973,6 +1149,16 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     for (int q = 0; q < 14; ++q) f->gldm[q] = per_n[q] ? g[q] / Nz : g[q];
     f->gldm[4] = g[3] / (Nz * Nz);
     free(P);
+  }
+
+  /* ---- GLRLM / GLSZM (readings c19, c20), when asked for ---- */
+  if (c->ng > 0 && c->families) {
+    const int64_t W = hi[0] - lo[0] + 1, H = hi[1] - lo[1] + 1, D = hi[2] - lo[2] + 1;
+    int* lev = (int*)calloc((size_t)(W * H * D), sizeof(int));
+    for (int64_t k = 0; k < N; ++k)
+      lev[((X[k][2] - lo[2]) * H + (X[k][1] - lo[1])) * W + (X[k][0] - lo[0])] = bin_of(c, I[k], mn, mx, c->ng) + 1;
+    run_zone_features(c, lev, W, H, D, N, f);
+    free(lev);
   }
   free(I);
   free(X);

@@ -839,3 +839,142 @@ def test_gldm_checkerboard_and_isolated_pixels(orc):
     t = _single(orc, img, mask, ng=4)
     assert t["GLDM_SDE"] == 1.0 and t["GLDM_LDE"] == 1.0
     assert t["GLDM_DN"] == 9.0 and t["GLDM_DNN"] == 1.0 and t["GLDM_DV"] == 0.0
+
+
+# --------------------------------------------------------------------------
+# GLRLM and GLSZM (optional families of the oracle).  Runs along a direction
+# v are the connected components of one level's indicator under a structure
+# holding only the centre and +-v; zones are its components under the full
+# 3^n structure (scipy.ndimage.label).  The features follow from the item
+# lists with np.unique.
+
+RL_COLS = ["GLRLM_" + n for n in ("SRE", "LRE", "GLNU", "GLNUN", "RLNU", "RLNUN", "RP", "GLV", "RV", "RE", "LGLRE",
+                                  "HGLRE", "SRLGLE", "SRHGLE", "LRLGLE", "LRHGLE")]
+SZ_COLS = ["GLSZM_" + n for n in ("SAE", "LAE", "GLNU", "GLNUN", "SZNU", "SZNUN", "ZP", "GLV", "ZV", "ZE", "LGLZE",
+                                  "HGLZE", "SALGLE", "SAHGLE", "LALGLE", "LAHGLE", "GLM", "ZSM")]
+
+
+def _levels(img, mask, label, ng):
+    m = mask == label
+    v = img[m].astype(np.int64)
+    mn, mx = v.min(), v.max()
+    lev = np.zeros(img.shape, dtype=np.int64)
+    lev[m] = np.minimum(ng * (v - mn) // (mx - mn), ng - 1) + 1 if mx > mn else 1
+    return lev
+
+
+def _axes(ndim):
+    """One vector of each of the 4 (2D) / 13 (3D) lattice axes."""
+    out = []
+    for v in np.ndindex(*(3,) * ndim):
+        v = np.array(v) - 1
+        nz = np.flatnonzero(v)
+        if nz.size and v[nz[0]] > 0:
+            out.append(v)
+    return out
+
+
+def _components(lev, structure):
+    import scipy.ndimage as ndi
+
+    lv, sz = [], []
+    for L in np.unique(lev[lev > 0]):
+        lab, n = ndi.label(lev == L, structure=structure)
+        counts = np.bincount(lab.ravel())[1:]
+        lv += [L] * n
+        sz += counts.tolist()
+    return np.array(lv, dtype=np.float64), np.array(sz, dtype=np.float64)
+
+
+def _item_features(i, s, npix):
+    M = i.size
+    _, ni = np.unique(i, return_counts=True)
+    _, ns = np.unique(s, return_counts=True)
+    _, nc = np.unique(np.stack([i, s]), axis=1, return_counts=True)
+    pc = nc / M
+    return [np.mean(1 / s ** 2), np.mean(s ** 2), np.sum(ni ** 2) / M, np.sum(ni ** 2) / M ** 2,
+            np.sum(ns ** 2) / M, np.sum(ns ** 2) / M ** 2, M / npix, np.var(i), np.var(s),
+            -np.sum(pc * np.log2(pc)), np.mean(1 / i ** 2), np.mean(i ** 2), np.mean(1 / (i * s) ** 2),
+            np.mean(i ** 2 / s ** 2), np.mean(s ** 2 / i ** 2), np.mean((i * s) ** 2), np.mean(i), np.mean(s)]
+
+
+def _glrlm_ref(lev, npix):
+    acc = np.zeros(16)
+    axes = _axes(lev.ndim)
+    for v in axes:
+        st = np.zeros((3,) * lev.ndim, dtype=bool)
+        c = np.ones(lev.ndim, dtype=int)
+        st[tuple(c)] = st[tuple(c + v)] = st[tuple(c - v)] = True
+        i, s = _components(lev, st)
+        acc += np.array(_item_features(i, s, npix)[:16])
+    return acc / len(axes)
+
+
+def _glszm_ref(lev, npix):
+    i, s = _components(lev, np.ones((3,) * lev.ndim, dtype=bool))
+    return _item_features(i, s, npix)
+
+
+@pytest.mark.parametrize("ndim,seed,ng", [(2, 1, 4), (2, 2, 32), (3, 3, 3), (3, 4, 16)])
+def test_glrlm_glszm_vs_ndimage_construction(orc, ndim, seed, ng):
+    rng = np.random.default_rng(90 + seed)
+    shape = (26, 29) if ndim == 2 else (9, 11, 12)
+    img = (rng.integers(0, 4, size=shape) * 900 + rng.integers(0, 2, size=shape)).astype(np.uint16)
+    mask = np.zeros(shape, dtype=np.int32)
+    grids = np.meshgrid(*[np.arange(sh) for sh in shape], indexing="ij")
+    for lab in range(1, 5):  # touching blobs, some cut by the border
+        c = [rng.uniform(-1, sh + 1) for sh in shape]
+        r = rng.uniform(2.5, 7.0)
+        mask[sum((g - ci) ** 2 for g, ci in zip(grids, c)) <= r * r] = lab
+    t = orc.extract(img, mask, ndim, ng=ng, families=("glrlm", "glszm"))
+    for row, lab in enumerate(t["LABEL"].astype(int)):
+        lev = _levels(img, mask, lab, ng)
+        npix = np.count_nonzero(mask == lab)
+        for name, v in zip(RL_COLS, _glrlm_ref(lev, npix)):
+            assert t[name][row] == pytest.approx(v, rel=1e-12, abs=1e-12), (lab, name)
+        for name, v in zip(SZ_COLS, _glszm_ref(lev, npix)):
+            assert t[name][row] == pytest.approx(v, rel=1e-12, abs=1e-12), (lab, name)
+
+
+def test_glrlm_line_closed_form(orc):
+    """A constant horizontal line of L pixels: one run of length L along 0
+    degrees, L runs of length 1 along 45, 90 and 135 degrees; each feature is
+    the mean of the four directions (each direction has one level and one
+    run length, so both normalised non-uniformities are 1)."""
+    L = 7
+    img = np.full((3, 10), 50, dtype=np.uint16)
+    mask = np.zeros((3, 10), dtype=np.int32)
+    mask[1, 2:2 + L] = 1
+    t = _single(orc, img, mask, ng=8, families=("glrlm",))
+    want = {"SRE": (1 / L ** 2 + 3) / 4, "LRE": (L ** 2 + 3) / 4, "GLNU": (1 + 3 * L) / 4,
+            "GLNUN": 1.0, "RLNU": (1 + 3 * L) / 4, "RLNUN": 1.0, "RP": (1 / L + 3) / 4,
+            "GLV": 0.0, "RV": 0.0, "RE": 0.0, "LGLRE": 1.0, "HGLRE": 1.0, "SRLGLE": (1 / L ** 2 + 3) / 4,
+            "SRHGLE": (1 / L ** 2 + 3) / 4, "LRLGLE": (L ** 2 + 3) / 4, "LRHGLE": (L ** 2 + 3) / 4}
+    for k, v in want.items():
+        assert t["GLRLM_" + k] == pytest.approx(v, rel=1e-14, abs=1e-15), k
+    assert not any(k.startswith("GLSZM_") for k in t)
+
+
+def test_glszm_checkerboard_is_two_zones(orc):
+    """A two-level checkerboard: with 8-connectivity the diagonal neighbours
+    join every cell of one colour into a single zone (with 4-connectivity
+    each cell would be its own zone)."""
+    n = 6
+    yy, xx = np.mgrid[0:n, 0:n]
+    img = ((xx + yy) % 2).astype(np.uint16)
+    mask = np.ones((n, n), dtype=np.int32)
+    t = _single(orc, img, mask, ng=2, families=("glszm",))
+    s = n * n / 2
+    want = {"ZP": 2 / n ** 2, "SAE": 1 / s ** 2, "LAE": s ** 2, "GLNU": 1.0, "GLNUN": 0.5, "SZNU": 2.0,
+            "SZNUN": 1.0, "ZE": 1.0, "GLV": 0.25, "ZV": 0.0, "GLM": 1.5, "ZSM": s,
+            "LGLZE": (1 + 1 / 4) / 2, "HGLZE": (1 + 4) / 2}
+    for k, v in want.items():
+        assert t["GLSZM_" + k] == pytest.approx(v, rel=1e-14, abs=1e-15), k
+
+
+def test_optional_families_are_off_by_default(orc):
+    img = np.arange(64, dtype=np.uint16).reshape(8, 8)
+    mask = np.ones((8, 8), dtype=np.int32)
+    t = orc.extract(img, mask, 2, ng=8)
+    assert not any(k.startswith(("GLRLM_", "GLSZM_")) for k in t)
+    assert "GLDM_SDE" in t and "NGTDM_COARSENESS" in t
