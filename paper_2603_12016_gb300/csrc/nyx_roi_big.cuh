@@ -30,9 +30,10 @@
 //                into global ones and the last span of the group reduces
 //                them to the per-offset sums that k_glcm_final turns into
 //                features
-//   k_big_ngtdm  units (ROI, chunk): NGTDM neighbourhood sums over a shared-
-//                memory window of bins (chunk plus a plane-and-row halo);
-//                the last unit of an ROI derives the features
+//   k_big_ngtdm  units (ROI, chunk): NGTDM neighbourhood sums and GLDM
+//                dependence counts over a shared-memory window of bins
+//                (chunk plus a plane-and-row halo); the last unit of an ROI
+//                derives the features
 //   k_big_order  ROIs without a value histogram (float images, 16-bit ROIs
 //                whose value range exceeds their pixel count): one block
 //                per ROI compacts the values in raster order and sorts them
@@ -1078,17 +1079,17 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
 }
 
 // NGTDM (Table S3 rows 246-250) and GLDM (rows 251-264) of big ROIs: units
-// (ROI, chunk) as in the pass kernels.  A unit stages the bins of its chunk plus a halo of one plane
-// and one row on each side (the Chebyshev-1 reach), in the raster of the box
-// padded by one sentinel cell, in shared memory, then sums each ROI voxel's
-// neighbour levels there at fixed displacements; when
-// the window exceeds NGT_WIN cells (very wide planes) the neighbours come
-// from global memory instead, one plane of up to 9 loads of each issued
-// together.  Per-level counts and fixed-point sums gather in shared memory,
-// go to the ROI's arena arrays, and the last chunk derives the features.
-// The GLDM dependence of a voxel (1 + its neighbours at its own level) comes
-// from the same neighbour visit; the (level, dependence) counts gather in a
-// dense shared array after the window and are added to the ROI's arena.
+// (ROI, chunk) as in the pass kernels.  A unit stages the bins of its chunk
+// plus a halo of one plane and one row on each side (the Chebyshev-1
+// reach), in the raster of the box padded by one sentinel cell, in shared
+// memory, then visits each ROI voxel's neighbours there at fixed
+// displacements; when the window exceeds NGT_WIN cells (very wide planes)
+// the neighbours come from global memory instead, one plane of up to 9
+// loads of each issued together.  The visit gives the NGTDM level sum and
+// count and the GLDM dependence (1 + the neighbours at the voxel's own
+// level).  NGTDM per-level counts and fixed-point sums, and the dense GLDM
+// (level, dependence) counts stored after the window, gather in shared
+// memory and go to the ROI's arena; the last chunk derives the features.
 constexpr int NGT_WIN = 49152;  // window cells (2-byte bins) in dynamic shared memory
 
 template <class T, int NDIM, class A>
