@@ -62,3 +62,44 @@ def test_params_default_and_validation(nyxlib):
     assert L.nyx_plan_create(None, ctypes.byref(p), ctypes.byref(ctypes.c_void_p())) == 1
     assert L.nyx_create(None, 0) == 1
     assert L.nyx_extract(None, None, None, None, 0, None, 0, None) == 1
+
+
+GEOMETRY = {"LABEL", "IMAGE", "AREA", "BBOX_XMIN", "BBOX_YMIN", "BBOX_ZMIN", "BBOX_WIDTH", "BBOX_HEIGHT", "BBOX_DEPTH",
+            "CENTROID_X", "CENTROID_Y", "CENTROID_Z"}
+
+
+def _feature_of_column(col):
+    """The feature name a table column belongs to: GLCM columns carry a
+    distance (and an offset) suffix, moment columns their indices."""
+    m = re.match(r"(GLCM_[A-Z0-9]+)_D\d+(_[AO]\d+)?$", col)
+    if m:
+        return m.group(1)
+    m = re.match(r"((INT|BIN)_(M|MU|ETA|NU|HU))\d+$", col)
+    if m:
+        return m.group(1)
+    return col
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_oracle_and_library_share_the_feature_registry(nyxlib, ndim):
+    """Every feature column of the oracle maps to a library feature id, and
+    every library feature id has an oracle column: the two sides agree on
+    the feature set by name, without a GPU."""
+    import numpy as np
+
+    import oracle
+
+    shape = (6, 6) if ndim == 2 else (3, 4, 4)
+    img = np.arange(int(np.prod(shape)), dtype=np.uint16).reshape(shape)
+    t = oracle.extract(img, np.ones(shape, dtype=np.int32), ndim, ng=8, dists=(1, 2))
+    ids = set()
+    for col in t:
+        if col in GEOMETRY:
+            continue
+        fid = nyxlib.feature_id(_feature_of_column(col))
+        assert fid >= 0, col
+        ids.add(fid)
+    # 2D has no z centroid; 3D moments have no normalised-raw and Hu families
+    absent = {nyxlib.feature_id("WEIGHTED_CENTROID_Z")} if ndim == 2 else \
+        {nyxlib.feature_id(n) for n in ("INT_NU", "INT_HU", "BIN_NU", "BIN_HU")}
+    assert ids == set(range(105)) - absent
