@@ -296,6 +296,22 @@ def run_scalability_sweep(args) -> int:
     return 0
 
 
+def run_family_sweep(args) -> int:
+    """Device ms of one extraction of the workload with the NGTDM and GLDM
+    families removed from the full feature set and alone."""
+    import torch
+
+    from paper_2603_12016_gb300 import scalability as S
+    from paper_2603_12016_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    w = W.config(args.workload)
+    out = S.family_costs(w, steps=max(args.steps // 5, 20))
+    print(json.dumps({"metric": "feature-family cost (device ms per extraction, no L2 flush)", "unit": "ms",
+                      "workload": w.name, "ms": {k: round(v, 4) for k, v in out.items()}}))
+    return 0
+
+
 def run_soft_sweep(args) -> int:
     """GLCM soft-feature grid: compute time over grey depth (Eq. 2) x nested
     distance sets (Eq. 3), checked for the ordering of Eq. 5, and the Eq. 8
@@ -340,11 +356,12 @@ def main() -> int:
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default class limits")
     ap.add_argument("--class-limits", default=None, help="warp,small,medium pixel limits instead of autotuning")
-    ap.add_argument("--sweep", default=None, choices=["soft", "scalability"],
+    ap.add_argument("--sweep", default=None, choices=["soft", "scalability", "families"],
                     help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
                          "separability grid on labelled texture classes; scalability: time over ROI size x ROI "
                          "count (GPU device, GPU end to end, CPU oracle) and the feature-group cost of an image "
-                         "of 100 ROIs of 100,000 px (one JSON line each, not bench lines)")
+                         "of 100 ROIs of 100,000 px; families: the workload with the NGTDM and GLDM removed "
+                         "and alone (one JSON line each, not bench lines)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -353,6 +370,8 @@ def main() -> int:
         return run_soft_sweep(args)
     if args.sweep == "scalability":
         return run_scalability_sweep(args)
+    if args.sweep == "families":
+        return run_family_sweep(args)
 
     import numpy as np
     import torch

@@ -12,8 +12,16 @@ from typing import Dict, Optional, Sequence
 
 import numpy as np
 
+GLCM = ["GLCM_" + f for f in ("ASM", "ACOR", "CLUPROM", "CLUSHADE", "CLUTEND", "CONTRAST", "CORR", "DIFAVE", "DIFENTRO",
+                                "DIFVAR", "DIS", "ENERGY", "ENTROPY", "HOM1", "HOM2", "IDM", "INFOMEAS1", "INFOMEAS2",
+                                "IDMN", "ID", "IDN", "IV", "JAVE", "JE", "JMAX", "SUMAVE", "SUMENT", "JVAR", "SUMVAR",
+                                "VARIANCE")]
+NGTDM = ["NGTDM_" + f for f in ("COARSENESS", "CONTRAST", "BUSYNESS", "COMPLEXITY", "STRENGTH")]
+GLDM = ["GLDM_" + f for f in ("SDE", "LDE", "GLN", "DN", "DNN", "GLV", "DV", "DE", "LGLE", "HGLE", "SDLGLE", "SDHGLE",
+                              "LDLGLE", "LDHGLE")]
+
 # broad feature groups of the library (Table S1/S5 intensity, Table S2
-# moments, Table S3 GLCM texture)
+# moments, Table S3 texture: GLCM, NGTDM and GLDM); together every feature
 GROUPS = {
     "intensity": ["MEAN", "MIN", "MAX", "RANGE", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS",
                   "KURTOSIS", "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED",
@@ -24,10 +32,7 @@ GROUPS = {
                   "MODE_PROBABILITY", "ENTROPY", "UNIFORMITY", "EDGE_INTEGRATED_INTENSITY", "EDGE_MAX_INTENSITY",
                   "EDGE_MIN_INTENSITY", "EDGE_MEAN_INTENSITY", "EDGE_STDDEV_INTENSITY"],
     "moments": ["INT_M", "INT_MU", "INT_ETA", "INT_NU", "INT_HU", "BIN_M", "BIN_MU", "BIN_ETA", "BIN_NU", "BIN_HU"],
-    "texture": ["GLCM_" + f for f in ("ASM", "ACOR", "CLUPROM", "CLUSHADE", "CLUTEND", "CONTRAST", "CORR", "DIFAVE",
-                                      "DIFENTRO", "DIFVAR", "DIS", "ENERGY", "ENTROPY", "HOM1", "HOM2", "IDM",
-                                      "INFOMEAS1", "INFOMEAS2", "IDMN", "ID", "IDN", "IV", "JAVE", "JE", "JMAX",
-                                      "SUMAVE", "SUMENT", "JVAR", "SUMVAR", "VARIANCE")],
+    "texture": GLCM + NGTDM + GLDM,
 }
 
 
@@ -101,6 +106,16 @@ def time_end_to_end(w, steps: int = 5, warmup: int = 2) -> Dict:
     ex.sync_status()
     return {"ms": float(np.median(ts)), "h2d_bytes": int(w.image.nbytes + w.mask.nbytes),
             "d2h_bytes": int(h_table.numel() * 8)}
+
+
+def family_costs(w, steps: int = 40) -> Dict[str, float]:
+    """Device ms with the NGTDM and GLDM families removed from the full set
+    and alone, which separates a family's own cost from its effect on the
+    rest of the step."""
+    base = GROUPS["intensity"] + GROUPS["moments"] + GLCM
+    cases = {"all": None, "all_but_gldm": base + NGTDM, "all_but_gldm_ngtdm": base, "gldm_only": GLDM,
+             "ngtdm_only": NGTDM, "ngtdm_gldm": NGTDM + GLDM, "intensity_only": GROUPS["intensity"]}
+    return {k: time_device(w, v, steps=steps) for k, v in cases.items()}
 
 
 def group_costs(w, steps: int = 10) -> Dict[str, float]:

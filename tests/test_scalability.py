@@ -35,3 +35,18 @@ def test_timing_helpers_and_groups():
     assert set(g) == {"intensity", "moments", "texture", "all"} and all(v > 0 for v in g.values())
     # every group alone costs no more than the whole feature set (10% timing slack)
     assert max(g["intensity"], g["moments"], g["texture"]) <= 1.1 * g["all"]
+
+
+def test_groups_cover_every_feature_once():
+    """The groups split the library's feature registry: every id in exactly
+    one group (checked against the C ABI's name lookup, no GPU)."""
+    from paper_2603_12016_gb300 import build
+    from paper_2603_12016_gb300 import scalability as S
+
+    build.build()
+    from paper_2603_12016_gb300 import nyx
+
+    ids = [nyx.feature_id(n) for g in S.GROUPS.values() for n in g]
+    assert min(ids) >= 0
+    assert sorted(ids) == list(range(len(ids)))
+    assert set(S.NGTDM + S.GLDM) <= set(S.GROUPS["texture"])
