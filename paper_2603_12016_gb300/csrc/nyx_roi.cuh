@@ -17,6 +17,12 @@
 //       about the exact centroid, raw/normalised moments and Hu invariants
 //       derived per ROI in FP64
 //   histogram features: shared-memory histogram with hist_bins bins
+//   edge intensity statistics (Table S1 rows 3-7): a face-neighbour test on
+//       the raster, folded into the two statistics passes
+//   NGTDM and GLDM (Table S3 rows 246-264): one visit of each pixel's
+//       Chebyshev-1 neighbours in the raster gives the NGTDM level sums and
+//       the GLDM dependence; per-level integer / fixed-point sums in shared
+//       memory, (level, dependence) cells in the shared hash table
 //   GLCM (Table S3 rows 140-174, Table S5 row 361): per offset, a shared
 //       hash table of (min bin, max bin) -> count with warp-aggregated
 //       inserts; features from the marginals p_x, p_{x+y}, p_{x-y} plus one
