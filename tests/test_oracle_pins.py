@@ -978,3 +978,27 @@ def test_optional_families_are_off_by_default(orc):
     t = orc.extract(img, mask, 2, ng=8)
     assert not any(k.startswith(("GLRLM_", "GLSZM_")) for k in t)
     assert "GLDM_SDE" in t and "NGTDM_COARSENESS" in t
+
+
+def test_glrlm_glszm_3d_closed_forms(orc):
+    """3D: a constant line of L voxels along z is one run along the z axis
+    and L runs of length 1 along each of the other 12 directions; a 3D
+    checkerboard under 26-connectivity is two zones (the diagonal
+    neighbours join each colour)."""
+    L = 5
+    img = np.full((7, 3, 3), 10, dtype=np.uint16)
+    mask = np.zeros((7, 3, 3), dtype=np.int32)
+    mask[1:1 + L, 1, 1] = 1
+    t = _single(orc, img, mask, ndim=3, ng=4, families=("glrlm", "glszm"))
+    assert t["GLRLM_RP"] == pytest.approx((1 / L + 12) / 13, rel=1e-14)
+    assert t["GLRLM_LRE"] == pytest.approx((L ** 2 + 12) / 13, rel=1e-14)
+    assert t["GLRLM_SRE"] == pytest.approx((1 / L ** 2 + 12) / 13, rel=1e-14)
+    assert t["GLRLM_RLNU"] == pytest.approx((1 + 12 * L) / 13, rel=1e-14)
+    assert t["GLSZM_ZP"] == pytest.approx(1 / L) and t["GLSZM_ZSM"] == L  # one zone
+    n = 4
+    zz, yy, xx = np.mgrid[0:n, 0:n, 0:n]
+    img = ((xx + yy + zz) % 2).astype(np.uint16)
+    mask = np.ones((n, n, n), dtype=np.int32)
+    t = _single(orc, img, mask, ndim=3, ng=2, families=("glszm",))
+    assert t["GLSZM_ZP"] == pytest.approx(2 / n ** 3) and t["GLSZM_ZSM"] == n ** 3 / 2
+    assert t["GLSZM_ZE"] == pytest.approx(1.0) and t["GLSZM_GLM"] == pytest.approx(1.5)
