@@ -193,6 +193,42 @@ def test_glcm_checkerboard(orc):
             assert t[f"GLCM_{name}_D1_A{a}"] == pytest.approx(val, abs=1e-12), (a, name)
 
 
+def test_glcm_uneven_two_level_golden(orc):
+    """Hand-derived matrices with uneven marginals: DIFENTRO = 1 bit and
+    CLUSHADE = +3/4 / -3/4 pin the log base and the sign of the third-order
+    cluster moment, which the checkerboard cases leave at 0."""
+    gold = json.load(open(os.path.join(GOLD, "glcm_uneven_two_level.json")))
+    for case, spec in gold["cases"].items():
+        f = orc.glcm_features(np.array(spec["P"], dtype=np.float64))
+        for name, val in spec["features"].items():
+            assert f[name] == pytest.approx(val, rel=1e-12, abs=1e-12), (case, name, f[name], val)
+    assert gold["cases"]["offdiag"]["features"]["DIFENTRO"] == 1.0
+    assert gold["cases"]["diagonal_uneven"]["features"]["CLUSHADE"] == 0.75
+    assert gold["cases"]["diagonal_uneven_mirror"]["features"]["CLUSHADE"] == -0.75
+
+
+def test_glcm_difentro_clushade_bruteforce(orc):
+    """DIFENTRO and CLUSHADE of random symmetric matrices (Ng <= 8) against
+    their definitions written out over p_{x-y} and (i + j - 2 mu)."""
+    rng = np.random.default_rng(11)
+    for trial in range(30):
+        ng = int(rng.integers(2, 9))
+        A = rng.integers(0, 6, size=(ng, ng)).astype(np.float64)
+        A[rng.random((ng, ng)) < 0.4] = 0
+        P = A + A.T
+        if P.sum() == 0:
+            continue
+        p = P / P.sum()
+        i = np.arange(1, ng + 1)
+        mu = float((p.sum(1) * i).sum())
+        shade = sum(p[a, b] * (i[a] + i[b] - 2 * mu) ** 3 for a in range(ng) for b in range(ng))
+        pd = np.array([sum(p[a, b] for a in range(ng) for b in range(ng) if abs(a - b) == k) for k in range(ng)])
+        difent = -sum(v * math.log(v, 2) for v in pd if v > 0)
+        f = orc.glcm_features(P)
+        assert f["CLUSHADE"] == pytest.approx(shade, rel=1e-10, abs=1e-12)
+        assert f["DIFENTRO"] == pytest.approx(difent, rel=1e-10, abs=1e-12)
+
+
 def test_glcm_feature_identities(orc):
     rng = np.random.default_rng(5)
     for trial in range(20):
