@@ -39,7 +39,12 @@ __device__ inline void acc_identity(SlotAcc& a) {
 }
 
 // Insert-or-find in the global label table; records new slots in slot_list.
+// Every table holds at least twice the labels its caller accepts, so once
+// more than half of the slots are taken the call ends in a capacity error
+// whatever happens next: give up at once instead of probing a nearly full
+// table slot by slot.
 __device__ int g_find_insert(const KParams& p, unsigned long long key) {
+  if (*(volatile unsigned*)p.n_used > (p.hmask >> 1) + 1u) return -1;
   unsigned h = (unsigned)mix64(key) & p.hmask;
   for (unsigned i = 0; i <= p.hmask; ++i) {
     unsigned long long k = p.keys[h];
@@ -937,6 +942,10 @@ cudaError_t launch_debug_bins(const KParams& p, uint16_t* out, int nsm, cudaStre
 constexpr unsigned NOALLOC_SLOTS = 2u * NYX_NOALLOC_MAX_LABELS;  // load factor <= 0.5
 constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_SLOTS * (8 + sizeof(SlotAcc) + 4) +
                                  2ull * 4 * NYX_NOALLOC_MAX_BATCH + 64;
+static_assert((NOALLOC_SLOTS & (NOALLOC_SLOTS - 1)) == 0, "the label table's probe mask needs a power of two");
+static_assert(sizeof(SlotAcc) % 8 == 0 && (8ull * NOALLOC_SLOTS) % 8 == 0 &&
+                  ((8ull + sizeof(SlotAcc) + 4) * NOALLOC_SLOTS) % 8 == 0 && (8ull * NYX_NOALLOC_MAX_BATCH) % 8 == 0,
+              "every part of the fixed array starts on an 8-byte boundary");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Device address of g_noalloc_scratch per device.  In host code the array's

@@ -87,3 +87,33 @@ def test_noalloc_count_changes_with_input_and_rejects_oversize(nyx):
     assert st == 6  # NYX_ERR_CAPACITY
     # the table recovers on the next call
     assert _noalloc(nyx, p, img, mask) == (0, 2)
+
+
+def test_noalloc_error_paths(nyx):
+    """Errors that the entry point reports without a result: a batch beyond
+    its fixed limit (rejected before any launch), a negative label, and a
+    mask with far more labels than the table holds, which must end with a
+    capacity error after a short scan rather than a table probed slot by
+    slot."""
+    import time
+
+    img = torch.zeros((64, 64), dtype=torch.uint16, device="cuda")
+    mask = torch.zeros((64, 64), dtype=torch.int32, device="cuda")
+    p = _params(nyx, (64, 64), 2, 0)
+    p.batch = 1025  # one more image than NYX_NOALLOC_MAX_BATCH
+    assert _noalloc(nyx, p, img, mask)[0] == 6  # NYX_ERR_CAPACITY
+    p = _params(nyx, (64, 64), 2, 0)
+    mask[3, 5] = -2
+    assert _noalloc(nyx, p, img, mask)[0] == 4  # NYX_ERR_BAD_LABEL
+    mask[3, 5] = 0
+    assert _noalloc(nyx, p, img, mask) == (0, 0)
+    # ~40K distinct labels, 2.5x the limit
+    many = torch.arange(1, 256 * 160 + 1, dtype=torch.int32, device="cuda").reshape(256, 160)
+    pm = _params(nyx, (256, 160), 2, 0)
+    zeros = torch.zeros((256, 160), dtype=torch.uint16, device="cuda")
+    _noalloc(nyx, pm, zeros, many)  # first call: module load and set-up
+    t0 = time.perf_counter()
+    st, _ = _noalloc(nyx, pm, zeros, many)
+    assert st == 6
+    assert time.perf_counter() - t0 < 1.0
+    assert _noalloc(nyx, p, img, mask) == (0, 0)
