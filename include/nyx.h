@@ -175,16 +175,26 @@ nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
  * depends on ROI size and count, Fig. 3f/g).  Every ROI
  * goes to the first class whose pixel limit and padded bounding-box cell
  * capacity it fits: one warp per ROI (capacity 256 px / 1,024 cells), one
- * 128-thread block (1,024 / 4,096), one 256-thread block (8,192 / 16,384),
+ * 128-thread block (1,024 / 4,096), one 512-thread block (8,192 / 16,384),
  * else the multi-block path.  lim_pix[3] sets the pixel limits of the first
  * three classes (0 disables a class; each at most its capacity above).
  * nyx_autotune times the extraction of (d_img, d_mask) under a grid of
- * limits (warp 0/128/256, small 0/512/1024, medium 4096/8192; `reps` timed
- * calls each after one synchronised warm-up), keeps the fastest and returns
- * it in h_lim_pix (host int32[3], may be NULL).  d_table / cap_roi as in
- * nyx_extract.  Synchronises.  Results do not depend on the limits beyond
- * floating-point rounding.  Errors: NYX_ERR_ARG, and those of nyx_extract. */
+ * limits (warp 0/64/128/256, small 0/512/1024, medium 2048/4096/8192), then
+ * under the label scan's tile heights (8/16/32 rows per warp, tiles of 128
+ * columns by 64/128/256 rows) with the best limits; each candidate is timed
+ * as the median of `reps` calls, every call preceded by a 256 MB write that
+ * flushes the L2 cache (allocated and freed inside this call).  It keeps the
+ * fastest setting in the plan and returns the limits in h_lim_pix (host
+ * int32[3], may be NULL); nyx_get_tuning reads the tile height too.
+ * d_table / cap_roi as in nyx_extract.  Synchronises.  Results do not depend
+ * on these settings beyond floating-point rounding.  Errors: NYX_ERR_ARG,
+ * and those of nyx_extract.
+ * nyx_set_tuning / nyx_get_tuning: t[0..2] the class pixel limits as above,
+ * t[3] the scan's rows per warp (0: chosen from the tile count; else 4, 8,
+ * 16 or 32); t is host int32[4].  Errors: NYX_ERR_ARG. */
 nyx_status nyx_set_class_limits(nyx_plan* plan, const int32_t* lim_pix);
+nyx_status nyx_set_tuning(nyx_plan* plan, const int32_t* t);
+nyx_status nyx_get_tuning(const nyx_plan* plan, int32_t* t);
 nyx_status nyx_autotune(nyx_plan* plan, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                         int reps, void* stream, int32_t* h_lim_pix);
 
@@ -268,6 +278,27 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
 #define NYX_N_PHASES 8
 nyx_status nyx_profile_enable(nyx_plan* plan, int slots);
 nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
+
+/* Profiling hook (not in the paper) for the graph-replayed extraction: with
+ * enable != 0 the captured graph of nyx_extract also records, as event
+ * nodes, a begin and an end CUDA event around each phase, on the stream that
+ * phase runs on (the size classes run as parallel branches).  Toggling drops
+ * the cached graphs.  nyx_graph_phase_times waits for the most recent replay
+ * and writes up to NYX_N_GPHASES durations in milliseconds, indexed by
+ * NYX_GPH_*: label scan, key sort + setup, the warp / small / medium block
+ * classes, the multi-block class, the GLCM feature kernel, the statistics
+ * kernel, the table reset, the per-ROI stage (from before the size classes
+ * fork to after they join: the four classes run as concurrent branches, so
+ * each class's own span includes waiting for SMs that the others hold), and
+ * the whole extraction.  A class that receives no ROI reads as about 0.
+ * Errors: NYX_ERR_ARG (null plan/ms), NYX_ERR_STATE (events off or graphs
+ * off), NYX_ERR_CUDA. */
+enum {
+  NYX_GPH_SCAN = 0, NYX_GPH_SORT, NYX_GPH_WARP, NYX_GPH_SMALL, NYX_GPH_MED, NYX_GPH_BIG, NYX_GPH_GLCMF,
+  NYX_GPH_STATSF, NYX_GPH_RESET, NYX_GPH_ROI, NYX_GPH_ALL, NYX_N_GPHASES
+};
+nyx_status nyx_graph_phase_events(nyx_plan* plan, int enable);
+nyx_status nyx_graph_phase_times(nyx_plan* plan, float* ms, int n);
 
 /* Allocation-free ROI count (the paper has no counterpart; this is a service
  * for callers that may not allocate device memory).  Some hosts cannot let a

@@ -7,6 +7,7 @@
 // word (and the ROI count in nyx_count_rois).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -106,6 +107,10 @@ struct nyx_plan {
   int prof_slots = 0;                // ring of event sets, 0 = off
   int64_t prof_count = 0;            // profiled extracts so far
   std::vector<cudaEvent_t> ev;       // prof_slots * (NYX_N_PHASES + 1)
+  // phase events inside the captured graph (begin / end per phase, recorded
+  // on the stream the phase runs on); null when off
+  bool gph = false;
+  cudaEvent_t gev[2 * NYX_N_GPHASES] = {};
   // CUDA graphs of the extraction sequence, keyed by its kernel parameters
   // (a few entries, least recently used replaced)
   static constexpr int NGRAPH = 4;
@@ -407,6 +412,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   // inverse-difference weights per difference level (float and double)
   const int ngw = p.glcm_levels > 0 ? p.glcm_levels : 1;
   const size_t o_wtab_f = take(4ull * 5 * ngw), o_wtab_d = take(8ull * 5 * ngw);
+  // c log2 c (2^-24 units) of the small counts of the entropy sums
+  const size_t o_clog = take(8ull * CLOG_N);
   // per-ROI statistics / moment sums (64 eight-byte slots)
   const size_t o_sacc = take((size_t)mr * 512);
   // key buffer of the key sorts (gathered keys; second run buffer of the multi-block sort)
@@ -494,6 +501,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.sacc = (unsigned char*)(w + o_sacc);
   k.wtab_f = (const float*)(w + o_wtab_f);
   k.wtab_d = (const double*)(w + o_wtab_d);
+  k.clog = (const long long*)(w + o_clog);
   std::vector<float> wf(5ull * ngw);
   std::vector<double> wd(5ull * ngw);
   for (int kk = 0; kk < ngw; ++kk) {
@@ -520,6 +528,11 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   e = cudaMemcpy(pl->d_col_map, pl->col_map.data(), 4ull * Q_TOTAL, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(w + o_wtab_f, wf.data(), 4ull * 5 * ngw, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(w + o_wtab_d, wd.data(), 8ull * 5 * ngw, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<long long> cl(CLOG_N, 0);
+    for (int c = 2; c < CLOG_N; ++c) cl[c] = llround((double)c * log2((double)c) * 16777216.0);
+    e = cudaMemcpy(w + o_clog, cl.data(), 8ull * CLOG_N, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(small, 0, 64);
   if (e == cudaSuccess) {
     e = launch_init_table(k, hcap, 0);
@@ -541,6 +554,8 @@ void nyx_plan_destroy(nyx_plan* pl) {
   if (!pl) return;
   cudaSetDevice(pl->ctx->device);
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : pl->gev)
+    if (e) cudaEventDestroy(e);
   drop_graph(pl);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   for (int i = 0; i < 2; ++i)
@@ -637,16 +652,29 @@ nyx_status nyx_count_rois(nyx_plan* pl, const void* d_img, const int32_t* d_mask
 // The launch sequence of one extraction (label scan, key sort + setup, the
 // four size classes, GLCM features, table reset).  `ev` (profiling) records
 // the phase boundaries; it is null when the sequence is captured.
-static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st);
+static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st,
+                               cudaEvent_t* gev = nullptr);
 
-static nyx_status enqueue_extract(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st) {
+// Graph phase event: begin (end = 0) or end (end = 1) of phase `ph`, as an
+// external event node of the graph being captured on stream `s`.
+static inline cudaError_t gmark(cudaEvent_t* gev, int ph, int end, cudaStream_t s) {
+  return gev ? cudaEventRecordWithFlags(gev[2 * ph + end], s, cudaEventRecordExternal) : cudaSuccess;
+}
+
+static nyx_status enqueue_extract(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st,
+                                  cudaEvent_t* gev = nullptr) {
   nyx_ctx* c = pl->ctx;
   nyx_status s;
   if (k.dbg_glcm) NYX_CUDA(c, cudaMemsetAsync(pl->d_dbg, 0, 4ull * pl->n_off * k.ng * k.ng, st));
+  NYX_CUDA(c, gmark(gev, NYX_GPH_ALL, 0, st));
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[0], st));
+  NYX_CUDA(c, gmark(gev, NYX_GPH_SCAN, 0, st));
   if ((s = run_front(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  NYX_CUDA(c, gmark(gev, NYX_GPH_SCAN, 1, st));
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[1], st));
-  return enqueue_back(pl, k, ev, st);
+  if ((s = enqueue_back(pl, k, ev, st, gev)) != NYX_OK) return s;
+  NYX_CUDA(c, gmark(gev, NYX_GPH_ALL, 1, st));
+  return NYX_OK;
 }
 
 static cudaError_t launch_class(const KParams& k, int cls, int fp64, int nsm, cudaStream_t st) {
@@ -674,14 +702,18 @@ static cudaError_t launch_big(const KParams& k, int fp64, int nsm, cudaStream_t 
 // feature kernel beside the statistics kernel.  Blocks of one class fill the
 // SMs that another class's tail leaves idle.  A class whose pixel limit is 0
 // receives no ROI and is not launched.
-static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st) {
+static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, cudaStream_t st,
+                               cudaEvent_t* gev) {
   nyx_ctx* c = pl->ctx;
   nyx_status s;
+  NYX_CUDA(c, gmark(gev, NYX_GPH_SORT, 0, st));
   if ((s = run_sort_setup(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  NYX_CUDA(c, gmark(gev, NYX_GPH_SORT, 1, st));
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[2], st));
   const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
   const bool fork = ev == nullptr && pl->side[0] != nullptr;
   cudaStream_t s_med = st, s_big = st;
+  NYX_CUDA(c, gmark(gev, NYX_GPH_ROI, 0, st));
   if (fork) {
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[0], st));
     for (int i = 0; i < 2; ++i) NYX_CUDA(c, cudaStreamWaitEvent(pl->side[i], pl->fork_ev[0], 0));
@@ -689,13 +721,18 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     s_big = pl->side[1];
   }
   for (int cls = 0; cls < 3; ++cls) {
-    const cudaError_t e = k.lim_pix[cls] > 0 ? launch_class(k, cls, fp64, c->nsm, cls == 2 ? s_med : st) : cudaSuccess;
+    cudaStream_t sc = cls == 2 ? s_med : st;
+    NYX_CUDA(c, gmark(gev, NYX_GPH_WARP + cls, 0, sc));
+    const cudaError_t e = k.lim_pix[cls] > 0 ? launch_class(k, cls, fp64, c->nsm, sc) : cudaSuccess;
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
+    NYX_CUDA(c, gmark(gev, NYX_GPH_WARP + cls, 1, sc));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
   }
   {
+    NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 0, s_big));
     const cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
+    NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 1, s_big));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[6], st));
   }
   if (fork) {  // join, then fork the GLCM feature kernel
@@ -704,6 +741,7 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[1], 0));
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[2], 0));
   }
+  NYX_CUDA(c, gmark(gev, NYX_GPH_ROI, 1, st));
   // the GLCM feature kernel, the statistics kernel and the label-table reset
   // touch disjoint data: three branches
   const bool reset = !(k.need & NEED_SAVE);  // a pass saved for backward keeps the label table
@@ -719,14 +757,22 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
       s_rs = pl->side[1];
     }
   }
+  NYX_CUDA(c, gmark(gev, NYX_GPH_GLCMF, 0, s_gl));
   if (k.need & NEED_GLCM) {
     cudaError_t e = launch_glcm_final(k, fp64, c->nsm, s_gl);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLCM feature kernel launch failed: %s", cudaGetErrorString(e));
   }
-  if (reset && s_rs != st && (s = run_reset(pl, const_cast<KParams&>(k), s_rs)) != NYX_OK) return s;
+  NYX_CUDA(c, gmark(gev, NYX_GPH_GLCMF, 1, s_gl));
+  if (reset && s_rs != st) {
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 0, s_rs));
+    if ((s = run_reset(pl, const_cast<KParams&>(k), s_rs)) != NYX_OK) return s;
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 1, s_rs));
+  }
   {  // statistics, moments and Hu invariants from the per-ROI sums
+    NYX_CUDA(c, gmark(gev, NYX_GPH_STATSF, 0, st));
     const cudaError_t e = launch_class(k, 3, fp64, c->nsm, st);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "statistics kernel launch failed: %s", cudaGetErrorString(e));
+    NYX_CUDA(c, gmark(gev, NYX_GPH_STATSF, 1, st));
   }
   if (s_gl != st) {
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[4], s_gl));
@@ -737,7 +783,14 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[5], 0));
   }
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
-  if (reset && s_rs == st && (s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+  if (reset && s_rs == st) {
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 0, st));
+    if ((s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 1, st));
+  } else if (!reset) {  // no reset in this sequence: an empty phase
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 0, st));
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 1, st));
+  }
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[NYX_N_PHASES], st));
   return NYX_OK;
 }
@@ -758,7 +811,7 @@ static nyx_status launch_graph(nyx_plan* pl, const KParams& k, cudaStream_t st) 
     if (pl->graph_exec[slot]) cudaGraphExecDestroy(pl->graph_exec[slot]);
     pl->graph_exec[slot] = nullptr;
     NYX_CUDA(c, cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed));
-    const nyx_status s = enqueue_extract(pl, k, nullptr, pl->cap_stream);
+    const nyx_status s = enqueue_extract(pl, k, nullptr, pl->cap_stream, pl->gph ? pl->gev : nullptr);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
     if (s != NYX_OK) {
@@ -937,6 +990,33 @@ nyx_status nyx_graph_captures(const nyx_plan* pl, int64_t* n) {
   return NYX_OK;
 }
 
+// Median device time of `reps` extractions, each after an L2 flush (a
+// write of `flush_bytes` over `flush`), with the plan's current settings.
+static nyx_status time_config(nyx_plan* pl, const void* d_img, const int32_t* d_mask, double* d_table,
+                              int64_t cap_roi, int reps, cudaStream_t st, void* flush, size_t flush_bytes,
+                              cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+  nyx_ctx* c = pl->ctx;
+  nyx_status s = nyx_extract(pl, d_img, d_mask, d_table, cap_roi, nullptr, NYX_SYNC, st);  // warm-up + check
+  if (s != NYX_OK) return s;
+  float t[100];
+  for (int r = 0; r < reps; ++r) {
+    if (flush) NYX_CUDA(c, cudaMemsetAsync(flush, r & 0xFF, flush_bytes, st));
+    NYX_CUDA(c, cudaEventRecord(e0, st));
+    if ((s = nyx_extract(pl, d_img, d_mask, d_table, cap_roi, nullptr, 0, st)) != NYX_OK) return s;
+    NYX_CUDA(c, cudaEventRecord(e1, st));
+    NYX_CUDA(c, cudaEventSynchronize(e1));
+    NYX_CUDA(c, cudaEventElapsedTime(&t[r], e0, e1));
+  }
+  for (int i = 1; i < reps; ++i)  // insertion sort, then the median
+    for (int j = i; j > 0 && t[j] < t[j - 1]; --j) {
+      const float x = t[j];
+      t[j] = t[j - 1];
+      t[j - 1] = x;
+    }
+  *ms_out = t[reps / 2];
+  return NYX_OK;
+}
+
 nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                         int reps, void* stream, int32_t* h_lim_pix) {
   if (!pl || reps < 1 || reps > 100) return NYX_ERR_ARG;
@@ -946,31 +1026,32 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   cudaStream_t st = (cudaStream_t)stream;
   NYX_CUDA(c, cudaSetDevice(c->device));
   // candidate pixel thresholds of the warp, small and medium classes (0 =
-  // class unused); the cell limits stay at each class's staging capacity
-  static const int cw[] = {0, 128, 256}, cs[] = {0, 512, 1024}, cm[] = {4096, 8192};
+  // class unused; the cell limits stay at each class's staging capacity),
+  // then the label scan's rows per warp (tile heights 64 / 128 / 256)
+  static const int cw[] = {0, 64, 128, 256}, cs[] = {0, 512, 1024}, cm[] = {2048, 4096, 8192}, cr[] = {8, 16, 32};
   const int saved_prof = pl->prof_slots;
   pl->prof_slots = 0;
   int best[3] = {pl->kp.lim_pix[0], pl->kp.lim_pix[1], pl->kp.lim_pix[2]};
-  float best_ms = 1e30f;
+  int best_rpt = pl->kp.scan_rpt;
+  float best_ms = 3.0e38f;
+  // an L2-sized write between timed calls, so that every candidate starts
+  // from cold caches as a new image would (an offline call: it may allocate)
+  const size_t flush_bytes = 256ull << 20;
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) flush = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   NYX_CUDA(c, cudaEventCreate(&e0));
   NYX_CUDA(c, cudaEventCreate(&e1));
   for (int a : cw)
     for (int b : cs)
       for (int m : cm) {
+        if ((b && b <= a) || m <= (a > b ? a : b)) continue;
         pl->kp.lim_pix[0] = a;
         pl->kp.lim_pix[1] = b;
         pl->kp.lim_pix[2] = m;
-        s = nyx_extract(pl, d_img, d_mask, d_table, cap_roi, nullptr, NYX_SYNC, stream);  // warm-up + check
-        if (s == NYX_OK) {
-          cudaEventRecord(e0, st);
-          for (int r = 0; r < reps && s == NYX_OK; ++r) s = nyx_extract(pl, d_img, d_mask, d_table, cap_roi, nullptr, 0, stream);
-          cudaEventRecord(e1, st);
-          cudaEventSynchronize(e1);
-        }
-        if (s != NYX_OK) break;
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
+        s = time_config(pl, d_img, d_mask, d_table, cap_roi, reps, st, flush, flush_bytes, e0, e1, &ms);
+        if (s != NYX_OK) break;
         if (ms < best_ms) {
           best_ms = ms;
           best[0] = a;
@@ -978,14 +1059,47 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
           best[2] = m;
         }
       }
+  for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = best[i];
+  if (s == NYX_OK) {
+    best_ms = 3.0e38f;
+    for (int r : cr) {
+      pl->kp.scan_rpt = r;
+      float ms = 0;
+      s = time_config(pl, d_img, d_mask, d_table, cap_roi, reps, st, flush, flush_bytes, e0, e1, &ms);
+      if (s != NYX_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_rpt = r;
+      }
+    }
+  }
+  pl->kp.scan_rpt = best_rpt;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = best[i];
+  if (flush) cudaFree(flush);
   drop_graph(pl);
   pl->prof_slots = saved_prof;
   if (s != NYX_OK) return s;
   if (h_lim_pix)
     for (int i = 0; i < 3; ++i) h_lim_pix[i] = best[i];
+  return NYX_OK;
+}
+
+nyx_status nyx_set_tuning(nyx_plan* pl, const int32_t* t) {
+  if (!pl || !t) return NYX_ERR_ARG;
+  if (t[3] != 0 && t[3] != 4 && t[3] != 8 && t[3] != 16 && t[3] != 32)
+    return fail(pl->ctx, NYX_ERR_ARG, "scan rows per warp must be 0, 4, 8, 16 or 32");
+  nyx_status s = nyx_set_class_limits(pl, t);
+  if (s != NYX_OK) return s;
+  pl->kp.scan_rpt = t[3];
+  drop_graph(pl);
+  return NYX_OK;
+}
+
+nyx_status nyx_get_tuning(const nyx_plan* pl, int32_t* t) {
+  if (!pl || !t) return NYX_ERR_ARG;
+  for (int i = 0; i < 3; ++i) t[i] = pl->kp.lim_pix[i];
+  t[3] = pl->kp.scan_rpt;
   return NYX_OK;
 }
 
@@ -1008,6 +1122,28 @@ nyx_status nyx_profile_enable(nyx_plan* pl, int slots) {
   for (auto& e : pl->ev) NYX_CUDA(pl->ctx, cudaEventCreate(&e));
   pl->prof_slots = slots;
   pl->prof_count = 0;
+  return NYX_OK;
+}
+
+nyx_status nyx_graph_phase_events(nyx_plan* pl, int enable) {
+  if (!pl) return NYX_ERR_ARG;
+  NYX_CUDA(pl->ctx, cudaSetDevice(pl->ctx->device));
+  if (enable && !pl->gev[0])
+    for (auto& e : pl->gev) NYX_CUDA(pl->ctx, cudaEventCreate(&e));
+  if ((enable != 0) != pl->gph) {
+    NYX_CUDA(pl->ctx, cudaDeviceSynchronize());
+    drop_graph(pl);  // the captured sequences differ by the event nodes
+  }
+  pl->gph = enable != 0;
+  return NYX_OK;
+}
+
+nyx_status nyx_graph_phase_times(nyx_plan* pl, float* ms, int n) {
+  if (!pl || !ms) return NYX_ERR_ARG;
+  if (!pl->gph || !pl->use_graphs) return fail(pl->ctx, NYX_ERR_STATE, "graph phase events are off");
+  NYX_CUDA(pl->ctx, cudaEventSynchronize(pl->gev[2 * NYX_GPH_ALL + 1]));
+  for (int i = 0; i < n && i < NYX_N_GPHASES; ++i)
+    NYX_CUDA(pl->ctx, cudaEventElapsedTime(&ms[i], pl->gev[2 * i], pl->gev[2 * i + 1]));
   return NYX_OK;
 }
 

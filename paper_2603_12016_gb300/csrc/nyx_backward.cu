@@ -12,8 +12,9 @@
 //     from the ROI's intensity centroid (weighted centroids, mass
 //     displacement, raw / central / normalised moments, Hu invariants).
 // So the VJP sum_F g_F dF/dI_k collapses, per ROI, to 6 + 1 + 20 numbers.
-// k_bwd_coef computes them in FP64 (one thread per ROI); k_bwd_pixel then
-// streams image and mask once and writes dL/dI (HBM-bound).
+// k_bwd_coef computes them in FP64 (one thread per ROI, no division inside
+// its loops); k_bwd_pixel then streams image and mask once and writes dL/dI
+// (HBM-bound).
 //
 //   d mean / dI_k  = 1/N
 //   d m_j / dI_k   = (j/N) (d_k^(j-1) - m_(j-1)),  m_0 = 1, m_1 = 0
@@ -51,10 +52,11 @@ __device__ inline double dpow(double x, int k) {
   return r;
 }
 
+// binomial coefficient C(n, k) for n <= 3 (the loops below are unrolled, so
+// the lookup folds to a constant; no FP64 division)
 __device__ inline double choose(int n, int k) {
-  double r = 1;
-  for (int i = 0; i < k; ++i) r = r * (n - i) / (i + 1);
-  return r;
+  constexpr double t[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+  return t[n][k];
 }
 
 // m00^(1 + o/2) (2D) or m00^(1 + o/3) (3D) for o = 0..3, from one square or
@@ -123,15 +125,16 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
     double m[7] = {1, 0, m2, m3, m4, m5, m6};
     // ---- intensity polynomial: a[j] multiplies d^j, asg multiplies sgn(d)
     double a[6] = {0, 0, 0, 0, 0, 0}, asg = 0, c[7] = {0, 0, 0, 0, 0, 0, 0};
+    const double iN = 1.0 / N;
     const double var = N > 1 ? m2 * N / (N - 1) : 0.0, sd = sqrt(var);
-    const double rms = sqrt(sv[SV_ENERGY] / N);
-    a[0] += gget(p, g, Q_STATS + S_MEAN) / N + gget(p, g, Q_STATS + S_II);
+    const double rms = sqrt(sv[SV_ENERGY] * iN);
+    a[0] += gget(p, g, Q_STATS + S_MEAN) * iN + gget(p, g, Q_STATS + S_II);
     {
       const double ge = gget(p, g, Q_STATS + S_ENERGY);  // 2 I = 2 (d + mean)
       a[1] += 2 * ge;
       a[0] += 2 * ge * mean;
       if (rms > 0) {
-        const double gr = gget(p, g, Q_STATS + S_RMS) / (N * rms);  // I / (N rms)
+        const double gr = gget(p, g, Q_STATS + S_RMS) * iN / rms;  // I / (N rms)
         a[1] += gr;
         a[0] += gr * mean;
       }
@@ -144,7 +147,7 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
       if (mean != 0) {
         const double gc = gget(p, g, Q_STATS + S_COV);
         c[2] += gc * dstd / mean;
-        a[0] -= gc * sd / (N * mean * mean);
+        a[0] -= gc * sd * iN / (mean * mean);
       }
     }
     if (m2 > 0) {
@@ -166,13 +169,13 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
       c[2] -= 3.0 * gf * m6 * r4;
     }
     for (int j = 2; j <= 6; ++j) {  // c_j (j/N) (d^(j-1) - m_(j-1))
-      a[j - 1] += c[j] * j / N;
-      a[0] -= c[j] * j * m[j - 1] / N;
+      a[j - 1] += c[j] * j * iN;
+      a[0] -= c[j] * j * m[j - 1] * iN;
     }
     {
       const double gm = gget(p, g, Q_STATS + S_MAD);
-      asg += gm / N;
-      a[0] -= gm * sv[SV_SGN] / (N * N);
+      asg += gm * iN;
+      a[0] -= gm * sv[SV_SGN] * iN * iN;
     }
     // ---- spatial polynomial in (u, v, w) = local coords - intensity centroid
     double b[NM];
@@ -181,7 +184,7 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
     const bool wvalid = sumI != 0;
     if (wvalid) {
       const double* MU = sv + SV_MU;
-      const double M00 = sumI;
+      const double M00 = sumI, iM00 = 1.0 / M00;
       // weighted centroids and mass displacement
       const double wc[3] = {sv[SV_X0] + cxyz[0], sv[SV_Y0] + cxyz[1], sv[SV_Z0] + cxyz[2]};
       const double bc[3] = {sv[SV_BX], sv[SV_BY], sv[SV_BZ]};
@@ -202,8 +205,17 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
       double nmu[4], nM[4];  // normalisations of the central and raw moments by order
       gnorm_table<NDIM>(mu00, nmu);
       gnorm_table<NDIM>(M00, nM);
+      const double imu00 = 1.0 / mu00;
+      double inmu[4], inM[4];
+      for (int o = 0; o < 4; ++o) {
+        inmu[o] = 1.0 / nmu[o];
+        inM[o] = 1.0 / nM[o];
+      }
+#pragma unroll
       for (int pp = 0; pp <= 3; ++pp)
+#pragma unroll
         for (int qq = 0; pp + qq <= 3; ++qq)
+#pragma unroll
           for (int rr = 0; rr <= (NDIM == 3 ? 3 - pp - qq : 0); ++rr) {
             const int k = bidx<NDIM>(pp, qq, rr);
             if (pp + qq + rr >= 2) geta[k] += gget(p, g, Q_MOM + F_ETA * 20 + k);
@@ -212,7 +224,7 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
         const int ie[7] = {bidx<2>(2, 0, 0), bidx<2>(0, 2, 0), bidx<2>(1, 1, 0), bidx<2>(3, 0, 0),
                            bidx<2>(2, 1, 0), bidx<2>(1, 2, 0), bidx<2>(0, 3, 0)};
         double e[7], dh[7][7];
-        for (int t = 0; t < 7; ++t) e[t] = MU[ie[t]] / nmu[t < 3 ? 2 : 3];
+        for (int t = 0; t < 7; ++t) e[t] = MU[ie[t]] * inmu[t < 3 ? 2 : 3];
         hu_partials(e, dh);
         for (int h = 0; h < 7; ++h) {
           const double gh = gget(p, g, Q_MOM + F_HU * 20 + h);
@@ -224,50 +236,64 @@ __global__ void k_bwd_coef(KParams p, const double* gtab, float* coef) {
       double gmu[NM];
       double cst = 0;  // constant term from the normalisations
       for (int k = 0; k < NM; ++k) gmu[k] = gget(p, g, Q_MOM + F_MU * 20 + k);
+#pragma unroll
       for (int pp = 0; pp <= 3; ++pp)
+#pragma unroll
         for (int qq = 0; pp + qq <= 3; ++qq)
+#pragma unroll
           for (int rr = 0; rr <= (NDIM == 3 ? 3 - pp - qq : 0); ++rr) {
             const int k = bidx<NDIM>(pp, qq, rr), o = pp + qq + rr;
             if (o >= 2 && geta[k] != 0) {
               const double gam = NDIM == 2 ? 1.0 + o / 2.0 : 1.0 + o / 3.0;
-              const double den = nmu[o];
-              gmu[k] += geta[k] / den;
-              cst -= geta[k] * gam * (MU[k] / den) / mu00;
+              const double iden = inmu[o];
+              gmu[k] += geta[k] * iden;
+              cst -= geta[k] * gam * (MU[k] * iden) * imu00;
             }
           }
+#pragma unroll
       for (int pp = 0; pp <= 3; ++pp)
+#pragma unroll
         for (int qq = 0; pp + qq <= 3; ++qq)
+#pragma unroll
           for (int rr = 0; rr <= (NDIM == 3 ? 3 - pp - qq : 0); ++rr) {
             const int k = bidx<NDIM>(pp, qq, rr);
             const double gk = gmu[k];
             if (gk == 0) continue;
             b[k] += gk;
-            if (pp > 0) b[lin[0]] -= gk * pp * MU[bidx<NDIM>(pp - 1, qq, rr)] / M00;
-            if (qq > 0) b[lin[1]] -= gk * qq * MU[bidx<NDIM>(pp, qq - 1, rr)] / M00;
-            if (NDIM == 3 && rr > 0) b[lin[2]] -= gk * rr * MU[bidx<NDIM>(pp, qq, rr - 1)] / M00;
+            if (pp > 0) b[lin[0]] -= gk * pp * MU[bidx<NDIM>(pp - 1, qq, rr)] * iM00;
+            if (qq > 0) b[lin[1]] -= gk * qq * MU[bidx<NDIM>(pp, qq - 1, rr)] * iM00;
+            if (NDIM == 3 && rr > 0) b[lin[2]] -= gk * rr * MU[bidx<NDIM>(pp, qq, rr - 1)] * iM00;
           }
       // raw and normalised raw moments: x^p y^q z^r expanded about the centroid
+#pragma unroll
       for (int pp = 0; pp <= 3; ++pp)
+#pragma unroll
         for (int qq = 0; pp + qq <= 3; ++qq)
+#pragma unroll
           for (int rr = 0; rr <= (NDIM == 3 ? 3 - pp - qq : 0); ++rr) {
             const int k = bidx<NDIM>(pp, qq, rr), o = pp + qq + rr;
             double gk = gget(p, g, Q_MOM + F_M * 20 + k);
             if (NDIM == 2) {
               const double gn = gget(p, g, Q_MOM + F_NU * 20 + k);
               if (gn != 0) {
-                const double den = nM[o], gam = 1.0 + o / 2.0;
+                const double iden = inM[o], gam = 1.0 + o / 2.0;
                 double Mk = 0;  // raw moment from the central ones
+#pragma unroll
                 for (int i2 = 0; i2 <= pp; ++i2)
+#pragma unroll
                   for (int j2 = 0; j2 <= qq; ++j2)
                     Mk += choose(pp, i2) * choose(qq, j2) * dpow(cxyz[0], pp - i2) * dpow(cxyz[1], qq - j2) *
                           MU[bidx<2>(i2, j2, 0)];
-                gk += gn / den;
-                cst -= gn * gam * (Mk / den) / M00;
+                gk += gn * iden;
+                cst -= gn * gam * (Mk * iden) * iM00;
               }
             }
             if (gk == 0) continue;
+#pragma unroll
             for (int i2 = 0; i2 <= pp; ++i2)
+#pragma unroll
               for (int j2 = 0; j2 <= qq; ++j2)
+#pragma unroll
                 for (int l2 = 0; l2 <= rr; ++l2)
                   b[bidx<NDIM>(i2, j2, l2)] += gk * choose(pp, i2) * choose(qq, j2) * choose(rr, l2) *
                                                dpow(cxyz[0], pp - i2) * dpow(cxyz[1], qq - j2) *
@@ -373,13 +399,22 @@ __global__ void k_bwd_pixel(KParams p, const float* coef, float* gimg) {
   }
 }
 
+// k_bwd_coef is bound by the FP64 pipe (a few FP64 operations per clock per
+// SM), one thread per ROI: one-warp blocks spread the ROIs over every SM
+// instead of filling a few SMs with 128-thread blocks.
+static int coef_blocks(const KParams& p, int nsm) {
+  int64_t nb = (p.cap_roi + 31) / 32;
+  if (nb > 64ll * nsm) nb = 64ll * nsm;
+  return nb < 1 ? 1 : (int)nb;
+}
+
 template <class T>
 cudaError_t launch_bwd_t(const KParams& p, const double* gtab, float* gimg, float* coef, int nsm, cudaStream_t st) {
   if (p.ndim == 3) {
-    k_bwd_coef<3><<<2 * nsm, 128, 0, st>>>(p, gtab, coef);
+    k_bwd_coef<3><<<coef_blocks(p, nsm), 32, 0, st>>>(p, gtab, coef);
     k_bwd_pixel<T, 3><<<8 * nsm, 256, 0, st>>>(p, coef, gimg);
   } else {
-    k_bwd_coef<2><<<2 * nsm, 128, 0, st>>>(p, gtab, coef);
+    k_bwd_coef<2><<<coef_blocks(p, nsm), 32, 0, st>>>(p, gtab, coef);
     k_bwd_pixel<T, 2><<<8 * nsm, 256, 0, st>>>(p, coef, gimg);
   }
   return cudaGetLastError();

@@ -28,6 +28,10 @@ constexpr int MAX_DIRS = 13;
 constexpr int NGLCM = 30;
 constexpr int SORT_CAP = 16384;  // ROIs sortable by the single-block label sort
 constexpr int GI_HOST = 12, GF_HOST = 8;  // GLCM accumulator sizes (int64 sums, float sums)
+// c log2 c (2^-24 units) of every count c < CLOG_N comes from the plan's table,
+// rounded once from FP64: it covers every count of the block classes (at
+// most 2 x 8,192 pairs per offset)
+constexpr int CLOG_N = 16385;
 
 // Per (image, label) accumulator filled by the label scan.  Intensities use
 // an order-preserving uint32 encoding so that min/max are integer atomics.
@@ -214,9 +218,11 @@ struct KParams {
   unsigned char* sacc;             // [max rows] statistics / moment sums for k_stats_final
   const float* wtab_f;             // [Ng][5] inverse-difference weights 1/(1+k), 1/(1+k^2),
   const double* wtab_d;            //   1/(1+k/Ng), 1/(1+k^2/Ng^2), 1/k^2 (0 at k = 0)
+  const long long* clog;           // [CLOG_N] c log2 c in units of 2^-24, rounded once from FP64 (128 KB)
   // label scan over rows [scan_row0, scan_row1) of the batch (scan_row1 = 0:
   // all rows); the mosaic path scans each band of tiles as it arrives
   int64_t scan_row0, scan_row1;
+  int scan_rpt;                    // label-scan rows per warp (tile height / 8); 0: chosen by tile count
   unsigned long long* sort_tmp;    // key buffer of the key sorts [max_rois]
 };
 

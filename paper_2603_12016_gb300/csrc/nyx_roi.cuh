@@ -53,7 +53,7 @@ using ClassW = RoiClass<32, 256, 1024>;    // one warp per ROI
 using ClassS = RoiClass<128, 1024, 4096, 6>;  // 6 blocks of ~37 KB shared memory fit an SM
 using ClassM = RoiClass<512, 8192, 16384>;
 
-constexpr int RED_MAX = 64;  // max values per block reduction
+constexpr int RED_MAX = 32;  // max values per block reduction (and per warp slot of the scratch)
 
 // shared-memory layout (byte offsets), identical on host and device
 struct SmemLayout {
@@ -186,73 +186,171 @@ __device__ inline bool edge_pixel(const uint16_t* raster, unsigned c, int pad, i
 // ----------------------------------------------------------------------------
 // block reductions (results are left in shared memory for every thread)
 
+// Slots of a warp reduce-scatter: the power of two at or above NV (<= 32).
+template <int NV>
+struct RsSlots {
+  static constexpr int S = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+  static constexpr int SH = S == 1 ? 5 : S == 2 ? 4 : S == 4 ? 3 : S == 8 ? 2 : S == 16 ? 1 : 0;  // log2(32 / S)
+};
+
+// Warp sums of NV values by recursive halving (reduce-scatter): at partner
+// distance o each lane keeps half of its slots and adds the other half
+// received from lane ^ o, so S slots cost S - 1 exchanges instead of 5 per
+// value; a butterfly over the remaining lane bits finishes.  Afterwards lane
+// l holds the warp total of slot l >> SH.  Float values travel as
+// compensated (hi, lo) pairs merged with two-sum; the order of operations is
+// fixed, so results are deterministic.
+template <class A, int NV>
+__device__ inline void warp_rs(const A (&v)[NV], A& hi_out, A& lo_out, const A* v_lo = nullptr) {
+  constexpr int S = RsSlots<NV>::S;
+  const int lane = threadIdx.x & 31;
+  A hi[S], lo[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    hi[i] = i < NV ? v[i] : (A)0;
+    lo[i] = (i < NV && v_lo) ? v_lo[i] : (A)0;
+  }
+#pragma unroll
+  for (int h = S / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const A sh = up ? hi[i] : hi[i + h], sl = up ? lo[i] : lo[i + h];
+      const A kh = up ? hi[i + h] : hi[i], kl = up ? lo[i + h] : lo[i];
+      const A rh = __shfl_xor_sync(0xFFFFFFFFu, sh, o);
+      if constexpr (std::is_same<A, float>::value) {
+        const float rl = __shfl_xor_sync(0xFFFFFFFFu, sl, o);
+        float s_, e_;
+        two_sum(kh, rh, s_, e_);
+        hi[i] = s_;
+        lo[i] = __fadd_rn(__fadd_rn(kl, rl), e_);
+      } else {
+        hi[i] = kh + rh;
+        (void)sl;
+        (void)kl;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16 >> (5 - RsSlots<NV>::SH); o >= 1; o >>= 1) {  // lane bits below the slot bits
+    const A rh = __shfl_xor_sync(0xFFFFFFFFu, hi[0], o);
+    if constexpr (std::is_same<A, float>::value) {
+      const float rl = __shfl_xor_sync(0xFFFFFFFFu, lo[0], o);
+      float s_, e_;
+      two_sum(hi[0], rh, s_, e_);
+      hi[0] = s_;
+      lo[0] = __fadd_rn(__fadd_rn(lo[0], rl), e_);
+    } else {
+      hi[0] += rh;
+    }
+  }
+  hi_out = hi[0];
+  lo_out = lo[0];
+}
+
 template <class C, class A, int NV>
 __device__ inline void block_sum(A (&v)[NV], double* scratch, A* out) {
-  static_assert(NV <= RED_MAX, "reduction too wide");
+  static_assert(NV <= RED_MAX && NV <= 32, "reduction too wide");
+  constexpr int SH = RsSlots<NV>::SH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  A hi, lo;
+  warp_rs<A, NV>(v, hi, lo);
+  const int slot = lane >> SH;
   if constexpr (std::is_same<A, float>::value) {
-    // compensated (hi, lo) float pairs through the warp tree and across warps
     float2* sc = (float2*)scratch;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      float hi = v[i], lo = 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
-        const float l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-        float s, e;
-        two_sum(hi, h2, s, e);
-        hi = s;
-        lo = __fadd_rn(__fadd_rn(lo, l2), e);
-      }
-      if (lane == 0) sc[warp * NV + i] = make_float2(hi, lo);
-    }
+    if ((lane & ((1 << SH) - 1)) == 0 && slot < NV) sc[warp * NV + slot] = make_float2(hi, lo);
     __syncthreads();
     for (int i = threadIdx.x; i < NV; i += C::NT) {
-      float hi = 0.f, lo = 0.f;
+      float h = 0.f, l = 0.f;
       for (int w = 0; w < C::NW; ++w) {
         const float2 x = sc[w * NV + i];
-        float s, e;
-        two_sum(hi, x.x, s, e);
-        hi = s;
-        lo = __fadd_rn(__fadd_rn(lo, x.y), e);
+        float s_, e_;
+        two_sum(h, x.x, s_, e_);
+        h = s_;
+        l = __fadd_rn(__fadd_rn(l, x.y), e_);
       }
-      out[i] = __fadd_rn(hi, lo);
+      out[i] = __fadd_rn(h, l);
     }
   } else {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double x = v[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-      if (lane == 0) scratch[warp * NV + i] = x;
-    }
+    (void)lo;
+    if ((lane & ((1 << SH) - 1)) == 0 && slot < NV) scratch[warp * NV + slot] = hi;
     __syncthreads();
     for (int i = threadIdx.x; i < NV; i += C::NT) {
-      double s = 0;
-      for (int w = 0; w < C::NW; ++w) s += scratch[w * NV + i];
-      out[i] = s;
+      double t = 0;
+      for (int w = 0; w < C::NW; ++w) t += scratch[w * NV + i];
+      out[i] = t;
     }
   }
   __syncthreads();
 }
 
+// Kahan-compensated running sum (per thread)
+template <class A>
+struct KSum {
+  A s, c;
+  __device__ KSum() : s(0), c(0) {}
+  __device__ void add(A x) {
+    const A y = x - c;
+    const A t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// Block sums of per-thread compensated float pairs (v.s - v.c), kept as
+// unrounded (hi, lo) pairs: out_hi[i] + out_lo[i] in FP64 is the total to
+// about 2^-44 relative, as the FP64 centroid and mean need.  Results in
+// shared memory for every thread.
+template <class C, int NV>
+__device__ inline void block_sum_pair(const KSum<float> (&v)[NV], double* scratch, float* out_hi, float* out_lo) {
+  static_assert(NV <= RED_MAX && NV <= 32, "reduction too wide");
+  constexpr int SH = RsSlots<NV>::SH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float vh[NV], vl[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    vh[i] = v[i].s;
+    vl[i] = -v[i].c;
+  }
+  float hi, lo;
+  warp_rs<float, NV>(vh, hi, lo, vl);
+  const int slot = lane >> SH;
+  float2* sc = (float2*)scratch;
+  if ((lane & ((1 << SH) - 1)) == 0 && slot < NV) sc[warp * NV + slot] = make_float2(hi, lo);
+  __syncthreads();
+  for (int i = threadIdx.x; i < NV; i += C::NT) {
+    float h = 0.f, l = 0.f;
+    for (int w = 0; w < C::NW; ++w) {
+      const float2 x = sc[w * NV + i];
+      float s_, e_;
+      two_sum(h, x.x, s_, e_);
+      h = s_;
+      l = __fadd_rn(__fadd_rn(l, x.y), e_);
+    }
+    two_sum(h, l, out_hi[i], out_lo[i]);  // normalised pair
+  }
+  __syncthreads();
+}
+
+// (hi, lo) float pair -> the nearest double of hi + lo, and a double split
+// into a float pair
+__device__ inline double pair_d(float hi, float lo) { return f2d(hi) + f2d(lo); }
+
 template <class C, int NV>
 __device__ inline void block_sum_i64(long long (&v)[NV], double* scratch_d, long long* out) {
   long long* scratch = (long long*)scratch_d;
+  constexpr int SH = RsSlots<NV>::SH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    long long x = v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-    if (lane == 0) scratch[warp * NV + i] = x;
-  }
+  long long hi, lo;
+  warp_rs<long long, NV>(v, hi, lo);
+  (void)lo;
+  const int slot = lane >> SH;
+  if ((lane & ((1 << SH) - 1)) == 0 && slot < NV) scratch[warp * NV + slot] = hi;
   __syncthreads();
   for (int i = threadIdx.x; i < NV; i += C::NT) {
-    long long s = 0;
-    for (int w = 0; w < C::NW; ++w) s += scratch[w * NV + i];
-    out[i] = s;
+    long long t = 0;
+    for (int w = 0; w < C::NW; ++w) t += scratch[w * NV + i];
+    out[i] = t;
   }
   __syncthreads();
 }
@@ -475,7 +573,7 @@ __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row
 template <class T, int NDIM, class A>
 __device__ __noinline__ void finalize_stats(const KParams& p, double* row, const A* res_st, int n, A mean, A sumI,
                                             A energy, unsigned vmin, unsigned vmax, int64_t bimg, int x0, int y0,
-                                            int z0, A cx, A cy, A cz, A bx, A by, A bz, bool wvalid, double* save) {
+                                            int z0, const double* cd, bool wvalid, double* save) {
   const A nan = anan<A>();
   const A nA = (A)n;
   const A dl = res_st[0] / nA;
@@ -512,17 +610,19 @@ __device__ __noinline__ void finalize_stats(const KParams& p, double* row, const
   putA(p, row, Q_STATS + S_COV, mean != 0 ? sd / mean : nan);
   putA(p, row, Q_STATS + S_COVERED, imx != imn ? (mx - mn) / (imx - imn) : nan);
   putA(p, row, Q_STATS + S_PIU, (mx + mn) != 0 ? (A)100 * ((A)1 - (mx - mn) / (mx + mn)) : nan);
-  // centroids in image coordinates: integer origin + local offset (exact sum
-  // in FP64 of two exactly converted terms keeps the local precision)
-  put(p, row, Q_CEN_X, i2d(x0) + to_d(bx));
-  put(p, row, Q_CEN_Y, i2d(y0) + to_d(by));
-  put(p, row, Q_CEN_Z, i2d(z0) + to_d(bz));
-  put(p, row, Q_STATS + S_WCX, wvalid ? i2d(x0) + to_d(cx) : to_d(nan));
-  put(p, row, Q_STATS + S_WCY, wvalid ? i2d(y0) + to_d(cy) : to_d(nan));
-  put(p, row, Q_STATS + S_WCZ, wvalid ? i2d(z0) + to_d(cz) : to_d(nan));
-  A md = (cx - bx) * (cx - bx) + (cy - by) * (cy - by);
-  if (NDIM == 3) md += (cz - bz) * (cz - bz);
-  putA(p, row, Q_STATS + S_MD, wvalid ? asqrt(md) : nan);
+  // centroids in image coordinates: integer origin + the FP64 local centroid;
+  // the mass displacement is the FP64 distance of the two centroids, which
+  // nearly coincide in symmetric ROIs (an FP32 difference would keep few
+  // digits of it)
+  put(p, row, Q_CEN_X, i2d(x0) + cd[3]);
+  put(p, row, Q_CEN_Y, i2d(y0) + cd[4]);
+  put(p, row, Q_CEN_Z, i2d(z0) + cd[5]);
+  put(p, row, Q_STATS + S_WCX, wvalid ? i2d(x0) + cd[0] : to_d(nan));
+  put(p, row, Q_STATS + S_WCY, wvalid ? i2d(y0) + cd[1] : to_d(nan));
+  put(p, row, Q_STATS + S_WCZ, wvalid ? i2d(z0) + cd[2] : to_d(nan));
+  double md = (cd[0] - cd[3]) * (cd[0] - cd[3]) + (cd[1] - cd[4]) * (cd[1] - cd[4]);
+  if (NDIM == 3) md += (cd[2] - cd[5]) * (cd[2] - cd[5]);
+  put(p, row, Q_STATS + S_MD, wvalid ? sqrt(md) : to_d(nan));
   if (save) {
     save[SV_N] = i2d(n);
     save[SV_MEAN] = to_d(mean);
@@ -530,12 +630,12 @@ __device__ __noinline__ void finalize_stats(const KParams& p, double* row, const
     save[SV_SGN] = to_d(res_st[7]);
     save[SV_ENERGY] = to_d(energy);
     save[SV_SUMI] = to_d(sumI);
-    save[SV_CX] = to_d(cx);
-    save[SV_CY] = to_d(cy);
-    save[SV_CZ] = to_d(cz);
-    save[SV_BX] = i2d(x0) + to_d(bx);
-    save[SV_BY] = i2d(y0) + to_d(by);
-    save[SV_BZ] = i2d(z0) + to_d(bz);
+    save[SV_CX] = cd[0];
+    save[SV_CY] = cd[1];
+    save[SV_CZ] = cd[2];
+    save[SV_BX] = i2d(x0) + cd[3];
+    save[SV_BY] = i2d(y0) + cd[4];
+    save[SV_BZ] = i2d(z0) + cd[5];
     save[SV_X0] = i2d(x0);
     save[SV_Y0] = i2d(y0);
     save[SV_Z0] = i2d(z0);
@@ -578,7 +678,10 @@ __device__ inline A i128A(__int128 x) {
 //   [12] sum e over p_x      [13] over p_{x+y}     [14] over p_{x-y}  (2^-24)
 //   [15..19] sum_k c_k w(k) over p_{x-y} for w = 1/(1+k), 1/(1+k^2),
 //            1/(1+k/Ng), 1/(1+k^2/Ng^2), 1/k^2 (k >= 1)  (2^-32)
-// Each fixed-point term is one rounding of a value computed in A.
+// In the per (ROI, offset) accumulator handed to k_glcm_final, [9] and
+// [12..14] are replaced by T log2 T minus the sum (gacc_value).
+// Each fixed-point term is one rounding of a value computed in A, except
+// c log2 c of counts below CLOG_N, which the plan tabulates from FP64.
 constexpr int GI = GI_HOST, GF = GF_HOST, GN = GI + GF;
 
 template <class A>
@@ -592,6 +695,29 @@ __device__ inline long long ent_fx(unsigned c) {
   const A ca = (A)c;
   return a2ll(ca * alog2(ca) * (A)16777216);
 }
+// c log2 c (2^-24 units): counts below CLOG_N from the plan's exact table
+// (the hot small counts stay in L1), larger ones computed
+template <class A>
+__device__ inline long long clog_fx(const long long* clog, unsigned c) {
+  return c < (unsigned)CLOG_N ? __ldg(clog + c) : ent_fx<A>(c);
+}
+
+// T log2 T (2^-24 units) of an offset's total mass T: from the table, or in
+// FP64 for the totals of the multi-block class beyond it
+__device__ inline long long tlog_fx(const long long* clog, long long T) {
+  if (T < CLOG_N) return __ldg(clog + T);
+  const double t = (double)T;
+  return __double2ll_rn(t * log2(t) * 16777216.0);
+}
+
+// The value handed to k_glcm_final for GLCM sum t: the entropy sums (joint,
+// p_x, p_{x+y}, p_{x-y}) become the exact integer numerators
+// T log2 T - sum c log2 c of T times the entropy, so that the feature kernel
+// divides without cancellation (each distribution sums to T).
+__device__ inline long long gacc_value(int t, long long v, long long TL) {
+  return (t == 9 || t == 12 || t == 13 || t == 14) ? TL - v : v;
+}
+
 // the inverse-difference family of one difference-marginal entry (c at k),
 // with the weights from the plan's table (rounded once on the host)
 template <class A>
@@ -620,10 +746,13 @@ __device__ inline long long mi_fx(unsigned Cc, long long T, unsigned pa, unsigne
 // GLCM features of one offset (Table S3 rows 140-174): every moment-type
 // feature from exact integer power sums (central moments of the sum /
 // difference / row distributions as exact integer numerators over powers of
-// T), the entropies from the marginal sums.  Accumulates the direction mean.
+// T), the entropies from the marginal sums.  Accumulates the direction mean
+// in FP64.  Every feature is a quotient of exact integer (or fixed-point)
+// numerators, so none cancels in A: the entropies come as T log2 T - sum c
+// log2 c, CORR as its exact covariance and variance numerators.
 template <class A>
 __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const long long* iv, int di, int dir,
-                                           A* gsum) {
+                                           double* f) {
   typedef __int128 I;
   const long long T = iv[0], S1 = iv[1], S2 = iv[2], S3 = iv[3], S4 = iv[4], D1 = iv[5], D2 = iv[6], Q2 = iv[7];
   const A Ta = i128A<A>(T), invT = (A)1 / Ta;
@@ -648,57 +777,57 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
   const A contrast = i128A<A>(D2) * invT;
   const A difave = i128A<A>(D1) * invT;
   const A difvar = i128A<A>(dvn) / T2;
-  const A cov = i128A<A>(cov_n) / (4 * T2);
   const A asmv = i128A<A>(iv[8]) / T2;
-  const A je = alog2(Ta) - i128A<A>(iv[9]) * ((A)(1.0 / 16777216.0) * invT);
-  const A mi = i128A<A>(iv[10]) * ((A)(1.0 / 4294967296.0) * invT);
-  const A E = (A)(1.0 / 16777216.0), Q = (A)(1.0 / 4294967296.0), lT = alog2(Ta);
-  A fv[GF];
-  fv[0] = lT - i128A<A>(iv[12]) * E * invT;  // HX
-  fv[1] = lT - i128A<A>(iv[13]) * E * invT;  // SUMENT
-  fv[2] = lT - i128A<A>(iv[14]) * E * invT;  // DIFENTRO
-  for (int k = 3; k < GF; ++k) fv[k] = i128A<A>(iv[12 + k]) * Q * invT;  // ID, IDM, IDN, IDMN, IV
-  const A hx = fv[0];
-  A f[NGLCM];
-  f[G_ASM] = asmv;
-  f[G_ACOR] = i128A<A>((I)S2 - D2) * invT / 4;
-  f[G_CLUPROM] = cluprom;
-  f[G_CLUSHADE] = clushade;
-  f[G_CLUTEND] = sumvar;
-  f[G_CONTRAST] = contrast;
-  f[G_CORR] = var_n > 0 ? i128A<A>(cov_n) / i128A<A>(var_n) : (A)1;
-  f[G_DIFAVE] = difave;
-  f[G_DIFENTRO] = fv[2];
-  f[G_DIFVAR] = difvar;
-  f[G_DIS] = difave;
-  f[G_ENERGY] = asqrt(asmv);
-  f[G_ENTROPY] = je;
-  f[G_HOM1] = fv[3];
-  f[G_HOM2] = fv[4];
-  f[G_IDM] = fv[4];
+  // entropies from their exact numerators T log2 T - sum c log2 c (2^-24
+  // units), mutual information (2^-32 units) and correlation from exact
+  // integer numerators: no cancellation in A
+  const A E = (A)(1.0 / 16777216.0), Qf = (A)(1.0 / 4294967296.0);
+  const A je = i128A<A>(iv[9]) * E * invT;
+  const A hx = i128A<A>(iv[12]) * E * invT;
+  const A sument = i128A<A>(iv[13]) * E * invT;
+  const A difent = i128A<A>(iv[14]) * E * invT;
+  const A mi = i128A<A>(iv[10]) * Qf * invT;
+  const A corr = var_n > 0 ? i128A<A>(cov_n) / i128A<A>(var_n) : (A)1;
+  A fv[5];
+  for (int k = 0; k < 5; ++k) fv[k] = i128A<A>(iv[15 + k]) * (A)(1.0 / 4294967296.0) * invT;  // ID, IDM, IDN, IDMN, IV
+  f[G_ASM] = to_d(asmv);
+  f[G_ACOR] = to_d(i128A<A>((I)S2 - D2) * invT / 4);
+  f[G_CLUPROM] = to_d(cluprom);
+  f[G_CLUSHADE] = to_d(clushade);
+  f[G_CLUTEND] = to_d(sumvar);
+  f[G_CONTRAST] = to_d(contrast);
+  f[G_CORR] = to_d(corr);
+  f[G_DIFAVE] = to_d(difave);
+  f[G_DIFENTRO] = to_d(difent);
+  f[G_DIFVAR] = to_d(difvar);
+  f[G_DIS] = to_d(difave);
+  f[G_ENERGY] = to_d(asqrt(asmv));
+  f[G_ENTROPY] = to_d(je);
+  f[G_HOM1] = to_d(fv[0]);
+  f[G_HOM2] = to_d(fv[1]);
+  f[G_IDM] = to_d(fv[1]);
   // HXY1 = HXY2 = HX + HY and HX = HY for a symmetric matrix, so
   // HXY - HXY1 = -MI and HXY2 - HXY = MI (mutual information)
-  f[G_INFOMEAS1] = hx > 0 ? -mi / hx : (A)0;
-  const A arg = -aexpm1((A)-2 * mi);  // 1 - exp(-2 MI) without cancellation for small MI
-  f[G_INFOMEAS2] = asqrt(arg > 0 ? arg : (A)0);
-  f[G_IDMN] = fv[6];
-  f[G_ID] = fv[3];
-  f[G_IDN] = fv[5];
-  f[G_IV] = fv[7];
-  f[G_JAVE] = mu;
-  f[G_JE] = je;
-  f[G_JMAX] = i128A<A>(iv[11]) * invT;
-  f[G_SUMAVE] = sumave;
-  f[G_SUMENT] = fv[1];
-  f[G_JVAR] = var;
-  f[G_SUMVAR] = sumvar;
-  f[G_VARIANCE] = var;
-  (void)cov;
-  for (int g = 0; g < NGLCM; ++g) {
-    if (p.per_offset) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
-    gsum[g] += f[g];
+  f[G_INFOMEAS1] = to_d(hx > 0 ? -mi / hx : (A)0);
+  {
+    const A arg = -aexpm1((A)-2 * mi);  // 1 - exp(-2 MI) without cancellation for small MI
+    f[G_INFOMEAS2] = to_d(asqrt(arg > 0 ? arg : (A)0));
   }
-  gsum[NGLCM] += 1;
+  f[G_IDMN] = to_d(fv[3]);
+  f[G_ID] = to_d(fv[0]);
+  f[G_IDN] = to_d(fv[2]);
+  f[G_IV] = to_d(fv[4]);
+  f[G_JAVE] = to_d(mu);
+  f[G_JE] = to_d(je);
+  f[G_JMAX] = to_d(i128A<A>(iv[11]) * invT);
+  f[G_SUMAVE] = to_d(sumave);
+  f[G_SUMENT] = to_d(sument);
+  f[G_JVAR] = to_d(var);
+  f[G_SUMVAR] = to_d(sumvar);
+  f[G_VARIANCE] = to_d(var);
+  if (p.per_offset)
+    for (int g = 0; g < NGLCM; ++g) put(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
+  f[NGLCM] = 1;
 }
 
 // Block reduction of the GN GLCM sums (index 11 is a maximum); results in
@@ -1014,14 +1143,18 @@ __device__ inline void store_gacc(const KParams& p, int64_t item, int oi, const 
 }
 
 // Per-ROI statistics and moment sums handed from the accumulation kernels to
-// k_stats_final (8-byte slots): [0..7] centred power sums, [8..27] intensity
-// moments, [28..47] binary moments, [48] mean, [49] sum I, [50] energy,
-// [51..53] intensity centroid, [54..56] binary centroid (ROI-local).
-constexpr int SACC_SLOTS = 64, SACC_BYTES = 8 * SACC_SLOTS;
+// k_stats_final, in slots of type A: [0..7] centred power sums, [8..27]
+// intensity moments, [28..47] binary moments, [48] mean, [49] sum I, [50]
+// energy, [51..53] the centre of the intensity moment sums, [54..56] that of
+// the binary ones (ROI-local); then, as FP64 at byte SACC_CD, the intensity
+// and binary centroids (ROI-local).
+constexpr int SACC_SLOTS = 64, SACC_BYTES = 8 * SACC_SLOTS, SACC_CD = 464;
 template <class A>
 __device__ inline void store_sacc(const KParams& p, int64_t item, int nm, const A* st, const A* mi, const A* mb,
-                                  A mean, A sumI, A energy, A cx, A cy, A cz, A bx, A by, A bz) {
+                                  A mean, A sumI, A energy, A cx, A cy, A cz, A bx, A by, A bz, const double* cd) {
   A* g = (A*)(p.sacc + (size_t)item * SACC_BYTES);
+  double* gd = (double*)(p.sacc + (size_t)item * SACC_BYTES + SACC_CD);
+  for (int i = threadIdx.x; i < 6; i += blockDim.x) gd[i] = cd[i];
   for (int i = threadIdx.x; i < 57; i += blockDim.x) {
     A v;
     if (i < 8) v = st[i];
@@ -1224,7 +1357,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
   __shared__ unsigned s_rowcnt[C::NW], s_rowbase[C::NW + 1];
   __shared__ FastDiv s_fd;
   __shared__ A s_sc[16];
+  __shared__ A s_sl[8];     // low parts of the pass-1 float sums
   __shared__ double s_sd[4];
+  __shared__ double s_cd[8];  // FP64 intensity and binary centroids (ROI-local)
   __shared__ long long s_i64[GN + 4];  // pass-1 sums, then the GLCM sums of an offset
   __shared__ unsigned s_bnd[4];
   __shared__ A s_pa[12];  // per-ROI scalars: mean (hi, lo), centroids, sums, edge mean
@@ -1414,7 +1549,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
       // [0] sum I, [1] sum x I, [2] sum y I, [3] sum z I, [4] sum x, [5] sum y, [6] sum z, [7] sum I^2,
       // [8] edge count, [9] edge sum d, [10] edge sum d^2 with d = code - vmin (exact for integer images)
       long long s[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-      A fs[6] = {0, 0, 0, 0, 0, 0};  // float images: sum I, x I, y I, z I, I^2, edge sum (I - min)
+      KSum<A> fs[6];  // float images: sum I, x I, y I, z I, I^2, edge sum (I - min), compensated
       for (int i = tid; i < n; i += C::NT) {
         const unsigned c = pc[i];
         const int x = NDIM == 3 ? (int)(c & 2047u) : (int)(c & 0xFFFFu);
@@ -1443,16 +1578,27 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
           }
         } else {
           const A v = decA<T, A>(pv[i]);
-          fs[0] += v;
-          fs[1] += (A)x * v;
-          fs[2] += (A)y * v;
-          fs[3] += (A)z * v;
-          fs[4] += v * v;
-          if (edge) fs[5] += v - (A)fmn;
+          fs[0].add(v);
+          fs[1].add((A)x * v);
+          fs[2].add((A)y * v);
+          fs[3].add((A)z * v);
+          fs[4].add(v * v);
+          if (edge) fs[5].add(v - (A)fmn);
         }
       }
       block_sum_i64<C, 11>(s, red, s_i64);
-      if (!Enc<T>::INTEGER) block_sum<C, A, 6>(fs, red, s_sc);
+      if constexpr (!Enc<T>::INTEGER) {
+        if constexpr (std::is_same<A, float>::value) {
+          block_sum_pair<C, 6>(fs, red, s_sc, s_sl);  // (hi, lo) pairs
+        } else {
+          A f6[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) f6[k] = fs[k].s - fs[k].c;
+          block_sum<C, A, 6>(f6, red, s_sc);
+          if (tid < 6) s_sl[tid] = 0;
+          __syncthreads();
+        }
+      }
       if (do_edge) block_minmax_u32<C>(emn, emx, red);
     }
     // per-ROI scalars by one thread, broadcast through shared memory: mean
@@ -1461,14 +1607,18 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     // when the weights sum to zero) and the binary centroid
     if (tid == 0) {
       const A nA = (A)n;
-      A sI, sxI, syI, szI, en, mhi, mlo;
+      A sI, en, mhi, mlo;
+      // FP64 sums for the centroids and the mean: exact integers (16-bit
+      // images) or the compensated float pairs
+      double dI, dxI, dyI, dzI;
       if (Enc<T>::INTEGER) {
         const long long si = s_i64[0];
         sI = (A)si;
-        sxI = (A)s_i64[1];
-        syI = (A)s_i64[2];
-        szI = (A)s_i64[3];
         en = (A)s_i64[7];
+        dI = (double)si;
+        dxI = (double)s_i64[1];
+        dyI = (double)s_i64[2];
+        dzI = (double)s_i64[3];
         if constexpr (std::is_same<A, float>::value) {
           const long long q = si / n, rm = si - q * n;  // mean = q + rm / n exactly
           mhi = (A)q;
@@ -1480,26 +1630,45 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
         put(p, row, Q_STATS + S_II, i2d(si));
         put(p, row, Q_STATS + S_ENERGY, i2d(s_i64[7]));
       } else {
-        sI = s_sc[0];
-        sxI = s_sc[1];
-        syI = s_sc[2];
-        szI = s_sc[3];
-        en = s_sc[4];
-        mhi = sI / nA;
-        mlo = 0;
-        putA(p, row, Q_STATS + S_II, sI);
+        if constexpr (std::is_same<A, float>::value) {
+          dI = pair_d(s_sc[0], s_sl[0]);
+          dxI = pair_d(s_sc[1], s_sl[1]);
+          dyI = pair_d(s_sc[2], s_sl[2]);
+          dzI = pair_d(s_sc[3], s_sl[3]);
+          const double md = dI / (double)n;  // mean as an unevaluated float pair
+          mhi = (A)md;
+          mlo = (A)(md - (double)mhi);
+        } else {
+          dI = s_sc[0];
+          dxI = s_sc[1];
+          dyI = s_sc[2];
+          dzI = s_sc[3];
+          mhi = s_sc[0] / nA;
+          mlo = 0;
+        }
+        sI = (A)dI;
+        en = s_sc[4] + s_sl[4];
+        put(p, row, Q_STATS + S_II, dI);
         putA(p, row, Q_STATS + S_ENERGY, en);
       }
-      const A bx_ = (A)s_i64[4] / nA, by_ = (A)s_i64[5] / nA, bz_ = (A)s_i64[6] / nA;
-      const bool wv = sI != 0;
+      // centroids in FP64 (ROI-local): binary from the exact coordinate sums,
+      // intensity-weighted from the sums above (binary when sum I = 0)
+      const double bxd = (double)s_i64[4] / n, byd = (double)s_i64[5] / n, bzd = (double)s_i64[6] / n;
+      const bool wv = dI != 0;
+      s_cd[0] = wv ? dxI / dI : bxd;
+      s_cd[1] = wv ? dyI / dI : byd;
+      s_cd[2] = wv ? dzI / dI : bzd;
+      s_cd[3] = bxd;
+      s_cd[4] = byd;
+      s_cd[5] = bzd;
       s_pa[0] = mhi;
       s_pa[1] = mlo;
-      s_pa[2] = wv ? sxI / sI : bx_;
-      s_pa[3] = wv ? syI / sI : by_;
-      s_pa[4] = wv ? szI / sI : bz_;
-      s_pa[5] = bx_;
-      s_pa[6] = by_;
-      s_pa[7] = bz_;
+      s_pa[2] = (A)s_cd[0];  // centres of the moment sums
+      s_pa[3] = (A)s_cd[1];
+      s_pa[4] = (A)s_cd[2];
+      s_pa[5] = (A)bxd;
+      s_pa[6] = (A)byd;
+      s_pa[7] = (A)bzd;
       s_pa[8] = sI;
       s_pa[9] = en;
       if (do_edge) {  // edge statistics (the float deviation follows in pass 2)
@@ -1516,8 +1685,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
           put(p, row, Q_EDGE + E_MIN, i2d((long long)emn - bias));
           putA(p, row, Q_EDGE + E_STD, estd);
         } else {
-          emean = (A)fmn + s_sc[5] / (A)ne;
-          putA(p, row, Q_EDGE + E_II, (A)fmn * (A)ne + s_sc[5]);
+          const A es5 = s_sc[5] + s_sl[5];
+          emean = (A)fmn + es5 / (A)ne;
+          putA(p, row, Q_EDGE + E_II, (A)fmn * (A)ne + es5);
           put(p, row, Q_EDGE + E_MAX, f2d(Enc<T>::decf(emx)));
           put(p, row, Q_EDGE + E_MIN, f2d(Enc<T>::decf(emn)));
         }
@@ -1619,7 +1789,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     // ---- the sums go to k_stats_final (one warp per ROI), which derives the
     // statistics, moments and Hu invariants, so no block waits on that
     // serial arithmetic
-    store_sacc<A>(p, item, NM, res_st, res_mi, res_mb, mu_hi + mu_lo, sumI, energy, cx, cy, cz, bx, by, bz);
+    store_sacc<A>(p, item, NM, res_st, res_mi, res_mb, mu_hi + mu_lo, sumI, energy, cx, cy, cz, bx, by, bz, s_cd);
     (void)wvalid;
 
     // ---- histogram features -------------------------------------------------
@@ -1736,7 +1906,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
           atomicAdd(&C2[a], cnt * j * j);
           atomicAdd(&Cm[a], (unsigned long long)cnt * inv_sq_fx(j));
           atomicAdd(&col[j - 1], cnt);
-          ent += ent_fx<A>(cnt);
+          ent += clog_fx<A>(p.clog, cnt);
         }
         __syncthreads();
         gldm_features<C, A>(
@@ -1751,15 +1921,26 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
     }
 
     // ---- GLCM ------------------------------------------------------------------
-    // Per offset: warp-aggregated inserts into a shared hash table of
-    // (min bin, max bin) -> count that also records its occupied slots, so
-    // every later pass and the clean-up cost O(cells), not O(capacity).
+    // Per offset, three passes and one reduction:
+    //   insert: warp-aggregated inserts of (min bin, max bin) into a shared
+    //     hash table that records its occupied slots, and the row marginal
+    //     p_x (one update per run of equal keys);
+    //   cells: the sum / difference marginals p_{x+y}, p_{x-y}, the sums
+    //     linear in the pairs (powers of i + j and |i - j|, sum i^2), sum C^2,
+    //     sum C log2 C, max C and the mutual information (p_x is final);
+    //   marginals: the entropies of p_x, p_{x+y}, p_{x-y} and the
+    //     inverse-difference family over their nonzero entries, zeroing them
+    //     as it goes, and the clean-up of the table;
+    //   reduction: 19 int64 sums (one maximum) over the warps.
+    // All sums are integers or fixed point, so nothing depends on the order
+    // of the hash table or of the atomics.
     if (need_glcm) {
       const int ng = p.ng;
       unsigned* px = marg;
       unsigned* psum = marg + ng;      // index a + b, 0 .. 2ng-2
       unsigned* pdiff = marg + 3 * ng; // index |a - b|
       uint16_t* cells = rank;          // occupied slots of the table (rank is free until the sort)
+      long long* s_cv = (long long*)red;  // [NW][19] per-warp sums
       int cap = 64;
       while (cap < 2 * n && cap < C::TAB) cap <<= 1;
       const bool dbg = p.dbg_roi == (int64_t)item;
@@ -1790,84 +1971,129 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
             // otherwise serialise on one address)
             npair += key != 0xFFFFFFFFu;
             const unsigned add = run_leader(key, 0xFFFFFFFFu);
-            if (add) tab_add(tab, cap, key, add, cells, &s_ncell);
+            if (add) {
+              tab_add(tab, cap, key, add, cells, &s_ncell);
+              atomicAdd(&px[key >> 8], add);
+              atomicAdd(&px[key & 255u], add);
+            }
           }
           npair = __reduce_add_sync(0xFFFFFFFFu, npair);
           if (lane == 0 && npair) atomicAdd(&s_npair, npair);
           __syncthreads();
           const int ncell = (int)s_ncell;
-          // pass 1 over the cells: marginals and exact integer power sums
-          long long iv[GN];
+          if (ncell == 0) {  // no pair for this offset (nothing was touched): every feature NaN
+            long long z[GN];
+            store_gacc(p, item, oi, z, true);
+            continue;
+          }
+          const long long Tl = 2 * (long long)s_npair;  // total mass of the symmetric matrix
+          // cell pass.  cv: [0..3] sum C k^m (k = i + j), [4..5] sum C d^m
+          // (d = |i - j|), [6] sum C i^2, [7] sum C^2, [8] sum C log2 C (2^-24),
+          // [9] mutual information (2^-32), [10] max C; C = the count of one
+          // matrix cell, each off-diagonal cell standing for its mirror too
+          long long cv[11];
 #pragma unroll
-          for (int k = 0; k < GN; ++k) iv[k] = 0;
-          for (int s = tid; s < ncell; s += C::NT) {
-            const unsigned wv = tab[cells[s]];
+          for (int k = 0; k < 11; ++k) cv[k] = 0;
+          for (int sc = tid; sc < ncell; sc += C::NT) {
+            const unsigned wv = tab[cells[sc]];
             const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
             const unsigned a = key >> 8, b = key & 255u;
-            atomicAdd(&px[a], cnt);
-            atomicAdd(&px[b], cnt);
             atomicAdd(&psum[a + b], 2 * cnt);
             atomicAdd(&pdiff[b - a], 2 * cnt);
             const long long Cm = 2 * (long long)cnt;  // mass of the cell pair (or of the doubled diagonal cell)
             const long long k = a + b + 2, d = b - a, k2 = k * k;
-            iv[0] += Cm;
-            iv[1] += Cm * k;
-            iv[2] += Cm * k2;
-            iv[3] += Cm * k2 * k;
-            iv[4] += Cm * k2 * k2;
-            iv[5] += Cm * d;
-            iv[6] += Cm * d * d;
-            iv[7] += (long long)cnt * ((long long)(a + 1) * (a + 1) + (long long)(b + 1) * (b + 1));
-            const long long Cc = a == b ? 2 * (long long)cnt : (long long)cnt;  // count of one matrix cell
+            cv[0] += Cm * k;
+            cv[1] += Cm * k2;
+            cv[2] += Cm * k2 * k;
+            cv[3] += Cm * k2 * k2;
+            cv[4] += Cm * d;
+            cv[5] += Cm * d * d;
+            cv[6] += (long long)cnt * ((long long)(a + 1) * (a + 1) + (long long)(b + 1) * (b + 1));
+            const long long Cc = a == b ? Cm : (long long)cnt;
             const long long mult = a == b ? 1 : 2;
-            iv[8] += mult * Cc * Cc;
-            iv[9] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
-            iv[11] = Cc > iv[11] ? Cc : iv[11];
+            cv[7] += mult * Cc * Cc;
+            cv[8] += mult * clog_fx<A>(p.clog, (unsigned)Cc);
+            cv[9] += mult * mi_fx<A>((unsigned)Cc, Tl, px[a], px[b]);
+            cv[10] = Cc > cv[10] ? Cc : cv[10];
             if (dbg) {
               p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + b] = (unsigned)Cc;
               p.dbg_glcm[(int64_t)oi * ng * ng + b * ng + a] = (unsigned)Cc;
             }
           }
-          __syncthreads();
-          if (ncell == 0) {  // no pair for this offset: every feature NaN
-            store_gacc(p, item, oi, iv, true);
-            continue;
-          }
-          // pass 2: marginal entropies and inverse differences (exact
-          // fixed-point sums), mutual information over the cells
-          const long long Tl = 2 * (long long)s_npair;  // total mass of the symmetric matrix
-          for (int a = tid; a < ng; a += C::NT)
-            if (px[a]) iv[12] += ent_fx<A>(px[a]);
-          for (int k = tid; k < 2 * ng - 1; k += C::NT)
-            if (psum[k]) iv[13] += ent_fx<A>(psum[k]);
-          for (int k = tid; k < ng; k += C::NT)
-            if (pdiff[k]) {
-              iv[14] += ent_fx<A>(pdiff[k]);
-              invdiff_fx<A>(p, pdiff[k], k, iv);
+          __syncthreads();  // the marginals are final, the table is read
+          // marginal entropies (2^-24) and inverse differences (2^-32) over
+          // the nonzero marginal entries, which are zeroed for the next
+          // offset; the table slots this offset used are cleared
+          long long mv[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) mv[k] = 0;
+          for (int i = tid; i < ng; i += C::NT) {
+            const unsigned c = px[i];
+            if (c) {
+              mv[0] += clog_fx<A>(p.clog, c);
+              px[i] = 0;
             }
-          for (int s = tid; s < ncell; s += C::NT) {
-            const unsigned wv = tab[cells[s]];
-            const unsigned key = wv >> 16, cnt = wv & 0xFFFFu;
-            const unsigned a = key >> 8, b = key & 255u;
-            const long long mult = a == b ? 1 : 2;
-            const unsigned Cc = a == b ? 2 * cnt : cnt;
-            iv[10] += mult * mi_fx<A>(Cc, Tl, px[a], px[b]);
           }
-          // thread t < GN reads back only the sum it wrote itself, and the
-          // next offset starts with a barrier: no trailing one needed
-          block_sum_glcm<C, false>(iv, red, s_i64);
-          store_gacc(p, item, oi, s_i64, false);  // features: k_glcm_final
-          // clean up only what this offset touched (each table slot is read
-          // and cleared by the thread that owns its cell)
-          for (int s = tid; s < ncell; s += C::NT) {
-            const unsigned h = cells[s];
-            const unsigned key = tab[h] >> 16;
-            const unsigned a = key >> 8, b = key & 255u;
-            px[a] = 0;
-            px[b] = 0;
-            psum[a + b] = 0;
-            pdiff[b - a] = 0;
-            tab[h] = 0;
+          for (int i = tid; i < 2 * ng - 1; i += C::NT) {
+            const unsigned c = psum[i];
+            if (c) {
+              mv[1] += clog_fx<A>(p.clog, c);
+              psum[i] = 0;
+            }
+          }
+          for (int i = tid; i < ng; i += C::NT) {
+            const unsigned c = pdiff[i];
+            if (c) {
+              mv[2] += clog_fx<A>(p.clog, c);
+              long long w5[GN];
+#pragma unroll
+              for (int q = 15; q < 20; ++q) w5[q] = 0;
+              invdiff_fx<A>(p, c, i, w5);
+#pragma unroll
+              for (int q = 0; q < 5; ++q) mv[3 + q] += w5[15 + q];
+              pdiff[i] = 0;
+            }
+          }
+          for (int sc = tid; sc < ncell; sc += C::NT) tab[cells[sc]] = 0;
+          // per-warp sums (reduce-scatter), [warp][0..10] cell values (10: max),
+          // [warp][11..18] marginal values
+          {
+            long long mx = cv[10];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+              mx = y > mx ? y : mx;
+            }
+            long long v10[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k) v10[k] = cv[k];
+            long long hi, lo;
+            warp_rs<long long, 10>(v10, hi, lo);
+            constexpr int SH = RsSlots<10>::SH;
+            int slot = lane >> SH;
+            if ((lane & ((1 << SH) - 1)) == 0 && slot < 10) s_cv[warp * 19 + slot] = hi;
+            if (lane == 0) s_cv[warp * 19 + 10] = mx;
+            warp_rs<long long, 8>(mv, hi, lo);
+            (void)lo;
+            constexpr int SH8 = RsSlots<8>::SH;
+            slot = lane >> SH8;
+            if ((lane & ((1 << SH8) - 1)) == 0) s_cv[warp * 19 + 11 + slot] = hi;
+          }
+          __syncthreads();
+          if (tid < GN) {  // combine and hand the sums to k_glcm_final
+            long long v;
+            if (tid == 0) {
+              v = Tl;
+            } else {
+              const int j = tid - 1;  // slot: 0..10 cell values, 11..18 marginal values
+              v = s_cv[j];
+              for (int w = 1; w < C::NW; ++w) {
+                const long long y = s_cv[w * 19 + j];
+                v = j == 10 ? (y > v ? y : v) : v + y;
+              }
+            }
+            long long* g = (long long*)(p.gacc + ((size_t)item * (p.n_dist * p.n_dirs) + oi) * GACC_BYTES);
+            g[tid] = gacc_value(tid, v, tid == 9 || tid >= 12 ? tlog_fx(p.clog, Tl) : 0);
           }
           if (tid == 0) {
             s_ncell = 0;
@@ -1989,9 +2215,10 @@ __global__ void __launch_bounds__(256) k_stats_final(KParams p) {
     double* row = p.table + item * p.n_col;
     double* save = (p.need & NEED_SAVE) ? p.saved + item * SV_WORDS : nullptr;
     const bool wvalid = g[49] != (A)0;
+    const double* cd = (const double*)(p.sacc + (size_t)item * SACC_BYTES + SACC_CD);
     if (lane == 0)
       finalize_stats<T, NDIM, A>(p, row, g, (int)r.n, g[48], g[49], g[50], r.vmin, r.vmax, (int64_t)(r.key >> 32),
-                                 r.x0, r.y0, r.z0, g[51], g[52], g[53], g[54], g[55], g[56], wvalid, save);
+                                 r.x0, r.y0, r.z0, cd, wvalid, save);
     if (p.need & (NEED_MOM_INT | NEED_SAVE))
       finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], wvalid, save ? save + SV_MU : nullptr);
     if (p.need & NEED_MOM_BIN) finalize_moments_warp<NDIM, A>(p, row, 5, g + 28, g[54], g[55], g[56], true, nullptr);

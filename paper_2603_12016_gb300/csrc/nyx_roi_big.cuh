@@ -66,18 +66,6 @@ __device__ inline int big_of_unit(const KParams& p, int n_big, unsigned u, bool 
   return lo;
 }
 
-// Kahan-compensated running sum (per thread)
-template <class A>
-struct KSum {
-  A s, c;
-  __device__ KSum() : s(0), c(0) {}
-  __device__ void add(A x) {
-    const A y = x - c;
-    const A t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
 
 // block sum of Kahan pairs: sums and negated corrections reduced separately
 // (each compensated), then added; out[] in shared memory for every thread
@@ -368,6 +356,7 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
   __shared__ double red[C::NW * RED_MAX];
   __shared__ long long s_i64[16];
   __shared__ A s_sc[16];
+  __shared__ A s_sl[8];  // low parts of the pass-1 float sums
   __shared__ int s_flag;
   __shared__ unsigned s_qc[C::NW * 64], s_qe[C::NW * 64];  // per-warp voxel queues
   const int tid = threadIdx.x;
@@ -464,7 +453,10 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
       }
     });
     block_sum_i64<C, 9>(s, red, s_i64);
-    if constexpr (!integer) block_sum_k<C, A, 5>(fs, red, s_sc);
+    if constexpr (!integer) {
+      if constexpr (std::is_same<A, float>::value) block_sum_pair<C, 5>(fs, red, s_sc, s_sl);
+      else block_sum_k<C, A, 5>(fs, red, s_sc);
+    }
     unsigned bmn = 0xFFFFFFFFu, bmx = 0;
     if (do_edge) {
       block_sum_i64<C, 3>(es, red, s_i64 + 9);
@@ -482,7 +474,11 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
       long long* pt = (long long*)(reg + L.part1) + (size_t)chunk * (BIG_P1 / 2);
       for (int k = 0; k < 9; ++k) pt[k] = s_i64[k];
       double* pf = (double*)(pt + 9);
-      for (int k = 0; k < 5; ++k) pf[k] = integer ? 0.0 : to_d(s_sc[k]);
+      for (int k = 0; k < 5; ++k) {  // float images: the pair hi + lo, exact in FP64
+        if constexpr (integer) pf[k] = 0.0;
+        else if constexpr (std::is_same<A, float>::value) pf[k] = pair_d(s_sc[k], s_sl[k]);
+        else pf[k] = s_sc[k];
+      }
       // [14] edge count, [15] sum d (float images: as a double), [16] sum d^2, [17] min code, [18] max code
       pt[14] = do_edge ? s_i64[9] : 0;
       if constexpr (integer) pt[15] = do_edge ? s_i64[10] : 0;
@@ -499,35 +495,27 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
     const int64_t bimg = (int64_t)(r.key >> 32);
     if (tid == 0) {
       long long t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      A fh[5] = {0, 0, 0, 0, 0}, fl[5] = {0, 0, 0, 0, 0};
+      double fd5[5] = {0, 0, 0, 0, 0};  // float images: chunk sums merged in FP64, chunk order
       for (int ch = 0; ch < br.nch; ++ch) {
         const long long* pt = (const long long*)(reg + L.part1) + (size_t)ch * (BIG_P1 / 2);
         for (int k = 0; k < 9; ++k) t[k] += __ldcg(pt + k);
         if constexpr (!integer) {
           const double* pf = (const double*)(pt + 9);
-          for (int k = 0; k < 5; ++k) {
-            const A x = (A)__ldcg(pf + k);
-            if constexpr (std::is_same<A, float>::value) {
-              float sum, err;
-              two_sum(fh[k], x, sum, err);
-              fh[k] = sum;
-              fl[k] += err;
-            } else {
-              fh[k] += x;
-            }
-          }
+          for (int k = 0; k < 5; ++k) fd5[k] += __ldcg(pf + k);
         }
       }
       if (t[8] != (long long)n) atomicOr(p.err, E_INTERNAL);
       const A nA = (A)n;
-      A sI, sxI, syI, szI, en, mhi, mlo;
+      A sI, en, mhi, mlo;
+      double dI, dxI, dyI, dzI;  // FP64 sums for the centroids
       if constexpr (integer) {
         const long long si = t[0];
         sI = (A)si;
-        sxI = (A)t[1];
-        syI = (A)t[2];
-        szI = (A)t[3];
         en = (A)t[7];
+        dI = (double)si;
+        dxI = (double)t[1];
+        dyI = (double)t[2];
+        dzI = (double)t[3];
         if constexpr (std::is_same<A, float>::value) {
           const long long q = si / n, rm = si - q * n;  // mean = q + rm / n exactly
           mhi = (A)q;
@@ -539,27 +527,31 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p1(KParams p
         put(p, row, Q_STATS + S_II, i2d(si));
         put(p, row, Q_STATS + S_ENERGY, i2d(t[7]));
       } else {
-        sI = fh[0] + fl[0];
-        sxI = fh[1] + fl[1];
-        syI = fh[2] + fl[2];
-        szI = fh[3] + fl[3];
-        en = fh[4] + fl[4];
-        mhi = sI / nA;
-        mlo = 0;
-        putA(p, row, Q_STATS + S_II, sI);
-        putA(p, row, Q_STATS + S_ENERGY, en);
+        dI = fd5[0];
+        dxI = fd5[1];
+        dyI = fd5[2];
+        dzI = fd5[3];
+        sI = (A)dI;
+        en = (A)fd5[4];
+        const double md = dI / (double)n;  // mean as an unevaluated pair in A
+        mhi = (A)md;
+        mlo = (A)(md - (double)mhi);
+        put(p, row, Q_STATS + S_II, dI);
+        put(p, row, Q_STATS + S_ENERGY, fd5[4]);
       }
-      const A bx_ = (A)t[4] / nA, by_ = (A)t[5] / nA, bz_ = (A)t[6] / nA;
-      const bool wv = sI != 0;
+      // FP64 centroids (ROI-local): binary from the exact coordinate sums,
+      // intensity-weighted from the sums above
+      const double bxd = (double)t[4] / n, byd = (double)t[5] / n, bzd = (double)t[6] / n;
+      const bool wv = dI != 0;
       double* st = p.big[b].st;
       st[0] = to_d(mhi);
       st[1] = to_d(mlo);
-      st[2] = to_d(wv ? sxI / sI : bx_);
-      st[3] = to_d(wv ? syI / sI : by_);
-      st[4] = to_d(wv ? szI / sI : bz_);
-      st[5] = to_d(bx_);
-      st[6] = to_d(by_);
-      st[7] = to_d(bz_);
+      st[2] = wv ? dxI / dI : bxd;
+      st[3] = wv ? dyI / dI : byd;
+      st[4] = wv ? dzI / dI : bzd;
+      st[5] = bxd;
+      st[6] = byd;
+      st[7] = bzd;
       st[8] = to_d(sI);
       st[9] = to_d(en);
       put(p, row, Q_LABEL, i2d(bx.label));
@@ -798,7 +790,10 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p2(KParams p
     const A sumI = (A)__ldcg(st + 8), energy = (A)__ldcg(st + 9);
     const bool wvalid = sumI != 0;
     // the merged sums go to k_stats_final like those of the block classes
-    store_sacc<A>(p, br.item, NM, res, res + 8, res + 8 + NM, mu_hi + mu_lo, sumI, energy, cx, cy, cz, bcx, bcy, bcz);
+    double cd[6];
+    for (int k = 0; k < 6; ++k) cd[k] = __ldcg(st + 2 + k);
+    store_sacc<A>(p, br.item, NM, res, res + 8, res + 8 + NM, mu_hi + mu_lo, sumI, energy, cx, cy, cz, bcx, bcy, bcz,
+                  cd);
     (void)n;
     (void)row;
     (void)bimg;
@@ -1031,7 +1026,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
         const long long Cc = a == bb ? 2 * (long long)cnt : (long long)cnt;
         const long long mult = a == bb ? 1 : 2;
         iv[8] += mult * Cc * Cc;
-        iv[9] += mult * __float2ll_rn((float)Cc * log2f((float)Cc) * 16777216.f);
+        iv[9] += mult * clog_fx<A>(p.clog, (unsigned)Cc);
         iv[11] = Cc > iv[11] ? Cc : iv[11];
         if (dbg) {
           p.dbg_glcm[(int64_t)oi * ng * ng + a * ng + bb] = (unsigned)Cc;
@@ -1054,12 +1049,12 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
       // marginal entropies and inverse differences (exact fixed-point sums),
       // mutual information over the cells
       for (int a = tid; a < ng; a += BIG_NT)
-        if (px[a]) iv[12] += ent_fx<A>(px[a]);
+        if (px[a]) iv[12] += clog_fx<A>(p.clog, px[a]);
       for (int k = tid; k < 2 * ng - 1; k += BIG_NT)
-        if (psum[k]) iv[13] += ent_fx<A>(psum[k]);
+        if (psum[k]) iv[13] += clog_fx<A>(p.clog, psum[k]);
       for (int k = tid; k < ng; k += BIG_NT)
         if (pdiff[k]) {
-          iv[14] += ent_fx<A>(pdiff[k]);
+          iv[14] += clog_fx<A>(p.clog, pdiff[k]);
           invdiff_fx<A>(p, pdiff[k], k, iv);
         }
       for (unsigned f = tid; f < ntri; f += BIG_NT) {
@@ -1072,6 +1067,10 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
         iv[10] += mult * mi_fx<A>(Cc, Tl, px[a], px[bb]);
       }
       block_sum_glcm<C>(iv, red, s_i64);
+      if (tid < GN) {  // entropy sums as numerators T log2 T - sum c log2 c
+        const long long TL = tid == 9 || tid >= 12 ? tlog_fx(p.clog, Tl) : 0;
+        s_i64[tid] = gacc_value(tid, s_i64[tid], TL);
+      }
       store_gacc(p, br.item, oi, s_i64, false);  // features: k_glcm_final
       __syncthreads();
     }
@@ -1282,7 +1281,7 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
         const unsigned c = __ldcg(gP + i);
         if (c) {
           atomicAdd(&scol[i % nj], c);
-          ent += ent_fx<A>(c);
+          ent += clog_fx<A>(p.clog, c);
         }
       }
       __syncthreads();

@@ -832,6 +832,7 @@ static cudaError_t launch_scan_t(const KParams& p, int nsm, cudaStream_t st) {
       rpt = c;
       break;
     }
+  if (p.scan_rpt > 0) rpt = p.scan_rpt < SCAN_RPT ? p.scan_rpt : SCAN_RPT;  // a tuned tile height
   k_scan<T><<<(int)grid, SCAN_NT, 0, st>>>(p, rpt);
   return cudaGetLastError();
 }

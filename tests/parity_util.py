@@ -5,12 +5,15 @@ values that are zero by symmetry are compared against their scale):
   exact     : counts, bounding boxes, min/max/range, labels, order statistics
               (same FP64 operations on the same sorted values), mode value
   RTOL_STAT : 1e-5 for first-order statistics and moments
-  RTOL_GLCM : 1e-4 for GLCM features (scale floor 1)
+  RTOL_GLCM : 1e-4 for GLCM features (floors in glcm_scale)
+  NGTDM / GLDM features: RTOL_STAT, relative, the GLDM variances on the
+              unit scale of an integer dependence / grey level
 |gpu - oracle| <= rtol * max(|oracle|, scale).
 """
 from __future__ import annotations
 
 import math
+import re
 from typing import Dict, List, Optional, Tuple
 
 import numpy as np
@@ -38,7 +41,17 @@ def scales(t: Dict[str, np.ndarray], name: str, ndim: int) -> np.ndarray:
     amax = np.maximum(np.abs(t.get("MIN", one)), np.abs(t.get("MAX", one)))
     ext = [t["BBOX_WIDTH"], t["BBOX_HEIGHT"], t.get("BBOX_DEPTH", one)]
     if name.startswith("GLCM_"):
-        return one
+        return glcm_scale(t, name)
+    if name.startswith("GLDM_"):
+        # dependences and grey levels are integers >= 1: their variances
+        # (near zero when every pixel shares one value) on that unit scale
+        if name in ("GLDM_DV", "GLDM_GLV"):
+            return one
+        return np.full(n, TINY)
+    if name.startswith("NGTDM_"):
+        # contrast, busyness, complexity and strength are exactly 0 in their
+        # degenerate cases (one grey level, no neighbour differences)
+        return np.full(n, TINY)
     if name in DIMENSIONLESS:
         return one
     if name in ("MEAN", "ROBUST_MEAN", "MEDIAN", "EDGE_MEAN_INTENSITY"):
@@ -97,6 +110,50 @@ def scales(t: Dict[str, np.ndarray], name: str, ndim: int) -> np.ndarray:
             deg = {1: 1, 2: 2, 3: 3, 4: 3, 5: 6, 6: 4, 7: 6}[h]
             return s2 ** deg
     return np.maximum(np.abs(t.get(name, one)), 1.0)
+
+
+TINY = 1e-300
+
+
+def glcm_scale(t: Dict[str, np.ndarray], name: str) -> np.ndarray:
+    """Natural scale of a GLCM feature column (direction mean or per offset).
+    Relative 1e-4 everywhere, with a floor only for features that vanish by
+    symmetry or degeneracy, at the feature's own scale:
+      CLUSHADE (zero for a symmetric sum distribution): CLUPROM^(3/4), the
+        bound of sum |i + j - 2 mu|^3 p by Hoelder's inequality;
+      CORR, INFOMEAS1, INFOMEAS2 (zero for uncorrelated / independent
+        matrices; dimensionless, |value| <= 1): 1e-2;
+      the entropies JE, ENTROPY, SUMENT, DIFENTRO (zero for a one-cell
+        distribution): 1e-2 bit;
+      CONTRAST, DIS, DIFAVE, DIFVAR, IV (zero when every pair lies on the
+        diagonal): their squared / first level unit times 1e-12;
+      the central moments CLUTEND, SUMVAR, CLUPROM, JVAR, VARIANCE (zero for
+        one grey level): 1e-10 times the matching power of the mean level,
+        the size of the FP64 cancellation in the oracle's two-pass form;
+      everything else (ASM, ENERGY, JMAX, ACOR, JAVE, SUMAVE, the inverse
+        differences): strictly positive, relative only."""
+    n = len(t["LABEL"])
+    base = name[len("GLCM_"):]
+    m = re.match(r"([A-Z0-9]+?)(_D\d+(?:_A\d+|_O\d+)?)$", base)
+    feat, suf = (m.group(1), m.group(2)) if m else (base, "")
+
+    def col(f):
+        v = t.get("GLCM_" + f + suf)
+        return np.abs(v) if v is not None else np.ones(n)
+
+    if feat == "CLUSHADE":
+        return col("CLUPROM") ** 0.75
+    if feat in ("CORR", "INFOMEAS1", "INFOMEAS2", "JE", "ENTROPY", "SUMENT", "DIFENTRO"):
+        return np.full(n, 1e-2)
+    if feat in ("CONTRAST", "DIS", "DIFAVE", "DIFVAR", "IV"):
+        return np.full(n, 1e-12)
+    if feat in ("CLUTEND", "SUMVAR"):
+        return 1e-10 * col("SUMAVE") ** 2
+    if feat == "CLUPROM":
+        return 1e-10 * col("SUMAVE") ** 4
+    if feat in ("JVAR", "VARIANCE"):
+        return 1e-10 * col("JAVE") ** 2
+    return np.full(n, TINY)
 
 
 def compare(gpu: Dict[str, np.ndarray], orc: Dict[str, np.ndarray], ndim: int, rtol_stat=RTOL_STAT,

@@ -145,3 +145,75 @@ def test_backward_label_map_kept_or_rebuilt():
     torch.cuda.synchronize()
     assert torch.equal(g_same, g_copy) and torch.equal(g_same, g_after)
     assert torch.count_nonzero(g_same[mask == 0]) == 0 and torch.count_nonzero(g_same) > 0
+
+
+def test_backward_full_size_batch_sampled_fd():
+    """The full differentiation workload (64 float32 512 x 512 images, ~3,000
+    ROIs, sizes 30-20,000 px, the multi-block class included) in the launch
+    configuration the benchmark times.  For a sample of ROIs: every pixel's
+    GPU gradient against the oracle's analytic FP64 gradient, pixel by pixel
+    at rel 1e-3 (floor: 1e-6 of the ROI's largest gradient, for pixels where
+    the gradient crosses zero); and 32 random pixels per ROI against central
+    finite differences (h = 1e-3) of the FP64 oracle forward, at rel 1e-3
+    plus the difference quotient's own rounding noise.  That noise is
+    measured, not assumed: |L(+h) + L(-h) - 2 L(0)| / (2h) for the same
+    pixel, which is the rounding of the three loss evaluations (the
+    curvature term is ~h L''/2, far below it).  Large features with small
+    per-pixel derivatives (mu20 near the centroid of a 20,000 px ROI: 1.4e10
+    against a change of 1e-2) make it reach 1e-2 of a pixel's gradient there.
+    A ROI's features depend only on its own pixels and on its neighbours'
+    labels (edge pixels), so both references are computed on a crop of the
+    ROI's bounding box with a one-pixel margin."""
+    from paper_2603_12016_gb300 import nyx
+
+    w = W.config("blobbatch")
+    rng = np.random.default_rng(29)
+    img = torch.from_numpy(w.image).cuda()
+    mask = torch.from_numpy(w.mask).cuda()
+    n_roi = int(sum(len(np.unique(m[m > 0])) for m in w.mask))
+    layer = nyx.FeatureLayer(w.image.shape, ndim=2, max_rois=8192, features=SMOOTH + FAMILIES)
+    x = img.clone().requires_grad_(True)
+    table = layer(x, mask)
+    assert table.shape[0] == n_roi
+    cols = layer.columns
+    tab = table.detach().cpu().numpy()
+    g = _upstream(cols, tab, rng)
+    table.backward(torch.from_numpy(g).cuda())
+    got = x.grad.detach().cpu().numpy().astype(np.float64)
+    rows = [(int(b), int(l)) for b, l in zip(tab[:, cols.index("IMAGE")], tab[:, cols.index("LABEL")])]
+    area = tab[:, cols.index("AREA")]
+    pick = set(rng.choice(len(rows), size=10, replace=False).tolist()) | {int(np.argmax(area)), int(np.argmin(area))}
+    assert area.max() > 8192  # the multi-block class is in the sample
+    for r in sorted(pick):
+        b, lab = rows[r]
+        m = w.mask[b]
+        ys, xs = np.nonzero(m == lab)
+        y0, y1 = max(ys.min() - 1, 0), min(ys.max() + 2, m.shape[0])
+        x0, x1 = max(xs.min() - 1, 0), min(xs.max() + 2, m.shape[1])
+        cm = np.where(m[y0:y1, x0:x1] == lab, lab, 0).astype(np.int32)
+        ci = w.image[b, y0:y1, x0:x1].astype(np.float64)
+        names = [c for j, c in enumerate(cols) if g[r, j] != 0]
+        gr = {c: g[r, cols.index(c)] for c in names}
+        # analytic FP64 gradient, every pixel of the ROI
+        ref = oracle.grad(ci, cm, 2, {c: np.array([v]) for c, v in gr.items()})
+        gg = got[b, y0:y1, x0:x1]
+        inr = cm > 0
+        scale = np.max(np.abs(ref[inr]))
+        bad = np.abs(gg[inr] - ref[inr]) > RTOL * np.maximum(np.abs(ref[inr]), 1e-3 * scale)
+        assert not bad.any(), (b, lab, int(area[r]), gg[inr][bad][:4], ref[inr][bad][:4])
+
+        def loss(im):
+            t = oracle.extract(im, cm, 2, ng=0)
+            return sum(gr[c] * float(t[c][0]) for c in names)
+
+        l0 = loss(ci)
+        for k in rng.choice(len(ys), size=min(32, len(ys)), replace=False):
+            yy, xx = ys[k] - y0, xs[k] - x0
+            ip, im_ = ci.copy(), ci.copy()
+            ip[yy, xx] += 1e-3
+            im_[yy, xx] -= 1e-3
+            lp, lm = loss(ip), loss(im_)
+            fd = (lp - lm) / 2e-3
+            noise = abs(lp + lm - 2 * l0) / 2e-3
+            gv = got[b, ys[k], xs[k]]
+            assert abs(gv - fd) <= RTOL * abs(fd) + 4 * noise + 1e-6 * scale, (b, lab, int(area[r]), gv, fd, noise)

@@ -123,3 +123,39 @@ def test_multiblock_key_sort_above_single_block_capacity(n_roi):
     sel = np.isin(g["LABEL"].astype(np.int64), pick)
     fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
     assert not fails, "\n".join(fails[:30])
+
+
+def test_mosaic_8192_streamed_sampled_parity():
+    """The 8192 x 8192 mosaic with 32,000 placed ROIs, streamed in 1024 x
+    1024 tiles (the launch the benchmark's streamed configuration uses at
+    this size): more ROIs than one block's key sort handles, ROIs crossing
+    tile borders merged in the label table.  The streamed table equals the
+    whole-image table bit for bit, and a sample of ROIs (border-crossing
+    ones, the largest, the smallest, random ones) matches the oracle."""
+    from paper_2603_12016_gb300 import nyx
+
+    m = W.mosaic_2d(size=8192, tile=1024, n_roi=32_000)
+    img, mask = m.assemble()
+    n_roi = int(np.count_nonzero(np.bincount(mask.ravel())[1:]))
+    assert n_roi > 16384
+    ex = nyx.Extractor(img.shape, torch.uint16, glcm_levels=64, dists=(1,), max_rois=2 * n_roi)
+    d_img = torch.empty(img.shape, dtype=torch.uint16, device="cuda")
+    d_mask = torch.empty(mask.shape, dtype=torch.int32, device="cuda")
+    got = ex.extract_tiles(m.tile, (1024, 1024), d_img, d_mask)
+    assert got.shape[0] == n_roi
+    whole = ex(to_torch(img), to_torch(mask))
+    assert torch.equal(torch.nan_to_num(got, nan=-7.0), torch.nan_to_num(whole, nan=-7.0))
+    g = _table(ex, got)
+    cross = sorted(_crossing(mask, 1024, 1024))
+    assert len(cross) > 500
+    lab, cnt = np.unique(mask[mask > 0], return_counts=True)
+    rng = np.random.default_rng(3)
+    pick = sorted(set(rng.choice(cross, 40, replace=False).tolist()) |
+                  set(rng.choice(lab, 40, replace=False).tolist()) |
+                  {int(lab[np.argmax(cnt)]), int(lab[np.argmin(cnt)])})
+    o = oracle.extract(img, mask, 2, ng=64, dists=(1,), hist_bins=256, rois=[oracle.roi_key(0, l) for l in pick],
+                       threads=8)
+    sel = np.isin(g["LABEL"].astype(np.int64), pick)
+    assert sel.sum() == len(pick)
+    fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
+    assert not fails, "\n".join(fails[:30])
