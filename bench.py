@@ -47,8 +47,9 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (SM clock, max clock, throttle reasons) while the
-    timed region runs."""
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) taken every
+    20 ms while the timed regions run; each sample is tagged with the region
+    (workload) that was being timed when it arrived."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -58,11 +59,12 @@ class ClockSampler:
         self.index = index
         self.rows = []
         self.proc = None
+        self.tag = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "25"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -73,8 +75,21 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 8:
-                self.rows.append(parts)
+            if len(parts) >= 8 and self.tag is not None:
+                self.rows.append([self.tag] + parts)
+
+    def region(self, tag):
+        sampler = self
+
+        class _R:
+            def __enter__(self):
+                sampler.tag = tag
+                time.sleep(0.05)  # let the sampler see the start of the region
+
+            def __exit__(self, *a):
+                sampler.tag = None
+
+        return _R()
 
     def __exit__(self, *a):
         if self.proc:
@@ -84,40 +99,56 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stats(rows):
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        out = self._stats(self.rows)
+        out["by_region"] = {t: self._stats([r for r in self.rows if r[0] == t])
+                            for t in dict.fromkeys(r[0] for r in self.rows)}
+        return out
 
 
-# DRAM bytes (read + write) per launch of a phase's kernel from one ncu
-# capture (profiles/roi_kernels_nuclei2d_2048.md), keyed by workload, phase
-# and class limits; entries are removed when the kernel changes.
-TRAFFIC = {
-    ("nuclei2d_2048_u16_4000roi", "roi_warp", (256, 1024, 8192)): 5.88e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_small", (256, 1024, 8192)): 16.58e6,
-    ("nuclei2d_2048_u16_4000roi", "roi_medium", (256, 1024, 8192)): 13.68e6,
-}
+# DRAM bytes (read + write) per launch of a phase's kernel, from one ncu
+# capture of the same bench command, keyed by workload, phase, class limits
+# and feature set, and valid only for the kernel sources they were taken
+# with (the hash below; any change to csrc/ voids them and traffic is null).
+TRAFFIC_SRC = None
+TRAFFIC = {}
 
 
-def roi_classes(w, lim_pix=None):
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources the library is built from."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2603_12016_gb300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def roi_classes(w, lim_pix):
     """Pixels and ROI count per size class (warp, small, medium, multi-block)
-    by the library's class rule: pixel count against the class limits
-    (default 256 / 1,024 / 8,192) and padded bounding-box cells against the
-    class capacities 1,024 / 4,096 / 16,384."""
-    import numpy as np
+    by the library's class rule: pixel count against the class limits and
+    padded bounding-box cells against the class capacities 1,024 / 4,096 /
+    16,384."""
     from scipy import ndimage
 
-    pad = max(w.params["dists"]) if w.params["glcm_levels"] > 0 else 0
-    lp = tuple(lim_pix) if lim_pix else (256, 1024, 8192)
+    pad = max(w.params["dists"])  # the plan pads every raster by the largest distance (>= 1)
+    lp = tuple(lim_pix)
     lims = ((lp[0], 1024), (lp[1], 4096), (lp[2], 16384))
     px, rows = [0, 0, 0, 0], [0, 0, 0, 0]
-    masks = w.mask if (w.mask.ndim == 3 and w.ndim == 2) else w.mask[None]
+    masks = w.mask.reshape((-1,) + w.mask.shape[-w.ndim:]) if w.mask.ndim > w.ndim else w.mask[None]
     for m in masks:
         cnt = np.bincount(m.ravel())
         for lab, sl in enumerate(ndimage.find_objects(m), start=1):
@@ -150,16 +181,45 @@ def reduce_over_ranks(dist, device, t_ms: float, units: int):
     return float(tt.item()), int(nn.item())
 
 
-def make_workload(name: str, rank: int):
+_MOSAIC = None
+
+
+def _mosaic_init(kw):
+    global _MOSAIC
+    from paper_2603_12016_gb300 import workloads as W
+
+    _MOSAIC = W.mosaic_2d(**kw)
+
+
+def _mosaic_tile(job):
+    return _MOSAIC.tile(*job)
+
+
+def make_workload(name: str, rank: int, procs: int = 1):
     from paper_2603_12016_gb300 import workloads as W
 
     if name.startswith("mosaic"):
-        # whole-slide stand-in generated tile by tile; the assembled arrays are
-        # what the host would stream
+        # whole-slide stand-in generated tile by tile (tiles in parallel
+        # processes, started with spawn before any CUDA call); the assembled
+        # arrays are what the host streams
         big = name == "mosaic"
-        m = W.mosaic_2d(size=32768 if big else 8192, tile=4096 if big else 1024,
-                        n_roi=500_000 if big else 32_000, seed=1005 + rank)
-        img, mask = m.assemble()
+        kw = dict(size=32768 if big else 8192, tile=4096 if big else 1024, n_roi=500_000 if big else 32_000,
+                  seed=1005 + rank)
+        m = W.mosaic_2d(**kw)
+        if procs > 1:
+            import multiprocessing as mp
+
+            img = np.empty((m.size, m.size), dtype=np.uint16)
+            mask = np.empty((m.size, m.size), dtype=np.int32)
+            t = m.tile_size
+            jobs = [(x0, y0, min(t, m.size - x0), min(t, m.size - y0))
+                    for y0 in range(0, m.size, t) for x0 in range(0, m.size, t)]
+            with mp.get_context("spawn").Pool(procs, initializer=_mosaic_init, initargs=(kw,)) as pool:
+                for (x0, y0, w_, h_), (ti, tm) in zip(jobs, pool.imap(_mosaic_tile, jobs)):
+                    img[y0:y0 + h_, x0:x0 + w_] = ti
+                    mask[y0:y0 + h_, x0:x0 + w_] = tm
+        else:
+            img, mask = m.assemble()
         n_roi = int(np.count_nonzero(np.bincount(mask.ravel())[1:]))
         return W.Workload(m.name, img, mask, 2, params=dict(m.params),
                           meta={"n_roi": n_roi, "tile": m.tile_size})
@@ -182,9 +242,9 @@ def run_reference(args) -> int:
     w = make_workload(args.workload, 0)
     cores = os.cpu_count() or 1
     image, mask, where = _oracle_view(w)
-    labels = np.unique(mask[mask > 0])
+    labels = _roi_keys(w, mask)
     sample = labels[: min(len(labels), args.ref_rois)]
-    keys = [oracle.roi_key(0, int(l)) for l in sample]
+    keys = [int(k) for k in sample]
     prm = w.params
     times = []
     for i in range(args.warmup + args.steps):
@@ -208,6 +268,14 @@ def run_reference(args) -> int:
     return 0
 
 
+def _roi_keys(w, mask):
+    """Oracle ROI keys (image << 32 | label) of every ROI, ascending."""
+    import oracle
+
+    per = mask.reshape((-1,) + mask.shape[-w.ndim:]) if mask.ndim > w.ndim else mask[None]
+    return [oracle.roi_key(b, int(l)) for b, m in enumerate(per) for l in np.unique(m[m > 0])]
+
+
 def _oracle_view(w):
     """Arrays the oracle samples from: the first 4096 x 4096 tile of a
     streamed mosaic (the oracle separates every pixel of its input first),
@@ -217,19 +285,19 @@ def _oracle_view(w):
     return w.image, w.mask, ""
 
 
-def cpu_baseline(w, budget_s: float):
+def cpu_baseline(w, budget_s: float, note: str = ""):
     """Time the oracle on the host cores on a bounded ROI sample."""
     import numpy as np
     import oracle
 
     cores = os.cpu_count() or 1
     image, mask, where = _oracle_view(w)
-    labels = np.unique(mask[mask > 0])
+    labels = _roi_keys(w, mask)
     prm = w.params
     n = 32
     while True:
         sample = labels[: min(n, len(labels))]
-        keys = [oracle.roi_key(0, int(l)) for l in sample]
+        keys = [int(k) for k in sample]
         t0 = time.perf_counter()
         oracle.extract(image, mask, w.ndim, ng=prm["glcm_levels"], dists=prm["dists"],
                        hist_bins=prm["hist_bins"], rois=keys, threads=cores)
@@ -238,7 +306,8 @@ def cpu_baseline(w, budget_s: float):
             break
         n = int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3))))
     return {"value": len(sample) / dt, "unit": "ROIs/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {len(sample)} of {len(labels)} ROIs of {w.name}{where}, {dt:.1f} s",
+            "sample": f"first {len(sample)} of {len(labels)} ROIs of {w.name}{where}, {dt:.1f} s"
+                      + (f"; oracle computes {note}" if note else ""),
             "seconds": dt}
 
 
@@ -341,157 +410,148 @@ def run_soft_sweep(args) -> int:
     return 0
 
 
-def main() -> int:
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nuclei2d")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison path")
-    ap.add_argument("--ref-rois", type=int, default=800)
-    ap.add_argument("--backward", dest="backward", action="store_true", default=None,
-                    help="time forward + backward (default for the blobbatch workloads)")
-    ap.add_argument("--no-backward", dest="backward", action="store_false")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default class limits")
-    ap.add_argument("--class-limits", default=None, help="warp,small,medium pixel limits instead of autotuning")
-    ap.add_argument("--sweep", default=None, choices=["soft", "scalability", "families"],
-                    help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
-                         "separability grid on labelled texture classes; scalability: time over ROI size x ROI "
-                         "count (GPU device, GPU end to end, CPU oracle) and the feature-group cost of an image "
-                         "of 100 ROIs of 100,000 px; families: the workload with the NGTDM and GLDM removed "
-                         "and alone (one JSON line each, not bench lines)")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.sweep == "soft":
-        return run_soft_sweep(args)
-    if args.sweep == "scalability":
-        return run_scalability_sweep(args)
-    if args.sweep == "families":
-        return run_family_sweep(args)
+EXTRA_CONFIGS = ("ct3d", "blobbatch", "mosaic")  # measured beside the headline, in sub-objects
 
-    import numpy as np
+
+def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None):
+    """Time one workload: CUDA-graph replay of nyx_extract (+ nyx_backward for
+    the differentiation workload) over device-resident inputs, L2 flushed
+    before every step; per-phase device times from the event nodes inside
+    the replayed graph; the dominant kernel's roofline; end to end through
+    the public API from pinned host memory.  Returns the measurement dict."""
     import torch
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2603_12016_gb300 import nyx, tuning
 
-        dist.init_process_group("nccl", device_id=dev)
-
-    from paper_2603_12016_gb300 import build, nyx
-
-    if rank == 0 or world == 1:
-        build.build()
-    if dist is not None:
-        dist.barrier()
-
-    w = make_workload(args.workload, rank)
     prm = w.params
     dtype = {np.uint16: torch.uint16, np.int16: torch.int16, np.float32: torch.float32}[w.image.dtype.type]
     max_rois = 8192 if w.meta["n_roi"] <= 8192 else 2 * w.meta["n_roi"]
-    tile = w.meta.get("tile")  # streamed mosaic: e2e goes through nyx_extract_tiles
+    tile = w.meta.get("tile")
+    feats = nyx.CORE_FEATURE_IDS if features == "core" else None
 
     def extractor(precision):
         return nyx.Extractor(w.image.shape, dtype, ndim=w.ndim, glcm_levels=prm["glcm_levels"], dists=prm["dists"],
-                             hist_bins=prm["hist_bins"], precision=precision, max_rois=max_rois, device=dev)
+                             hist_bins=prm["hist_bins"], precision=precision, max_rois=max_rois, device=dev,
+                             features=feats)
 
     ex = extractor("fp32")
+    sig = tuning.signature(w.image.shape, str(w.image.dtype), w.ndim, prm["glcm_levels"], prm["dists"], features)
+    dev_name = torch.cuda.get_device_name(dev)
+    if args.class_limits:
+        limits = tuple(int(v) for v in args.class_limits.split(","))
+        limits, lim_src = (limits + (0,))[:4], "command line"
+        ex.set_tuning(*limits)
+    else:
+        limits, lim_src = tuning.limits_for(ex, dev_name, sig)
     img = torch.from_numpy(w.image).to(dev)
     mask = torch.from_numpy(w.mask).to(dev)
-    table = torch.empty((max_rois, len(ex.columns)), dtype=torch.float64, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n_col = len(ex.columns)
+    table = torch.empty((max_rois, n_col), dtype=torch.float64, device=dev)
+    if flush is None:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # differentiation workload: a step is the forward pass plus the backward
-    # pass for a fixed random upstream gradient dL/dtable
-    bwd = args.backward if args.backward is not None else args.workload.startswith("blobbatch")
+    bwd = name.startswith("blobbatch") if args.backward is None else args.backward
     gen = torch.Generator(device=dev).manual_seed(5)
-    gtab = torch.randn((max_rois, len(ex.columns)), dtype=torch.float64, device=dev, generator=gen) if bwd else None
+    gtab = torch.randn((max_rois, n_col), dtype=torch.float64, device=dev, generator=gen) if bwd else None
     gimg = torch.empty(img.shape, dtype=torch.float32, device=dev) if bwd else None
 
-    def one_step(e, im, mk):
+    def one_step(e, im, mk, bwd_ev=None):
         n = e.extract_into(im, mk, table, save_for_backward=bwd)
         if bwd:
+            if bwd_ev:
+                bwd_ev[0].record(stream)
             e.backward(im, mk, gtab, out=gimg)
+            if bwd_ev:
+                bwd_ev[1].record(stream)
         return n
 
-    def timed(e, steps, warmup):
-        """Per-step device times (CUDA events on the launching stream) of
-        back-to-back steps; the extraction replays its captured CUDA graph."""
+    def timed(e, steps, warmup, phases=True):
+        """Per-step device times (CUDA events on the launching stream) and,
+        with phases, the per-phase times of each step's graph replay."""
+        e.graph_phase_events(phases)
         for _ in range(warmup):
             one_step(e, img, mask)
         e.sync_status()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ms, ph = [], []
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
+        n = None
         for i in range(steps):
             flush.zero_()
-            starts[i].record(stream)
-            n = one_step(e, img, mask)
-            ends[i].record(stream)
+            s_, t_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            bev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if bwd else None
+            s_.record(stream)
+            n = one_step(e, img, mask, bev)
+            t_.record(stream)
+            t_.synchronize()
+            ms.append(s_.elapsed_time(t_))
+            if phases:
+                d = e.graph_phase_times()
+                if bwd:
+                    d["backward"] = bev[0].elapsed_time(bev[1])
+                ph.append(d)
         torch.cuda.synchronize(dev)
         e.sync_status()
-        return [s.elapsed_time(t) for s, t in zip(starts, ends)], int(n.item())
+        e.graph_phase_events(False)
+        return ms, ph, int(n.item())
 
-    def phase_profile(e, steps):
-        """Per-phase times from the library's event ring (direct launches)."""
-        e.profile(steps)
-        for _ in range(steps):
-            flush.zero_()
-            one_step(e, img, mask)
-        torch.cuda.synchronize(dev)
-        e.sync_status()
-        per = [e.phase_times(back=b) for b in range(steps)]
-        e.profile(0)
-        return {k: sum(p[k] for p in per) / steps for k in PHASES}
-
-    limits = None
-    if args.class_limits:
-        limits = tuple(int(v) for v in args.class_limits.split(","))
-        ex.set_class_limits(*limits)
-    elif not args.no_autotune:
-        limits = ex.autotune(img, mask, reps=3)
-    with ClockSampler(local) as clk:
-        ms, n_roi = timed(ex, args.steps, args.warmup)
-    clocks = clk.summary()
-    phases = phase_profile(ex, min(args.steps, 10))
+    with clk.region(name + ("" if features == "all" else "/" + features)):
+        ms, ph, n_roi = timed(ex, args.steps, args.warmup)
     t_step, n_total = reduce_over_ranks(dist, dev, statistics.median(ms), n_roi)
-    value = n_total / (t_step * 1e-3)
-    px_total = w.image.size * world
-    n_col = len(ex.columns)
-    peak, peak_kind = _peaks()
-    alg = algorithmic_bytes(w, n_roi, n_col)
-    pipe_gbs = alg / (t_step * 1e-3) / 1e9
+    phases = {k: sum(p[k] for p in ph) / len(ph) for k in ph[0]}
+    res = {"workload": w.name, "features": features, "n_roi": n_roi, "n_col": n_col,
+           "value": n_total / (t_step * 1e-3), "unit": "ROIs/s", "ms_per_step": t_step,
+           "step": "forward + backward" if bwd else "forward",
+           "class_limits_px": list(limits[:3]), "scan_rows_per_warp": limits[3], "class_limits_source": lim_src,
+           "mpix_per_s": w.image.size * (dist.get_world_size() if dist else 1) / (t_step * 1e-3) / 1e6,
+           "phases_ms": {k: round(v, 5) for k, v in phases.items()}}
+    if light:
+        return res
 
-    # dominant kernel and its roofline: algorithmic bytes of the phase that
-    # takes longest (the scan streams image + mask once; a ROI class reads
-    # its ROIs' pixels and mask once and writes their table rows; the GLCM
-    # feature kernel reads the per-offset sums and writes the GLCM columns)
-    dom = max(phases, key=phases.get)
-    cls_px, cls_rows = roi_classes(w, limits)
+    # dominant kernel (longest phase of the replayed graph) and its roofline:
+    # algorithmic bytes per launch (the scan streams image + mask once; a ROI
+    # class reads its ROIs' pixels and mask once and writes their table rows;
+    # the backward pass reads image + mask and writes the gradient)
+    cls_px, cls_rows = roi_classes(w, limits[:3])
     n_off = len(prm["dists"]) * (13 if w.ndim == 3 else 4) if prm["glcm_levels"] > 0 else 0
     per_px = w.image.itemsize + 4
-    dom_bytes = {"scan": w.image.nbytes + w.mask.nbytes,
-                 "roi_warp": cls_px[0] * per_px + 8 * cls_rows[0] * n_col,
-                 "roi_small": cls_px[1] * per_px + 8 * cls_rows[1] * n_col,
-                 "roi_medium": cls_px[2] * per_px + 8 * cls_rows[2] * n_col,
-                 "roi_big": cls_px[3] * per_px + 8 * cls_rows[3] * n_col,
-                 "final": n_roi * (512 + n_off * 160 + 8 * n_col)}.get(dom, 0)
+    # The four size classes run as concurrent graph branches, each holding SMs
+    # the others wait for, so a class's own span is not its kernel time; the
+    # per-ROI stage (fork to join) is timed as one unit with the bytes of
+    # every ROI pixel and table row.
+    alg_by_phase = {"scan": w.image.nbytes + w.mask.nbytes,
+                    "roi_stage": sum(cls_px) * per_px + 8 * n_roi * n_col,
+                    "glcm_final": n_roi * n_off * 160,
+                    "stats_final": n_roi * 512,
+                    "backward": w.image.nbytes + w.mask.nbytes + 4 * w.image.size}
+    cand = {k: v for k, v in phases.items() if k in alg_by_phase}
+    dom = max(cand, key=cand.get)
+    dom_bytes = alg_by_phase[dom]
     dom_gbs = dom_bytes / (phases[dom] * 1e-3) / 1e9
-    traffic = TRAFFIC.get((w.name, dom, tuple(limits) if limits else None))
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
-                "frac": dom_gbs / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes": int(dom_bytes)}
+    peak, peak_kind = _peaks()
+    src = kernel_source_hash()
+    tr = TRAFFIC.get((w.name, dom, tuple(limits), features)) if TRAFFIC_SRC == src else None
+    kern = {"roi_stage": "per-ROI stage: k_roi warp/small/medium classes + multi-block kernels, concurrent",
+            "scan": "k_scan (label scan)", "backward": "k_bwd_coef + k_bwd_pixel",
+            "glcm_final": "k_glcm_final", "stats_final": "k_stats_final"}[dom]
+    res["roofline"] = {"bound": "hbm", "kernel": kern, "phase": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
+                       "frac": dom_gbs / peak, "traffic": tr, "peak_kind": peak_kind,
+                       "algorithmic_bytes": int(dom_bytes), "avg_launch_ms": phases[dom],
+                       "timing": "CUDA event nodes inside each timed graph replay, on the kernel's own stream"}
+    alg = algorithmic_bytes(w, n_roi, n_col) + (4 * w.image.size if bwd else 0)
+    res["pipeline_hbm"] = {"algorithmic_bytes": alg, "achieved_gbs": alg / (t_step * 1e-3) / 1e9,
+                           "frac": alg / (t_step * 1e-3) / 1e9 / peak, "peak": peak, "peak_kind": peak_kind}
+    res["roi_mpix_per_s"] = float((w.mask > 0).sum()) / (t_step * 1e-3) / 1e6
+    res["l2"] = "flushed (256 MB write) before every step"
+    # our kernels per step: front (counters + scan), key sort, setup; the
+    # block classes with a nonzero limit; the multi-block path (zero, pass 1,
+    # pass 2, order statistics, + GLCM, + neighbour kernel); GLCM features;
+    # statistics; reset; backward: coefficients + per-pixel gradient + reset
+    glcm = prm["glcm_levels"] > 0
+    n_cls = sum(1 for v in limits if v > 0)
+    per_step = 3 + n_cls + 4 + (2 if glcm else 0) + (1 if glcm else 0) + 1 + 1 + (3 if bwd else 0)
+    res["gpu_launches"] = per_step * args.steps
 
     # end to end through the public API: pinned host inputs -> H2D -> extract -> D2H
     h_img = torch.from_numpy(w.image).pin_memory()
@@ -509,73 +569,140 @@ def main() -> int:
     e2e_steps = args.steps if tile is None else min(args.steps, 3)
     for i in range(args.warmup + e2e_steps):
         torch.cuda.synchronize(dev)
-        s, t = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
+        s_, t_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
         if tile is None:
             d_img.copy_(h_img, non_blocking=True)
             d_mask.copy_(h_mask, non_blocking=True)
-            n = one_step(ex, d_img, d_mask)
+            one_step(ex, d_img, d_mask)
         else:  # tiles streamed from host memory, band scans overlapping the host
             ex.extract_tiles(tile_source, (tile, tile), d_img, d_mask, table=table)
         h_table[:n_roi].copy_(table[:n_roi], non_blocking=True)
         if bwd:
             h_grad.copy_(gimg, non_blocking=True)
-        t.record(stream)
-        t.synchronize()
+        t_.record(stream)
+        t_.synchronize()
         if i >= args.warmup:
-            e2e_ms.append(s.elapsed_time(t))
+            e2e_ms.append(s_.elapsed_time(t_))
     e2e_t, _ = reduce_over_ranks(dist, dev, statistics.median(e2e_ms), n_roi)
-    e2e = {"value": n_total / (e2e_t * 1e-3), "unit": "ROIs/s",
-           "h2d_bytes_per_step": int(w.image.nbytes + w.mask.nbytes), "api": "nyx_extract_tiles" if tile else "nyx_extract",
-           "d2h_bytes_per_step": int(8 * n_roi * n_col + (4 * w.image.size if bwd else 0)), "ms_per_step": e2e_t}
-
-    fp64 = None
+    res["e2e"] = {"value": n_total / (e2e_t * 1e-3), "unit": "ROIs/s",
+                  "h2d_bytes_per_step": int(w.image.nbytes + w.mask.nbytes),
+                  "api": "nyx_extract_tiles" if tile else "nyx_extract",
+                  "d2h_bytes_per_step": int(8 * n_roi * n_col + (4 * w.image.size if bwd else 0)),
+                  "ms_per_step": e2e_t}
+    del h_img, h_mask, h_table, h_grad, d_img, d_mask
     if not args.no_fp64:
         ex64 = extractor("fp64")
-        if limits is not None:
-            ex64.set_class_limits(*limits)
-        ms64, _ = timed(ex64, max(3, args.steps // 4), 3)
+        ex64.set_tuning(*limits)
+        ms64, _, _ = timed(ex64, max(3, args.steps // 4), 3, phases=False)
         t64 = statistics.median(ms64)
-        fp64 = {"value": n_roi / (t64 * 1e-3), "unit": "ROIs/s", "ms_per_step": t64,
-                "speedup_fp32_over_fp64": t64 / t_step}
+        res["fp64_plain"] = {"value": n_roi / (t64 * 1e-3), "unit": "ROIs/s", "ms_per_step": t64,
+                             "speedup_fp32_over_fp64": t64 / t_step}
+        del ex64
+    return res
 
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nuclei2d")
+    ap.add_argument("--configs", default=",".join(EXTRA_CONFIGS),
+                    help="workloads measured beside the headline (comma list, '' for none)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison path")
+    ap.add_argument("--ref-rois", type=int, default=800)
+    ap.add_argument("--backward", dest="backward", action="store_true", default=None,
+                    help="time forward + backward (default for the blobbatch workloads)")
+    ap.add_argument("--no-backward", dest="backward", action="store_false")
+    ap.add_argument("--class-limits", default=None,
+                    help="warp,small,medium pixel limits[,scan rows per warp] instead of the tuned ones")
+    ap.add_argument("--sweep", default=None, choices=["soft", "scalability", "families"],
+                    help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
+                         "separability grid on labelled texture classes; scalability: time over ROI size x ROI "
+                         "count (GPU device, GPU end to end, CPU oracle) and the feature-group cost of an image "
+                         "of 100 ROIs of 100,000 px; families: the workload with the NGTDM and GLDM removed "
+                         "and alone (one JSON line each, not bench lines)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.sweep == "soft":
+        return run_soft_sweep(args)
+    if args.sweep == "scalability":
+        return run_scalability_sweep(args)
+    if args.sweep == "families":
+        return run_family_sweep(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    extra = [c for c in args.configs.split(",") if c]
+    # workloads first: the mosaic's tiles are generated in spawned processes,
+    # before this process makes any CUDA call
+    procs = max(1, min(16, (os.cpu_count() or 1) // max(1, world)))
+    wl = {name: make_workload(name, rank, procs) for name in [args.workload] + extra}
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2603_12016_gb300 import build
+
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clk = ClockSampler(local)
+    with clk:
+        head = run_config(args.workload, wl[args.workload], dev, dist, args, "core", clk, flush=flush)
+        allf = run_config(args.workload, wl[args.workload], dev, dist, args, "all", clk, light=True, flush=flush)
+        subs = {}
+        for name in extra:
+            subs[name] = run_config(name, wl[name], dev, dist, args, "all", clk, flush=flush)
     if rank != 0:
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return 0
-    cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(w, 20.0)
-    # begin, scan, key sort, setup, the block classes whose pixel limit is
-    # above 0, reset; multi-block class: zero, pass 1, pass 2, sorted order
-    # statistics (+ GLCM, + NGTDM); statistics final (+ GLCM features)
-    glcm = w.params["glcm_levels"] > 0
-    n_cls = sum(1 for v in (limits or (256, 1024, 8192)) if v > 0)
-    launches_per_step = 5 + n_cls + 4 + (2 if glcm else 0) + 1 + (1 if glcm else 0)
-    if bwd:  # begin, scan, key sort, setup, coefficients, per-pixel gradient, reset
-        launches_per_step += 7
+        head["cpu_baseline"] = cpu_baseline(wl[args.workload], 20.0, "all families (a superset of the timed set)")
+        for name in extra:
+            subs[name]["cpu_baseline"] = cpu_baseline(wl[name], 8.0, "all families")
+    w = wl[args.workload]
+    prm = w.params
     line = {
-        "metric": METRIC, "value": value, "unit": "ROIs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["value"], "unit": "ROIs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": w.name, "image": list(w.image.shape), "pixel_dtype": str(w.image.dtype),
-                   "n_roi": n_roi, "n_col": n_col, "glcm_levels": prm["glcm_levels"], "dists": list(prm["dists"]),
-                   "hist_bins": prm["hist_bins"], "features": "all", "step": "forward + backward" if bwd else "forward",
-                   "l2": "flushed (256 MB write) between steps", "class_limits_px": list(limits) if limits else None,
+                   "n_roi": head["n_roi"], "n_col": head["n_col"], "glcm_levels": prm["glcm_levels"],
+                   "dists": list(prm["dists"]), "hist_bins": prm["hist_bins"],
+                   "features": "hot-path set: first-order + order statistics, histogram, raw/central/normalised "
+                               "moments + Hu (intensity and binary), GLCM (30 features, direction means)",
+                   "step": head["step"], "l2": head["l2"], "class_limits_px": head["class_limits_px"],
+                   "scan_rows_per_warp": head["scan_rows_per_warp"],
+                   "class_limits_source": head["class_limits_source"],
                    "timing": "median of per-step CUDA-event times, CUDA-graph replay",
                    "parallelism": f"replicas{world}"},
-        "mpix_per_s": px_total / (t_step * 1e-3) / 1e6,
-        "roi_mpix_per_s": float((w.mask > 0).sum()) * world / (t_step * 1e-3) / 1e6,
-        "pipeline_hbm": {"algorithmic_bytes": alg, "achieved_gbs": pipe_gbs, "frac": pipe_gbs / peak,
-                         "peak": peak, "peak_kind": peak_kind},
-        "phases_ms": phases,
-        "roofline": roofline,
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "fp64_plain": fp64,
-        "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps,
+        "mpix_per_s": head["mpix_per_s"], "roi_mpix_per_s": head["roi_mpix_per_s"],
+        "pipeline_hbm": head["pipeline_hbm"], "phases_ms": head["phases_ms"], "roofline": head["roofline"],
+        "cpu_baseline": head.get("cpu_baseline"), "e2e": head["e2e"], "fp64_plain": head.get("fp64_plain"),
+        "all_features": {k: allf[k] for k in ("value", "unit", "ms_per_step", "n_col", "class_limits_px",
+                                               "class_limits_source", "phases_ms")},
+        "configs": subs,
+        "clocks": clk.summary(),
+        "gpu_launches": head["gpu_launches"],
+        "kernel_source": kernel_source_hash(),
     }
     print(json.dumps(line))
     if dist is not None:

@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
     L.nyx_count_rois_noalloc.restype = ctypes.c_int
     L.nyx_profile_enable.argtypes = [vp, ctypes.c_int]
     L.nyx_phase_times.argtypes = [vp, ctypes.c_int, P(ctypes.c_float), ctypes.c_int]
+    L.nyx_graph_phase_events.argtypes = [vp, ctypes.c_int]
+    L.nyx_graph_phase_times.argtypes = [vp, P(ctypes.c_float), ctypes.c_int]
     L.nyx_extract_tiles.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, TILE_FN, vp, vp, vp, vp, ctypes.c_int64, vp,
                                     ctypes.c_uint32, vp]
     L.nyx_extract_tiles.restype = ctypes.c_int
@@ -96,10 +98,13 @@ def lib() -> ctypes.CDLL:
     L.nyx_graph_captures.argtypes = [vp, P(ctypes.c_int64)]
     L.nyx_set_class_limits.argtypes = [vp, P(ctypes.c_int32)]
     L.nyx_autotune.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, vp, P(ctypes.c_int32)]
+    L.nyx_set_tuning.argtypes = [vp, P(ctypes.c_int32)]
+    L.nyx_get_tuning.argtypes = [vp, P(ctypes.c_int32)]
     for f in ("nyx_params_default", "nyx_create", "nyx_plan_create", "nyx_num_columns", "nyx_column_name",
               "nyx_count_rois", "nyx_extract", "nyx_sync_status", "nyx_backward", "nyx_debug_select",
               "nyx_debug_glcm", "nyx_debug_bins", "nyx_profile_enable", "nyx_phase_times", "nyx_use_graphs",
-              "nyx_graph_captures", "nyx_set_class_limits", "nyx_autotune"):
+              "nyx_graph_captures", "nyx_set_class_limits", "nyx_autotune", "nyx_graph_phase_events",
+              "nyx_graph_phase_times", "nyx_set_tuning", "nyx_get_tuning"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -107,6 +112,14 @@ def lib() -> ctypes.CDLL:
 
 def feature_id(name: str) -> int:
     return lib().nyx_feature_id(name.encode())
+
+
+# Feature ids of the hot-path feature set: first-order and order statistics
+# with the histogram features (Table S1 / S5, ids 0-40), raw / central /
+# normalised moments with Hu invariants (Table S2 / S5, ids 41-50) and the
+# GLCM features (Table S3, ids 51-80).  Ids 81 and up are the edge intensity
+# statistics, NGTDM and GLDM.
+CORE_FEATURE_IDS = tuple(range(81))
 
 
 def _stream_ptr(device: torch.device) -> int:
@@ -118,7 +131,7 @@ class Extractor:
 
     shape: (H, W) / (B, H, W) for ndim=2, (D, H, W) / (B, D, H, W) for
     ndim=3.  features: iterable of feature names (see nyx_feature_id) or
-    None for every feature (untargeted extraction)."""
+    feature ids, or None for every feature (untargeted extraction)."""
 
     def __init__(self, shape: Sequence[int], dtype: torch.dtype, ndim: int = 2, glcm_levels: int = 64,
                  dists: Sequence[int] = (1,), glcm_per_offset_cols: bool = False, hist_bins: int = 256,
@@ -145,7 +158,7 @@ class Extractor:
         if features is not None:
             mask = [0, 0, 0, 0]
             for f in features:
-                fid = feature_id(f)
+                fid = int(f) if isinstance(f, int) else feature_id(f)
                 if fid < 0:
                     raise KeyError(f"unknown feature {f}")
                 mask[fid >> 6] |= 1 << (fid & 63)
@@ -294,14 +307,26 @@ class Extractor:
         lim = (ctypes.c_int32 * 3)(warp, small, medium)
         self._check(lib().nyx_set_class_limits(self._plan, lim))
 
-    def autotune(self, img: torch.Tensor, mask: torch.Tensor, reps: int = 3) -> Tuple[int, int, int]:
-        """Time a grid of class limits on this input, keep the fastest."""
+    def autotune(self, img: torch.Tensor, mask: torch.Tensor, reps: int = 5) -> Tuple[int, int, int, int]:
+        """Time a grid of class limits, then of label-scan tile heights, on
+        this input (L2 flushed before every timed call), keep the fastest;
+        returns (warp, small, medium pixel limits, scan rows per warp)."""
         img, mask = self._inputs(img, mask)
         table = torch.empty((self.max_rois, len(self.columns)), dtype=torch.float64, device=self.device)
         lim = (ctypes.c_int32 * 3)()
         self._check(lib().nyx_autotune(self._plan, img.data_ptr(), mask.data_ptr(), table.data_ptr(), table.shape[0],
                                        int(reps), _stream_ptr(self.device), lim))
-        return tuple(int(v) for v in lim)
+        return self.tuning()
+
+    def tuning(self) -> Tuple[int, int, int, int]:
+        """(warp, small, medium pixel limits, scan rows per warp; 0 = chosen per call)."""
+        t = (ctypes.c_int32 * 4)()
+        self._check(lib().nyx_get_tuning(self._plan, t))
+        return tuple(int(v) for v in t)
+
+    def set_tuning(self, warp: int, small: int, medium: int, scan_rows: int = 0):
+        t = (ctypes.c_int32 * 4)(warp, small, medium, scan_rows)
+        self._check(lib().nyx_set_tuning(self._plan, t))
 
     def profile(self, slots: int = 1):
         """Record per-phase CUDA events for the next extracts (ring of
@@ -312,6 +337,20 @@ class Extractor:
         ms = (ctypes.c_float * len(self.PHASES))()
         self._check(lib().nyx_phase_times(self._plan, int(back), ms, len(self.PHASES)))
         return dict(zip(self.PHASES, [float(v) for v in ms]))
+
+    GRAPH_PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final",
+                    "stats_final", "reset", "roi_stage", "all")
+
+    def graph_phase_events(self, enable: bool = True):
+        """Record a begin and an end event around each phase inside the
+        replayed CUDA graph, on the stream the phase runs on."""
+        self._check(lib().nyx_graph_phase_events(self._plan, int(bool(enable))))
+
+    def graph_phase_times(self) -> dict:
+        """Per-phase durations (ms) of the most recent graph replay."""
+        ms = (ctypes.c_float * len(self.GRAPH_PHASES))()
+        self._check(lib().nyx_graph_phase_times(self._plan, ms, len(self.GRAPH_PHASES)))
+        return dict(zip(self.GRAPH_PHASES, [float(v) for v in ms]))
 
     def debug_select(self, roi: int):
         self._check(lib().nyx_debug_select(self._plan, int(roi)))
