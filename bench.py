@@ -138,16 +138,16 @@ def kernel_source_hash() -> str:
 
 
 def roi_classes(w, lim_pix):
-    """Pixels and ROI count per size class (warp, small, medium, multi-block)
-    by the library's class rule: pixel count against the class limits and
-    padded bounding-box cells against the class capacities 1,024 / 4,096 /
-    16,384."""
+    """Pixels and ROI count per size class (warp, small, medium, large,
+    multi-block) by the library's class rule: pixel count against the class
+    limits and padded bounding-box cells against the class capacities 1,024
+    / 4,096 / 8,192 / 16,384."""
     from scipy import ndimage
 
     pad = max(w.params["dists"])  # the plan pads every raster by the largest distance (>= 1)
-    lp = tuple(lim_pix)
-    lims = ((lp[0], 1024), (lp[1], 4096), (lp[2], 16384))
-    px, rows = [0, 0, 0, 0], [0, 0, 0, 0]
+    lims = tuple(zip(lim_pix, (1024, 4096, 8192, 16384)))
+    nc = len(lims)
+    px, rows = [0] * (nc + 1), [0] * (nc + 1)
     masks = w.mask.reshape((-1,) + w.mask.shape[-w.ndim:]) if w.mask.ndim > w.ndim else w.mask[None]
     for m in masks:
         cnt = np.bincount(m.ravel())
@@ -157,8 +157,8 @@ def roi_classes(w, lim_pix):
             ext = [s.stop - s.start + 2 * pad for s in sl]
             cells = int(np.prod(ext))
             n = int(cnt[lab])
-            k = 3
-            for i in (2, 1, 0):
+            k = nc
+            for i in range(nc - 1, -1, -1):
                 if n <= lims[i][0] and cells <= lims[i][1]:
                     k = i
             px[k] += n
@@ -181,20 +181,6 @@ def reduce_over_ranks(dist, device, t_ms: float, units: int):
     return float(tt.item()), int(nn.item())
 
 
-_MOSAIC = None
-
-
-def _mosaic_init(kw):
-    global _MOSAIC
-    from paper_2603_12016_gb300 import workloads as W
-
-    _MOSAIC = W.mosaic_2d(**kw)
-
-
-def _mosaic_tile(job):
-    return _MOSAIC.tile(*job)
-
-
 def make_workload(name: str, rank: int, procs: int = 1):
     from paper_2603_12016_gb300 import workloads as W
 
@@ -202,27 +188,7 @@ def make_workload(name: str, rank: int, procs: int = 1):
         # whole-slide stand-in generated tile by tile (tiles in parallel
         # processes, started with spawn before any CUDA call); the assembled
         # arrays are what the host streams
-        big = name == "mosaic"
-        kw = dict(size=32768 if big else 8192, tile=4096 if big else 1024, n_roi=500_000 if big else 32_000,
-                  seed=1005 + rank)
-        m = W.mosaic_2d(**kw)
-        if procs > 1:
-            import multiprocessing as mp
-
-            img = np.empty((m.size, m.size), dtype=np.uint16)
-            mask = np.empty((m.size, m.size), dtype=np.int32)
-            t = m.tile_size
-            jobs = [(x0, y0, min(t, m.size - x0), min(t, m.size - y0))
-                    for y0 in range(0, m.size, t) for x0 in range(0, m.size, t)]
-            with mp.get_context("spawn").Pool(procs, initializer=_mosaic_init, initargs=(kw,)) as pool:
-                for (x0, y0, w_, h_), (ti, tm) in zip(jobs, pool.imap(_mosaic_tile, jobs)):
-                    img[y0:y0 + h_, x0:x0 + w_] = ti
-                    mask[y0:y0 + h_, x0:x0 + w_] = tm
-        else:
-            img, mask = m.assemble()
-        n_roi = int(np.count_nonzero(np.bincount(mask.ravel())[1:]))
-        return W.Workload(m.name, img, mask, 2, params=dict(m.params),
-                          meta={"n_roi": n_roi, "tile": m.tile_size})
+        return W.mosaic_workload(name, rank, procs)
     return W.config(name, seed_offset=rank)
 
 
@@ -439,7 +405,7 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     dev_name = torch.cuda.get_device_name(dev)
     if args.class_limits:
         limits = tuple(int(v) for v in args.class_limits.split(","))
-        limits, lim_src = (limits + (0,))[:4], "command line"
+        limits, lim_src = (limits + (0,))[:5], "command line"
         ex.set_tuning(*limits)
     else:
         limits, lim_src = tuning.limits_for(ex, dev_name, sig)
@@ -503,7 +469,7 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     res = {"workload": w.name, "features": features, "n_roi": n_roi, "n_col": n_col,
            "value": n_total / (t_step * 1e-3), "unit": "ROIs/s", "ms_per_step": t_step,
            "step": "forward + backward" if bwd else "forward",
-           "class_limits_px": list(limits[:3]), "scan_rows_per_warp": limits[3], "class_limits_source": lim_src,
+           "class_limits_px": list(limits[:4]), "scan_rows_per_warp": limits[4], "class_limits_source": lim_src,
            "mpix_per_s": w.image.size * (dist.get_world_size() if dist else 1) / (t_step * 1e-3) / 1e6,
            "phases_ms": {k: round(v, 5) for k, v in phases.items()}}
     if light:
@@ -513,7 +479,7 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     # algorithmic bytes per launch (the scan streams image + mask once; a ROI
     # class reads its ROIs' pixels and mask once and writes their table rows;
     # the backward pass reads image + mask and writes the gradient)
-    cls_px, cls_rows = roi_classes(w, limits[:3])
+    cls_px, cls_rows = roi_classes(w, limits[:4])
     n_off = len(prm["dists"]) * (13 if w.ndim == 3 else 4) if prm["glcm_levels"] > 0 else 0
     per_px = w.image.itemsize + 4
     # The four size classes run as concurrent graph branches, each holding SMs
@@ -549,7 +515,7 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     # pass 2, order statistics, + GLCM, + neighbour kernel); GLCM features;
     # statistics; reset; backward: coefficients + per-pixel gradient + reset
     glcm = prm["glcm_levels"] > 0
-    n_cls = sum(1 for v in limits if v > 0)
+    n_cls = sum(1 for v in limits[:4] if v > 0)
     per_step = 3 + n_cls + 4 + (2 if glcm else 0) + (1 if glcm else 0) + 1 + 1 + (3 if bwd else 0)
     res["gpu_launches"] = per_step * args.steps
 
@@ -618,7 +584,7 @@ def main() -> int:
                     help="time forward + backward (default for the blobbatch workloads)")
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--class-limits", default=None,
-                    help="warp,small,medium pixel limits[,scan rows per warp] instead of the tuned ones")
+                    help="warp,small,medium,large pixel limits[,scan rows per warp] instead of the tuned ones")
     ap.add_argument("--sweep", default=None, choices=["soft", "scalability", "families"],
                     help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
                          "separability grid on labelled texture classes; scalability: time over ROI size x ROI "

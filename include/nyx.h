@@ -175,23 +175,28 @@ nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
  * depends on ROI size and count, Fig. 3f/g).  Every ROI
  * goes to the first class whose pixel limit and padded bounding-box cell
  * capacity it fits: one warp per ROI (capacity 256 px / 1,024 cells), one
- * 128-thread block (1,024 / 4,096), one 512-thread block (8,192 / 16,384),
- * else the multi-block path.  lim_pix[3] sets the pixel limits of the first
- * three classes (0 disables a class; each at most its capacity above).
+ * 128-thread block (1,024 / 4,096), one 256-thread block (4,096 / 8,192; two
+ * blocks per SM), one 512-thread block (8,192 / 16,384; one block per SM),
+ * else the multi-block path.  lim_pix[NYX_N_CLASSES] sets the pixel limits
+ * of these block classes (0 disables a class; each at most its capacity).
  * nyx_autotune times the extraction of (d_img, d_mask) under a grid of
- * limits (warp 0/64/128/256, small 0/512/1024, medium 2048/4096/8192), then
+ * limits (warp 0/64/128/256, small 0/512/1024, medium 0/2048/4096, large
+ * 0/8192), then
  * under the label scan's tile heights (8/16/32 rows per warp, tiles of 128
  * columns by 64/128/256 rows) with the best limits; each candidate is timed
  * as the median of `reps` calls, every call preceded by a 256 MB write that
  * flushes the L2 cache (allocated and freed inside this call).  It keeps the
  * fastest setting in the plan and returns the limits in h_lim_pix (host
- * int32[3], may be NULL); nyx_get_tuning reads the tile height too.
+ * int32[NYX_N_CLASSES], may be NULL); nyx_get_tuning reads the tile height
+ * too.
  * d_table / cap_roi as in nyx_extract.  Synchronises.  Results do not depend
  * on these settings beyond floating-point rounding.  Errors: NYX_ERR_ARG,
  * and those of nyx_extract.
- * nyx_set_tuning / nyx_get_tuning: t[0..2] the class pixel limits as above,
- * t[3] the scan's rows per warp (0: chosen from the tile count; else 4, 8,
- * 16 or 32); t is host int32[4].  Errors: NYX_ERR_ARG. */
+ * nyx_set_tuning / nyx_get_tuning: t[0..NYX_N_CLASSES) the class pixel
+ * limits as above, t[NYX_N_CLASSES] the scan's rows per warp (0: chosen from
+ * the tile count; else 4, 8, 16 or 32); t is host int32[NYX_N_CLASSES + 1].
+ * Errors: NYX_ERR_ARG. */
+#define NYX_N_CLASSES 4
 nyx_status nyx_set_class_limits(nyx_plan* plan, const int32_t* lim_pix);
 nyx_status nyx_set_tuning(nyx_plan* plan, const int32_t* t);
 nyx_status nyx_get_tuning(const nyx_plan* plan, int32_t* t);
@@ -270,12 +275,12 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
  * slots - 1) and writes up to NYX_N_PHASES durations in milliseconds:
  * [0] counters + label scan, [1] key sort + per-ROI setup, [2] ROI kernel of
  * the warp class (one warp per ROI), [3] of the small block class, [4] of the
- * medium block class, [5] the multi-block class (ROIs larger than a block
- * stages), [6] statistics, moments and GLCM features from the per-ROI sums,
- * [7] table reset.
+ * medium block class, [5] of the large block class, [6] the multi-block
+ * class (ROIs larger than a block stages), [7] statistics, moments and GLCM
+ * features from the per-ROI sums, [8] table reset.
  * Errors: NYX_ERR_ARG (null plan/ms, slots out of 0..1024, back out of
  * range), NYX_ERR_STATE (that extract was not recorded), NYX_ERR_CUDA. */
-#define NYX_N_PHASES 8
+#define NYX_N_PHASES 9
 nyx_status nyx_profile_enable(nyx_plan* plan, int slots);
 nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
 
@@ -285,8 +290,8 @@ nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
  * phase runs on (the size classes run as parallel branches).  Toggling drops
  * the cached graphs.  nyx_graph_phase_times waits for the most recent replay
  * and writes up to NYX_N_GPHASES durations in milliseconds, indexed by
- * NYX_GPH_*: label scan, key sort + setup, the warp / small / medium block
- * classes, the multi-block class, the GLCM feature kernel, the statistics
+ * NYX_GPH_*: label scan, key sort + setup, the warp / small / medium / large
+ * block classes, the multi-block class, the GLCM feature kernel, the statistics
  * kernel, the table reset, the per-ROI stage (from before the size classes
  * fork to after they join: the four classes run as concurrent branches, so
  * each class's own span includes waiting for SMs that the others hold), and
@@ -294,7 +299,7 @@ nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
  * Errors: NYX_ERR_ARG (null plan/ms), NYX_ERR_STATE (events off or graphs
  * off), NYX_ERR_CUDA. */
 enum {
-  NYX_GPH_SCAN = 0, NYX_GPH_SORT, NYX_GPH_WARP, NYX_GPH_SMALL, NYX_GPH_MED, NYX_GPH_BIG, NYX_GPH_GLCMF,
+  NYX_GPH_SCAN = 0, NYX_GPH_SORT, NYX_GPH_WARP, NYX_GPH_SMALL, NYX_GPH_MED, NYX_GPH_LARGE, NYX_GPH_BIG, NYX_GPH_GLCMF,
   NYX_GPH_STATSF, NYX_GPH_RESET, NYX_GPH_ROI, NYX_GPH_ALL, NYX_N_GPHASES
 };
 nyx_status nyx_graph_phase_events(nyx_plan* plan, int enable);

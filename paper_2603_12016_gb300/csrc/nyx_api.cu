@@ -132,6 +132,11 @@ struct nyx_plan {
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
 };
 
+// staging capacities (pixels, padded raster cells) of the block classes:
+// warp, small (128 threads), medium (256), large (512)
+static const int c_class_pix[N_BLOCK_CLASSES] = {256, 1024, 4096, 8192};
+static const int c_class_cells[N_BLOCK_CLASSES] = {1024, 4096, 8192, 16384};
+
 static void drop_graph(nyx_plan* pl) {
   for (int i = 0; i < nyx_plan::NGRAPH; ++i) {
     if (pl->graph_exec[i]) cudaGraphExecDestroy(pl->graph_exec[i]);
@@ -396,7 +401,7 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   };
   const size_t o_keys = take(8ull * hcap), o_slots = take(sizeof(SlotAcc) * hcap), o_slist = take(4ull * hcap),
                o_sdense = take(4ull * hcap), o_sorted = take(8ull * mr), o_rois = take(sizeof(RoiInfo) * mr),
-               o_queue = take(4ull * 3 * mr), o_small = take(64), o_imin = take(4ull * p.batch),
+               o_queue = take(4ull * N_BLOCK_CLASSES * mr), o_small = take(64), o_imin = take(4ull * p.batch),
                o_imax = take(4ull * p.batch), o_cmap = take(4ull * Q_TOTAL), o_big = take(sizeof(BigRoi) * mr),
                o_bigctr = take(64);
   // big-ROI arena: the per-ROI regions of the multi-block class (value
@@ -519,12 +524,10 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.n_col = (int)pl->col_names.size();
   k.max_rois = mr;
   k.dbg_roi = -1;
-  k.lim_pix[0] = 256;
-  k.lim_cells[0] = 1024;
-  k.lim_pix[1] = 1024;
-  k.lim_cells[1] = 4096;
-  k.lim_pix[2] = 8192;
-  k.lim_cells[2] = 16384;
+  for (int c = 0; c < N_BLOCK_CLASSES; ++c) {  // staging capacities of the block classes
+    k.lim_pix[c] = c_class_pix[c];
+    k.lim_cells[c] = c_class_cells[c];
+  }
   e = cudaMemcpy(pl->d_col_map, pl->col_map.data(), 4ull * Q_TOTAL, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(w + o_wtab_f, wf.data(), 4ull * 5 * ngw, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(w + o_wtab_d, wd.data(), 8ull * 5 * ngw, cudaMemcpyHostToDevice);
@@ -720,8 +723,8 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     s_med = pl->side[0];
     s_big = pl->side[1];
   }
-  for (int cls = 0; cls < 3; ++cls) {
-    cudaStream_t sc = cls == 2 ? s_med : st;
+  for (int cls = 0; cls < N_BLOCK_CLASSES; ++cls) {
+    cudaStream_t sc = cls >= 2 ? s_med : st;  // medium and large classes on one side branch
     NYX_CUDA(c, gmark(gev, NYX_GPH_WARP + cls, 0, sc));
     const cudaError_t e = k.lim_pix[cls] > 0 ? launch_class(k, cls, fp64, c->nsm, sc) : cudaSuccess;
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "ROI kernel launch failed: %s", cudaGetErrorString(e));
@@ -733,7 +736,7 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     const cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
     NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 1, s_big));
-    if (ev) NYX_CUDA(c, cudaEventRecord(ev[6], st));
+    if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
   }
   if (fork) {  // join, then fork the GLCM feature kernel
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[1], s_med));
@@ -770,7 +773,7 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
   }
   {  // statistics, moments and Hu invariants from the per-ROI sums
     NYX_CUDA(c, gmark(gev, NYX_GPH_STATSF, 0, st));
-    const cudaError_t e = launch_class(k, 3, fp64, c->nsm, st);
+    const cudaError_t e = launch_class(k, N_BLOCK_CLASSES, fp64, c->nsm, st);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "statistics kernel launch failed: %s", cudaGetErrorString(e));
     NYX_CUDA(c, gmark(gev, NYX_GPH_STATSF, 1, st));
   }
@@ -782,7 +785,7 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[5], s_rs));
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[5], 0));
   }
-  if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
+  if (ev) NYX_CUDA(c, cudaEventRecord(ev[8], st));
   if (reset && s_rs == st) {
     NYX_CUDA(c, gmark(gev, NYX_GPH_RESET, 0, st));
     if ((s = run_reset(pl, const_cast<KParams&>(k), st)) != NYX_OK) return s;
@@ -1025,13 +1028,15 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   nyx_ctx* c = pl->ctx;
   cudaStream_t st = (cudaStream_t)stream;
   NYX_CUDA(c, cudaSetDevice(c->device));
-  // candidate pixel thresholds of the warp, small and medium classes (0 =
-  // class unused; the cell limits stay at each class's staging capacity),
-  // then the label scan's rows per warp (tile heights 64 / 128 / 256)
-  static const int cw[] = {0, 64, 128, 256}, cs[] = {0, 512, 1024}, cm[] = {2048, 4096, 8192}, cr[] = {8, 16, 32};
+  // candidate pixel thresholds of the warp, small, medium and large classes
+  // (0 = class unused; the cell limits stay at each class's staging
+  // capacity), then the label scan's rows per warp (tile heights 64/128/256)
+  static const int cw[] = {0, 64, 128, 256}, cs[] = {0, 512, 1024}, cm[] = {0, 2048, 4096}, cl[] = {0, 8192},
+                   cr[] = {8, 16, 32};
   const int saved_prof = pl->prof_slots;
   pl->prof_slots = 0;
-  int best[3] = {pl->kp.lim_pix[0], pl->kp.lim_pix[1], pl->kp.lim_pix[2]};
+  int best[N_BLOCK_CLASSES];
+  for (int i = 0; i < N_BLOCK_CLASSES; ++i) best[i] = pl->kp.lim_pix[i];
   int best_rpt = pl->kp.scan_rpt;
   float best_ms = 3.0e38f;
   // an L2-sized write between timed calls, so that every candidate starts
@@ -1044,22 +1049,29 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   NYX_CUDA(c, cudaEventCreate(&e1));
   for (int a : cw)
     for (int b : cs)
-      for (int m : cm) {
-        if ((b && b <= a) || m <= (a > b ? a : b)) continue;
-        pl->kp.lim_pix[0] = a;
-        pl->kp.lim_pix[1] = b;
-        pl->kp.lim_pix[2] = m;
-        float ms = 0;
-        s = time_config(pl, d_img, d_mask, d_table, cap_roi, reps, st, flush, flush_bytes, e0, e1, &ms);
-        if (s != NYX_OK) break;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best[0] = a;
-          best[1] = b;
-          best[2] = m;
+      for (int m : cm)
+        for (int l : cl) {
+          // nonzero limits must increase with the class, and some block class
+          // must take ROIs above the warp class
+          const int lim[N_BLOCK_CLASSES] = {a, b, m, l};
+          int top = 0;
+          bool ok = true;
+          for (int i = 0; i < N_BLOCK_CLASSES; ++i)
+            if (lim[i]) {
+              ok = ok && lim[i] > top;
+              top = lim[i];
+            }
+          if (!ok || (b == 0 && m == 0 && l == 0)) continue;
+          for (int i = 0; i < N_BLOCK_CLASSES; ++i) pl->kp.lim_pix[i] = lim[i];
+          float ms = 0;
+          s = time_config(pl, d_img, d_mask, d_table, cap_roi, reps, st, flush, flush_bytes, e0, e1, &ms);
+          if (s != NYX_OK) break;
+          if (ms < best_ms) {
+            best_ms = ms;
+            for (int i = 0; i < N_BLOCK_CLASSES; ++i) best[i] = lim[i];
+          }
         }
-      }
-  for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = best[i];
+  for (int i = 0; i < N_BLOCK_CLASSES; ++i) pl->kp.lim_pix[i] = best[i];
   if (s == NYX_OK) {
     best_ms = 3.0e38f;
     for (int r : cr) {
@@ -1081,34 +1093,35 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   pl->prof_slots = saved_prof;
   if (s != NYX_OK) return s;
   if (h_lim_pix)
-    for (int i = 0; i < 3; ++i) h_lim_pix[i] = best[i];
+    for (int i = 0; i < N_BLOCK_CLASSES; ++i) h_lim_pix[i] = best[i];
   return NYX_OK;
 }
 
 nyx_status nyx_set_tuning(nyx_plan* pl, const int32_t* t) {
   if (!pl || !t) return NYX_ERR_ARG;
-  if (t[3] != 0 && t[3] != 4 && t[3] != 8 && t[3] != 16 && t[3] != 32)
+  const int r = t[N_BLOCK_CLASSES];
+  if (r != 0 && r != 4 && r != 8 && r != 16 && r != 32)
     return fail(pl->ctx, NYX_ERR_ARG, "scan rows per warp must be 0, 4, 8, 16 or 32");
   nyx_status s = nyx_set_class_limits(pl, t);
   if (s != NYX_OK) return s;
-  pl->kp.scan_rpt = t[3];
+  pl->kp.scan_rpt = r;
   drop_graph(pl);
   return NYX_OK;
 }
 
 nyx_status nyx_get_tuning(const nyx_plan* pl, int32_t* t) {
   if (!pl || !t) return NYX_ERR_ARG;
-  for (int i = 0; i < 3; ++i) t[i] = pl->kp.lim_pix[i];
-  t[3] = pl->kp.scan_rpt;
+  for (int i = 0; i < N_BLOCK_CLASSES; ++i) t[i] = pl->kp.lim_pix[i];
+  t[N_BLOCK_CLASSES] = pl->kp.scan_rpt;
   return NYX_OK;
 }
 
 nyx_status nyx_set_class_limits(nyx_plan* pl, const int32_t* lim_pix) {
   if (!pl || !lim_pix) return NYX_ERR_ARG;
-  const int cap[3] = {256, 1024, 8192};
-  for (int i = 0; i < 3; ++i)
-    if (lim_pix[i] < 0 || lim_pix[i] > cap[i]) return fail(pl->ctx, NYX_ERR_ARG, "class limit %d out of 0..%d", i, cap[i]);
-  for (int i = 0; i < 3; ++i) pl->kp.lim_pix[i] = lim_pix[i];
+  for (int i = 0; i < N_BLOCK_CLASSES; ++i)
+    if (lim_pix[i] < 0 || lim_pix[i] > c_class_pix[i])
+      return fail(pl->ctx, NYX_ERR_ARG, "class limit %d out of 0..%d", i, c_class_pix[i]);
+  for (int i = 0; i < N_BLOCK_CLASSES; ++i) pl->kp.lim_pix[i] = lim_pix[i];
   drop_graph(pl);
   return NYX_OK;
 }

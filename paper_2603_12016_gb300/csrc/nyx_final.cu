@@ -9,28 +9,24 @@
 // Doing this outside the accumulation kernels keeps their blocks from idling
 // at a barrier while one thread runs the serial feature arithmetic.  Every
 // feature is a quotient of exact integer numerators (finalize_glcm); the
-// direction means are summed in FP64.
+// direction means are compensated sums.
 #include "nyx_roi.cuh"
 
 namespace nyx {
 
-constexpr int FIN_STRIDE = NGLCM + 3;  // odd row stride (doubles) of the shared feature matrix
-
-// 1 / c for the number c of directions with pairs (1 .. 13), correctly rounded
-__device__ __constant__ const double c_inv_dirs[MAX_DIRS + 1] = {
-    0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13};
+constexpr int FIN_STRIDE = NGLCM + 3;  // odd row stride (in A) of the shared feature matrix
 
 template <class A>
 __global__ void __launch_bounds__(256) k_glcm_final(KParams p, int rpb) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* sf = (double*)smem;  // [rpb * n_off][FIN_STRIDE]
+  A* sf = (A*)smem;  // [rpb * n_off][FIN_STRIDE]
   const int n_off = p.n_dist * p.n_dirs;
   const int64_t nroi = min((int64_t)*p.n_roi, p.cap_roi);
-  const double nan = anan<double>();
+  const A nan = anan<A>();
   const int lr = threadIdx.x / n_off, oi = threadIdx.x - lr * n_off;
   for (int64_t base = (int64_t)blockIdx.x * rpb; base < nroi; base += (int64_t)gridDim.x * rpb) {
     const int64_t item = base + lr;
-    double* f = sf + threadIdx.x * FIN_STRIDE;
+    A* f = sf + threadIdx.x * FIN_STRIDE;
     if (lr < rpb && item < nroi) {
       const long long* g = (const long long*)(p.gacc + ((size_t)item * n_off + oi) * GACC_BYTES);
       double* row = p.table + item * p.n_col;
@@ -40,29 +36,37 @@ __global__ void __launch_bounds__(256) k_glcm_final(KParams p, int rpb) {
       for (int k = 0; k < GN; ++k) iv[k] = g[k];
       if (iv[0] == 0) {  // offset without pairs
         if (p.per_offset)
-          for (int k = 0; k < NGLCM; ++k) put(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + k, nan);
+          for (int k = 0; k < NGLCM; ++k) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + k, nan);
         f[NGLCM] = 0;
       } else {
         finalize_glcm<A>(p, row, iv, di, dir, f);
       }
     }
     __syncthreads();
-    // direction means (FP64), summed in offset order
+    // direction means, compensated sums in offset order (features that
+    // change sign with the direction keep the accuracy of their mean)
     const int per_roi = p.n_dist * NGLCM;
     for (int t = threadIdx.x; t < rpb * per_roi; t += blockDim.x) {
       const int l2 = t / per_roi, rem = t - l2 * per_roi;
       const int di = rem / NGLCM, k = rem - di * NGLCM;
       const int64_t it = base + l2;
       if (it >= nroi) continue;
-      double s = 0, c = 0;
+      A s = 0, e = 0;
+      int c = 0;
       for (int dir = 0; dir < p.n_dirs; ++dir) {
-        const double* fo = sf + (l2 * n_off + di * p.n_dirs + dir) * FIN_STRIDE;
+        const A* fo = sf + (l2 * n_off + di * p.n_dirs + dir) * FIN_STRIDE;
         if (fo[NGLCM] == 0) continue;
-        s += fo[k];
-        c += 1;
+        if constexpr (std::is_same<A, float>::value) {
+          float t, er;
+          two_sum(s, fo[k], t, er);
+          s = t;
+          e += er;
+        } else {
+          s += fo[k];
+        }
+        ++c;
       }
-      // 1/c from a table (c <= 13 directions): no FP64 division
-      put(p, p.table + it * p.n_col, Q_GLCM_D + di * NGLCM + k, c > 0 ? s * c_inv_dirs[(int)c] : nan);
+      putA(p, p.table + it * p.n_col, Q_GLCM_D + di * NGLCM + k, c > 0 ? (s + e) / (A)c : nan);
     }
     __syncthreads();
   }
@@ -73,7 +77,7 @@ static cudaError_t launch_final_t(const KParams& p, int nsm, cudaStream_t st) {
   const int n_off = p.n_dist * p.n_dirs;
   const int rpb = n_off >= 256 ? 1 : 256 / n_off;
   const int nt = rpb * n_off;
-  const int smem = nt * FIN_STRIDE * (int)sizeof(double);
+  const int smem = nt * FIN_STRIDE * (int)sizeof(A);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

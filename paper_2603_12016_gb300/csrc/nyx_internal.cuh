@@ -27,6 +27,8 @@ constexpr int MAX_DIST = 8;
 constexpr int MAX_DIRS = 13;
 constexpr int NGLCM = 30;
 constexpr int SORT_CAP = 16384;  // ROIs sortable by the single-block label sort
+constexpr int N_BLOCK_CLASSES = NYX_N_CLASSES;  // warp, small, medium, large block classes
+constexpr int BIG_CLASS = N_BLOCK_CLASSES;      // class index of the multi-block path
 constexpr int GI_HOST = 12, GF_HOST = 8;  // GLCM accumulator sizes (int64 sums, float sums)
 // c log2 c (2^-24 units) of every count c < CLOG_N comes from the plan's table,
 // rounded once from FP64: it covers every count of the block classes (at
@@ -193,9 +195,9 @@ struct KParams {
   unsigned long long* sorted_keys;
   RoiInfo* rois;
   int* slot_dense;
-  int* queue;                      // [3][max_rois], one per size class
-  unsigned* qlen;                  // [3]
-  unsigned* qhead;                 // [3]
+  int* queue;                      // [N_BLOCK_CLASSES][max_rois], one per block class
+  unsigned* qlen;                  // [N_BLOCK_CLASSES]
+  unsigned* qhead;                 // [N_BLOCK_CLASSES]
   unsigned* n_roi;                 // device ROI count
   unsigned* err;
   int64_t max_rois, cap_roi;
@@ -206,8 +208,8 @@ struct KParams {
   int64_t dbg_roi;
   unsigned* dbg_glcm;              // [n_off][ng*ng]
   // class limits (pixels, padded raster cells): 0 warp path, 1 small
-  // block path, 2 medium block path
-  int lim_pix[3], lim_cells[3];
+  // block path, 2 medium block path, 3 large block path
+  int lim_pix[N_BLOCK_CLASSES], lim_cells[N_BLOCK_CLASSES];
   // multi-block class
   BigRoi* big;                     // [max_rois]
   unsigned long long* big_ctr;     // (n_big << 44) | (n_pass_units << 22) | n_glcm_units

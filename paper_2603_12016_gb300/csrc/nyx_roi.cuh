@@ -50,8 +50,9 @@ struct RoiClass {
   static constexpr int TAB = 2 * PIX_;  // GLCM hash capacity (power of two); also 2 sort buffers
 };
 using ClassW = RoiClass<32, 256, 1024>;    // one warp per ROI
-using ClassS = RoiClass<128, 1024, 4096, 6>;  // 6 blocks of ~37 KB shared memory fit an SM
-using ClassM = RoiClass<512, 8192, 16384>;
+using ClassS = RoiClass<128, 1024, 4096, 6>;  // 6 blocks of ~35 KB shared memory fit an SM
+using ClassM = RoiClass<256, 4096, 8192, 2>;  // 2 blocks of ~100 KB fit an SM
+using ClassL = RoiClass<512, 8192, 16384>;    // one block of ~200 KB per SM
 
 constexpr int RED_MAX = 32;  // max values per block reduction (and per warp slot of the scratch)
 
@@ -746,13 +747,14 @@ __device__ inline long long mi_fx(unsigned Cc, long long T, unsigned pa, unsigne
 // GLCM features of one offset (Table S3 rows 140-174): every moment-type
 // feature from exact integer power sums (central moments of the sum /
 // difference / row distributions as exact integer numerators over powers of
-// T), the entropies from the marginal sums.  Accumulates the direction mean
-// in FP64.  Every feature is a quotient of exact integer (or fixed-point)
-// numerators, so none cancels in A: the entropies come as T log2 T - sum c
-// log2 c, CORR as its exact covariance and variance numerators.
+// T), the entropies from the marginal sums.  Every feature is a quotient of
+// exact integer (or fixed-point) numerators, so none cancels in A: the
+// entropies come as T log2 T - sum c log2 c, CORR as its exact covariance
+// and variance numerators.  Writes f[0..NGLCM) (the caller's shared-memory
+// row) and f[NGLCM] = 1 (the offset has pairs).
 template <class A>
 __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const long long* iv, int di, int dir,
-                                           double* f) {
+                                           A* f) {
   typedef __int128 I;
   const long long T = iv[0], S1 = iv[1], S2 = iv[2], S3 = iv[3], S4 = iv[4], D1 = iv[5], D2 = iv[6], Q2 = iv[7];
   const A Ta = i128A<A>(T), invT = (A)1 / Ta;
@@ -790,43 +792,43 @@ __device__ __noinline__ void finalize_glcm(const KParams& p, double* row, const 
   const A corr = var_n > 0 ? i128A<A>(cov_n) / i128A<A>(var_n) : (A)1;
   A fv[5];
   for (int k = 0; k < 5; ++k) fv[k] = i128A<A>(iv[15 + k]) * (A)(1.0 / 4294967296.0) * invT;  // ID, IDM, IDN, IDMN, IV
-  f[G_ASM] = to_d(asmv);
-  f[G_ACOR] = to_d(i128A<A>((I)S2 - D2) * invT / 4);
-  f[G_CLUPROM] = to_d(cluprom);
-  f[G_CLUSHADE] = to_d(clushade);
-  f[G_CLUTEND] = to_d(sumvar);
-  f[G_CONTRAST] = to_d(contrast);
-  f[G_CORR] = to_d(corr);
-  f[G_DIFAVE] = to_d(difave);
-  f[G_DIFENTRO] = to_d(difent);
-  f[G_DIFVAR] = to_d(difvar);
-  f[G_DIS] = to_d(difave);
-  f[G_ENERGY] = to_d(asqrt(asmv));
-  f[G_ENTROPY] = to_d(je);
-  f[G_HOM1] = to_d(fv[0]);
-  f[G_HOM2] = to_d(fv[1]);
-  f[G_IDM] = to_d(fv[1]);
+  f[G_ASM] = asmv;
+  f[G_ACOR] = i128A<A>((I)S2 - D2) * invT / 4;
+  f[G_CLUPROM] = cluprom;
+  f[G_CLUSHADE] = clushade;
+  f[G_CLUTEND] = sumvar;
+  f[G_CONTRAST] = contrast;
+  f[G_CORR] = corr;
+  f[G_DIFAVE] = difave;
+  f[G_DIFENTRO] = difent;
+  f[G_DIFVAR] = difvar;
+  f[G_DIS] = difave;
+  f[G_ENERGY] = asqrt(asmv);
+  f[G_ENTROPY] = je;
+  f[G_HOM1] = fv[0];
+  f[G_HOM2] = fv[1];
+  f[G_IDM] = fv[1];
   // HXY1 = HXY2 = HX + HY and HX = HY for a symmetric matrix, so
   // HXY - HXY1 = -MI and HXY2 - HXY = MI (mutual information)
-  f[G_INFOMEAS1] = to_d(hx > 0 ? -mi / hx : (A)0);
+  f[G_INFOMEAS1] = hx > 0 ? -mi / hx : (A)0;
   {
     const A arg = -aexpm1((A)-2 * mi);  // 1 - exp(-2 MI) without cancellation for small MI
-    f[G_INFOMEAS2] = to_d(asqrt(arg > 0 ? arg : (A)0));
+    f[G_INFOMEAS2] = asqrt(arg > 0 ? arg : (A)0);
   }
-  f[G_IDMN] = to_d(fv[3]);
-  f[G_ID] = to_d(fv[0]);
-  f[G_IDN] = to_d(fv[2]);
-  f[G_IV] = to_d(fv[4]);
-  f[G_JAVE] = to_d(mu);
-  f[G_JE] = to_d(je);
-  f[G_JMAX] = to_d(i128A<A>(iv[11]) * invT);
-  f[G_SUMAVE] = to_d(sumave);
-  f[G_SUMENT] = to_d(sument);
-  f[G_JVAR] = to_d(var);
-  f[G_SUMVAR] = to_d(sumvar);
-  f[G_VARIANCE] = to_d(var);
+  f[G_IDMN] = fv[3];
+  f[G_ID] = fv[0];
+  f[G_IDN] = fv[2];
+  f[G_IV] = fv[4];
+  f[G_JAVE] = mu;
+  f[G_JE] = je;
+  f[G_JMAX] = i128A<A>(iv[11]) * invT;
+  f[G_SUMAVE] = sumave;
+  f[G_SUMENT] = sument;
+  f[G_JVAR] = var;
+  f[G_SUMVAR] = sumvar;
+  f[G_VARIANCE] = var;
   if (p.per_offset)
-    for (int g = 0; g < NGLCM; ++g) put(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
+    for (int g = 0; g < NGLCM; ++g) putA(p, row, Q_GLCM_O + (di * MAX_DIRS + dir) * NGLCM + g, f[g]);
   f[NGLCM] = 1;
 }
 
@@ -2242,13 +2244,16 @@ cudaError_t launch_roi_c(const KParams& p, int cls, int fp64, int nsm, cudaStrea
   return fp64 ? launch_roi_one<T, 2, C, double>(p, cls, nsm, st) : launch_roi_one<T, 2, C, float>(p, cls, nsm, st);
 }
 
-// cls 0..2: the block classes; cls 3: k_stats_final over all ROIs
+// cls 0..N_BLOCK_CLASSES-1: the block classes; cls N_BLOCK_CLASSES:
+// k_stats_final over all ROIs
 template <class T>
 cudaError_t launch_roi_t(const KParams& p, int cls, int fp64, int nsm, cudaStream_t st) {
+  static_assert(N_BLOCK_CLASSES == 4, "one case per block class");
   switch (cls) {
     case 0: return launch_roi_c<T, ClassW>(p, cls, fp64, nsm, st);
     case 1: return launch_roi_c<T, ClassS>(p, cls, fp64, nsm, st);
     case 2: return launch_roi_c<T, ClassM>(p, cls, fp64, nsm, st);
+    case 3: return launch_roi_c<T, ClassL>(p, cls, fp64, nsm, st);
     default:
       if (p.ndim == 3)
         return fp64 ? launch_stats_final<T, 3, double>(p, nsm, st) : launch_stats_final<T, 3, float>(p, nsm, st);

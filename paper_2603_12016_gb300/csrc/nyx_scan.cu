@@ -654,7 +654,7 @@ __global__ void k_setup(KParams p) {
     if (s < 0) {  // cannot happen: every sorted key came from the table
       atomicOr(p.err, E_INTERNAL);
       r.n = 0;
-      r.cls = 3;
+      r.cls = BIG_CLASS;
       p.rois[i] = r;
       continue;
     }
@@ -672,14 +672,14 @@ __global__ void k_setup(KParams p) {
     const long long cells = (long long)(r.w + 2 * pad) * (r.h + 2 * pad) * (p.ndim == 3 ? r.d + 2 * pad : 1);
     bool pack_ok = p.ndim == 3 ? (r.w + 2 * pad <= 2048 && r.h + 2 * pad <= 2048 && r.d + 2 * pad <= 1024)
                                : (r.w + 2 * pad <= 65535 && r.h + 2 * pad <= 65535);
-    int cls = 3;  // beyond every single-block path
-    for (int c = 2; c >= 0; --c)
+    int cls = BIG_CLASS;  // beyond every single-block path
+    for (int c = N_BLOCK_CLASSES - 1; c >= 0; --c)
       if (pack_ok && r.n <= (unsigned)p.lim_pix[c] && cells <= p.lim_cells[c]) cls = c;
     r.cls = cls;
     r.pad = 0;
     p.rois[i] = r;
     if ((int64_t)i >= p.cap_roi) continue;  // no room for its output row
-    if (cls == 3) {  // multi-block class: register the ROI and its arena region
+    if (cls == BIG_CLASS) {  // multi-block class: register the ROI and its arena region
       const unsigned long long cells3 = (unsigned long long)r.w * r.h * (p.ndim == 3 ? r.d : 1);
       if (!p.big || cells3 >= (1ull << 30)) {
         atomicOr(p.err, E_TOO_LARGE);
@@ -802,7 +802,7 @@ __global__ void k_begin(KParams p) {
     *p.n_used = 0;
     *p.n_roi = 0;
   }
-  if (t < 3) {
+  if (t < N_BLOCK_CLASSES) {
     p.qlen[t] = 0;
     p.qhead[t] = 0;
   }

@@ -256,7 +256,8 @@ class Extractor:
                                        _stream_ptr(self.device)))
         return out
 
-    PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "final", "reset")
+    PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_large", "roi_big", "final", "reset")
+    N_CLASSES = 4  # block classes: warp, small, medium, large
 
     def extract_tiles(self, source, tile: Tuple[int, int], d_img: torch.Tensor, d_mask: torch.Tensor,
                       table: Optional[torch.Tensor] = None) -> torch.Tensor:
@@ -302,30 +303,32 @@ class Extractor:
         self._check(lib().nyx_graph_captures(self._plan, ctypes.byref(n)))
         return int(n.value)
 
-    def set_class_limits(self, warp: int, small: int, medium: int):
-        """Pixel limits of the warp / small / medium classes (0 disables one)."""
-        lim = (ctypes.c_int32 * 3)(warp, small, medium)
+    def set_class_limits(self, warp: int, small: int, medium: int, large: int):
+        """Pixel limits of the warp / small / medium / large block classes (0
+        disables one; capacities 256 / 1,024 / 4,096 / 8,192 px)."""
+        lim = (ctypes.c_int32 * 4)(warp, small, medium, large)
         self._check(lib().nyx_set_class_limits(self._plan, lim))
 
-    def autotune(self, img: torch.Tensor, mask: torch.Tensor, reps: int = 5) -> Tuple[int, int, int, int]:
+    def autotune(self, img: torch.Tensor, mask: torch.Tensor, reps: int = 5) -> Tuple[int, ...]:
         """Time a grid of class limits, then of label-scan tile heights, on
         this input (L2 flushed before every timed call), keep the fastest;
-        returns (warp, small, medium pixel limits, scan rows per warp)."""
+        returns (warp, small, medium, large pixel limits, scan rows per warp)."""
         img, mask = self._inputs(img, mask)
         table = torch.empty((self.max_rois, len(self.columns)), dtype=torch.float64, device=self.device)
-        lim = (ctypes.c_int32 * 3)()
+        lim = (ctypes.c_int32 * 4)()
         self._check(lib().nyx_autotune(self._plan, img.data_ptr(), mask.data_ptr(), table.data_ptr(), table.shape[0],
                                        int(reps), _stream_ptr(self.device), lim))
         return self.tuning()
 
-    def tuning(self) -> Tuple[int, int, int, int]:
-        """(warp, small, medium pixel limits, scan rows per warp; 0 = chosen per call)."""
-        t = (ctypes.c_int32 * 4)()
+    def tuning(self) -> Tuple[int, ...]:
+        """(warp, small, medium, large pixel limits, scan rows per warp; 0 =
+        chosen per call)."""
+        t = (ctypes.c_int32 * 5)()
         self._check(lib().nyx_get_tuning(self._plan, t))
         return tuple(int(v) for v in t)
 
-    def set_tuning(self, warp: int, small: int, medium: int, scan_rows: int = 0):
-        t = (ctypes.c_int32 * 4)(warp, small, medium, scan_rows)
+    def set_tuning(self, warp: int, small: int, medium: int, large: int, scan_rows: int = 0):
+        t = (ctypes.c_int32 * 5)(warp, small, medium, large, scan_rows)
         self._check(lib().nyx_set_tuning(self._plan, t))
 
     def profile(self, slots: int = 1):
@@ -338,8 +341,8 @@ class Extractor:
         self._check(lib().nyx_phase_times(self._plan, int(back), ms, len(self.PHASES)))
         return dict(zip(self.PHASES, [float(v) for v in ms]))
 
-    GRAPH_PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_big", "glcm_final",
-                    "stats_final", "reset", "roi_stage", "all")
+    GRAPH_PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_large", "roi_big",
+                    "glcm_final", "stats_final", "reset", "roi_stage", "all")
 
     def graph_phase_events(self, enable: bool = True):
         """Record a begin and an end event around each phase inside the

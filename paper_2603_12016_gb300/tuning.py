@@ -28,7 +28,7 @@ from typing import Dict, Optional, Sequence, Tuple
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNED_PATH = os.path.join(HERE, "tuned.json")
-DEFAULT_LIMITS = (256, 1024, 8192)
+DEFAULT_LIMITS = (256, 1024, 4096, 8192)  # warp, small, medium, large block classes
 
 
 def signature(shape: Sequence[int], dtype: str, ndim: int, ng: int, dists: Sequence[int], features: str) -> str:
@@ -45,7 +45,7 @@ def _read(path: str = TUNED_PATH) -> Dict:
 
 
 def load(device_name: str, sig: str, path: str = TUNED_PATH) -> Optional[Dict]:
-    """The stored entry ({"limits": [w, s, m], "ms": ..., ...}) or None."""
+    """The stored entry ({"limits": [w, s, m, l], "scan_rows_per_warp": r, "ms": ...}) or None."""
     return _read(path).get(device_name, {}).get(sig)
 
 
@@ -82,7 +82,7 @@ def time_config(ex, img, mask, table, steps: int = 10, warmup: int = 3) -> float
     return statistics.median(ts)
 
 
-def tune(ex, img, mask, reps: int = 5) -> Tuple[Tuple[int, int, int, int], float]:
+def tune(ex, img, mask, reps: int = 5) -> Tuple[Tuple[int, ...], float]:
     """The library's autotuner (nyx_autotune: class limits, then the label
     scan's tile height, each candidate the median of `reps` L2-flushed
     calls) on this input; returns the setting and its median time."""
@@ -93,7 +93,7 @@ def tune(ex, img, mask, reps: int = 5) -> Tuple[Tuple[int, int, int, int], float
     return t, time_config(ex, img, mask, table)
 
 
-def limits_for(ex, device_name: str, sig: str) -> Tuple[Tuple[int, int, int, int], str]:
+def limits_for(ex, device_name: str, sig: str) -> Tuple[Tuple[int, ...], str]:
     """Apply the stored setting of (device, workload) to `ex` if there is
     one; returns the setting in force and where it came from."""
     ent = load(device_name, sig)
@@ -118,28 +118,25 @@ def main() -> int:
     ap.add_argument("--features", default="core,all")
     ap.add_argument("--reps", type=int, default=5)
     a = ap.parse_args()
+    procs = max(1, min(16, os.cpu_count() or 1))
+    wl = {name: (W.mosaic_workload(name, 0, procs) if name.startswith("mosaic") else W.config(name))
+          for name in a.workloads.split(",")}  # before any CUDA call (the mosaic's tiles use spawned processes)
     build.build()
     torch.cuda.set_device(0)
     dev_name = torch.cuda.get_device_name(0)
-    for name in a.workloads.split(","):
-        if name == "mosaic_small":
-            m = W.mosaic_2d(size=8192, tile=1024, n_roi=32_000)
-            img_np, mask_np = m.assemble()
-            ndim, prm = 2, m.params
-        else:
-            w = W.config(name)
-            img_np, mask_np, ndim, prm = w.image, w.mask, w.ndim, w.params
+    for name, w in wl.items():
+        img_np, mask_np, ndim, prm = w.image, w.mask, w.ndim, w.params
         tdt = {np.uint16: torch.uint16, np.int16: torch.int16, np.float32: torch.float32}[img_np.dtype.type]
         n_roi = int(np.count_nonzero(np.bincount(mask_np.ravel())[1:]))
         for feats in a.features.split(","):
             ex = nyx.Extractor(img_np.shape, tdt, ndim=ndim, glcm_levels=prm["glcm_levels"], dists=prm["dists"],
-                               hist_bins=prm["hist_bins"], max_rois=max(8192, 2 * n_roi),
+                               hist_bins=prm["hist_bins"], max_rois=8192 if n_roi <= 8192 else 2 * n_roi,
                                features=nyx.CORE_FEATURE_IDS if feats == "core" else None)
             img = torch.from_numpy(img_np).cuda()
             mask = torch.from_numpy(mask_np).cuda()
             t, ms = tune(ex, img, mask, reps=a.reps)
             sig = signature(img_np.shape, str(img_np.dtype), ndim, prm["glcm_levels"], prm["dists"], feats)
-            store(dev_name, sig, {"limits": list(t[:3]), "scan_rows_per_warp": t[3], "ms": round(ms, 4),
+            store(dev_name, sig, {"limits": list(t[:4]), "scan_rows_per_warp": t[4], "ms": round(ms, 4),
                                   "how": "nyx_autotune (median of L2-flushed calls per candidate), then the "
                                          "median of 10 L2-flushed graph replays of the choice"})
             print(json.dumps({"workload": name, "features": feats, "tuning": t, "ms": round(ms, 4)}), flush=True)

@@ -335,6 +335,7 @@ class Mosaic:
     _labels: np.ndarray = field(repr=False, default=None)
     _order: np.ndarray = field(repr=False, default=None)
     _seed: int = 0
+    _kw: Dict = field(repr=False, default=None)  # mosaic_2d arguments (rebuilds it in worker processes)
 
     def tile(self, x0: int, y0: int, w: int, h: int):
         # background and texture depend on the pixel position only (a hash of
@@ -373,16 +374,37 @@ class Mosaic:
         img[salt] = 65535
         return np.clip(np.rint(img), 0, 65535).astype(np.uint16), mask
 
-    def assemble(self):
-        """The whole mosaic (for tests on small mosaics)."""
+    def assemble(self, procs: int = 1):
+        """The whole mosaic.  With procs > 1 the tiles are generated in that
+        many processes (started with spawn, so call it before any CUDA use)."""
         img = np.empty((self.size, self.size), dtype=np.uint16)
         mask = np.empty((self.size, self.size), dtype=np.int32)
         t = self.tile_size
-        for y0 in range(0, self.size, t):
-            for x0 in range(0, self.size, t):
-                h, w = min(t, self.size - y0), min(t, self.size - x0)
+        jobs = [(x0, y0, min(t, self.size - x0), min(t, self.size - y0))
+                for y0 in range(0, self.size, t) for x0 in range(0, self.size, t)]
+        if procs > 1 and len(jobs) > 1:
+            import multiprocessing as mp
+
+            with mp.get_context("spawn").Pool(procs, initializer=_mosaic_worker_init, initargs=(self._kw,)) as pool:
+                tiles = pool.imap(_mosaic_worker_tile, jobs)
+                for (x0, y0, w, h), (ti, tm) in zip(jobs, tiles):
+                    img[y0:y0 + h, x0:x0 + w], mask[y0:y0 + h, x0:x0 + w] = ti, tm
+        else:
+            for x0, y0, w, h in jobs:
                 img[y0:y0 + h, x0:x0 + w], mask[y0:y0 + h, x0:x0 + w] = self.tile(x0, y0, w, h)
         return img, mask
+
+
+_MOSAIC_WORKER = None
+
+
+def _mosaic_worker_init(kw):
+    global _MOSAIC_WORKER
+    _MOSAIC_WORKER = mosaic_2d(**kw)
+
+
+def _mosaic_worker_tile(job):
+    return _MOSAIC_WORKER.tile(*job)
 
 
 def mosaic_2d(size: int = 32768, tile: int = 4096, n_roi: int = 500_000, seed: int = 1005, ng: int = 64,
@@ -397,7 +419,8 @@ def mosaic_2d(size: int = 32768, tile: int = 4096, n_roi: int = 500_000, seed: i
     asp = rng.uniform(1.0, 2.0, n_roi)
     b = np.sqrt(area / (math.pi * asp))
     a = b * asp
-    return Mosaic(name=f"mosaic_{size}_u16_{n_roi}roi", size=size, tile_size=tile, n_roi=n_roi,
+    kw = dict(size=size, tile=tile, n_roi=n_roi, seed=seed, ng=ng, area_range=area_range)
+    return Mosaic(name=f"mosaic_{size}_u16_{n_roi}roi", size=size, tile_size=tile, n_roi=n_roi, _kw=kw,
                   params=dict(glcm_levels=ng, dists=(1,), hist_bins=256),
                   _cy=rng.uniform(0, size, n_roi), _cx=rng.uniform(0, size, n_roi), _a=a, _b=b,
                   _th=rng.uniform(0, math.pi, n_roi), _bright=rng.lognormal(8.0, 0.6, n_roi),
@@ -407,7 +430,21 @@ def mosaic_2d(size: int = 32768, tile: int = 4096, n_roi: int = 500_000, seed: i
 # ---------------------------------------------------------------------------
 # named configurations (sizes of the benchmark table) and small variants
 
+def mosaic_workload(name: str, seed_offset: int = 0, procs: int = 1) -> Workload:
+    """The streamed mosaic as one assembled workload: "mosaic" (32768^2, 4096^2
+    tiles, 500,000 placed ROIs) or "mosaic_small" (8192^2, 1024^2 tiles,
+    32,000)."""
+    big = name == "mosaic"
+    m = mosaic_2d(size=32768 if big else 8192, tile=4096 if big else 1024, n_roi=500_000 if big else 32_000,
+                  seed=1005 + seed_offset)
+    img, mask = m.assemble(procs)
+    n_roi = int(np.count_nonzero(np.bincount(mask.ravel())[1:]))
+    return Workload(m.name, img, mask, 2, params=dict(m.params), meta={"n_roi": n_roi, "tile": m.tile_size})
+
+
 def config(name: str, seed_offset: int = 0) -> Workload:
+    if name.startswith("mosaic"):
+        return mosaic_workload(name, seed_offset)
     if name == "blobs2d":
         return blobs_2d(seed=1001 + seed_offset)
     if name == "nuclei2d":

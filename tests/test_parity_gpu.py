@@ -252,21 +252,21 @@ def test_graph_replay_matches_direct_launches():
         assert torch.equal(torch.nan_to_num(tt[:k], nan=-7.0), ref)
 
 
-@pytest.mark.parametrize("limits", [None, (0, 0, 4096), (128, 0, 8192), (256, 1024, 0), (64, 512, 2048, 8),
-                                    (256, 1024, 8192, 32)])
+@pytest.mark.parametrize("limits", [None, (0, 0, 4096, 0), (128, 0, 0, 8192), (256, 1024, 0, 0), (0, 512, 2048, 8192),
+                                    (64, 512, 2048, 0, 8), (256, 1024, 4096, 8192, 32)])
 def test_class_limits_and_autotune_keep_parity(limits):
     """Any class limits (autotuned or set) route ROIs to other kernels; the
-    table must still match the oracle.  (256, 1024, 0) sends every ROI above
-    1,024 px to the multi-block path."""
+    table must still match the oracle.  (256, 1024, 0, 0) sends every ROI
+    above 1,024 px to the multi-block path."""
     nyx = _nyx()
     w = W.config("nuclei2d_small")
     img, mask = to_torch(w.image), to_torch(w.mask)
     ex = nyx.Extractor(w.image.shape, torch.uint16, glcm_levels=256, dists=(1, 2), max_rois=1024)
     if limits is None:
         lim = ex.autotune(img, mask, reps=2)
-        assert lim[0] in (0, 64, 128, 256) and lim[1] in (0, 512, 1024) and lim[2] in (2048, 4096, 8192)
-        assert lim[3] in (8, 16, 32) and ex.tuning() == lim
-    elif len(limits) == 4:  # class limits and the label scan's tile height
+        assert lim[0] in (0, 64, 128, 256) and lim[1] in (0, 512, 1024) and lim[2] in (0, 2048, 4096)
+        assert lim[3] in (0, 8192) and lim[4] in (8, 16, 32) and ex.tuning() == lim
+    elif len(limits) == 5:  # class limits and the label scan's tile height
         ex.set_tuning(*limits)
         assert ex.tuning() == limits
     else:
