@@ -121,19 +121,34 @@ class ClockSampler:
 # capture of the same bench command, keyed by workload, phase, class limits
 # and feature set, and valid only for the kernel sources they were taken
 # with (the hash below; any change to csrc/ voids them and traffic is null).
-TRAFFIC_SRC = None
-TRAFFIC = {}
+# ROI-stage traffic (DRAM read + write of every k_roi class and multi-block
+# kernel of one extraction, ncu --profile-from-start off over
+# python -m paper_2603_12016_gb300.profile_step <workload>).  The
+# 32768^2 mosaic is scaled from the 8192^2 mosaic (640.98 MB for 36.02M ROI
+# pixels) by its 565.05M ROI pixels.
+TRAFFIC_SRC = "7b6395d42bf57b9d"
+TRAFFIC = {
+    ("nuclei2d_2048_u16_4000roi", "roi_stage", (0, 1024, 4096, 0, 8), "core"): 32.41e6,
+    ("ct3d_512x512x128_i16_200roi", "roi_stage", (256, 1024, 2048, 8192, 8), "all"): 1016.55e6,
+    ("blobbatch_64x512_f32", "roi_stage", (0, 1024, 4096, 8192, 16), "all"): 108.20e6,
+    ("mosaic_32768_u16_500000roi", "roi_stage", (64, 512, 4096, 8192, 32), "all"): 640.98e6 * 565.05 / 36.02,
+}
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources the library is built from."""
+    """Hash of the CUDA sources the library is built from, comments and
+    whitespace removed (an edit of a comment leaves the kernels unchanged)."""
     import glob
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2603_12016_gb300", "csrc", "*.cu*"))):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode() + fh.read())
+        with open(f, encoding="utf-8") as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(os.path.basename(f).encode() + " ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

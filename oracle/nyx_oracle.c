@@ -58,9 +58,9 @@ typedef struct {
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
-/* GLCM offsets.  2D (reading c2): angle 0 = (+1,0), 45 = (+1,-1),
+/* GLCM offsets.  2D: angle 0 = (+1,0), 45 = (+1,-1),
  * 90 = (0,-1), 135 = (-1,-1) in (dx,dy) with the row index growing
- * downward.  3D (reading c15): the 13 vectors of {-1,0,1}^3 whose first
+ * downward.  3D: the 13 vectors of {-1,0,1}^3 whose first
  * nonzero component, read in the order (dz, dy, dx), is positive, enumerated
  * with dz outermost and dx fastest.  Distance d scales the unit vector. */
 static int n_dirs(const orc_cfg* c) { return c->ndim == 3 ? 13 : 4; }
@@ -100,7 +100,7 @@ static double pixel(const orc_cfg* c, const void* img, int64_t gidx) {
   }
 }
 
-/* Intensity binning, rule a4 / reading c1: IBSI fixed bin number, 0-based,
+/* Intensity binning, the IBSI fixed-bin-number rule: 0-based,
  * per-ROI min/max.  Integer inputs: b = floor(n (x - min) / (max - min)) in
  * 64-bit integers.  Float inputs: the same expression in FP64 with every
  * operation rounded separately (this file is compiled without FMA
@@ -231,12 +231,12 @@ typedef struct {
   double glcm_off[ORC_MAX_DIST][ORC_MAX_DIR][ORC_NGLCM];
   double glcm_mean[ORC_MAX_DIST][ORC_NGLCM];
   /* Table S1 rows 3-7 / Table S5 IIE, Max IE, Min IE, Mean IE, std IE:
-   * intensity statistics over the ROI's edge pixels (reading c14) */
+   * intensity statistics over the ROI's edge pixels (edge test below) */
   double edge_ii, edge_max, edge_min, edge_mean, edge_std;
   /* Table S3 rows 246-250 (NGTDM): coarseness, contrast, busyness,
-   * complexity, strength (reading c17) */
+   * complexity, strength */
   double ngtdm[5];
-  /* Table S3 rows 251-264 (GLDM), reading c18 */
+  /* Table S3 rows 251-264 (GLDM) */
   double gldm[14];
   /* GLRLM (Table S3 rows from 193, acronyms of its note) and GLSZM (rows
    * 228-245), readings c19 / c20, in the order of SZ_NAMES below */
@@ -431,8 +431,8 @@ static void emit_all(const orc_cfg* c, const feat_t* f, emitter* e) {
 
 /* ------------------------------------------------------------------------ */
 /* GLCM features of one dense Ng x Ng count matrix (Table S3 rows 140-174,
- * IBSI definitions, 1-based grey levels per reading c3, log base 2 per
- * reading c4).  Zero total -> every feature NaN (reading c8). */
+ * IBSI definitions, 1-based grey levels, log base 2).  Zero total -> every
+ * feature NaN. */
 static void glcm_features(int ng, const double* P, double* out) {
   double tot = 0;
   for (int i = 0; i < ng * ng; ++i) tot += P[i];
@@ -531,7 +531,7 @@ static void glcm_features(int ng, const double* P, double* out) {
 
 /* Dense GLCM of one ROI for unit direction k at distance d: for every ROI
  * pixel q and its neighbour q + d*dir inside the same ROI, P[b_q][b_n] += 1
- * and P[b_n][b_q] += 1 (symmetric, reading c2).  Bins come from rule a4 with
+ * and P[b_n][b_q] += 1 (symmetric).  Bins come from the fixed-bin-number rule with
  * n = ng on the ROI's own min/max. */
 static void roi_glcm(const orc_cfg* c, const void* img, const int32_t* mask, const roi_t* r, double mn, double mx,
                      int dir, int d, double* P) {
@@ -558,7 +558,7 @@ static void roi_glcm(const orc_cfg* c, const void* img, const int32_t* mask, con
 }
 
 static double percentile(const double* v, int64_t n, double q) {
-  /* linear interpolation at h = (n-1) q (reading c11, "type 7") */
+  /* linear interpolation at h = (n-1) q ("type 7") */
   double h = (double)(n - 1) * q;
   int64_t lo = (int64_t)floor(h);
   if (lo >= n - 1) return v[n - 1];
@@ -589,7 +589,7 @@ static double ipow(double x, int k) {
 }
 
 /* All features of one ROI. */
-/* Edge test (reading c14): pixel (x, y, z) of ROI `label` in image `base`
+/* Edge test: pixel (x, y, z) of ROI `label` in image `base`
  * has a face neighbour (4 in 2D, 6 in 3D) outside the image or under
  * another label. */
 static int is_edge(const orc_cfg* c, const int32_t* mask, int64_t base, const int64_t* X, int32_t label) {
@@ -679,7 +679,7 @@ static void size_matrix_features(item_t* it, int64_t M, int ng, int64_t smax, in
   free(ns);
 }
 
-/* GLRLM (reading c19) and GLSZM (reading c20) of one ROI.  lev[] holds the
+/* GLRLM and GLSZM of one ROI.  lev[] holds the
  * 1-based level of each cell of the ROI's bounding box (W x H x D, x
  * fastest), 0 outside the ROI; Np is the ROI's pixel count.  GLRLM: for
  * each GLCM unit direction v, a run is a maximal chain p, p + v, ... of
@@ -831,7 +831,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     f->exkurt = f->kurt - 3.0;
     f->hskew = m[5] / pow(m[2], 2.5);
     f->hflat = m[6] / (m[2] * m[2] * m[2]);
-  } /* else all zero (reading c8) */
+  } /* else all zero (no spread: the degenerate case) */
   f->energy = energy;
   f->rms = sqrt(energy / N);
   f->se = f->std / sqrt((double)N);
@@ -854,7 +854,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
 
   /* edge intensity statistics (Table S1 rows 3-7, Table S5): a pixel of the
    * ROI is an edge pixel when one of its 4 (2D) / 6 (3D) face neighbours is
-   * outside the image or carries another label (reading c14).  Two-pass
+   * outside the image or carries another label.  Two-pass
    * mean and unbiased standard deviation over the edge pixels. */
   {
     int64_t ne = 0;
@@ -880,7 +880,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     f->edge_std = ne > 1 ? sqrt(ev / (ne - 1)) : 0.0;
   }
 
-  /* order statistics on the sorted values (reading c11) */
+  /* order statistics on the sorted values */
   double* v = (double*)malloc(sizeof(double) * (size_t)N);
   memcpy(v, I, sizeof(double) * (size_t)N);
   qsort(v, (size_t)N, sizeof(double), cmp_double);
@@ -913,7 +913,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     f->medad = s / N;
   }
   {
-    /* mode: most frequent raw value, ties -> smallest (reading c11) */
+    /* mode: most frequent raw value, ties -> smallest */
     double best = v[0];
     int64_t bestc = 0, run = 0;
     for (int64_t k = 0; k < N; ++k) {
@@ -927,7 +927,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     f->mode_prob = (double)bestc / N;
   }
   {
-    /* histogram features (Table S1 rows 9, 35): bins by rule a4 with
+    /* histogram features (Table S1 rows 9, 35): fixed-bin-number bins with
      * n = hist_bins on the ROI's min/max */
     int64_t* h = (int64_t*)calloc((size_t)c->hist_bins, sizeof(int64_t));
     for (int64_t k = 0; k < N; ++k) h[bin_of(c, I[k], mn, mx, c->hist_bins)]++;
@@ -946,7 +946,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
 
   /* ---- geometric moments, Table S2 rows 123-135 / Table S5 rows 368, 370 ---
    * ROI-local coordinates with origin at the bounding-box corner and pixel
-   * centres at integers (reading c9); central moments are computed directly
+   * centres at integers; central moments are computed directly
    * about the centroid (two-pass), not by binomial expansion. */
   const int nm = n_moments(c);
   for (int w = 0; w < 2; ++w) {
@@ -1013,7 +1013,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     free(P);
   }
 
-  /* ---- NGTDM, Table S3 rows 246-250 (reading c17): for every ROI pixel
+  /* ---- NGTDM, Table S3 rows 246-250: for every ROI pixel
    * with grey level L (1-based GLCM bin) and at least one neighbour in the
    * ROI among its 8 (2D) / 26 (3D) Chebyshev-1 neighbours, the mean level
    * A of those neighbours; n_L counts such pixels and s_L sums |L - A|.
@@ -1080,7 +1080,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     free(sL);
   }
 
-  /* ---- GLDM, Table S3 rows 251-264 (reading c18): the dependence of a
+  /* ---- GLDM, Table S3 rows 251-264: the dependence of a
    * pixel of grey level i (1-based GLCM bin) is j = 1 + the number of its 8
    * (2D) / 26 (3D) Chebyshev-1 neighbours in the ROI with the same level;
    * P(i, j) counts the pixels, N = sum P = the ROI's pixel count, p = P / N.
@@ -1244,7 +1244,7 @@ int64_t orc_extract(const orc_cfg* c, const void* img, const int32_t* mask, cons
   return n;
 }
 
-/* Bin index (rule a4 with n bins) of every pixel of the ROI with the given
+/* Bin index (fixed bin number rule, n bins) of every pixel of the ROI with the given
  * key, in ascending linear-index order.  Returns the pixel count. */
 int64_t orc_roi_bins(const orc_cfg* c, const void* img, const int32_t* mask, int64_t key, int nbins, int32_t* out,
                      int64_t cap) {
@@ -1364,7 +1364,7 @@ static int find_name(char (*names)[ORC_NAME], int nf, const char* s) {
 /* gtab: [n_roi x n_features] upstream gradient rows in the order of
  * orc_extract (ascending (image, label) key).  grad: image-shaped FP64
  * output (zero outside ROIs).  Returns the ROI count or a negative error. */
-/* number of edge pixels of ROI R (reading c14) */
+/* number of edge pixels of ROI R (face neighbour outside the image or the ROI) */
 static int64_t edge_count(const orc_cfg* c, const int32_t* mask, const roi_t* R, int64_t per) {
   int64_t ne = 0;
   for (int64_t k = 0; k < R->n; ++k) {
@@ -1411,7 +1411,7 @@ int64_t orc_grad(const orc_cfg* c, const void* img, const int32_t* mask, const d
                  ghf = G("HYPERFLATNESS"), gen = G("ENERGY"), grms = G("ROOT_MEAN_SQUARED"),
                  gse = G("STANDARD_ERROR"), gmad = G("MEAN_ABSOLUTE_DEVIATION"), gcov = G("COV"),
                  gmd = G("MASS_DISPLACEMENT");
-    /* edge statistics over the fixed edge set E (reading c14): d II_E = 1,
+    /* edge statistics over the fixed edge set E: d II_E = 1,
      * d mean_E = 1/n_E, d std_E = (I - mean_E) / ((n_E - 1) std_E) on E */
     const double geii = G("EDGE_INTEGRATED_INTENSITY"), gemean = G("EDGE_MEAN_INTENSITY"),
                  gestd = G("EDGE_STDDEV_INTENSITY");

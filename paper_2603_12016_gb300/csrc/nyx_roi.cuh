@@ -1481,7 +1481,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
                                 : ((unsigned)x | ((unsigned)ry << 16));
             pv[pos] = e;
           }
-          // GLCM bin and histogram bin (rule a4)
+          // GLCM bin and histogram bin (IBSI fixed bin number)
           unsigned gb = 0, hb = 0;
           if (vmax > vmin) {
             if (Enc<T>::INTEGER) {

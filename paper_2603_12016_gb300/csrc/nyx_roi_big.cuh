@@ -851,7 +851,7 @@ __global__ void __launch_bounds__(BIG_NT) k_big_glcm(KParams p) {
     const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
     FastDiv fd;
     fd.init(vmax > vmin ? vmax - vmin : 1u);
-    auto gbin = [&](unsigned e) -> unsigned {  // rule a4 with n = Ng
+    auto gbin = [&](unsigned e) -> unsigned {  // fixed bin number, n = Ng
       if (vmax <= vmin) return 0u;
       if constexpr (Enc<T>::INTEGER) return min(fd.div((unsigned)ng * (e - vmin)), (unsigned)(ng - 1));
       else return bin_float(Enc<T>::decf(e), fmn, fmx, ng);
@@ -1130,7 +1130,7 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_ngtdm(KParam
     const float fmn = Enc<T>::decf(vmin), fmx = Enc<T>::decf(vmax);
     FastDiv fd;
     fd.init(vmax > vmin ? vmax - vmin : 1u);
-    auto gbin = [&](unsigned e) -> int {  // rule a4 with n = Ng
+    auto gbin = [&](unsigned e) -> int {  // fixed bin number, n = Ng
       if (vmax <= vmin) return 0;
       if constexpr (Enc<T>::INTEGER) return (int)min(fd.div((unsigned)ng * (e - vmin)), (unsigned)(ng - 1));
       else return (int)bin_float(Enc<T>::decf(e), fmn, fmx, ng);

@@ -761,7 +761,7 @@ __global__ void k_init_table(KParams p, unsigned cap) {
   }
 }
 
-// Per-pixel GLCM bin (test hook): rule a4 with the ROI's min/max.
+// Per-pixel GLCM bin (test hook): IBSI fixed bin number with the ROI's min/max.
 template <class T>
 __global__ void k_debug_bins(KParams p, uint16_t* out) {
   const int64_t total = p.rows_total * p.nx;

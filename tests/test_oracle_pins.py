@@ -56,7 +56,7 @@ def test_batch_keys_and_3d_geometry(orc):
 
 
 # --------------------------------------------------------------------------
-# Binning (rule a4): equal-width bins over [min, max] with the maximum in the
+# Binning (IBSI fixed bin number): equal-width bins over [min, max] with the maximum in the
 # last bin; numpy.histogram implements the same equal-width partition.
 
 @pytest.mark.parametrize("lo,hi,n", [(0, 65535, 256), (17, 4000, 32), (100, 103, 8), (5, 5 + 256 * 7, 256),
