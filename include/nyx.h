@@ -276,8 +276,9 @@ nyx_status nyx_debug_bins(nyx_plan* plan, const void* d_img, const int32_t* d_ma
  * [0] counters + label scan, [1] key sort + per-ROI setup, [2] ROI kernel of
  * the warp class (one warp per ROI), [3] of the small block class, [4] of the
  * medium block class, [5] of the large block class, [6] the multi-block
- * class (ROIs larger than a block stages), [7] statistics, moments and GLCM
- * features from the per-ROI sums, [8] table reset.
+ * class (ROIs larger than a block stages; with GLRLM / GLSZM selected it
+ * includes their kernels), [7] statistics, moments and GLCM features from the
+ * per-ROI sums, [8] table reset.
  * Errors: NYX_ERR_ARG (null plan/ms, slots out of 0..1024, back out of
  * range), NYX_ERR_STATE (that extract was not recorded), NYX_ERR_CUDA. */
 #define NYX_N_PHASES 9
@@ -295,12 +296,15 @@ nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
  * kernel, the table reset, the per-ROI stage (from before the size classes
  * fork to after they join: the four classes run as concurrent branches, so
  * each class's own span includes waiting for SMs that the others hold), and
- * the whole extraction.  A class that receives no ROI reads as about 0.
+ * the whole extraction, and the block-class GLRLM / GLSZM kernels (a branch
+ * of their own beside the size classes, inside the per-ROI stage; the
+ * multi-block GLRLM / GLSZM kernels follow the multi-block class on its
+ * branch and count to it).  A class that receives no ROI reads as about 0.
  * Errors: NYX_ERR_ARG (null plan/ms), NYX_ERR_STATE (events off or graphs
  * off), NYX_ERR_CUDA. */
 enum {
   NYX_GPH_SCAN = 0, NYX_GPH_SORT, NYX_GPH_WARP, NYX_GPH_SMALL, NYX_GPH_MED, NYX_GPH_LARGE, NYX_GPH_BIG, NYX_GPH_GLCMF,
-  NYX_GPH_STATSF, NYX_GPH_RESET, NYX_GPH_ROI, NYX_GPH_ALL, NYX_N_GPHASES
+  NYX_GPH_STATSF, NYX_GPH_RESET, NYX_GPH_ROI, NYX_GPH_ALL, NYX_GPH_RZ, NYX_N_GPHASES
 };
 nyx_status nyx_graph_phase_events(nyx_plan* plan, int enable);
 nyx_status nyx_graph_phase_times(nyx_plan* plan, float* ms, int n);

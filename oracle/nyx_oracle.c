@@ -603,7 +603,7 @@ static int is_edge(const orc_cfg* c, const int32_t* mask, int64_t base, const in
   return 0;
 }
 
-/* ---- run-length and size-zone matrices (readings c19, c20) ----
+/* ---- run-length and size-zone matrices ----
  * Both matrices count items (runs or zones) by grey level i (1-based GLCM
  * bin) and size s (run length or zone area).  With M items over Np ROI
  * pixels, p = count(i, s) / M, and sums over the items:
@@ -1151,7 +1151,7 @@ static void compute_roi(const orc_cfg* c, const void* img, const int32_t* mask, 
     free(P);
   }
 
-  /* ---- GLRLM / GLSZM (readings c19, c20), when asked for ---- */
+  /* ---- GLRLM / GLSZM, when asked for ---- */
   if (c->ng > 0 && c->families) {
     const int64_t W = hi[0] - lo[0] + 1, H = hi[1] - lo[1] + 1, D = hi[2] - lo[2] + 1;
     int* lev = (int*)calloc((size_t)(W * H * D), sizeof(int));

@@ -25,6 +25,9 @@ cudaError_t launch_big_u16(const KParams& p, int fp64, int nsm, cudaStream_t st)
 cudaError_t launch_big_i16(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_big_f32(const KParams& p, int fp64, int nsm, cudaStream_t st);
 cudaError_t launch_glcm_final(const KParams& p, int fp64, int nsm, cudaStream_t st);
+cudaError_t launch_rz_u16(const KParams& p, int big, int nsm, cudaStream_t st);
+cudaError_t launch_rz_i16(const KParams& p, int big, int nsm, cudaStream_t st);
+cudaError_t launch_rz_f32(const KParams& p, int big, int nsm, cudaStream_t st);
 cudaError_t launch_front(const KParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_begin(const KParams& p, cudaStream_t st);
 cudaError_t launch_scan(const KParams& p, int nsm, cudaStream_t st);
@@ -39,7 +42,8 @@ using namespace nyx;
 
 // ---------------------------------------------------------------------------
 // feature registry: ids 0..40 statistics, 41..50 moment families, 51..80 GLCM,
-// 81..85 edge intensity statistics, 86..90 NGTDM, 91..104 GLDM
+// 81..85 edge intensity statistics, 86..90 NGTDM, 91..104 GLDM, 105..120
+// GLRLM, 121..138 GLSZM
 
 namespace {
 
@@ -67,7 +71,17 @@ const char* GLDM_NAMES[N_GLDM] = {"GLDM_SDE",    "GLDM_LDE",  "GLDM_GLN",    "GL
                                   "GLDM_SDLGLE", "GLDM_SDHGLE", "GLDM_LDLGLE", "GLDM_LDHGLE"};
 constexpr int FID_NGTDM = FID_EDGE + N_EDGE;  // 86
 constexpr int FID_GLDM = FID_NGTDM + N_NGTDM; // 91
-constexpr int N_FID = FID_GLDM + N_GLDM;      // 105
+const char* GLRLM_NAMES[N_GLRLM] = {"GLRLM_SRE",    "GLRLM_LRE",    "GLRLM_GLNU",   "GLRLM_GLNUN",
+                                    "GLRLM_RLNU",   "GLRLM_RLNUN",  "GLRLM_RP",     "GLRLM_GLV",
+                                    "GLRLM_RV",     "GLRLM_RE",     "GLRLM_LGLRE",  "GLRLM_HGLRE",
+                                    "GLRLM_SRLGLE", "GLRLM_SRHGLE", "GLRLM_LRLGLE", "GLRLM_LRHGLE"};
+const char* GLSZM_NAMES[N_GLSZM] = {"GLSZM_SAE",    "GLSZM_LAE",    "GLSZM_GLNU",   "GLSZM_GLNUN", "GLSZM_SZNU",
+                                    "GLSZM_SZNUN",  "GLSZM_ZP",     "GLSZM_GLV",    "GLSZM_ZV",    "GLSZM_ZE",
+                                    "GLSZM_LGLZE",  "GLSZM_HGLZE",  "GLSZM_SALGLE", "GLSZM_SAHGLE", "GLSZM_LALGLE",
+                                    "GLSZM_LAHGLE", "GLSZM_GLM",    "GLSZM_ZSM"};
+constexpr int FID_GLRLM = FID_GLDM + N_GLDM;    // 105
+constexpr int FID_GLSZM = FID_GLRLM + N_GLRLM;  // 121
+constexpr int N_FID = FID_GLSZM + N_GLSZM;      // 139
 
 bool is_order_stat(int s) {
   return s == S_MEDIAN || s == S_P01 || s == S_P10 || s == S_P25 || s == S_P75 || s == S_P90 || s == S_P99 ||
@@ -119,8 +133,8 @@ struct nyx_plan {
   // branches of the extraction that run beside the caller's stream (the
   // medium class, the multi-block path, the GLCM feature kernel, the label
   // table reset), with the events that fork and join them
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t fork_ev[6] = {};
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork_ev[8] = {};
   cudaGraphExec_t graph_exec[NGRAPH] = {};
   KParams graph_key[NGRAPH];
   int64_t graph_used[NGRAPH] = {};
@@ -241,6 +255,10 @@ int nyx_feature_id(const char* name) {
     if (!strcmp(name, NGTDM_NAMES[q])) return FID_NGTDM + q;
   for (int q = 0; q < N_GLDM; ++q)
     if (!strcmp(name, GLDM_NAMES[q])) return FID_GLDM + q;
+  for (int q = 0; q < N_GLRLM; ++q)
+    if (!strcmp(name, GLRLM_NAMES[q])) return FID_GLRLM + q;
+  for (int q = 0; q < N_GLSZM; ++q)
+    if (!strcmp(name, GLSZM_NAMES[q])) return FID_GLSZM + q;
   return -1;
 }
 
@@ -345,6 +363,12 @@ static void build_columns(nyx_plan* pl) {
   if (p.glcm_levels > 0)
     for (int q = 0; q < N_GLDM; ++q)
       if (fbit(p, FID_GLDM + q)) add(Q_GLDM + q, GLDM_NAMES[q]);
+  if (p.glcm_levels > 0)
+    for (int q = 0; q < N_GLRLM; ++q)
+      if (fbit(p, FID_GLRLM + q)) add(Q_GLRLM + q, GLRLM_NAMES[q]);
+  if (p.glcm_levels > 0)
+    for (int q = 0; q < N_GLSZM; ++q)
+      if (fbit(p, FID_GLSZM + q)) add(Q_GLSZM + q, GLSZM_NAMES[q]);
 }
 
 // GLCM unit directions: 2D angles 0/45/90/135 degrees as (dx,dy) = (1,0),
@@ -408,9 +432,21 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   // histograms, co-occurrence triangles, partial sums, float sort buffers).
   // Sorting needs 2 words per ROI pixel; the rest is per-ROI bookkeeping.
   const unsigned long long total_px = (unsigned long long)p.batch * p.dims[0] * p.dims[1] * p.dims[2];
-  unsigned long long arena_words = 3ull * total_px + (1ull << 24);
+  bool want_rl = false, want_sz = false;  // GLRLM / GLSZM selected
+  if (p.glcm_levels > 0) {
+    for (int q = 0; q < N_GLRLM; ++q) want_rl |= fbit(p, FID_GLRLM + q);
+    for (int q = 0; q < N_GLSZM; ++q) want_sz |= fbit(p, FID_GLSZM + q);
+  }
+  if (want_sz && total_px >= (1ull << 32)) {
+    delete pl;
+    return fail(ctx, NYX_ERR_SHAPE, "GLSZM features need fewer than 2^32 pixels per call (32-bit zone parents)");
+  }
+  // the run / zone item tables of the multi-block ROIs: a few words per pixel
+  unsigned long long arena_words = (want_rl || want_sz ? 11ull : 3ull) * total_px + (1ull << 24);
   if (arena_words > (1ull << 30)) arena_words = 1ull << 30;  // 4 GiB: large mosaics hold few multi-block ROIs
   const size_t o_arena = take(4ull * arena_words);
+  // zone parents and areas of the multi-block ROIs (GLSZM): one word each per pixel
+  const size_t o_zpar = want_sz ? take(8ull * total_px) : 0;  // parents, then areas (cleared together)
   // per (ROI, offset) GLCM accumulators (GI int64 + GF sums in 8-byte slots)
   const int n_off_all = p.glcm_levels > 0 ? p.n_dist * (p.ndim == 3 ? 13 : 4) : 0;
   const size_t o_gacc = take((size_t)mr * n_off_all * (8 * (GI_HOST + GF_HOST)));
@@ -419,6 +455,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   const size_t o_wtab_f = take(4ull * 5 * ngw), o_wtab_d = take(8ull * 5 * ngw);
   // c log2 c (2^-24 units) of the small counts of the entropy sums
   const size_t o_clog = take(8ull * CLOG_N);
+  // round(2^63 / i^2) per level and round(2^63 / s^2) per run length / zone area (GLRLM / GLSZM)
+  const size_t o_rzqi = take(8ull * 257), o_rzqs = take(8ull * (RZ_STAB + 1));
   // per-ROI statistics / moment sums (64 eight-byte slots)
   const size_t o_sacc = take((size_t)mr * 512);
   // key buffer of the key sorts (gathered keys; second run buffer of the multi-block sort)
@@ -479,7 +517,11 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
       if (fbit(p, FID_GLDM + q)) need |= NEED_GLDM;
   // the edge test and the NGTDM / GLDM neighbourhoods read neighbours from
   // the padded bin raster
-  if ((need & (NEED_EDGE | NEED_NGTDM | NEED_GLDM)) && k.pad < 1) k.pad = 1;
+  if (want_rl) need |= NEED_GLRLM;
+  if (want_sz) need |= NEED_GLSZM;
+  // (and the run / zone kernels' own raster has one border cell, which the
+  // class cell limits must cover)
+  if ((need & (NEED_EDGE | NEED_NGTDM | NEED_GLDM | NEED_GLRLM | NEED_GLSZM)) && k.pad < 1) k.pad = 1;
   k.need = need;
   k.keys = (unsigned long long*)(w + o_keys);
   k.slots = (SlotAcc*)(w + o_slots);
@@ -495,6 +537,9 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.err = small + 2;
   k.qlen = small + 4;
   k.qhead = small + 8;
+  k.rz_head = small + 12;
+  k.zpar = want_sz ? (unsigned*)(w + o_zpar) : nullptr;
+  k.zcnt = want_sz ? (unsigned*)(w + o_zpar) + total_px : nullptr;
   k.img_vmin = (unsigned*)(w + o_imin);
   k.img_vmax = (unsigned*)(w + o_imax);
   k.big = (BigRoi*)(w + o_big);
@@ -507,6 +552,8 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.wtab_f = (const float*)(w + o_wtab_f);
   k.wtab_d = (const double*)(w + o_wtab_d);
   k.clog = (const long long*)(w + o_clog);
+  k.rz_qi = (const unsigned long long*)(w + o_rzqi);
+  k.rz_qs = (const unsigned long long*)(w + o_rzqs);
   std::vector<float> wf(5ull * ngw);
   std::vector<double> wd(5ull * ngw);
   for (int kk = 0; kk < ngw; ++kk) {
@@ -536,14 +583,22 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
     for (int c = 2; c < CLOG_N; ++c) cl[c] = llround((double)c * log2((double)c) * 16777216.0);
     e = cudaMemcpy(w + o_clog, cl.data(), 8ull * CLOG_N, cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) {  // round(2^63 / d) for d = i^2 and d = s^2, exact integer arithmetic
+    auto q63 = [](unsigned long long d) { return d == 1 ? (1ull << 63) : ((1ull << 63) + d / 2) / d; };
+    std::vector<unsigned long long> qi(257, 0), qs(RZ_STAB + 1, 0);
+    for (unsigned long long i = 1; i <= 256; ++i) qi[i] = q63(i * i);
+    for (unsigned long long v = 1; v <= (unsigned long long)RZ_STAB; ++v) qs[v] = q63(v * v);
+    e = cudaMemcpy(w + o_rzqi, qi.data(), 8ull * 257, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w + o_rzqs, qs.data(), 8ull * (RZ_STAB + 1), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(small, 0, 64);
   if (e == cudaSuccess) {
     e = launch_init_table(k, hcap, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->side[i], cudaStreamNonBlocking);
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->fork_ev[i], cudaEventDisableTiming);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&pl->side[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->fork_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(pl->ws);
     delete pl;
@@ -561,9 +616,9 @@ void nyx_plan_destroy(nyx_plan* pl) {
     if (e) cudaEventDestroy(e);
   drop_graph(pl);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (pl->side[i]) cudaStreamDestroy(pl->side[i]);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 8; ++i)
     if (pl->fork_ev[i]) cudaEventDestroy(pl->fork_ev[i]);
   for (int i = 0; i < 2; ++i) {
     if (pl->stage[i]) cudaFreeHost(pl->stage[i]);
@@ -688,6 +743,15 @@ static cudaError_t launch_class(const KParams& k, int cls, int fp64, int nsm, cu
   }
 }
 
+// GLRLM / GLSZM: the block path (big = 0) or the multi-block path (big = 1)
+static cudaError_t launch_rz(const KParams& k, int big, int nsm, cudaStream_t st) {
+  switch (k.dtype) {
+    case NYX_U16: return launch_rz_u16(k, big, nsm, st);
+    case NYX_I16: return launch_rz_i16(k, big, nsm, st);
+    default: return launch_rz_f32(k, big, nsm, st);
+  }
+}
+
 static cudaError_t launch_big(const KParams& k, int fp64, int nsm, cudaStream_t st) {
   switch (k.dtype) {
     case NYX_U16: return launch_big_u16(k, fp64, nsm, st);
@@ -715,13 +779,15 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
   if (ev) NYX_CUDA(c, cudaEventRecord(ev[2], st));
   const int fp64 = pl->prm.precision == NYX_PREC_FP64_PLAIN;
   const bool fork = ev == nullptr && pl->side[0] != nullptr;
-  cudaStream_t s_med = st, s_big = st;
+  const bool rz = (k.need & (NEED_GLRLM | NEED_GLSZM)) != 0;
+  cudaStream_t s_med = st, s_big = st, s_rz = st;
   NYX_CUDA(c, gmark(gev, NYX_GPH_ROI, 0, st));
   if (fork) {
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[0], st));
-    for (int i = 0; i < 2; ++i) NYX_CUDA(c, cudaStreamWaitEvent(pl->side[i], pl->fork_ev[0], 0));
+    for (int i = 0; i < (rz ? 3 : 2); ++i) NYX_CUDA(c, cudaStreamWaitEvent(pl->side[i], pl->fork_ev[0], 0));
     s_med = pl->side[0];
     s_big = pl->side[1];
+    if (rz) s_rz = pl->side[2];
   }
   for (int cls = 0; cls < N_BLOCK_CLASSES; ++cls) {
     cudaStream_t sc = cls >= 2 ? s_med : st;  // medium and large classes on one side branch
@@ -731,10 +797,21 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, gmark(gev, NYX_GPH_WARP + cls, 1, sc));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[3 + cls], st));
   }
+  if (rz) {  // block-class GLRLM / GLSZM: reads the image and ROI table only, writes its own columns
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RZ, 0, s_rz));
+    const cudaError_t e = launch_rz(k, 0, c->nsm, s_rz);
+    if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLRLM / GLSZM kernel launch failed: %s", cudaGetErrorString(e));
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RZ, 1, s_rz));
+  } else {
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RZ, 0, st));
+    NYX_CUDA(c, gmark(gev, NYX_GPH_RZ, 1, st));
+  }
   {
     NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 0, s_big));
-    const cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
+    cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
+    if (rz && (e = launch_rz(k, 1, c->nsm, s_big)) != cudaSuccess)
+      return fail(c, NYX_ERR_CUDA, "multi-block GLRLM / GLSZM kernel launch failed: %s", cudaGetErrorString(e));
     NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 1, s_big));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
   }
@@ -743,6 +820,10 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
     NYX_CUDA(c, cudaEventRecord(pl->fork_ev[2], s_big));
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[1], 0));
     NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[2], 0));
+    if (rz) {
+      NYX_CUDA(c, cudaEventRecord(pl->fork_ev[6], s_rz));
+      NYX_CUDA(c, cudaStreamWaitEvent(st, pl->fork_ev[6], 0));
+    }
   }
   NYX_CUDA(c, gmark(gev, NYX_GPH_ROI, 1, st));
   // the GLCM feature kernel, the statistics kernel and the label-table reset

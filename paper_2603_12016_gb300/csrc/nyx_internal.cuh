@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "nyx.h"
@@ -34,6 +35,9 @@ constexpr int GI_HOST = 12, GF_HOST = 8;  // GLCM accumulator sizes (int64 sums,
 // rounded once from FP64: it covers every count of the block classes (at
 // most 2 x 8,192 pairs per offset)
 constexpr int CLOG_N = 16385;
+// round(2^63 / s^2) of every run length / zone area up to RZ_STAB (the
+// largest of the block classes) comes from the plan's table
+constexpr int RZ_STAB = 16384;
 
 // Per (image, label) accumulator filled by the label scan.  Intensities use
 // an order-preserving uint32 encoding so that min/max are integer atomics.
@@ -112,7 +116,11 @@ enum : int {
   N_NGTDM = 5,
   Q_GLDM = Q_NGTDM + N_NGTDM,         // + k (GLDM features)
   N_GLDM = 14,
-  Q_TOTAL = Q_GLDM + N_GLDM
+  Q_GLRLM = Q_GLDM + N_GLDM,          // + k (GLRLM features, direction means)
+  N_GLRLM = 16,
+  Q_GLSZM = Q_GLRLM + N_GLRLM,        // + k (GLSZM features)
+  N_GLSZM = 18,
+  Q_TOTAL = Q_GLSZM + N_GLSZM
 };
 
 // NGTDM features (Table S3 rows 246-250), index within Q_NGTDM
@@ -157,6 +165,8 @@ enum : unsigned {
   NEED_EDGE = 128u,   // edge intensity statistics
   NEED_NGTDM = 256u,  // neighbourhood grey-tone difference matrix
   NEED_GLDM = 512u,   // grey-level dependence matrix
+  NEED_GLRLM = 1024u, // grey-level run-length matrices
+  NEED_GLSZM = 2048u, // grey-level size-zone matrix
 };
 
 // saved per-ROI state for the backward pass (FP64 words per ROI)
@@ -226,6 +236,13 @@ struct KParams {
   int64_t scan_row0, scan_row1;
   int scan_rpt;                    // label-scan rows per warp (tile height / 8); 0: chosen by tile count
   unsigned long long* sort_tmp;    // key buffer of the key sorts [max_rois]
+  // GLRLM / GLSZM: work counters of the two block tiers; zone parents and
+  // areas of the multi-block ROIs, one word per image pixel (GLSZM only)
+  unsigned* rz_head;               // [2]
+  const unsigned long long* rz_qi; // [257] round(2^63 / i^2), levels i = 1..256
+  const unsigned long long* rz_qs; // [RZ_STAB + 1] round(2^63 / s^2), sizes s = 1..RZ_STAB
+  unsigned* zpar;
+  unsigned* zcnt;
 };
 
 // Fields of the packed big-ROI counter (one atomic hands out the big-ROI
@@ -242,8 +259,27 @@ __host__ __device__ inline unsigned big_units2(unsigned long long c) { return (u
 constexpr int BIG_P1 = 38;   // pass-1 partial per chunk: 9 int64 + 5 doubles + 5 edge words (8 bytes each)
 constexpr int BIG_P2 = 98;   // pass-2 partial per chunk: 48 doubles + the edge squared deviations
 struct BigLayout {
-  unsigned long long ctr, hist, vhist, tri, ngt, gld, zero_end, part1, part2, fsort, total;
+  unsigned long long ctr, hist, vhist, tri, ngt, gld, rzh, zero_end, part1, part2, fsort, total;
 };
+
+// GLRLM / GLSZM sets of the selection: one per unit direction, one for the zones
+__host__ __device__ inline int rz_sets(const KParams& p) {
+  return ((p.need & NEED_GLRLM) ? (p.ndim == 3 ? 13 : 4) : 0) + ((p.need & NEED_GLSZM) ? 1 : 0);
+}
+// Slots of each set's item table of a multi-block ROI: a set holds at most
+// min(n, sqrt(2 n Ng)) distinct (level, size) keys (its sizes sum to at most
+// n), kept at a load of at most two thirds; a power of two.
+__host__ __device__ inline unsigned long long rz_hcap(const KParams& p, unsigned n) {
+  if (!rz_sets(p)) return 0;
+  double b = sqrt(2.0 * (double)n * (double)p.ng) + 2.0;
+  if (b > (double)n) b = (double)n;
+  const unsigned long long keys = (unsigned long long)b + 16;
+  unsigned long long cap = 64;
+  while (cap < keys + keys / 2) cap <<= 1;
+  return cap;
+}
+constexpr int RZ_NV_HOST = 26;  // reduced values per set (u64), kept per set in the arena
+
 __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int nsp, unsigned range, unsigned n) {
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
   const bool glcm = (p.need & NEED_GLCM) != 0;
@@ -257,6 +293,9 @@ __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int n
   L.tri = o;      o = (o + (nsp > 1 ? n_off * tri : 0) + 3) & ~3ull;
   L.ngt = o;      o = (o + ((p.need & NEED_NGTDM) ? 3ull * p.ng : 0) + 3) & ~3ull;  // S[ng] int64, then n[ng] u32
   L.gld = o;      o = (o + ((p.need & NEED_GLDM) ? (unsigned long long)p.ng * (p.ndim == 3 ? 27 : 9) : 0) + 3) & ~3ull;
+  // per set: u64 keys (0 = empty) of rz_hcap slots; then the u32 counts of
+  // every set; then each set's reduced values (u64)
+  L.rzh = o;      o = (o + (unsigned long long)rz_sets(p) * (3ull * rz_hcap(p, n) + 2ull * RZ_NV_HOST) + 3) & ~3ull;
   L.zero_end = o;
   L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
   L.part2 = o;    o += (unsigned long long)nch * BIG_P2;

@@ -478,7 +478,9 @@ __device__ inline void hu7(A n20, A n02, A n11, A n30, A n21, A n12, A n03, A* h
   h[6] = b * s * (s * s - 3 * t * t) - a * t * (3 * s * s - t * t);
 }
 
-// normalisation mu00^(1 + o/2) (2D) or mu000^(1 + o/3) (3D)
+// normalisation mu00^(1 + o/2) (2D) or mu000^(1 + o/3) (3D): a real power of
+// a negative mu000 exists only for an integer exponent (NaN otherwise, as
+// for the FP64 power function)
 template <int NDIM, class A>
 __device__ inline A norm_pow(A m00, int o) {
   if (NDIM == 2) {
@@ -489,6 +491,7 @@ __device__ inline A norm_pow(A m00, int o) {
       default: return m00 * m00 * asqrt(m00);
     }
   }
+  if (m00 < 0 && (o == 1 || o == 2)) return anan<A>();
   const A c = acbrt(m00);
   switch (o) {
     case 0: return m00;
@@ -498,36 +501,55 @@ __device__ inline A norm_pow(A m00, int o) {
   }
 }
 
-// One weighting's moments, one lane per moment.  Cs[] are the centred sums
-// sum w (x - c0)^p (y - c1)^q (z - c2)^r about the FP32 rounding of the
-// centroid (c0, c1, c2); that rounding (< 1e-5 px) moves every moment by far
-// less than the accumulation error, so Cs are the central moments mu_pqr.
-// Raw moments follow by the binomial expansion about the centroid.  valid =
-// false (zero total weight) leaves raw moments finite and every derived value
-// NaN.  Hu invariants are evaluated on eta rescaled to O(1) and scaled back by
-// an exact power of two, so tiny intensity-weighted invariants neither
-// underflow nor lose precision in FP32.
+// One weighting's moments, one lane per moment (every lane of the warp calls
+// it).  Cs[] are the sums sum w (x - s0)^p (y - s1)^q (z - s2)^r about the
+// centre s, an FP32 point inside the bounding box: the weighted centroid
+// when it lies in the box, else the binary centroid (a signed intensity
+// image whose weights nearly cancel puts the weighted centroid far outside,
+// where the expansions below would cancel catastrophically).  With W the
+// total weight and ci the FP64 weighted centroid, the first-order sums are
+// W (ci - s) exactly; raw moments follow by the binomial expansion about s,
+// central moments by the expansion about s - ci (zero when s is ci's
+// rounding).  valid = false (zero total weight) leaves raw moments finite
+// and every derived value NaN.  Hu invariants are evaluated on eta rescaled
+// to O(1) and scaled back by an exact power of two, so tiny
+// intensity-weighted invariants neither underflow nor lose precision in
+// FP32.
 template <int NDIM, class A>
-__device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row, int wbase, const A* Cs, A c0, A c1,
-                                                   A c2, bool valid, double* save_mu) {
+__device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row, int wbase, const A* Cs, A s0, A s1,
+                                                   A s2, const double* ci, double W, bool valid, double* save_mu) {
   constexpr int NM = NDIM == 3 ? 20 : 10;
   const int lane = threadIdx.x & 31;
-  if (lane >= NM) return;
+  const bool act = lane < NM;
   const A nan = anan<A>();
-  int a, b, c;
-  mexp<NDIM>(lane, a, b, c);
+  int a = 0, b = 0, c = 0;
+  if (act) mexp<NDIM>(lane, a, b, c);
   const int o = a + b + c;
-  A mu = Cs[lane];
-  if (valid && o == 1) mu = 0;  // first-order central moments vanish at the centroid
-  const A pw0[4] = {1, c0, c0 * c0, c0 * c0 * c0}, pw1[4] = {1, c1, c1 * c1, c1 * c1 * c1},
-          pw2[4] = {1, c2, c2 * c2, c2 * c2 * c2};
-  A M = 0;
-  for (int i = 0; i <= a; ++i)
-    for (int j = 0; j <= b; ++j)
-      for (int l = 0; l <= c; ++l) {
-        const A muk = (valid && i + j + l == 1) ? (A)0 : Cs[midx<NDIM>(i, j, l)];
-        M += (A)(c_binom[a][i] * c_binom[b][j] * c_binom[c][l]) * pw0[a - i] * pw1[b - j] * pw2[c - l] * muk;
-      }
+  const A f1[3] = {(A)(W * (ci[0] - (double)s0)), (A)(W * (ci[1] - (double)s1)),
+                   (A)(NDIM == 3 ? W * (ci[2] - (double)s2) : 0.0)};
+  const A d0 = (A)((double)s0 - ci[0]), d1 = (A)((double)s1 - ci[1]), d2 = (A)(NDIM == 3 ? (double)s2 - ci[2] : 0.0);
+  const A pw0[4] = {1, s0, s0 * s0, s0 * s0 * s0}, pw1[4] = {1, s1, s1 * s1, s1 * s1 * s1},
+          pw2[4] = {1, s2, s2 * s2, s2 * s2 * s2};
+  const A pd0[4] = {1, d0, d0 * d0, d0 * d0 * d0}, pd1[4] = {1, d1, d1 * d1, d1 * d1 * d1},
+          pd2[4] = {1, d2, d2 * d2, d2 * d2 * d2};
+  A M = 0, mu = 0;
+  if (act)
+    for (int i = 0; i <= a; ++i)
+      for (int j = 0; j <= b; ++j)
+        for (int l = 0; l <= c; ++l) {
+          const int q = i + j + l;
+          const A sv = q == 1 ? f1[i ? 0 : (j ? 1 : 2)] : Cs[midx<NDIM>(i, j, l)];
+          const A bc = (A)(c_binom[a][i] * c_binom[b][j] * c_binom[c][l]);
+          M += bc * pw0[a - i] * pw1[b - j] * pw2[c - l] * sv;
+          mu += bc * pd0[a - i] * pd1[b - j] * pd2[c - l] * sv;
+        }
+  if (o == 1) mu = 0;  // first-order central moments vanish at the centroid
+  // the central moments the Hu invariants need, from their lanes
+  const A m20 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(2, 0, 0)), m02 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(0, 2, 0)),
+          m11 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(1, 1, 0)), m30 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(3, 0, 0)),
+          m21 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(2, 1, 0)), m12 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(1, 2, 0)),
+          m03 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(0, 3, 0));
+  if (!act) return;
   const A mu00 = Cs[0];
   putA(p, row, Q_MOM + (wbase + F_M) * 20 + lane, M);
   putA(p, row, Q_MOM + (wbase + F_MU) * 20 + lane, valid ? mu : nan);
@@ -536,7 +558,7 @@ __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row
   if (save_mu) save_mu[lane] = to_d(mu);
   if (NDIM == 2 && lane == 0) {
     const A g20 = norm_pow<2>(mu00, 2), g30 = norm_pow<2>(mu00, 3);
-    const A e20 = Cs[midx<2>(2, 0, 0)] / g20, e02 = Cs[midx<2>(0, 2, 0)] / g20, e11 = Cs[midx<2>(1, 1, 0)] / g20;
+    const A e20 = m20 / g20, e02 = m02 / g20, e11 = m11 / g20;
     // scale lambda = 2^k close to eta20 + eta02: eta_o / lambda^(o/2) = O(1)
     int k = 0;
     if (valid) {
@@ -556,8 +578,7 @@ __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row
       il15 = ldexp(1.0, -(3 * k) / 2);
     }
     A h[7];
-    hu7<A>(e20 * il, e02 * il, e11 * il, Cs[midx<2>(3, 0, 0)] / g30 * il15, Cs[midx<2>(2, 1, 0)] / g30 * il15,
-           Cs[midx<2>(1, 2, 0)] / g30 * il15, Cs[midx<2>(0, 3, 0)] / g30 * il15, h);
+    hu7<A>(e20 * il, e02 * il, e11 * il, m30 / g30 * il15, m21 / g30 * il15, m12 / g30 * il15, m03 / g30 * il15, h);
     const int deg[7] = {1, 2, 3, 3, 6, 4, 6};  // degree of each invariant in eta20-like units
     for (int i = 0; i < 7; ++i) {
       double v;
@@ -1665,9 +1686,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_roi(KParams p, int cls) {
       s_cd[5] = bzd;
       s_pa[0] = mhi;
       s_pa[1] = mlo;
-      s_pa[2] = (A)s_cd[0];  // centres of the moment sums
-      s_pa[3] = (A)s_cd[1];
-      s_pa[4] = (A)s_cd[2];
+      // centre of the intensity-weighted moment sums: the weighted centroid
+      // if it lies in the bounding box, else the binary one
+      const bool inbox = wv && s_cd[0] >= 0 && s_cd[0] <= W - 1 && s_cd[1] >= 0 && s_cd[1] <= H - 1 &&
+                         (NDIM != 3 || (s_cd[2] >= 0 && s_cd[2] <= D - 1));
+      s_pa[2] = (A)(inbox ? s_cd[0] : bxd);
+      s_pa[3] = (A)(inbox ? s_cd[1] : byd);
+      s_pa[4] = (A)(inbox ? s_cd[2] : bzd);
       s_pa[5] = (A)bxd;
       s_pa[6] = (A)byd;
       s_pa[7] = (A)bzd;
@@ -2222,8 +2247,10 @@ __global__ void __launch_bounds__(256) k_stats_final(KParams p) {
       finalize_stats<T, NDIM, A>(p, row, g, (int)r.n, g[48], g[49], g[50], r.vmin, r.vmax, (int64_t)(r.key >> 32),
                                  r.x0, r.y0, r.z0, cd, wvalid, save);
     if (p.need & (NEED_MOM_INT | NEED_SAVE))
-      finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], wvalid, save ? save + SV_MU : nullptr);
-    if (p.need & NEED_MOM_BIN) finalize_moments_warp<NDIM, A>(p, row, 5, g + 28, g[54], g[55], g[56], true, nullptr);
+      finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], cd, to_d(g[49]), wvalid,
+                                     save ? save + SV_MU : nullptr);
+    if (p.need & NEED_MOM_BIN)
+      finalize_moments_warp<NDIM, A>(p, row, 5, g + 28, g[54], g[55], g[56], cd + 3, (double)r.n, true, nullptr);
   }
 }
 

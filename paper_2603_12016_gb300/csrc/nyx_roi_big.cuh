@@ -677,8 +677,14 @@ __global__ void __launch_bounds__(BIG_NT, big_pass_minb<A>()) k_big_p2(KParams p
     const unsigned c0 = (unsigned)chunk * BIG_CHUNK, c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
     const double* st = p.big[b].st;
     const A mu_hi = (A)__ldcg(st + 0), mu_lo = (A)__ldcg(st + 1);
-    const A cx = (A)__ldcg(st + 2), cy = (A)__ldcg(st + 3), cz = (A)__ldcg(st + 4);
-    const A bcx = (A)__ldcg(st + 5), bcy = (A)__ldcg(st + 6), bcz = (A)__ldcg(st + 7);
+    // centre of the intensity-weighted moment sums: the weighted centroid if
+    // it lies in the bounding box, else the binary one (as in the block classes)
+    const double ci0 = __ldcg(st + 2), ci1 = __ldcg(st + 3), ci2 = __ldcg(st + 4);
+    const double cb0 = __ldcg(st + 5), cb1 = __ldcg(st + 6), cb2 = __ldcg(st + 7);
+    const bool inbox = ci0 >= 0 && ci0 <= bx.W - 1 && ci1 >= 0 && ci1 <= bx.H - 1 &&
+                       (NDIM != 3 || (ci2 >= 0 && ci2 <= bx.D - 1));
+    const A cx = (A)(inbox ? ci0 : cb0), cy = (A)(inbox ? ci1 : cb1), cz = (A)(inbox ? ci2 : cb2);
+    const A bcx = (A)cb0, bcy = (A)cb1, bcz = (A)cb2;
     double* part = (double*)(reg + L.part2) + (size_t)chunk * (BIG_P2 / 2);
     // one pass: centred power sums and both moment sets, plain per-thread
     // sums over at most BIG_CHUNK / BIG_NT = 32 cells (as in the block

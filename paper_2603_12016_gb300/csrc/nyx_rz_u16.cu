@@ -1,0 +1,6 @@
+// nyx_rz_u16.cu -- GLRLM / GLSZM kernels for uint16_t images (see nyx_runzone.cuh).
+#include "nyx_runzone.cuh"
+
+namespace nyx {
+cudaError_t launch_rz_u16(const KParams& p, int big, int nsm, cudaStream_t st) { return launch_rz_t<uint16_t>(p, big, nsm, st); }
+}  // namespace nyx

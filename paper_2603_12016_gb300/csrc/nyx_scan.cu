@@ -806,6 +806,7 @@ __global__ void k_begin(KParams p) {
     p.qlen[t] = 0;
     p.qhead[t] = 0;
   }
+  if (t < 2 && p.rz_head) p.rz_head[t] = 0;
   if (t < 3 && p.big_ctr) {
     if (t == 0) *p.big_ctr = 0;
     p.big_used[t] = 0;

@@ -118,7 +118,7 @@ def feature_id(name: str) -> int:
 # with the histogram features (Table S1 / S5, ids 0-40), raw / central /
 # normalised moments with Hu invariants (Table S2 / S5, ids 41-50) and the
 # GLCM features (Table S3, ids 51-80).  Ids 81 and up are the edge intensity
-# statistics, NGTDM and GLDM.
+# statistics, NGTDM, GLDM, GLRLM and GLSZM.
 CORE_FEATURE_IDS = tuple(range(81))
 
 
@@ -342,7 +342,7 @@ class Extractor:
         return dict(zip(self.PHASES, [float(v) for v in ms]))
 
     GRAPH_PHASES = ("scan", "sort_setup", "roi_warp", "roi_small", "roi_medium", "roi_large", "roi_big",
-                    "glcm_final", "stats_final", "reset", "roi_stage", "all")
+                    "glcm_final", "stats_final", "reset", "roi_stage", "all", "roi_runzone")
 
     def graph_phase_events(self, enable: bool = True):
         """Record a begin and an end event around each phase inside the

@@ -9,7 +9,8 @@ warm-up extractions, then one more (forward + backward for the float batch)
 between cudaProfilerStart and cudaProfilerStop, so that a profiler started
 with capture off records exactly that extraction's launches.  The hot-path
 feature set is used for the 2048² nuclei workload (as in the benchmark's
-headline line), the full set elsewhere.
+headline line; --all selects the full set there too), the full set
+elsewhere.
 
     python -m paper_2603_12016_gb300.profile_step nuclei2d --subsets
 
@@ -26,7 +27,8 @@ import sys
 
 SUBSETS = (("base", ["MEAN"]), ("order", ["MEAN", "MEDIAN"]), ("histogram", ["MEAN", "ENTROPY"]),
            ("moments", ["MEAN", "INT_M", "BIN_M"]), ("glcm", ["MEAN", "GLCM_ASM"]),
-           ("ngtdm", ["MEAN", "NGTDM_COARSENESS"]), ("gldm", ["MEAN", "GLDM_SDE"]), ("core", "core"),
+           ("ngtdm", ["MEAN", "NGTDM_COARSENESS"]), ("gldm", ["MEAN", "GLDM_SDE"]), ("glrlm", ["MEAN", "GLRLM_SRE"]),
+           ("glszm", ["MEAN", "GLSZM_SAE"]), ("core", "core"),
            ("all", None))
 
 
@@ -56,7 +58,8 @@ def main(argv=None) -> int:
 
     argv = sys.argv[1:] if argv is None else argv
     subsets = "--subsets" in argv
-    argv = [a for a in argv if a != "--subsets"]
+    full = "--all" in argv  # the full feature set for the 2048^2 nuclei workload too
+    argv = [a for a in argv if a not in ("--subsets", "--all")]
     names = (argv[0] if argv else "nuclei2d").split(",")
     procs = max(1, min(16, os.cpu_count() or 1))
     # build every workload before the first CUDA call (the mosaic's tiles use spawned processes)
@@ -80,7 +83,7 @@ def main(argv=None) -> int:
             del ex, table
         return 0
     for n, w in wl.items():
-        feats = "core" if n == "nuclei2d" else "all"
+        feats = "core" if n == "nuclei2d" and not full else "all"
         prm = w.params
         tdt = {np.uint16: torch.uint16, np.int16: torch.int16, np.float32: torch.float32}[w.image.dtype.type]
         nr = w.meta["n_roi"]

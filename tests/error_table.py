@@ -70,7 +70,7 @@ def _gpu_and_oracle(name, sample, threads):
         sel = np.isin(keys, np.array(rois, dtype=np.int64))
         g = {k: v[sel] for k, v in g.items()}
     o = oracle.extract(img, mask, ndim, ng=max(prm.get("glcm_levels", 2) or 2, 2), dists=prm.get("dists", (1,)),
-                       hist_bins=prm.get("hist_bins", 256), rois=rois, threads=threads)
+                       hist_bins=prm.get("hist_bins", 256), rois=rois, threads=threads, families=("glrlm", "glszm"))
     return g, o, ndim, len(g["LABEL"])
 
 

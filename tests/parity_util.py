@@ -48,6 +48,13 @@ def scales(t: Dict[str, np.ndarray], name: str, ndim: int) -> np.ndarray:
         if name in ("GLDM_DV", "GLDM_GLV"):
             return one
         return np.full(n, TINY)
+    if name.startswith(("GLRLM_", "GLSZM_")):
+        # the level and size variances vanish for one item or equal items,
+        # the entropies for one (level, size) cell: unit scale; the rest are
+        # positive means and ratios of positive sums
+        if name.endswith(("_GLV", "_RV", "_ZV", "_RE", "_ZE")):
+            return one
+        return np.full(n, TINY)
     if name.startswith("NGTDM_"):
         # contrast, busyness, complexity and strength are exactly 0 in their
         # degenerate cases (one grey level, no neighbour differences)

@@ -46,6 +46,8 @@ def test_feature_ids(nyxlib):
     assert fid("EDGE_INTEGRATED_INTENSITY") == 81 and fid("EDGE_STDDEV_INTENSITY") == 85
     assert fid("NGTDM_COARSENESS") == 86 and fid("NGTDM_STRENGTH") == 90
     assert fid("GLDM_SDE") == 91 and fid("GLDM_LDHGLE") == 104
+    assert fid("GLRLM_SRE") == 105 and fid("GLRLM_LRHGLE") == 120
+    assert fid("GLSZM_SAE") == 121 and fid("GLSZM_ZSM") == 138
     assert fid("NOPE") == -1
     ids = [fid(n) for n in ("MEAN", "INT_HU", "GLCM_CORR")]
     assert len(set(ids)) == 3
@@ -91,7 +93,7 @@ def test_oracle_and_library_share_the_feature_registry(nyxlib, ndim):
 
     shape = (6, 6) if ndim == 2 else (3, 4, 4)
     img = np.arange(int(np.prod(shape)), dtype=np.uint16).reshape(shape)
-    t = oracle.extract(img, np.ones(shape, dtype=np.int32), ndim, ng=8, dists=(1, 2))
+    t = oracle.extract(img, np.ones(shape, dtype=np.int32), ndim, ng=8, dists=(1, 2), families=("glrlm", "glszm"))
     ids = set()
     for col in t:
         if col in GEOMETRY:
@@ -102,4 +104,4 @@ def test_oracle_and_library_share_the_feature_registry(nyxlib, ndim):
     # 2D has no z centroid; 3D moments have no normalised-raw and Hu families
     absent = {nyxlib.feature_id("WEIGHTED_CENTROID_Z")} if ndim == 2 else \
         {nyxlib.feature_id(n) for n in ("INT_NU", "INT_HU", "BIN_NU", "BIN_HU")}
-    assert ids == set(range(105)) - absent
+    assert ids == set(range(139)) - absent

@@ -50,7 +50,7 @@ def _run(w, precision="fp32", per_offset=True, max_rois=256, features=None):
                        max_rois=max_rois, features=features)
     g = gpu_table(ex, to_torch(w.image), to_torch(w.mask))
     o = oracle.extract(w.image, w.mask, w.ndim, ng=max(ng, 2), dists=prm["dists"], hist_bins=prm["hist_bins"],
-                       threads=8)
+                       threads=8, families=("glrlm", "glszm"))
     return ex, g, o
 
 
@@ -179,7 +179,7 @@ def _sampled(w, ndim, rng_seed, n_random=8, features=None):
     pick = set(order[:3].tolist()) | set(order[-3:].tolist()) | set(rng.choice(len(keys), n_random, replace=False).tolist())
     rows = np.array(sorted(pick))
     o = oracle.extract(w.image, w.mask, ndim, ng=max(ng, 2), dists=prm["dists"], hist_bins=prm["hist_bins"],
-                       rois=[int(keys[i]) for i in rows], threads=8)
+                       rois=[int(keys[i]) for i in rows], threads=8, families=("glrlm", "glszm"))
     g = {k: v[rows] for k, v in g.items()}
     return g, o
 

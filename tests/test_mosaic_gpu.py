@@ -67,7 +67,7 @@ def test_tiles_match_whole_image_and_oracle():
     pick = sorted(set(rng.choice(cross, 24, replace=False).tolist()) |
                   set(rng.choice(g["LABEL"].astype(np.int64), 8, replace=False).tolist()))
     o = oracle.extract(img, mask, 2, ng=64, dists=(1,), hist_bins=256, rois=[oracle.roi_key(0, l) for l in pick],
-                       threads=8)
+                       threads=8, families=("glrlm", "glszm"))
     sel = np.isin(g["LABEL"].astype(np.int64), pick)
     fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
     assert not fails, "\n".join(fails[:30])
@@ -119,7 +119,7 @@ def test_multiblock_key_sort_above_single_block_capacity(n_roi):
     assert np.array_equal(g["AREA"].astype(np.int64), cnt)
     pick = [int(lab[i]) for i in rng.choice(len(lab), 16, replace=False)] + [int(lab[0]), int(lab[-1])]
     o = oracle.extract(img, mask, 2, ng=8, dists=(1,), hist_bins=256, rois=[oracle.roi_key(0, l) for l in pick],
-                       threads=8)
+                       threads=8, families=("glrlm", "glszm"))
     sel = np.isin(g["LABEL"].astype(np.int64), pick)
     fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
     assert not fails, "\n".join(fails[:30])
@@ -154,7 +154,7 @@ def test_mosaic_8192_streamed_sampled_parity():
                   set(rng.choice(lab, 40, replace=False).tolist()) |
                   {int(lab[np.argmax(cnt)]), int(lab[np.argmin(cnt)])})
     o = oracle.extract(img, mask, 2, ng=64, dists=(1,), hist_bins=256, rois=[oracle.roi_key(0, l) for l in pick],
-                       threads=8)
+                       threads=8, families=("glrlm", "glszm"))
     sel = np.isin(g["LABEL"].astype(np.int64), pick)
     assert sel.sum() == len(pick)
     fails = compare({k: v[sel] for k, v in g.items()}, o, 2)

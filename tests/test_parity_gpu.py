@@ -38,7 +38,7 @@ def _run(w, precision="fp32", per_offset=True, features=None, max_rois=None, roi
                        max_rois=max_rois or max(1024, 2 * w.meta["n_roi"]))
     g = gpu_table(ex, to_torch(w.image), to_torch(w.mask))
     o = oracle.extract(w.image, w.mask, w.ndim, ng=max(ng, 2), dists=prm["dists"], hist_bins=prm["hist_bins"],
-                       rois=rois, threads=8)
+                       rois=rois, threads=8, families=("glrlm", "glszm"))
     if rois is not None:
         keys = (g["IMAGE"].astype(np.int64) << 32) | g["LABEL"].astype(np.int64)
         sel = np.isin(keys, np.array(sorted(rois), dtype=np.int64))
@@ -253,11 +253,11 @@ def test_graph_replay_matches_direct_launches():
 
 
 @pytest.mark.parametrize("limits", [None, (0, 0, 4096, 0), (128, 0, 0, 8192), (256, 1024, 0, 0), (0, 512, 2048, 8192),
-                                    (64, 512, 2048, 0, 8), (256, 1024, 4096, 8192, 32)])
+                                    (64, 512, 2048, 0, 8), (256, 1024, 4096, 8192, 32), (0, 0, 0, 0)])
 def test_class_limits_and_autotune_keep_parity(limits):
     """Any class limits (autotuned or set) route ROIs to other kernels; the
     table must still match the oracle.  (256, 1024, 0, 0) sends every ROI
-    above 1,024 px to the multi-block path."""
+    above 1,024 px to the multi-block path, (0, 0, 0, 0) every ROI."""
     nyx = _nyx()
     w = W.config("nuclei2d_small")
     img, mask = to_torch(w.image), to_torch(w.mask)
@@ -272,7 +272,7 @@ def test_class_limits_and_autotune_keep_parity(limits):
     else:
         ex.set_class_limits(*limits)
     g = gpu_table(ex, img, mask)
-    o = oracle.extract(w.image, w.mask, 2, ng=256, dists=(1, 2), hist_bins=256, threads=8)
+    o = oracle.extract(w.image, w.mask, 2, ng=256, dists=(1, 2), hist_bins=256, threads=8, families=("glrlm", "glszm"))
     _assert_parity(g, o, 2)
 
 
@@ -313,3 +313,31 @@ def test_key_sort_paths(case):
         m = (mask[k >> 32] if nb > 1 else mask) == (k & 0xFFFFFFFF)
         assert area == m.sum()
     _assert_parity(g, o, 2)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_signed_intensities_summing_near_zero(ndim):
+    """int16 ROIs whose intensities nearly cancel (CT values around 0 HU) put
+    the intensity-weighted centroid far outside the ROI: the raw and central
+    intensity moments must still match the FP64 definition, and eta with a
+    negative total intensity is NaN wherever the normalising power is not
+    real."""
+    nyx = _nyx()
+    rng = np.random.default_rng(61 + ndim)
+    shape = (96, 96) if ndim == 2 else (16, 48, 48)
+    img = rng.integers(-250, 251, size=shape).astype(np.int16)
+    mask = np.zeros(shape, dtype=np.int32)
+    if ndim == 2:
+        for k in range(9):
+            y, x = 4 + 30 * (k // 3), 4 + 30 * (k % 3)
+            mask[y:y + 22, x:x + 20 + k] = k + 1
+        mask[0, 0] = 10
+    else:
+        mask[2:14, 4:22, 4:22] = 1
+        mask[2:14, 26:44, 26:44] = 2
+        mask[0, 0, 0] = 3
+        img[0, 0, 0] = -17
+    ex = nyx.Extractor(shape, torch.int16, ndim=ndim, glcm_levels=16, dists=(1,), max_rois=64)
+    g = gpu_table(ex, to_torch(img), to_torch(mask))
+    o = oracle.extract(img, mask, ndim, ng=16, dists=(1,), threads=8, families=("glrlm", "glszm"))
+    _assert_parity(g, o, ndim)
