@@ -238,7 +238,7 @@ struct KParams {
   unsigned long long* sort_tmp;    // key buffer of the key sorts [max_rois]
   // GLRLM / GLSZM: work counters of the two block tiers; zone parents and
   // areas of the multi-block ROIs, one word per image pixel (GLSZM only)
-  unsigned* rz_head;               // [2]
+  unsigned* rz_head;               // [N_BLOCK_CLASSES]
   const unsigned long long* rz_qi; // [257] round(2^63 / i^2), levels i = 1..256
   const unsigned long long* rz_qs; // [RZ_STAB + 1] round(2^63 / s^2), sizes s = 1..RZ_STAB
   unsigned* zpar;

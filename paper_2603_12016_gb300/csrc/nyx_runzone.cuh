@@ -34,8 +34,9 @@
 //       level raster (one sentinel cell around the bounding box) in shared
 //       memory; runs walk the raster, zones are a union-find on 16-bit
 //       parent indices in shared memory; (i, s) counts in a shared hash.
-//       Tier 1 takes the warp and small classes (<= 4,096 padded cells),
-//       tier 2 the medium and large classes (<= 16,384).
+//       Tier k drains the queue of size class k: one warp for the warp
+//       class (<= 1,024 padded cells), blocks for the small (<= 4,096),
+//       medium (<= 8,192) and large (<= 16,384) classes.
 //   multi-block ROIs, units (ROI, chunk of BIG_CHUNK cells), zone parents
 //   and areas one 32-bit word each per image pixel, cleared by one memset:
 //       k_rzb_items  runs, walking through global memory (a run may cross
@@ -67,8 +68,10 @@ template <int NT_, int CELLS_, int PIX_, int HC_, int HS_>
 struct RzTier {
   static constexpr int NT = NT_, NW = NT_ / 32, CELLS = CELLS_, PIX = PIX_, HC = HC_, HS = HS_;
 };
+using RzT0 = RzTier<32, 1024, 256, 512, 64>;
 using RzT1 = RzTier<128, 4096, 1024, 2048, 128>;
-using RzT2 = RzTier<256, 16384, 8192, 4096, 256>;
+using RzT2 = RzTier<256, 8192, 4096, 4096, 256>;
+using RzT3 = RzTier<256, 16384, 8192, 4096, 256>;
 constexpr int RZ_NV = 26;          // reduced values per set
 constexpr int RZ_BIG_HS = 8192;    // size-marginal slots of k_rzb_final
 constexpr int RZ_BIG_SH = 4096;    // shared item slots per unit of the multi-block kernels
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
   __shared__ RoiInfo s_r;
   const int tid = threadIdx.x;
   const bool do_rl = (p.need & NEED_GLRLM) != 0, do_sz = (p.need & NEED_GLSZM) != 0;
-  const int cl = tier == 1 ? 0 : 2;  // this tier drains the queues of classes cl and cl + 1
+  const int cl = tier;  // the size class whose queue this tier drains
   const T* img = (const T*)p.img;
   for (int i = tid; i < 256; i += Z::NT) {
     lvl_n[i] = 0;
@@ -572,11 +575,8 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
   };
   for (;;) {
     if (tid == 0) {
-      const unsigned w = atomicAdd(p.rz_head + (tier - 1), 1u);
-      const unsigned q0 = p.qlen[cl], q1 = p.qlen[cl + 1];
-      int it = -1;
-      if (w < q0) it = p.queue[(int64_t)cl * p.max_rois + w];
-      else if (w < q0 + q1) it = p.queue[(int64_t)(cl + 1) * p.max_rois + (w - q0)];
+      const unsigned w = atomicAdd(p.rz_head + tier, 1u);
+      const int it = w < p.qlen[cl] ? p.queue[(int64_t)cl * p.max_rois + w] : -1;
       s_item = it;
       if (it >= 0) s_r = p.rois[it];
     }
@@ -705,15 +705,21 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
     if (tid <= ND && ((tid < ND && do_rl) || (tid == ND && do_sz)))
       rz_features(red[tid], r.n, tid < ND ? 16 : 18, sf[tid], false);
     __syncthreads();
-    if (do_rl && tid < 16) {
-      double m = 0;
-      for (int k = 0; k < ND; ++k) m += sf[k][tid];
-      const int col = p.col_map[Q_GLRLM + tid];
-      if (col >= 0) p.table[(int64_t)item * p.n_col + col] = m * (1.0 / ND);
-    }
-    if (do_sz && tid >= 32 && tid < 32 + 18) {
-      const int col = p.col_map[Q_GLSZM + tid - 32];
-      if (col >= 0) p.table[(int64_t)item * p.n_col + col] = sf[ND][tid - 32];
+    for (int q = tid; q < 34; q += Z::NT) {  // 16 GLRLM columns, then 18 GLSZM
+      double v;
+      int col;
+      if (q < 16) {
+        if (!do_rl) continue;
+        v = 0;
+        for (int k = 0; k < ND; ++k) v += sf[k][q];
+        v *= 1.0 / ND;
+        col = p.col_map[Q_GLRLM + q];
+      } else {
+        if (!do_sz) continue;
+        v = sf[ND][q - 16];
+        col = p.col_map[Q_GLSZM + q - 16];
+      }
+      if (col >= 0) p.table[(int64_t)item * p.n_col + col] = v;
     }
     __syncthreads();  // every thread is done with s_item / s_r / red / sf
   }
@@ -964,9 +970,15 @@ static cudaError_t rz_launch(int nt, int smem, int nsm, const KParams& p, cudaSt
 // block path: both tiers, on one stream
 template <class T, int NDIM>
 cudaError_t launch_rz_blocks_one(const KParams& p, int nsm, cudaStream_t st) {
-  cudaError_t e = rz_launch<k_rz<T, NDIM, RzT1>>(RzT1::NT, rz_smem_bytes<RzT1>(), nsm, p, st, 1);
-  if (e != cudaSuccess) return e;
-  return rz_launch<k_rz<T, NDIM, RzT2>>(RzT2::NT, rz_smem_bytes<RzT2>(), nsm, p, st, 2);
+  cudaError_t e = cudaSuccess;
+  if (p.lim_pix[0] > 0 && (e = rz_launch<k_rz<T, NDIM, RzT0>>(RzT0::NT, rz_smem_bytes<RzT0>(), nsm, p, st, 0)))
+    return e;
+  if (p.lim_pix[1] > 0 && (e = rz_launch<k_rz<T, NDIM, RzT1>>(RzT1::NT, rz_smem_bytes<RzT1>(), nsm, p, st, 1)))
+    return e;
+  if (p.lim_pix[2] > 0 && (e = rz_launch<k_rz<T, NDIM, RzT2>>(RzT2::NT, rz_smem_bytes<RzT2>(), nsm, p, st, 2)))
+    return e;
+  if (p.lim_pix[3] > 0) e = rz_launch<k_rz<T, NDIM, RzT3>>(RzT3::NT, rz_smem_bytes<RzT3>(), nsm, p, st, 3);
+  return e;
 }
 
 // multi-block path, after the multi-block kernels (which clear the ROIs'

@@ -645,7 +645,9 @@ __global__ void k_msort_done(KParams p) {
 // append it to that class's work queue.
 __global__ void k_setup(KParams p) {
   const unsigned n = *p.n_roi;
-  const int pad = (p.need & (NEED_GLCM | NEED_EDGE | NEED_NGTDM | NEED_GLDM)) ? p.pad : 0;
+  // padded cells: the GLCM / edge / NGTDM / GLDM raster of k_roi and the
+  // GLRLM / GLSZM raster (one border cell) must fit the class
+  const int pad = (p.need & (NEED_GLCM | NEED_EDGE | NEED_NGTDM | NEED_GLDM | NEED_GLRLM | NEED_GLSZM)) ? p.pad : 0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned long long key = p.sorted_keys[i];
     const int s = g_find(p.keys, p.hmask, key);
@@ -806,7 +808,7 @@ __global__ void k_begin(KParams p) {
     p.qlen[t] = 0;
     p.qhead[t] = 0;
   }
-  if (t < 2 && p.rz_head) p.rz_head[t] = 0;
+  if (t < N_BLOCK_CLASSES && p.rz_head) p.rz_head[t] = 0;
   if (t < 3 && p.big_ctr) {
     if (t == 0) *p.big_ctr = 0;
     p.big_used[t] = 0;
