@@ -446,7 +446,10 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   if (arena_words > (1ull << 30)) arena_words = 1ull << 30;  // 4 GiB: large mosaics hold few multi-block ROIs
   const size_t o_arena = take(4ull * arena_words);
   // zone parents and areas of the multi-block ROIs (GLSZM): one word each per pixel
-  const size_t o_zpar = want_sz ? take(8ull * total_px) : 0;  // parents, then areas (cleared together)
+  // multi-block GLRLM / GLSZM, one word each per pixel, cleared together every
+  // call: the (ROI, level) tag of every multi-block ROI pixel, then (GLSZM)
+  // the zone parents and areas
+  const size_t o_zbuf = (want_rl || want_sz) ? take((want_sz ? 12ull : 4ull) * total_px) : 0;
   // per (ROI, offset) GLCM accumulators (GI int64 + GF sums in 8-byte slots)
   const int n_off_all = p.glcm_levels > 0 ? p.n_dist * (p.ndim == 3 ? 13 : 4) : 0;
   const size_t o_gacc = take((size_t)mr * n_off_all * (8 * (GI_HOST + GF_HOST)));
@@ -538,8 +541,9 @@ nyx_status nyx_plan_create(nyx_ctx* ctx, const nyx_params* params, nyx_plan** ou
   k.qlen = small + 4;
   k.qhead = small + 8;
   k.rz_head = small + 12;
-  k.zpar = want_sz ? (unsigned*)(w + o_zpar) : nullptr;
-  k.zcnt = want_sz ? (unsigned*)(w + o_zpar) + total_px : nullptr;
+  k.ztag = (want_rl || want_sz) ? (unsigned*)(w + o_zbuf) : nullptr;
+  k.zpar = want_sz ? (unsigned*)(w + o_zbuf) + total_px : nullptr;
+  k.zcnt = want_sz ? (unsigned*)(w + o_zbuf) + 2 * total_px : nullptr;
   k.img_vmin = (unsigned*)(w + o_imin);
   k.img_vmax = (unsigned*)(w + o_imax);
   k.big = (BigRoi*)(w + o_big);

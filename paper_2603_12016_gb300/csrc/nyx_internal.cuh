@@ -241,6 +241,7 @@ struct KParams {
   unsigned* rz_head;               // [N_BLOCK_CLASSES]
   const unsigned long long* rz_qi; // [257] round(2^63 / i^2), levels i = 1..256
   const unsigned long long* rz_qs; // [RZ_STAB + 1] round(2^63 / s^2), sizes s = 1..RZ_STAB
+  unsigned* ztag;                  // (multi-block ROI index + 1) << 9 | level of its pixels, else 0
   unsigned* zpar;
   unsigned* zcnt;
 };

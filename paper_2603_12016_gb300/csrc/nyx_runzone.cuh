@@ -329,8 +329,8 @@ struct RzLevel {
 };
 
 // ---- hash tables of items ---------------------------------------------------
-// block path: key (i << 16 | s) (i >= 1, so 0 = empty), one item added
-__device__ inline void rz_insert(unsigned* key, unsigned* cnt, int cap, unsigned k, unsigned* err) {
+// block path: key (i << 16 | s) (i >= 1, so 0 = empty), n items added
+__device__ inline void rz_insert(unsigned* key, unsigned* cnt, int cap, unsigned k, unsigned n, unsigned* err) {
   unsigned h = ((k * 2654435761u) >> 16) & (unsigned)(cap - 1);
   for (int probe = 0; probe < cap; ++probe) {
     unsigned cur = ((volatile unsigned*)key)[h];
@@ -339,7 +339,7 @@ __device__ inline void rz_insert(unsigned* key, unsigned* cnt, int cap, unsigned
       if (cur == 0) cur = k;
     }
     if (cur == k) {
-      atomicAdd(cnt + h, 1u);
+      atomicAdd(cnt + h, n);
       return;
     }
     h = (h + 1) & (unsigned)(cap - 1);
@@ -389,7 +389,7 @@ struct RzTab {
 
 // one item into the unit's shared table (a few probes), else straight into
 // the ROI's global one
-__device__ inline void rz_item(rz_u64* skey, unsigned* scnt, const RzTab& g, rz_u64 k, unsigned* err) {
+__device__ inline void rz_item(rz_u64* skey, unsigned* scnt, const RzTab& g, rz_u64 k, unsigned n, unsigned* err) {
   unsigned h = (unsigned)((k * 0x9E3779B97F4A7C15ull) >> 40) & (unsigned)(RZ_BIG_SH - 1);
   for (int probe = 0; probe < 32; ++probe) {
     rz_u64 cur = ((volatile rz_u64*)skey)[h];
@@ -398,12 +398,21 @@ __device__ inline void rz_item(rz_u64* skey, unsigned* scnt, const RzTab& g, rz_
       if (cur == 0) cur = k;
     }
     if (cur == k) {
-      atomicAdd(scnt + h, 1u);
+      atomicAdd(scnt + h, n);
       return;
     }
     h = (h + 1) & (unsigned)(RZ_BIG_SH - 1);
   }
-  g.add(k, 1u, err);
+  g.add(k, n, err);
+}
+
+// warp-aggregated version: every lane of the warp calls it with its key (0:
+// none), and lanes with equal keys add their items once, through the lowest
+// of them (in smooth images many runs share a key and would serialise on one
+// shared-memory counter)
+__device__ inline void rz_item_warp(rz_u64* skey, unsigned* scnt, const RzTab& g, rz_u64 k, unsigned* err) {
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+  if (k && (peers & lanemask_lt()) == 0) rz_item(skey, scnt, g, k, (unsigned)__popc(peers), err);
 }
 
 // ---- union-find ---------------------------------------------------------------
@@ -655,7 +664,7 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
           if (!L || rast[c - dv] == L) continue;  // not a run start (the border stops every walk)
           unsigned len = 1;
           for (int q = c + dv; rast[q] == L; q += dv) ++len;
-          rz_insert(hkey, hcnt, hc, (L << 16) | len, p.err);
+          rz_insert(hkey, hcnt, hc, (L << 16) | len, 1u, p.err);
         }
         __syncthreads();  // also: the previous set's marginal pass is done with lvl / hs
         reduce_set(k);
@@ -697,7 +706,7 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
       }
       __syncthreads();
       for (int c = tid; c < cells; c += Z::NT)
-        if (rast[c] & 0x8000) rz_insert(hkey, hcnt, hc, ((unsigned)(rast[c] & 0x1FF) << 16) | par[c], p.err);
+        if (rast[c] & 0x8000) rz_insert(hkey, hcnt, hc, ((unsigned)(rast[c] & 0x1FF) << 16) | par[c], 1u, p.err);
       __syncthreads();
       reduce_set(ND);
     }
@@ -735,8 +744,9 @@ struct RzBig {
   RzTab tab;
   unsigned c0, c1;
   int item;
-  unsigned n;
+  unsigned n, tag0;  // tag0: (multi-block ROI index + 1) << 9
   __device__ void init(const KParams& p, int b, int chunk) {
+    tag0 = (unsigned)(b + 1) << 9;
     const BigRoi br = p.big[b];
     const RoiInfo r = p.rois[br.item];
     bx.init(p, r, NDIM);
@@ -747,6 +757,12 @@ struct RzBig {
     c1 = min(bx.cells, c0 + (unsigned)BIG_CHUNK);
     item = br.item;
     n = r.n;
+  }
+  // tag (ROI + 1) << 9 | level of box cell (x, y, z) from the tag array, 0
+  // off every multi-block ROI (or off the box)
+  __device__ unsigned tag_at(const KParams& p, int x, int y, int z) const {
+    if (x < 0 || y < 0 || z < 0 || x >= bx.W || y >= bx.H || z >= bx.D) return 0u;
+    return __ldg(p.ztag + bx.origin + ((int64_t)z * p.ny + y) * p.nx + x);
   }
   // level of box cell (x, y, z), 0 off the ROI (or off the box)
   __device__ unsigned level_at(const KParams& p, const T* img, int x, int y, int z) const {
@@ -782,6 +798,22 @@ __device__ inline void rz_flush(rz_u64* skey, unsigned* scnt, const RzTab& g, un
   __syncthreads();
 }
 
+// the tag array: (multi-block ROI index + 1) << 9 | level of every pixel of
+// a multi-block ROI (the array is cleared before), so that the items kernel
+// compares one word per neighbour
+template <class T, int NDIM>
+__global__ void __launch_bounds__(BIG_NT) k_rzb_tags(KParams p) {
+  const int tid = threadIdx.x;
+  const T* img = (const T*)p.img;
+  rz_units<T, NDIM>(p, [&](const RzBig<T, NDIM>& g) {
+    for (unsigned c = g.c0 + tid; c < g.c1; c += BIG_NT) {
+      int x, y, z;
+      const int64_t off = g.bx.offset(c, x, y, z, p);
+      if (__ldg(p.mask + off) == g.bx.label) p.ztag[off] = g.tag0 | g.lev(Enc<T>::enc(__ldg(img + off)));
+    }
+  });
+}
+
 // runs (GLRLM) and zone links (GLSZM) of the unit's cells: a run starts where
 // the predecessor along its direction is not of its level and is walked to its
 // end; a cell is linked to every forward neighbour of its level (the walk's
@@ -796,7 +828,6 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_items(KParams p) {
   constexpr int ND = NDIM == 3 ? 13 : 4;
   const int tid = threadIdx.x;
   const bool do_rl = (p.need & NEED_GLRLM) != 0, do_sz = (p.need & NEED_GLSZM) != 0;
-  const T* img = (const T*)p.img;
   if (tid < ND) rz_dir(NDIM, tid, s_d[tid][0], s_d[tid][1], s_d[tid][2]);
   for (int i = tid; i < RZ_BIG_SH; i += BIG_NT) {
     skey[i] = 0;
@@ -804,24 +835,35 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_items(KParams p) {
   }
   __syncthreads();
   rz_units<T, NDIM>(p, [&](const RzBig<T, NDIM>& g) {
-    for (unsigned c = g.c0 + tid; c < g.c1; c += BIG_NT) {
-      int x, y, z;
-      const int64_t off = g.bx.offset(c, x, y, z, p);
-      if (__ldg(p.mask + off) != g.bx.label) continue;
-      const unsigned L = g.lev(Enc<T>::enc(__ldg(img + off)));
+    for (unsigned cb = g.c0; cb < g.c1; cb += BIG_NT) {  // whole warps, for the aggregated inserts
+      const unsigned c = cb + tid;
+      int x = 0, y = 0, z = 0;
+      int64_t off = 0;
+      unsigned tg = 0;
+      if (c < g.c1) {
+        off = g.bx.offset(c, x, y, z, p);
+        tg = __ldg(p.ztag + off);
+        if ((tg & ~511u) != g.tag0) tg = 0;  // not this ROI's pixel
+      }
+      const unsigned L = tg & 511u;
 #pragma unroll 1
       for (int k = 0; k < ND; ++k) {
         const int dx = s_d[k][0], dy = s_d[k][1], dz = s_d[k][2];
-        const bool next = g.level_at(p, img, x + dx, y + dy, z + dz) == L;
-        if (do_sz && next)
-          rzg_union(p.zpar, (unsigned)off, (unsigned)(off + ((int64_t)dz * p.ny + dy) * p.nx + dx), p.err);
-        if (!do_rl || g.level_at(p, img, x - dx, y - dy, z - dz) == L) continue;  // not a run start
-        unsigned len = 1;
-        if (next) {
-          len = 2;
-          while (g.level_at(p, img, x + (int)len * dx, y + (int)len * dy, z + (int)len * dz) == L) ++len;
+        rz_u64 key = 0;
+        if (tg) {
+          const bool next = g.tag_at(p, x + dx, y + dy, z + dz) == tg;
+          if (do_sz && next)
+            rzg_union(p.zpar, (unsigned)off, (unsigned)(off + ((int64_t)dz * p.ny + dy) * p.nx + dx), p.err);
+          if (do_rl && g.tag_at(p, x - dx, y - dy, z - dz) != tg) {  // a run start
+            unsigned len = 1;
+            if (next) {
+              len = 2;
+              while (g.tag_at(p, x + (int)len * dx, y + (int)len * dy, z + (int)len * dz) == tg) ++len;
+            }
+            key = ((rz_u64)k << 48) | ((rz_u64)L << 32) | len;
+          }
         }
-        rz_item(skey, scnt, g.tab, ((rz_u64)k << 48) | ((rz_u64)L << 32) | len, p.err);
+        rz_item_warp(skey, scnt, g.tab, key, p.err);
       }
     }
     rz_flush(skey, scnt, g.tab, p.err);
@@ -852,20 +894,23 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_zones(KParams p) {
   unsigned* scnt = (unsigned*)(skey + RZ_BIG_SH);
   constexpr int ND = NDIM == 3 ? 13 : 4;
   const int tid = threadIdx.x;
-  const T* img = (const T*)p.img;
   for (int i = tid; i < RZ_BIG_SH; i += BIG_NT) {
     skey[i] = 0;
     scnt[i] = 0;
   }
   __syncthreads();
   rz_units<T, NDIM>(p, [&](const RzBig<T, NDIM>& g) {
-    for (unsigned c = g.c0 + tid; c < g.c1; c += BIG_NT) {
-      int x, y, z;
-      const int64_t off = g.bx.offset(c, x, y, z, p);
-      if (__ldg(p.mask + off) != g.bx.label || __ldcg(p.zpar + off) != 0u) continue;  // roots only
-      const unsigned L = g.lev(Enc<T>::enc(__ldg(img + off)));
-      rz_item(skey, scnt, g.tab, ((rz_u64)ND << 48) | ((rz_u64)L << 32) | __ldcg(p.zcnt + off),
-              p.err);
+    for (unsigned cb = g.c0; cb < g.c1; cb += BIG_NT) {
+      const unsigned c = cb + tid;
+      rz_u64 key = 0;
+      if (c < g.c1) {
+        int x, y, z;
+        const int64_t off = g.bx.offset(c, x, y, z, p);
+        const unsigned tg = __ldg(p.ztag + off);
+        if ((tg & ~511u) == g.tag0 && __ldcg(p.zpar + off) == 0u)  // a root of this ROI
+          key = ((rz_u64)ND << 48) | ((rz_u64)(tg & 511u) << 32) | __ldcg(p.zcnt + off);
+      }
+      rz_item_warp(skey, scnt, g.tab, key, p.err);
     }
     rz_flush(skey, scnt, g.tab, p.err);
   });
@@ -987,10 +1032,11 @@ template <class T, int NDIM>
 cudaError_t launch_rz_big_one(const KParams& p, int nsm, cudaStream_t st) {
   const int sh = RZ_BIG_SH * 12;
   cudaError_t e = cudaSuccess;
-  if (p.need & NEED_GLSZM) {  // every pixel its own zone (parent 0), areas 0: one clear of both arrays
+  {  // tags 0, every pixel its own zone (parent 0), areas 0: one clear
     const unsigned long long px = (unsigned long long)p.batch * p.nx * p.ny * p.nz;
-    if ((e = cudaMemsetAsync(p.zpar, 0, 8ull * px, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.ztag, 0, ((p.need & NEED_GLSZM) ? 12ull : 4ull) * px, st)) != cudaSuccess) return e;
   }
+  if ((e = rz_launch<k_rzb_tags<T, NDIM>>(BIG_NT, 0, nsm, p, st)) != cudaSuccess) return e;
   if ((e = rz_launch<k_rzb_items<T, NDIM>>(BIG_NT, sh, nsm, p, st)) != cudaSuccess) return e;
   if (p.need & NEED_GLSZM) {
     if ((e = rz_launch<k_rzb_count<T, NDIM>>(BIG_NT, 0, nsm, p, st)) != cudaSuccess) return e;
