@@ -59,7 +59,8 @@ typedef unsigned long long rz_u64;
 typedef unsigned __int128 rz_u128;
 
 // Tier geometry of the block path: threads, max padded cells, max pixels,
-// joint-hash slots, size-marginal slots.  The hash sizes follow from the
+// joint-hash slots, size-marginal slots (twice the threads of the matching
+// k_roi class measured faster: the sets are short phases between barriers).  The hash sizes follow from the
 // number of distinct (i, s) keys of a set: their sizes sum to at most the
 // ROI's pixel count N, so there are at most sqrt(2 N Ng) of them (<= 724
 // for N = 1,024, <= 2,048 for N = 8,192 at Ng = 256), and at most sqrt(2 N)
@@ -69,9 +70,9 @@ struct RzTier {
   static constexpr int NT = NT_, NW = NT_ / 32, CELLS = CELLS_, PIX = PIX_, HC = HC_, HS = HS_;
 };
 using RzT0 = RzTier<32, 1024, 256, 512, 64>;
-using RzT1 = RzTier<128, 4096, 1024, 2048, 128>;
-using RzT2 = RzTier<256, 8192, 4096, 4096, 256>;
-using RzT3 = RzTier<256, 16384, 8192, 4096, 256>;
+using RzT1 = RzTier<256, 4096, 1024, 2048, 128>;
+using RzT2 = RzTier<512, 8192, 4096, 4096, 256>;
+using RzT3 = RzTier<512, 16384, 8192, 4096, 256>;
 constexpr int RZ_NV = 26;          // reduced values per set
 constexpr int RZ_BIG_HS = 8192;    // size-marginal slots of k_rzb_final
 constexpr int RZ_BIG_SH = 4096;    // shared item slots per unit of the multi-block kernels
