@@ -105,6 +105,28 @@ __host__ __device__ inline void rz_dir(int ndim, int k, int& dx, int& dy, int& d
   dx = dy = dz = 0;
 }
 
+// Zone links that can be skipped: a cell p links to each forward neighbour
+// n = p + d of its level, unless an earlier direction d' (in rz_dir order)
+// gave a neighbour m = p + d' of its level adjacent to n (Chebyshev distance
+// 1).  Then p -- m and m -- n are links too (n is another of m's 26
+// neighbours), both from a source later in the (raster index, reversed
+// direction order) order than p -- n (m and n come after p in raster order;
+// p -- m has an earlier direction), so by induction from the last links p
+// and n end in one zone.  In a uniform region one link per cell remains.
+// adj_mask(d): the directions d' < d whose neighbours are adjacent to p + d.
+__host__ __device__ inline unsigned rz_adj_mask(int ndim, int d) {
+  int ax, ay, az;
+  rz_dir(ndim, d, ax, ay, az);
+  unsigned m = 0;
+  for (int e = 0; e < d; ++e) {
+    int bx, by, bz;
+    rz_dir(ndim, e, bx, by, bz);
+    const int cx = ax - bx, cy = ay - by, cz = az - bz;
+    if (cx >= -1 && cx <= 1 && cy >= -1 && cy <= 1 && cz >= -1 && cz <= 1) m |= 1u << e;
+  }
+  return m;
+}
+
 // ---- fixed-point terms -----------------------------------------------------
 // round(2^63 / d) for 1 <= d < 2^62
 __device__ inline rz_u64 rz_q63(rz_u64 d) {
@@ -412,6 +434,7 @@ __device__ inline void rz_item(rz_u64* skey, unsigned* scnt, const RzTab& g, rz_
 // of them (in smooth images many runs share a key and would serialise on one
 // shared-memory counter)
 __device__ inline void rz_item_warp(rz_u64* skey, unsigned* scnt, const RzTab& g, rz_u64 k, unsigned* err) {
+  if (!__any_sync(0xFFFFFFFFu, k != 0)) return;
   const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
   if (k && (peers & lanemask_lt()) == 0) rz_item(skey, scnt, g, k, (unsigned)__popc(peers), err);
 }
@@ -523,12 +546,14 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
   __shared__ rz_u64 red[ND + 1][RZ_NV];
   __shared__ double sf[ND + 1][18];
   __shared__ int s_dv[13];
+  __shared__ unsigned s_adj[13];
   __shared__ int s_item;
   __shared__ RoiInfo s_r;
   const int tid = threadIdx.x;
   const bool do_rl = (p.need & NEED_GLRLM) != 0, do_sz = (p.need & NEED_GLSZM) != 0;
   const int cl = tier;  // the size class whose queue this tier drains
   const T* img = (const T*)p.img;
+  if (tid < ND) s_adj[tid] = rz_adj_mask(NDIM, tid);
   for (int i = tid; i < 256; i += Z::NT) {
     lvl_n[i] = 0;
     lvl_a[i] = 0;
@@ -679,10 +704,13 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
       for (int c = tid; c < cells; c += Z::NT) {
         const unsigned L = rast[c];
         if (!L) continue;
+        unsigned same = 0;  // directions whose neighbour has this level
 #pragma unroll 1
         for (int k = 0; k < ND; ++k) {
           const int n = c + s_dv[k];
-          if (rast[n] == L) rz_union(par, c, n, p.err);
+          if (rast[n] != L) continue;
+          if (!(s_adj[k] & same)) rz_union(par, c, n, p.err);  // else already joined through an adjacent one
+          same |= 1u << k;
         }
       }
       __syncthreads();
@@ -826,10 +854,14 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_items(KParams p) {
   rz_u64* skey = (rz_u64*)rz_smem;
   unsigned* scnt = (unsigned*)(skey + RZ_BIG_SH);
   __shared__ int s_d[13][3];
+  __shared__ unsigned s_adj[13];
   constexpr int ND = NDIM == 3 ? 13 : 4;
   const int tid = threadIdx.x;
   const bool do_rl = (p.need & NEED_GLRLM) != 0, do_sz = (p.need & NEED_GLSZM) != 0;
-  if (tid < ND) rz_dir(NDIM, tid, s_d[tid][0], s_d[tid][1], s_d[tid][2]);
+  if (tid < ND) {
+    rz_dir(NDIM, tid, s_d[tid][0], s_d[tid][1], s_d[tid][2]);
+    s_adj[tid] = rz_adj_mask(NDIM, tid);
+  }
   for (int i = tid; i < RZ_BIG_SH; i += BIG_NT) {
     skey[i] = 0;
     scnt[i] = 0;
@@ -847,14 +879,16 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_items(KParams p) {
         if ((tg & ~511u) != g.tag0) tg = 0;  // not this ROI's pixel
       }
       const unsigned L = tg & 511u;
+      unsigned same = 0;  // directions whose neighbour has this level
 #pragma unroll 1
       for (int k = 0; k < ND; ++k) {
         const int dx = s_d[k][0], dy = s_d[k][1], dz = s_d[k][2];
         rz_u64 key = 0;
         if (tg) {
           const bool next = g.tag_at(p, x + dx, y + dy, z + dz) == tg;
-          if (do_sz && next)
+          if (do_sz && next && !(s_adj[k] & same))  // else already joined through an adjacent neighbour
             rzg_union(p.zpar, (unsigned)off, (unsigned)(off + ((int64_t)dz * p.ny + dy) * p.nx + dx), p.err);
+          if (next) same |= 1u << k;
           if (do_rl && g.tag_at(p, x - dx, y - dy, z - dz) != tg) {  // a run start
             unsigned len = 1;
             if (next) {
