@@ -296,10 +296,9 @@ nyx_status nyx_phase_times(nyx_plan* plan, int back, float* ms, int n);
  * kernel, the table reset, the per-ROI stage (from before the size classes
  * fork to after they join: the four classes run as concurrent branches, so
  * each class's own span includes waiting for SMs that the others hold), and
- * the whole extraction, and the block-class GLRLM / GLSZM kernels (a branch
- * of their own beside the size classes, inside the per-ROI stage; the
- * multi-block GLRLM / GLSZM kernels follow the multi-block class on its
- * branch and count to it).  A class that receives no ROI reads as about 0.
+ * the whole extraction, and the GLRLM / GLSZM kernels (block classes, then
+ * multi-block ROIs: a branch of their own beside the size classes, inside
+ * the per-ROI stage).  A class that receives no ROI reads as about 0.
  * Errors: NYX_ERR_ARG (null plan/ms), NYX_ERR_STATE (events off or graphs
  * off), NYX_ERR_CUDA. */
 enum {

@@ -803,7 +803,8 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
   }
   if (rz) {  // block-class GLRLM / GLSZM: reads the image and ROI table only, writes its own columns
     NYX_CUDA(c, gmark(gev, NYX_GPH_RZ, 0, s_rz));
-    const cudaError_t e = launch_rz(k, 0, c->nsm, s_rz);
+    cudaError_t e = launch_rz(k, 0, c->nsm, s_rz);
+    if (e == cudaSuccess) e = launch_rz(k, 1, c->nsm, s_rz);  // then the multi-block ROIs, on the same branch
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "GLRLM / GLSZM kernel launch failed: %s", cudaGetErrorString(e));
     NYX_CUDA(c, gmark(gev, NYX_GPH_RZ, 1, s_rz));
   } else {
@@ -812,10 +813,8 @@ static nyx_status enqueue_back(nyx_plan* pl, const KParams& k, cudaEvent_t* ev, 
   }
   {
     NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 0, s_big));
-    cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
+    const cudaError_t e = launch_big(k, fp64, c->nsm, s_big);
     if (e != cudaSuccess) return fail(c, NYX_ERR_CUDA, "multi-block ROI kernel launch failed: %s", cudaGetErrorString(e));
-    if (rz && (e = launch_rz(k, 1, c->nsm, s_big)) != cudaSuccess)
-      return fail(c, NYX_ERR_CUDA, "multi-block GLRLM / GLSZM kernel launch failed: %s", cudaGetErrorString(e));
     NYX_CUDA(c, gmark(gev, NYX_GPH_BIG, 1, s_big));
     if (ev) NYX_CUDA(c, cudaEventRecord(ev[7], st));
   }

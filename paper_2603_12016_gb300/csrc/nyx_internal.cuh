@@ -280,6 +280,11 @@ __host__ __device__ inline unsigned long long rz_hcap(const KParams& p, unsigned
   return cap;
 }
 constexpr int RZ_NV_HOST = 26;  // reduced values per set (u64), kept per set in the arena
+// words of a multi-block ROI's GLRLM / GLSZM region (a multiple of 4)
+__host__ __device__ inline unsigned long long rz_words(const KParams& p, unsigned n) {
+  const int sets = rz_sets(p);
+  return sets ? (((unsigned long long)sets * (3ull * rz_hcap(p, n) + 2ull * RZ_NV_HOST) + 4 + 3) & ~3ull) : 0ull;
+}
 
 __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int nsp, unsigned range, unsigned n) {
   const unsigned long long n_off = (unsigned long long)p.n_dist * p.n_dirs;
@@ -294,13 +299,15 @@ __host__ __device__ inline BigLayout big_layout(const KParams& p, int nch, int n
   L.tri = o;      o = (o + (nsp > 1 ? n_off * tri : 0) + 3) & ~3ull;
   L.ngt = o;      o = (o + ((p.need & NEED_NGTDM) ? 3ull * p.ng : 0) + 3) & ~3ull;  // S[ng] int64, then n[ng] u32
   L.gld = o;      o = (o + ((p.need & NEED_GLDM) ? (unsigned long long)p.ng * (p.ndim == 3 ? 27 : 9) : 0) + 3) & ~3ull;
-  // per set: u64 keys (0 = empty) of rz_hcap slots; then the u32 counts of
-  // every set; then each set's reduced values (u64)
-  L.rzh = o;      o = (o + (unsigned long long)rz_sets(p) * (3ull * rz_hcap(p, n) + 2ull * RZ_NV_HOST) + 3) & ~3ull;
   L.zero_end = o;
   L.part1 = o;    o += (unsigned long long)nch * BIG_P1;
   L.part2 = o;    o += (unsigned long long)nch * BIG_P2;
   L.fsort = o;    o += fsort ? 2ull * n : 0;
+  // GLRLM / GLSZM (cleared by their own first kernel, which runs beside the
+  // multi-block kernels): per set u64 keys (0 = empty) of rz_hcap slots; the
+  // u32 counts of every set; each set's reduced values (u64); a counter
+  o = (o + 3) & ~3ull;
+  L.rzh = o;      o += rz_words(p, n);
   L.total = (o + 3) & ~3ull;
   return L;
 }

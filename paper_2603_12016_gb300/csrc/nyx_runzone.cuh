@@ -378,6 +378,7 @@ struct RzTab {
   rz_u64* key;
   unsigned* cnt;
   rz_u64* red;
+  unsigned* ctr;  // arrivals of k_rzb_final's (ROI, set) units
   rz_u64 cap;
   int nsets;
   __device__ void init(unsigned* base, rz_u64 cap_, int nsets_) {
@@ -386,6 +387,7 @@ struct RzTab {
     key = (rz_u64*)base;
     cnt = (unsigned*)(key + cap * nsets);
     red = (rz_u64*)(cnt + cap * nsets);
+    ctr = (unsigned*)(red + (rz_u64)RZ_NV * nsets);
   }
   // table of a key's set (the zones are the last table)
   __device__ int tix(rz_u64 k) const { return min((int)(k >> 48), nsets - 1); }
@@ -835,6 +837,11 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_tags(KParams p) {
   const int tid = threadIdx.x;
   const T* img = (const T*)p.img;
   rz_units<T, NDIM>(p, [&](const RzBig<T, NDIM>& g) {
+    if (g.c0 == 0) {  // the ROI's first unit clears its item tables, values and counter
+      uint4* zr = (uint4*)g.tab.key;
+      const unsigned long long n4 = rz_words(p, g.n) / 4;
+      for (unsigned long long i = tid; i < n4; i += BIG_NT) zr[i] = make_uint4(0, 0, 0, 0);
+    }
     for (unsigned c = g.c0 + tid; c < g.c1; c += BIG_NT) {
       int x, y, z;
       const int64_t off = g.bx.offset(c, x, y, z, p);
@@ -1002,7 +1009,7 @@ __global__ void __launch_bounds__(BIG_NT) k_rzb_final(KParams p) {
     rz_marg_pass<BIG_NT>(p, lvl_n, lvl_a, hs_key, hs_cnt, RZ_BIG_HS, jv, ent, red);
     __syncthreads();
     if (tid < RZ_NV) __stcg(tab.red + (rz_u64)t * RZ_NV + tid, red[tid]);
-    if (!last_arrival(reg + L.ctr + 3, (unsigned)nsets, &s_flag)) continue;
+    if (!last_arrival(tab.ctr, (unsigned)nsets, &s_flag)) continue;
     // every set of this ROI is reduced: features, one thread per set
     if (tid < nsets) {
       rz_u64 v[RZ_NV];
@@ -1061,8 +1068,8 @@ cudaError_t launch_rz_blocks_one(const KParams& p, int nsm, cudaStream_t st) {
   return e;
 }
 
-// multi-block path, after the multi-block kernels (which clear the ROIs'
-// arena regions) on the same stream
+// multi-block path (self-contained: it clears its own arena regions, so it
+// runs beside the multi-block feature kernels)
 template <class T, int NDIM>
 cudaError_t launch_rz_big_one(const KParams& p, int nsm, cudaStream_t st) {
   const int sh = RZ_BIG_SH * 12;
