@@ -190,8 +190,10 @@ nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
  * int32[NYX_N_CLASSES], may be NULL); nyx_get_tuning reads the tile height
  * too.
  * d_table / cap_roi as in nyx_extract.  Synchronises.  Results do not depend
- * on these settings beyond floating-point rounding.  Errors: NYX_ERR_ARG,
- * and those of nyx_extract.
+ * on these settings beyond floating-point rounding.  Limits whose extraction
+ * ends in NYX_ERR_CAPACITY (so many ROIs routed to the multi-block class
+ * that its workspace overflows) are skipped as candidates.  Errors:
+ * NYX_ERR_ARG, and those of nyx_extract.
  * nyx_set_tuning / nyx_get_tuning: t[0..NYX_N_CLASSES) the class pixel
  * limits as above, t[NYX_N_CLASSES] the scan's rows per warp (0: chosen from
  * the tile count; else 4, 8, 16 or 32); t is host int32[NYX_N_CLASSES + 1].

@@ -1149,6 +1149,10 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
           for (int i = 0; i < N_BLOCK_CLASSES; ++i) pl->kp.lim_pix[i] = lim[i];
           float ms = 0;
           s = time_config(pl, d_img, d_mask, d_table, cap_roi, reps, st, flush, flush_bytes, e0, e1, &ms);
+          if (s == NYX_ERR_CAPACITY) {  // these limits overflow the multi-block arena: not a candidate
+            s = NYX_OK;
+            continue;
+          }
           if (s != NYX_OK) break;
           if (ms < best_ms) {
             best_ms = ms;
