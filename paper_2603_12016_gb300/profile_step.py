@@ -14,7 +14,7 @@ elsewhere.
 
     python -m paper_2603_12016_gb300.profile_step nuclei2d --subsets
 
-instead profiles one extraction of the 2048² nuclei workload per feature
+instead profiles one extraction of the named workload per feature
 subset (MEAN alone, then MEAN plus one feature family), with the class
 limits of the hot-path set; the differences of the per-kernel instruction
 counts attribute the fused kernel's work to the families.
@@ -73,7 +73,8 @@ def main(argv=None) -> int:
         img, mask = torch.from_numpy(w.image).cuda(), torch.from_numpy(w.mask).cuda()
         sig = tuning.signature(w.image.shape, str(w.image.dtype), w.ndim, prm["glcm_levels"], prm["dists"], "core")
         for name, f in SUBSETS:
-            ex = nyx.Extractor(w.image.shape, torch.uint16, ndim=w.ndim, glcm_levels=prm["glcm_levels"],
+            tdt = {np.uint16: torch.uint16, np.int16: torch.int16, np.float32: torch.float32}[w.image.dtype.type]
+            ex = nyx.Extractor(w.image.shape, tdt, ndim=w.ndim, glcm_levels=prm["glcm_levels"],
                                dists=prm["dists"], hist_bins=prm["hist_bins"], max_rois=8192,
                                features=nyx.CORE_FEATURE_IDS if f == "core" else f)
             t, _ = tuning.limits_for(ex, dev, sig)
