@@ -131,7 +131,7 @@ class ClockSampler:
 TRAFFIC_SRC = "8c44d8939d686254"
 TRAFFIC = {
     ("nuclei2d_2048_u16_4000roi", "roi_stage", (256, 1024, 4096, 0, 8), "core"): 36.25e6,
-    ("ct3d_512x512x128_i16_200roi", "roi_stage", (64, 1024, 2048, 8192, 16), "all"): 2720.28e6 + 12 * 512 * 512 * 128,
+    ("ct3d_512x512x128_i16_200roi", "roi_stage", (64, 1024, 2048, 8192, 16), "all"): 3612.29e6 + 12 * 512 * 512 * 128,
     ("blobbatch_64x512_f32", "roi_stage", (0, 1024, 4096, 8192, 16), "all"): 108.20e6,
     ("mosaic_32768_u16_500000roi", "roi_stage", (0, 512, 4096, 8192, 32), "all"): 1336.67e6 * 565.05 / 36.02
     + 12 * 32768 * 32768,
