@@ -350,8 +350,8 @@ def run_scalability_sweep(args) -> int:
 
 
 def run_family_sweep(args) -> int:
-    """Device ms of one extraction of the workload with the NGTDM and GLDM
-    families removed from the full feature set and alone."""
+    """Device ms of one extraction of the workload with the NGTDM, GLDM,
+    GLRLM and GLSZM families removed from the full feature set and alone."""
     import torch
 
     from paper_2603_12016_gb300 import scalability as S
@@ -607,8 +607,8 @@ def main() -> int:
                     help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
                          "separability grid on labelled texture classes; scalability: time over ROI size x ROI "
                          "count (GPU device, GPU end to end, CPU oracle) and the feature-group cost of an image "
-                         "of 100 ROIs of 100,000 px; families: the workload with the NGTDM and GLDM removed "
-                         "and alone (one JSON line each, not bench lines)")
+                         "of 100 ROIs of 100,000 px; families: the workload with the NGTDM, GLDM, GLRLM and "
+                         "GLSZM families removed and alone (one JSON line each, not bench lines)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -19,9 +19,14 @@ GLCM = ["GLCM_" + f for f in ("ASM", "ACOR", "CLUPROM", "CLUSHADE", "CLUTEND", "
 NGTDM = ["NGTDM_" + f for f in ("COARSENESS", "CONTRAST", "BUSYNESS", "COMPLEXITY", "STRENGTH")]
 GLDM = ["GLDM_" + f for f in ("SDE", "LDE", "GLN", "DN", "DNN", "GLV", "DV", "DE", "LGLE", "HGLE", "SDLGLE", "SDHGLE",
                               "LDLGLE", "LDHGLE")]
+GLRLM = ["GLRLM_" + f for f in ("SRE", "LRE", "GLNU", "GLNUN", "RLNU", "RLNUN", "RP", "GLV", "RV", "RE", "LGLRE",
+                                "HGLRE", "SRLGLE", "SRHGLE", "LRLGLE", "LRHGLE")]
+GLSZM = ["GLSZM_" + f for f in ("SAE", "LAE", "GLNU", "GLNUN", "SZNU", "SZNUN", "ZP", "GLV", "ZV", "ZE", "LGLZE",
+                                "HGLZE", "SALGLE", "SAHGLE", "LALGLE", "LAHGLE", "GLM", "ZSM")]
 
 # broad feature groups of the library (Table S1/S5 intensity, Table S2
-# moments, Table S3 texture: GLCM, NGTDM and GLDM); together every feature
+# moments, Table S3 texture: GLCM, NGTDM, GLDM, GLRLM and GLSZM); together
+# every feature
 GROUPS = {
     "intensity": ["MEAN", "MIN", "MAX", "RANGE", "VARIANCE", "VARIANCE_BIASED", "STDDEV", "STDDEV_BIASED", "SKEWNESS",
                   "KURTOSIS", "EXCESS_KURTOSIS", "HYPERSKEWNESS", "HYPERFLATNESS", "ENERGY", "ROOT_MEAN_SQUARED",
@@ -32,7 +37,7 @@ GROUPS = {
                   "MODE_PROBABILITY", "ENTROPY", "UNIFORMITY", "EDGE_INTEGRATED_INTENSITY", "EDGE_MAX_INTENSITY",
                   "EDGE_MIN_INTENSITY", "EDGE_MEAN_INTENSITY", "EDGE_STDDEV_INTENSITY"],
     "moments": ["INT_M", "INT_MU", "INT_ETA", "INT_NU", "INT_HU", "BIN_M", "BIN_MU", "BIN_ETA", "BIN_NU", "BIN_HU"],
-    "texture": GLCM + NGTDM + GLDM,
+    "texture": GLCM + NGTDM + GLDM + GLRLM + GLSZM,
 }
 
 
@@ -109,12 +114,14 @@ def time_end_to_end(w, steps: int = 5, warmup: int = 2) -> Dict:
 
 
 def family_costs(w, steps: int = 40) -> Dict[str, float]:
-    """Device ms with the NGTDM and GLDM families removed from the full set
-    and alone, which separates a family's own cost from its effect on the
-    rest of the step."""
+    """Device ms with the NGTDM, GLDM, GLRLM and GLSZM families removed from
+    the full set and alone, which separates a family's own cost from its
+    effect on the rest of the step."""
     base = GROUPS["intensity"] + GROUPS["moments"] + GLCM
-    cases = {"all": None, "all_but_gldm": base + NGTDM, "all_but_gldm_ngtdm": base, "gldm_only": GLDM,
-             "ngtdm_only": NGTDM, "ngtdm_gldm": NGTDM + GLDM, "intensity_only": GROUPS["intensity"]}
+    cases = {"all": None, "all_but_glrlm_glszm": base + NGTDM + GLDM, "all_but_gldm": base + NGTDM + GLRLM + GLSZM,
+             "all_but_four": base, "gldm_only": GLDM, "ngtdm_only": NGTDM, "ngtdm_gldm": NGTDM + GLDM,
+             "glrlm_only": GLRLM, "glszm_only": GLSZM, "glrlm_glszm": GLRLM + GLSZM,
+             "intensity_only": GROUPS["intensity"]}
     return {k: time_device(w, v, steps=steps) for k, v in cases.items()}
 
 

@@ -33,10 +33,9 @@ def test_timing_helpers_and_groups():
     assert 0 < dev and e2e["h2d_bytes"] == w.image.nbytes + w.mask.nbytes
     g = S.group_costs(w, steps=5)
     assert set(g) == {"intensity", "moments", "texture", "all"} and all(v > 0 for v in g.values())
-    # every group alone costs no more than the whole feature set (timing
+    # every group alone costs no more than the whole feature set (10% timing
     # slack; the texture group is most of the set on ROIs this large)
-    assert max(g["intensity"], g["moments"]) <= 1.1 * g["all"]
-    assert g["texture"] <= 1.25 * g["all"]
+    assert max(g["intensity"], g["moments"], g["texture"]) <= 1.1 * g["all"]
 
 
 def test_groups_cover_every_feature_once():
@@ -50,5 +49,6 @@ def test_groups_cover_every_feature_once():
 
     ids = [nyx.feature_id(n) for g in S.GROUPS.values() for n in g]
     assert min(ids) >= 0
-    assert sorted(ids) == list(range(len(ids)))
-    assert set(S.NGTDM + S.GLDM) <= set(S.GROUPS["texture"])
+    # the registry holds ids 0..138; the last one is the final GLSZM feature
+    assert sorted(ids) == list(range(139)) and nyx.feature_id("GLSZM_ZSM") == 138
+    assert set(S.NGTDM + S.GLDM + S.GLRLM + S.GLSZM) <= set(S.GROUPS["texture"])
