@@ -423,7 +423,7 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     dev_name = torch.cuda.get_device_name(dev)
     if args.class_limits:
         limits = tuple(int(v) for v in args.class_limits.split(","))
-        limits, lim_src = (limits + (0,))[:5], "command line"
+        limits, lim_src = (limits + (0, 0))[:6], "command line"
         ex.set_tuning(*limits)
     else:
         limits, lim_src = tuning.limits_for(ex, dev_name, sig)
@@ -487,7 +487,8 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     res = {"workload": w.name, "features": features, "n_roi": n_roi, "n_col": n_col,
            "value": n_total / (t_step * 1e-3), "unit": "ROIs/s", "ms_per_step": t_step,
            "step": "forward + backward" if bwd else "forward",
-           "class_limits_px": list(limits[:4]), "scan_rows_per_warp": limits[4], "class_limits_source": lim_src,
+           "class_limits_px": list(limits[:4]), "scan_rows_per_warp": limits[4], "scan_staging": limits[5],
+           "class_limits_source": lim_src,
            "mpix_per_s": w.image.size * (dist.get_world_size() if dist else 1) / (t_step * 1e-3) / 1e6,
            "phases_ms": {k: round(v, 5) for k, v in phases.items()}}
     if light:
@@ -517,7 +518,8 @@ def run_config(name, w, dev, dist, args, features, clk, light=False, flush=None)
     src = kernel_source_hash()
     tr = TRAFFIC.get((w.name, dom, tuple(limits), features)) if TRAFFIC_SRC == src else None
     kern = {"roi_stage": "per-ROI stage: k_roi warp/small/medium classes + multi-block kernels, concurrent",
-            "scan": "k_scan (label scan)", "backward": "k_bwd_coef + k_bwd_pixel",
+            "scan": "k_scan_tma (label scan, bulk-copy staged; k_scan where the row pitch rules it out)",
+            "backward": "k_bwd_coef + k_bwd_pixel",
             "glcm_final": "k_glcm_final", "stats_final": "k_stats_final"}[dom]
     res["roofline"] = {"bound": "hbm", "kernel": kern, "phase": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                        "frac": dom_gbs / peak, "traffic": tr, "peak_kind": peak_kind,
@@ -602,7 +604,8 @@ def main() -> int:
                     help="time forward + backward (default for the blobbatch workloads)")
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--class-limits", default=None,
-                    help="warp,small,medium,large pixel limits[,scan rows per warp] instead of the tuned ones")
+                    help="warp,small,medium,large pixel limits[,scan rows per warp[,scan staging 0 TMA / 1 "
+                         "register loads]] instead of the tuned ones")
     ap.add_argument("--sweep", default=None, choices=["soft", "scalability", "families"],
                     help="soft: the GLCM timing grid of Eqs. 2-5 on the 2048^2 nuclei workload and the Eq. 8 "
                          "separability grid on labelled texture classes; scalability: time over ROI size x ROI "
@@ -675,6 +678,8 @@ def main() -> int:
                                "moments + Hu (intensity and binary), GLCM (30 features, direction means)",
                    "step": head["step"], "l2": head["l2"], "class_limits_px": head["class_limits_px"],
                    "scan_rows_per_warp": head["scan_rows_per_warp"],
+                   "scan_staging": ["bulk tensor copies (TMA) where the row pitch allows",
+                                    "register loads"][head["scan_staging"]],
                    "class_limits_source": head["class_limits_source"],
                    "timing": "median of per-step CUDA-event times, CUDA-graph replay",
                    "parallelism": f"replicas{world}"},

@@ -143,7 +143,13 @@ int nyx_feature_id(const char* name);
  * (image, label > 0) pairs) in *n_roi.  Synchronises `stream` (reads 8 bytes
  * back).  d_img: dims x batch pixels of params.dtype; d_mask: int32, same
  * shape; both 16-byte aligned.  Errors: NYX_ERR_ARG, NYX_ERR_BAD_LABEL,
- * NYX_ERR_CAPACITY (more than max_rois), NYX_ERR_CUDA. */
+ * NYX_ERR_CAPACITY (more than max_rois), NYX_ERR_CUDA.
+ * Staging (this call and every extraction): by default, when both row
+ * pitches (x extent times the pixel size, and times 4 for the mask) are
+ * multiples of 16 bytes, the scan stages rows of image and mask into shared
+ * memory by 2D bulk tensor copies (TMA); otherwise, or after
+ * nyx_set_scan_staging(plan, 1), it loads them into registers.  The results
+ * are identical. */
 nyx_status nyx_count_rois(nyx_plan* plan, const void* d_img, const int32_t* d_mask, int64_t* n_roi,
                           void* stream);
 
@@ -181,9 +187,9 @@ nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
  * of these block classes (0 disables a class; each at most its capacity).
  * nyx_autotune times the extraction of (d_img, d_mask) under a grid of
  * limits (warp 0/64/128/256, small 0/512/1024, medium 0/2048/4096, large
- * 0/8192), then
- * under the label scan's tile heights (8/16/32 rows per warp, tiles of 128
- * columns by 64/128/256 rows) with the best limits; each candidate is timed
+ * 0/8192), then times the label scan alone under its tile heights (8/16/32
+ * rows per warp, tiles of 128 columns by 64/128/256 rows) and both stagings
+ * of its rows (below); each candidate is timed
  * as the median of `reps` calls, every call preceded by a 256 MB write that
  * flushes the L2 cache (allocated and freed inside this call).  It keeps the
  * fastest setting in the plan and returns the limits in h_lim_pix (host
@@ -197,11 +203,16 @@ nyx_status nyx_graph_captures(const nyx_plan* plan, int64_t* n);
  * nyx_set_tuning / nyx_get_tuning: t[0..NYX_N_CLASSES) the class pixel
  * limits as above, t[NYX_N_CLASSES] the scan's rows per warp (0: chosen from
  * the tile count; else 4, 8, 16 or 32); t is host int32[NYX_N_CLASSES + 1].
- * Errors: NYX_ERR_ARG. */
+ * nyx_set_scan_staging / nyx_get_scan_staging: how the label scan reads its
+ * rows, 0 = bulk tensor copies into shared memory where the row pitch
+ * allows (the default), 1 = register loads; the autotuner times both with
+ * each tile height.  Errors: NYX_ERR_ARG. */
 #define NYX_N_CLASSES 4
 nyx_status nyx_set_class_limits(nyx_plan* plan, const int32_t* lim_pix);
 nyx_status nyx_set_tuning(nyx_plan* plan, const int32_t* t);
 nyx_status nyx_get_tuning(const nyx_plan* plan, int32_t* t);
+nyx_status nyx_set_scan_staging(nyx_plan* plan, int mode);
+nyx_status nyx_get_scan_staging(const nyx_plan* plan, int* mode);
 nyx_status nyx_autotune(nyx_plan* plan, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                         int reps, void* stream, int32_t* h_lim_pix);
 

@@ -1104,6 +1104,41 @@ static nyx_status time_config(nyx_plan* pl, const void* d_img, const int32_t* d_
   return NYX_OK;
 }
 
+// Median device time of the label scan alone (counter reset + scan), each
+// call after the same L2 flush; its label table is reset outside the timed
+// region.
+static nyx_status time_scan(nyx_plan* pl, const void* d_img, const int32_t* d_mask, int reps, cudaStream_t st,
+                            void* flush, size_t flush_bytes, cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+  nyx_ctx* c = pl->ctx;
+  nyx_status s;
+  if ((s = flush_live(pl, st)) != NYX_OK) return s;
+  KParams k = pl->kp;
+  k.img = d_img;
+  k.mask = d_mask;
+  k.vec = (k.nx % 4) == 0;
+  if ((s = run_front(pl, k, st)) != NYX_OK) return s;  // warm-up
+  if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
+  float t[100];
+  for (int r = 0; r < reps; ++r) {
+    if (flush) NYX_CUDA(c, cudaMemsetAsync(flush, r & 0xFF, flush_bytes, st));
+    NYX_CUDA(c, cudaEventRecord(e0, st));
+    if ((s = run_front(pl, k, st)) != NYX_OK) return s;
+    NYX_CUDA(c, cudaEventRecord(e1, st));
+    NYX_CUDA(c, cudaEventSynchronize(e1));
+    NYX_CUDA(c, cudaEventElapsedTime(&t[r], e0, e1));
+    if ((s = run_reset(pl, k, st)) != NYX_OK) return s;
+  }
+  if ((s = read_err(pl, st)) != NYX_OK) return s;
+  for (int i = 1; i < reps; ++i)
+    for (int j = i; j > 0 && t[j] < t[j - 1]; --j) {
+      const float x = t[j];
+      t[j] = t[j - 1];
+      t[j - 1] = x;
+    }
+  *ms_out = t[reps / 2];
+  return NYX_OK;
+}
+
 nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, double* d_table, int64_t cap_roi,
                         int reps, void* stream, int32_t* h_lim_pix) {
   if (!pl || reps < 1 || reps > 100) return NYX_ERR_ARG;
@@ -1114,14 +1149,15 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   NYX_CUDA(c, cudaSetDevice(c->device));
   // candidate pixel thresholds of the warp, small, medium and large classes
   // (0 = class unused; the cell limits stay at each class's staging
-  // capacity), then the label scan's rows per warp (tile heights 64/128/256)
+  // capacity), then, timing the label scan alone, its rows per warp (tile
+  // heights 64/128/256) under either staging of its rows
   static const int cw[] = {0, 64, 128, 256}, cs[] = {0, 512, 1024}, cm[] = {0, 2048, 4096}, cl[] = {0, 8192},
                    cr[] = {8, 16, 32};
   const int saved_prof = pl->prof_slots;
   pl->prof_slots = 0;
   int best[N_BLOCK_CLASSES];
   for (int i = 0; i < N_BLOCK_CLASSES; ++i) best[i] = pl->kp.lim_pix[i];
-  int best_rpt = pl->kp.scan_rpt;
+  int best_rpt = pl->kp.scan_rpt, best_stage = pl->kp.scan_stage;
   float best_ms = 3.0e38f;
   // an L2-sized write between timed calls, so that every candidate starts
   // from cold caches as a new image would (an offline call: it may allocate)
@@ -1162,18 +1198,22 @@ nyx_status nyx_autotune(nyx_plan* pl, const void* d_img, const int32_t* d_mask, 
   for (int i = 0; i < N_BLOCK_CLASSES; ++i) pl->kp.lim_pix[i] = best[i];
   if (s == NYX_OK) {
     best_ms = 3.0e38f;
-    for (int r : cr) {
-      pl->kp.scan_rpt = r;
-      float ms = 0;
-      s = time_config(pl, d_img, d_mask, d_table, cap_roi, reps, st, flush, flush_bytes, e0, e1, &ms);
-      if (s != NYX_OK) break;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_rpt = r;
+    for (int g = 0; g < 2 && s == NYX_OK; ++g)  // bulk tensor copies (where legal), then register loads
+      for (int r : cr) {
+        pl->kp.scan_rpt = r;
+        pl->kp.scan_stage = g;
+        float ms = 0;
+        s = time_scan(pl, d_img, d_mask, reps, st, flush, flush_bytes, e0, e1, &ms);
+        if (s != NYX_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_rpt = r;
+          best_stage = g;
+        }
       }
-    }
   }
   pl->kp.scan_rpt = best_rpt;
+  pl->kp.scan_stage = best_stage;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (flush) cudaFree(flush);
@@ -1201,6 +1241,20 @@ nyx_status nyx_get_tuning(const nyx_plan* pl, int32_t* t) {
   if (!pl || !t) return NYX_ERR_ARG;
   for (int i = 0; i < N_BLOCK_CLASSES; ++i) t[i] = pl->kp.lim_pix[i];
   t[N_BLOCK_CLASSES] = pl->kp.scan_rpt;
+  return NYX_OK;
+}
+
+nyx_status nyx_set_scan_staging(nyx_plan* pl, int mode) {
+  if (!pl) return NYX_ERR_ARG;
+  if (mode != 0 && mode != 1) return fail(pl->ctx, NYX_ERR_ARG, "scan staging must be 0 or 1");
+  pl->kp.scan_stage = mode;
+  drop_graph(pl);
+  return NYX_OK;
+}
+
+nyx_status nyx_get_scan_staging(const nyx_plan* pl, int* mode) {
+  if (!pl || !mode) return NYX_ERR_ARG;
+  *mode = pl->kp.scan_stage;
   return NYX_OK;
 }
 

@@ -235,6 +235,7 @@ struct KParams {
   // all rows); the mosaic path scans each band of tiles as it arrives
   int64_t scan_row0, scan_row1;
   int scan_rpt;                    // label-scan rows per warp (tile height / 8); 0: chosen by tile count
+  int scan_stage;                  // label-scan staging: 0 bulk tensor copies where legal, 1 register loads
   unsigned long long* sort_tmp;    // key buffer of the key sorts [max_rois]
   // GLRLM / GLSZM: work counters of the two block tiers; zone parents and
   // areas of the multi-block ROIs, one word per image pixel (GLSZM only)

@@ -575,11 +575,10 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
   // (a set has at most HC / 2 distinct keys, the hashes' load bound)
   unsigned* lst = (unsigned*)par;
   static_assert(2 * Z::CELLS >= 8 * (Z::HC / 2), "HC / 2 compacted cells fit in the parent array");
-  __shared__ unsigned s_nl;
+  __shared__ unsigned s_nl;  // list length; 0 whenever a set starts (reset once every thread has read it)
+  if (tid == 0) s_nl = 0;
   int hc = Z::HC;  // hash slots this ROI uses (set per ROI)
   auto joint = [&](auto f) {
-    if (tid == 0) s_nl = 0;
-    __syncthreads();
     const int lane = tid & 31;
     for (int h0 = 0; h0 < hc; h0 += Z::NT) {
       const int h = h0 + tid;
@@ -682,6 +681,7 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
       rz_u64 ent;
       rz_joint_pass(joint, p, lvl_n, lvl_a, hs_key, hs_cnt, Z::HS, jv, ent);
       __syncthreads();
+      if (tid == 0) s_nl = 0;  // every thread has read the list length
       rz_marg_pass<Z::NT>(p, lvl_n, lvl_a, hs_key, hs_cnt, Z::HS, jv, ent, red[set]);
     };
     if (do_rl) {
@@ -725,11 +725,13 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
           atomicAdd(zw + (rt >> 1), 1u << (16 * (rt & 1)));  // areas <= 8,192: no carry between halves
         }
       __syncthreads();
-      for (int c = tid; c < cells; c += Z::NT)  // mark the roots (levels take 9 bits)
-        if (rast[c] && par[c] == c) rast[c] |= 0x8000;
-      __syncthreads();
-      for (int c = tid; c < cells; c += Z::NT)  // each root's area, parked in its parent slot
-        if (rast[c] & 0x8000) par[c] = (uint16_t)((zw[c >> 1] >> (16 * (c & 1))) & 0xFFFFu);
+      // mark the roots (levels take 9 bits) and park each root's area in its
+      // parent slot (only a cell's own thread reads or writes its slot here)
+      for (int c = tid; c < cells; c += Z::NT)
+        if (rast[c] && par[c] == c) {
+          rast[c] |= 0x8000;
+          par[c] = (uint16_t)((zw[c >> 1] >> (16 * (c & 1))) & 0xFFFFu);
+        }
       __syncthreads();
       for (int i = tid; i < Z::HC; i += Z::NT) {
         hkey[i] = 0;

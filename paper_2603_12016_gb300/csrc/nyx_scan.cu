@@ -13,6 +13,9 @@
 //   warp    : lanes holding the same label merge with match/reduce intrinsics
 //   block   : a shared-memory hash table per 32 x 128 tile
 //   global  : one insert + field atomics per (tile, label)
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdio>
 #include <cstring>
 
@@ -235,6 +238,304 @@ template <> __device__ inline bool nonfinite_raw<float>(const uint4& v) {
   return ((v.x & E) == E) | ((v.y & E) == E) | ((v.z & E) == E) | ((v.w & E) == E);
 }
 
+// What a lane carries from row to row: its two open labels, the current
+// image's intensity range and the error bits.
+struct ScanLane {
+  Slot A, B;
+  unsigned im_mn, im_mx;
+  int64_t im_b;
+  unsigned errbits;
+};
+
+// One row of a lane's 4-column strip (mask words mc, image word vc, nvalid
+// of the 4 columns inside the image) at plane position (y, z, b); next_row:
+// this is not the warp's first row of the tile, so y advances first (and a
+// finished plane is flushed).  Called by the whole warp.
+template <class T>
+__device__ __forceinline__ void scan_row(const KParams& p, unsigned long long* s_key, SlotAcc* s_acc, ScanLane& S,
+                                         const int4 mc, const typename Vec4<T>::V vc, int nvalid, int xs, int lane,
+                                         bool next_row, int& y, int& z, int64_t& b) {
+  if (next_row && ++y == p.ny) {  // warp-uniform: a new plane (or image) starts
+    slot_flush_warp(p, s_key, s_acc, S.A, xs, z, b, S.errbits);
+    slot_flush_warp(p, s_key, s_acc, S.B, xs, z, b, S.errbits);
+    y = 0;
+    if (++z == p.nz) {
+      z = 0;
+      ++b;
+    }
+  }
+  if (b != S.im_b) {  // warp-uniform: close the previous image's range
+    unsigned mn = __reduce_min_sync(0xFFFFFFFFu, S.im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, S.im_mx);
+    if (lane == 0 && S.im_b >= 0) {
+      atomicMin(&p.img_vmin[S.im_b], mn);
+      atomicMax(&p.img_vmax[S.im_b], mx);
+    }
+    S.im_b = b;
+    S.im_mn = 0xFFFFFFFFu;
+    S.im_mx = 0;
+  }
+  int L[4] = {mc.x, mc.y, mc.z, mc.w};
+  unsigned ev[4];
+  unpack4<T>(vc, ev);
+  bool uni;
+  unsigned rmn, rmx;
+  if (nvalid == 4) {
+    rmn = min(min(ev[0], ev[1]), min(ev[2], ev[3]));
+    rmx = max(max(ev[0], ev[1]), max(ev[2], ev[3]));
+    uni = (L[0] == L[1]) & (L[1] == L[2]) & (L[2] == L[3]);
+  } else {  // right edge of the image: pixels past it are background
+    rmn = 0xFFFFFFFFu;
+    rmx = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j < nvalid) {
+        rmn = min(rmn, ev[j]);
+        rmx = max(rmx, ev[j]);
+      } else {
+        L[j] = 0;
+      }
+    }
+    uni = false;
+  }
+  S.im_mn = min(S.im_mn, rmn);
+  S.im_mx = max(S.im_mx, rmx);
+  if ((L[0] | L[1] | L[2] | L[3]) < 0) S.errbits |= E_BAD_LABEL;
+  if (nonfinite_raw<T>(vc)) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (L[j] > 0 && !finite_enc<T>(ev[j])) S.errbits |= E_NONFINITE;
+  }
+  if (uni && L[0] <= 0) return;  // background row segment
+  if (uni && L[0] == S.A.lab) {
+    S.A.cnt += 4;
+    S.A.xb = 0xFu;
+    S.A.vmn = min(S.A.vmn, rmn);
+    S.A.vmx = max(S.A.vmx, rmx);
+    S.A.ymx = y;
+    return;
+  }
+  if (uni && L[0] == S.B.lab) {
+    S.B.cnt += 4;
+    S.B.xb = 0xFu;
+    S.B.vmn = min(S.B.vmn, rmn);
+    S.B.vmx = max(S.B.vmx, rmx);
+    S.B.ymx = y;
+    return;
+  }
+  unsigned mA = 0, mB = 0, mo = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (L[j] > 0) {
+      if (L[j] == S.A.lab) mA |= 1u << j;
+      else if (L[j] == S.B.lab) mB |= 1u << j;
+      else mo |= 1u << j;
+    }
+  while (mo) {  // a label in neither slot: give it a slot
+    const int j = __ffs(mo) - 1;
+    const int nl = j == 0 ? L[0] : j == 1 ? L[1] : j == 2 ? L[2] : L[3];
+    // an empty slot, else one without pixels on this row, else B; the
+    // displaced label keeps the pixels it has on this row
+    const bool useA = S.A.lab == 0 || (S.B.lab != 0 && mA == 0);
+    if (useA) {
+      if (S.A.lab > 0) {
+        slot_add(S.A, mA, ev, y);
+        slot_insert(p, s_key, s_acc, S.A, xs, z, b, S.errbits);
+      }
+      slot_open(S.A, nl, y);
+    } else {
+      if (S.B.lab > 0) {
+        slot_add(S.B, mB, ev, y);
+        slot_insert(p, s_key, s_acc, S.B, xs, z, b, S.errbits);
+      }
+      slot_open(S.B, nl, y);
+    }
+    unsigned mn = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if ((mo >> q & 1) && L[q] == nl) mn |= 1u << q;
+    mo &= ~mn;
+    if (useA) mA = mn;
+    else mB = mn;
+  }
+  slot_add(S.A, mA, ev, y);
+  slot_add(S.B, mB, ev, y);
+}
+
+// Tile geometry of warp `warp` in tile t: first column of the lane's strip,
+// columns of it inside the image, first row and rows (0 past the scan range).
+struct ScanTile {
+  int64_t xs64, rw0;
+  int xs, nvalid, nr;
+};
+// a / d and its remainder, by 32-bit division when both operands fit
+__device__ inline int64_t div_rem(int64_t a, int64_t d, int64_t& r) {
+  if (((a | d) >> 31) == 0) {
+    const unsigned q = (unsigned)a / (unsigned)d;
+    r = a - (int64_t)q * d;
+    return q;
+  }
+  const int64_t q = a / d;
+  r = a - q * d;
+  return q;
+}
+
+__device__ inline ScanTile scan_tile(const KParams& p, int64_t t, int64_t ntx, int64_t r0, int64_t r1, int rpt,
+                                     int warp, int lane) {
+  ScanTile g;
+  int64_t tx;
+  const int64_t ty = div_rem(t, ntx, tx);
+  g.xs64 = tx * TX + 4 * lane;
+  g.xs = (int)g.xs64;
+  g.nvalid = (int)max((int64_t)0, min((int64_t)4, p.nx - g.xs64));
+  g.rw0 = r0 + ty * (8ll * rpt) + (int64_t)warp * rpt;
+  g.nr = (int)max((int64_t)0, min((int64_t)rpt, r1 - g.rw0));
+  return g;
+}
+
+__device__ inline void scan_lane_init(ScanLane& S) {
+  S.im_mn = 0xFFFFFFFFu;
+  S.im_mx = 0;
+  S.im_b = -1;
+  S.errbits = 0;
+  S.A.lab = S.B.lab = 0;
+}
+
+// End of a tile: the warp's open labels into the tile table, then the whole
+// block moves the tile table into the global label table.
+__device__ inline void scan_tile_end(const KParams& p, unsigned long long* s_key, SlotAcc* s_acc, ScanLane& S,
+                                     int xs, int z, int64_t b) {
+  slot_flush_warp(p, s_key, s_acc, S.A, xs, z, b, S.errbits);
+  slot_flush_warp(p, s_key, s_acc, S.B, xs, z, b, S.errbits);
+  __syncthreads();
+  for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
+    unsigned long long k = s_key[i];
+    if (k == EMPTY_KEY) continue;
+    int g = g_find_insert(p, k);
+    if (g >= 0) acc_merge_acc(&p.slots[g], s_acc[i]);
+    else S.errbits |= E_HASH_FULL;
+    s_key[i] = EMPTY_KEY;
+    acc_identity(s_acc[i]);
+  }
+  __syncthreads();
+}
+
+// The warps' last image ranges and error bits out to global memory: the
+// block merges its warps' ranges first, one update per distinct image (a
+// warp-per-update scheme sends thousands of updates to the same address).
+// Called by the whole block.
+__device__ inline void scan_finish(const KParams& p, ScanLane& S, int lane) {
+  constexpr int NW = SCAN_NT / 32;
+  __shared__ long long s_fb[NW];
+  __shared__ unsigned s_fmn[NW], s_fmx[NW];
+  const int warp = threadIdx.x >> 5;
+  const unsigned mn = __reduce_min_sync(0xFFFFFFFFu, S.im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, S.im_mx);
+  const bool any = __any_sync(0xFFFFFFFFu, S.im_b >= 0);
+  const long long bb = __reduce_max_sync(0xFFFFFFFFu, (unsigned)(S.im_b + 1)) - 1;  // warp-uniform image index
+  if (lane == 0) {
+    s_fb[warp] = any ? bb : -1;
+    s_fmn[warp] = mn;
+    s_fmx[warp] = mx;
+  }
+  const unsigned e = __reduce_or_sync(0xFFFFFFFFu, S.errbits);
+  if (lane == 0 && e) atomicOr(p.err, e);
+  __syncthreads();
+  if (threadIdx.x < NW) {
+    const int w = threadIdx.x;
+    const long long b = s_fb[w];
+    if (b >= 0) {
+      bool first = true;
+      unsigned m0 = 0xFFFFFFFFu, m1 = 0;
+      for (int v = 0; v < NW; ++v)
+        if (s_fb[v] == b) {
+          first &= v >= w;
+          m0 = min(m0, s_fmn[v]);
+          m1 = max(m1, s_fmx[v]);
+        }
+      if (first) {
+        atomicMin(&p.img_vmin[b], m0);
+        atomicMax(&p.img_vmax[b], m1);
+      }
+    }
+  }
+}
+
+__device__ inline void scan_plane_pos(const KParams& p, int64_t row, int& y, int& z, int64_t& b) {
+  int64_t yr, zr;
+  const int64_t zb = div_rem(row, p.ny, yr);
+  b = div_rem(zb, p.nz, zr);
+  y = (int)yr;
+  z = (int)zr;
+}
+
+
+// ---- bulk-copy (TMA) staging of the label scan -----------------------------
+// Each warp streams its rows through a ring of TMA_NS shared-memory stages of
+// TMA_SR rows x 128 columns of mask (int32) then image; one lane issues the
+// 2D tensor copies, each stage completes on its own mbarrier.
+constexpr int TMA_SR = 2;  // rows per stage
+constexpr int TMA_NS = 3;  // stages per warp
+template <class T> constexpr int tma_stage_bytes() { return TMA_SR * TX * (4 + (int)sizeof(T)); }
+template <class T> constexpr int tma_smem_bytes() { return (SCAN_NT / 32) * TMA_NS * tma_stage_bytes<T>(); }
+// resident blocks per SM the register budget is set for: what the staging
+// ring leaves of the SM's shared memory
+template <class T> constexpr int scan_tma_minb() { return sizeof(T) == 4 ? 3 : 4; }
+
+__device__ inline unsigned smem_addr(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+
+__device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// make barrier initialisation visible to the bulk-copy (async) proxy
+__device__ inline void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ inline void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ inline bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of `parity` to complete; false after about a second
+// (the copy never landed: the caller reports E_TIMEOUT and stops).
+__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && global_ns() - t0 > 1000000000ull) return false;
+  }
+  return false;
+}
+
+// 2D tiled tensor copy global -> shared of the box at element (x, y),
+// completing `bar`'s transaction count
+__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
 }  // namespace
 
 // Each warp takes rpt consecutive rows of a 128-column tile (tile height
@@ -257,171 +558,135 @@ __global__ void __launch_bounds__(SCAN_NT, scan_minb<T>()) k_scan(KParams p, int
   __syncthreads();
   using V = typename Vec4<T>::V;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ty_rows = 8ll * rpt;
   const int64_t r0 = p.scan_row0, r1 = p.scan_row1 > 0 ? p.scan_row1 : p.rows_total;
-  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (r1 - r0 + ty_rows - 1) / ty_rows;
+  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (r1 - r0 + 8ll * rpt - 1) / (8ll * rpt);
   const int64_t ntiles = ntx * nty;
-  unsigned im_mn = 0xFFFFFFFFu, im_mx = 0;
-  int64_t im_b = -1;
-  unsigned errbits = 0;
-  Slot A, B;
-  A.lab = B.lab = 0;
+  ScanLane S;
+  scan_lane_init(S);
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t ty = t / ntx, tx = t - ty * ntx;
-    const int64_t xs64 = tx * TX + 4 * lane;
-    const int xs = (int)xs64;
-    const int nvalid = (int)max((int64_t)0, min((int64_t)4, p.nx - xs64));
-    const int64_t rw0 = r0 + ty * ty_rows + (int64_t)warp * rpt;
-    const int nr = (int)max((int64_t)0, min((int64_t)rpt, r1 - rw0));
+    const ScanTile g = scan_tile(p, t, ntx, r0, r1, rpt, warp, lane);
     int y = 0, z = 0;
     int64_t b = 0;
     int4 m0, m1;
     V v0, v1;
-    if (nr > 0) {
-      y = (int)(rw0 % p.ny);
-      const int64_t zb = rw0 / p.ny;
-      z = (int)(zb % p.nz);
-      b = zb / p.nz;
-      load_raw<T>(p, rw0 * p.nx, xs64, nvalid, m0, v0);
+    if (g.nr > 0) {
+      scan_plane_pos(p, g.rw0, y, z, b);
+      load_raw<T>(p, g.rw0 * p.nx, g.xs64, g.nvalid, m0, v0);
     }
-    if (nr > 1) load_raw<T>(p, (rw0 + 1) * p.nx, xs64, nvalid, m1, v1);
-    for (int i = 0; i < nr; ++i) {
+    if (g.nr > 1) load_raw<T>(p, (g.rw0 + 1) * p.nx, g.xs64, g.nvalid, m1, v1);
+    for (int i = 0; i < g.nr; ++i) {
       const int4 mc = m0;
       const V vc = v0;
       m0 = m1;
       v0 = v1;
-      if (i + 2 < nr) load_raw<T>(p, (rw0 + i + 2) * p.nx, xs64, nvalid, m1, v1);
-      if (i > 0 && ++y == p.ny) {  // warp-uniform: a new plane (or image) starts
-        slot_flush_warp(p, s_key, s_acc, A, xs, z, b, errbits);
-        slot_flush_warp(p, s_key, s_acc, B, xs, z, b, errbits);
-        y = 0;
-        if (++z == p.nz) {
-          z = 0;
-          ++b;
-        }
-      }
-      if (b != im_b) {  // warp-uniform: close the previous image's range
-        unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
-        if (lane == 0 && im_b >= 0) {
-          atomicMin(&p.img_vmin[im_b], mn);
-          atomicMax(&p.img_vmax[im_b], mx);
-        }
-        im_b = b;
-        im_mn = 0xFFFFFFFFu;
-        im_mx = 0;
-      }
-      int L[4] = {mc.x, mc.y, mc.z, mc.w};
-      unsigned ev[4];
-      unpack4<T>(vc, ev);
-      bool uni;
-      unsigned rmn, rmx;
-      if (nvalid == 4) {
-        rmn = min(min(ev[0], ev[1]), min(ev[2], ev[3]));
-        rmx = max(max(ev[0], ev[1]), max(ev[2], ev[3]));
-        uni = (L[0] == L[1]) & (L[1] == L[2]) & (L[2] == L[3]);
-      } else {  // right edge of the image: pixels past it are background
-        rmn = 0xFFFFFFFFu;
-        rmx = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (j < nvalid) {
-            rmn = min(rmn, ev[j]);
-            rmx = max(rmx, ev[j]);
-          } else {
-            L[j] = 0;
-          }
-        }
-        uni = false;
-      }
-      im_mn = min(im_mn, rmn);
-      im_mx = max(im_mx, rmx);
-      if ((L[0] | L[1] | L[2] | L[3]) < 0) errbits |= E_BAD_LABEL;
-      if (nonfinite_raw<T>(vc)) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (L[j] > 0 && !finite_enc<T>(ev[j])) errbits |= E_NONFINITE;
-      }
-      if (uni && L[0] <= 0) continue;  // background row segment
-      if (uni && L[0] == A.lab) {
-        A.cnt += 4;
-        A.xb = 0xFu;
-        A.vmn = min(A.vmn, rmn);
-        A.vmx = max(A.vmx, rmx);
-        A.ymx = y;
-        continue;
-      }
-      if (uni && L[0] == B.lab) {
-        B.cnt += 4;
-        B.xb = 0xFu;
-        B.vmn = min(B.vmn, rmn);
-        B.vmx = max(B.vmx, rmx);
-        B.ymx = y;
-        continue;
-      }
-      unsigned mA = 0, mB = 0, mo = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (L[j] > 0) {
-          if (L[j] == A.lab) mA |= 1u << j;
-          else if (L[j] == B.lab) mB |= 1u << j;
-          else mo |= 1u << j;
-        }
-      while (mo) {  // a label in neither slot: give it a slot
-        const int j = __ffs(mo) - 1;
-        const int nl = j == 0 ? L[0] : j == 1 ? L[1] : j == 2 ? L[2] : L[3];
-        // an empty slot, else one without pixels on this row, else B; the
-        // displaced label keeps the pixels it has on this row
-        const bool useA = A.lab == 0 || (B.lab != 0 && mA == 0);
-        if (useA) {
-          if (A.lab > 0) {
-            slot_add(A, mA, ev, y);
-            slot_insert(p, s_key, s_acc, A, xs, z, b, errbits);
-          }
-          slot_open(A, nl, y);
-        } else {
-          if (B.lab > 0) {
-            slot_add(B, mB, ev, y);
-            slot_insert(p, s_key, s_acc, B, xs, z, b, errbits);
-          }
-          slot_open(B, nl, y);
-        }
-        unsigned mn = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if ((mo >> q & 1) && L[q] == nl) mn |= 1u << q;
-        mo &= ~mn;
-        if (useA) mA = mn;
-        else mB = mn;
-      }
-      slot_add(A, mA, ev, y);
-      slot_add(B, mB, ev, y);
+      if (i + 2 < g.nr) load_raw<T>(p, (g.rw0 + i + 2) * p.nx, g.xs64, g.nvalid, m1, v1);
+      scan_row<T>(p, s_key, s_acc, S, mc, vc, g.nvalid, g.xs, lane, i > 0, y, z, b);
     }
-    slot_flush_warp(p, s_key, s_acc, A, xs, z, b, errbits);
-    slot_flush_warp(p, s_key, s_acc, B, xs, z, b, errbits);
-    __syncthreads();
-    // flush the tile table to the global label table
-    for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
-      unsigned long long k = s_key[i];
-      if (k == EMPTY_KEY) continue;
-      int g = g_find_insert(p, k);
-      if (g >= 0) acc_merge_acc(&p.slots[g], s_acc[i]);
-      else errbits |= E_HASH_FULL;
-      s_key[i] = EMPTY_KEY;
-      acc_identity(s_acc[i]);
-    }
-    __syncthreads();
+    scan_tile_end(p, s_key, s_acc, S, g.xs, z, b);
   }
-  {
-    unsigned mn = __reduce_min_sync(0xFFFFFFFFu, im_mn), mx = __reduce_max_sync(0xFFFFFFFFu, im_mx);
-    bool any = __any_sync(0xFFFFFFFFu, im_b >= 0);
-    long long bb = __reduce_max_sync(0xFFFFFFFFu, (unsigned)(im_b + 1)) - 1;  // warp-uniform image index
-    if (lane == 0 && any && bb >= 0) {
-      atomicMin(&p.img_vmin[bb], mn);
-      atomicMax(&p.img_vmax[bb], mx);
-    }
+  scan_finish(p, S, lane);
+}
+
+// The same scan with its rows staged by bulk tensor copies (TMA) instead of
+// register loads: each warp keeps TMA_NS stages of TMA_SR rows in flight
+// (lane 0 issues the copies of the warp's own row sequence, continuing into
+// its next tile), so the bytes in flight no longer cost registers; lanes read
+// their 4-pixel strip from shared memory (16 B of mask + 8 or 16 B of image,
+// consecutive across the warp).  Columns and rows past the image arrive as
+// zeros (background).  Used when both tensor maps could be encoded.
+template <class T>
+__global__ void __launch_bounds__(SCAN_NT, scan_tma_minb<T>())
+    k_scan_tma(const __grid_constant__ CUtensorMap tm_mask, const __grid_constant__ CUtensorMap tm_img, KParams p,
+               int rpt) {
+  __shared__ unsigned long long s_key[SCAP];
+  __shared__ SlotAcc s_acc[SCAP];
+  __shared__ unsigned long long s_bar[SCAN_NT / 32][TMA_NS];
+  extern __shared__ __align__(128) unsigned char st_smem[];
+  using V = typename Vec4<T>::V;
+  constexpr unsigned STAGE_B = tma_stage_bytes<T>(), MASK_B = TMA_SR * TX * 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < SCAP; i += SCAN_NT) {
+    s_key[i] = EMPTY_KEY;
+    acc_identity(s_acc[i]);
   }
-  errbits = __reduce_or_sync(0xFFFFFFFFu, errbits);
-  if (lane == 0 && errbits) atomicOr(p.err, errbits);
+  if (lane == 0) {
+    for (int q = 0; q < TMA_NS; ++q) mbar_init(&s_bar[warp][q], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int64_t r0 = p.scan_row0, r1 = p.scan_row1 > 0 ? p.scan_row1 : p.rows_total;
+  const int64_t ntx = (p.nx + TX - 1) / TX, nty = (r1 - r0 + 8ll * rpt - 1) / (8ll * rpt);
+  const int64_t ntiles = ntx * nty;
+  unsigned char* wst = st_smem + (size_t)warp * TMA_NS * STAGE_B;
+  // copy cursor (lane 0): tile and chunk of the next copy, copies issued
+  int64_t pt = blockIdx.x;
+  int pc = 0;
+  unsigned pseq = 0;
+  ScanTile pg = scan_tile(p, pt, ntx, r0, r1, rpt, warp, 0);  // of tile pt
+  auto issue = [&]() {
+    while (pt < ntiles) {
+      if (pc * TMA_SR < pg.nr) {
+        const unsigned q = pseq % TMA_NS;
+        unsigned char* dst = wst + q * STAGE_B;
+        const int x = (int)pg.xs64, y = (int)(pg.rw0 + (int64_t)pc * TMA_SR);
+        mbar_arrive_expect_tx(&s_bar[warp][q], STAGE_B);
+        tma_load_2d(dst, &tm_mask, x, y, &s_bar[warp][q]);
+        tma_load_2d(dst + MASK_B, &tm_img, x, y, &s_bar[warp][q]);
+        ++pc;
+        ++pseq;
+        return;
+      }
+      pt += gridDim.x;
+      pc = 0;
+      if (pt < ntiles) pg = scan_tile(p, pt, ntx, r0, r1, rpt, warp, 0);
+    }
+  };
+  if (lane == 0)
+    for (int q = 0; q < TMA_NS; ++q) issue();
+  unsigned cseq = 0;     // chunk being read
+  unsigned dead_at = 0;  // first chunk not waited for, once a wait ran out
+  bool dead = false;     // warp-uniform
+  ScanLane S;
+  scan_lane_init(S);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const ScanTile g = scan_tile(p, t, ntx, r0, r1, rpt, warp, lane);
+    int y = 0, z = 0;
+    int64_t b = 0;
+    if (g.nr > 0) scan_plane_pos(p, g.rw0, y, z, b);
+    for (int i = 0; i < g.nr; ++i) {
+      const int sub = i % TMA_SR;
+      if (sub == 0) {
+        if (i > 0) {  // the previous chunk is read: its stage takes the next copy
+          __syncwarp();
+          if (lane == 0 && !dead) issue();
+          ++cseq;
+        }
+        if (!dead) {
+          const bool ok = mbar_wait(&s_bar[warp][cseq % TMA_NS], (cseq / TMA_NS) & 1u);
+          dead = !__all_sync(0xFFFFFFFFu, ok);
+          if (dead) {
+            dead_at = cseq;
+            S.errbits |= E_TIMEOUT;
+          }
+        }
+      }
+      if (dead) continue;
+      const unsigned char* st = wst + (cseq % TMA_NS) * STAGE_B;
+      const int4 mc = *(const int4*)(st + 4 * (sub * TX + 4 * lane));
+      const V vc = *(const V*)(st + MASK_B + sizeof(T) * (sub * TX + 4 * lane));
+      scan_row<T>(p, s_key, s_acc, S, mc, vc, g.nvalid, g.xs, lane, i > 0, y, z, b);
+    }
+    if (g.nr > 0) {
+      __syncwarp();
+      if (lane == 0 && !dead) issue();
+      ++cseq;
+    }
+    scan_tile_end(p, s_key, s_acc, S, g.xs, z, b);
+  }
+  // a warp that gave up still lets its copies in flight land (bounded)
+  if (dead && lane == 0)
+    for (unsigned q = dead_at; q < pseq; ++q) mbar_wait(&s_bar[warp][q % TMA_NS], (q / TMA_NS) & 1u);
+  scan_finish(p, S, lane);
 }
 
 // Sort the distinct keys ascending (one block): dense ROI id = rank of its
@@ -819,14 +1084,53 @@ __global__ void k_begin(KParams p) {
   }
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime (the library
+// links no libcuda); null when the driver does not offer it
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+static EncodeTiledFn tma_encoder() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (EncodeTiledFn)f;
+  }();
+  return fn;
+}
+
+// Tensor maps of mask (int32) and image (raw 16- or 32-bit words) as 2D
+// arrays of rows_total rows x nx columns, box 128 columns x TMA_SR rows.
+// False (register-load scan) when the plan asks for register loads, or
+// unless both row pitches are multiples of 16 bytes, both bases 16-byte
+// aligned and the row count fits 32 bits.
 template <class T>
-static cudaError_t launch_scan_t(const KParams& p, int nsm, cudaStream_t st) {
-  int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<T>, SCAN_NT, 0);
-  if (e != cudaSuccess) return e;
-  const int64_t grid = (int64_t)(nb > 0 ? nb : 1) * nsm;
-  // rows per warp and tile: the tallest tile that still gives every block
-  // two tiles (taller tiles spread the per-tile table flush over more rows)
+static bool scan_tensor_maps(const KParams& p, CUtensorMap& tm_mask, CUtensorMap& tm_img) {
+  const int64_t es = (int64_t)sizeof(T);
+  if (p.scan_stage != 0) return false;
+  if (p.nx <= 0 || p.rows_total <= 0 || p.nx % 4 || (p.nx * es) % 16 || p.nx > INT32_MAX || p.rows_total > INT32_MAX)
+    return false;
+  if ((((uintptr_t)p.mask) | ((uintptr_t)p.img)) & 15u) return false;
+  const EncodeTiledFn enc = tma_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.rows_total};
+  const cuuint64_t pitch_m[1] = {(cuuint64_t)p.nx * 4u}, pitch_i[1] = {(cuuint64_t)(p.nx * es)};
+  const cuuint32_t box[2] = {(cuuint32_t)TX, (cuuint32_t)TMA_SR}, estr[2] = {1u, 1u};
+  if (enc(&tm_mask, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, (void*)p.mask, dims, pitch_m, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  return enc(&tm_img, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void*)p.img,
+             dims, pitch_i, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// rows per warp and tile: the tallest tile that still gives every block
+// two tiles (taller tiles spread the per-tile table flush over more rows),
+// unless a tuned tile height is set
+static int scan_rows_per_warp(const KParams& p, int64_t grid) {
   const int64_t rows = (p.scan_row1 > 0 ? p.scan_row1 : p.rows_total) - p.scan_row0;
   const int64_t ntx = (p.nx + TX - 1) / TX;
   int rpt = SCAN_RPT / 4;
@@ -835,8 +1139,28 @@ static cudaError_t launch_scan_t(const KParams& p, int nsm, cudaStream_t st) {
       rpt = c;
       break;
     }
-  if (p.scan_rpt > 0) rpt = p.scan_rpt < SCAN_RPT ? p.scan_rpt : SCAN_RPT;  // a tuned tile height
-  k_scan<T><<<(int)grid, SCAN_NT, 0, st>>>(p, rpt);
+  if (p.scan_rpt > 0) rpt = p.scan_rpt < SCAN_RPT ? p.scan_rpt : SCAN_RPT;
+  return rpt;
+}
+
+template <class T>
+static cudaError_t launch_scan_t(const KParams& p, int nsm, cudaStream_t st) {
+  int nb = 0;
+  cudaError_t e;
+  CUtensorMap tm_mask, tm_img;
+  if (scan_tensor_maps<T>(p, tm_mask, tm_img)) {
+    constexpr int smem = tma_smem_bytes<T>();
+    if ((e = cudaFuncSetAttribute(k_scan_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan_tma<T>, SCAN_NT, smem)) != cudaSuccess)
+      return e;
+    const int64_t grid = (int64_t)(nb > 0 ? nb : 1) * nsm;
+    k_scan_tma<T><<<(int)grid, SCAN_NT, smem, st>>>(tm_mask, tm_img, p, scan_rows_per_warp(p, grid));
+    return cudaGetLastError();
+  }
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<T>, SCAN_NT, 0)) != cudaSuccess) return e;
+  const int64_t grid = (int64_t)(nb > 0 ? nb : 1) * nsm;
+  k_scan<T><<<(int)grid, SCAN_NT, 0, st>>>(p, scan_rows_per_warp(p, grid));
   return cudaGetLastError();
 }
 

@@ -100,11 +100,14 @@ def lib() -> ctypes.CDLL:
     L.nyx_autotune.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, vp, P(ctypes.c_int32)]
     L.nyx_set_tuning.argtypes = [vp, P(ctypes.c_int32)]
     L.nyx_get_tuning.argtypes = [vp, P(ctypes.c_int32)]
+    L.nyx_set_scan_staging.argtypes = [vp, ctypes.c_int]
+    L.nyx_get_scan_staging.argtypes = [vp, P(ctypes.c_int)]
     for f in ("nyx_params_default", "nyx_create", "nyx_plan_create", "nyx_num_columns", "nyx_column_name",
               "nyx_count_rois", "nyx_extract", "nyx_sync_status", "nyx_backward", "nyx_debug_select",
               "nyx_debug_glcm", "nyx_debug_bins", "nyx_profile_enable", "nyx_phase_times", "nyx_use_graphs",
               "nyx_graph_captures", "nyx_set_class_limits", "nyx_autotune", "nyx_graph_phase_events",
-              "nyx_graph_phase_times", "nyx_set_tuning", "nyx_get_tuning"):
+              "nyx_graph_phase_times", "nyx_set_tuning", "nyx_get_tuning", "nyx_set_scan_staging",
+              "nyx_get_scan_staging"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -310,9 +313,9 @@ class Extractor:
         self._check(lib().nyx_set_class_limits(self._plan, lim))
 
     def autotune(self, img: torch.Tensor, mask: torch.Tensor, reps: int = 5) -> Tuple[int, ...]:
-        """Time a grid of class limits, then of label-scan tile heights, on
-        this input (L2 flushed before every timed call), keep the fastest;
-        returns (warp, small, medium, large pixel limits, scan rows per warp)."""
+        """Time a grid of class limits, then of label-scan tile heights under
+        both row stagings, on this input (L2 flushed before every timed
+        call), keep the fastest; returns tuning()."""
         img, mask = self._inputs(img, mask)
         table = torch.empty((self.max_rois, len(self.columns)), dtype=torch.float64, device=self.device)
         lim = (ctypes.c_int32 * 4)()
@@ -321,15 +324,24 @@ class Extractor:
         return self.tuning()
 
     def tuning(self) -> Tuple[int, ...]:
-        """(warp, small, medium, large pixel limits, scan rows per warp; 0 =
-        chosen per call)."""
+        """(warp, small, medium, large pixel limits, scan rows per warp (0 =
+        chosen per call), scan staging (0 = bulk tensor copies where the row
+        pitch allows, 1 = register loads))."""
         t = (ctypes.c_int32 * 5)()
         self._check(lib().nyx_get_tuning(self._plan, t))
-        return tuple(int(v) for v in t)
+        g = ctypes.c_int(0)
+        self._check(lib().nyx_get_scan_staging(self._plan, ctypes.byref(g)))
+        return tuple(int(v) for v in t) + (int(g.value),)
 
-    def set_tuning(self, warp: int, small: int, medium: int, large: int, scan_rows: int = 0):
+    def set_tuning(self, warp: int, small: int, medium: int, large: int, scan_rows: int = 0, scan_staging: int = 0):
         t = (ctypes.c_int32 * 5)(warp, small, medium, large, scan_rows)
         self._check(lib().nyx_set_tuning(self._plan, t))
+        self._check(lib().nyx_set_scan_staging(self._plan, int(scan_staging)))
+
+    def set_scan_staging(self, mode: int):
+        """Label-scan row staging: 0 = bulk tensor copies into shared memory
+        where the row pitch allows (default), 1 = register loads."""
+        self._check(lib().nyx_set_scan_staging(self._plan, int(mode)))
 
     def profile(self, slots: int = 1):
         """Record per-phase CUDA events for the next extracts (ring of

@@ -18,6 +18,9 @@ instead profiles one extraction of the named workload per feature
 subset (MEAN alone, then MEAN plus one feature family), with the class
 limits of the hot-path set; the differences of the per-kernel instruction
 counts attribute the fused kernel's work to the families.
+
+    --scan-staging=0|1 overrides the stored label-scan row staging (0 bulk
+    tensor copies where the row pitch allows, 1 register loads).
 """
 from __future__ import annotations
 
@@ -59,7 +62,9 @@ def main(argv=None) -> int:
     argv = sys.argv[1:] if argv is None else argv
     subsets = "--subsets" in argv
     full = "--all" in argv  # the full feature set for the 2048^2 nuclei workload too
-    argv = [a for a in argv if a not in ("--subsets", "--all")]
+    stg = [int(a.split("=", 1)[1]) for a in argv if a.startswith("--scan-staging=")]
+    stg = stg[-1] if stg else None
+    argv = [a for a in argv if a not in ("--subsets", "--all") and not a.startswith("--scan-staging=")]
     names = (argv[0] if argv else "nuclei2d").split(",")
     procs = max(1, min(16, os.cpu_count() or 1))
     # build every workload before the first CUDA call (the mosaic's tiles use spawned processes)
@@ -93,6 +98,9 @@ def main(argv=None) -> int:
                            features=nyx.CORE_FEATURE_IDS if feats == "core" else None)
         sig = tuning.signature(w.image.shape, str(w.image.dtype), w.ndim, prm["glcm_levels"], prm["dists"], feats)
         t, src = tuning.limits_for(ex, dev, sig)
+        if stg is not None:
+            ex.set_scan_staging(stg)
+            t = ex.tuning()
         img, mask = torch.from_numpy(w.image).cuda(), torch.from_numpy(w.mask).cuda()
         bwd = n.startswith("blobbatch")
         table = torch.empty((ex.max_rois, len(ex.columns)), dtype=torch.float64, device="cuda")

@@ -45,7 +45,8 @@ def _read(path: str = TUNED_PATH) -> Dict:
 
 
 def load(device_name: str, sig: str, path: str = TUNED_PATH) -> Optional[Dict]:
-    """The stored entry ({"limits": [w, s, m, l], "scan_rows_per_warp": r, "ms": ...}) or None."""
+    """The stored entry ({"limits": [w, s, m, l], "scan_rows_per_warp": r, "scan_staging": g, "ms": ...})
+    or None."""
     return _read(path).get(device_name, {}).get(sig)
 
 
@@ -98,10 +99,11 @@ def limits_for(ex, device_name: str, sig: str) -> Tuple[Tuple[int, ...], str]:
     one; returns the setting in force and where it came from."""
     ent = load(device_name, sig)
     if ent:
-        t = tuple(int(v) for v in ent["limits"]) + (int(ent.get("scan_rows_per_warp", 0)),)
+        t = tuple(int(v) for v in ent["limits"]) + (int(ent.get("scan_rows_per_warp", 0)),
+                                                      int(ent.get("scan_staging", 0)))
         ex.set_tuning(*t)
         return t, "tuned.json"
-    t = DEFAULT_LIMITS + (0,)
+    t = DEFAULT_LIMITS + (0, 0)
     ex.set_tuning(*t)
     return t, "default"
 
@@ -136,7 +138,8 @@ def main() -> int:
             mask = torch.from_numpy(mask_np).cuda()
             t, ms = tune(ex, img, mask, reps=a.reps)
             sig = signature(img_np.shape, str(img_np.dtype), ndim, prm["glcm_levels"], prm["dists"], feats)
-            store(dev_name, sig, {"limits": list(t[:4]), "scan_rows_per_warp": t[4], "ms": round(ms, 4),
+            store(dev_name, sig, {"limits": list(t[:4]), "scan_rows_per_warp": t[4], "scan_staging": t[5],
+                                  "ms": round(ms, 4),
                                   "how": "nyx_autotune (median of L2-flushed calls per candidate), then the "
                                          "median of 10 L2-flushed graph replays of the choice"})
             print(json.dumps({"workload": name, "features": feats, "tuning": t, "ms": round(ms, 4)}), flush=True)

@@ -253,7 +253,8 @@ def test_graph_replay_matches_direct_launches():
 
 
 @pytest.mark.parametrize("limits", [None, (0, 0, 4096, 0), (128, 0, 0, 8192), (256, 1024, 0, 0), (0, 512, 2048, 8192),
-                                    (64, 512, 2048, 0, 8), (256, 1024, 4096, 8192, 32), (0, 0, 0, 0)])
+                                    (64, 512, 2048, 0, 8), (256, 1024, 4096, 8192, 32), (0, 1024, 4096, 0, 16, 1),
+                                    (0, 0, 0, 0)])
 def test_class_limits_and_autotune_keep_parity(limits):
     """Any class limits (autotuned or set) route ROIs to other kernels; the
     table must still match the oracle.  (256, 1024, 0, 0) sends every ROI
@@ -265,10 +266,10 @@ def test_class_limits_and_autotune_keep_parity(limits):
     if limits is None:
         lim = ex.autotune(img, mask, reps=2)
         assert lim[0] in (0, 64, 128, 256) and lim[1] in (0, 512, 1024) and lim[2] in (0, 2048, 4096)
-        assert lim[3] in (0, 8192) and lim[4] in (8, 16, 32) and ex.tuning() == lim
-    elif len(limits) == 5:  # class limits and the label scan's tile height
+        assert lim[3] in (0, 8192) and lim[4] in (8, 16, 32) and lim[5] in (0, 1) and ex.tuning() == lim
+    elif len(limits) >= 5:  # class limits, the label scan's tile height [and row staging]
         ex.set_tuning(*limits)
-        assert ex.tuning() == limits
+        assert ex.tuning() == (limits + (0,))[:6]
     else:
         ex.set_class_limits(*limits)
     g = gpu_table(ex, img, mask)
