@@ -159,3 +159,60 @@ def test_mosaic_8192_streamed_sampled_parity():
     assert sel.sum() == len(pick)
     fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
     assert not fails, "\n".join(fails[:30])
+
+
+def test_mosaic_32768_full_size_sampled_parity():
+    """The benchmark's streamed-mosaic workload at its full size (32768 x
+    32768 u16, 500,000 placed ROIs, 4096 x 4096 tiles, every feature family)
+    in the benchmark's launch configuration (its stored tuning, the image
+    resident in HBM): the table equals the tile-streamed extraction bit for
+    bit, and a sample of ROIs (tile-border crossers, the largest, the
+    smallest, random ones) matches the oracle, which reads the whole
+    mosaic."""
+    import os
+
+    from paper_2603_12016_gb300 import nyx, tuning
+
+    procs = max(1, min(16, os.cpu_count() or 1))
+    w = W.mosaic_workload("mosaic", 0, procs)  # tiles generated in spawned processes
+    img, mask, prm = w.image, w.mask, w.params
+    n_roi = w.meta["n_roi"]
+    assert img.shape == (32768, 32768) and n_roi > 400_000
+    ex = nyx.Extractor(img.shape, torch.uint16, glcm_levels=prm["glcm_levels"], dists=prm["dists"],
+                       hist_bins=prm["hist_bins"], max_rois=2 * n_roi)
+    sig = tuning.signature(img.shape, str(img.dtype), 2, prm["glcm_levels"], prm["dists"], "all")
+    tuning.limits_for(ex, torch.cuda.get_device_name(0), sig)
+    d_img, d_mask = to_torch(img), to_torch(mask)
+    table = torch.empty((2 * n_roi, len(ex.columns)), dtype=torch.float64, device="cuda")
+    n = ex.extract_into(d_img, d_mask, table)
+    ex.sync_status()
+    assert n == n_roi
+    whole = table[:n].clone()
+    d_img.zero_()
+    d_mask.zero_()
+
+    def tile_source(x0, y0, tw, th):
+        return img[y0:y0 + th, x0:x0 + tw], mask[y0:y0 + th, x0:x0 + tw]
+
+    got = ex.extract_tiles(tile_source, (4096, 4096), d_img, d_mask)
+    assert torch.equal(torch.nan_to_num(got, nan=-7.0), torch.nan_to_num(whole, nan=-7.0))
+    g = _table(ex, whole)
+    del d_img, d_mask, table, got, whole
+    torch.cuda.empty_cache()
+    # the sample, chosen from the mask alone
+    cnt = np.bincount(mask.ravel())
+    labs = np.flatnonzero(cnt[1:]) + 1
+    assert len(labs) == n_roi
+    cross = sorted(_crossing(mask, 4096, 4096))
+    assert len(cross) > 1000
+    rng = np.random.default_rng(11)
+    pick = sorted(set(rng.choice(cross, 24, replace=False).tolist()) |
+                  set(rng.choice(labs, 24, replace=False).tolist()) |
+                  {int(labs[np.argmax(cnt[labs])]), int(labs[np.argmin(cnt[labs])])})
+    lab = g["LABEL"].astype(np.int64)
+    o = oracle.extract(img, mask, 2, ng=prm["glcm_levels"], dists=prm["dists"], hist_bins=prm["hist_bins"],
+                       rois=[oracle.roi_key(0, l) for l in pick], threads=procs, families=("glrlm", "glszm"))
+    sel = np.isin(lab, pick)
+    assert sel.sum() == len(pick)
+    fails = compare({k: v[sel] for k, v in g.items()}, o, 2)
+    assert not fails, "\n".join(fails[:30])
