@@ -353,13 +353,22 @@ struct RzLevel {
 
 // ---- hash tables of items ---------------------------------------------------
 // block path: key (i << 16 | s) (i >= 1, so 0 = empty), n items added
-__device__ inline void rz_insert(unsigned* key, unsigned* cnt, int cap, unsigned k, unsigned n, unsigned* err) {
+// Insert-or-add into a block's joint hash; the thread that claims an empty
+// slot appends its index to the occupied list lst (length *nl, room for
+// lcap), so that the set's per-cell pass visits occupied slots only.
+__device__ inline void rz_insert(unsigned* key, unsigned* cnt, int cap, unsigned k, unsigned n, uint16_t* lst,
+                                 unsigned* nl, unsigned lcap, unsigned* err) {
   unsigned h = ((k * 2654435761u) >> 16) & (unsigned)(cap - 1);
   for (int probe = 0; probe < cap; ++probe) {
     unsigned cur = ((volatile unsigned*)key)[h];
     if (cur == 0) {
       cur = atomicCAS(key + h, 0u, k);
-      if (cur == 0) cur = k;
+      if (cur == 0) {
+        const unsigned at = atomicAdd(nl, 1u);
+        if (at < lcap) lst[at] = (uint16_t)h;
+        else atomicOr(err, E_INTERNAL);
+        cur = k;
+      }
     }
     if (cur == k) {
       atomicAdd(cnt + h, n);
@@ -524,7 +533,7 @@ __device__ inline void rzg_union(unsigned* par, unsigned a, unsigned b, unsigned
 // zone areas (two 16-bit counters a word) while the zones are counted.
 template <class Z>
 constexpr int rz_smem_bytes() {
-  return 4 * Z::CELLS + 8 * Z::HC;
+  return 4 * Z::CELLS + 8 * Z::HC + 2 * (Z::HC / 2);
 }
 
 // Set k's reduced values land in red[k] (GLRLM directions 0..ND-1, zones
@@ -542,6 +551,7 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
   unsigned* hkey = (unsigned*)(par + Z::CELLS);
   unsigned* hcnt = hkey + Z::HC;
   unsigned* zw = hkey;
+  uint16_t* slst = (uint16_t*)(hcnt + Z::HC);  // occupied joint-hash slots of the current set
   __shared__ unsigned lvl_n[256];
   __shared__ rz_u64 lvl_a[256];
   __shared__ unsigned hs_key[Z::HS], hs_cnt[Z::HS];
@@ -568,45 +578,20 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
     hkey[i] = 0;
     hcnt[i] = 0;
   }
-  // the occupied cells of the joint hash: first compacted (and cleared) into
-  // a dense (key, count) list in the parent array's words, which no set
-  // needs while its items are reduced, so that the per-cell work runs on
-  // full warps; then handed to f
-  // (a set has at most HC / 2 distinct keys, the hashes' load bound)
-  unsigned* lst = (unsigned*)par;
-  static_assert(2 * Z::CELLS >= 8 * (Z::HC / 2), "HC / 2 compacted cells fit in the parent array");
+  // the occupied cells of the joint hash, from the list of slots their
+  // inserts claimed (a set has at most HC / 2 distinct keys, the hashes'
+  // load bound): each is cleared and handed to f
   __shared__ unsigned s_nl;  // list length; 0 whenever a set starts (reset once every thread has read it)
   if (tid == 0) s_nl = 0;
   int hc = Z::HC;  // hash slots this ROI uses (set per ROI)
   auto joint = [&](auto f) {
-    const int lane = tid & 31;
-    for (int h0 = 0; h0 < hc; h0 += Z::NT) {
-      const int h = h0 + tid;
-      const unsigned k = h < hc ? hkey[h] : 0u;
-      const unsigned c = k ? hcnt[h] : 0u;
-      if (k) {
-        hkey[h] = 0;
-        hcnt[h] = 0;
-      }
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, k != 0);
-      unsigned base = 0;
-      if (lane == 0 && bal) base = atomicAdd(&s_nl, (unsigned)__popc(bal));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (k) {
-        const unsigned at = base + __popc(bal & ((1u << lane) - 1u));
-        if (at < (unsigned)(Z::HC / 2)) {
-          lst[2 * at] = k;
-          lst[2 * at + 1] = c;
-        } else {
-          atomicOr(p.err, E_INTERNAL);
-        }
-      }
-    }
-    __syncthreads();
     const unsigned nl = min(s_nl, (unsigned)(Z::HC / 2));
     for (unsigned i = tid; i < nl; i += Z::NT) {
-      const unsigned k = lst[2 * i];
-      f(k >> 16, (rz_u64)(k & 0xFFFFu), lst[2 * i + 1]);
+      const unsigned h = slst[i];
+      const unsigned k = hkey[h], c = hcnt[h];
+      hkey[h] = 0;
+      hcnt[h] = 0;
+      f(k >> 16, (rz_u64)(k & 0xFFFFu), c);
     }
   };
   for (;;) {
@@ -692,7 +677,7 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
           if (!L || rast[c - dv] == L) continue;  // not a run start (the border stops every walk)
           unsigned len = 1;
           for (int q = c + dv; rast[q] == L; q += dv) ++len;
-          rz_insert(hkey, hcnt, hc, (L << 16) | len, 1u, p.err);
+          rz_insert(hkey, hcnt, hc, (L << 16) | len, 1u, slst, &s_nl, Z::HC / 2, p.err);
         }
         __syncthreads();  // also: the previous set's marginal pass is done with lvl / hs
         reduce_set(k);
@@ -739,7 +724,9 @@ __global__ void __launch_bounds__(Z::NT) k_rz(KParams p, int tier) {
       }
       __syncthreads();
       for (int c = tid; c < cells; c += Z::NT)
-        if (rast[c] & 0x8000) rz_insert(hkey, hcnt, hc, ((unsigned)(rast[c] & 0x1FF) << 16) | par[c], 1u, p.err);
+        if (rast[c] & 0x8000)
+          rz_insert(hkey, hcnt, hc, ((unsigned)(rast[c] & 0x1FF) << 16) | par[c], 1u, slst, &s_nl, Z::HC / 2,
+                    p.err);
       __syncthreads();
       reduce_set(ND);
     }
