@@ -128,12 +128,12 @@ class ClockSampler:
 # a memset ncu does not list).  The 32768^2 mosaic is scaled from the 8192^2
 # mosaic: kernel bytes by ROI pixels (565.05M / 36.02M), the clear by
 # image pixels.
-TRAFFIC_SRC = "bbe497d3d8558cce"
+TRAFFIC_SRC = "5c8e901f3cf897dd"
 TRAFFIC = {
-    ("nuclei2d_2048_u16_4000roi", "roi_stage", (256, 1024, 4096, 8192, 8, 1), "core"): 36.25e6,
-    ("ct3d_512x512x128_i16_200roi", "roi_stage", (0, 1024, 2048, 8192, 32, 0), "all"): 3530.86e6 + 12 * 512 * 512 * 128,
-    ("blobbatch_64x512_f32", "roi_stage", (0, 1024, 4096, 8192, 16, 0), "all"): 108.18e6,
-    ("mosaic_32768_u16_500000roi", "roi_stage", (0, 512, 4096, 8192, 32, 0), "all"): 1337.55e6 * 565.05 / 36.02
+    ("nuclei2d_2048_u16_4000roi", "roi_stage", (256, 1024, 4096, 8192, 8, 1), "core"): 36.27e6,
+    ("ct3d_512x512x128_i16_200roi", "roi_stage", (0, 1024, 2048, 8192, 32, 0), "all"): 3559.32e6 + 12 * 512 * 512 * 128,
+    ("blobbatch_64x512_f32", "roi_stage", (0, 1024, 4096, 8192, 16, 0), "all"): 108.17e6,
+    ("mosaic_32768_u16_500000roi", "roi_stage", (0, 512, 4096, 8192, 32, 0), "all"): 1339.65e6 * 565.05 / 36.02
     + 12 * 32768 * 32768,
 }
 

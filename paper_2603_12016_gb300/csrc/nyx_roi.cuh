@@ -556,7 +556,7 @@ __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row
   if (o >= 2) putA(p, row, Q_MOM + (wbase + F_ETA) * 20 + lane, valid ? mu / norm_pow<NDIM>(mu00, o) : nan);
   if (NDIM == 2) putA(p, row, Q_MOM + (wbase + F_NU) * 20 + lane, valid ? M / norm_pow<NDIM>(mu00, o) : nan);
   if (save_mu) save_mu[lane] = to_d(mu);
-  if (NDIM == 2 && lane == 0) {
+  if (NDIM == 2) {  // every active lane computes the invariants, lane i stores the i-th
     const A g20 = norm_pow<2>(mu00, 2), g30 = norm_pow<2>(mu00, 3);
     const A e20 = m20 / g20, e02 = m02 / g20, e11 = m11 / g20;
     // scale lambda = 2^k close to eta20 + eta02: eta_o / lambda^(o/2) = O(1)
@@ -579,19 +579,27 @@ __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row
     }
     A h[7];
     hu7<A>(e20 * il, e02 * il, e11 * il, m30 / g30 * il15, m21 / g30 * il15, m12 / g30 * il15, m03 / g30 * il15, h);
-    const int deg[7] = {1, 2, 3, 3, 6, 4, 6};  // degree of each invariant in eta20-like units
-    for (int i = 0; i < 7; ++i) {
+    constexpr int deg[7] = {1, 2, 3, 3, 6, 4, 6};  // degree of each invariant in eta20-like units
+    A hm = 0;
+    int dm = 0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+      if (lane == i) {
+        hm = h[i];
+        dm = deg[i];
+      }
+    if (lane < 7) {
       double v;
-      if constexpr (std::is_same<A, float>::value) v = f2d_scaled(h[i], k * deg[i]);
-      else v = ldexp(h[i], k * deg[i]);
-      put(p, row, Q_MOM + (wbase + F_HU) * 20 + i, valid ? v : to_d(nan));
+      if constexpr (std::is_same<A, float>::value) v = f2d_scaled(hm, k * dm);
+      else v = ldexp(hm, k * dm);
+      put(p, row, Q_MOM + (wbase + F_HU) * 20 + lane, valid ? v : to_d(nan));
     }
   }
 }
 
 // Statistics of Table S1 / S5 from the centred power sums S_k = sum (I - c)^k
 // about a centring point c close to the mean; the residual offset S_1 / n is
-// removed by a binomial shift.
+// removed by a binomial shift.  Called by all 32 lanes of a warp.
 template <class T, int NDIM, class A>
 __device__ __noinline__ void finalize_stats(const KParams& p, double* row, const A* res_st, int n, A mean, A sumI,
                                             A energy, unsigned vmin, unsigned vmax, int64_t bimg, int x0, int y0,
@@ -614,38 +622,64 @@ __device__ __noinline__ void finalize_stats(const KParams& p, double* row, const
   const A sd = asqrt(var);
   const A mn = decA<T, A>(vmin), mx = decA<T, A>(vmax);
   const A imn = decA<T, A>(p.img_vmin[bimg]), imx = decA<T, A>(p.img_vmax[bimg]);
-  putA(p, row, Q_STATS + S_MEAN, mean);
-  putA(p, row, Q_STATS + S_VAR, var);
-  putA(p, row, Q_STATS + S_VAR_B, m2);
-  putA(p, row, Q_STATS + S_STD, sd);
-  putA(p, row, Q_STATS + S_STD_B, asqrt(m2));
   const bool pos = m2 > 0;
   const A kurt = pos ? m[4] / (m2 * m2) : (A)0;
-  putA(p, row, Q_STATS + S_SKEW, pos ? m[3] / (m2 * asqrt(m2)) : (A)0);
-  putA(p, row, Q_STATS + S_KURT, kurt);
-  putA(p, row, Q_STATS + S_EXKURT, pos ? kurt - 3 : (A)0);
-  putA(p, row, Q_STATS + S_HSKEW, pos ? m[5] / (m2 * m2 * asqrt(m2)) : (A)0);
-  putA(p, row, Q_STATS + S_HFLAT, pos ? m[6] / (m2 * m2 * m2) : (A)0);
-  putA(p, row, Q_STATS + S_RMS, asqrt(energy / nA));
-  putA(p, row, Q_STATS + S_SE, sd / asqrt(nA));
-  putA(p, row, Q_STATS + S_MAD, res_st[6] / nA);
-  putA(p, row, Q_STATS + S_COV, mean != 0 ? sd / mean : nan);
-  putA(p, row, Q_STATS + S_COVERED, imx != imn ? (mx - mn) / (imx - imn) : nan);
-  putA(p, row, Q_STATS + S_PIU, (mx + mn) != 0 ? (A)100 * ((A)1 - (mx - mn) / (mx + mn)) : nan);
+  // every lane of the warp computes every value; lane j stores value j, so
+  // the columns leave in one warp-wide store instead of one after another
+  constexpr int NA = 16;
+  const A va[NA] = {mean,
+                    var,
+                    m2,
+                    sd,
+                    asqrt(m2),
+                    pos ? m[3] / (m2 * asqrt(m2)) : (A)0,
+                    kurt,
+                    pos ? kurt - 3 : (A)0,
+                    pos ? m[5] / (m2 * m2 * asqrt(m2)) : (A)0,
+                    pos ? m[6] / (m2 * m2 * m2) : (A)0,
+                    asqrt(energy / nA),
+                    sd / asqrt(nA),
+                    res_st[6] / nA,
+                    mean != 0 ? sd / mean : nan,
+                    imx != imn ? (mx - mn) / (imx - imn) : nan,
+                    (mx + mn) != 0 ? (A)100 * ((A)1 - (mx - mn) / (mx + mn)) : nan};
+  constexpr int qa[NA] = {S_MEAN, S_VAR, S_VAR_B, S_STD, S_STD_B, S_SKEW, S_KURT, S_EXKURT,
+                          S_HSKEW, S_HFLAT, S_RMS, S_SE, S_MAD, S_COV, S_COVERED, S_PIU};
   // centroids in image coordinates: integer origin + the FP64 local centroid;
   // the mass displacement is the FP64 distance of the two centroids, which
   // nearly coincide in symmetric ROIs (an FP32 difference would keep few
   // digits of it)
-  put(p, row, Q_CEN_X, i2d(x0) + cd[3]);
-  put(p, row, Q_CEN_Y, i2d(y0) + cd[4]);
-  put(p, row, Q_CEN_Z, i2d(z0) + cd[5]);
-  put(p, row, Q_STATS + S_WCX, wvalid ? i2d(x0) + cd[0] : to_d(nan));
-  put(p, row, Q_STATS + S_WCY, wvalid ? i2d(y0) + cd[1] : to_d(nan));
-  put(p, row, Q_STATS + S_WCZ, wvalid ? i2d(z0) + cd[2] : to_d(nan));
   double md = (cd[0] - cd[3]) * (cd[0] - cd[3]) + (cd[1] - cd[4]) * (cd[1] - cd[4]);
   if (NDIM == 3) md += (cd[2] - cd[5]) * (cd[2] - cd[5]);
-  put(p, row, Q_STATS + S_MD, wvalid ? sqrt(md) : to_d(nan));
-  if (save) {
+  constexpr int ND = 7;
+  const double vd[ND] = {i2d(x0) + cd[3],
+                         i2d(y0) + cd[4],
+                         i2d(z0) + cd[5],
+                         wvalid ? i2d(x0) + cd[0] : to_d(nan),
+                         wvalid ? i2d(y0) + cd[1] : to_d(nan),
+                         wvalid ? i2d(z0) + cd[2] : to_d(nan),
+                         wvalid ? sqrt(md) : to_d(nan)};
+  constexpr int qd[ND] = {Q_CEN_X, Q_CEN_Y, Q_CEN_Z, Q_STATS + S_WCX, Q_STATS + S_WCY, Q_STATS + S_WCZ,
+                          Q_STATS + S_MD};
+  const int lane = threadIdx.x & 31;
+  A a_mine = 0;
+  double d_mine = 0;
+  int q_mine = -1;
+#pragma unroll
+  for (int j = 0; j < NA; ++j)
+    if (lane == j) {
+      a_mine = va[j];
+      q_mine = Q_STATS + qa[j];
+    }
+#pragma unroll
+  for (int j = 0; j < ND; ++j)
+    if (lane == NA + j) q_mine = qd[j];
+#pragma unroll
+  for (int j = 0; j < ND; ++j)
+    if (lane == NA + j) d_mine = vd[j];
+  if (lane < NA) putA(p, row, q_mine, a_mine);
+  else if (q_mine >= 0) put(p, row, q_mine, d_mine);
+  if (save && lane == 0) {
     save[SV_N] = i2d(n);
     save[SV_MEAN] = to_d(mean);
     for (int k = 2; k <= 6; ++k) save[SV_M2 + k - 2] = to_d(m[k]);
@@ -2230,10 +2264,10 @@ cudaError_t launch_roi_one(const KParams& p, int cls, int nsm, cudaStream_t st) 
 
 // First-order statistics (Table S1/S5), moments and Hu invariants (Table S2,
 // S5) of every ROI from the sums its accumulation kernel left in sacc: one
-// warp per ROI (lane 0 the statistics, lanes 0..NM-1 the moments).
+// warp per ROI (the statistics one column per lane, lanes 0..NM-1 the
+// moments).
 template <class T, int NDIM, class A>
 __global__ void __launch_bounds__(256) k_stats_final(KParams p) {
-  const int lane = threadIdx.x & 31;
   const int64_t nroi = min((int64_t)*p.n_roi, p.cap_roi);
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < nroi; item += nw) {
@@ -2243,9 +2277,8 @@ __global__ void __launch_bounds__(256) k_stats_final(KParams p) {
     double* save = (p.need & NEED_SAVE) ? p.saved + item * SV_WORDS : nullptr;
     const bool wvalid = g[49] != (A)0;
     const double* cd = (const double*)(p.sacc + (size_t)item * SACC_BYTES + SACC_CD);
-    if (lane == 0)
-      finalize_stats<T, NDIM, A>(p, row, g, (int)r.n, g[48], g[49], g[50], r.vmin, r.vmax, (int64_t)(r.key >> 32),
-                                 r.x0, r.y0, r.z0, cd, wvalid, save);
+    finalize_stats<T, NDIM, A>(p, row, g, (int)r.n, g[48], g[49], g[50], r.vmin, r.vmax, (int64_t)(r.key >> 32),
+                               r.x0, r.y0, r.z0, cd, wvalid, save);
     if (p.need & (NEED_MOM_INT | NEED_SAVE))
       finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], cd, to_d(g[49]), wvalid,
                                      save ? save + SV_MU : nullptr);
