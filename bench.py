@@ -128,12 +128,12 @@ class ClockSampler:
 # a memset ncu does not list).  The 32768^2 mosaic is scaled from the 8192^2
 # mosaic: kernel bytes by ROI pixels (565.05M / 36.02M), the clear by
 # image pixels.
-TRAFFIC_SRC = "5c8e901f3cf897dd"
+TRAFFIC_SRC = "c39cc1dc7bf2efff"
 TRAFFIC = {
-    ("nuclei2d_2048_u16_4000roi", "roi_stage", (256, 1024, 4096, 8192, 8, 1), "core"): 36.27e6,
-    ("ct3d_512x512x128_i16_200roi", "roi_stage", (0, 1024, 2048, 8192, 32, 0), "all"): 3559.32e6 + 12 * 512 * 512 * 128,
-    ("blobbatch_64x512_f32", "roi_stage", (0, 1024, 4096, 8192, 16, 0), "all"): 108.17e6,
-    ("mosaic_32768_u16_500000roi", "roi_stage", (0, 512, 4096, 8192, 32, 0), "all"): 1339.65e6 * 565.05 / 36.02
+    ("nuclei2d_2048_u16_4000roi", "roi_stage", (256, 1024, 4096, 8192, 8, 1), "core"): 36.26e6,
+    ("ct3d_512x512x128_i16_200roi", "roi_stage", (0, 1024, 2048, 8192, 32, 0), "all"): 3527.77e6 + 12 * 512 * 512 * 128,
+    ("blobbatch_64x512_f32", "roi_stage", (0, 1024, 4096, 8192, 16, 0), "all"): 108.23e6,
+    ("mosaic_32768_u16_500000roi", "roi_stage", (0, 512, 4096, 8192, 32, 0), "all"): 1335.98e6 * 565.05 / 36.02
     + 12 * 32768 * 32768,
 }
 

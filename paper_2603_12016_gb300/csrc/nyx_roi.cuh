@@ -517,10 +517,11 @@ __device__ inline A norm_pow(A m00, int o) {
 // FP32.
 template <int NDIM, class A>
 __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row, int wbase, const A* Cs, A s0, A s1,
-                                                   A s2, const double* ci, double W, bool valid, double* save_mu) {
+                                                   A s2, const double* ci, double W, bool valid, double* save_mu,
+                                                   bool on = true, int lb = 0) {
   constexpr int NM = NDIM == 3 ? 20 : 10;
-  const int lane = threadIdx.x & 31;
-  const bool act = lane < NM;
+  const int lane = (int)(threadIdx.x & 31) - lb;  // index within this lane's group of moments
+  const bool act = on && lane >= 0 && lane < NM;
   const A nan = anan<A>();
   int a = 0, b = 0, c = 0;
   if (act) mexp<NDIM>(lane, a, b, c);
@@ -545,10 +546,13 @@ __device__ __noinline__ void finalize_moments_warp(const KParams& p, double* row
         }
   if (o == 1) mu = 0;  // first-order central moments vanish at the centroid
   // the central moments the Hu invariants need, from their lanes
-  const A m20 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(2, 0, 0)), m02 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(0, 2, 0)),
-          m11 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(1, 1, 0)), m30 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(3, 0, 0)),
-          m21 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(2, 1, 0)), m12 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(1, 2, 0)),
-          m03 = __shfl_sync(0xFFFFFFFFu, mu, midx<NDIM>(0, 3, 0));
+  const A m20 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(2, 0, 0)),
+          m02 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(0, 2, 0)),
+          m11 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(1, 1, 0)),
+          m30 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(3, 0, 0)),
+          m21 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(2, 1, 0)),
+          m12 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(1, 2, 0)),
+          m03 = __shfl_sync(0xFFFFFFFFu, mu, lb + midx<NDIM>(0, 3, 0));
   if (!act) return;
   const A mu00 = Cs[0];
   putA(p, row, Q_MOM + (wbase + F_M) * 20 + lane, M);
@@ -2279,11 +2283,21 @@ __global__ void __launch_bounds__(256) k_stats_final(KParams p) {
     const double* cd = (const double*)(p.sacc + (size_t)item * SACC_BYTES + SACC_CD);
     finalize_stats<T, NDIM, A>(p, row, g, (int)r.n, g[48], g[49], g[50], r.vmin, r.vmax, (int64_t)(r.key >> 32),
                                r.x0, r.y0, r.z0, cd, wvalid, save);
-    if (p.need & (NEED_MOM_INT | NEED_SAVE))
-      finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], cd, to_d(g[49]), wvalid,
-                                     save ? save + SV_MU : nullptr);
-    if (p.need & NEED_MOM_BIN)
-      finalize_moments_warp<NDIM, A>(p, row, 5, g + 28, g[54], g[55], g[56], cd + 3, (double)r.n, true, nullptr);
+    const bool need_int = (p.need & (NEED_MOM_INT | NEED_SAVE)) != 0, need_bin = (p.need & NEED_MOM_BIN) != 0;
+    if (NDIM == 2) {  // both weightings at once: intensity on lanes 0..15, binary on lanes 16..31
+      const bool hb = (threadIdx.x & 16) != 0;
+      if (need_int || need_bin)
+        finalize_moments_warp<NDIM, A>(p, row, hb ? 5 : 0, g + (hb ? 28 : 8), hb ? g[54] : g[51], hb ? g[55] : g[52],
+                                       hb ? g[56] : g[53], hb ? cd + 3 : cd, hb ? (double)r.n : to_d(g[49]),
+                                       hb || wvalid, hb || !save ? nullptr : save + SV_MU, hb ? need_bin : need_int,
+                                       hb ? 16 : 0);
+    } else {
+      if (need_int)
+        finalize_moments_warp<NDIM, A>(p, row, 0, g + 8, g[51], g[52], g[53], cd, to_d(g[49]), wvalid,
+                                       save ? save + SV_MU : nullptr);
+      if (need_bin)
+        finalize_moments_warp<NDIM, A>(p, row, 5, g + 28, g[54], g[55], g[56], cd + 3, (double)r.n, true, nullptr);
+    }
   }
 }
 
