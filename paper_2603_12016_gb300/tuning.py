@@ -5,7 +5,8 @@ block, a medium block, several blocks per ROI).  Which ROI goes to which
 class is decided by pixel limits; the best limits depend on the GPU and on
 the workload's ROI size distribution ("Results, Scalability": ROI size decides
 where a GPU pays off).  The label scan's tile shape (128 columns by 64, 128
-or 256 rows) is the other tuned launch parameter.  `tune` runs the library's
+or 256 rows) and how it stages its rows (bulk tensor copies or register
+loads) are the other tuned launch parameters.  `tune` runs the library's
 autotuner (nyx_autotune: every candidate timed with the L2 cache flushed
 before each call) on a given input.  Results are stored in tuned.json next to
 this file, keyed by the device name and a workload signature (image shape,
