@@ -529,8 +529,9 @@ __device__ inline void rzg_union(unsigned* par, unsigned a, unsigned b, unsigned
 
 // ---- block path ------------------------------------------------------------
 // Dynamic shared memory: level raster (u16, CELLS), union-find parents (u16,
-// CELLS), then the joint hash (HC keys, HC counts), whose words hold the
-// zone areas (two 16-bit counters a word) while the zones are counted.
+// CELLS), the joint hash (HC keys, HC counts), whose words hold the zone
+// areas (two 16-bit counters a word) while the zones are counted, then the
+// list of occupied hash slots (u16, HC / 2).
 template <class Z>
 constexpr int rz_smem_bytes() {
   return 4 * Z::CELLS + 8 * Z::HC + 2 * (Z::HC / 2);
